@@ -1,0 +1,152 @@
+"""Seeded synthetic inputs shared by the tests, the benchmark and the smoke check.
+
+This module holds problem descriptions and the design-field generator only: no
+step of the lattice kinetic scheme or its adjoint lives here.  Both the CUDA
+library and the CPU oracle receive what this module produces.
+
+Design field recipe (all 2-D workloads):
+  1. u ~ U[0, 1) on the node lattice from numpy's PCG64 ``default_rng(seed)``;
+  2. separable Gaussian filter, sigma = ``sigma`` nodes, truncated at 3 sigma,
+     reflecting edges;
+  3. standardise to z (mean 0, std 1);
+  4. gamma = clip(0.5 + 0.5 z, 0, 1);
+  5. gamma = 1 on the non-design strips: ``strip`` node columns at the inlet and
+     at the outlet, and every edge node.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field, asdict, replace
+from typing import List
+
+import numpy as np
+
+T_FIXED = 0
+T_FLUX = 1
+
+
+def _gauss1d(a: np.ndarray, sigma: float, axis: int) -> np.ndarray:
+    """Gaussian smoothing along one axis, truncated at 3 sigma, reflecting edges
+    (the edge sample is repeated, as in scipy's 'reflect' mode)."""
+    r = int(3.0 * sigma + 0.5)
+    x = np.arange(-r, r + 1, dtype=np.float64)
+    k = np.exp(-0.5 * (x / sigma) ** 2)
+    k /= k.sum()
+    pad = [(0, 0)] * a.ndim
+    pad[axis] = (r, r)
+    ap = np.pad(a, pad, mode="symmetric")
+    out = np.zeros_like(a)
+    n = a.shape[axis]
+    for q, kq in enumerate(k):
+        sl = [slice(None)] * a.ndim
+        sl[axis] = slice(q, q + n)
+        out += kq * ap[tuple(sl)]
+    return out
+
+
+def gamma_field(nx: int, ny: int, seed: int, sigma: float = 4.0, strip: int = 4) -> np.ndarray:
+    """Seeded smoothed-noise design field, shape (ny, nx), float64 in [0, 1]."""
+    rng = np.random.default_rng(seed)
+    noise = rng.random((ny, nx))
+    s = _gauss1d(_gauss1d(noise, sigma, 0), sigma, 1)
+    z = (s - s.mean()) / max(float(s.std()), 1e-300)
+    g = np.clip(0.5 + 0.5 * z, 0.0, 1.0)
+    g[:, :strip] = 1.0
+    g[:, nx - strip:] = 1.0
+    g[0, :] = 1.0
+    g[-1, :] = 1.0
+    g[:, 0] = 1.0
+    g[:, -1] = 1.0
+    return g
+
+
+@dataclass
+class Problem:
+    """One 2-D channel / box problem (lattice units, dx = dt = 1)."""
+
+    nx: int
+    ny: int
+    nu: float
+    alpha_bar: float
+    q_alpha: float = 0.1
+    u_max: float = 0.05
+    pulse_mean: float = 1.0
+    pulse_amp: float = 0.0
+    pulse_period: float = 0.0
+    in_y0: int = 0
+    in_y1: int = -1          # -1: ny - 1
+    out_y0: int = 1
+    out_y1: int = -2         # -2: ny - 2
+    rho_out: float = 1.0
+    thermal: int = 0
+    K_f: float = 0.0
+    K_s: float = 0.0
+    q_K: float = 0.1
+    t_kind: List[int] = field(default_factory=lambda: [T_FIXED, T_FLUX, T_FIXED, T_FLUX])
+    t_val: List[float] = field(default_factory=lambda: [0.0, 0.0, 1.0, 0.0])
+    kappa_T: float = 0.0
+    steady: bool = True
+    n_steps: int = 1000
+    n_adj: int = 1000
+    seed: int = 1
+    sigma: float = 4.0
+    strip: int = 4
+
+    def __post_init__(self):
+        if self.in_y1 < 0:
+            self.in_y1 = self.ny + self.in_y1
+        if self.out_y1 < 0:
+            self.out_y1 = self.ny + self.out_y1
+
+    @property
+    def n_nodes(self) -> int:
+        return self.nx * self.ny
+
+    def gamma(self) -> np.ndarray:
+        return gamma_field(self.nx, self.ny, self.seed, self.sigma, self.strip)
+
+    def with_(self, **kw) -> "Problem":
+        return replace(self, **kw)
+
+    def as_dict(self) -> dict:
+        return asdict(self)
+
+
+def channel(nx: int, ny: int, Re: float, u_max: float = 0.05, **kw) -> Problem:
+    """Channel with a parabolic inlet over the whole left edge, pressure outlet on
+    the right edge, no-slip walls top and bottom.  nu = u_max L / Re with L the
+    inlet width in lattice units (ny - 1); alpha_bar = 1e3 nu."""
+    L = ny - 1
+    nu = u_max * L / Re
+    kw.setdefault("alpha_bar", 1e3 * nu)
+    return Problem(nx=nx, ny=ny, nu=nu, u_max=u_max, **kw)
+
+
+def config1() -> Problem:
+    """64x64 steady channel, Re = 10, 5000 forward + 5000 adjoint steps."""
+    return channel(64, 64, Re=10.0, seed=1, n_steps=5000, n_adj=5000)
+
+
+def config2() -> Problem:
+    """512x256 steady channel, Re = 100, 20000 forward + 20000 adjoint steps."""
+    return channel(512, 256, Re=100.0, seed=2, n_steps=20000, n_adj=20000)
+
+
+def config3() -> Problem:
+    """1024x512 unsteady thermal channel, Re = 200, Pr = 0.71, heated bottom wall,
+    pulsed inlet u_max (0.75 + 0.25 sin(2 pi t / 2000)), 20000 steps."""
+    p = channel(1024, 512, Re=200.0, seed=3, steady=False, n_steps=20000, n_adj=20000,
+                pulse_mean=0.75, pulse_amp=0.25, pulse_period=2000.0, thermal=1,
+                kappa_T=1e-4)
+    p.K_f = p.nu / 0.71
+    p.K_s = p.K_f
+    return p
+
+
+def roofline2d(n: int = 8192) -> Problem:
+    """Large 2-D steady channel used to load HBM (working set >> L2)."""
+    return channel(n, n, Re=100.0 * (n - 1) / 255.0, seed=6, n_steps=200, n_adj=200)
+
+
+def poiseuille(nx: int = 33, ny: int = 17, nu: float = 0.1, u_max: float = 0.02) -> Problem:
+    """Empty channel (gamma = 1 everywhere) for the Poiseuille pin."""
+    return Problem(nx=nx, ny=ny, nu=nu, alpha_bar=1e3 * nu, u_max=u_max)

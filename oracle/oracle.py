@@ -1,0 +1,297 @@
+"""ctypes front end of the FP64 CPU oracle (``lks_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test-suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers.  Nothing in the product package may import
+this module.
+
+Every function here only marshals arrays into the C oracle and strings its steps
+together in the order of the paper's procedure (Sec. 2.7, Steps 2-5):
+state by LKS, objective, adjoint by ALKS, sensitivity.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "lks_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "liblks_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NADJ = 9
+ADJ_NAMES = ("rho_t", "ux_t", "uy_t", "sxx_t", "sxy_t", "syy_t", "T_t", "qx_t", "qy_t")
+
+
+class OrcProblem(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int),
+        ("nu", C.c_double),
+        ("alpha_bar", C.c_double), ("q_alpha", C.c_double),
+        ("u_max", C.c_double),
+        ("pulse_mean", C.c_double), ("pulse_amp", C.c_double), ("pulse_period", C.c_double),
+        ("in_y0", C.c_int), ("in_y1", C.c_int),
+        ("out_y0", C.c_int), ("out_y1", C.c_int),
+        ("rho_out", C.c_double),
+        ("thermal", C.c_int),
+        ("K_f", C.c_double), ("K_s", C.c_double), ("q_K", C.c_double),
+        ("t_kind", C.c_int * 4),
+        ("t_val", C.c_double * 4),
+        ("kappa_T", C.c_double),
+    ]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with gcc (FP64, OpenMP).  Returns the library path."""
+    with _lock:
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+            return _LIB
+        os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+        tmp = _LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
+               "-o", tmp, _SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+        return _LIB
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        P = C.POINTER(C.c_double)
+        PP = C.POINTER(P)
+        prob = C.POINTER(OrcProblem)
+        L.orc_forward_node.argtypes = [prob, P, C.c_double, P, P, P, P, C.c_int, C.c_int, P]
+        L.orc_forward_step.argtypes = [prob, P, C.c_double, P, P, P, P, P, P, P, P]
+        L.orc_objective.argtypes = [prob, P, P, P, P]
+        L.orc_objective.restype = C.c_double
+        L.orc_dJdu_node.argtypes = [prob, P, P, P, C.c_int, C.c_int, P, P]
+        L.orc_bc_flow.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                  C.POINTER(C.c_int), P, P]
+        L.orc_bc_thermal.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
+                                     C.POINTER(C.c_int), P, P]
+        L.orc_adjoint_step.argtypes = [prob, P, P, P, P, P, P, PP, PP, P]
+        L.orc_sensitivity_accum.argtypes = [prob, P, P, P, P, PP, P]
+        L.orc_forward.argtypes = [prob, P, C.c_int, C.c_int, P, P, P, P, P, P]
+        L.orc_forward.restype = C.c_double
+        L.orc_steady_adjoint.argtypes = [prob, P, P, P, P, C.c_int, P, P]
+        L.orc_steady_adjoint.restype = C.c_double
+        L.orc_unsteady_adjoint.argtypes = [prob, P, C.c_int, P, P, P]
+        L.orc_set_threads.argtypes = [C.c_int]
+        L.orc_get_threads.restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def set_threads(n: int) -> None:
+    lib().orc_set_threads(int(n))
+
+
+def get_threads() -> int:
+    return int(lib().orc_get_threads())
+
+
+def _p(a: np.ndarray):
+    assert a.dtype == np.float64 and a.flags.c_contiguous
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _pp(arrs):
+    P = C.POINTER(C.c_double)
+    return (P * len(arrs))(*[_p(a) for a in arrs])
+
+
+def make_problem(pb) -> OrcProblem:
+    """OrcProblem from an ``inputs.Problem`` (or any object with the same fields)."""
+    s = OrcProblem()
+    for name, _ in OrcProblem._fields_:
+        if name in ("t_kind", "t_val"):
+            continue
+        setattr(s, name, type(getattr(s, name))(getattr(pb, name)))
+    for e in range(4):
+        s.t_kind[e] = int(pb.t_kind[e])
+        s.t_val[e] = float(pb.t_val[e])
+    return s
+
+
+class State:
+    """rho, u, v, T fields, each (ny, nx) float64."""
+
+    def __init__(self, ny: int, nx: int):
+        self.rho = np.ones((ny, nx))
+        self.u = np.zeros((ny, nx))
+        self.v = np.zeros((ny, nx))
+        self.T = np.zeros((ny, nx))
+
+    def copy(self) -> "State":
+        s = State(*self.rho.shape)
+        s.rho, s.u, s.v, s.T = self.rho.copy(), self.u.copy(), self.v.copy(), self.T.copy()
+        return s
+
+
+def _g(gamma):
+    return np.ascontiguousarray(gamma, dtype=np.float64)
+
+
+def forward(pb, gamma: np.ndarray, n_steps: int, state: Optional[State] = None, t0: int = 0,
+            traj: bool = False, accumulate_J: bool = False):
+    """LKS march (Step 2).  Returns (state, residual, traj or None, J_sum)."""
+    L = lib()
+    prob = make_problem(pb)
+    g = _g(gamma)
+    st = state.copy() if state is not None else State(pb.ny, pb.nx)
+    tr = np.zeros((n_steps + 1, 3, pb.ny, pb.nx)) if traj else None
+    Jacc = C.c_double(0.0)
+    res = L.orc_forward(C.byref(prob), _p(g), int(t0), int(n_steps), _p(st.rho), _p(st.u),
+                        _p(st.v), _p(st.T), _p(tr) if traj else None,
+                        C.byref(Jacc) if accumulate_J else None)
+    return st, res, tr, Jacc.value
+
+
+def forward_to_steady(pb, gamma, tol=1e-13, max_steps=200000, chunk=500, state=None):
+    """LKS march until max |u(t) - u(t-1)| < tol (or max_steps)."""
+    st = state
+    done = 0
+    res = np.inf
+    while done < max_steps:
+        st, res, _, _ = forward(pb, gamma, chunk, state=st)
+        done += chunk
+        if res < tol:
+            break
+    return st, res, done
+
+
+def forward_step(pb, gamma, t, st: State) -> State:
+    L = lib()
+    prob = make_problem(pb)
+    g = _g(gamma)
+    out = State(pb.ny, pb.nx)
+    L.orc_forward_step(C.byref(prob), _p(g), float(t), _p(st.rho), _p(st.u), _p(st.v), _p(st.T),
+                       _p(out.rho), _p(out.u), _p(out.v), _p(out.T))
+    return out
+
+
+def forward_node(pb, gamma, t, st: State, i: int, j: int) -> np.ndarray:
+    L = lib()
+    prob = make_problem(pb)
+    g = _g(gamma)
+    o = np.zeros(4)
+    L.orc_forward_node(C.byref(prob), _p(g), float(t), _p(st.rho), _p(st.u), _p(st.v), _p(st.T),
+                       int(i), int(j), _p(o))
+    return o
+
+
+def objective(pb, gamma, st: State) -> float:
+    """J_O of one state (Step 3)."""
+    L = lib()
+    prob = make_problem(pb)
+    return float(L.orc_objective(C.byref(prob), _p(_g(gamma)), _p(st.u), _p(st.v), _p(st.T)))
+
+
+def dJdu(pb, gamma, st: State):
+    """dJ_O/du, dJ_O/dv at every node."""
+    L = lib()
+    prob = make_problem(pb)
+    g = _g(gamma)
+    ju = np.zeros((pb.ny, pb.nx))
+    jv = np.zeros((pb.ny, pb.nx))
+    a, b = C.c_double(), C.c_double()
+    for j in range(pb.ny):
+        for i in range(pb.nx):
+            L.orc_dJdu_node(C.byref(prob), _p(g), _p(st.u), _p(st.v), i, j, C.byref(a), C.byref(b))
+            ju[j, i], jv[j, i] = a.value, b.value
+    return ju, jv
+
+
+def adjoint_step(pb, gamma, st1: State, st0: State, adj1: np.ndarray) -> np.ndarray:
+    """One ALKS step: adjoint (NADJ, ny, nx) at level t+1 -> level t."""
+    L = lib()
+    prob = make_problem(pb)
+    a1 = np.ascontiguousarray(adj1, dtype=np.float64)
+    a0 = np.zeros_like(a1)
+    work = np.zeros((5, pb.ny, pb.nx))
+    L.orc_adjoint_step(C.byref(prob), _p(_g(gamma)), _p(st1.u), _p(st1.v), _p(st0.u), _p(st0.v),
+                       _p(st0.T), _pp([a1[q] for q in range(NADJ)]),
+                       _pp([a0[q] for q in range(NADJ)]), _p(work))
+    return a0
+
+
+def sensitivity_level(pb, gamma, st: State, adj: np.ndarray) -> np.ndarray:
+    """Sensitivity integrand of one level (interior nodes, zero on edges)."""
+    L = lib()
+    prob = make_problem(pb)
+    a = np.ascontiguousarray(adj, dtype=np.float64)
+    s = np.zeros((pb.ny, pb.nx))
+    L.orc_sensitivity_accum(C.byref(prob), _p(_g(gamma)), _p(st.u), _p(st.v), _p(st.T),
+                            _pp([a[q] for q in range(NADJ)]), _p(s))
+    return s
+
+
+def steady_adjoint(pb, gamma, st: State, n_iter: int):
+    """ALKS iterated with the frozen state (Step 4) and the sensitivity (Step 5).
+    Returns (adjoint (NADJ, ny, nx), dJ/dgamma (ny, nx), last change)."""
+    L = lib()
+    prob = make_problem(pb)
+    adj = np.zeros((NADJ, pb.ny, pb.nx))
+    sens = np.zeros((pb.ny, pb.nx))
+    res = L.orc_steady_adjoint(C.byref(prob), _p(_g(gamma)), _p(st.u), _p(st.v), _p(st.T),
+                               int(n_iter), _p(adj), _p(sens))
+    return adj, sens, res
+
+
+def unsteady_adjoint(pb, gamma, traj: np.ndarray):
+    """ALKS marched backward over a stored trajectory (levels 0..n)."""
+    L = lib()
+    prob = make_problem(pb)
+    n = traj.shape[0] - 1
+    tr = np.ascontiguousarray(traj, dtype=np.float64)
+    adj = np.zeros((NADJ, pb.ny, pb.nx))
+    sens = np.zeros((pb.ny, pb.nx))
+    L.orc_unsteady_adjoint(C.byref(prob), _p(_g(gamma)), int(n), _p(tr), _p(adj), _p(sens))
+    return adj, sens
+
+
+def steady_gradient(pb, gamma, n_steps: Optional[int] = None, n_adj: Optional[int] = None):
+    """Steps 2-5 for a steady problem with fixed step counts.
+    Returns dict(J, dJdgamma, state, adjoint)."""
+    n_steps = pb.n_steps if n_steps is None else n_steps
+    n_adj = pb.n_adj if n_adj is None else n_adj
+    st, _, _, _ = forward(pb, gamma, n_steps)
+    J = objective(pb, gamma, st)
+    adj, sens, _ = steady_adjoint(pb, gamma, st, n_adj)
+    return dict(J=J, dJdgamma=sens, state=st, adjoint=adj)
+
+
+def unsteady_gradient(pb, gamma, n_steps: Optional[int] = None):
+    """Steps 2-5 for an unsteady problem; J = sum over levels 1..n of J_O."""
+    n_steps = pb.n_steps if n_steps is None else n_steps
+    st, _, tr, J = forward(pb, gamma, n_steps, traj=True, accumulate_J=True)
+    adj, sens = unsteady_adjoint(pb, gamma, tr)
+    return dict(J=J, dJdgamma=sens, state=st, adjoint=adj, traj=tr)
+
+
+def bc_flow(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, kT: float = 0.0):
+    """Least-squares adjoint boundary rule for one node (flow lattice)."""
+    L = lib()
+    f = np.ascontiguousarray(known, dtype=np.float64).copy()
+    um = (C.c_int * 9)(*[int(x) for x in unknown_mask])
+    mult = np.zeros(2)
+    L.orc_bc_flow(int(n[0]), int(n[1]), int(pressure), float(A), float(kT), um, _p(f), _p(mult))
+    return f, mult
+
+
+def bc_thermal(n, flux: bool, B: float, un: float, known: np.ndarray, unknown_mask):
+    """Least-squares adjoint boundary rule for one node (thermal lattice)."""
+    L = lib()
+    g = np.ascontiguousarray(known, dtype=np.float64).copy()
+    um = (C.c_int * 9)(*[int(x) for x in unknown_mask])
+    mult = np.zeros(1)
+    L.orc_bc_thermal(int(n[0]), int(n[1]), int(flux), float(B), float(un), um, _p(g), _p(mult))
+    return g, float(mult[0])
