@@ -91,11 +91,12 @@ class Problem:
     sigma: float = 4.0
     strip: int = 4
 
-    def __post_init__(self):
-        if self.in_y1 < 0:
-            self.in_y1 = self.ny + self.in_y1
-        if self.out_y1 < 0:
-            self.out_y1 = self.ny + self.out_y1
+    def resolved(self, name: str):
+        """Field value with negative span ends counted from the top edge (ny + v)."""
+        v = getattr(self, name)
+        if name in ("in_y0", "in_y1", "out_y0", "out_y1") and v < 0:
+            return self.ny + v
+        return v
 
     @property
     def n_nodes(self) -> int:

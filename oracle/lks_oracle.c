@@ -160,6 +160,29 @@ static double ddy(const double *f, int nx, int ny, int i, int j) {
     return (AT(f, i, j + 1) - AT(f, i, j - 1)) / 2.0;
 }
 
+/* Velocity gradient entering f^eq at node (i, j): g = du/dx, du/dy, dv/dx, dv/dy.
+ * The operator above everywhere, except the derivative of the normal velocity
+ * component along the edge normal at edge nodes, which is taken from continuity,
+ * Eq. (cont): du_n/dn = -du_s/ds with the derivative along the edge (central
+ * differences along the edge; zero at corner nodes, where both edges carry a zero
+ * tangential velocity).  The one-sided normal derivative of u_n makes the march
+ * unstable for A < 0 (nu > 1/6); for the exact solutions the two agree. */
+static void vel_grad(const double *u, const double *v, int nx, int ny, int i, int j, double *g) {
+    g[0] = ddx(u, nx, ny, i, j);
+    g[1] = ddy(u, nx, ny, i, j);
+    g[2] = ddx(v, nx, ny, i, j);
+    g[3] = ddy(v, nx, ny, i, j);
+    int xe = (i == 0 || i == nx - 1), ye = (j == 0 || j == ny - 1);
+    if (xe && ye) {
+        g[0] = 0.0;
+        g[3] = 0.0;
+    } else if (xe) {
+        g[0] = -g[3];
+    } else if (ye) {
+        g[3] = -g[0];
+    }
+}
+
 /* ------------------------------------------------------------------------- */
 /* Equilibria                                                                 */
 /* ------------------------------------------------------------------------- */
@@ -202,8 +225,9 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
         known[k] = inside(nx, ny, si, sj);
         f[k] = g[k] = 0.0;
         if (!known[k]) continue;
-        f[k] = feq(k, A, AT(rho, si, sj), AT(u, si, sj), AT(v, si, sj), ddx(u, nx, ny, si, sj),
-                   ddy(u, nx, ny, si, sj), ddx(v, nx, ny, si, sj), ddy(v, nx, ny, si, sj));
+        double gu[4];
+        vel_grad(u, v, nx, ny, si, sj, gu);
+        f[k] = feq(k, A, AT(rho, si, sj), AT(u, si, sj), AT(v, si, sj), gu[0], gu[1], gu[2], gu[3]);
         if (p->thermal)
             g[k] = geq(k, AT(T, si, sj), AT(u, si, sj), AT(v, si, sj), B_of(p, AT(gamma, si, sj)),
                        ddx(T, nx, ny, si, sj), ddy(T, nx, ny, si, sj));
@@ -521,6 +545,12 @@ static void adjoint_eq_fields(const orc_problem *p, const double *gamma, const d
         }
 }
 
+/* Exported form of the equilibrium coefficients above (P, V, G at every node). */
+void orc_adjoint_eq(const orc_problem *p, const double *gamma, const double *u, const double *v,
+                    double *const *a, double *P, double *Vx, double *Vy, double *G, double *Bwork) {
+    adjoint_eq_fields(p, gamma, u, v, a, P, Vx, Vy, G, Bwork);
+}
+
 /* Adjoint node update at level t from the equilibrium coefficients at level t+1
  * (already evaluated into P, Vx, Vy, G), the state at level t (u0, v0, T0) and
  * gamma.  out[0..8] in the adjoint field order.
@@ -609,9 +639,14 @@ void orc_adjoint_step(const orc_problem *p, const double *gamma, const double *u
 /* Sensitivity integrand at one level (Sec. 2.5), accumulated into sens:
  *   dJ_O/dgamma + 3 alpha' u.u~ - B' grad T . q~     (interior nodes)
  * with dJ_O/dgamma = alpha' |u|^2.  Edge nodes do not use gamma in the forward
- * scheme and receive nothing. */
-void orc_sensitivity_accum(const orc_problem *p, const double *gamma, const double *u,
-                           const double *v, const double *T, double *const *a, double *sens) {
+ * scheme and receive nothing.  parts selects the terms: bit 0 the flow and
+ * objective terms, bit 1 the thermal term.  In the unsteady sum the flow terms of
+ * level t pair u(t) (which alpha_gamma scales in the step t-1 -> t) with u~(t),
+ * for t = 1..n; the thermal term pairs grad T(t) (which B_gamma multiplies in the
+ * step t -> t+1) with q~(t), for t = 0..n-1. */
+void orc_sensitivity_parts(const orc_problem *p, const double *gamma, const double *u,
+                           const double *v, const double *T, double *const *a, double *sens,
+                           int parts) {
     int nx = p->nx, ny = p->ny;
 #pragma omp parallel for schedule(static)
     for (int j = 1; j < ny - 1; ++j)
@@ -619,11 +654,17 @@ void orc_sensitivity_accum(const orc_problem *p, const double *gamma, const doub
             double gm = AT(gamma, i, j);
             double da = dalpha_of(p, gm);
             double uu = AT(u, i, j), vv = AT(v, i, j);
-            double s = da * (uu * uu + vv * vv) + 3.0 * da * (uu * AT(a[1], i, j) + vv * AT(a[2], i, j));
-            if (p->thermal)
+            double s = 0.0;
+            if (parts & 1) s += da * (uu * uu + vv * vv) + 3.0 * da * (uu * AT(a[1], i, j) + vv * AT(a[2], i, j));
+            if (p->thermal && (parts & 2))
                 s -= dB_of(p, gm) * (ddx(T, nx, ny, i, j) * AT(a[7], i, j) + ddy(T, nx, ny, i, j) * AT(a[8], i, j));
             AT(sens, i, j) += s;
         }
+}
+
+void orc_sensitivity_accum(const orc_problem *p, const double *gamma, const double *u,
+                           const double *v, const double *T, double *const *a, double *sens) {
+    orc_sensitivity_parts(p, gamma, u, v, T, a, sens, 3);
 }
 
 /* ------------------------------------------------------------------------- */
@@ -728,8 +769,9 @@ double orc_steady_adjoint(const orc_problem *p, const double *gamma, const doubl
 
 /* Unsteady adjoint over a stored trajectory traj (levels 0..n_steps, each u, v, T).
  * Terminal condition (Eqs. afinitial, aginitial): adjoint at level n_steps+1 is
- * zero; for t = n_steps .. 1 the ALKS step gives level t and the sensitivity of
- * level t is accumulated.  adj receives the adjoint at level 1. */
+ * zero; for t = n_steps .. 0 the ALKS step gives level t and the sensitivity terms
+ * of level t are accumulated (flow terms for t >= 1, thermal term for t < n_steps).
+ * adj receives the adjoint at level 0. */
 void orc_unsteady_adjoint(const orc_problem *p, const double *gamma, int n_steps,
                           const double *traj, double *adj, double *sens) {
     size_t N = (size_t)p->nx * p->ny;
@@ -739,7 +781,7 @@ void orc_unsteady_adjoint(const orc_problem *p, const double *gamma, int n_steps
     memset(adj, 0, NADJ * N * sizeof(double));
     memset(sens, 0, N * sizeof(double));
     double *cur = adj, *nxt = other; /* cur: level t+1 */
-    for (int t = n_steps; t >= 1; --t) {
+    for (int t = n_steps; t >= 0; --t) {
         const double *L1 = traj + (size_t)(t < n_steps ? t + 1 : t) * 3 * N;
         const double *L0 = traj + (size_t)t * 3 * N;
         for (int q = 0; q < NADJ; ++q) {
@@ -747,7 +789,8 @@ void orc_unsteady_adjoint(const orc_problem *p, const double *gamma, int n_steps
             a0[q] = nxt + q * N;
         }
         orc_adjoint_step(p, gamma, L1, L1 + N, L0, L0 + N, L0 + 2 * N, a1, a0, work);
-        orc_sensitivity_accum(p, gamma, L0, L0 + N, L0 + 2 * N, a0, sens);
+        orc_sensitivity_parts(p, gamma, L0, L0 + N, L0 + 2 * N, a0, sens,
+                              (t >= 1 ? 1 : 0) | (t < n_steps ? 2 : 0));
         double *tmp = cur;
         cur = nxt;
         nxt = tmp;

@@ -78,6 +78,8 @@ def lib():
         L.orc_bc_thermal.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                      C.POINTER(C.c_int), P, P]
         L.orc_adjoint_step.argtypes = [prob, P, P, P, P, P, P, PP, PP, P]
+        L.orc_adjoint_eq.argtypes = [prob, P, P, P, PP, P, P, P, P, P]
+        L.orc_adjoint_node.argtypes = [prob, P, P, P, P, P, P, P, P, C.c_int, C.c_int, P]
         L.orc_sensitivity_accum.argtypes = [prob, P, P, P, P, PP, P]
         L.orc_forward.argtypes = [prob, P, C.c_int, C.c_int, P, P, P, P, P, P]
         L.orc_forward.restype = C.c_double
@@ -114,7 +116,8 @@ def make_problem(pb) -> OrcProblem:
     for name, _ in OrcProblem._fields_:
         if name in ("t_kind", "t_val"):
             continue
-        setattr(s, name, type(getattr(s, name))(getattr(pb, name)))
+        val = pb.resolved(name) if hasattr(pb, "resolved") else getattr(pb, name)
+        setattr(s, name, type(getattr(s, name))(val))
     for e in range(4):
         s.t_kind[e] = int(pb.t_kind[e])
         s.t_val[e] = float(pb.t_val[e])
@@ -221,6 +224,35 @@ def adjoint_step(pb, gamma, st1: State, st0: State, adj1: np.ndarray) -> np.ndar
                        _p(st0.T), _pp([a1[q] for q in range(NADJ)]),
                        _pp([a0[q] for q in range(NADJ)]), _p(work))
     return a0
+
+
+def adjoint_eq(pb, gamma, st: State, adj: np.ndarray) -> np.ndarray:
+    """Adjoint equilibrium coefficients (P, Vx, Vy, G) at every node, Eqs. (afeq), (ageq)."""
+    L = lib()
+    prob = make_problem(pb)
+    a = np.ascontiguousarray(adj, dtype=np.float64)
+    out = np.zeros((5, pb.ny, pb.nx))
+    L.orc_adjoint_eq(C.byref(prob), _p(_g(gamma)), _p(st.u), _p(st.v),
+                     _pp([a[q] for q in range(NADJ)]), _p(out[0]), _p(out[1]), _p(out[2]),
+                     _p(out[3]), _p(out[4]))
+    return out[:4].copy()
+
+
+def adjoint_gather(pb, gamma, PVG: np.ndarray, st0: State) -> np.ndarray:
+    """Adjoint moments at level t from given equilibrium coefficients (P, Vx, Vy, G)
+    of level t+1 (gather, boundary rule, sources, moments) at every node."""
+    L = lib()
+    prob = make_problem(pb)
+    g = _g(gamma)
+    c = [np.ascontiguousarray(PVG[q], dtype=np.float64) for q in range(4)]
+    out = np.zeros((NADJ, pb.ny, pb.nx))
+    o = np.zeros(NADJ)
+    for j in range(pb.ny):
+        for i in range(pb.nx):
+            L.orc_adjoint_node(C.byref(prob), _p(g), _p(c[0]), _p(c[1]), _p(c[2]), _p(c[3]),
+                               _p(st0.u), _p(st0.v), _p(st0.T), i, j, _p(o))
+            out[:, j, i] = o
+    return out
 
 
 def sensitivity_level(pb, gamma, st: State, adj: np.ndarray) -> np.ndarray:
