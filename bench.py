@@ -1,0 +1,297 @@
+"""Benchmark: forward + adjoint lattice updates per second (MLUPS) of the LKS / ALKS
+gradient on one GB300, plus roofline, end-to-end and CPU-oracle figures.
+
+One step = one full gradient of the workload (LKS forward march, ALKS adjoint march,
+sensitivity).  Default workload: 512 x 256 steady channel, Re = 100, 20000 forward
++ 20000 adjoint steps, FP32 (the second configuration of the paper-derived set).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                    [--workload config2|roofline8192|config1]
+
+Under torchrun every rank runs an independent replica (designs are independent;
+no collective on the data path); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import inputs  # noqa: E402
+
+# Algorithmic bytes per node of one launch (FP32 fields, read once + written once;
+# gradients recomputed from the halo; gamma read once).
+BYTES_FWD = 4 * (3 + 3 + 1)            # drho,u,v in; drho,u,v out; gamma
+BYTES_ADJ_STEADY = 4 * (6 + 6 + 2 + 1)  # 6 adjoint fields in + out; u,v; gamma
+
+METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e-3 rel"
+
+
+def workload(name: str):
+    if name == "config2":
+        return inputs.config2(), "config2: 512x256 steady channel, Re=100, 20000+20000 steps, FP32"
+    if name == "config1":
+        return inputs.config1(), "config1: 64x64 steady channel, Re=10, 5000+5000 steps, FP32"
+    if name == "roofline8192":
+        pb = inputs.roofline2d(8192)
+        return pb, "roofline8192: 8192x8192 steady channel, 200+200 steps, FP32"
+    raise SystemExit(f"unknown workload {name}")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax.append(float(p[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_baseline(pb, n_fwd: int, n_adj: int):
+    """The FP64 oracle on the host cores, on a bounded sample of the workload: the
+    full lattice for n_fwd forward + n_adj adjoint steps (steady iteration)."""
+    from oracle import oracle as O
+    O.build()
+    g = pb.gamma()
+    t0 = time.perf_counter()
+    st, _, _, _ = O.forward(pb, g, n_fwd)
+    O.steady_adjoint(pb, g, st, n_adj)
+    dt = time.perf_counter() - t0
+    mlups = pb.n_nodes * (n_fwd + n_adj) / dt / 1e6
+    return {"value": mlups, "unit": "MLUPS", "cores": O.get_threads(), "kind": "oracle",
+            "sample": f"{pb.nx}x{pb.ny} lattice, {n_fwd} forward + {n_adj} adjoint steps (of "
+                      f"{pb.n_steps}+{pb.n_adj}), FP64, {dt:.1f} s"}
+
+
+def run_reference(args):
+    """Reference arm: the FP64 CPU oracle as it stands, timed on the host cores."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    pb, desc = workload(args.workload)
+    n_f, n_a = (60, 60) if args.workload == "config2" else (20, 20)
+    if args.workload == "config1":
+        n_f, n_a = 500, 500
+    from oracle import oracle as O
+    O.build()
+    g = pb.gamma()
+    for _ in range(args.warmup):
+        st, _, _, _ = O.forward(pb, g, 2)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        st, _, _, _ = O.forward(pb, g, n_f)
+        O.steady_adjoint(pb, g, st, n_a)
+        times.append(time.perf_counter() - t0)
+    dt = sum(times)
+    value = pb.n_nodes * (n_f + n_a) * args.steps / dt / 1e6
+    cb = {"value": value, "unit": "MLUPS", "cores": O.get_threads(), "kind": "oracle",
+          "sample": f"each step: {pb.nx}x{pb.ny} lattice, {n_f} forward + {n_a} adjoint steps (FP64)"}
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "l2": "n/a (CPU)"},
+        "cpu_baseline": cb, "e2e": {"value": value, "unit": "MLUPS", "h2d_bytes_per_step": 0,
+                                     "d2h_bytes_per_step": 0}}))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+
+    from paper_2411_03090_gb300 import LKS
+
+    pb, desc = workload(args.workload)
+    g_np = pb.gamma()
+    gamma = torch.from_numpy(g_np).to(dev, torch.float32)
+    s = LKS(pb, real="f32", device=dev)
+    stream = s.stream
+    N = pb.n_nodes
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+
+    def one_gradient(ev=None):
+        J = s.lks_forward(gamma)
+        if ev is not None:
+            ev[1].record(stream)
+        s.alks_adjoint()
+        if ev is not None:
+            ev[2].record(stream)
+        g = s.lks_sensitivity()
+        return J, g
+
+    for _ in range(max(args.warmup, 3)):
+        one_gradient()
+    torch.cuda.synchronize()
+
+    launches0 = s.query().kernel_launches
+    clocks = ClockSampler(local)
+    clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    step_ms, fwd_ms, adj_ms = [], [], []
+    for _ in range(args.steps):
+        flush.fill_(1.0)  # evict the previous gradient's working set from L2
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        ev[0].record(stream)
+        one_gradient(ev)
+        ev[3].record(stream)
+        torch.cuda.synchronize()
+        step_ms.append(ev[0].elapsed_time(ev[3]))
+        fwd_ms.append(ev[0].elapsed_time(ev[1]))
+        adj_ms.append(ev[1].elapsed_time(ev[2]))
+    torch.cuda.synchronize()
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        dist.barrier()
+    clk = clocks.stop()
+    launches = s.query().kernel_launches - launches0
+
+    updates_per_step = N * (pb.n_steps + pb.n_adj)
+    value = world * updates_per_step * args.steps / (total_ms * 1e-3) / 1e6
+
+    # Dominant kernel (adjoint step): algorithmic bytes per launch / mean duration.
+    hbm, peak_kind = peaks()
+    adj_launch_s = (sum(adj_ms) / len(adj_ms)) * 1e-3 / pb.n_adj
+    fwd_launch_s = (sum(fwd_ms) / len(fwd_ms)) * 1e-3 / pb.n_steps
+    adj_gbs = BYTES_ADJ_STEADY * N / adj_launch_s / 1e9
+    fwd_gbs = BYTES_FWD * N / fwd_launch_s / 1e9
+    traffic = None
+    roofline = {"bound": "hbm", "kernel": "adj_step_kernel<float,false>", "achieved": adj_gbs, "peak": hbm,
+                "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                "algorithmic_bytes_per_node": BYTES_ADJ_STEADY, "mean_launch_us": adj_launch_s * 1e6,
+                "forward": {"kernel": "fwd_step_kernel<float,false>", "achieved": fwd_gbs,
+                            "frac": fwd_gbs / hbm, "algorithmic_bytes_per_node": BYTES_FWD,
+                            "mean_launch_us": fwd_launch_s * 1e6}}
+
+    # End to end through the C ABI with host buffers (pinned), copies inside.
+    g_host = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
+    grad_host = torch.empty(pb.ny, pb.nx, dtype=torch.float32).pin_memory().numpy()
+    s.gradient_host(g_host, grad_host)
+    e2e_t = []
+    for _ in range(max(2, min(args.steps, 3))):
+        flush.fill_(1.0)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.gradient_host(g_host, grad_host)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_val = world * updates_per_step / (sum(e2e_t) / len(e2e_t)) / 1e6
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "lattice": f"{pb.nx}x{pb.ny}", "forward_steps": pb.n_steps,
+                   "adjoint_steps": pb.n_adj, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3},
+        "roofline": roofline,
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N + 8 + 4},
+        "gpu_launches": int(launches),
+        "clocks": clk,
+    }
+    if not args.no_cpu_baseline:
+        try:
+            out["cpu_baseline"] = cpu_baseline(pb, 40, 40) if args.workload == "config2" else \
+                cpu_baseline(pb, 5, 5)
+        except Exception as e:  # the oracle is a reported baseline, not the product
+            out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

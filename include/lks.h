@@ -1,0 +1,190 @@
+/*
+ * lks.h -- C ABI of the GB300 (sm_103a) implementation of the Lattice Kinetic
+ * Scheme (LKS) state march, the Adjoint Lattice Kinetic Scheme (ALKS) and the
+ * design sensitivity of Tanabe, Yaji and Ushijima, "Adjoint lattice kinetic scheme
+ * for topology optimization in fluid problems" (arXiv 2411.03090).
+ *
+ * The calls follow the paper's optimization procedure (Sec. 2.7):
+ *   Step 2  state fields by LKS               -> lks_forward
+ *   Step 3  objective J                       -> lks_forward (J_dev)
+ *   Step 4  adjoint fields by ALKS            -> alks_adjoint
+ *   Step 5  design sensitivity dJ/dgamma      -> lks_sensitivity
+ * for the problem  min_gamma J(gamma, U(gamma)),  0 <= gamma <= 1  (Eq. obj).
+ *
+ * Conventions
+ *  - Lattice units: dx = dt = 1.  D2Q9 lattice; nodes sit on the domain edges.
+ *  - A field is an array of nx*ny values, node (i, j) at j*nx + i (x fastest),
+ *    dense, in the element type `real_type` of the descriptor (float or double).
+ *  - Pointers named *_dev are device pointers on the current device; *_host are
+ *    host pointers (pageable or pinned).
+ *  - Ownership: the caller owns every buffer it passes in, including the workspace
+ *    given to lks_create.  The library allocates no device memory at any point and
+ *    keeps no pointer to caller buffers beyond the call, except the workspace.
+ *  - Every call is ordered on the CUDA stream given to lks_create and returns
+ *    without synchronising, unless stated otherwise.
+ *  - Errors: arguments are checked on the host before any launch; a failing check
+ *    returns LKS_ERR_INVALID_ARG and launches nothing.  Conditions detected on the
+ *    device (non-finite or runaway velocity) are recorded in a status word in the
+ *    workspace and reported by the next call that synchronises (lks_query,
+ *    lks_gradient_host).  Calls never throw.  lks_last_error gives a message.
+ */
+#ifndef LKS_H
+#define LKS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LKS_DESC_VERSION 1
+
+typedef enum {
+    LKS_OK = 0,
+    LKS_ERR_INVALID_ARG = 1,   /* bad descriptor, size or pointer                 */
+    LKS_ERR_WORKSPACE = 2,     /* workspace too small or misaligned               */
+    LKS_ERR_CUDA = 3,          /* a CUDA runtime call failed                      */
+    LKS_ERR_UNSTABLE = 4,      /* non-finite or |u| > 0.5 seen on the device       */
+    LKS_ERR_NOT_CONVERGED = 5, /* reserved for tolerance-driven marches           */
+    LKS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                    */
+    LKS_ERR_STATE = 7          /* calls in the wrong order (e.g. adjoint first)    */
+} lks_status;
+
+typedef enum { LKS_REAL_F32 = 0, LKS_REAL_F64 = 1 } lks_real_type;
+
+/* Storage type of checkpoint snapshots (unsteady problems). */
+typedef enum { LKS_SNAP_F32 = 0, LKS_SNAP_BF16 = 1, LKS_SNAP_F16 = 2 } lks_snap_type;
+
+/* Thermal edge conditions (Sec. 2.4): prescribed temperature T = T_bar, or
+ * prescribed heat flux -q.n = q_bar_w. */
+typedef enum { LKS_T_FIXED = 0, LKS_T_FLUX = 1 } lks_thermal_kind;
+
+/* Problem descriptor.  Geometry: inlet (prescribed velocity, parabola over the
+ * span [in_y0, in_y1] of the left edge, zero elsewhere on that edge); pressure
+ * outlet (rho = rho_out, tangential velocity zero) over [out_y0, out_y1] of the
+ * right edge, walls elsewhere on the right edge; no-slip walls at the bottom and
+ * top edges; corners are wall nodes. */
+typedef struct {
+    int32_t version;          /* LKS_DESC_VERSION                                   */
+    int32_t nx, ny;           /* nodes per direction, >= 5                           */
+    int32_t real_type;        /* lks_real_type of every field passed in or out       */
+    double nu;                /* kinematic viscosity, Eq. (A): nu = (1/6 - 2A/9)     */
+    double alpha_bar;         /* Brinkman interpolation, Eq. (brinkman)              */
+    double q_alpha;
+    double u_max;             /* inlet peak velocity                                */
+    double pulse_mean;        /* u_in(t) = u_max (pulse_mean + pulse_amp sin(2 pi t / pulse_period)) */
+    double pulse_amp;
+    double pulse_period;      /* <= 0: steady inlet u_max * pulse_mean               */
+    int32_t in_y0, in_y1;     /* inlet span, inclusive                               */
+    int32_t out_y0, out_y1;   /* outlet span, inclusive, inside [1, ny-2]            */
+    double rho_out;           /* outlet density, p_bar = rho_out / 3                 */
+    int32_t thermal;          /* 1: thermal lattice for T (Eqs. T, geq2)             */
+    int32_t steady;           /* 1: steady (adjoint iterated on the final state)     */
+    double K_f, K_s, q_K;     /* thermal diffusivity interpolation, Eq. (conductivity) */
+    int32_t t_kind[4];        /* thermal condition per edge: left, right, bottom, top */
+    double t_val[4];          /* T_bar or q_bar_w per edge                           */
+    double kappa_T;           /* weight of the temperature term in the objective     */
+    int32_t n_steps;          /* forward steps                                       */
+    int32_t n_adj;            /* steady: adjoint iterations; unsteady: ignored       */
+    int32_t checkpoint_every; /* unsteady: K > 0 recompute segments of K steps from
+                                 snapshots; 0 keeps every level (plain form)         */
+    int32_t snapshot_type;    /* lks_snap_type of the checkpoint snapshots           */
+    int32_t reserved[8];      /* must be zero                                        */
+} lks_problem_desc;
+
+/* Counters and the device status word, filled by lks_query. */
+typedef struct {
+    int64_t forward_steps;    /* forward steps launched since create (incl. recompute) */
+    int64_t adjoint_steps;    /* adjoint steps launched since create                 */
+    int64_t kernel_launches;  /* kernels launched since create                       */
+    size_t workspace_bytes;   /* workspace in use                                    */
+    int32_t device_status;    /* lks_status recorded on the device (0 = none)        */
+    int32_t phase;            /* 0 created, 1 forward done, 2 adjoint done           */
+} lks_stats;
+
+typedef struct lks_handle lks_handle;
+
+/* Workspace bytes for a problem (host only, pure).  Errors: LKS_ERR_INVALID_ARG
+ * for a bad descriptor. */
+lks_status lks_workspace_size(const lks_problem_desc *desc, size_t *bytes);
+
+/* Creates a handle on the current device.  workspace_dev: caller-owned device
+ * memory of at least lks_workspace_size bytes, 256-byte aligned, kept alive and
+ * unused by the caller until lks_destroy.  stream: a cudaStream_t (NULL = legacy
+ * default stream).  Host allocation of the handle itself only. */
+lks_status lks_create(const lks_problem_desc *desc, void *workspace_dev, size_t bytes,
+                      void *stream, lks_handle **out);
+
+/* Step 2 + 3 (Sec. 2.4, Eqs. rho, u, T with feq2, geq2, lbef_ex; objective Eq. fj):
+ * marches the state from rest (rho = 1, u = 0, T = 0) for n_steps steps with the
+ * design field gamma_dev (nx*ny, real_type, values in [0, 1]; copied into the
+ * workspace) and writes the objective J to J_dev (one double, device).  Steady: J
+ * is J_O of the final state.  Unsteady: J is the sum of J_O over levels 1..n_steps;
+ * snapshots or the full trajectory are kept for the adjoint.  J_O is the total
+ * dissipation over interior nodes, sum nu/2 S:S + alpha_gamma |u|^2, plus kappa_T T. */
+lks_status lks_forward(lks_handle *h, const void *gamma_dev, double *J_dev);
+
+/* Step 4 (Sec. 2.5, Eqs. ap-aq, afeq, ageq, albef_ex, ftilde; App. A): the ALKS
+ * march from the terminal condition (Eqs. afinitial, aginitial) with the
+ * generalized-inverse edge rule.  Steady: n_adj iterations on the final state.
+ * Unsteady: backward over all levels (recomputing segments from snapshots when
+ * checkpoint_every > 0) and the sensitivity accumulated on the way.
+ * LKS_ERR_STATE if lks_forward has not run. */
+lks_status alks_adjoint(lks_handle *h);
+
+/* Step 5 (Sec. 2.5, the integrand of <J', dgamma>): writes dJ/dgamma (nx*ny,
+ * real_type, device) = dJ_O/dgamma + 3 alpha' u.u~ - B' grad T . q~ on interior
+ * nodes (summed over levels when unsteady) and 0 on edge nodes.  LKS_ERR_STATE if
+ * alks_adjoint has not run. */
+lks_status lks_sensitivity(lks_handle *h, void *dJdgamma_dev);
+
+/* Steps 2-5 end to end with host buffers: copies gamma_host to the device, runs
+ * lks_forward, alks_adjoint and lks_sensitivity, copies J and dJ/dgamma back and
+ * synchronises the stream.  Returns the device status word if it is set. */
+lks_status lks_gradient_host(lks_handle *h, const void *gamma_host, double *J_host,
+                             void *dJdgamma_host);
+
+/* State access for tests and tools: fields (nx*ny, real_type, device) drho, u, v, T
+ * where drho = rho - 1 is the density deviation the library stores (T ignored
+ * unless thermal).  lks_set_state also sets the time level t of the state (the
+ * inlet pulse of the next step uses t + 1); gamma_dev as in lks_forward. */
+lks_status lks_set_state(lks_handle *h, const void *gamma_dev, const void *drho_dev,
+                         const void *u_dev, const void *v_dev, const void *T_dev, int32_t t);
+lks_status lks_get_state(lks_handle *h, void *drho_dev, void *u_dev, void *v_dev, void *T_dev);
+
+/* n forward steps from the current state (no objective, no snapshots). */
+lks_status lks_march(lks_handle *h, int32_t n);
+
+/* Adjoint fields (9 arrays of nx*ny, real_type, device, in the order rho~, u~_x,
+ * u~_y, s~_xx, s~_xy, s~_yy, T~, q~_x, q~_y; the thermal three are ignored unless
+ * thermal). */
+lks_status alks_set_adjoint(lks_handle *h, void *const *fields_dev);
+lks_status alks_get_adjoint(lks_handle *h, void *const *fields_dev);
+
+/* n ALKS steps from the current adjoint fields with the state frozen at the
+ * current state (the steady iteration of alks_adjoint). */
+lks_status alks_march(lks_handle *h, int32_t n);
+
+/* Counters and device status (synchronises the stream). */
+lks_status lks_query(lks_handle *h, lks_stats *out);
+
+/* Destroys the handle (host memory only; the workspace stays the caller's). */
+lks_status lks_destroy(lks_handle *h);
+
+/* Static message for a status; last error message of a handle (never NULL). */
+const char *lks_status_string(lks_status s);
+const char *lks_last_error(const lks_handle *h);
+
+/* Host-only: the edge-class moment maps used by the adjoint kernels, for checks on
+ * a CPU.  cls: 0 left face, 1 right pressure face, 2 right wall face, 3 bottom
+ * face, 4 top face, 5..8 corners (bottom-left, bottom-right, top-left, top-right).
+ * out: 6 x 9 doubles, row r = moment r (rho~, u~_x, u~_y, s~_xx, s~_xy, s~_yy) as a
+ * linear function of the nine gathered f~ (unknown entries ignored).  Eq. (ftilde)
+ * generalised to every face by the least squares of Sec. 2.5. */
+lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LKS_H */

@@ -1,0 +1,9 @@
+"""GB300-native (sm_103a) Lattice Kinetic Scheme / Adjoint Lattice Kinetic Scheme
+for density-based fluid topology optimisation (arXiv 2411.03090).
+
+The compute path is the CUDA library behind ``include/lks.h``; ``lks`` is its
+ctypes binding and ``autograd`` wraps gamma -> J as a torch.autograd.Function.
+"""
+from .lks import LKS, LKSError, load, make_desc, workspace_size, edge_moment_map  # noqa: F401
+
+__all__ = ["LKS", "LKSError", "load", "make_desc", "workspace_size", "edge_moment_map"]

@@ -1,0 +1,961 @@
+// lks_capi.cu -- host side of the C ABI declared in include/lks.h: descriptor
+// checks, workspace layout, the generalized-inverse edge maps of the adjoint, and
+// the stream-ordered orchestration of the LKS / ALKS marches (arXiv 2411.03090,
+// Sec. 2.7 Steps 2-5).  Every step of the path runs in the kernels of
+// lks_kernels.cuh; this file only sizes, orders and launches them.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lks.h"
+#include "lks_kernels.cuh"
+
+using namespace lks;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
+
+const int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+const int CYh[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+
+// ------------------------------------------------------------------------------------
+// Workspace layout
+// ------------------------------------------------------------------------------------
+struct Layout {
+  size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
+  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, tmap = 0;
+  size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
+  int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
+  int fwd_blocks = 0, obj_blocks = 0;
+  int n_ckpt = 0, seg_levels = 0;
+  size_t N = 0, rsize = 4, snap_elem = 4;
+};
+
+int obj_grid(size_t N) { return (int)std::min<size_t>((N + NTHREADS - 1) / NTHREADS, 1024); }
+
+lks_status check_desc(const lks_problem_desc* d, std::string* why) {
+  auto bad = [&](const char* m) {
+    if (why) *why = m;
+    return LKS_ERR_INVALID_ARG;
+  };
+  if (!d) return bad("descriptor is NULL");
+  if (d->version != LKS_DESC_VERSION) return bad("descriptor version mismatch");
+  if (d->nx < 5 || d->ny < 5) return bad("nx and ny must be >= 5");
+  if ((int64_t)d->nx * d->ny > (int64_t)1 << 31) return bad("lattice larger than 2^31 nodes");
+  if (d->real_type != LKS_REAL_F32 && d->real_type != LKS_REAL_F64) return bad("real_type must be F32 or F64");
+  if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
+  if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
+  if (d->in_y0 < 0 || d->in_y1 > d->ny - 1 || d->in_y1 <= d->in_y0) return bad("bad inlet span");
+  if (d->out_y0 < 1 || d->out_y1 > d->ny - 2 || d->out_y1 < d->out_y0) return bad("bad outlet span");
+  if (d->n_steps < 1) return bad("n_steps must be >= 1");
+  if (d->steady && d->n_adj < 1) return bad("n_adj must be >= 1 for a steady problem");
+  if (d->thermal) {
+    if (!(d->q_K > 0.0)) return bad("q_K must be > 0");
+    for (int e = 0; e < 4; ++e)
+      if (d->t_kind[e] != LKS_T_FIXED && d->t_kind[e] != LKS_T_FLUX) return bad("bad thermal edge kind");
+  }
+  if (d->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
+  if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
+  for (int q = 0; q < 8; ++q)
+    if (d->reserved[q] != 0) return bad("reserved fields must be zero");
+  return LKS_OK;
+}
+
+Layout make_layout(const lks_problem_desc* d) {
+  Layout L;
+  L.N = (size_t)d->nx * d->ny;
+  L.rsize = d->real_type == LKS_REAL_F64 ? 8 : 4;
+  L.nF = d->thermal ? 4 : 3;
+  L.nA = d->thermal ? 9 : 6;
+  L.nT = d->thermal ? 3 : 2;
+  const int gx = (d->nx + TX - 1) / TX, gy = (d->ny + TY - 1) / TY;
+  L.fwd_blocks = gx * gy;
+  L.obj_blocks = obj_grid(L.N);
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = off;
+    off = align_up(off + bytes);
+    return o;
+  };
+  const size_t fb = L.N * L.rsize;
+  L.gamma = take(fb);
+  L.stA = take(fb * L.nF);
+  L.stB = take(fb * L.nF);
+  L.adA = take(fb * L.nA);
+  L.adB = take(fb * L.nA);
+  L.jfwd = take(sizeof(double) * L.fwd_blocks);
+  L.jobj = take(sizeof(double) * L.obj_blocks);
+  L.jval = take(sizeof(double));
+  L.status = take(sizeof(int));
+  L.emap = take(L.rsize * 9 * 54);
+  L.tmap = take(L.rsize * 9 * 27);
+  if (!d->steady) {
+    L.sens = take(fb);
+    L.sens64 = take(sizeof(double) * L.N);
+    if (d->checkpoint_every == 0) {
+      L.traj = take(fb * L.nT * ((size_t)d->n_steps + 1));
+    } else {
+      const int K = d->checkpoint_every;
+      L.n_ckpt = (d->n_steps + K - 1) / K;
+      L.snap_elem = d->snapshot_type == LKS_SNAP_F32 ? 4 : 2;
+      L.snaps = take(L.snap_elem * L.N * L.nF * (size_t)L.n_ckpt);
+      L.scales = take(sizeof(float) * 2 * L.nF * (size_t)L.n_ckpt);
+      L.seg_levels = K + 2;
+      L.seg = take(fb * L.nT * (size_t)L.seg_levels);
+    }
+  }
+  L.total = off;
+  return L;
+}
+
+// ------------------------------------------------------------------------------------
+// Generalized-inverse edge maps (Sec. 2.5; App. A)
+// ------------------------------------------------------------------------------------
+// Solves min ||Acols x + b||_2 for several right-hand sides by the normal equations.
+// A: 9 x nc (row major); zero columns are dropped (their unknowns set to zero).
+void lsq_solve(const double* A, int nc, const double* rhs /* 9 */, double* x) {
+  int live[16], nl = 0;
+  for (int cidx = 0; cidx < nc; ++cidx) {
+    double s = 0;
+    for (int r = 0; r < 9; ++r) s += std::fabs(A[r * nc + cidx]);
+    x[cidx] = 0.0;
+    if (s > 0) live[nl++] = cidx;
+  }
+  double G[16][17];
+  for (int a = 0; a < nl; ++a) {
+    for (int b = 0; b < nl; ++b) {
+      double s = 0;
+      for (int r = 0; r < 9; ++r) s += A[r * nc + live[a]] * A[r * nc + live[b]];
+      G[a][b] = s;
+    }
+    double s = 0;
+    for (int r = 0; r < 9; ++r) s += A[r * nc + live[a]] * rhs[r];
+    G[a][nl] = s;
+  }
+  for (int col = 0; col < nl; ++col) {
+    int p = col;
+    for (int r = col + 1; r < nl; ++r)
+      if (std::fabs(G[r][col]) > std::fabs(G[p][col])) p = r;
+    for (int q = 0; q <= nl; ++q) std::swap(G[col][q], G[p][q]);
+    for (int r = 0; r < nl; ++r) {
+      if (r == col) continue;
+      const double f = G[r][col] / G[col][col];
+      for (int q = col; q <= nl; ++q) G[r][q] -= f * G[col][q];
+    }
+  }
+  for (int a = 0; a < nl; ++a) x[live[a]] = G[a][nl] / G[a][a];
+}
+
+void class_geometry(int cls, int* nx, int* ny, int* pressure) {
+  static const int tab[9][3] = {{-1, 0, 0}, {1, 0, 1}, {1, 0, 0}, {0, -1, 0}, {0, 1, 0},
+                                {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 1, 0}};
+  *nx = tab[cls][0];
+  *ny = tab[cls][1];
+  *pressure = tab[cls][2];
+}
+
+// Flow: 6 x 9 moment map for edge class cls at parameter A.
+void flow_moment_map(double A, int cls, double* out) {
+  int n_x, n_y, pres;
+  class_geometry(cls, &n_x, &n_y, &pres);
+  bool unk[9];
+  int U[9], nu = 0;
+  for (int k = 0; k < 9; ++k) {
+    unk[k] = (CXh[k] * n_x > 0) || (CYh[k] * n_y > 0);
+    if (unk[k]) U[nu++] = k;
+  }
+  double M[9][9];
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) {
+      const int cnc = CXh[c] * n_x + CYh[c] * n_y;
+      const double cc = CXh[c] * CXh[r] + CYh[c] * CYh[r];
+      M[r][c] = (r == c ? (double)(CXh[r] * n_x + CYh[r] * n_y) : 0.0) - 2.0 * A * Wh[c] * cnc * cc;
+    }
+  const int nc = nu + 2;
+  std::vector<double> Am(9 * nc);
+  for (int r = 0; r < 9; ++r) {
+    for (int q = 0; q < nu; ++q) Am[r * nc + q] = M[r][U[q]];
+    if (pres) {
+      Am[r * nc + nu] = 1.0;
+      Am[r * nc + nu + 1] = (double)(CXh[r] * (-n_y) + CYh[r] * n_x);
+    } else {
+      Am[r * nc + nu] = CXh[r];
+      Am[r * nc + nu + 1] = CYh[r];
+    }
+  }
+  double X[9][9] = {};  // X[u][k]: unknown u from known k
+  for (int k = 0; k < 9; ++k) {
+    if (unk[k]) continue;
+    double rhs[9], x[16];
+    for (int r = 0; r < 9; ++r) rhs[r] = -M[r][k];
+    lsq_solve(Am.data(), nc, rhs, x);
+    for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
+  }
+  for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < 9; ++k) {
+      auto mom = [&](int kk) {
+        const double cx = CXh[kk], cy = CYh[kk];
+        const double f[6] = {1, cx, cy, cx * cx, cx * cy, cy * cy};
+        return Wh[kk] * f[r];
+      };
+      double s = 0.0;
+      if (!unk[k]) {
+        s = mom(k);
+        for (int q = 0; q < nu; ++q) s += mom(U[q]) * X[U[q]][k];
+      }
+      out[r * 9 + k] = s;
+    }
+}
+
+// Thermal: 3 x 9 moment map (T~, q~x, q~y) for edge class cls, thermal kind and B.
+void thermal_moment_map(double B, int cls, int flux, double* out) {
+  int n_x, n_y, pres;
+  class_geometry(cls, &n_x, &n_y, &pres);
+  bool unk[9];
+  int U[9], nu = 0;
+  for (int k = 0; k < 9; ++k) {
+    unk[k] = (CXh[k] * n_x > 0) || (CYh[k] * n_y > 0);
+    if (unk[k]) U[nu++] = k;
+  }
+  double M[9][9];
+  for (int r = 0; r < 9; ++r)
+    for (int c = 0; c < 9; ++c) {
+      const int cnc = CXh[c] * n_x + CYh[c] * n_y;
+      M[r][c] = (r == c ? (double)(CXh[r] * n_x + CYh[r] * n_y) : 0.0) - B * Wh[c] * cnc;
+    }
+  const int nc = nu + 1;
+  std::vector<double> Am(9 * nc);
+  for (int r = 0; r < 9; ++r) {
+    for (int q = 0; q < nu; ++q) Am[r * nc + q] = M[r][U[q]];
+    Am[r * nc + nu] = flux ? (double)(CXh[r] * n_x + CYh[r] * n_y) : 1.0;
+  }
+  double X[9][9] = {};
+  for (int k = 0; k < 9; ++k) {
+    if (unk[k]) continue;
+    double rhs[9], x[16];
+    for (int r = 0; r < 9; ++r) rhs[r] = -M[r][k];
+    lsq_solve(Am.data(), nc, rhs, x);
+    for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
+  }
+  for (int r = 0; r < 3; ++r)
+    for (int k = 0; k < 9; ++k) {
+      auto mom = [&](int kk) {
+        const double f[3] = {1.0, (double)CXh[kk], (double)CYh[kk]};
+        return Wh[kk] * f[r];
+      };
+      double s = 0.0;
+      if (!unk[k]) {
+        s = mom(k);
+        for (int q = 0; q < nu; ++q) s += mom(U[q]) * X[U[q]][k];
+      }
+      out[r * 9 + k] = s;
+    }
+}
+
+int class_thermal_edge(int cls) {
+  static const int e[9] = {0, 1, 1, 2, 3, 2, 2, 3, 3};
+  return e[cls];
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// Handle
+// ------------------------------------------------------------------------------------
+struct lks_handle {
+  lks_problem_desc d;
+  Layout L;
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  cudaStream_t stream = nullptr;
+  int device = 0;
+  int cur = 0;      // which state buffer holds the current state (0 = A)
+  int acur = 0;     // which adjoint buffer holds the current adjoint
+  int t = 0;        // time level of the current state
+  int phase = 0;
+  int64_t fwd_steps = 0, adj_steps = 0, launches = 0;
+  std::vector<double> emap_h, tmap_h;
+  std::vector<float> emap_f, tmap_f;
+  std::string err;
+};
+
+namespace {
+
+lks_status fail(lks_handle* h, lks_status s, const std::string& m) {
+  if (h) h->err = m;
+  return s;
+}
+
+#define CKH(h, call)                                                                    \
+  do {                                                                                  \
+    cudaError_t e_ = (call);                                                            \
+    if (e_ != cudaSuccess)                                                              \
+      return fail(h, LKS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename R>
+Coef<R> make_coef(const lks_problem_desc& d) {
+  Coef<R> c;
+  c.A = (R)((1.0 / 6.0 - d.nu) * 4.5);
+  c.nu = (R)d.nu;
+  c.alpha_bar = (R)d.alpha_bar;
+  c.q_alpha = (R)d.q_alpha;
+  c.drho_out = (R)(d.rho_out - 1.0);
+  c.K_f = (R)d.K_f;
+  c.K_s = (R)d.K_s;
+  c.q_K = (R)d.q_K;
+  c.kappa_T = (R)d.kappa_T;
+  for (int e = 0; e < 4; ++e) c.t_val[e] = (R)d.t_val[e];
+  return c;
+}
+
+Geom make_geom(const lks_problem_desc& d) {
+  Geom g;
+  g.nx = d.nx;
+  g.ny = d.ny;
+  g.in_y0 = d.in_y0;
+  g.in_y1 = d.in_y1;
+  g.out_y0 = d.out_y0;
+  g.out_y1 = d.out_y1;
+  for (int e = 0; e < 4; ++e) g.t_kind[e] = d.thermal ? d.t_kind[e] : 0;
+  return g;
+}
+
+double inlet_amp(const lks_problem_desc& d, int t) {
+  double a = d.pulse_mean;
+  if (d.pulse_period > 0.0) a += d.pulse_amp * std::sin(2.0 * M_PI * (double)t / d.pulse_period);
+  return d.u_max * a;
+}
+
+template <typename R>
+R* fld(lks_handle* h, size_t off, int k) {
+  return reinterpret_cast<R*>(h->ws + off) + (size_t)k * h->L.N;
+}
+
+template <typename R>
+R* state_ptr(lks_handle* h, int which, int f) {
+  return fld<R>(h, which == 0 ? h->L.stA : h->L.stB, f);
+}
+template <typename R>
+R* adj_ptr(lks_handle* h, int which, int f) {
+  return fld<R>(h, which == 0 ? h->L.adA : h->L.adB, f);
+}
+
+template <typename R>
+lks_status set_smem_attrs() {
+  const int fs = (int)(fwd_smem_elems<false>() * sizeof(R)), fst = (int)(fwd_smem_elems<true>() * sizeof(R));
+  const int as = (int)(adj_smem_elems<false>() * sizeof(R)), ast = (int)(adj_smem_elems<true>() * sizeof(R));
+  cudaError_t e = cudaSuccess;
+  e = cudaFuncSetAttribute(fwd_step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, fs);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(fwd_step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, fst);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(adj_step_kernel<R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, as);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(adj_step_kernel<R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, ast);
+  return e == cudaSuccess ? LKS_OK : LKS_ERR_CUDA;
+}
+
+// One forward step: state `cur` -> other buffer, new level t_new.
+template <typename R>
+lks_status launch_fwd(lks_handle* h, int t_new, double* Jpartial, R* tu, R* tv, R* tT) {
+  const auto& d = h->d;
+  FwdArgs<R> a;
+  const int src = h->cur, dst = 1 - h->cur;
+  a.drho = state_ptr<R>(h, src, 0);
+  a.u = state_ptr<R>(h, src, 1);
+  a.v = state_ptr<R>(h, src, 2);
+  a.T = d.thermal ? state_ptr<R>(h, src, 3) : nullptr;
+  a.drho_n = state_ptr<R>(h, dst, 0);
+  a.u_n = state_ptr<R>(h, dst, 1);
+  a.v_n = state_ptr<R>(h, dst, 2);
+  a.T_n = d.thermal ? state_ptr<R>(h, dst, 3) : nullptr;
+  a.gamma = fld<R>(h, h->L.gamma, 0);
+  a.u_in = (R)inlet_amp(d, t_new);
+  a.J_partial = Jpartial;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.traj_u = tu;
+  a.traj_v = tv;
+  a.traj_T = tT;
+  const dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY);
+  const Geom g = make_geom(d);
+  const Coef<R> c = make_coef<R>(d);
+  if (d.thermal)
+    fwd_step_kernel<R, true><<<grid, NTHREADS, fwd_smem_elems<true>() * sizeof(R), h->stream>>>(a, g, c);
+  else
+    fwd_step_kernel<R, false><<<grid, NTHREADS, fwd_smem_elems<false>() * sizeof(R), h->stream>>>(a, g, c);
+  CKH(h, cudaGetLastError());
+  h->cur = dst;
+  h->t = t_new;
+  h->fwd_steps++;
+  h->launches++;
+  return LKS_OK;
+}
+
+// One adjoint step: adjoint `acur` (level t+1) -> other buffer (level t).
+template <typename R>
+lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, const R* v0, const R* T0,
+                      R* sens, int sens_flow, int sens_thermal) {
+  const auto& d = h->d;
+  AdjArgs<R> a;
+  const int src = h->acur, dst = 1 - h->acur;
+  for (int f = 0; f < 9; ++f) {
+    const int ff = (f < h->L.nA) ? f : 0;
+    a.m1[f] = adj_ptr<R>(h, src, ff);
+    a.m0[f] = adj_ptr<R>(h, dst, ff);
+  }
+  a.u1 = u1;
+  a.v1 = v1;
+  a.u0 = u0;
+  a.v0 = v0;
+  a.T0 = T0;
+  a.gamma = fld<R>(h, h->L.gamma, 0);
+  a.emap = reinterpret_cast<const R*>(h->ws + h->L.emap);
+  a.tmap = reinterpret_cast<const R*>(h->ws + h->L.tmap);
+  a.sens = sens;
+  a.sens_flow = sens_flow;
+  a.sens_thermal = sens_thermal;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  const dim3 grid((d.nx + TX - 1) / TX, (d.ny + TY - 1) / TY);
+  const Geom g = make_geom(d);
+  const Coef<R> c = make_coef<R>(d);
+  if (d.thermal)
+    adj_step_kernel<R, true><<<grid, NTHREADS, adj_smem_elems<true>() * sizeof(R), h->stream>>>(a, g, c);
+  else
+    adj_step_kernel<R, false><<<grid, NTHREADS, adj_smem_elems<false>() * sizeof(R), h->stream>>>(a, g, c);
+  CKH(h, cudaGetLastError());
+  h->acur = dst;
+  h->adj_steps++;
+  h->launches++;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status launch_objective(lks_handle* h, const R* u, const R* v, const R* T, double* partial) {
+  const auto& d = h->d;
+  const Geom g = make_geom(d);
+  const Coef<R> c = make_coef<R>(d);
+  const R* gam = fld<R>(h, h->L.gamma, 0);
+  if (d.thermal)
+    objective_kernel<R, true><<<h->L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, gam, g, c, partial);
+  else
+    objective_kernel<R, false><<<h->L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, gam, g, c, partial);
+  CKH(h, cudaGetLastError());
+  h->launches++;
+  return LKS_OK;
+}
+
+int elementwise_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+
+// Snapshot encode / decode of one field with a per-field scale (max |x|).
+template <typename R, typename S>
+__global__ void absmax_kernel(const R* __restrict__ x, size_t n, float* out) {
+  float m = 0.f;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    m = fmaxf(m, fabsf((float)x[o]));
+  for (int s = 16; s > 0; s >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, s));
+  if ((threadIdx.x & 31) == 0) atomicMax(reinterpret_cast<int*>(out), __float_as_int(m));
+}
+
+template <typename S>
+__device__ __forceinline__ S to_snap(float v);
+template <>
+__device__ __forceinline__ float to_snap<float>(float v) { return v; }
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_snap<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
+template <>
+__device__ __forceinline__ __half to_snap<__half>(float v) { return __float2half_rn(v); }
+__device__ __forceinline__ float from_snap(float v) { return v; }
+__device__ __forceinline__ float from_snap(__nv_bfloat16 v) { return __bfloat162float(v); }
+__device__ __forceinline__ float from_snap(__half v) { return __half2float(v); }
+
+template <typename R, typename S>
+__global__ void encode_kernel(const R* __restrict__ x, S* __restrict__ y, size_t n, const float* scale) {
+  const float s = *scale;
+  const float inv = s > 0.f ? 1.f / s : 0.f;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    y[o] = to_snap<S>((float)x[o] * inv);
+}
+template <typename R, typename S>
+__global__ void decode_kernel(const S* __restrict__ y, R* __restrict__ x, size_t n, const float* scale) {
+  const float s = *scale;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    x[o] = (R)(from_snap(y[o]) * s);
+}
+
+template <typename R>
+lks_status snapshot_store(lks_handle* h, int idx) {
+  const auto& L = h->L;
+  const size_t N = L.N;
+  float* sc = reinterpret_cast<float*>(h->ws + L.scales) + (size_t)idx * 2 * L.nF;
+  unsigned char* base = h->ws + L.snaps + (size_t)idx * L.nF * N * L.snap_elem;
+  const int gsz = elementwise_grid(N);
+  if (h->d.snapshot_type == LKS_SNAP_F32 && sizeof(R) == 4) {
+    CKH(h, cudaMemcpyAsync(base, state_ptr<R>(h, h->cur, 0), N * L.nF * sizeof(R), cudaMemcpyDeviceToDevice,
+                           h->stream));
+    return LKS_OK;
+  }
+  CKH(h, cudaMemsetAsync(sc, 0, sizeof(float) * L.nF, h->stream));
+  for (int f = 0; f < L.nF; ++f) {
+    const R* x = state_ptr<R>(h, h->cur, f);
+    absmax_kernel<R, float><<<gsz, 256, 0, h->stream>>>(x, N, sc + f);
+    unsigned char* dst = base + (size_t)f * N * L.snap_elem;
+    switch (h->d.snapshot_type) {
+      case LKS_SNAP_BF16:
+        encode_kernel<R, __nv_bfloat16><<<gsz, 256, 0, h->stream>>>(x, reinterpret_cast<__nv_bfloat16*>(dst), N, sc + f);
+        break;
+      case LKS_SNAP_F16:
+        encode_kernel<R, __half><<<gsz, 256, 0, h->stream>>>(x, reinterpret_cast<__half*>(dst), N, sc + f);
+        break;
+      default:
+        encode_kernel<R, float><<<gsz, 256, 0, h->stream>>>(x, reinterpret_cast<float*>(dst), N, sc + f);
+    }
+    h->launches += 2;
+  }
+  CKH(h, cudaGetLastError());
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status snapshot_load(lks_handle* h, int idx) {
+  const auto& L = h->L;
+  const size_t N = L.N;
+  const float* sc = reinterpret_cast<const float*>(h->ws + L.scales) + (size_t)idx * 2 * L.nF;
+  const unsigned char* base = h->ws + L.snaps + (size_t)idx * L.nF * N * L.snap_elem;
+  const int gsz = elementwise_grid(N);
+  if (h->d.snapshot_type == LKS_SNAP_F32 && sizeof(R) == 4) {
+    CKH(h, cudaMemcpyAsync(state_ptr<R>(h, h->cur, 0), base, N * L.nF * sizeof(R), cudaMemcpyDeviceToDevice,
+                           h->stream));
+    return LKS_OK;
+  }
+  for (int f = 0; f < L.nF; ++f) {
+    R* x = state_ptr<R>(h, h->cur, f);
+    const unsigned char* src = base + (size_t)f * N * L.snap_elem;
+    switch (h->d.snapshot_type) {
+      case LKS_SNAP_BF16:
+        decode_kernel<R, __nv_bfloat16><<<gsz, 256, 0, h->stream>>>(reinterpret_cast<const __nv_bfloat16*>(src), x, N, sc + f);
+        break;
+      case LKS_SNAP_F16:
+        decode_kernel<R, __half><<<gsz, 256, 0, h->stream>>>(reinterpret_cast<const __half*>(src), x, N, sc + f);
+        break;
+      default:
+        decode_kernel<R, float><<<gsz, 256, 0, h->stream>>>(reinterpret_cast<const float*>(src), x, N, sc + f);
+    }
+    h->launches++;
+  }
+  CKH(h, cudaGetLastError());
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
+  const auto& d = h->d;
+  const auto& L = h->L;
+  const size_t fb = L.N * sizeof(R);
+  if (gamma_dev != h->ws + L.gamma)
+    CKH(h, cudaMemcpyAsync(h->ws + L.gamma, gamma_dev, fb, cudaMemcpyDeviceToDevice, h->stream));
+  CKH(h, cudaMemsetAsync(h->ws + L.stA, 0, fb * L.nF, h->stream));
+  CKH(h, cudaMemsetAsync(h->ws + L.status, 0, sizeof(int), h->stream));
+  h->cur = 0;
+  h->t = 0;
+  double* jfwd = reinterpret_cast<double*>(h->ws + L.jfwd);
+  double* jobj = reinterpret_cast<double*>(h->ws + L.jobj);
+  double* jval = reinterpret_cast<double*>(h->ws + L.jval);
+  lks_status st;
+  if (d.steady) {
+    for (int s = 1; s <= d.n_steps; ++s)
+      if ((st = launch_fwd<R>(h, s, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
+    CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
+  } else {
+    CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
+    const bool plain = d.checkpoint_every == 0;
+    if (plain) {  // level 0 of the trajectory
+      R* tr = fld<R>(h, L.traj, 0);
+      for (int f = 0; f < L.nT; ++f)
+        CKH(h, cudaMemcpyAsync(tr + (size_t)f * L.N, state_ptr<R>(h, h->cur, f == 2 ? 3 : f + 1), fb,
+                               cudaMemcpyDeviceToDevice, h->stream));
+    }
+    for (int t = 0; t < d.n_steps; ++t) {
+      if (!plain && t % d.checkpoint_every == 0)
+        if ((st = snapshot_store<R>(h, t / d.checkpoint_every)) != LKS_OK) return st;
+      R *tu = nullptr, *tv = nullptr, *tT = nullptr;
+      if (plain) {
+        R* tr = fld<R>(h, L.traj, 0) + (size_t)(t + 1) * L.nT * L.N;
+        tu = tr;
+        tv = tr + L.N;
+        tT = d.thermal ? tr + 2 * L.N : nullptr;
+      }
+      if ((st = launch_fwd<R>(h, t + 1, t >= 1 ? jfwd : nullptr, tu, tv, tT)) != LKS_OK) return st;
+    }
+  }
+  R* u = state_ptr<R>(h, h->cur, 1);
+  R* v = state_ptr<R>(h, h->cur, 2);
+  R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
+  if ((st = launch_objective<R>(h, u, v, T, jobj)) != LKS_OK) return st;
+  reduce_partials_kernel<<<1, NTHREADS, 0, h->stream>>>(jobj, L.obj_blocks, jfwd, d.steady ? 0 : L.fwd_blocks, jval);
+  CKH(h, cudaGetLastError());
+  h->launches++;
+  if (J_dev) CKH(h, cudaMemcpyAsync(J_dev, jval, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
+  h->phase = 1;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status flush_sens(lks_handle* h) {
+  const auto& L = h->L;
+  flush_accum_kernel<R><<<elementwise_grid(L.N), 256, 0, h->stream>>>(fld<R>(h, L.sens, 0),
+                                                                       reinterpret_cast<double*>(h->ws + L.sens64), L.N);
+  CKH(h, cudaGetLastError());
+  h->launches++;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status adjoint_impl(lks_handle* h) {
+  const auto& d = h->d;
+  const auto& L = h->L;
+  const size_t fb = L.N * sizeof(R);
+  CKH(h, cudaMemsetAsync(h->ws + L.adA, 0, fb * L.nA, h->stream));
+  h->acur = 0;
+  lks_status st;
+  if (d.steady) {
+    const R* u = state_ptr<R>(h, h->cur, 1);
+    const R* v = state_ptr<R>(h, h->cur, 2);
+    const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
+    for (int it = 0; it < d.n_adj; ++it)
+      if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+    h->phase = 2;
+    return LKS_OK;
+  }
+  CKH(h, cudaMemsetAsync(h->ws + L.sens, 0, fb, h->stream));
+  CKH(h, cudaMemsetAsync(h->ws + L.sens64, 0, sizeof(double) * L.N, h->stream));
+  const int n = d.n_steps;
+  const int t_end = d.thermal ? 0 : 1;
+  const int flush_every = 256;
+  int since_flush = 0;
+  auto level_ptrs = [&](R* base, int lev, const R** u, const R** v, const R** T) {
+    R* p = base + (size_t)lev * L.nT * L.N;
+    *u = p;
+    *v = p + L.N;
+    *T = d.thermal ? p + 2 * L.N : nullptr;
+  };
+  if (d.checkpoint_every == 0) {
+    R* tr = fld<R>(h, L.traj, 0);
+    for (int t = n; t >= t_end; --t) {
+      const R *u1, *v1, *T1, *u0, *v0, *T0;
+      level_ptrs(tr, std::min(t + 1, n), &u1, &v1, &T1);
+      level_ptrs(tr, t, &u0, &v0, &T0);
+      if ((st = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return st;
+      if (++since_flush == flush_every) {
+        if ((st = flush_sens<R>(h)) != LKS_OK) return st;
+        since_flush = 0;
+      }
+    }
+  } else {
+    const int K = d.checkpoint_every;
+    R* seg = fld<R>(h, L.seg, 0);
+    for (int s = L.n_ckpt - 1; s >= 0; --s) {
+      const int t_lo = s * K, t_hi = std::min((s + 1) * K, n), top = std::min(t_hi + 1, n);
+      h->cur = 0;
+      if ((st = snapshot_load<R>(h, s)) != LKS_OK) return st;
+      // level t_lo into the segment buffer, then recompute t_lo+1 .. top
+      for (int f = 0; f < L.nT; ++f)
+        CKH(h, cudaMemcpyAsync(seg + (size_t)f * L.N, state_ptr<R>(h, h->cur, f == 2 ? 3 : f + 1), fb,
+                               cudaMemcpyDeviceToDevice, h->stream));
+      for (int t = t_lo; t < top; ++t) {
+        R* p = seg + (size_t)(t + 1 - t_lo) * L.nT * L.N;
+        if ((st = launch_fwd<R>(h, t + 1, nullptr, p, p + L.N, d.thermal ? p + 2 * L.N : nullptr)) != LKS_OK)
+          return st;
+      }
+      const int t_stop = (s == 0) ? t_end : t_lo + 1;
+      for (int t = t_hi; t >= t_stop; --t) {
+        const R *u1, *v1, *T1, *u0, *v0, *T0;
+        level_ptrs(seg, std::min(t + 1, n) - t_lo, &u1, &v1, &T1);
+        level_ptrs(seg, t - t_lo, &u0, &v0, &T0);
+        if ((st = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return st;
+        if (++since_flush == flush_every) {
+          if ((st = flush_sens<R>(h)) != LKS_OK) return st;
+          since_flush = 0;
+        }
+      }
+    }
+  }
+  if ((st = flush_sens<R>(h)) != LKS_OK) return st;
+  h->phase = 2;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status sensitivity_impl(lks_handle* h, void* out) {
+  const auto& d = h->d;
+  const auto& L = h->L;
+  if (d.steady) {
+    const Geom g = make_geom(d);
+    const Coef<R> c = make_coef<R>(d);
+    const R* u = state_ptr<R>(h, h->cur, 1);
+    const R* v = state_ptr<R>(h, h->cur, 2);
+    const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
+    const R* ux = adj_ptr<R>(h, h->acur, 1);
+    const R* uy = adj_ptr<R>(h, h->acur, 2);
+    const R* qx = d.thermal ? adj_ptr<R>(h, h->acur, 7) : nullptr;
+    const R* qy = d.thermal ? adj_ptr<R>(h, h->acur, 8) : nullptr;
+    const R* gam = fld<R>(h, L.gamma, 0);
+    if (d.thermal)
+      sensitivity_kernel<R, true><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, qx, qy, gam, g, c,
+                                                                            reinterpret_cast<R*>(out));
+    else
+      sensitivity_kernel<R, false><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, qx, qy, gam, g, c,
+                                                                             reinterpret_cast<R*>(out));
+  } else {
+    copy_shift_kernel<double, R><<<elementwise_grid(L.N), 256, 0, h->stream>>>(
+        reinterpret_cast<const double*>(h->ws + L.sens64), reinterpret_cast<R*>(out), L.N, 0.0);
+  }
+  CKH(h, cudaGetLastError());
+  h->launches++;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status upload_maps(lks_handle* h) {
+  const auto& d = h->d;
+  const double A = (1.0 / 6.0 - d.nu) * 4.5;
+  h->emap_h.assign(9 * 54, 0.0);
+  h->tmap_h.assign(9 * 27, 0.0);
+  for (int cls = 0; cls < 9; ++cls) {
+    flow_moment_map(A, cls, &h->emap_h[cls * 54]);
+    if (d.thermal) {
+      const double B = 3.0 * (1.0 / 6.0 - d.K_f);  // gamma = 1 on edges
+      thermal_moment_map(B, cls, d.t_kind[class_thermal_edge(cls)] == LKS_T_FLUX, &h->tmap_h[cls * 27]);
+    }
+  }
+  if (sizeof(R) == 8) {
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_h.data(), 9 * 54 * 8, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.tmap, h->tmap_h.data(), 9 * 27 * 8, cudaMemcpyHostToDevice));
+  } else {
+    h->emap_f.assign(h->emap_h.begin(), h->emap_h.end());
+    h->tmap_f.assign(h->tmap_h.begin(), h->tmap_h.end());
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_f.data(), 9 * 54 * 4, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.tmap, h->tmap_f.data(), 9 * 27 * 4, cudaMemcpyHostToDevice));
+  }
+  return LKS_OK;
+}
+
+lks_status check_handle(lks_handle* h) { return h ? LKS_OK : LKS_ERR_INVALID_ARG; }
+
+}  // namespace
+
+// ------------------------------------------------------------------------------------
+// C ABI
+// ------------------------------------------------------------------------------------
+extern "C" {
+
+const char* lks_status_string(lks_status s) {
+  switch (s) {
+    case LKS_OK: return "ok";
+    case LKS_ERR_INVALID_ARG: return "invalid argument";
+    case LKS_ERR_WORKSPACE: return "workspace too small or misaligned";
+    case LKS_ERR_CUDA: return "CUDA error";
+    case LKS_ERR_UNSTABLE: return "non-finite or runaway velocity";
+    case LKS_ERR_NOT_CONVERGED: return "not converged";
+    case LKS_ERR_TIMEOUT: return "device wait timed out";
+    case LKS_ERR_STATE: return "calls out of order";
+  }
+  return "unknown status";
+}
+
+const char* lks_last_error(const lks_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+lks_status lks_workspace_size(const lks_problem_desc* desc, size_t* bytes) {
+  if (!bytes) return LKS_ERR_INVALID_ARG;
+  lks_status s = check_desc(desc, nullptr);
+  if (s != LKS_OK) return s;
+  *bytes = make_layout(desc).total;
+  return LKS_OK;
+}
+
+lks_status lks_create(const lks_problem_desc* desc, void* workspace, size_t bytes, void* stream,
+                      lks_handle** out) {
+  if (!out) return LKS_ERR_INVALID_ARG;
+  *out = nullptr;
+  std::string why;
+  lks_status s = check_desc(desc, &why);
+  if (s != LKS_OK) return s;
+  const Layout L = make_layout(desc);
+  if (!workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+    return LKS_ERR_WORKSPACE;
+  lks_handle* h = new (std::nothrow) lks_handle();
+  if (!h) return LKS_ERR_INVALID_ARG;
+  h->d = *desc;
+  h->L = L;
+  h->ws = reinterpret_cast<unsigned char*>(workspace);
+  h->ws_bytes = bytes;
+  h->stream = reinterpret_cast<cudaStream_t>(stream);
+  cudaGetDevice(&h->device);
+  s = desc->real_type == LKS_REAL_F64 ? set_smem_attrs<double>() : set_smem_attrs<float>();
+  if (s == LKS_OK) s = desc->real_type == LKS_REAL_F64 ? upload_maps<double>(h) : upload_maps<float>(h);
+  if (s != LKS_OK) {
+    delete h;
+    return s;
+  }
+  *out = h;
+  return LKS_OK;
+}
+
+lks_status lks_destroy(lks_handle* h) {
+  if (!h) return LKS_ERR_INVALID_ARG;
+  delete h;
+  return LKS_OK;
+}
+
+lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
+  if (check_handle(h) != LKS_OK || !gamma_dev) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  return h->d.real_type == LKS_REAL_F64 ? forward_impl<double>(h, gamma_dev, J_dev)
+                                        : forward_impl<float>(h, gamma_dev, J_dev);
+}
+
+lks_status alks_adjoint(lks_handle* h) {
+  if (check_handle(h) != LKS_OK) return LKS_ERR_INVALID_ARG;
+  if (h->phase < 1) return fail(h, LKS_ERR_STATE, "alks_adjoint before lks_forward");
+  return h->d.real_type == LKS_REAL_F64 ? adjoint_impl<double>(h) : adjoint_impl<float>(h);
+}
+
+lks_status lks_sensitivity(lks_handle* h, void* out) {
+  if (check_handle(h) != LKS_OK || !out) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  if (h->phase < 2) return fail(h, LKS_ERR_STATE, "lks_sensitivity before alks_adjoint");
+  return h->d.real_type == LKS_REAL_F64 ? sensitivity_impl<double>(h, out) : sensitivity_impl<float>(h, out);
+}
+
+lks_status lks_gradient_host(lks_handle* h, const void* gamma_host, double* J_host, void* grad_host) {
+  if (check_handle(h) != LKS_OK || !gamma_host || !J_host || !grad_host)
+    return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const size_t fb = h->L.N * h->L.rsize;
+  // The gradient is staged in the inactive adjoint buffer's first field, gamma in
+  // the workspace copy itself (lks_forward copies device to device onto itself).
+  unsigned char* g_dev = h->ws + h->L.gamma;
+  CKH(h, cudaMemcpyAsync(g_dev, gamma_host, fb, cudaMemcpyHostToDevice, h->stream));
+  lks_status s = lks_forward(h, g_dev, nullptr);
+  if (s == LKS_OK) s = alks_adjoint(h);
+  if (s != LKS_OK) return s;
+  unsigned char* grad_dev = h->ws + (h->acur == 0 ? h->L.adB : h->L.adA);
+  if ((s = lks_sensitivity(h, grad_dev)) != LKS_OK) return s;
+  CKH(h, cudaMemcpyAsync(grad_host, grad_dev, fb, cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaMemcpyAsync(J_host, h->ws + h->L.jval, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  int status = 0;
+  CKH(h, cudaMemcpyAsync(&status, h->ws + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaStreamSynchronize(h->stream));
+  if (status != 0) return fail(h, (lks_status)status, "device status set during the gradient");
+  return LKS_OK;
+}
+
+lks_status lks_set_state(lks_handle* h, const void* gamma_dev, const void* rho_dev, const void* u_dev,
+                         const void* v_dev, const void* T_dev, int32_t t) {
+  if (check_handle(h) != LKS_OK || !gamma_dev || !rho_dev || !u_dev || !v_dev || (h->d.thermal && !T_dev))
+    return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const size_t fb = h->L.N * h->L.rsize;
+  CKH(h, cudaMemcpyAsync(h->ws + h->L.gamma, gamma_dev, fb, cudaMemcpyDeviceToDevice, h->stream));
+  const void* src[4] = {rho_dev, u_dev, v_dev, T_dev};
+  h->cur = 0;
+  for (int f = 0; f < h->L.nF; ++f)
+    CKH(h, cudaMemcpyAsync(h->ws + h->L.stA + (size_t)f * fb, src[f], fb, cudaMemcpyDeviceToDevice, h->stream));
+  h->t = t;
+  if (h->phase < 1) h->phase = 1;
+  return LKS_OK;
+}
+
+lks_status lks_get_state(lks_handle* h, void* rho_dev, void* u_dev, void* v_dev, void* T_dev) {
+  if (check_handle(h) != LKS_OK || !rho_dev || !u_dev || !v_dev || (h->d.thermal && !T_dev))
+    return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const size_t fb = h->L.N * h->L.rsize;
+  void* dst[4] = {rho_dev, u_dev, v_dev, T_dev};
+  const size_t base = h->cur == 0 ? h->L.stA : h->L.stB;
+  for (int f = 0; f < h->L.nF; ++f)
+    CKH(h, cudaMemcpyAsync(dst[f], h->ws + base + (size_t)f * fb, fb, cudaMemcpyDeviceToDevice, h->stream));
+  return LKS_OK;
+}
+
+lks_status lks_march(lks_handle* h, int32_t n) {
+  if (check_handle(h) != LKS_OK || n < 0) return fail(h, LKS_ERR_INVALID_ARG, "bad argument");
+  for (int s = 0; s < n; ++s) {
+    lks_status st = h->d.real_type == LKS_REAL_F64
+                        ? launch_fwd<double>(h, h->t + 1, nullptr, nullptr, nullptr, nullptr)
+                        : launch_fwd<float>(h, h->t + 1, nullptr, nullptr, nullptr, nullptr);
+    if (st != LKS_OK) return st;
+  }
+  return LKS_OK;
+}
+
+lks_status alks_set_adjoint(lks_handle* h, void* const* fields) {
+  if (check_handle(h) != LKS_OK || !fields) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const size_t fb = h->L.N * h->L.rsize;
+  h->acur = 0;
+  for (int f = 0; f < h->L.nA; ++f) {
+    if (!fields[f]) return fail(h, LKS_ERR_INVALID_ARG, "null field");
+    CKH(h, cudaMemcpyAsync(h->ws + h->L.adA + (size_t)f * fb, fields[f], fb, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return LKS_OK;
+}
+
+lks_status alks_get_adjoint(lks_handle* h, void* const* fields) {
+  if (check_handle(h) != LKS_OK || !fields) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const size_t fb = h->L.N * h->L.rsize;
+  const size_t base = h->acur == 0 ? h->L.adA : h->L.adB;
+  for (int f = 0; f < h->L.nA; ++f) {
+    if (!fields[f]) return fail(h, LKS_ERR_INVALID_ARG, "null field");
+    CKH(h, cudaMemcpyAsync(fields[f], h->ws + base + (size_t)f * fb, fb, cudaMemcpyDeviceToDevice, h->stream));
+  }
+  return LKS_OK;
+}
+
+lks_status alks_march(lks_handle* h, int32_t n) {
+  if (check_handle(h) != LKS_OK || n < 0) return fail(h, LKS_ERR_INVALID_ARG, "bad argument");
+  for (int s = 0; s < n; ++s) {
+    lks_status st;
+    if (h->d.real_type == LKS_REAL_F64) {
+      const double* u = state_ptr<double>(h, h->cur, 1);
+      const double* v = state_ptr<double>(h, h->cur, 2);
+      const double* T = h->d.thermal ? state_ptr<double>(h, h->cur, 3) : nullptr;
+      st = launch_adj<double>(h, u, v, u, v, T, nullptr, 0, 0);
+    } else {
+      const float* u = state_ptr<float>(h, h->cur, 1);
+      const float* v = state_ptr<float>(h, h->cur, 2);
+      const float* T = h->d.thermal ? state_ptr<float>(h, h->cur, 3) : nullptr;
+      st = launch_adj<float>(h, u, v, u, v, T, nullptr, 0, 0);
+    }
+    if (st != LKS_OK) return st;
+  }
+  if (h->phase < 2) h->phase = 2;
+  return LKS_OK;
+}
+
+lks_status lks_query(lks_handle* h, lks_stats* out) {
+  if (check_handle(h) != LKS_OK || !out) return LKS_ERR_INVALID_ARG;
+  int status = 0;
+  CKH(h, cudaMemcpyAsync(&status, h->ws + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaStreamSynchronize(h->stream));
+  out->forward_steps = h->fwd_steps;
+  out->adjoint_steps = h->adj_steps;
+  out->kernel_launches = h->launches;
+  out->workspace_bytes = h->L.total;
+  out->device_status = status;
+  out->phase = h->phase;
+  return status ? (lks_status)status : LKS_OK;
+}
+
+lks_status lks_edge_moment_map(double A, int32_t cls, double* out) {
+  if (!out || cls < 0 || cls > 8) return LKS_ERR_INVALID_ARG;
+  flow_moment_map(A, cls, out);
+  return LKS_OK;
+}
+
+}  // extern "C"

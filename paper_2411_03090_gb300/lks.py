@@ -1,0 +1,276 @@
+"""Python binding of the C ABI in ``include/lks.h`` (argument marshalling only).
+
+Every computation runs in the CUDA kernels of ``_lib/liblks.so``; PyTorch supplies
+device memory (the workspace and the caller's buffers) and the CUDA stream.  The
+names follow the C entry points: ``lks_forward`` (Steps 2-3 of the paper's
+procedure, Sec. 2.7), ``alks_adjoint`` (Step 4), ``lks_sensitivity`` (Step 5).
+
+If the library is missing this module raises; there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional, Sequence
+
+import numpy as np
+import torch
+
+from . import _build
+
+LKS_DESC_VERSION = 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "unstable",
+          5: "not converged", 6: "timeout", 7: "calls out of order"}
+REAL = {"f32": 0, "f64": 1}
+SNAP = {"f32": 0, "bf16": 1, "f16": 2}
+N_ADJ_FIELDS = 9
+ADJ_NAMES = ("rho_t", "ux_t", "uy_t", "sxx_t", "sxy_t", "syy_t", "T_t", "qx_t", "qy_t")
+
+
+class LKSError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({STATUS.get(status, '?')})")
+        self.status = status
+
+
+class Desc(C.Structure):
+    """Mirror of ``lks_problem_desc``."""
+
+    _fields_ = [
+        ("version", C.c_int32), ("nx", C.c_int32), ("ny", C.c_int32), ("real_type", C.c_int32),
+        ("nu", C.c_double), ("alpha_bar", C.c_double), ("q_alpha", C.c_double),
+        ("u_max", C.c_double), ("pulse_mean", C.c_double), ("pulse_amp", C.c_double),
+        ("pulse_period", C.c_double),
+        ("in_y0", C.c_int32), ("in_y1", C.c_int32), ("out_y0", C.c_int32), ("out_y1", C.c_int32),
+        ("rho_out", C.c_double),
+        ("thermal", C.c_int32), ("steady", C.c_int32),
+        ("K_f", C.c_double), ("K_s", C.c_double), ("q_K", C.c_double),
+        ("t_kind", C.c_int32 * 4), ("t_val", C.c_double * 4),
+        ("kappa_T", C.c_double),
+        ("n_steps", C.c_int32), ("n_adj", C.c_int32),
+        ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
+        ("reserved", C.c_int32 * 8),
+    ]
+
+
+class Stats(C.Structure):
+    _fields_ = [("forward_steps", C.c_int64), ("adjoint_steps", C.c_int64),
+                ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_size_t),
+                ("device_status", C.c_int32), ("phase", C.c_int32)]
+
+
+# Every symbol the header declares (checked by the CPU test-suite).
+EXPORTS = ("lks_workspace_size", "lks_create", "lks_forward", "alks_adjoint", "lks_sensitivity",
+           "lks_gradient_host", "lks_set_state", "lks_get_state", "lks_march", "alks_set_adjoint",
+           "alks_get_adjoint", "alks_march", "lks_query", "lks_destroy", "lks_status_string",
+           "lks_last_error", "lks_edge_moment_map")
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = True):
+    """Load ``liblks.so`` (building it first if asked); raises if it cannot."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build_if_missing:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"CUDA library {_build.LIB} is missing; run __graft_entry__.build()")
+    L = C.CDLL(_build.LIB)
+    vp, i32, dp = C.c_void_p, C.c_int32, C.POINTER(C.c_double)
+    hp = C.c_void_p
+    L.lks_workspace_size.argtypes = [C.POINTER(Desc), C.POINTER(C.c_size_t)]
+    L.lks_create.argtypes = [C.POINTER(Desc), vp, C.c_size_t, vp, C.POINTER(hp)]
+    L.lks_forward.argtypes = [hp, vp, vp]
+    L.alks_adjoint.argtypes = [hp]
+    L.lks_sensitivity.argtypes = [hp, vp]
+    L.lks_gradient_host.argtypes = [hp, vp, vp, vp]
+    L.lks_set_state.argtypes = [hp, vp, vp, vp, vp, vp, i32]
+    L.lks_get_state.argtypes = [hp, vp, vp, vp, vp]
+    L.lks_march.argtypes = [hp, i32]
+    L.alks_set_adjoint.argtypes = [hp, C.POINTER(vp)]
+    L.alks_get_adjoint.argtypes = [hp, C.POINTER(vp)]
+    L.alks_march.argtypes = [hp, i32]
+    L.lks_query.argtypes = [hp, C.POINTER(Stats)]
+    L.lks_destroy.argtypes = [hp]
+    L.lks_status_string.argtypes = [i32]
+    L.lks_status_string.restype = C.c_char_p
+    L.lks_last_error.argtypes = [hp]
+    L.lks_last_error.restype = C.c_char_p
+    L.lks_edge_moment_map.argtypes = [C.c_double, i32, dp]
+    for name in EXPORTS:
+        if name not in ("lks_status_string", "lks_last_error"):
+            getattr(L, name).restype = C.c_int
+    _lib = L
+    return L
+
+
+def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32") -> Desc:
+    """Descriptor from an ``inputs.Problem``-like object."""
+    d = Desc()
+    d.version = LKS_DESC_VERSION
+    d.nx, d.ny = int(pb.nx), int(pb.ny)
+    d.real_type = REAL[real]
+    for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
+                 "rho_out", "K_f", "K_s", "q_K", "kappa_T"):
+        setattr(d, name, float(getattr(pb, name)))
+    res = pb.resolved if hasattr(pb, "resolved") else (lambda n: getattr(pb, n))
+    d.in_y0, d.in_y1 = int(res("in_y0")), int(res("in_y1"))
+    d.out_y0, d.out_y1 = int(res("out_y0")), int(res("out_y1"))
+    d.thermal = int(pb.thermal)
+    d.steady = int(bool(pb.steady))
+    for e in range(4):
+        d.t_kind[e] = int(pb.t_kind[e])
+        d.t_val[e] = float(pb.t_val[e])
+    d.n_steps = int(pb.n_steps)
+    d.n_adj = int(pb.n_adj)
+    d.checkpoint_every = int(checkpoint_every)
+    d.snapshot_type = SNAP[snapshot]
+    return d
+
+
+def workspace_size(desc: Desc) -> int:
+    L = load()
+    n = C.c_size_t(0)
+    _check(L.lks_workspace_size(C.byref(desc), C.byref(n)), "lks_workspace_size")
+    return int(n.value)
+
+
+def _check(status: int, what: str, handle=None) -> None:
+    if status != 0:
+        msg = what
+        if handle is not None:
+            msg += ": " + load().lks_last_error(handle).decode()
+        raise LKSError(status, msg)
+
+
+def edge_moment_map(A: float, cls: int) -> np.ndarray:
+    """Host-only: the 6 x 9 adjoint edge moment map of class ``cls``."""
+    out = np.zeros(54)
+    _check(load().lks_edge_moment_map(float(A), int(cls),
+                                      out.ctypes.data_as(C.POINTER(C.c_double))), "edge map")
+    return out.reshape(6, 9)
+
+
+class LKS:
+    """One problem on one device: owns its workspace (a torch uint8 tensor) and the
+    library handle.  Fields are (ny, nx) tensors of the descriptor's real type."""
+
+    def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
+                 device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LKS library needs a CUDA device")
+        self.L = load()
+        self.pb = pb
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot)
+        self.dtype = torch.float64 if real == "f64" else torch.float32
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.shape = (int(pb.ny), int(pb.nx))
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            nbytes = workspace_size(self.desc)
+            self.workspace = torch.empty(nbytes, dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            _check(self.L.lks_create(C.byref(self.desc), C.c_void_p(self.workspace.data_ptr()),
+                                     C.c_size_t(nbytes), C.c_void_p(self.stream.cuda_stream),
+                                     C.byref(h)), "lks_create")
+        self.h = h
+        self.J = torch.zeros((), dtype=torch.float64, device=self.device)
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.L.lks_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    # -- helpers ------------------------------------------------------------------------
+    def _field(self, t: torch.Tensor) -> torch.Tensor:
+        if t.dtype != self.dtype or t.device != self.device or tuple(t.shape) != self.shape:
+            t = t.to(device=self.device, dtype=self.dtype).reshape(self.shape)
+        return t.contiguous()
+
+    def _ptr(self, t: torch.Tensor):
+        return C.c_void_p(t.data_ptr())
+
+    def empty(self) -> torch.Tensor:
+        return torch.empty(self.shape, dtype=self.dtype, device=self.device)
+
+    # -- Steps 2-5 ----------------------------------------------------------------------
+    def lks_forward(self, gamma: torch.Tensor) -> torch.Tensor:
+        g = self._field(gamma)
+        _check(self.L.lks_forward(self.h, self._ptr(g), C.c_void_p(self.J.data_ptr())),
+               "lks_forward", self.h)
+        self._gamma_keep = g
+        return self.J
+
+    def alks_adjoint(self) -> None:
+        _check(self.L.alks_adjoint(self.h), "alks_adjoint", self.h)
+
+    def lks_sensitivity(self, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+        out = self.empty() if out is None else out
+        _check(self.L.lks_sensitivity(self.h, self._ptr(out)), "lks_sensitivity", self.h)
+        return out
+
+    def gradient(self, gamma: torch.Tensor):
+        """(J, dJ/dgamma) with device buffers."""
+        J = self.lks_forward(gamma).clone()
+        self.alks_adjoint()
+        return J, self.lks_sensitivity()
+
+    def gradient_host(self, gamma_host: np.ndarray, grad_host: Optional[np.ndarray] = None):
+        """End to end through the C ABI with host buffers (copies inside)."""
+        npdt = np.float64 if self.dtype == torch.float64 else np.float32
+        g = np.ascontiguousarray(gamma_host, dtype=npdt)
+        out = np.empty(self.shape, dtype=npdt) if grad_host is None else grad_host
+        J = C.c_double(0.0)
+        _check(self.L.lks_gradient_host(self.h, g.ctypes.data_as(C.c_void_p), C.byref(J),
+                                        out.ctypes.data_as(C.c_void_p)), "lks_gradient_host", self.h)
+        return J.value, out
+
+    # -- state access and single marches ------------------------------------------------
+    def set_state(self, gamma, drho, u, v, T=None, t: int = 0) -> None:
+        fs = [self._field(x) for x in (gamma, drho, u, v)]
+        Tt = self._field(T) if T is not None else fs[1]
+        self._keep = fs + [Tt]
+        _check(self.L.lks_set_state(self.h, *[self._ptr(x) for x in fs], self._ptr(Tt), int(t)),
+               "lks_set_state", self.h)
+
+    def get_state(self):
+        out = [self.empty() for _ in range(4)]
+        _check(self.L.lks_get_state(self.h, *[self._ptr(x) for x in out]), "lks_get_state", self.h)
+        return out  # drho, u, v, T
+
+    def march(self, n: int) -> None:
+        _check(self.L.lks_march(self.h, int(n)), "lks_march", self.h)
+
+    def set_adjoint(self, fields: Sequence[torch.Tensor]) -> None:
+        fs = [self._field(f) for f in fields]
+        while len(fs) < N_ADJ_FIELDS:
+            fs.append(fs[0])
+        self._akeep = fs
+        arr = (C.c_void_p * N_ADJ_FIELDS)(*[f.data_ptr() for f in fs])
+        _check(self.L.alks_set_adjoint(self.h, arr), "alks_set_adjoint", self.h)
+
+    def get_adjoint(self):
+        out = [self.empty() for _ in range(N_ADJ_FIELDS)]
+        arr = (C.c_void_p * N_ADJ_FIELDS)(*[f.data_ptr() for f in out])
+        _check(self.L.alks_get_adjoint(self.h, arr), "alks_get_adjoint", self.h)
+        return out
+
+    def adjoint_march(self, n: int) -> None:
+        _check(self.L.alks_march(self.h, int(n)), "alks_march", self.h)
+
+    def query(self) -> Stats:
+        s = Stats()
+        st = self.L.lks_query(self.h, C.byref(s))
+        if st not in (0, s.device_status):
+            _check(st, "lks_query", self.h)
+        return s

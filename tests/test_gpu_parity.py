@@ -1,0 +1,236 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: the FP64 instance of the kernels agrees with the oracle to rounding
+(<= 1e-10 relative); the FP32 path keeps fields within 1e-5 relative L2 and
+gradients within 1e-3 relative L2 of the oracle.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+from oracle import oracle as O
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU collection
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from paper_2411_03090_gb300 import LKS, LKSError  # noqa: E402
+from paper_2411_03090_gb300.autograd import objective  # noqa: E402
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def small(steady=True, **kw):
+    """70 x 40 nodes: three tiles across x and y with ragged last tiles."""
+    base = dict(seed=1, sigma=2.0, strip=2, n_steps=300, n_adj=300)
+    base.update(kw)
+    if not steady:
+        base.update(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=120.0)
+    return inputs.channel(70, 40, Re=10.0, **base)
+
+
+def oracle_state(st):
+    return [st.rho - 1.0, st.u, st.v]
+
+
+def gpu_state(s):
+    d, u, v, T = [x.double().cpu().numpy() for x in s.get_state()]
+    return [d, u, v], T
+
+
+# ---------------------------------------------------------------------------------------
+# Forward
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("real,tol", [("f64", 1e-12), ("f32", 1e-5)])
+def test_forward_matches_oracle(real, tol):
+    pb = small()
+    g = pb.gamma()
+    s = LKS(pb, real=real)
+    J = s.lks_forward(torch.from_numpy(g)).item()
+    st, _, _, _ = O.forward(pb, g, pb.n_steps)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(st)):
+        assert rel_l2(a, b) <= tol
+    assert abs(J - O.objective(pb, g, st)) <= tol * abs(J)
+
+
+@pytest.mark.parametrize("nu", [0.1, 0.315])
+def test_poiseuille_on_gpu(nu):
+    """Empty channel converges to the exact Poiseuille profile (FP64 instance)."""
+    pb = inputs.poiseuille(70, 33, nu=nu, u_max=0.02).with_(n_steps=30000)
+    s = LKS(pb, real="f64")
+    s.lks_forward(torch.ones(pb.ny, pb.nx, dtype=torch.float64))
+    (d, u, v), _ = gpu_state(s)
+    H = pb.ny - 1
+    y = np.arange(pb.ny)
+    U = 4 * pb.u_max * y * (H - y) / H ** 2
+    assert np.abs(u - U[:, None]).max() <= 1e-9 * pb.u_max
+    assert np.abs(v).max() <= 1e-9 * pb.u_max
+
+
+def test_single_step_full_size_config2():
+    """512 x 256 (the benchmark lattice), FP32, launch configuration of the bench:
+    one step from a developed state equals the oracle's step from the same state."""
+    pb = inputs.config2()
+    g = pb.gamma()
+    s = LKS(pb, real="f32")
+    gt = torch.from_numpy(g)
+    s.set_state(gt, torch.zeros(pb.ny, pb.nx), torch.zeros(pb.ny, pb.nx), torch.zeros(pb.ny, pb.nx), t=0)
+    s.march(400)
+    (d0, u0, v0), _ = gpu_state(s)
+    s.march(1)
+    (d1, u1, v1), _ = gpu_state(s)
+    st = O.State(pb.ny, pb.nx)
+    st.rho, st.u, st.v = d0 + 1.0, u0, v0
+    ref = O.forward_step(pb, g.astype(np.float32).astype(np.float64), 401, st)
+    for a, b, scale in ((d1, ref.rho - 1.0, np.abs(d0).max()), (u1, ref.u, pb.u_max),
+                        (v1, ref.v, pb.u_max)):
+        assert np.abs(a - b).max() <= 2e-6 * scale
+
+
+# ---------------------------------------------------------------------------------------
+# Adjoint and sensitivity
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("real,ftol,gtol", [("f64", 1e-11, 1e-10), ("f32", 1e-5, 1e-3)])
+def test_steady_gradient_matches_oracle(real, ftol, gtol):
+    pb = small()
+    g = pb.gamma()
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.steady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= ftol * abs(ref["J"])
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    for q in range(6):
+        assert rel_l2(adj[q], ref["adjoint"][q]) <= gtol, q
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= gtol
+    assert s.query().device_status == 0
+
+
+@pytest.mark.parametrize("real,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_config1_full(real, tol):
+    """64 x 64, Re = 10 (nu = 0.315, A < 0), 5000 forward + 5000 adjoint steps."""
+    pb = inputs.config1()
+    g = pb.gamma()
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.steady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= (1e-11 if real == "f64" else 1e-5) * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= tol
+
+
+def test_single_adjoint_step_full_size_config2():
+    """512 x 256, FP32: one ALKS step from developed adjoint fields equals the
+    oracle's step from the same fields."""
+    pb = inputs.config2()
+    g = pb.gamma()
+    gf = g.astype(np.float32).astype(np.float64)
+    s = LKS(pb, real="f32")
+    gt = torch.from_numpy(g)
+    z = torch.zeros(pb.ny, pb.nx)
+    s.set_state(gt, z, z, z, t=0)
+    s.march(300)
+    s.set_adjoint([z] * 6)
+    s.adjoint_march(200)
+    a0 = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    s.adjoint_march(1)
+    a1 = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    (d, u, v), _ = gpu_state(s)
+    st = O.State(pb.ny, pb.nx)
+    st.rho, st.u, st.v = d + 1.0, u, v
+    full = np.zeros((9, pb.ny, pb.nx))
+    full[:6] = np.stack(a0)
+    ref = O.adjoint_step(pb, gf, st, st, full)
+    for q in range(6):
+        scale = np.abs(ref[q]).max()
+        assert np.abs(a1[q] - ref[q]).max() <= 1e-5 * scale, q
+
+
+def test_sensitivity_zero_on_edges_and_finite():
+    pb = small()
+    s = LKS(pb, real="f32")
+    _, grad = s.gradient(torch.from_numpy(pb.gamma()))
+    gr = grad.cpu().numpy()
+    assert np.all(np.isfinite(gr))
+    assert np.all(gr[0, :] == 0) and np.all(gr[-1, :] == 0)
+    assert np.all(gr[:, 0] == 0) and np.all(gr[:, -1] == 0)
+
+
+# ---------------------------------------------------------------------------------------
+# Unsteady: plain trajectory and recomputation checkpoints
+# ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("real,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_unsteady_plain_matches_oracle(real, tol):
+    pb = small(steady=False, n_steps=200)
+    g = pb.gamma()
+    s = LKS(pb, real=real, checkpoint_every=0)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= (1e-11 if real == "f64" else 1e-5) * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= tol
+
+
+@pytest.mark.parametrize("K", [1, 37, 64, 200, 500])
+def test_checkpoint_f32_snapshots_equal_plain(K):
+    """Recomputation from FP32 snapshots reproduces the stored trajectory exactly, so
+    the gradient equals the plain form bit for bit (any K, ragged last segment)."""
+    pb = small(steady=False, n_steps=200)
+    g = torch.from_numpy(pb.gamma())
+    J0, g0 = LKS(pb, real="f32", checkpoint_every=0).gradient(g)
+    J1, g1 = LKS(pb, real="f32", checkpoint_every=K, snapshot="f32").gradient(g)
+    assert J0.item() == J1.item()
+    assert torch.equal(g0, g1)
+
+
+@pytest.mark.parametrize("snap", ["bf16", "f16"])
+def test_checkpoint_reduced_snapshots_close(snap):
+    """BF16 / FP16 snapshots with per-field scaling: the gradient stays within 1e-2
+    relative L2 of the plain FP32 form (the error is reported by the benchmark)."""
+    pb = small(steady=False, n_steps=200)
+    g = torch.from_numpy(pb.gamma())
+    _, g0 = LKS(pb, real="f32", checkpoint_every=0).gradient(g)
+    _, g1 = LKS(pb, real="f32", checkpoint_every=50, snapshot=snap).gradient(g)
+    assert rel_l2(g1.double().cpu().numpy(), g0.double().cpu().numpy()) <= 1e-2
+
+
+# ---------------------------------------------------------------------------------------
+# API behaviour
+# ---------------------------------------------------------------------------------------
+def test_gradient_host_matches_device():
+    pb = small()
+    g = pb.gamma()
+    s = LKS(pb, real="f32")
+    J, grad = s.gradient(torch.from_numpy(g))
+    Jh, gh = s.gradient_host(g)
+    assert Jh == J.item()
+    np.testing.assert_array_equal(gh, grad.cpu().numpy())
+
+
+def test_autograd_function():
+    pb = small()
+    s = LKS(pb, real="f64")
+    gam = torch.from_numpy(pb.gamma()).cuda().requires_grad_(True)
+    J = objective(gam, s)
+    (2.0 * J).backward()
+    ref = O.steady_gradient(pb, pb.gamma())
+    assert rel_l2(gam.grad.cpu().numpy(), 2.0 * ref["dJdgamma"]) <= 1e-10
+
+
+def test_call_order_and_unstable_status():
+    pb = small()
+    s = LKS(pb, real="f32")
+    with pytest.raises(LKSError) as e:
+        s.alks_adjoint()
+    assert e.value.status == 7
+    # an inlet above the |u| <= 0.5 bound is reported through the device status word
+    bad = small(n_steps=5).with_(u_max=0.7)
+    sb = LKS(bad, real="f32")
+    sb.lks_forward(torch.from_numpy(bad.gamma()))
+    st = sb.query()
+    assert st.device_status == 4
