@@ -179,9 +179,11 @@ const char *lks_last_error(const lks_handle *h);
 /* Host-only: the edge-class moment maps used by the adjoint kernels, for checks on
  * a CPU.  cls: 0 left face, 1 right pressure face, 2 right wall face, 3 bottom
  * face, 4 top face, 5..8 corners (bottom-left, bottom-right, top-left, top-right).
- * out: 6 x 9 doubles, row r = moment r (rho~, u~_x, u~_y, s~_xx, s~_xy, s~_yy) as a
- * linear function of the nine gathered f~ (unknown entries ignored).  Eq. (ftilde)
- * generalised to every face by the least squares of Sec. 2.5. */
+ * out: 6 x 10 doubles, row r = moment r (rho~, u~_x, u~_y, s~_xx, s~_xy, s~_yy) as a
+ * linear function of the nine gathered f~ (columns 0..8; unknown entries ignored)
+ * and of the heat-flux coupling kappa~ T (column 9).  Eq. (ftilde) generalised to
+ * every face by the least squares of Sec. 2.5 (Eqs. afboundaryu, afboundaryp,
+ * afboundaryuq, afboundarypq). */
 lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
 
 #ifdef __cplusplus

@@ -34,7 +34,7 @@ const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0
 // ------------------------------------------------------------------------------------
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
-  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, tmap = 0;
+  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0;
   size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
@@ -98,8 +98,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.jobj = take(sizeof(double) * L.obj_blocks);
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
-  L.emap = take(L.rsize * 9 * 54);
-  L.tmap = take(L.rsize * 9 * 27);
+  L.emap = take(L.rsize * 9 * 60);
   if (!d->steady) {
     L.sens = take(fb);
     L.sens64 = take(sizeof(double) * L.N);
@@ -165,7 +164,10 @@ void class_geometry(int cls, int* nx, int* ny, int* pressure) {
   *pressure = tab[cls][2];
 }
 
-// Flow: 6 x 9 moment map for edge class cls at parameter A.
+// Flow: 6 x 10 moment map for edge class cls at parameter A: columns 0..8 map the
+// nine gathered f~ (unknown entries ignored); column 9 is the response of the
+// moments to the heat-flux coupling term kappa~ T (c.n) of Eqs. afboundaryuq /
+// afboundarypq, which enters the residual as -kappa~ T (c_i.n).
 void flow_moment_map(double A, int cls, double* out) {
   int n_x, n_y, pres;
   class_geometry(cls, &n_x, &n_y, &pres);
@@ -194,78 +196,28 @@ void flow_moment_map(double A, int cls, double* out) {
       Am[r * nc + nu + 1] = CYh[r];
     }
   }
-  double X[9][9] = {};  // X[u][k]: unknown u from known k
-  for (int k = 0; k < 9; ++k) {
-    if (unk[k]) continue;
+  double X[9][10] = {};  // X[u][k]: unknown u from known k; column 9: from kappa~ T
+  for (int k = 0; k < 10; ++k) {
+    if (k < 9 && unk[k]) continue;
     double rhs[9], x[16];
-    for (int r = 0; r < 9; ++r) rhs[r] = -M[r][k];
+    for (int r = 0; r < 9; ++r) rhs[r] = k < 9 ? -M[r][k] : (double)(CXh[r] * n_x + CYh[r] * n_y);
     lsq_solve(Am.data(), nc, rhs, x);
     for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
   }
   for (int r = 0; r < 6; ++r)
-    for (int k = 0; k < 9; ++k) {
+    for (int k = 0; k < 10; ++k) {
       auto mom = [&](int kk) {
         const double cx = CXh[kk], cy = CYh[kk];
         const double f[6] = {1, cx, cy, cx * cx, cx * cy, cy * cy};
         return Wh[kk] * f[r];
       };
       double s = 0.0;
-      if (!unk[k]) {
-        s = mom(k);
+      if (k == 9 || !unk[k]) {
+        s = k < 9 ? mom(k) : 0.0;
         for (int q = 0; q < nu; ++q) s += mom(U[q]) * X[U[q]][k];
       }
-      out[r * 9 + k] = s;
+      out[r * 10 + k] = s;
     }
-}
-
-// Thermal: 3 x 9 moment map (T~, q~x, q~y) for edge class cls, thermal kind and B.
-void thermal_moment_map(double B, int cls, int flux, double* out) {
-  int n_x, n_y, pres;
-  class_geometry(cls, &n_x, &n_y, &pres);
-  bool unk[9];
-  int U[9], nu = 0;
-  for (int k = 0; k < 9; ++k) {
-    unk[k] = (CXh[k] * n_x > 0) || (CYh[k] * n_y > 0);
-    if (unk[k]) U[nu++] = k;
-  }
-  double M[9][9];
-  for (int r = 0; r < 9; ++r)
-    for (int c = 0; c < 9; ++c) {
-      const int cnc = CXh[c] * n_x + CYh[c] * n_y;
-      M[r][c] = (r == c ? (double)(CXh[r] * n_x + CYh[r] * n_y) : 0.0) - B * Wh[c] * cnc;
-    }
-  const int nc = nu + 1;
-  std::vector<double> Am(9 * nc);
-  for (int r = 0; r < 9; ++r) {
-    for (int q = 0; q < nu; ++q) Am[r * nc + q] = M[r][U[q]];
-    Am[r * nc + nu] = flux ? (double)(CXh[r] * n_x + CYh[r] * n_y) : 1.0;
-  }
-  double X[9][9] = {};
-  for (int k = 0; k < 9; ++k) {
-    if (unk[k]) continue;
-    double rhs[9], x[16];
-    for (int r = 0; r < 9; ++r) rhs[r] = -M[r][k];
-    lsq_solve(Am.data(), nc, rhs, x);
-    for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
-  }
-  for (int r = 0; r < 3; ++r)
-    for (int k = 0; k < 9; ++k) {
-      auto mom = [&](int kk) {
-        const double f[3] = {1.0, (double)CXh[kk], (double)CYh[kk]};
-        return Wh[kk] * f[r];
-      };
-      double s = 0.0;
-      if (!unk[k]) {
-        s = mom(k);
-        for (int q = 0; q < nu; ++q) s += mom(U[q]) * X[U[q]][k];
-      }
-      out[r * 9 + k] = s;
-    }
-}
-
-int class_thermal_edge(int cls) {
-  static const int e[9] = {0, 1, 1, 2, 3, 2, 2, 3, 3};
-  return e[cls];
 }
 
 }  // namespace
@@ -285,8 +237,8 @@ struct lks_handle {
   int t = 0;        // time level of the current state
   int phase = 0;
   int64_t fwd_steps = 0, adj_steps = 0, launches = 0;
-  std::vector<double> emap_h, tmap_h;
-  std::vector<float> emap_f, tmap_f;
+  std::vector<double> emap_h;
+  std::vector<float> emap_f;
   std::string err;
 };
 
@@ -422,7 +374,6 @@ lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, cons
   a.T0 = T0;
   a.gamma = fld<R>(h, h->L.gamma, 0);
   a.emap = reinterpret_cast<const R*>(h->ws + h->L.emap);
-  a.tmap = reinterpret_cast<const R*>(h->ws + h->L.tmap);
   a.sens = sens;
   a.sens_flow = sens_flow;
   a.sens_thermal = sens_thermal;
@@ -730,23 +681,13 @@ template <typename R>
 lks_status upload_maps(lks_handle* h) {
   const auto& d = h->d;
   const double A = (1.0 / 6.0 - d.nu) * 4.5;
-  h->emap_h.assign(9 * 54, 0.0);
-  h->tmap_h.assign(9 * 27, 0.0);
-  for (int cls = 0; cls < 9; ++cls) {
-    flow_moment_map(A, cls, &h->emap_h[cls * 54]);
-    if (d.thermal) {
-      const double B = 3.0 * (1.0 / 6.0 - d.K_f);  // gamma = 1 on edges
-      thermal_moment_map(B, cls, d.t_kind[class_thermal_edge(cls)] == LKS_T_FLUX, &h->tmap_h[cls * 27]);
-    }
-  }
+  h->emap_h.assign(9 * 60, 0.0);
+  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &h->emap_h[cls * 60]);
   if (sizeof(R) == 8) {
-    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_h.data(), 9 * 54 * 8, cudaMemcpyHostToDevice));
-    CKH(h, cudaMemcpy(h->ws + h->L.tmap, h->tmap_h.data(), 9 * 27 * 8, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_h.data(), 9 * 60 * 8, cudaMemcpyHostToDevice));
   } else {
     h->emap_f.assign(h->emap_h.begin(), h->emap_h.end());
-    h->tmap_f.assign(h->tmap_h.begin(), h->tmap_h.end());
-    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_f.data(), 9 * 54 * 4, cudaMemcpyHostToDevice));
-    CKH(h, cudaMemcpy(h->ws + h->L.tmap, h->tmap_f.data(), 9 * 27 * 4, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_f.data(), 9 * 60 * 4, cudaMemcpyHostToDevice));
   }
   return LKS_OK;
 }
@@ -954,7 +895,10 @@ lks_status lks_query(lks_handle* h, lks_stats* out) {
 
 lks_status lks_edge_moment_map(double A, int32_t cls, double* out) {
   if (!out || cls < 0 || cls > 8) return LKS_ERR_INVALID_ARG;
-  flow_moment_map(A, cls, out);
+  double full[60];
+  flow_moment_map(A, cls, full);
+  for (int r = 0; r < 6; ++r)
+    for (int k = 0; k < 10; ++k) out[r * 10 + k] = full[r * 10 + k];
   return LKS_OK;
 }
 

@@ -396,6 +396,73 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
   }
 }
 
+// Thermal adjoint edge rule at one node (App. A, Eqs. agboundaryT / agboundaryq):
+// residual r_i = (n.c_i) g~_i - B sum_j w_j (n.c_j) g~_j + m_i with the multiplier
+// column m = 1 (prescribed T) or m = c.n - u.n (prescribed flux); the g~_i whose
+// gather point is off the lattice and the multiplier minimise ||r||_2 over the nine
+// rows (normal equations in double; unknown links with c.n = 0 do not enter the
+// residual and are set to zero).  g[] holds the known values (zeros elsewhere) on
+// entry and all nine on exit; returns the multiplier.
+__device__ __forceinline__ double thermal_edge_solve(int n_x, int n_y, double B, bool flux, double un,
+                                                     double* g) {
+  constexpr int cx_[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
+  constexpr int cy_[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
+  constexpr double w_[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
+  int live[5];
+  int nl = 0;
+  double sknown = 0.0;  // sum_j w_j (n.c_j) g_j over known j
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const int cn = cx_[k] * n_x + cy_[k] * n_y;
+    const bool unk = (cx_[k] * n_x > 0) || (cy_[k] * n_y > 0);
+    if (unk) {
+      g[k] = 0.0;
+      if (cn != 0 && nl < 4) live[nl++] = k;
+    } else {
+      sknown += w_[k] * cn * g[k];
+    }
+  }
+  const int nc = nl + 1;
+  double G[5][6];
+  for (int a = 0; a < nc; ++a)
+    for (int b = 0; b <= nc; ++b) G[a][b] = 0.0;
+#pragma unroll
+  for (int r = 0; r < 9; ++r) {
+    const int cnr = cx_[r] * n_x + cy_[r] * n_y;
+    const bool unk_r = (cx_[r] * n_x > 0) || (cy_[r] * n_y > 0);
+    double col[5];
+    for (int a = 0; a < nl; ++a) {
+      const int u = live[a];
+      const int cnu = cx_[u] * n_x + cy_[u] * n_y;
+      col[a] = (r == u ? (double)cnu : 0.0) - B * w_[u] * cnu;
+    }
+    col[nl] = flux ? ((double)cnr - un) : 1.0;
+    const double rhs = -((unk_r ? 0.0 : cnr * g[r]) - B * sknown);
+    for (int a = 0; a < nc; ++a) {
+      for (int b = 0; b < nc; ++b) G[a][b] += col[a] * col[b];
+      G[a][nc] += col[a] * rhs;
+    }
+  }
+  for (int cc = 0; cc < nc; ++cc) {
+    int p = cc;
+    for (int r = cc + 1; r < nc; ++r)
+      if (fabs(G[r][cc]) > fabs(G[p][cc])) p = r;
+    if (p != cc)
+      for (int q = 0; q <= nc; ++q) {
+        const double t = G[cc][q];
+        G[cc][q] = G[p][q];
+        G[p][q] = t;
+      }
+    for (int r = 0; r < nc; ++r) {
+      if (r == cc) continue;
+      const double f = G[r][cc] / G[cc][cc];
+      for (int q = cc; q <= nc; ++q) G[r][q] -= f * G[cc][q];
+    }
+  }
+  for (int a = 0; a < nl; ++a) g[live[a]] = G[a][nc] / G[a][a];
+  return G[nl][nc] / G[nl][nl];
+}
+
 // =====================================================================================
 // ALKS step
 // =====================================================================================
@@ -409,8 +476,8 @@ struct AdjArgs {
   const R* v0;
   const R* T0;
   const R* gamma;
-  const R* emap;    // 9 classes x 6 x 9 edge moment maps (flow)
-  const R* tmap;    // 9 classes x 3 x 9 edge moment maps (thermal, T-fixed or flux at u.n = 0)
+  const R* emap;    // 9 classes x 6 x 10 edge moment maps (flow); column 9 is the
+                    // moments' response to the heat-flux coupling kappa~ T
   R* sens;          // optional: sensitivity accumulator (interior nodes)
   int sens_flow;    // add the flow and objective terms of level t
   int sens_thermal; // add the thermal term of level t
@@ -583,23 +650,40 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
         ft[k] = in ? cP[qg] + R(cx) * cVx[qg] + R(cy) * cVy[qg] : R(0);
         if (TH) gt[k] = in ? cG[qg] : R(0);
       }
-      const R* M = a.emap + ec * 54;
+      R kT = R(0);
+      if (TH) {
+        // Thermal edge rule solved per node (its multiplier column depends on u.n).
+        int nxo, nyo;
+        node_class(g, i, j, nxo, nyo);
+        const int e = thermal_edge(g, i, j);
+        const bool flux = g.t_kind[e] != 0;
+        const double un = (double)(su0[s2] * R(nxo) + sv0[s2] * R(nyo));
+        double gd[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
+        const double kap = thermal_edge_solve(nxo, nyo, (double)B_of(c, __ldg(a.gamma + (size_t)j * nx + i)),
+                                              flux, un, gd);
+        R T_, qx_, qy_;
+        T_ = qx_ = qy_ = R(0);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const R gk = (R)gd[k] * wk<R>(k);
+          T_ += gk;
+          qx_ += R(cxk(k)) * gk;
+          qy_ += R(cyk(k)) * gk;
+        }
+        m[6] = T_;
+        m[7] = qx_;
+        m[8] = qy_;
+        if (flux) kT = (R)kap * sT0[s2];
+      }
+      const R* M = a.emap + ec * 60;
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
         R s = R(0);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) s += M[r * 9 + k] * ft[k];
-        m[r] = s;
-      }
-      if (TH) {
-        const R* Mt = a.tmap + ec * 27;
-#pragma unroll
-        for (int r = 0; r < 3; ++r) {
-          R s = R(0);
-#pragma unroll
-          for (int k = 0; k < 9; ++k) s += Mt[r * 9 + k] * gt[k];
-          m[6 + r] = s;
-        }
+        for (int k = 0; k < 9; ++k) s += M[r * 10 + k] * ft[k];
+        m[r] = s + M[r * 10 + 9] * kT;
       }
     }
     const size_t o = (size_t)j * nx + i;

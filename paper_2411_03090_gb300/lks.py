@@ -150,11 +150,12 @@ def _check(status: int, what: str, handle=None) -> None:
 
 
 def edge_moment_map(A: float, cls: int) -> np.ndarray:
-    """Host-only: the 6 x 9 adjoint edge moment map of class ``cls``."""
-    out = np.zeros(54)
+    """Host-only: the 6 x 10 adjoint edge moment map of class ``cls`` (column 9: the
+    response to the heat-flux coupling kappa~ T)."""
+    out = np.zeros(60)
     _check(load().lks_edge_moment_map(float(A), int(cls),
                                       out.ctypes.data_as(C.POINTER(C.c_double))), "edge map")
-    return out.reshape(6, 9)
+    return out.reshape(6, 10)
 
 
 class LKS:
