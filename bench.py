@@ -42,9 +42,10 @@ def workload(name: str):
         return inputs.config2(), "config2: 512x256 steady channel, Re=100, 20000+20000 steps, FP32"
     if name == "config1":
         return inputs.config1(), "config1: 64x64 steady channel, Re=10, 5000+5000 steps, FP32"
-    if name == "roofline8192":
-        pb = inputs.roofline2d(8192)
-        return pb, "roofline8192: 8192x8192 steady channel, 200+200 steps, FP32"
+    if name.startswith("roofline"):
+        n = int(name[len("roofline"):])
+        pb = inputs.roofline2d(n)
+        return pb, f"{name}: {n}x{n} steady channel, {pb.n_steps}+{pb.n_adj} steps, FP32"
     raise SystemExit(f"unknown workload {name}")
 
 
@@ -167,6 +168,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -253,17 +255,19 @@ def main():
                             "mean_launch_us": fwd_launch_s * 1e6}}
 
     # End to end through the C ABI with host buffers (pinned), copies inside.
-    g_host = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
-    grad_host = torch.empty(pb.ny, pb.nx, dtype=torch.float32).pin_memory().numpy()
-    s.gradient_host(g_host, grad_host)
-    e2e_t = []
-    for _ in range(max(2, min(args.steps, 3))):
-        flush.fill_(1.0)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
+    e2e_val = None
+    if not args.no_e2e:
+        g_host = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
+        grad_host = torch.empty(pb.ny, pb.nx, dtype=torch.float32).pin_memory().numpy()
         s.gradient_host(g_host, grad_host)
-        e2e_t.append(time.perf_counter() - t0)
-    e2e_val = world * updates_per_step / (sum(e2e_t) / len(e2e_t)) / 1e6
+        e2e_t = []
+        for _ in range(max(2, min(args.steps, 3))):
+            flush.fill_(1.0)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            s.gradient_host(g_host, grad_host)
+            e2e_t.append(time.perf_counter() - t0)
+        e2e_val = world * updates_per_step / (sum(e2e_t) / len(e2e_t)) / 1e6
 
     if rank != 0:
         if world > 1:

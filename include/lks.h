@@ -176,6 +176,29 @@ lks_status lks_destroy(lks_handle *h);
 const char *lks_status_string(lks_status s);
 const char *lks_last_error(const lks_handle *h);
 
+/* Steps 2-5 without any device allocation, for callers that cannot call cudaMalloc
+ * and cannot hand the library a workspace: a plugin whose host application owns all
+ * device memory through a fixed pool, or a latency-critical loop in which the
+ * implicit synchronisation of cudaMalloc / cudaFree is not allowed.  The paper has
+ * no counterpart; this is a packaging variant of lks_forward + alks_adjoint +
+ * lks_sensitivity (same kernels, same results).
+ *
+ * The workspace comes from one static device array of LKS_NOALLOC_SCRATCH_BYTES
+ * (8 MiB) inside the library; every GPU that loads the library holds it until the
+ * process exits.  A problem whose lks_workspace_size exceeds it is rejected with
+ * LKS_ERR_WORKSPACE before any GPU work (about 100 000 nodes fit for a steady FP32
+ * problem, e.g. 256 x 256).  gamma_dev, J_dev (one double) and dJdgamma_dev
+ * (nx*ny, real_type) are the caller's device buffers; stream orders the work.
+ * The first call on a device looks up the array's device address (once per
+ * device, with that device current); make that first call before any stream
+ * capture.  Every call shares the array and leaves its contents behind (each
+ * call clears what it needs zeroed), so calls that overlap on the GPU -- on
+ * different streams, or from different host threads -- race and corrupt each
+ * other: order them.  Host memory for a temporary handle is still allocated. */
+#define LKS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
+lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_dev, double *J_dev,
+                                void *dJdgamma_dev, void *stream);
+
 /* Host-only: the edge-class moment maps used by the adjoint kernels, for checks on
  * a CPU.  cls: 0 left face, 1 right pressure face, 2 right wall face, 3 bottom
  * face, 4 top face, 5..8 corners (bottom-left, bottom-right, top-left, top-right).

@@ -11,6 +11,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -891,6 +892,85 @@ lks_status lks_query(lks_handle* h, lks_stats* out) {
   out->device_status = status;
   out->phase = h->phase;
   return status ? (lks_status)status : LKS_OK;
+}
+
+// ------------------------------------------------------------------------------------
+// Allocation-free gradient (lks_gradient_noalloc): workspace in a static device array
+// ------------------------------------------------------------------------------------
+}  // extern "C"
+
+namespace {
+// Scratch of the allocation-free entry point; in host code this name is only a
+// stand-in, the device address comes from cudaGetSymbolAddress.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[LKS_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_noalloc_mu;
+void* g_noalloc_ptr[kMaxDevices] = {};
+
+// Device address of the static scratch on the current device (looked up once per
+// device, with that device current).
+lks_status noalloc_scratch(void** out, int* dev_out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return LKS_ERR_CUDA;
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return LKS_ERR_CUDA;
+    g_noalloc_ptr[dev] = p;
+  }
+  *out = g_noalloc_ptr[dev];
+  *dev_out = dev;
+  return LKS_OK;
+}
+
+// The edge maps, copied in stream order (pageable source: staged at the call).
+template <typename R>
+lks_status upload_maps_async(lks_handle* h) {
+  const double A = (1.0 / 6.0 - h->d.nu) * 4.5;
+  h->emap_h.assign(9 * 60, 0.0);
+  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &h->emap_h[cls * 60]);
+  if (sizeof(R) == 8) {
+    CKH(h, cudaMemcpyAsync(h->ws + h->L.emap, h->emap_h.data(), 9 * 60 * 8, cudaMemcpyHostToDevice, h->stream));
+  } else {
+    h->emap_f.assign(h->emap_h.begin(), h->emap_h.end());
+    CKH(h, cudaMemcpyAsync(h->ws + h->L.emap, h->emap_f.data(), 9 * 60 * 4, cudaMemcpyHostToDevice, h->stream));
+  }
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status noalloc_run(lks_handle* h, const void* gamma_dev, double* J_dev, void* grad_dev) {
+  lks_status s = set_smem_attrs<R>();
+  if (s == LKS_OK) s = upload_maps_async<R>(h);
+  if (s == LKS_OK) s = forward_impl<R>(h, gamma_dev, J_dev);
+  if (s == LKS_OK) s = adjoint_impl<R>(h);
+  if (s == LKS_OK) s = sensitivity_impl<R>(h, grad_dev);
+  return s;
+}
+}  // namespace
+
+extern "C" {
+
+lks_status lks_gradient_noalloc(const lks_problem_desc* desc, const void* gamma_dev, double* J_dev,
+                                void* dJdgamma_dev, void* stream) {
+  if (!gamma_dev || !J_dev || !dJdgamma_dev) return LKS_ERR_INVALID_ARG;
+  lks_status s = check_desc(desc, nullptr);
+  if (s != LKS_OK) return s;
+  const Layout L = make_layout(desc);
+  if (L.total > LKS_NOALLOC_SCRATCH_BYTES) return LKS_ERR_WORKSPACE;  // problem too large
+  void* ws = nullptr;
+  int dev = 0;
+  if ((s = noalloc_scratch(&ws, &dev)) != LKS_OK) return s;
+  lks_handle h;
+  h.d = *desc;
+  h.L = L;
+  h.ws = reinterpret_cast<unsigned char*>(ws);
+  h.ws_bytes = LKS_NOALLOC_SCRATCH_BYTES;
+  h.stream = reinterpret_cast<cudaStream_t>(stream);
+  h.device = dev;
+  return desc->real_type == LKS_REAL_F64 ? noalloc_run<double>(&h, gamma_dev, J_dev, dJdgamma_dev)
+                                         : noalloc_run<float>(&h, gamma_dev, J_dev, dJdgamma_dev);
 }
 
 lks_status lks_edge_moment_map(double A, int32_t cls, double* out) {

@@ -63,7 +63,7 @@ class Stats(C.Structure):
 EXPORTS = ("lks_workspace_size", "lks_create", "lks_forward", "alks_adjoint", "lks_sensitivity",
            "lks_gradient_host", "lks_set_state", "lks_get_state", "lks_march", "alks_set_adjoint",
            "alks_get_adjoint", "alks_march", "lks_query", "lks_destroy", "lks_status_string",
-           "lks_last_error", "lks_edge_moment_map")
+           "lks_last_error", "lks_edge_moment_map", "lks_gradient_noalloc")
 
 _lib = None
 
@@ -103,6 +103,7 @@ def load(build_if_missing: bool = True):
     L.lks_last_error.argtypes = [hp]
     L.lks_last_error.restype = C.c_char_p
     L.lks_edge_moment_map.argtypes = [C.c_double, i32, dp]
+    L.lks_gradient_noalloc.argtypes = [C.POINTER(Desc), vp, vp, vp, vp]
     for name in EXPORTS:
         if name not in ("lks_status_string", "lks_last_error"):
             getattr(L, name).restype = C.c_int
