@@ -56,6 +56,11 @@ typedef enum { LKS_REAL_F32 = 0, LKS_REAL_F64 = 1 } lks_real_type;
 /* Storage type of checkpoint snapshots (unsteady problems). */
 typedef enum { LKS_SNAP_F32 = 0, LKS_SNAP_BF16 = 1, LKS_SNAP_F16 = 2 } lks_snap_type;
 
+/* How the steady marches run: one kernel launch per time step over 32x16 tiles,
+ * or one cooperative launch per march in which every tile stays resident in the
+ * shared memory of its CTA (lattices whose tiles fit the GPU at once). */
+typedef enum { LKS_PATH_AUTO = 0, LKS_PATH_STEP = 1, LKS_PATH_RESIDENT = 2 } lks_exec_path;
+
 /* Thermal edge conditions (Sec. 2.4): prescribed temperature T = T_bar, or
  * prescribed heat flux -q.n = q_bar_w. */
 typedef enum { LKS_T_FIXED = 0, LKS_T_FLUX = 1 } lks_thermal_kind;
@@ -90,7 +95,10 @@ typedef struct {
     int32_t checkpoint_every; /* unsteady: K > 0 recompute segments of K steps from
                                  snapshots; 0 keeps every level (plain form)         */
     int32_t snapshot_type;    /* lks_snap_type of the checkpoint snapshots           */
-    int32_t reserved[8];      /* must be zero                                        */
+    int32_t exec_path;        /* lks_exec_path: 0 automatic, 1 one kernel launch per
+                                 step, 2 resident persistent march (steady problems
+                                 whose tiles fit on the GPU at once)                 */
+    int32_t reserved[7];      /* must be zero                                        */
 } lks_problem_desc;
 
 /* Counters and the device status word, filled by lks_query. */

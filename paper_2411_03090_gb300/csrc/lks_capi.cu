@@ -18,6 +18,7 @@
 
 #include "../../include/lks.h"
 #include "lks_kernels.cuh"
+#include "lks_resident.cuh"
 
 using namespace lks;
 
@@ -35,7 +36,7 @@ const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0
 // ------------------------------------------------------------------------------------
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
-  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0;
+  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0;
   size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
@@ -68,7 +69,8 @@ lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   }
   if (d->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
-  for (int q = 0; q < 8; ++q)
+  if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_RESIDENT) return bad("bad exec_path");
+  for (int q = 0; q < 7; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }
@@ -100,6 +102,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
   L.emap = take(L.rsize * 9 * 60);
+  L.flags = take(sizeof(int) * (size_t)((d->nx + 31) / 32) * (size_t)((d->ny + 7) / 8));
   if (!d->steady) {
     L.sens = take(fb);
     L.sens64 = take(sizeof(double) * L.N);
@@ -393,6 +396,128 @@ lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, cons
   return LKS_OK;
 }
 
+// ------------------------------------------------------------------------------------
+// Resident (persistent, cooperative) marches
+// ------------------------------------------------------------------------------------
+struct ResPlan {
+  int TXR = 0, TYR = 0, ntiles = 0;
+};
+
+int device_sms(lks_handle* h) {
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  return sms;
+}
+
+// Tile shape of a resident march: the most tiles that still leave one CTA per SM;
+// if even the largest tile needs more CTAs than SMs, none (the per-step path runs).
+ResPlan plan_resident(lks_handle* h) {
+  static const int cfg[3][2] = {{64, 16}, {32, 16}, {32, 8}};
+  ResPlan best;
+  const int sms = device_sms(h);
+  for (auto& c : cfg) {
+    const int nt = ((h->d.nx + c[0] - 1) / c[0]) * ((h->d.ny + c[1] - 1) / c[1]);
+    if (nt <= sms && nt > best.ntiles) {
+      best.TXR = c[0];
+      best.TYR = c[1];
+      best.ntiles = nt;
+    }
+  }
+  return best;
+}
+
+bool resident_wanted(lks_handle* h) {
+  if (h->d.exec_path == LKS_PATH_STEP || !h->d.steady) return false;
+  int coop = 0;
+  cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
+  return coop && plan_resident(h).ntiles > 0;
+}
+
+template <typename R, bool TH, int TXR, int TYR>
+lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
+  constexpr int NT = 256;
+  const auto& d = h->d;
+  const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
+  const size_t smem = (size_t)fwd_res_smem_elems<TH, TXR, TYR>() * sizeof(R);
+  auto kern = fwd_resident_kernel<R, TH, TXR, TYR, NT>;
+  CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CKH(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1 || nt > per_sm * device_sms(h)) return fail(h, LKS_ERR_INVALID_ARG, "resident march does not fit");
+  ResArgs<R> a{};
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < h->L.nF; ++f) a.buf[b][f] = state_ptr<R>(h, b, f);
+  a.cur = h->cur;
+  a.gamma = fld<R>(h, h->L.gamma, 0);
+  a.flags = reinterpret_cast<int*>(h->ws + h->L.flags);
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.n_steps = n;
+  a.t0 = h->t;
+  a.u_in = (R)inlet_amp(d, h->t + 1);
+  a.ntx = ntx;
+  Geom g = make_geom(d);
+  Coef<R> c = make_coef<R>(d);
+  CKH(h, cudaMemsetAsync(a.flags, 0, sizeof(int) * nt, h->stream));
+  void* args[] = {&a, &g, &c};
+  CKH(h, cudaLaunchCooperativeKernel((const void*)kern, dim3(nt), dim3(NT), args, smem, h->stream));
+  h->cur = (h->cur + n) & 1;
+  h->t += n;
+  h->fwd_steps += n;
+  h->launches++;
+  return LKS_OK;
+}
+
+template <typename R, int TXR, int TYR>
+lks_status launch_adj_resident_cfg(lks_handle* h, int n) {
+  constexpr int NT = 256;
+  const auto& d = h->d;
+  const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
+  const size_t smem = (size_t)adj_res_smem_elems<TXR, TYR>() * sizeof(R);
+  auto kern = adj_resident_kernel<R, TXR, TYR, NT>;
+  CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  CKH(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
+  if (per_sm < 1 || nt > per_sm * device_sms(h)) return fail(h, LKS_ERR_INVALID_ARG, "resident march does not fit");
+  ResArgs<R> a{};
+  for (int b = 0; b < 2; ++b)
+    for (int f = 0; f < 6; ++f) a.buf[b][f] = adj_ptr<R>(h, b, f);
+  a.cur = h->acur;
+  a.u = state_ptr<R>(h, h->cur, 1);
+  a.v = state_ptr<R>(h, h->cur, 2);
+  a.gamma = fld<R>(h, h->L.gamma, 0);
+  a.emap = reinterpret_cast<const R*>(h->ws + h->L.emap);
+  a.flags = reinterpret_cast<int*>(h->ws + h->L.flags);
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.n_steps = n;
+  a.ntx = ntx;
+  Geom g = make_geom(d);
+  Coef<R> c = make_coef<R>(d);
+  CKH(h, cudaMemsetAsync(a.flags, 0, sizeof(int) * nt, h->stream));
+  void* args[] = {&a, &g, &c};
+  CKH(h, cudaLaunchCooperativeKernel((const void*)kern, dim3(nt), dim3(NT), args, smem, h->stream));
+  h->acur = (h->acur + n) & 1;
+  h->adj_steps += n;
+  h->launches++;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status launch_fwd_resident(lks_handle* h, int n) {
+  const ResPlan p = plan_resident(h);
+  const bool th = h->d.thermal != 0;
+  if (p.TXR == 64) return th ? launch_fwd_resident_cfg<R, true, 64, 16>(h, n) : launch_fwd_resident_cfg<R, false, 64, 16>(h, n);
+  if (p.TYR == 16) return th ? launch_fwd_resident_cfg<R, true, 32, 16>(h, n) : launch_fwd_resident_cfg<R, false, 32, 16>(h, n);
+  return th ? launch_fwd_resident_cfg<R, true, 32, 8>(h, n) : launch_fwd_resident_cfg<R, false, 32, 8>(h, n);
+}
+
+template <typename R>
+lks_status launch_adj_resident(lks_handle* h, int n) {
+  const ResPlan p = plan_resident(h);
+  if (p.TXR == 64) return launch_adj_resident_cfg<R, 64, 16>(h, n);
+  if (p.TYR == 16) return launch_adj_resident_cfg<R, 32, 16>(h, n);
+  return launch_adj_resident_cfg<R, 32, 8>(h, n);
+}
+
 template <typename R>
 lks_status launch_objective(lks_handle* h, const R* u, const R* v, const R* T, double* partial) {
   const auto& d = h->d;
@@ -526,9 +651,13 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   double* jval = reinterpret_cast<double*>(h->ws + L.jval);
   lks_status st;
   if (d.steady) {
-    for (int s = 1; s <= d.n_steps; ++s)
-      if ((st = launch_fwd<R>(h, s, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
-    CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
+    if (resident_wanted(h)) {
+      if ((st = launch_fwd_resident<R>(h, d.n_steps)) != LKS_OK) return st;
+    } else {
+      if (d.exec_path == LKS_PATH_RESIDENT) return fail(h, LKS_ERR_INVALID_ARG, "resident march unavailable");
+      for (int s = 1; s <= d.n_steps; ++s)
+        if ((st = launch_fwd<R>(h, s, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
+    }
   } else {
     CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
     const bool plain = d.checkpoint_every == 0;
@@ -585,8 +714,12 @@ lks_status adjoint_impl(lks_handle* h) {
     const R* u = state_ptr<R>(h, h->cur, 1);
     const R* v = state_ptr<R>(h, h->cur, 2);
     const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
-    for (int it = 0; it < d.n_adj; ++it)
-      if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+    if (!d.thermal && resident_wanted(h)) {
+      if ((st = launch_adj_resident<R>(h, d.n_adj)) != LKS_OK) return st;
+    } else {
+      for (int it = 0; it < d.n_adj; ++it)
+        if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+    }
     h->phase = 2;
     return LKS_OK;
   }

@@ -195,10 +195,13 @@ constexpr int fwd_smem_elems() {
 
 // One LKS step (Eqs. rho, u, T; f^eq Eq. feq2, g^eq Eq. geq2; implicit Brinkman of
 // Eq. lbef_ex; edge rules of Sec. 2.4).  Each node's f_k^eq is written as
-//   f_k^eq = w_k (a0 + c_x bx + c_y by + c_x^2 qxx + c_y^2 qyy + c_x c_y qxy)
-// with a0 = drho - 3/2 |u|^2, bx = 3u, by = 3v, qxx = 9/2 u^2 + A S_xx,
-// qyy = 9/2 v^2 + A S_yy, qxy = 9 u v + 2 A S_xy; g_k^eq = w_k (t0 + c.tq) with
-// t0 = T, tq = 3 T u + B grad T.
+//   f_k^eq = w_k (drho + e0 + c_x bx + c_y by + c_x^2 qxx + c_y^2 qyy + c_x c_y qxy)
+// with e0 = -3/2 |u|^2, bx = 3u, by = 3v, qxx = 9/2 u^2 + A S_xx,
+// qyy = 9/2 v^2 + A S_yy, qxy = 9 u v + 2 A S_xy; g_k^eq = w_k (T + c.tq) with
+// tq = 3 T u + B grad T.  The new density is accumulated as an increment on the
+// node's own value, drho(x) + sum_k w_k [(drho(x - c_k) - drho(x)) + ...] (the
+// weights of the sum add to one, also in the edge rule), which keeps FP32 rounding
+// of a large pressure level out of the O(u) terms; T likewise.
 template <typename R, bool TH>
 __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g, Coef<R> c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -264,7 +267,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
       dvdy = -dudx;
     }
     const R Sxx = R(2) * dudx, Syy = R(2) * dvdy, Sxy = dudy + dvdx;
-    ca0[q] = sr[q] - R(1.5) * (uu * uu + vv * vv);
+    ca0[q] = -R(1.5) * (uu * uu + vv * vv);
     cbx[q] = R(3) * uu;
     cby[q] = R(3) * vv;
     cqx[q] = R(4.5) * uu * uu + c.A * Sxx;
@@ -305,32 +308,37 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
     int nxo, nyo;
     const int cls = node_class(g, i, j, nxo, nyo);
     R drn, un, vn, Tn = R(0);
+    const R drx = sr[q];
     if (cls == C_INTERIOR) {
       const int W = q - 1, E = q + 1, S = q - H1X, N = q + H1X;
-      const R f0 = ca0[q] * (R(4) / R(9));
-      const R f1 = (ca0[W] + cbx[W] + cqx[W]) * (R(1) / R(9));
-      const R f3 = (ca0[E] - cbx[E] + cqx[E]) * (R(1) / R(9));
-      const R f2 = (ca0[S] + cby[S] + cqy[S]) * (R(1) / R(9));
-      const R f4 = (ca0[N] - cby[N] + cqy[N]) * (R(1) / R(9));
       const int SW = S - 1, SE = S + 1, NE = N + 1, NW = N - 1;
-      const R d5 = ca0[SW] + cqx[SW] + cqy[SW], d6 = ca0[SE] + cqx[SE] + cqy[SE];
-      const R d7 = ca0[NE] + cqx[NE] + cqy[NE], d8 = ca0[NW] + cqx[NW] + cqy[NW];
+      // populations without the node's own density (increment form)
+      const R f0 = ca0[q] * (R(4) / R(9));
+      const R f1 = ((sr[W] - drx) + ca0[W] + cbx[W] + cqx[W]) * (R(1) / R(9));
+      const R f3 = ((sr[E] - drx) + ca0[E] - cbx[E] + cqx[E]) * (R(1) / R(9));
+      const R f2 = ((sr[S] - drx) + ca0[S] + cby[S] + cqy[S]) * (R(1) / R(9));
+      const R f4 = ((sr[N] - drx) + ca0[N] - cby[N] + cqy[N]) * (R(1) / R(9));
+      const R d5 = (sr[SW] - drx) + ca0[SW] + cqx[SW] + cqy[SW];
+      const R d6 = (sr[SE] - drx) + ca0[SE] + cqx[SE] + cqy[SE];
+      const R d7 = (sr[NE] - drx) + ca0[NE] + cqx[NE] + cqy[NE];
+      const R d8 = (sr[NW] - drx) + ca0[NW] + cqx[NW] + cqy[NW];
       const R f5 = (d5 + cbx[SW] + cby[SW] + cqxy[SW]) * (R(1) / R(36));
       const R f6 = (d6 - cbx[SE] + cby[SE] - cqxy[SE]) * (R(1) / R(36));
       const R f7 = (d7 - cbx[NE] - cby[NE] + cqxy[NE]) * (R(1) / R(36));
       const R f8 = (d8 + cbx[NW] - cby[NW] - cqxy[NW]) * (R(1) / R(36));
-      drn = f0 + f1 + f2 + f3 + f4 + f5 + f6 + f7 + f8;
+      drn = drx + (f0 + f1 + f2 + f3 + f4 + f5 + f6 + f7 + f8);
       const R us = f1 - f3 + f5 - f6 - f7 + f8;
       const R vs = f2 - f4 + f5 + f6 - f7 - f8;
       const R inv = R(1) / (R(1) + alpha_of(c, __ldg(a.gamma + (size_t)j * nx + i)));
       un = us * inv;
       vn = vs * inv;
       if (TH) {
-        R Ts = ct0[q] * (R(4) / R(9));
-        Ts += (ct0[W] + ctx[W] + ct0[E] - ctx[E] + ct0[S] + cty[S] + ct0[N] - cty[N]) * (R(1) / R(9));
-        Ts += (ct0[SW] + ctx[SW] + cty[SW] + ct0[SE] - ctx[SE] + cty[SE] + ct0[NE] - ctx[NE] -
-               cty[NE] + ct0[NW] + ctx[NW] - cty[NW]) * (R(1) / R(36));
-        Tn = Ts;
+        const R Tx = ct0[q];
+        R Ts = ((ct0[W] - Tx) + ctx[W] + (ct0[E] - Tx) - ctx[E] + (ct0[S] - Tx) + cty[S] +
+                (ct0[N] - Tx) - cty[N]) * (R(1) / R(9));
+        Ts += ((ct0[SW] - Tx) + ctx[SW] + cty[SW] + (ct0[SE] - Tx) - ctx[SE] + cty[SE] +
+               (ct0[NE] - Tx) - ctx[NE] - cty[NE] + (ct0[NW] - Tx) + ctx[NW] - cty[NW]) * (R(1) / R(36));
+        Tn = Tx + Ts;
       }
     } else {
       // Edge node: the nine streamed populations, split by c.n.
@@ -341,13 +349,14 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
         const int si = i - cx, sj = j - cy;
         if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
         const int qs = q - cx - cy * H1X;
-        const R fk = wk<R>(k) * (ca0[qs] + R(cx) * cbx[qs] + R(cy) * cby[qs] + R(cx * cx) * cqx[qs] +
-                                 R(cy * cy) * cqy[qs] + R(cx * cy) * cqxy[qs]);
+        // increments on the node's own drho and T (the edge weights add to one)
+        const R fk = wk<R>(k) * ((sr[qs] - drx) + ca0[qs] + R(cx) * cbx[qs] + R(cy) * cby[qs] +
+                                 R(cx * cx) * cqx[qs] + R(cy * cy) * cqy[qs] + R(cx * cy) * cqxy[qs]);
         const int cn = cx * nxo + cy * nyo;
         if (cn == 0) s0 += fk;
         else if (cn > 0) sp += fk;
         if (TH) {
-          const R gk = wk<R>(k) * (ct0[qs] + R(cx) * ctx[qs] + R(cy) * cty[qs]);
+          const R gk = wk<R>(k) * ((ct0[qs] - ct0[q]) + R(cx) * ctx[qs] + R(cy) * cty[qs]);
           if (cn == 0) g0 += gk;
           else if (cn > 0) gp += gk;
         }
@@ -363,10 +372,10 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
           un = a.u_in * (R)(4.0 * y * (H - y) / (H * H));
         }
         vn = R(0);
-        drn = s0 + R(2) * sp - (un * R(nxo) + vn * R(nyo));
+        drn = drx + (s0 + R(2) * sp - (un * R(nxo) + vn * R(nyo)));
       } else {
         drn = c.drho_out;
-        const R unorm = s0 + R(2) * sp - c.drho_out;
+        const R unorm = (s0 + R(2) * sp) + (drx - c.drho_out);
         un = unorm * R(nxo);
         vn = unorm * R(nyo);
       }
@@ -378,7 +387,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
           const int jn = (j == 0) ? 1 : ny - 2;
           Tn = sT[(jn - y0 + 2) * H2X + (tx + 2)];
         } else {
-          Tn = (g0 + R(2) * gp + c.t_val[e]) / (R(1) + un * R(nxo) + vn * R(nyo));
+          Tn = (ct0[q] + g0 + R(2) * gp + c.t_val[e]) / (R(1) + un * R(nxo) + vn * R(nyo));
         }
       }
     }

@@ -23,6 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "u
           5: "not converged", 6: "timeout", 7: "calls out of order"}
 REAL = {"f32": 0, "f64": 1}
 SNAP = {"f32": 0, "bf16": 1, "f16": 2}
+PATH = {"auto": 0, "step": 1, "resident": 2}
 N_ADJ_FIELDS = 9
 ADJ_NAMES = ("rho_t", "ux_t", "uy_t", "sxx_t", "sxy_t", "syy_t", "T_t", "qx_t", "qy_t")
 
@@ -49,7 +50,7 @@ class Desc(C.Structure):
         ("kappa_T", C.c_double),
         ("n_steps", C.c_int32), ("n_adj", C.c_int32),
         ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
-        ("reserved", C.c_int32 * 8),
+        ("exec_path", C.c_int32), ("reserved", C.c_int32 * 7),
     ]
 
 
@@ -111,7 +112,8 @@ def load(build_if_missing: bool = True):
     return L
 
 
-def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32") -> Desc:
+def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
+              path: str = "auto") -> Desc:
     """Descriptor from an ``inputs.Problem``-like object."""
     d = Desc()
     d.version = LKS_DESC_VERSION
@@ -132,6 +134,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.n_adj = int(pb.n_adj)
     d.checkpoint_every = int(checkpoint_every)
     d.snapshot_type = SNAP[snapshot]
+    d.exec_path = PATH[path]
     return d
 
 
@@ -164,12 +167,13 @@ class LKS:
     library handle.  Fields are (ny, nx) tensors of the descriptor's real type."""
 
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
-                 device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None):
+                 device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
+                 path: str = "auto"):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.pb = pb
-        self.desc = make_desc(pb, real, checkpoint_every, snapshot)
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.shape = (int(pb.ny), int(pb.nx))

@@ -48,11 +48,12 @@ def gpu_state(s):
 # ---------------------------------------------------------------------------------------
 # Forward
 # ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("path", ["step", "resident"])
 @pytest.mark.parametrize("real,tol", [("f64", 1e-12), ("f32", 1e-5)])
-def test_forward_matches_oracle(real, tol):
+def test_forward_matches_oracle(real, tol, path):
     pb = small()
     g = pb.gamma()
-    s = LKS(pb, real=real)
+    s = LKS(pb, real=real, path=path)
     J = s.lks_forward(torch.from_numpy(g)).item()
     st, _, _, _ = O.forward(pb, g, pb.n_steps)
     got, _ = gpu_state(s)
@@ -98,11 +99,12 @@ def test_single_step_full_size_config2():
 # ---------------------------------------------------------------------------------------
 # Adjoint and sensitivity
 # ---------------------------------------------------------------------------------------
+@pytest.mark.parametrize("path", ["step", "resident"])
 @pytest.mark.parametrize("real,ftol,gtol", [("f64", 1e-11, 1e-10), ("f32", 1e-5, 1e-3)])
-def test_steady_gradient_matches_oracle(real, ftol, gtol):
+def test_steady_gradient_matches_oracle(real, ftol, gtol, path):
     pb = small()
     g = pb.gamma()
-    s = LKS(pb, real=real)
+    s = LKS(pb, real=real, path=path)
     J, grad = s.gradient(torch.from_numpy(g))
     ref = O.steady_gradient(pb, g)
     assert abs(J.item() - ref["J"]) <= ftol * abs(ref["J"])
@@ -156,6 +158,18 @@ def test_single_adjoint_step_full_size_config2():
     for q in range(6):
         scale = np.abs(ref[q]).max()
         assert np.abs(a1[q] - ref[q]).max() <= 1e-5 * scale, q
+
+
+def test_resident_equals_step_path_config2():
+    """512 x 256 (the benchmark lattice), FP32: the resident persistent marches and
+    the one-launch-per-step kernels give the same gradient (same arithmetic; only
+    the compiler's operation fusion may differ)."""
+    pb = inputs.config2().with_(n_steps=2000, n_adj=2000)
+    g = torch.from_numpy(pb.gamma())
+    Ja, ga = LKS(pb, real="f32", path="resident").gradient(g)
+    Jb, gb = LKS(pb, real="f32", path="step").gradient(g)
+    assert abs(Ja.item() - Jb.item()) <= 1e-6 * abs(Jb.item())
+    assert rel_l2(ga.cpu().numpy(), gb.cpu().numpy()) <= 1e-5
 
 
 def test_sensitivity_zero_on_edges_and_finite():
