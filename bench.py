@@ -247,12 +247,17 @@ def main():
     adj_gbs = BYTES_ADJ_STEADY * N / adj_launch_s / 1e9
     fwd_gbs = BYTES_FWD * N / fwd_launch_s / 1e9
     traffic = None
-    roofline = {"bound": "hbm", "kernel": "adj_step_kernel<float,false>", "achieved": adj_gbs, "peak": hbm,
+    st = s.query()
+    kname = {1: ("adj_step_kernel<float,false>", "fwd_step_kernel<float,false>"),
+             2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>")}
+    adj_k = kname.get(st.adj_path, kname[1])[0]
+    fwd_k = kname.get(st.fwd_path, kname[1])[1]
+    roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
                 "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_node": BYTES_ADJ_STEADY, "mean_launch_us": adj_launch_s * 1e6,
-                "forward": {"kernel": "fwd_step_kernel<float,false>", "achieved": fwd_gbs,
+                "algorithmic_bytes_per_node": BYTES_ADJ_STEADY, "mean_step_us": adj_launch_s * 1e6,
+                "forward": {"kernel": fwd_k, "achieved": fwd_gbs,
                             "frac": fwd_gbs / hbm, "algorithmic_bytes_per_node": BYTES_FWD,
-                            "mean_launch_us": fwd_launch_s * 1e6}}
+                            "mean_step_us": fwd_launch_s * 1e6}}
 
     # End to end through the C ABI with host buffers (pinned), copies inside.
     e2e_val = None

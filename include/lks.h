@@ -109,6 +109,8 @@ typedef struct {
     size_t workspace_bytes;   /* workspace in use                                    */
     int32_t device_status;    /* lks_status recorded on the device (0 = none)        */
     int32_t phase;            /* 0 created, 1 forward done, 2 adjoint done           */
+    int32_t fwd_path;         /* lks_exec_path the last forward march ran on         */
+    int32_t adj_path;         /* lks_exec_path the last adjoint march ran on         */
 } lks_stats;
 
 typedef struct lks_handle lks_handle;

@@ -240,6 +240,7 @@ struct lks_handle {
   int acur = 0;     // which adjoint buffer holds the current adjoint
   int t = 0;        // time level of the current state
   int phase = 0;
+  int fwd_path = 0, adj_path = 0;
   int64_t fwd_steps = 0, adj_steps = 0, launches = 0;
   std::vector<double> emap_h;
   std::vector<float> emap_f;
@@ -356,6 +357,7 @@ lks_status launch_fwd(lks_handle* h, int t_new, double* Jpartial, R* tu, R* tv, 
   h->t = t_new;
   h->fwd_steps++;
   h->launches++;
+  h->fwd_path = LKS_PATH_STEP;
   return LKS_OK;
 }
 
@@ -393,6 +395,7 @@ lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, cons
   h->acur = dst;
   h->adj_steps++;
   h->launches++;
+  h->adj_path = LKS_PATH_STEP;
   return LKS_OK;
 }
 
@@ -400,8 +403,11 @@ lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, cons
 // Resident (persistent, cooperative) marches
 // ------------------------------------------------------------------------------------
 struct ResPlan {
-  int TXR = 0, TYR = 0, ntiles = 0;
+  int cfg = -1, ntiles = 0;
 };
+
+// Tile shapes of the resident marches: {TXR, TYR, threads}.
+constexpr int kResCfg[3][3] = {{64, 16, 512}, {32, 16, 256}, {32, 8, 256}};
 
 int device_sms(lks_handle* h) {
   int sms = 0;
@@ -409,33 +415,43 @@ int device_sms(lks_handle* h) {
   return sms;
 }
 
-// Tile shape of a resident march: the most tiles that still leave one CTA per SM;
-// if even the largest tile needs more CTAs than SMs, none (the per-step path runs).
-ResPlan plan_resident(lks_handle* h) {
-  static const int cfg[3][2] = {{64, 16}, {32, 16}, {32, 8}};
+size_t res_smem_bytes(const lks_problem_desc& d, bool adjoint, int cfg) {
+  const size_t rs = d.real_type == LKS_REAL_F64 ? 8 : 4;
+  const int tx = kResCfg[cfg][0], ty = kResCfg[cfg][1];
+  const size_t a2 = (size_t)(tx + 4) * (ty + 4), a1 = (size_t)(tx + 2) * (ty + 2), no = (size_t)tx * ty;
+  if (adjoint) return rs * (8 * a2 + 9 * a1 + 3 * no);
+  return rs * ((d.thermal ? 4 : 3) * a2 + (d.thermal ? 19 : 9) * a1 + no);
+}
+
+// Tile shape of a resident march: the most tiles that still leave one CTA per SM
+// and fit the shared memory of an SM; none if the lattice needs more CTAs than SMs
+// (the one-launch-per-step path runs then).
+ResPlan plan_resident(lks_handle* h, bool adjoint) {
   ResPlan best;
   const int sms = device_sms(h);
-  for (auto& c : cfg) {
-    const int nt = ((h->d.nx + c[0] - 1) / c[0]) * ((h->d.ny + c[1] - 1) / c[1]);
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  for (int k = 0; k < 3; ++k) {
+    const int nt = ((h->d.nx + kResCfg[k][0] - 1) / kResCfg[k][0]) * ((h->d.ny + kResCfg[k][1] - 1) / kResCfg[k][1]);
+    if (res_smem_bytes(h->d, adjoint, k) + 1024 > (size_t)optin) continue;
     if (nt <= sms && nt > best.ntiles) {
-      best.TXR = c[0];
-      best.TYR = c[1];
+      best.cfg = k;
       best.ntiles = nt;
     }
   }
   return best;
 }
 
-bool resident_wanted(lks_handle* h) {
+bool resident_wanted(lks_handle* h, bool adjoint) {
   if (h->d.exec_path == LKS_PATH_STEP || !h->d.steady) return false;
+  if (adjoint && h->d.thermal) return false;
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
-  return coop && plan_resident(h).ntiles > 0;
+  return coop && plan_resident(h, adjoint).ntiles > 0;
 }
 
-template <typename R, bool TH, int TXR, int TYR>
+template <typename R, bool TH, int TXR, int TYR, int NT>
 lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
-  constexpr int NT = 256;
   const auto& d = h->d;
   const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
   const size_t smem = (size_t)fwd_res_smem_elems<TH, TXR, TYR>() * sizeof(R);
@@ -464,12 +480,12 @@ lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
   h->t += n;
   h->fwd_steps += n;
   h->launches++;
+  h->fwd_path = LKS_PATH_RESIDENT;
   return LKS_OK;
 }
 
-template <typename R, int TXR, int TYR>
+template <typename R, int TXR, int TYR, int NT>
 lks_status launch_adj_resident_cfg(lks_handle* h, int n) {
-  constexpr int NT = 256;
   const auto& d = h->d;
   const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
   const size_t smem = (size_t)adj_res_smem_elems<TXR, TYR>() * sizeof(R);
@@ -498,24 +514,25 @@ lks_status launch_adj_resident_cfg(lks_handle* h, int n) {
   h->acur = (h->acur + n) & 1;
   h->adj_steps += n;
   h->launches++;
+  h->adj_path = LKS_PATH_RESIDENT;
   return LKS_OK;
 }
 
 template <typename R>
 lks_status launch_fwd_resident(lks_handle* h, int n) {
-  const ResPlan p = plan_resident(h);
+  const int k = plan_resident(h, false).cfg;
   const bool th = h->d.thermal != 0;
-  if (p.TXR == 64) return th ? launch_fwd_resident_cfg<R, true, 64, 16>(h, n) : launch_fwd_resident_cfg<R, false, 64, 16>(h, n);
-  if (p.TYR == 16) return th ? launch_fwd_resident_cfg<R, true, 32, 16>(h, n) : launch_fwd_resident_cfg<R, false, 32, 16>(h, n);
-  return th ? launch_fwd_resident_cfg<R, true, 32, 8>(h, n) : launch_fwd_resident_cfg<R, false, 32, 8>(h, n);
+  if (k == 0) return th ? launch_fwd_resident_cfg<R, true, 64, 16, 512>(h, n) : launch_fwd_resident_cfg<R, false, 64, 16, 512>(h, n);
+  if (k == 1) return th ? launch_fwd_resident_cfg<R, true, 32, 16, 256>(h, n) : launch_fwd_resident_cfg<R, false, 32, 16, 256>(h, n);
+  return th ? launch_fwd_resident_cfg<R, true, 32, 8, 256>(h, n) : launch_fwd_resident_cfg<R, false, 32, 8, 256>(h, n);
 }
 
 template <typename R>
 lks_status launch_adj_resident(lks_handle* h, int n) {
-  const ResPlan p = plan_resident(h);
-  if (p.TXR == 64) return launch_adj_resident_cfg<R, 64, 16>(h, n);
-  if (p.TYR == 16) return launch_adj_resident_cfg<R, 32, 16>(h, n);
-  return launch_adj_resident_cfg<R, 32, 8>(h, n);
+  const int k = plan_resident(h, true).cfg;
+  if (k == 0) return launch_adj_resident_cfg<R, 64, 16, 512>(h, n);
+  if (k == 1) return launch_adj_resident_cfg<R, 32, 16, 256>(h, n);
+  return launch_adj_resident_cfg<R, 32, 8, 256>(h, n);
 }
 
 template <typename R>
@@ -651,7 +668,7 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   double* jval = reinterpret_cast<double*>(h->ws + L.jval);
   lks_status st;
   if (d.steady) {
-    if (resident_wanted(h)) {
+    if (resident_wanted(h, false)) {
       if ((st = launch_fwd_resident<R>(h, d.n_steps)) != LKS_OK) return st;
     } else {
       if (d.exec_path == LKS_PATH_RESIDENT) return fail(h, LKS_ERR_INVALID_ARG, "resident march unavailable");
@@ -714,7 +731,7 @@ lks_status adjoint_impl(lks_handle* h) {
     const R* u = state_ptr<R>(h, h->cur, 1);
     const R* v = state_ptr<R>(h, h->cur, 2);
     const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
-    if (!d.thermal && resident_wanted(h)) {
+    if (resident_wanted(h, true)) {
       if ((st = launch_adj_resident<R>(h, d.n_adj)) != LKS_OK) return st;
     } else {
       for (int it = 0; it < d.n_adj; ++it)
@@ -1024,6 +1041,8 @@ lks_status lks_query(lks_handle* h, lks_stats* out) {
   out->workspace_bytes = h->L.total;
   out->device_status = status;
   out->phase = h->phase;
+  out->fwd_path = h->fwd_path;
+  out->adj_path = h->adj_path;
   return status ? (lks_status)status : LKS_OK;
 }
 

@@ -57,7 +57,8 @@ class Desc(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("forward_steps", C.c_int64), ("adjoint_steps", C.c_int64),
                 ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_size_t),
-                ("device_status", C.c_int32), ("phase", C.c_int32)]
+                ("device_status", C.c_int32), ("phase", C.c_int32),
+                ("fwd_path", C.c_int32), ("adj_path", C.c_int32)]
 
 
 # Every symbol the header declares (checked by the CPU test-suite).
