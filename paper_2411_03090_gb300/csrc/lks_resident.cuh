@@ -8,6 +8,8 @@
 // flag (release) and, for the next step, first computes everything that needs no
 // halo (the tile interior), then waits for its eight neighbours' flags (acquire,
 // bounded spin), reloads only the two-node halo ring and finishes the tile band.
+// Only the band (the two outer rows and columns the neighbours read) goes to global
+// memory each step; the interior stays in shared memory until the last step.
 // No kernel launch and no grid-wide barrier per step.
 //
 // Streaming is done in push form: each node first evaluates the nine values it
@@ -163,6 +165,23 @@ __device__ __forceinline__ bool coef_inner(int lx, int ly) {
 template <int TXR, int TYR>
 __device__ __forceinline__ bool out_inner(int ox, int oy) {
   return ox >= 2 && ox <= TXR - 3 && oy >= 2 && oy <= TYR - 3;
+}
+
+// Positions of the halo-1 region outside the inner block, enumerated directly:
+// rows 0, 1, TYR, TYR+1 at full width, then columns 0, 1, TXR, TXR+1 of rows
+// 2 .. TYR-1.  Count 4 (TXR+2) + 4 (TYR-2).
+template <int TXR, int TYR>
+__device__ __forceinline__ void band_coef_pos(int t, int& lx, int& ly) {
+  constexpr int LX1 = TXR + 2, LY1 = TYR + 2;
+  if (t < 4 * LX1) {
+    const int r = t / LX1;
+    lx = t - r * LX1;
+    ly = r < 2 ? r : LY1 - 4 + r;
+  } else {
+    const int u = t - 4 * LX1, r = u / 4, cidx = u - r * 4;
+    ly = 2 + r;
+    lx = cidx < 2 ? cidx : LX1 - 4 + cidx;
+  }
 }
 
 template <bool TH, int TXR, int TYR>
@@ -393,9 +412,10 @@ __global__ void __launch_bounds__(NT, 1) fwd_resident_kernel(ResArgs<R> a, Geom 
       __syncthreads();
     }
     // (3) outer push values and the tile band
-    for (int q = threadIdx.x; q < A1; q += NT) {
-      const int ly = q / LX1, lx = q - ly * LX1;
-      if (!coef_inner<TXR, TYR>(lx, ly)) coef(lx, ly);
+    for (int t = threadIdx.x; t < 4 * (LX1 + TYR - 2); t += NT) {
+      int lx, ly;
+      band_coef_pos<TXR, TYR>(t, lx, ly);
+      coef(lx, ly);
     }
     __syncthreads();
 #pragma unroll
@@ -408,37 +428,39 @@ __global__ void __launch_bounds__(NT, 1) fwd_resident_kernel(ResArgs<R> a, Geom 
       }
     }
     __syncthreads();  // every read of this level is done
-    // (4) write the new level (shared + global) and publish it
+    // (4) the band (what the neighbours read) to shared and global memory, publish;
+    // then the interior to shared memory (to global memory after the last step)
     const int nb = (a.cur + s + 1) & 1;
-    auto put = [&](int ox, int oy, const R* o) {
+    const bool last = s == a.n_steps - 1;
+    auto put = [&](int ox, int oy, const R* o, bool global) {
       const int i = x0 + ox, j = y0 + oy;
       if (i >= nx || j >= ny) return;
       const int s2 = (oy + 2) * LX2 + (ox + 2);
       const size_t off = (size_t)j * nx + i;
       for (int f = 0; f < nf; ++f) {
         sf[f][s2] = o[f];
-        __stcg(a.buf[nb][f] + off, o[f]);
+        if (global) __stcg(a.buf[nb][f] + off, o[f]);
       }
     };
-#pragma unroll
-    for (int p = 0; p < PI; ++p) {
-      const int t = threadIdx.x + p * NT;
-      if (t < NOI) {
-        int ox, oy;
-        inner_pos(t, ox, oy);
-        put(ox, oy, oi[p]);
-      }
-    }
 #pragma unroll
     for (int p = 0; p < PO; ++p) {
       const int t = threadIdx.x + p * NT;
       if (t < NOO) {
         int ox, oy;
         outer_pos(t, ox, oy);
-        put(ox, oy, oo[p]);
+        put(ox, oy, oo[p], true);
       }
     }
     res_publish(a.flags, tile, s + 1);
+#pragma unroll
+    for (int p = 0; p < PI; ++p) {
+      const int t = threadIdx.x + p * NT;
+      if (t < NOI) {
+        int ox, oy;
+        inner_pos(t, ox, oy);
+        put(ox, oy, oi[p], last);
+      }
+    }
     __syncthreads();
   }
 }
@@ -619,9 +641,10 @@ __global__ void __launch_bounds__(NT, 1) adj_resident_kernel(ResArgs<R> a, Geom 
       res_load_ring<R, TXR, TYR, NT, 6>(sa, a.buf[pb], 6, x0, y0, nx, ny);
       __syncthreads();
     }
-    for (int q = threadIdx.x; q < A1; q += NT) {
-      const int ly = q / LX1, lx = q - ly * LX1;
-      if (!coef_inner<TXR, TYR>(lx, ly)) coef(lx, ly);
+    for (int t = threadIdx.x; t < 4 * (LX1 + TYR - 2); t += NT) {
+      int lx, ly;
+      band_coef_pos<TXR, TYR>(t, lx, ly);
+      coef(lx, ly);
     }
     __syncthreads();
 #pragma unroll
@@ -635,7 +658,8 @@ __global__ void __launch_bounds__(NT, 1) adj_resident_kernel(ResArgs<R> a, Geom 
     }
     __syncthreads();
     const int nb = (a.cur + s + 1) & 1;
-    auto put = [&](int ox, int oy, const R* o) {
+    const bool last = s == a.n_steps - 1;
+    auto put = [&](int ox, int oy, const R* o, bool global) {
       const int i = x0 + ox, j = y0 + oy;
       if (i >= nx || j >= ny) return;
       const int s2 = (oy + 2) * LX2 + (ox + 2);
@@ -643,28 +667,28 @@ __global__ void __launch_bounds__(NT, 1) adj_resident_kernel(ResArgs<R> a, Geom 
 #pragma unroll
       for (int f = 0; f < 6; ++f) {
         sa[f][s2] = o[f];
-        __stcg(a.buf[nb][f] + off, o[f]);
+        if (global) __stcg(a.buf[nb][f] + off, o[f]);
       }
     };
-#pragma unroll
-    for (int p = 0; p < PI; ++p) {
-      const int t = threadIdx.x + p * NT;
-      if (t < NOI) {
-        int ox, oy;
-        inner_pos(t, ox, oy);
-        put(ox, oy, oi[p]);
-      }
-    }
 #pragma unroll
     for (int p = 0; p < PO; ++p) {
       const int t = threadIdx.x + p * NT;
       if (t < NOO) {
         int ox, oy;
         outer_pos(t, ox, oy);
-        put(ox, oy, oo[p]);
+        put(ox, oy, oo[p], true);
       }
     }
     res_publish(a.flags, tile, s + 1);
+#pragma unroll
+    for (int p = 0; p < PI; ++p) {
+      const int t = threadIdx.x + p * NT;
+      if (t < NOI) {
+        int ox, oy;
+        inner_pos(t, ox, oy);
+        put(ox, oy, oi[p], last);
+      }
+    }
     __syncthreads();
   }
 }
