@@ -14,11 +14,13 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/lks.h"
 #include "lks_kernels.cuh"
 #include "lks_resident.cuh"
+#include "lks_tma.cuh"
 
 using namespace lks;
 
@@ -244,6 +246,8 @@ struct lks_handle {
   int64_t fwd_steps = 0, adj_steps = 0, launches = 0;
   std::vector<double> emap_h;
   std::vector<float> emap_f;
+  std::unordered_map<uint64_t, CUtensorMap> tmaps;  // (pointer, box) -> tensor map
+  int tma_grid_fwd = 0, tma_grid_adj = 0;
   std::string err;
 };
 
@@ -325,9 +329,21 @@ lks_status set_smem_attrs() {
 }
 
 // One forward step: state `cur` -> other buffer, new level t_new.
+template <bool TH>
+lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT);
+bool tma_ok(lks_handle* h);
+template <bool TH, bool SAME>
+lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
+                          const float* T0, float* sens, int sens_flow, int sens_thermal);
+
 template <typename R>
 lks_status launch_fwd(lks_handle* h, int t_new, double* Jpartial, R* tu, R* tv, R* tT) {
   const auto& d = h->d;
+  if constexpr (sizeof(R) == 4) {
+    if (tma_ok(h))
+      return d.thermal ? launch_fwd_tma<true>(h, t_new, Jpartial, tu, tv, tT)
+                       : launch_fwd_tma<false>(h, t_new, Jpartial, tu, tv, tT);
+  }
   FwdArgs<R> a;
   const int src = h->cur, dst = 1 - h->cur;
   a.drho = state_ptr<R>(h, src, 0);
@@ -366,6 +382,16 @@ template <typename R>
 lks_status launch_adj(lks_handle* h, const R* u1, const R* v1, const R* u0, const R* v0, const R* T0,
                       R* sens, int sens_flow, int sens_thermal) {
   const auto& d = h->d;
+  if constexpr (sizeof(R) == 4) {
+    if (tma_ok(h)) {
+      const bool same = (u0 == u1 && v0 == v1);
+      if (d.thermal)
+        return same ? launch_adj_tma<true, true>(h, u1, v1, u0, v0, T0, sens, sens_flow, sens_thermal)
+                    : launch_adj_tma<true, false>(h, u1, v1, u0, v0, T0, sens, sens_flow, sens_thermal);
+      return same ? launch_adj_tma<false, true>(h, u1, v1, u0, v0, T0, sens, sens_flow, sens_thermal)
+                  : launch_adj_tma<false, false>(h, u1, v1, u0, v0, T0, sens, sens_flow, sens_thermal);
+    }
+  }
   AdjArgs<R> a;
   const int src = h->acur, dst = 1 - h->acur;
   for (int f = 0; f < 9; ++f) {
@@ -533,6 +559,144 @@ lks_status launch_adj_resident(lks_handle* h, int n) {
   if (k == 0) return launch_adj_resident_cfg<R, 64, 16, 512>(h, n);
   if (k == 1) return launch_adj_resident_cfg<R, 32, 16, 256>(h, n);
   return launch_adj_resident_cfg<R, 32, 8, 256>(h, n);
+}
+
+// ------------------------------------------------------------------------------------
+// TMA-staged per-step kernels (FP32, nx % 4 == 0)
+// ------------------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = []() -> EncodeTiledFn {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return nullptr;
+    return reinterpret_cast<EncodeTiledFn>(p);
+  }();
+  return fn;
+}
+
+constexpr int kFwdTX = 64, kFwdTY = 16, kAdjTX = 64, kAdjTY = 8;
+
+bool tma_ok(lks_handle* h) {
+  return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
+}
+
+// Tensor map of one field (nx x ny floats) for boxes of bw x bh, cached per handle.
+lks_status field_map(lks_handle* h, const void* ptr, int bw, int bh, CUtensorMap* out) {
+  const uint64_t key = reinterpret_cast<uint64_t>(ptr) ^ ((uint64_t)bw << 48) ^ ((uint64_t)bh << 56);
+  auto it = h->tmaps.find(key);
+  if (it != h->tmaps.end()) {
+    *out = it->second;
+    return LKS_OK;
+  }
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)h->d.nx, (cuuint64_t)h->d.ny};
+  const cuuint64_t strides[1] = {(cuuint64_t)h->d.nx * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)bw, (cuuint32_t)bh};
+  const cuuint32_t es[2] = {1, 1};
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(ptr), dims, strides, box, es,
+                                 CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(h, LKS_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  h->tmaps.emplace(key, m);
+  *out = m;
+  return LKS_OK;
+}
+
+template <typename K>
+int persistent_grid(lks_handle* h, K kern, size_t smem, int ntiles) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem) != cudaSuccess || per_sm < 1)
+    per_sm = 1;
+  return std::max(1, std::min(ntiles, per_sm * device_sms(h)));
+}
+
+template <bool TH>
+lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
+  constexpr int NF = fwd_tma_nf<TH>();
+  constexpr int BW = kFwdTX + 8, BH = kFwdTY + 4;
+  const auto& d = h->d;
+  const int src = h->cur, dst = 1 - h->cur;
+  TmaMaps<NF> maps;
+  lks_status st;
+  for (int f = 0; f < (TH ? 4 : 3); ++f)
+    if ((st = field_map(h, state_ptr<float>(h, src, f), BW, BH, &maps.m[f])) != LKS_OK) return st;
+  if (TH && (st = field_map(h, fld<float>(h, h->L.gamma, 0), BW, BH, &maps.m[NF - 1])) != LKS_OK) return st;
+  FwdTmaArgs<TH> a;
+  a.drho_n = state_ptr<float>(h, dst, 0);
+  a.u_n = state_ptr<float>(h, dst, 1);
+  a.v_n = state_ptr<float>(h, dst, 2);
+  a.T_n = TH ? state_ptr<float>(h, dst, 3) : nullptr;
+  a.gamma = fld<float>(h, h->L.gamma, 0);
+  a.u_in = (float)inlet_amp(d, t_new);
+  a.J_partial = Jpartial;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.traj_u = tu;
+  a.traj_v = tv;
+  a.traj_T = tT;
+  a.ntx = (d.nx + kFwdTX - 1) / kFwdTX;
+  a.ntiles = a.ntx * ((d.ny + kFwdTY - 1) / kFwdTY);
+  const size_t smem = fwd_tma_smem_bytes<TH, kFwdTX, kFwdTY>();
+  auto kern = fwd_tma_kernel<TH, kFwdTX, kFwdTY, NTHREADS>;
+  if (!h->tma_grid_fwd) {
+    CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    h->tma_grid_fwd = persistent_grid(h, kern, smem, a.ntiles);
+  }
+  kern<<<h->tma_grid_fwd, NTHREADS, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  CKH(h, cudaGetLastError());
+  h->cur = dst;
+  h->t = t_new;
+  h->fwd_steps++;
+  h->launches++;
+  h->fwd_path = LKS_PATH_STEP;
+  return LKS_OK;
+}
+
+template <bool TH, bool SAME>
+lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
+                          const float* T0, float* sens, int sens_flow, int sens_thermal) {
+  constexpr int NF = adj_tma_nf<TH, SAME>();
+  constexpr int NA = TH ? 9 : 6;
+  constexpr int BW = kAdjTX + 8, BH = kAdjTY + 4;
+  const auto& d = h->d;
+  const int src = h->acur, dst = 1 - h->acur;
+  TmaMaps<NF> maps;
+  lks_status st;
+  int f = 0;
+  for (int q = 0; q < NA; ++q)
+    if ((st = field_map(h, adj_ptr<float>(h, src, q), BW, BH, &maps.m[f++])) != LKS_OK) return st;
+  const float* extra[6] = {u1, v1, u0, v0, T0, fld<float>(h, h->L.gamma, 0)};
+  for (int q = 0; q < 6; ++q) {
+    if (SAME && (q == 2 || q == 3)) continue;
+    if (!TH && q >= 4) continue;
+    if ((st = field_map(h, extra[q], BW, BH, &maps.m[f++])) != LKS_OK) return st;
+  }
+  AdjTmaArgs<TH> a;
+  for (int q = 0; q < 9; ++q) a.m0[q] = adj_ptr<float>(h, dst, q < NA ? q : 0);
+  a.gamma = fld<float>(h, h->L.gamma, 0);
+  a.emap = reinterpret_cast<const float*>(h->ws + h->L.emap);
+  a.sens = sens;
+  a.sens_flow = sens_flow;
+  a.sens_thermal = sens_thermal;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.ntx = (d.nx + kAdjTX - 1) / kAdjTX;
+  a.ntiles = a.ntx * ((d.ny + kAdjTY - 1) / kAdjTY);
+  const size_t smem = adj_tma_smem_bytes<TH, SAME, kAdjTX, kAdjTY>();
+  auto kern = adj_tma_kernel<TH, SAME, kAdjTX, kAdjTY, NTHREADS>;
+  CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  const int grid = persistent_grid(h, kern, smem, a.ntiles);
+  kern<<<grid, NTHREADS, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  CKH(h, cudaGetLastError());
+  h->acur = dst;
+  h->adj_steps++;
+  h->launches++;
+  h->adj_path = LKS_PATH_STEP;
+  return LKS_OK;
 }
 
 template <typename R>

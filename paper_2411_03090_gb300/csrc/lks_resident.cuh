@@ -210,6 +210,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_resident_kernel(ResArgs<R> a, Geom 
   R* sinv = cB + (TH ? A1 : 0);      // 1 / (1 + alpha) on the tile
   __shared__ int s_abort;
 
+  if (a.status && *reinterpret_cast<const volatile int*>(a.status) == 6) return;  // earlier timeout
   const int nx = g.nx, ny = g.ny;
   const int tile = blockIdx.x, tx = tile % a.ntx, ty = tile / a.ntx;
   const int nty = gridDim.x / a.ntx;
@@ -492,6 +493,7 @@ __global__ void __launch_bounds__(NT, 1) adj_resident_kernel(ResArgs<R> a, Geom 
   R* sinv = sjv + NO;
   __shared__ int s_abort;
 
+  if (a.status && *reinterpret_cast<const volatile int*>(a.status) == 6) return;  // earlier timeout
   const int nx = g.nx, ny = g.ny;
   const int tile = blockIdx.x, tx = tile % a.ntx, ty = tile / a.ntx;
   const int nty = gridDim.x / a.ntx;

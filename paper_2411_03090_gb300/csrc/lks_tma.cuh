@@ -1,0 +1,551 @@
+// lks_tma.cuh -- TMA-staged, software-pipelined forms of the one-launch-per-step LKS
+// and ALKS kernels (FP32) for lattices too large to stay resident.
+//
+// Each CTA is persistent over a static list of tiles.  Thread 0 issues 2-D tensor
+// copies (cp.async.bulk.tensor) of every field the step reads, for the tile's box
+// with a two-node halo, into one of two shared-memory stages; an mbarrier with a
+// transaction count signals arrival.  While the CTA computes tile k from one stage,
+// the copies of tile k+1 fill the other.  Out-of-lattice parts of a box arrive as
+// zeros (tensor-map fill), so no thread computes a load address.
+//
+// TMA alignment: the box starts at x0 - 4 (a multiple of four floats, 16 bytes) and
+// is TX + 8 floats wide; rows are nx floats apart, so the lattice needs nx % 4 == 0
+// (the host falls back to the plain kernels otherwise).  Waits on an mbarrier are
+// bounded; on timeout the kernel records LKS_ERR_TIMEOUT, waits (bounded) for its
+// own copies and returns.
+//
+// The arithmetic per node is that of fwd_step_kernel / adj_step_kernel, in push
+// form (each halo-1 node first writes the nine values it streams; an output node
+// sums nine shared-memory values).
+#pragma once
+#include <cuda.h>
+
+#include "lks_kernels.cuh"
+
+namespace lks {
+
+constexpr int TMA_BXPAD = 4;  // left pad of a box (floats), keeps x aligned to 16 B
+
+template <int NF>
+struct TmaMaps {
+  CUtensorMap m[NF];
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// A launch that follows a timed-out wait returns at once (status word already 6).
+__device__ __forceinline__ bool timed_out_before(const int* status) {
+  return status && *reinterpret_cast<const volatile int*>(status) == 6;
+}
+
+// Bounded wait for an mbarrier phase.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+  for (long long it = 0; it < (1ll << 20); ++it) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (it > 16) __nanosleep(20);
+  }
+  return false;
+}
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+__device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// ---------------------------------------------------------------------------------
+// Forward
+// ---------------------------------------------------------------------------------
+template <bool TH>
+struct FwdTmaArgs {
+  float* drho_n;
+  float* u_n;
+  float* v_n;
+  float* T_n;
+  const float* gamma;
+  float u_in;
+  double* J_partial;   // per-CTA accumulator of J_O(old state), or null
+  int* status;
+  float* traj_u;
+  float* traj_v;
+  float* traj_T;
+  int ntx, ntiles;
+};
+
+// fields staged per stage: drho, u, v (, T, gamma)
+template <bool TH>
+__host__ __device__ constexpr int fwd_tma_nf() {
+  return TH ? 5 : 3;
+}
+template <bool TH, int TX_, int TY_>
+constexpr int fwd_tma_smem_bytes() {
+  return 2 * fwd_tma_nf<TH>() * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 64;
+}
+
+template <bool TH, int TX_, int TY_, int NT>
+__global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ TmaMaps<fwd_tma_nf<TH>()> maps,
+                                                     FwdTmaArgs<TH> a, Geom g, Coef<float> c) {
+  constexpr int NF = fwd_tma_nf<TH>();
+  constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
+  constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage = reinterpret_cast<float*>(smem_raw);           // [2][NF][BOX]
+  float* F = stage + 2 * NF * BOX;                              // [9][A1]
+  float* Gp = F + 9 * A1;                                       // thermal [9][A1]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(Gp + (TH ? 9 * A1 : 0));
+  static_assert(NT == NTHREADS, "block_sum assumes NTHREADS threads");
+  __shared__ double red[NTHREADS / 32];
+
+  if (timed_out_before(a.status)) return;
+  const int nx = g.nx, ny = g.ny;
+  auto issue = [&](int tile, int st) {
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    mbar_expect_tx(&bar[st], NF * BOX * 4);
+    for (int f = 0; f < NF; ++f)
+      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], tx * TX_ - TMA_BXPAD, ty * TY_ - 2, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    if ((int)blockIdx.x < a.ntiles) issue(blockIdx.x, 0);
+  }
+  __syncthreads();
+
+  double jloc = 0.0;
+  int it = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < a.ntiles) issue(tile + gridDim.x, st ^ 1);
+    if (!mbar_wait(&bar[st], (it >> 1) & 1)) {
+      raise_status(a.status, 6);
+      if (threadIdx.x == 0) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+      return;
+    }
+    const float* sdr = stage + (st * NF + 0) * BOX;
+    const float* su = stage + (st * NF + 1) * BOX;
+    const float* sv = stage + (st * NF + 2) * BOX;
+    const float* sT = stage + (st * NF + 3) * BOX;
+    const float* sg = stage + (st * NF + 4) * BOX;
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    const int x0 = tx * TX_, y0 = ty * TY_;
+
+    // push values on the halo-1 region
+    for (int q = threadIdx.x; q < A1; q += NT) {
+      const int ly = q / LX1, lx = q - ly * LX1;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (i < 0 || i >= nx || j < 0 || j >= ny) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          F[k * A1 + q] = 0.f;
+          if (TH) Gp[k * A1 + q] = 0.f;
+        }
+        continue;
+      }
+      const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
+      const float uu = su[s2], vv = sv[s2];
+      float dudx = dfdx<float, BW>(su, sx, sy, i, nx);
+      const float dudy = dfdy<float, BW>(su, sx, sy, j, ny);
+      const float dvdx = dfdx<float, BW>(sv, sx, sy, i, nx);
+      float dvdy = dfdy<float, BW>(sv, sx, sy, j, ny);
+      const bool xe = (i == 0 || i == nx - 1), ye = (j == 0 || j == ny - 1);
+      if (xe && ye) {
+        dudx = 0.f;
+        dvdy = 0.f;
+      } else if (xe) {
+        dudx = -dvdy;
+      } else if (ye) {
+        dvdy = -dudx;
+      }
+      const float e0 = -1.5f * (uu * uu + vv * vv);
+      const float bx = 3.f * uu, by = 3.f * vv;
+      const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
+      const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
+      const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
+      const float dr = sdr[s2];
+      F[q] = e0 * (4.f / 9.f);
+      F[1 * A1 + q] = ((dr - sdr[s2 + 1]) + e0 + bx + qxx) * (1.f / 9.f);
+      F[3 * A1 + q] = ((dr - sdr[s2 - 1]) + e0 - bx + qxx) * (1.f / 9.f);
+      F[2 * A1 + q] = ((dr - sdr[s2 + BW]) + e0 + by + qyy) * (1.f / 9.f);
+      F[4 * A1 + q] = ((dr - sdr[s2 - BW]) + e0 - by + qyy) * (1.f / 9.f);
+      const float d0 = e0 + qxx + qyy;
+      F[5 * A1 + q] = (((dr - sdr[s2 + BW + 1]) + d0) + bx + by + qxy) * (1.f / 36.f);
+      F[6 * A1 + q] = (((dr - sdr[s2 + BW - 1]) + d0) - bx + by - qxy) * (1.f / 36.f);
+      F[7 * A1 + q] = (((dr - sdr[s2 - BW - 1]) + d0) - bx - by + qxy) * (1.f / 36.f);
+      F[8 * A1 + q] = (((dr - sdr[s2 - BW + 1]) + d0) + bx - by - qxy) * (1.f / 36.f);
+      if (TH) {
+        const float TT = sT[s2];
+        const float Bn = B_of(c, sg[s2]);
+        const float tq_x = 3.f * TT * uu + Bn * dfdx<float, BW>(sT, sx, sy, i, nx);
+        const float tq_y = 3.f * TT * vv + Bn * dfdy<float, BW>(sT, sx, sy, j, ny);
+        Gp[q] = 0.f;
+        Gp[1 * A1 + q] = ((TT - sT[s2 + 1]) + tq_x) * (1.f / 9.f);
+        Gp[3 * A1 + q] = ((TT - sT[s2 - 1]) - tq_x) * (1.f / 9.f);
+        Gp[2 * A1 + q] = ((TT - sT[s2 + BW]) + tq_y) * (1.f / 9.f);
+        Gp[4 * A1 + q] = ((TT - sT[s2 - BW]) - tq_y) * (1.f / 9.f);
+        Gp[5 * A1 + q] = ((TT - sT[s2 + BW + 1]) + tq_x + tq_y) * (1.f / 36.f);
+        Gp[6 * A1 + q] = ((TT - sT[s2 + BW - 1]) - tq_x + tq_y) * (1.f / 36.f);
+        Gp[7 * A1 + q] = ((TT - sT[s2 - BW - 1]) - tq_x - tq_y) * (1.f / 36.f);
+        Gp[8 * A1 + q] = ((TT - sT[s2 - BW + 1]) + tq_x - tq_y) * (1.f / 36.f);
+      }
+      // objective of the old state at interior tile nodes (unsteady accumulation)
+      if (a.J_partial && lx >= 1 && lx <= TX_ && ly >= 1 && ly <= TY_ && i > 0 && j > 0 && i < nx - 1 &&
+          j < ny - 1) {
+        const float cSxx = (su[s2 + 1] - su[s2 - 1]), cSyy = (sv[s2 + BW] - sv[s2 - BW]);
+        const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
+        const float al = alpha_of(c, TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i));
+        jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+        if (TH) jloc += (double)(c.kappa_T * sT[s2]);
+      }
+    }
+    __syncthreads();
+
+    for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
+      const int oy = q / TX_, ox = q - oy * TX_;
+      const int i = x0 + ox, j = y0 + oy;
+      if (i >= nx || j >= ny) continue;
+      const int q1 = (oy + 1) * LX1 + (ox + 1);
+      const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
+      int nxo, nyo;
+      const int cls = node_class(g, i, j, nxo, nyo);
+      const float drx = sdr[s2];
+      float fk[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) fk[k] = F[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
+      float drn, un, vn, Tn = 0.f;
+      if (cls == C_INTERIOR) {
+        drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
+        const float gm = TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i);
+        const float inv = 1.f / (1.f + alpha_of(c, gm));
+        un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
+        vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+        if (TH) {
+          float gs = 0.f;
+#pragma unroll
+          for (int k = 1; k < 9; ++k) gs += Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
+          Tn = sT[s2] + gs;
+        }
+      } else {
+        float s0 = 0.f, sp = 0.f, g0 = 0.f, gp = 0.f;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const int cx = cxk(k), cy = cyk(k);
+          const int si = i - cx, sj = j - cy;
+          if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
+          const int cn = cx * nxo + cy * nyo;
+          if (cn == 0) s0 += fk[k];
+          else if (cn > 0) sp += fk[k];
+          if (TH) {
+            const float gk = Gp[k * A1 + q1 - cx - cy * LX1];
+            if (cn == 0) g0 += gk;
+            else if (cn > 0) gp += gk;
+          }
+        }
+        if (cls == C_CORNER) {
+          const int jn = (j == 0) ? 1 : ny - 2;
+          drn = sdr[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
+          un = vn = 0.f;
+        } else if (cls == C_VELOCITY) {
+          un = 0.f;
+          if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
+            const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
+            un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
+          }
+          vn = 0.f;
+          drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
+        } else {
+          drn = c.drho_out;
+          const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
+          un = unorm * (float)nxo;
+          vn = unorm * (float)nyo;
+        }
+        if (TH) {
+          const int e = thermal_edge(g, i, j);
+          if (g.t_kind[e] == 0) {
+            Tn = c.t_val[e];
+          } else if (cls == C_CORNER) {
+            const int jn = (j == 0) ? 1 : ny - 2;
+            Tn = sT[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
+          } else {
+            Tn = (sT[s2] + g0 + 2.f * gp + c.t_val[e]) / (1.f + un * (float)nxo + vn * (float)nyo);
+          }
+        }
+      }
+      const size_t o = (size_t)j * nx + i;
+      a.drho_n[o] = drn;
+      a.u_n[o] = un;
+      a.v_n[o] = vn;
+      if (TH) a.T_n[o] = Tn;
+      if (a.traj_u) {
+        a.traj_u[o] = un;
+        a.traj_v[o] = vn;
+        if (TH) a.traj_T[o] = Tn;
+      }
+      if (bad_velocity(un, vn)) raise_status(a.status, 4);
+    }
+    __syncthreads();  // stage st and the push arrays are free again
+  }
+  if (a.J_partial) {
+    const double s = block_sum(jloc, red);
+    if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
+  }
+}
+
+// ---------------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------------
+template <bool TH>
+struct AdjTmaArgs {
+  float* m0[9];       // adjoint moments at level t
+  const float* gamma;
+  const float* emap;  // 9 classes x 6 x 10
+  float* sens;        // optional sensitivity accumulator
+  int sens_flow, sens_thermal;
+  int* status;
+  int ntx, ntiles;
+};
+
+// Staged fields: 6 adjoint (+3 thermal), u1, v1, [u0, v0], thermal: T0, gamma.
+template <bool TH, bool SAME>
+__host__ __device__ constexpr int adj_tma_nf() {
+  return (TH ? 9 : 6) + 2 + (SAME ? 0 : 2) + (TH ? 2 : 0);
+}
+template <bool TH, bool SAME, int TX_, int TY_>
+constexpr int adj_tma_smem_bytes() {
+  return 2 * adj_tma_nf<TH, SAME>() * (TX_ + 8) * (TY_ + 4) * 4 + (9 + 3 + (TH ? 1 : 0)) * (TX_ + 2) * (TY_ + 2) * 4 +
+         64;
+}
+
+template <bool TH, bool SAME, int TX_, int TY_, int NT>
+__global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ TmaMaps<adj_tma_nf<TH, SAME>()> maps,
+                                                     AdjTmaArgs<TH> a, Geom g, Coef<float> c) {
+  constexpr int NF = adj_tma_nf<TH, SAME>();
+  constexpr int NA = TH ? 9 : 6;
+  constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
+  constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
+  // stage field indices
+  constexpr int FU1 = NA, FV1 = NA + 1, FU0 = SAME ? NA : NA + 2, FV0 = SAME ? NA + 1 : NA + 3;
+  constexpr int FT0 = SAME ? NA + 2 : NA + 4, FG = FT0 + 1;
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float* stage = reinterpret_cast<float*>(smem_raw);  // [2][NF][BOX]
+  float* Pq = stage + 2 * NF * BOX;                    // [9][A1] push values P + c_k.V
+  float* cS = Pq + 9 * A1;                             // [3][A1] strain of the level-t state
+  float* cG = cS + 3 * A1;                             // thermal: G~ on the halo-1 region
+  uint64_t* bar = reinterpret_cast<uint64_t*>(cG + (TH ? A1 : 0));
+
+  if (timed_out_before(a.status)) return;
+  const int nx = g.nx, ny = g.ny;
+  auto issue = [&](int tile, int st) {
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    mbar_expect_tx(&bar[st], NF * BOX * 4);
+    for (int f = 0; f < NF; ++f)
+      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], tx * TX_ - TMA_BXPAD, ty * TY_ - 2, &bar[st]);
+  };
+  if (threadIdx.x == 0) {
+    mbar_init(&bar[0], 1);
+    mbar_init(&bar[1], 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    if ((int)blockIdx.x < a.ntiles) issue(blockIdx.x, 0);
+  }
+  __syncthreads();
+
+  int it = 0;
+  for (int tile = blockIdx.x; tile < a.ntiles; tile += gridDim.x, ++it) {
+    const int st = it & 1;
+    if (threadIdx.x == 0 && tile + (int)gridDim.x < a.ntiles) issue(tile + gridDim.x, st ^ 1);
+    if (!mbar_wait(&bar[st], (it >> 1) & 1)) {
+      raise_status(a.status, 6);
+      if (threadIdx.x == 0) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+      return;
+    }
+    const float* S = stage + st * NF * BOX;
+    const float* sa0 = S + 0 * BOX;
+    const float* sa3 = S + 3 * BOX;
+    const float* sa4 = S + 4 * BOX;
+    const float* sa5 = S + 5 * BOX;
+    const float* su1 = S + FU1 * BOX;
+    const float* sv1 = S + FV1 * BOX;
+    const float* su0 = S + FU0 * BOX;
+    const float* sv0 = S + FV0 * BOX;
+    const float* sT0 = S + FT0 * BOX;
+    const float* sg = S + FG * BOX;
+    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    const int x0 = tx * TX_, y0 = ty * TY_;
+
+    for (int q = threadIdx.x; q < A1; q += NT) {
+      const int ly = q / LX1, lx = q - ly * LX1;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (i < 0 || i >= nx || j < 0 || j >= ny) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = 0.f;
+        cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
+        if (TH) cG[q] = 0.f;
+        continue;
+      }
+      const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
+      const float rt = sa0[s2], ux = S[BOX + s2], uy = S[2 * BOX + s2];
+      const float sxx = sa3[s2], sxy = sa4[s2], syy = sa5[s2];
+      const float uu = su1[s2], vv = sv1[s2];
+      const float Dx = 2.f * (dfdx<float, BW>(sa3, sx, sy, i, nx) + dfdy<float, BW>(sa4, sx, sy, j, ny));
+      const float Dy = 2.f * (dfdx<float, BW>(sa4, sx, sy, i, nx) + dfdy<float, BW>(sa5, sx, sy, j, ny));
+      const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
+      const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
+      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
+        cS[q] = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
+        cS[A1 + q] = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
+        cS[2 * A1 + q] = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
+      } else {
+        cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
+      }
+      if (TH) {
+        const float* sTt = S + 6 * BOX;
+        const float* sqx = S + 7 * BOX;
+        const float* sqy = S + 8 * BOX;
+        const float qx = sqx[s2], qy = sqy[s2];
+        const float divq = dfdx<float, BW>(sqx, sx, sy, i, nx) + dfdy<float, BW>(sqy, sx, sy, j, ny);
+        // grad B from B(gamma) at the neighbours (same operator as for every field)
+        const float Bc = B_of(c, sg[s2]);
+        float dBx, dBy;
+        if (i == 0) dBx = (-3.f * Bc + 4.f * B_of(c, sg[s2 + 1]) - B_of(c, sg[s2 + 2])) * 0.5f;
+        else if (i == nx - 1) dBx = (3.f * Bc - 4.f * B_of(c, sg[s2 - 1]) + B_of(c, sg[s2 - 2])) * 0.5f;
+        else dBx = (B_of(c, sg[s2 + 1]) - B_of(c, sg[s2 - 1])) * 0.5f;
+        if (j == 0) dBy = (-3.f * Bc + 4.f * B_of(c, sg[s2 + BW]) - B_of(c, sg[s2 + 2 * BW])) * 0.5f;
+        else if (j == ny - 1) dBy = (3.f * Bc - 4.f * B_of(c, sg[s2 - BW]) + B_of(c, sg[s2 - 2 * BW])) * 0.5f;
+        else dBy = (B_of(c, sg[s2 + BW]) - B_of(c, sg[s2 - BW])) * 0.5f;
+        cG[q] = sTt[s2] + 3.f * (qx * uu + qy * vv) - Bc * divq - (dBx * qx + dBy * qy);
+      }
+    }
+    __syncthreads();
+
+    for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
+      const int oy = q / TX_, ox = q - oy * TX_;
+      const int i = x0 + ox, j = y0 + oy;
+      if (i >= nx || j >= ny) continue;
+      const int q1 = (oy + 1) * LX1 + (ox + 1);
+      const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
+      const bool interior = i > 0 && j > 0 && i < nx - 1 && j < ny - 1;
+      float ft[9], gt[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        const int qg = q1 + cxk(k) + cyk(k) * LX1;
+        ft[k] = Pq[k * A1 + qg];
+        if (TH) gt[k] = cG[qg];
+      }
+      float m[9];
+      if (interior) {
+        const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+        const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
+        m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
+        m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
+        m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
+        m[3] = w1 * ax + w5 * dg;
+        m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
+        m[5] = w1 * ay + w5 * dg;
+        const float gm = TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i);
+        const float al = alpha_of(c, gm);
+        const float uu0 = su0[s2], vv0 = sv0[s2];
+        const float ju = c.nu * (cS[q1 - 1] - cS[q1 + 1] + cS[A1 + q1 - LX1] - cS[A1 + q1 + LX1]) + 2.f * al * uu0;
+        const float jv = c.nu * (cS[2 * A1 + q1 - LX1] - cS[2 * A1 + q1 + LX1] + cS[A1 + q1 - 1] - cS[A1 + q1 + 1]) +
+                         2.f * al * vv0;
+        float cpx = 0.f, cpy = 0.f;
+        if (TH) {
+          const float gx = gt[1] + gt[3], gy = gt[2] + gt[4], gd = gt[5] + gt[6] + gt[7] + gt[8];
+          m[6] = w0 * gt[0] + w1 * (gx + gy) + w5 * gd - c.kappa_T;
+          m[7] = w1 * (gt[1] - gt[3]) + w5 * (gt[5] - gt[6] - gt[7] + gt[8]);
+          m[8] = w1 * (gt[2] - gt[4]) + w5 * (gt[5] + gt[6] - gt[7] - gt[8]);
+          const float T0 = sT0[s2];
+          cpx = T0 * m[7];
+          cpy = T0 * m[8];
+        }
+        const float inv = 1.f / (1.f + al);
+        m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
+        m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
+        if (a.sens) {
+          float sacc = 0.f;
+          if (a.sens_flow) {
+            const float da = dalpha_of(c, gm);
+            sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
+          }
+          if (TH && a.sens_thermal) {
+            const float dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * 0.5f;
+            const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
+            sacc -= dB_of(c, gm) * (dTx * m[7] + dTy * m[8]);
+          }
+          a.sens[(size_t)j * nx + i] += sacc;
+        }
+      } else {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+          const int gi = i + cxk(k), gj = j + cyk(k);
+          if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
+            ft[k] = 0.f;
+            gt[k] = 0.f;
+          }
+        }
+        float kT = 0.f;
+        if (TH) {
+          int nxo, nyo;
+          node_class(g, i, j, nxo, nyo);
+          const int e = thermal_edge(g, i, j);
+          const bool flux = g.t_kind[e] != 0;
+          const double un = (double)(su0[s2] * (float)nxo + sv0[s2] * (float)nyo);
+          double gd[9];
+#pragma unroll
+          for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
+          const double kap = thermal_edge_solve(nxo, nyo, (double)B_of(c, sg[s2]), flux, un, gd);
+          float T_ = 0.f, qx_ = 0.f, qy_ = 0.f;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const float gk = (float)gd[k] * wk<float>(k);
+            T_ += gk;
+            qx_ += (float)cxk(k) * gk;
+            qy_ += (float)cyk(k) * gk;
+          }
+          m[6] = T_;
+          m[7] = qx_;
+          m[8] = qy_;
+          if (flux) kT = (float)kap * sT0[s2];
+        }
+        const float* M = a.emap + edge_class(g, i, j) * 60;
+#pragma unroll
+        for (int r = 0; r < 6; ++r) {
+          float acc = 0.f;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
+          m[r] = acc + M[r * 10 + 9] * kT;
+        }
+      }
+      const size_t o = (size_t)j * nx + i;
+#pragma unroll
+      for (int f = 0; f < NA; ++f) a.m0[f][o] = m[f];
+      if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
+    }
+    __syncthreads();
+  }
+}
+
+}  // namespace lks

@@ -27,13 +27,15 @@ def rel_l2(a, b):
     return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
 
 
-def small(steady=True, **kw):
-    """70 x 40 nodes: three tiles across x and y with ragged last tiles."""
+def small(steady=True, nx=70, **kw):
+    """70 x 40 nodes: three tiles across x and y with ragged last tiles (plain
+    per-step kernels).  nx = 136: a multiple of four, so the FP32 per-step marches
+    run the TMA-staged kernels, again with ragged last tiles (136 = 2 x 64 + 8)."""
     base = dict(seed=1, sigma=2.0, strip=2, n_steps=300, n_adj=300)
     base.update(kw)
     if not steady:
         base.update(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=120.0)
-    return inputs.channel(70, 40, Re=10.0, **base)
+    return inputs.channel(nx, 40, Re=10.0, **base)
 
 
 def oracle_state(st):
@@ -254,3 +256,121 @@ def test_call_order_and_unstable_status():
     sb.lks_forward(torch.from_numpy(bad.gamma()))
     st = sb.query()
     assert st.device_status == 4
+
+
+# ---------------------------------------------------------------------------------------
+# Thermal lattice (T-fixed inlet and heated bottom wall, adiabatic top and outlet)
+# ---------------------------------------------------------------------------------------
+def thermal_small(steady, nx=70, **kw):
+    base = dict(seed=3, sigma=2.0, strip=2, n_steps=200, n_adj=200, thermal=1, kappa_T=1e-2,
+                t_kind=[0, 1, 0, 1], t_val=[0.0, 0.0, 1.0, 0.0])
+    base.update(kw)
+    if not steady:
+        base.update(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=120.0)
+    p = inputs.channel(nx, 40, Re=10.0, **base)
+    p.K_f = p.nu / 0.71
+    p.K_s = p.K_f
+    return p
+
+
+@pytest.mark.parametrize("path", ["step", "resident"])
+@pytest.mark.parametrize("real,tol", [("f64", 1e-11), ("f32", 1e-5)])
+def test_thermal_forward_matches_oracle(real, tol, path):
+    pb = thermal_small(True)
+    g = pb.gamma()
+    s = LKS(pb, real=real, path=path)
+    J = s.lks_forward(torch.from_numpy(g)).item()
+    st, _, _, _ = O.forward(pb, g, pb.n_steps)
+    got, T = gpu_state(s)
+    for a, b in zip(got, oracle_state(st)):
+        assert rel_l2(a, b) <= tol
+    assert rel_l2(T, st.T) <= tol
+    assert abs(J - O.objective(pb, g, st)) <= 10 * tol * abs(J)
+
+
+@pytest.mark.parametrize("real,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_thermal_steady_gradient_matches_oracle(real, tol):
+    pb = thermal_small(True)
+    g = pb.gamma()
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.steady_gradient(pb, g)
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    for q in range(9):
+        assert rel_l2(adj[q], ref["adjoint"][q]) <= tol, q
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= tol
+
+
+@pytest.mark.parametrize("real,tol", [("f64", 1e-10), ("f32", 1e-3)])
+def test_thermal_unsteady_gradient_matches_oracle(real, tol):
+    """Unsteady thermal problem with a conductivity contrast (K_s = 2 K_f), so the
+    B'(gamma) grad T . q~ term of the sensitivity is exercised."""
+    pb = thermal_small(False, n_steps=150)
+    pb.K_s = 2.0 * pb.K_f
+    g = pb.gamma()
+    s = LKS(pb, real=real, checkpoint_every=0)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= (1e-11 if real == "f64" else 1e-5) * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= tol
+
+
+def test_thermal_checkpoints_equal_plain():
+    pb = thermal_small(False, n_steps=150)
+    g = torch.from_numpy(pb.gamma())
+    J0, g0 = LKS(pb, real="f32", checkpoint_every=0).gradient(g)
+    J1, g1 = LKS(pb, real="f32", checkpoint_every=40, snapshot="f32").gradient(g)
+    assert J0.item() == J1.item()
+    assert torch.equal(g0, g1)
+
+
+
+# ---------------------------------------------------------------------------------------
+# TMA-staged per-step kernels (FP32, nx % 4 == 0)
+# ---------------------------------------------------------------------------------------
+def test_tma_forward_matches_oracle():
+    pb = small(nx=136)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="step")
+    J = s.lks_forward(torch.from_numpy(g)).item()
+    st, _, _, _ = O.forward(pb, g, pb.n_steps)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(st)):
+        assert rel_l2(a, b) <= 1e-5
+    assert abs(J - O.objective(pb, g, st)) <= 1e-5 * abs(J)
+
+
+def test_tma_steady_gradient_matches_oracle():
+    pb = small(nx=136)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="step")
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.steady_gradient(pb, g)
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    for q in range(6):
+        assert rel_l2(adj[q], ref["adjoint"][q]) <= 1e-3, q
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+
+
+@pytest.mark.parametrize("K", [0, 64])
+def test_tma_unsteady_gradient_matches_oracle(K):
+    pb = small(steady=False, nx=136, n_steps=200)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", checkpoint_every=K)
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+
+
+@pytest.mark.parametrize("steady", [True, False])
+def test_tma_thermal_gradient_matches_oracle(steady):
+    pb = thermal_small(steady, nx=136, n_steps=150)
+    if not steady:
+        pb.K_s = 2.0 * pb.K_f
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="step")
+    J, grad = s.gradient(torch.from_numpy(g))
+    ref = O.steady_gradient(pb, g) if steady else O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= 1e-4 * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
