@@ -247,7 +247,7 @@ struct lks_handle {
   std::vector<double> emap_h;
   std::vector<float> emap_f;
   std::unordered_map<uint64_t, CUtensorMap> tmaps;  // (pointer, box) -> tensor map
-  int tma_grid_fwd = 0, tma_grid_adj = 0;
+  int tma_grid_fwd = 0, tma_grid_adj[2][2] = {{0, 0}, {0, 0}};  // adj: [thermal][same state]
   std::string err;
 };
 
@@ -580,7 +580,8 @@ EncodeTiledFn encode_fn() {
   return fn;
 }
 
-constexpr int kFwdTX = 64, kFwdTY = 16, kAdjTX = 64, kAdjTY = 8;
+constexpr int kFwdTX = 64, kFwdTY = 8, kAdjTX = 64, kAdjTY = 8;
+constexpr int kFwdNT = 256, kAdjNT = 512;
 
 bool tma_ok(lks_handle* h) {
   return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
@@ -609,9 +610,9 @@ lks_status field_map(lks_handle* h, const void* ptr, int bw, int bh, CUtensorMap
 }
 
 template <typename K>
-int persistent_grid(lks_handle* h, K kern, size_t smem, int ntiles) {
+int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
   int per_sm = 0;
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NTHREADS, smem) != cudaSuccess || per_sm < 1)
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, nt, smem) != cudaSuccess || per_sm < 1)
     per_sm = 1;
   return std::max(1, std::min(ntiles, per_sm * device_sms(h)));
 }
@@ -642,12 +643,12 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
   a.ntx = (d.nx + kFwdTX - 1) / kFwdTX;
   a.ntiles = a.ntx * ((d.ny + kFwdTY - 1) / kFwdTY);
   const size_t smem = fwd_tma_smem_bytes<TH, kFwdTX, kFwdTY>();
-  auto kern = fwd_tma_kernel<TH, kFwdTX, kFwdTY, NTHREADS>;
+  auto kern = fwd_tma_kernel<TH, kFwdTX, kFwdTY, kFwdNT>;
   if (!h->tma_grid_fwd) {
     CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    h->tma_grid_fwd = persistent_grid(h, kern, smem, a.ntiles);
+    h->tma_grid_fwd = persistent_grid(h, kern, kFwdNT, smem, a.ntiles);
   }
-  kern<<<h->tma_grid_fwd, NTHREADS, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  kern<<<h->tma_grid_fwd, kFwdNT, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->cur = dst;
   h->t = t_new;
@@ -687,10 +688,13 @@ lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const
   a.ntx = (d.nx + kAdjTX - 1) / kAdjTX;
   a.ntiles = a.ntx * ((d.ny + kAdjTY - 1) / kAdjTY);
   const size_t smem = adj_tma_smem_bytes<TH, SAME, kAdjTX, kAdjTY>();
-  auto kern = adj_tma_kernel<TH, SAME, kAdjTX, kAdjTY, NTHREADS>;
-  CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  const int grid = persistent_grid(h, kern, smem, a.ntiles);
-  kern<<<grid, NTHREADS, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  auto kern = adj_tma_kernel<TH, SAME, kAdjTX, kAdjTY, kAdjNT>;
+  int& grid = h->tma_grid_adj[TH ? 1 : 0][SAME ? 1 : 0];
+  if (!grid) {
+    CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    grid = persistent_grid(h, kern, kAdjNT, smem, a.ntiles);
+  }
+  kern<<<grid, kAdjNT, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->acur = dst;
   h->adj_steps++;

@@ -152,7 +152,9 @@ __device__ __forceinline__ void raise_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
-// FP64 block reduction of one value per thread; thread 0 receives the sum.
+// FP64 block reduction of one value per thread (NT threads); thread 0 receives the
+// sum, in a fixed order.
+template <int NT = NTHREADS>
 __device__ __forceinline__ double block_sum(double v, double* red) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -160,7 +162,7 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   __syncthreads();
   double s = 0.0;
   if (threadIdx.x == 0)
-    for (int q = 0; q < NTHREADS / 32; ++q) s += red[q];
+    for (int q = 0; q < NT / 32; ++q) s += red[q];
   __syncthreads();
   return s;
 }

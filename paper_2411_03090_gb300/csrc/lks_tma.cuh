@@ -55,6 +55,18 @@ __device__ __forceinline__ bool timed_out_before(const int* status) {
   return status && *reinterpret_cast<const volatile int*>(status) == 6;
 }
 
+// Dynamic shared memory rounded up to 128 bytes (tensor copies need a 128-byte
+// aligned shared destination); the kernels declare no static shared memory.
+__device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
+  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+}
+// Self-check before any copy: the stages 128-byte and the mbarriers 8-byte aligned.
+__device__ __forceinline__ bool tma_layout_ok(const void* stage, const void* bar, int* status) {
+  const bool ok = (smem_u32(stage) & 127u) == 0 && (smem_u32(bar) & 7u) == 0;
+  if (!ok && threadIdx.x == 0) raise_status(status, 3);
+  return ok;
+}
+
 // Bounded wait for an mbarrier phase.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (long long it = 0; it < (1ll << 20); ++it) {
@@ -99,7 +111,7 @@ __host__ __device__ constexpr int fwd_tma_nf() {
 }
 template <bool TH, int TX_, int TY_>
 constexpr int fwd_tma_smem_bytes() {
-  return 2 * fwd_tma_nf<TH>() * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 64;
+  return 2 * fwd_tma_nf<TH>() * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 384;
 }
 
 template <bool TH, int TX_, int TY_, int NT>
@@ -108,15 +120,15 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
   constexpr int NF = fwd_tma_nf<TH>();
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
   constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* stage = reinterpret_cast<float*>(smem_raw);           // [2][NF][BOX]
-  float* F = stage + 2 * NF * BOX;                              // [9][A1]
-  float* Gp = F + 9 * A1;                                       // thermal [9][A1]
+  extern __shared__ unsigned char smem_raw[];
+  float* stage = reinterpret_cast<float*>(smem_base128(smem_raw));  // [2][NF][BOX]
+  float* F = stage + 2 * NF * BOX;                                   // [9][A1]
+  float* Gp = F + 9 * A1;                                            // thermal [9][A1]
   uint64_t* bar = reinterpret_cast<uint64_t*>(Gp + (TH ? 9 * A1 : 0));
-  static_assert(NT == NTHREADS, "block_sum assumes NTHREADS threads");
-  __shared__ double red[NTHREADS / 32];
+  double* red = reinterpret_cast<double*>(bar + 2);                  // NT / 32 doubles
 
   if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(stage, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny;
   auto issue = [&](int tile, int st) {
     const int tx = tile % a.ntx, ty = tile / a.ntx;
@@ -307,7 +319,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     __syncthreads();  // stage st and the push arrays are free again
   }
   if (a.J_partial) {
-    const double s = block_sum(jloc, red);
+    const double s = block_sum<NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
   }
 }
@@ -334,7 +346,7 @@ __host__ __device__ constexpr int adj_tma_nf() {
 template <bool TH, bool SAME, int TX_, int TY_>
 constexpr int adj_tma_smem_bytes() {
   return 2 * adj_tma_nf<TH, SAME>() * (TX_ + 8) * (TY_ + 4) * 4 + (9 + 3 + (TH ? 1 : 0)) * (TX_ + 2) * (TY_ + 2) * 4 +
-         64;
+         256;
 }
 
 template <bool TH, bool SAME, int TX_, int TY_, int NT>
@@ -347,14 +359,15 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
   // stage field indices
   constexpr int FU1 = NA, FV1 = NA + 1, FU0 = SAME ? NA : NA + 2, FV0 = SAME ? NA + 1 : NA + 3;
   constexpr int FT0 = SAME ? NA + 2 : NA + 4, FG = FT0 + 1;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
-  float* stage = reinterpret_cast<float*>(smem_raw);  // [2][NF][BOX]
+  extern __shared__ unsigned char smem_raw[];
+  float* stage = reinterpret_cast<float*>(smem_base128(smem_raw));  // [2][NF][BOX]
   float* Pq = stage + 2 * NF * BOX;                    // [9][A1] push values P + c_k.V
   float* cS = Pq + 9 * A1;                             // [3][A1] strain of the level-t state
   float* cG = cS + 3 * A1;                             // thermal: G~ on the halo-1 region
   uint64_t* bar = reinterpret_cast<uint64_t*>(cG + (TH ? A1 : 0));
 
   if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(stage, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny;
   auto issue = [&](int tile, int st) {
     const int tx = tile % a.ntx, ty = tile / a.ntx;
