@@ -38,7 +38,7 @@ const double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0
 // ------------------------------------------------------------------------------------
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
-  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0;
+  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0, mat = 0;
   size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
@@ -105,6 +105,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.status = take(sizeof(int));
   L.emap = take(L.rsize * 9 * 60);
   L.flags = take(sizeof(int) * (size_t)((d->nx + 31) / 32) * (size_t)((d->ny + 7) / 8));
+  L.mat = take(fb * 3);  // 1/(1+alpha), alpha, B (FP32 staged kernels)
   if (!d->steady) {
     L.sens = take(fb);
     L.sens64 = take(sizeof(double) * L.N);
@@ -619,15 +620,17 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
 
 template <bool TH>
 lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
-  constexpr int NF = fwd_tma_nf<TH>();
+  constexpr int NF = fwd_tma_nf(TH);
   constexpr int BW = kFwdTX + 8, BH = kFwdTY + 4;
   const auto& d = h->d;
   const int src = h->cur, dst = 1 - h->cur;
   TmaMaps<NF> maps;
   lks_status st;
-  for (int f = 0; f < (TH ? 4 : 3); ++f)
-    if ((st = field_map(h, state_ptr<float>(h, src, f), BW, BH, &maps.m[f])) != LKS_OK) return st;
-  if (TH && (st = field_map(h, fld<float>(h, h->L.gamma, 0), BW, BH, &maps.m[NF - 1])) != LKS_OK) return st;
+  const float* mat = fld<float>(h, h->L.mat, 0);
+  const float* fsrc[6] = {state_ptr<float>(h, src, 0), state_ptr<float>(h, src, 1), state_ptr<float>(h, src, 2), mat,
+                          TH ? state_ptr<float>(h, src, 3) : nullptr, mat + 2 * h->L.N};
+  for (int f = 0; f < NF; ++f)
+    if ((st = field_map(h, fsrc[f], BW, BH, &maps.m[f])) != LKS_OK) return st;
   FwdTmaArgs<TH> a;
   a.drho_n = state_ptr<float>(h, dst, 0);
   a.u_n = state_ptr<float>(h, dst, 1);
@@ -661,7 +664,7 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
 template <bool TH, bool SAME>
 lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
                           const float* T0, float* sens, int sens_flow, int sens_thermal) {
-  constexpr int NF = adj_tma_nf<TH, SAME>();
+  constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
   constexpr int BW = kAdjTX + 8, BH = kAdjTY + 4;
   const auto& d = h->d;
@@ -671,12 +674,14 @@ lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const
   int f = 0;
   for (int q = 0; q < NA; ++q)
     if ((st = field_map(h, adj_ptr<float>(h, src, q), BW, BH, &maps.m[f++])) != LKS_OK) return st;
-  const float* extra[6] = {u1, v1, u0, v0, T0, fld<float>(h, h->L.gamma, 0)};
-  for (int q = 0; q < 6; ++q) {
+  const float* mat = fld<float>(h, h->L.mat, 0);
+  const float* extra[8] = {u1, v1, u0, v0, mat + h->L.N, mat, T0, mat + 2 * h->L.N};  // ..., alpha, 1/(1+alpha), T0, B
+  for (int q = 0; q < 8; ++q) {
     if (SAME && (q == 2 || q == 3)) continue;
-    if (!TH && q >= 4) continue;
+    if (!TH && q >= 6) continue;
     if ((st = field_map(h, extra[q], BW, BH, &maps.m[f++])) != LKS_OK) return st;
   }
+  if (f != NF) return fail(h, LKS_ERR_INVALID_ARG, "tensor map count");
   AdjTmaArgs<TH> a;
   for (int q = 0; q < 9; ++q) a.m0[q] = adj_ptr<float>(h, dst, q < NA ? q : 0);
   a.gamma = fld<float>(h, h->L.gamma, 0);
@@ -820,6 +825,21 @@ lks_status snapshot_load(lks_handle* h, int idx) {
   return LKS_OK;
 }
 
+// Material fields 1/(1+alpha), alpha, B of the current design (FP32 staged kernels).
+template <typename R>
+lks_status update_materials(lks_handle* h) {
+  if constexpr (sizeof(R) == 4) {
+    if (!tma_ok(h)) return LKS_OK;
+    float* m = fld<float>(h, h->L.mat, 0);
+    material_kernel<<<elementwise_grid(h->L.N), 256, 0, h->stream>>>(fld<float>(h, h->L.gamma, 0), h->L.N,
+                                                                     make_coef<float>(h->d), m, m + h->L.N,
+                                                                     h->d.thermal ? m + 2 * h->L.N : nullptr);
+    CKH(h, cudaGetLastError());
+    h->launches++;
+  }
+  return LKS_OK;
+}
+
 template <typename R>
 lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   const auto& d = h->d;
@@ -831,6 +851,7 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   CKH(h, cudaMemsetAsync(h->ws + L.status, 0, sizeof(int), h->stream));
   h->cur = 0;
   h->t = 0;
+  if (lks_status ms = update_materials<R>(h); ms != LKS_OK) return ms;
   double* jfwd = reinterpret_cast<double*>(h->ws + L.jfwd);
   double* jobj = reinterpret_cast<double*>(h->ws + L.jobj);
   double* jval = reinterpret_cast<double*>(h->ws + L.jval);
@@ -1130,7 +1151,7 @@ lks_status lks_set_state(lks_handle* h, const void* gamma_dev, const void* rho_d
     CKH(h, cudaMemcpyAsync(h->ws + h->L.stA + (size_t)f * fb, src[f], fb, cudaMemcpyDeviceToDevice, h->stream));
   h->t = t;
   if (h->phase < 1) h->phase = 1;
-  return LKS_OK;
+  return h->d.real_type == LKS_REAL_F64 ? update_materials<double>(h) : update_materials<float>(h);
 }
 
 lks_status lks_get_state(lks_handle* h, void* rho_dev, void* u_dev, void* v_dev, void* T_dev) {

@@ -6,11 +6,18 @@
 // with a two-node halo, into one of two shared-memory stages; an mbarrier with a
 // transaction count signals arrival.  While the CTA computes tile k from one stage,
 // the copies of tile k+1 fill the other.  Out-of-lattice parts of a box arrive as
-// zeros (tensor-map fill), so no thread computes a load address.
+// zeros (tensor-map fill), so no thread computes a load address.  The material
+// fields 1/(1 + alpha_gamma), alpha_gamma and B_gamma are computed once per march
+// (material_kernel) and staged like the state, so the step kernels read no
+// per-node global memory and divide nothing.
+//
+// Tiles whose two-node halo stays clear of the domain edge take a path without
+// any edge test; edge tiles take the general path with the edge rules.
 //
 // TMA alignment: the box starts at x0 - 4 (a multiple of four floats, 16 bytes) and
 // is TX + 8 floats wide; rows are nx floats apart, so the lattice needs nx % 4 == 0
-// (the host falls back to the plain kernels otherwise).  Waits on an mbarrier are
+// (the host falls back to the plain kernels otherwise).  Shared stages are
+// 128-byte aligned (checked before the first copy).  Waits on an mbarrier are
 // bounded; on timeout the kernel records LKS_ERR_TIMEOUT, waits (bounded) for its
 // own copies and returns.
 //
@@ -19,6 +26,8 @@
 // sums nine shared-memory values).
 #pragma once
 #include <cuda.h>
+
+#include <type_traits>
 
 #include "lks_kernels.cuh"
 
@@ -54,7 +63,6 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 __device__ __forceinline__ bool timed_out_before(const int* status) {
   return status && *reinterpret_cast<const volatile int*>(status) == 6;
 }
-
 // Dynamic shared memory rounded up to 128 bytes (tensor copies need a 128-byte
 // aligned shared destination); the kernels declare no static shared memory.
 __device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
@@ -66,7 +74,6 @@ __device__ __forceinline__ bool tma_layout_ok(const void* stage, const void* bar
   if (!ok && threadIdx.x == 0) raise_status(status, 3);
   return ok;
 }
-
 // Bounded wait for an mbarrier phase.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   for (long long it = 0; it < (1ll << 20); ++it) {
@@ -84,6 +91,25 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
 }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
+
+// Material fields of one march: 1 / (1 + alpha_gamma), alpha_gamma (Eq. brinkman)
+// and B_gamma (Eqs. conductivity, B), one float each per node.
+__global__ void material_kernel(const float* __restrict__ gamma, size_t n, Coef<float> c, float* __restrict__ binv,
+                                float* __restrict__ alpha, float* __restrict__ B) {
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    const float gm = gamma[o];
+    const float al = alpha_of(c, gm);
+    binv[o] = 1.f / (1.f + al);
+    alpha[o] = al;
+    if (B) B[o] = B_of(c, gm);
+  }
+}
+
+// Interior test of a tile: every node of its halo-1 ring is a non-edge node, so the
+// central differences and the interior update apply everywhere.
+__device__ __forceinline__ bool tile_is_interior(int x0, int y0, int tx_, int ty_, int nx, int ny) {
+  return x0 >= 2 && y0 >= 2 && x0 + tx_ + 2 <= nx && y0 + ty_ + 2 <= ny;
+}
 
 // ---------------------------------------------------------------------------------
 // Forward
@@ -104,20 +130,17 @@ struct FwdTmaArgs {
   int ntx, ntiles;
 };
 
-// fields staged per stage: drho, u, v (, T, gamma)
-template <bool TH>
-__host__ __device__ constexpr int fwd_tma_nf() {
-  return TH ? 5 : 3;
-}
+// fields staged per stage: drho, u, v, 1/(1+alpha) (, T, B)
+__host__ __device__ constexpr int fwd_tma_nf(bool th) { return th ? 6 : 4; }
 template <bool TH, int TX_, int TY_>
 constexpr int fwd_tma_smem_bytes() {
-  return 2 * fwd_tma_nf<TH>() * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 384;
+  return 2 * fwd_tma_nf(TH) * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 384;
 }
 
 template <bool TH, int TX_, int TY_, int NT>
-__global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ TmaMaps<fwd_tma_nf<TH>()> maps,
+__global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ TmaMaps<fwd_tma_nf(TH)> maps,
                                                      FwdTmaArgs<TH> a, Geom g, Coef<float> c) {
-  constexpr int NF = fwd_tma_nf<TH>();
+  constexpr int NF = fwd_tma_nf(TH);
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
   constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
   extern __shared__ unsigned char smem_raw[];
@@ -158,163 +181,189 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     const float* sdr = stage + (st * NF + 0) * BOX;
     const float* su = stage + (st * NF + 1) * BOX;
     const float* sv = stage + (st * NF + 2) * BOX;
-    const float* sT = stage + (st * NF + 3) * BOX;
-    const float* sg = stage + (st * NF + 4) * BOX;
+    const float* sbi = stage + (st * NF + 3) * BOX;  // 1 / (1 + alpha)
+    const float* sT = stage + (st * NF + 4) * BOX;   // thermal
+    const float* sB = stage + (st * NF + 5) * BOX;   // thermal
     const int tx = tile % a.ntx, ty = tile / a.ntx;
     const int x0 = tx * TX_, y0 = ty * TY_;
 
     // push values on the halo-1 region
-    for (int q = threadIdx.x; q < A1; q += NT) {
-      const int ly = q / LX1, lx = q - ly * LX1;
-      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
-      if (i < 0 || i >= nx || j < 0 || j >= ny) {
+    auto phase_a = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      for (int q = threadIdx.x; q < A1; q += NT) {
+        const int ly = q / LX1, lx = q - ly * LX1;
+        const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+        if (EDGE && (i < 0 || i >= nx || j < 0 || j >= ny)) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          F[k * A1 + q] = 0.f;
-          if (TH) Gp[k * A1 + q] = 0.f;
-        }
-        continue;
-      }
-      const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
-      const float uu = su[s2], vv = sv[s2];
-      float dudx = dfdx<float, BW>(su, sx, sy, i, nx);
-      const float dudy = dfdy<float, BW>(su, sx, sy, j, ny);
-      const float dvdx = dfdx<float, BW>(sv, sx, sy, i, nx);
-      float dvdy = dfdy<float, BW>(sv, sx, sy, j, ny);
-      const bool xe = (i == 0 || i == nx - 1), ye = (j == 0 || j == ny - 1);
-      if (xe && ye) {
-        dudx = 0.f;
-        dvdy = 0.f;
-      } else if (xe) {
-        dudx = -dvdy;
-      } else if (ye) {
-        dvdy = -dudx;
-      }
-      const float e0 = -1.5f * (uu * uu + vv * vv);
-      const float bx = 3.f * uu, by = 3.f * vv;
-      const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
-      const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
-      const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
-      const float dr = sdr[s2];
-      F[q] = e0 * (4.f / 9.f);
-      F[1 * A1 + q] = ((dr - sdr[s2 + 1]) + e0 + bx + qxx) * (1.f / 9.f);
-      F[3 * A1 + q] = ((dr - sdr[s2 - 1]) + e0 - bx + qxx) * (1.f / 9.f);
-      F[2 * A1 + q] = ((dr - sdr[s2 + BW]) + e0 + by + qyy) * (1.f / 9.f);
-      F[4 * A1 + q] = ((dr - sdr[s2 - BW]) + e0 - by + qyy) * (1.f / 9.f);
-      const float d0 = e0 + qxx + qyy;
-      F[5 * A1 + q] = (((dr - sdr[s2 + BW + 1]) + d0) + bx + by + qxy) * (1.f / 36.f);
-      F[6 * A1 + q] = (((dr - sdr[s2 + BW - 1]) + d0) - bx + by - qxy) * (1.f / 36.f);
-      F[7 * A1 + q] = (((dr - sdr[s2 - BW - 1]) + d0) - bx - by + qxy) * (1.f / 36.f);
-      F[8 * A1 + q] = (((dr - sdr[s2 - BW + 1]) + d0) + bx - by - qxy) * (1.f / 36.f);
-      if (TH) {
-        const float TT = sT[s2];
-        const float Bn = B_of(c, sg[s2]);
-        const float tq_x = 3.f * TT * uu + Bn * dfdx<float, BW>(sT, sx, sy, i, nx);
-        const float tq_y = 3.f * TT * vv + Bn * dfdy<float, BW>(sT, sx, sy, j, ny);
-        Gp[q] = 0.f;
-        Gp[1 * A1 + q] = ((TT - sT[s2 + 1]) + tq_x) * (1.f / 9.f);
-        Gp[3 * A1 + q] = ((TT - sT[s2 - 1]) - tq_x) * (1.f / 9.f);
-        Gp[2 * A1 + q] = ((TT - sT[s2 + BW]) + tq_y) * (1.f / 9.f);
-        Gp[4 * A1 + q] = ((TT - sT[s2 - BW]) - tq_y) * (1.f / 9.f);
-        Gp[5 * A1 + q] = ((TT - sT[s2 + BW + 1]) + tq_x + tq_y) * (1.f / 36.f);
-        Gp[6 * A1 + q] = ((TT - sT[s2 + BW - 1]) - tq_x + tq_y) * (1.f / 36.f);
-        Gp[7 * A1 + q] = ((TT - sT[s2 - BW - 1]) - tq_x - tq_y) * (1.f / 36.f);
-        Gp[8 * A1 + q] = ((TT - sT[s2 - BW + 1]) + tq_x - tq_y) * (1.f / 36.f);
-      }
-      // objective of the old state at interior tile nodes (unsteady accumulation)
-      if (a.J_partial && lx >= 1 && lx <= TX_ && ly >= 1 && ly <= TY_ && i > 0 && j > 0 && i < nx - 1 &&
-          j < ny - 1) {
-        const float cSxx = (su[s2 + 1] - su[s2 - 1]), cSyy = (sv[s2 + BW] - sv[s2 - BW]);
-        const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
-        const float al = alpha_of(c, TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i));
-        jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
-        if (TH) jloc += (double)(c.kappa_T * sT[s2]);
-      }
-    }
-    __syncthreads();
-
-    for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
-      const int oy = q / TX_, ox = q - oy * TX_;
-      const int i = x0 + ox, j = y0 + oy;
-      if (i >= nx || j >= ny) continue;
-      const int q1 = (oy + 1) * LX1 + (ox + 1);
-      const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
-      int nxo, nyo;
-      const int cls = node_class(g, i, j, nxo, nyo);
-      const float drx = sdr[s2];
-      float fk[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) fk[k] = F[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
-      float drn, un, vn, Tn = 0.f;
-      if (cls == C_INTERIOR) {
-        drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
-        const float gm = TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i);
-        const float inv = 1.f / (1.f + alpha_of(c, gm));
-        un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
-        vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
-        if (TH) {
-          float gs = 0.f;
-#pragma unroll
-          for (int k = 1; k < 9; ++k) gs += Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
-          Tn = sT[s2] + gs;
-        }
-      } else {
-        float s0 = 0.f, sp = 0.f, g0 = 0.f, gp = 0.f;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) {
-          const int cx = cxk(k), cy = cyk(k);
-          const int si = i - cx, sj = j - cy;
-          if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
-          const int cn = cx * nxo + cy * nyo;
-          if (cn == 0) s0 += fk[k];
-          else if (cn > 0) sp += fk[k];
-          if (TH) {
-            const float gk = Gp[k * A1 + q1 - cx - cy * LX1];
-            if (cn == 0) g0 += gk;
-            else if (cn > 0) gp += gk;
+          for (int k = 0; k < 9; ++k) {
+            F[k * A1 + q] = 0.f;
+            if (TH) Gp[k * A1 + q] = 0.f;
           }
+          continue;
         }
-        if (cls == C_CORNER) {
-          const int jn = (j == 0) ? 1 : ny - 2;
-          drn = sdr[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
-          un = vn = 0.f;
-        } else if (cls == C_VELOCITY) {
-          un = 0.f;
-          if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
-            const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
-            un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
+        const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
+        const float uu = su[s2], vv = sv[s2];
+        float dudx, dudy, dvdx, dvdy;
+        if (EDGE) {
+          dudx = dfdx<float, BW>(su, sx, sy, i, nx);
+          dudy = dfdy<float, BW>(su, sx, sy, j, ny);
+          dvdx = dfdx<float, BW>(sv, sx, sy, i, nx);
+          dvdy = dfdy<float, BW>(sv, sx, sy, j, ny);
+          const bool xe = (i == 0 || i == nx - 1), ye = (j == 0 || j == ny - 1);
+          if (xe && ye) {
+            dudx = 0.f;
+            dvdy = 0.f;
+          } else if (xe) {
+            dudx = -dvdy;
+          } else if (ye) {
+            dvdy = -dudx;
           }
-          vn = 0.f;
-          drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
         } else {
-          drn = c.drho_out;
-          const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
-          un = unorm * (float)nxo;
-          vn = unorm * (float)nyo;
+          dudx = (su[s2 + 1] - su[s2 - 1]) * 0.5f;
+          dudy = (su[s2 + BW] - su[s2 - BW]) * 0.5f;
+          dvdx = (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
+          dvdy = (sv[s2 + BW] - sv[s2 - BW]) * 0.5f;
         }
+        const float e0 = -1.5f * (uu * uu + vv * vv);
+        const float bx = 3.f * uu, by = 3.f * vv;
+        const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
+        const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
+        const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
+        const float dr = sdr[s2];
+        F[q] = e0 * (4.f / 9.f);
+        F[1 * A1 + q] = ((dr - sdr[s2 + 1]) + e0 + bx + qxx) * (1.f / 9.f);
+        F[3 * A1 + q] = ((dr - sdr[s2 - 1]) + e0 - bx + qxx) * (1.f / 9.f);
+        F[2 * A1 + q] = ((dr - sdr[s2 + BW]) + e0 + by + qyy) * (1.f / 9.f);
+        F[4 * A1 + q] = ((dr - sdr[s2 - BW]) + e0 - by + qyy) * (1.f / 9.f);
+        const float d0 = e0 + qxx + qyy;
+        F[5 * A1 + q] = (((dr - sdr[s2 + BW + 1]) + d0) + bx + by + qxy) * (1.f / 36.f);
+        F[6 * A1 + q] = (((dr - sdr[s2 + BW - 1]) + d0) - bx + by - qxy) * (1.f / 36.f);
+        F[7 * A1 + q] = (((dr - sdr[s2 - BW - 1]) + d0) - bx - by + qxy) * (1.f / 36.f);
+        F[8 * A1 + q] = (((dr - sdr[s2 - BW + 1]) + d0) + bx - by - qxy) * (1.f / 36.f);
         if (TH) {
-          const int e = thermal_edge(g, i, j);
-          if (g.t_kind[e] == 0) {
-            Tn = c.t_val[e];
-          } else if (cls == C_CORNER) {
+          const float TT = sT[s2];
+          const float Bn = sB[s2];
+          const float dTx = EDGE ? dfdx<float, BW>(sT, sx, sy, i, nx) : (sT[s2 + 1] - sT[s2 - 1]) * 0.5f;
+          const float dTy = EDGE ? dfdy<float, BW>(sT, sx, sy, j, ny) : (sT[s2 + BW] - sT[s2 - BW]) * 0.5f;
+          const float tq_x = 3.f * TT * uu + Bn * dTx;
+          const float tq_y = 3.f * TT * vv + Bn * dTy;
+          Gp[q] = 0.f;
+          Gp[1 * A1 + q] = ((TT - sT[s2 + 1]) + tq_x) * (1.f / 9.f);
+          Gp[3 * A1 + q] = ((TT - sT[s2 - 1]) - tq_x) * (1.f / 9.f);
+          Gp[2 * A1 + q] = ((TT - sT[s2 + BW]) + tq_y) * (1.f / 9.f);
+          Gp[4 * A1 + q] = ((TT - sT[s2 - BW]) - tq_y) * (1.f / 9.f);
+          Gp[5 * A1 + q] = ((TT - sT[s2 + BW + 1]) + tq_x + tq_y) * (1.f / 36.f);
+          Gp[6 * A1 + q] = ((TT - sT[s2 + BW - 1]) - tq_x + tq_y) * (1.f / 36.f);
+          Gp[7 * A1 + q] = ((TT - sT[s2 - BW - 1]) - tq_x - tq_y) * (1.f / 36.f);
+          Gp[8 * A1 + q] = ((TT - sT[s2 - BW + 1]) + tq_x - tq_y) * (1.f / 36.f);
+        }
+        // objective of the old state at interior tile nodes (unsteady accumulation)
+        if (a.J_partial && lx >= 1 && lx <= TX_ && ly >= 1 && ly <= TY_ &&
+            (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1))) {
+          const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
+          const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
+          const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
+          const float al = __fdividef(1.f, sbi[s2]) - 1.f;
+          jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+          if (TH) jloc += (double)(c.kappa_T * sT[s2]);
+        }
+      }
+    };
+
+    auto phase_b = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
+        const int oy = q / TX_, ox = q - oy * TX_;
+        const int i = x0 + ox, j = y0 + oy;
+        if (EDGE && (i >= nx || j >= ny)) continue;
+        const int q1 = (oy + 1) * LX1 + (ox + 1);
+        const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
+        int nxo = 0, nyo = 0;
+        const int cls = EDGE ? node_class(g, i, j, nxo, nyo) : C_INTERIOR;
+        const float drx = sdr[s2];
+        float fk[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) fk[k] = F[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
+        float drn, un, vn, Tn = 0.f;
+        if (cls == C_INTERIOR) {
+          drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
+          const float inv = sbi[s2];
+          un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
+          vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+          if (TH) {
+            float gs = 0.f;
+#pragma unroll
+            for (int k = 1; k < 9; ++k) gs += Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
+            Tn = sT[s2] + gs;
+          }
+        } else {
+          float s0 = 0.f, sp = 0.f, g0 = 0.f, gp = 0.f;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int cx = cxk(k), cy = cyk(k);
+            const int si = i - cx, sj = j - cy;
+            if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
+            const int cn = cx * nxo + cy * nyo;
+            if (cn == 0) s0 += fk[k];
+            else if (cn > 0) sp += fk[k];
+            if (TH) {
+              const float gk = Gp[k * A1 + q1 - cx - cy * LX1];
+              if (cn == 0) g0 += gk;
+              else if (cn > 0) gp += gk;
+            }
+          }
+          if (cls == C_CORNER) {
             const int jn = (j == 0) ? 1 : ny - 2;
-            Tn = sT[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
+            drn = sdr[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
+            un = vn = 0.f;
+          } else if (cls == C_VELOCITY) {
+            un = 0.f;
+            if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
+              const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
+              un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
+            }
+            vn = 0.f;
+            drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
           } else {
-            Tn = (sT[s2] + g0 + 2.f * gp + c.t_val[e]) / (1.f + un * (float)nxo + vn * (float)nyo);
+            drn = c.drho_out;
+            const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
+            un = unorm * (float)nxo;
+            vn = unorm * (float)nyo;
+          }
+          if (TH) {
+            const int e = thermal_edge(g, i, j);
+            if (g.t_kind[e] == 0) {
+              Tn = c.t_val[e];
+            } else if (cls == C_CORNER) {
+              const int jn = (j == 0) ? 1 : ny - 2;
+              Tn = sT[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
+            } else {
+              Tn = (sT[s2] + g0 + 2.f * gp + c.t_val[e]) / (1.f + un * (float)nxo + vn * (float)nyo);
+            }
           }
         }
+        const size_t o = (size_t)j * nx + i;
+        a.drho_n[o] = drn;
+        a.u_n[o] = un;
+        a.v_n[o] = vn;
+        if (TH) a.T_n[o] = Tn;
+        if (a.traj_u) {
+          a.traj_u[o] = un;
+          a.traj_v[o] = vn;
+          if (TH) a.traj_T[o] = Tn;
+        }
+        if (bad_velocity(un, vn)) raise_status(a.status, 4);
       }
-      const size_t o = (size_t)j * nx + i;
-      a.drho_n[o] = drn;
-      a.u_n[o] = un;
-      a.v_n[o] = vn;
-      if (TH) a.T_n[o] = Tn;
-      if (a.traj_u) {
-        a.traj_u[o] = un;
-        a.traj_v[o] = vn;
-        if (TH) a.traj_T[o] = Tn;
-      }
-      if (bad_velocity(un, vn)) raise_status(a.status, 4);
+    };
+
+    if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
+      phase_a(std::false_type{});
+      __syncthreads();
+      phase_b(std::false_type{});
+    } else {
+      phase_a(std::true_type{});
+      __syncthreads();
+      phase_b(std::true_type{});
     }
     __syncthreads();  // stage st and the push arrays are free again
   }
@@ -338,32 +387,32 @@ struct AdjTmaArgs {
   int ntx, ntiles;
 };
 
-// Staged fields: 6 adjoint (+3 thermal), u1, v1, [u0, v0], thermal: T0, gamma.
-template <bool TH, bool SAME>
-__host__ __device__ constexpr int adj_tma_nf() {
-  return (TH ? 9 : 6) + 2 + (SAME ? 0 : 2) + (TH ? 2 : 0);
+// Staged fields: 6 adjoint (+3 thermal), u1, v1, [u0, v0], alpha, 1/(1+alpha),
+// thermal: T0, B.
+__host__ __device__ constexpr int adj_tma_nf(bool th, bool same) {
+  return (th ? 9 : 6) + 2 + (same ? 0 : 2) + 2 + (th ? 2 : 0);
 }
 template <bool TH, bool SAME, int TX_, int TY_>
 constexpr int adj_tma_smem_bytes() {
-  return 2 * adj_tma_nf<TH, SAME>() * (TX_ + 8) * (TY_ + 4) * 4 + (9 + 3 + (TH ? 1 : 0)) * (TX_ + 2) * (TY_ + 2) * 4 +
+  return 2 * adj_tma_nf(TH, SAME) * (TX_ + 8) * (TY_ + 4) * 4 + (9 + 3 + (TH ? 1 : 0)) * (TX_ + 2) * (TY_ + 2) * 4 +
          256;
 }
 
 template <bool TH, bool SAME, int TX_, int TY_, int NT>
-__global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ TmaMaps<adj_tma_nf<TH, SAME>()> maps,
+__global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ TmaMaps<adj_tma_nf(TH, SAME)> maps,
                                                      AdjTmaArgs<TH> a, Geom g, Coef<float> c) {
-  constexpr int NF = adj_tma_nf<TH, SAME>();
+  constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
   constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
   // stage field indices
   constexpr int FU1 = NA, FV1 = NA + 1, FU0 = SAME ? NA : NA + 2, FV0 = SAME ? NA + 1 : NA + 3;
-  constexpr int FT0 = SAME ? NA + 2 : NA + 4, FG = FT0 + 1;
+  constexpr int FAL = SAME ? NA + 2 : NA + 4, FBI = FAL + 1, FT0 = FAL + 2, FB = FAL + 3;
   extern __shared__ unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_base128(smem_raw));  // [2][NF][BOX]
-  float* Pq = stage + 2 * NF * BOX;                    // [9][A1] push values P + c_k.V
-  float* cS = Pq + 9 * A1;                             // [3][A1] strain of the level-t state
-  float* cG = cS + 3 * A1;                             // thermal: G~ on the halo-1 region
+  float* Pq = stage + 2 * NF * BOX;                                  // [9][A1] push values P + c_k.V
+  float* cS = Pq + 9 * A1;                                           // [3][A1] strain of the level-t state
+  float* cG = cS + 3 * A1;                                           // thermal: G~ on the halo-1 region
   uint64_t* bar = reinterpret_cast<uint64_t*>(cG + (TH ? A1 : 0));
 
   if (timed_out_before(a.status)) return;
@@ -402,160 +451,184 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
     const float* sv1 = S + FV1 * BOX;
     const float* su0 = S + FU0 * BOX;
     const float* sv0 = S + FV0 * BOX;
-    const float* sT0 = S + FT0 * BOX;
-    const float* sg = S + FG * BOX;
+    const float* sal = S + FAL * BOX;
+    const float* sbi = S + FBI * BOX;
+    const float* sT0 = S + FT0 * BOX;  // thermal
+    const float* sB = S + FB * BOX;    // thermal
     const int tx = tile % a.ntx, ty = tile / a.ntx;
     const int x0 = tx * TX_, y0 = ty * TY_;
 
-    for (int q = threadIdx.x; q < A1; q += NT) {
-      const int ly = q / LX1, lx = q - ly * LX1;
-      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
-      if (i < 0 || i >= nx || j < 0 || j >= ny) {
+    auto phase_a = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      for (int q = threadIdx.x; q < A1; q += NT) {
+        const int ly = q / LX1, lx = q - ly * LX1;
+        const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+        if (EDGE && (i < 0 || i >= nx || j < 0 || j >= ny)) {
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = 0.f;
-        cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
-        if (TH) cG[q] = 0.f;
-        continue;
-      }
-      const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
-      const float rt = sa0[s2], ux = S[BOX + s2], uy = S[2 * BOX + s2];
-      const float sxx = sa3[s2], sxy = sa4[s2], syy = sa5[s2];
-      const float uu = su1[s2], vv = sv1[s2];
-      const float Dx = 2.f * (dfdx<float, BW>(sa3, sx, sy, i, nx) + dfdy<float, BW>(sa4, sx, sy, j, ny));
-      const float Dy = 2.f * (dfdx<float, BW>(sa4, sx, sy, i, nx) + dfdy<float, BW>(sa5, sx, sy, j, ny));
-      const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
-      const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
+          for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = 0.f;
+          cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
+          if (TH) cG[q] = 0.f;
+          continue;
+        }
+        const int sx = lx + TMA_BXPAD - 1, sy = ly + 1, s2 = sy * BW + sx;
+        const float rt = sa0[s2], ux = S[BOX + s2], uy = S[2 * BOX + s2];
+        const float sxx = sa3[s2], sxy = sa4[s2], syy = sa5[s2];
+        const float uu = su1[s2], vv = sv1[s2];
+        float Dx, Dy;
+        if (EDGE) {
+          Dx = 2.f * (dfdx<float, BW>(sa3, sx, sy, i, nx) + dfdy<float, BW>(sa4, sx, sy, j, ny));
+          Dy = 2.f * (dfdx<float, BW>(sa4, sx, sy, i, nx) + dfdy<float, BW>(sa5, sx, sy, j, ny));
+        } else {
+          Dx = 2.f * ((sa3[s2 + 1] - sa3[s2 - 1]) * 0.5f + (sa4[s2 + BW] - sa4[s2 - BW]) * 0.5f);
+          Dy = 2.f * ((sa4[s2 + 1] - sa4[s2 - 1]) * 0.5f + (sa5[s2 + BW] - sa5[s2 - BW]) * 0.5f);
+        }
+        const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
+        const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
 #pragma unroll
-      for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
-      if (i > 0 && j > 0 && i < nx - 1 && j < ny - 1) {
-        cS[q] = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
-        cS[A1 + q] = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
-        cS[2 * A1 + q] = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
-      } else {
-        cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
-      }
-      if (TH) {
-        const float* sTt = S + 6 * BOX;
-        const float* sqx = S + 7 * BOX;
-        const float* sqy = S + 8 * BOX;
-        const float qx = sqx[s2], qy = sqy[s2];
-        const float divq = dfdx<float, BW>(sqx, sx, sy, i, nx) + dfdy<float, BW>(sqy, sx, sy, j, ny);
-        // grad B from B(gamma) at the neighbours (same operator as for every field)
-        const float Bc = B_of(c, sg[s2]);
-        float dBx, dBy;
-        if (i == 0) dBx = (-3.f * Bc + 4.f * B_of(c, sg[s2 + 1]) - B_of(c, sg[s2 + 2])) * 0.5f;
-        else if (i == nx - 1) dBx = (3.f * Bc - 4.f * B_of(c, sg[s2 - 1]) + B_of(c, sg[s2 - 2])) * 0.5f;
-        else dBx = (B_of(c, sg[s2 + 1]) - B_of(c, sg[s2 - 1])) * 0.5f;
-        if (j == 0) dBy = (-3.f * Bc + 4.f * B_of(c, sg[s2 + BW]) - B_of(c, sg[s2 + 2 * BW])) * 0.5f;
-        else if (j == ny - 1) dBy = (3.f * Bc - 4.f * B_of(c, sg[s2 - BW]) + B_of(c, sg[s2 - 2 * BW])) * 0.5f;
-        else dBy = (B_of(c, sg[s2 + BW]) - B_of(c, sg[s2 - BW])) * 0.5f;
-        cG[q] = sTt[s2] + 3.f * (qx * uu + qy * vv) - Bc * divq - (dBx * qx + dBy * qy);
-      }
-    }
-    __syncthreads();
-
-    for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
-      const int oy = q / TX_, ox = q - oy * TX_;
-      const int i = x0 + ox, j = y0 + oy;
-      if (i >= nx || j >= ny) continue;
-      const int q1 = (oy + 1) * LX1 + (ox + 1);
-      const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
-      const bool interior = i > 0 && j > 0 && i < nx - 1 && j < ny - 1;
-      float ft[9], gt[9];
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        const int qg = q1 + cxk(k) + cyk(k) * LX1;
-        ft[k] = Pq[k * A1 + qg];
-        if (TH) gt[k] = cG[qg];
-      }
-      float m[9];
-      if (interior) {
-        const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-        const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
-        m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
-        m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
-        m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
-        m[3] = w1 * ax + w5 * dg;
-        m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
-        m[5] = w1 * ay + w5 * dg;
-        const float gm = TH ? sg[s2] : __ldg(a.gamma + (size_t)j * nx + i);
-        const float al = alpha_of(c, gm);
-        const float uu0 = su0[s2], vv0 = sv0[s2];
-        const float ju = c.nu * (cS[q1 - 1] - cS[q1 + 1] + cS[A1 + q1 - LX1] - cS[A1 + q1 + LX1]) + 2.f * al * uu0;
-        const float jv = c.nu * (cS[2 * A1 + q1 - LX1] - cS[2 * A1 + q1 + LX1] + cS[A1 + q1 - 1] - cS[A1 + q1 + 1]) +
-                         2.f * al * vv0;
-        float cpx = 0.f, cpy = 0.f;
+        for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
+        if (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)) {
+          cS[q] = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
+          cS[A1 + q] = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
+          cS[2 * A1 + q] = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
+        } else {
+          cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
+        }
         if (TH) {
-          const float gx = gt[1] + gt[3], gy = gt[2] + gt[4], gd = gt[5] + gt[6] + gt[7] + gt[8];
-          m[6] = w0 * gt[0] + w1 * (gx + gy) + w5 * gd - c.kappa_T;
-          m[7] = w1 * (gt[1] - gt[3]) + w5 * (gt[5] - gt[6] - gt[7] + gt[8]);
-          m[8] = w1 * (gt[2] - gt[4]) + w5 * (gt[5] + gt[6] - gt[7] - gt[8]);
-          const float T0 = sT0[s2];
-          cpx = T0 * m[7];
-          cpy = T0 * m[8];
-        }
-        const float inv = 1.f / (1.f + al);
-        m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
-        m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
-        if (a.sens) {
-          float sacc = 0.f;
-          if (a.sens_flow) {
-            const float da = dalpha_of(c, gm);
-            sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
+          const float* sTt = S + 6 * BOX;
+          const float* sqx = S + 7 * BOX;
+          const float* sqy = S + 8 * BOX;
+          const float qx = sqx[s2], qy = sqy[s2];
+          float divq, dBx, dBy;
+          if (EDGE) {
+            divq = dfdx<float, BW>(sqx, sx, sy, i, nx) + dfdy<float, BW>(sqy, sx, sy, j, ny);
+            dBx = dfdx<float, BW>(sB, sx, sy, i, nx);
+            dBy = dfdy<float, BW>(sB, sx, sy, j, ny);
+          } else {
+            divq = (sqx[s2 + 1] - sqx[s2 - 1]) * 0.5f + (sqy[s2 + BW] - sqy[s2 - BW]) * 0.5f;
+            dBx = (sB[s2 + 1] - sB[s2 - 1]) * 0.5f;
+            dBy = (sB[s2 + BW] - sB[s2 - BW]) * 0.5f;
           }
-          if (TH && a.sens_thermal) {
-            const float dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * 0.5f;
-            const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
-            sacc -= dB_of(c, gm) * (dTx * m[7] + dTy * m[8]);
-          }
-          a.sens[(size_t)j * nx + i] += sacc;
+          cG[q] = sTt[s2] + 3.f * (qx * uu + qy * vv) - sB[s2] * divq - (dBx * qx + dBy * qy);
         }
-      } else {
+      }
+    };
+
+    auto phase_b = [&](auto edge_tag) {
+      constexpr bool EDGE = decltype(edge_tag)::value;
+      for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
+        const int oy = q / TX_, ox = q - oy * TX_;
+        const int i = x0 + ox, j = y0 + oy;
+        if (EDGE && (i >= nx || j >= ny)) continue;
+        const int q1 = (oy + 1) * LX1 + (ox + 1);
+        const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
+        const bool interior = !EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1);
+        float ft[9], gt[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          const int gi = i + cxk(k), gj = j + cyk(k);
-          if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
-            ft[k] = 0.f;
-            gt[k] = 0.f;
-          }
+          const int qg = q1 + cxk(k) + cyk(k) * LX1;
+          ft[k] = Pq[k * A1 + qg];
+          if (TH) gt[k] = cG[qg];
         }
-        float kT = 0.f;
-        if (TH) {
-          int nxo, nyo;
-          node_class(g, i, j, nxo, nyo);
-          const int e = thermal_edge(g, i, j);
-          const bool flux = g.t_kind[e] != 0;
-          const double un = (double)(su0[s2] * (float)nxo + sv0[s2] * (float)nyo);
-          double gd[9];
-#pragma unroll
-          for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
-          const double kap = thermal_edge_solve(nxo, nyo, (double)B_of(c, sg[s2]), flux, un, gd);
-          float T_ = 0.f, qx_ = 0.f, qy_ = 0.f;
+        float m[9];
+        if (interior) {
+          const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+          const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
+          m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
+          m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
+          m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
+          m[3] = w1 * ax + w5 * dg;
+          m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
+          m[5] = w1 * ay + w5 * dg;
+          const float al = sal[s2];
+          const float uu0 = su0[s2], vv0 = sv0[s2];
+          const float ju = c.nu * (cS[q1 - 1] - cS[q1 + 1] + cS[A1 + q1 - LX1] - cS[A1 + q1 + LX1]) + 2.f * al * uu0;
+          const float jv = c.nu * (cS[2 * A1 + q1 - LX1] - cS[2 * A1 + q1 + LX1] + cS[A1 + q1 - 1] - cS[A1 + q1 + 1]) +
+                           2.f * al * vv0;
+          float cpx = 0.f, cpy = 0.f;
+          if (TH) {
+            const float gx = gt[1] + gt[3], gy = gt[2] + gt[4], gd = gt[5] + gt[6] + gt[7] + gt[8];
+            m[6] = w0 * gt[0] + w1 * (gx + gy) + w5 * gd - c.kappa_T;
+            m[7] = w1 * (gt[1] - gt[3]) + w5 * (gt[5] - gt[6] - gt[7] + gt[8]);
+            m[8] = w1 * (gt[2] - gt[4]) + w5 * (gt[5] + gt[6] - gt[7] - gt[8]);
+            const float T0 = sT0[s2];
+            cpx = T0 * m[7];
+            cpy = T0 * m[8];
+          }
+          const float inv = sbi[s2];
+          m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
+          m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
+          if (a.sens) {
+            const float gm = __ldg(a.gamma + (size_t)j * nx + i);
+            float sacc = 0.f;
+            if (a.sens_flow) {
+              const float dd = c.q_alpha + gm;
+              const float da = __fdividef(-c.alpha_bar * c.q_alpha * (1.f + c.q_alpha), dd * dd);
+              sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
+            }
+            if (TH && a.sens_thermal) {
+              const float dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * 0.5f;
+              const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
+              sacc -= dB_of(c, gm) * (dTx * m[7] + dTy * m[8]);
+            }
+            a.sens[(size_t)j * nx + i] += sacc;
+          }
+        } else {
 #pragma unroll
           for (int k = 0; k < 9; ++k) {
-            const float gk = (float)gd[k] * wk<float>(k);
-            T_ += gk;
-            qx_ += (float)cxk(k) * gk;
-            qy_ += (float)cyk(k) * gk;
+            const int gi = i + cxk(k), gj = j + cyk(k);
+            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) {
+              ft[k] = 0.f;
+              gt[k] = 0.f;
+            }
           }
-          m[6] = T_;
-          m[7] = qx_;
-          m[8] = qy_;
-          if (flux) kT = (float)kap * sT0[s2];
-        }
-        const float* M = a.emap + edge_class(g, i, j) * 60;
+          float kT = 0.f;
+          if (TH) {
+            int nxo, nyo;
+            node_class(g, i, j, nxo, nyo);
+            const int e = thermal_edge(g, i, j);
+            const bool flux = g.t_kind[e] != 0;
+            const double un = (double)(su0[s2] * (float)nxo + sv0[s2] * (float)nyo);
+            double gd[9];
 #pragma unroll
-        for (int r = 0; r < 6; ++r) {
-          float acc = 0.f;
+            for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
+            const double kap = thermal_edge_solve(nxo, nyo, (double)sB[s2], flux, un, gd);
+            float T_ = 0.f, qx_ = 0.f, qy_ = 0.f;
 #pragma unroll
-          for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
-          m[r] = acc + M[r * 10 + 9] * kT;
+            for (int k = 0; k < 9; ++k) {
+              const float gk = (float)gd[k] * wk<float>(k);
+              T_ += gk;
+              qx_ += (float)cxk(k) * gk;
+              qy_ += (float)cyk(k) * gk;
+            }
+            m[6] = T_;
+            m[7] = qx_;
+            m[8] = qy_;
+            if (flux) kT = (float)kap * sT0[s2];
+          }
+          const float* M = a.emap + edge_class(g, i, j) * 60;
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
+            m[r] = acc + M[r * 10 + 9] * kT;
+          }
         }
+        const size_t o = (size_t)j * nx + i;
+#pragma unroll
+        for (int f = 0; f < NA; ++f) a.m0[f][o] = m[f];
+        if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
       }
-      const size_t o = (size_t)j * nx + i;
-#pragma unroll
-      for (int f = 0; f < NA; ++f) a.m0[f][o] = m[f];
-      if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
+    };
+
+    if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
+      phase_a(std::false_type{});
+      __syncthreads();
+      phase_b(std::false_type{});
+    } else {
+      phase_a(std::true_type{});
+      __syncthreads();
+      phase_b(std::true_type{});
     }
     __syncthreads();
   }
