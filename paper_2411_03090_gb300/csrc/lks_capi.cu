@@ -582,7 +582,7 @@ EncodeTiledFn encode_fn() {
 }
 
 constexpr int kFwdTX = 64, kFwdTY = 8, kAdjTX = 64, kAdjTY = 8;
-constexpr int kFwdNT = 256, kAdjNT = 512;
+constexpr int kFwdNT = 512, kAdjNT = 512;
 
 bool tma_ok(lks_handle* h) {
   return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
@@ -631,6 +631,16 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
                           TH ? state_ptr<float>(h, src, 3) : nullptr, mat + 2 * h->L.N};
   for (int f = 0; f < NF; ++f)
     if ((st = field_map(h, fsrc[f], BW, BH, &maps.m[f])) != LKS_OK) return st;
+  FwdOutMaps<TH> omaps;
+  {
+    const float* outs[7] = {state_ptr<float>(h, dst, 0), state_ptr<float>(h, dst, 1), state_ptr<float>(h, dst, 2),
+                            TH ? state_ptr<float>(h, dst, 3) : nullptr, tu, tv, tT};
+    int nf = 0;
+    for (int k = 0; k < 7; ++k) {
+      if (!outs[k]) continue;
+      if ((st = field_map(h, outs[k], kFwdTX, kFwdTY, &omaps.m[nf++])) != LKS_OK) return st;
+    }
+  }
   FwdTmaArgs<TH> a;
   a.drho_n = state_ptr<float>(h, dst, 0);
   a.u_n = state_ptr<float>(h, dst, 1);
@@ -651,7 +661,7 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
     CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     h->tma_grid_fwd = persistent_grid(h, kern, kFwdNT, smem, a.ntiles);
   }
-  kern<<<h->tma_grid_fwd, kFwdNT, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  kern<<<h->tma_grid_fwd, kFwdNT, smem, h->stream>>>(maps, omaps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->cur = dst;
   h->t = t_new;
@@ -682,6 +692,9 @@ lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const
     if ((st = field_map(h, extra[q], BW, BH, &maps.m[f++])) != LKS_OK) return st;
   }
   if (f != NF) return fail(h, LKS_ERR_INVALID_ARG, "tensor map count");
+  AdjOutMaps<TH> omaps;
+  for (int q = 0; q < NA; ++q)
+    if ((st = field_map(h, adj_ptr<float>(h, dst, q), kAdjTX, kAdjTY, &omaps.m[q])) != LKS_OK) return st;
   AdjTmaArgs<TH> a;
   for (int q = 0; q < 9; ++q) a.m0[q] = adj_ptr<float>(h, dst, q < NA ? q : 0);
   a.gamma = fld<float>(h, h->L.gamma, 0);
@@ -699,7 +712,7 @@ lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const
     CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     grid = persistent_grid(h, kern, kAdjNT, smem, a.ntiles);
   }
-  kern<<<grid, kAdjNT, smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  kern<<<grid, kAdjNT, smem, h->stream>>>(maps, omaps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->acur = dst;
   h->adj_steps++;

@@ -89,6 +89,15 @@ __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, i
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
       : "memory");
 }
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, int x, int y, const void* src) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%1, %2}], [%3];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y), "r"(smem_u32(src))
+               : "memory");
+}
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read0() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
@@ -114,6 +123,13 @@ __device__ __forceinline__ bool tile_is_interior(int x0, int y0, int tx_, int ty
 // ---------------------------------------------------------------------------------
 // Forward
 // ---------------------------------------------------------------------------------
+// Output tensor maps of the forward kernel (boxes TX x TY, no halo): new drho, u, v
+// (, T), then the trajectory copies u, v (, T) when stored.
+template <bool TH>
+struct FwdOutMaps {
+  CUtensorMap m[TH ? 7 : 5];
+};
+
 template <bool TH>
 struct FwdTmaArgs {
   float* drho_n;
@@ -134,18 +150,22 @@ struct FwdTmaArgs {
 __host__ __device__ constexpr int fwd_tma_nf(bool th) { return th ? 6 : 4; }
 template <bool TH, int TX_, int TY_>
 constexpr int fwd_tma_smem_bytes() {
-  return 2 * fwd_tma_nf(TH) * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 + 384;
+  return 2 * fwd_tma_nf(TH) * (TX_ + 8) * (TY_ + 4) * 4 + (TH ? 18 : 9) * (TX_ + 2) * (TY_ + 2) * 4 +
+         (TH ? 4 : 3) * TX_ * TY_ * 4 + 384;
 }
 
 template <bool TH, int TX_, int TY_, int NT>
 __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ TmaMaps<fwd_tma_nf(TH)> maps,
+                                                     const __grid_constant__ FwdOutMaps<TH> omaps,
                                                      FwdTmaArgs<TH> a, Geom g, Coef<float> c) {
   constexpr int NF = fwd_tma_nf(TH);
+  constexpr int NO = TH ? 4 : 3;
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
   constexpr int LX1 = TX_ + 2, LY1 = TY_ + 2, A1 = LX1 * LY1;
   extern __shared__ unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_base128(smem_raw));  // [2][NF][BOX]
-  float* F = stage + 2 * NF * BOX;                                   // [9][A1]
+  float* sout = stage + 2 * NF * BOX;                                // [NO][TX*TY] output tile
+  float* F = sout + NO * TX_ * TY_;                                  // [9][A1]
   float* Gp = F + 9 * A1;                                            // thermal [9][A1]
   uint64_t* bar = reinterpret_cast<uint64_t*>(Gp + (TH ? 9 * A1 : 0));
   double* red = reinterpret_cast<double*>(bar + 2);                  // NT / 32 doubles
@@ -175,7 +195,10 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     if (threadIdx.x == 0 && tile + (int)gridDim.x < a.ntiles) issue(tile + gridDim.x, st ^ 1);
     if (!mbar_wait(&bar[st], (it >> 1) & 1)) {
       raise_status(a.status, 6);
-      if (threadIdx.x == 0) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+      if (threadIdx.x == 0) {
+        mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+        bulk_wait0();
+      }
       return;
     }
     const float* sdr = stage + (st * NF + 0) * BOX;
@@ -342,20 +365,15 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
             }
           }
         }
-        const size_t o = (size_t)j * nx + i;
-        a.drho_n[o] = drn;
-        a.u_n[o] = un;
-        a.v_n[o] = vn;
-        if (TH) a.T_n[o] = Tn;
-        if (a.traj_u) {
-          a.traj_u[o] = un;
-          a.traj_v[o] = vn;
-          if (TH) a.traj_T[o] = Tn;
-        }
+        sout[q] = drn;
+        sout[TX_ * TY_ + q] = un;
+        sout[2 * TX_ * TY_ + q] = vn;
+        if (TH) sout[3 * TX_ * TY_ + q] = Tn;
         if (bad_velocity(un, vn)) raise_status(a.status, 4);
       }
     };
 
+    if (threadIdx.x == 0) bulk_wait_read0();  // the previous tile's output copies have left sout
     if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
       phase_a(std::false_type{});
       __syncthreads();
@@ -365,8 +383,19 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
       __syncthreads();
       phase_b(std::true_type{});
     }
-    __syncthreads();  // stage st and the push arrays are free again
+    fence_proxy_async();  // make this thread's sout writes visible to the bulk copies
+    __syncthreads();      // stage st and the push arrays are free again; sout complete
+    if (threadIdx.x == 0) {
+      for (int f = 0; f < NO; ++f) tma_store_2d(&omaps.m[f], x0, y0, sout + f * TX_ * TY_);
+      if (a.traj_u) {
+        tma_store_2d(&omaps.m[NO], x0, y0, sout + TX_ * TY_);
+        tma_store_2d(&omaps.m[NO + 1], x0, y0, sout + 2 * TX_ * TY_);
+        if (TH) tma_store_2d(&omaps.m[NO + 2], x0, y0, sout + 3 * TX_ * TY_);
+      }
+      bulk_commit();
+    }
   }
+  if (threadIdx.x == 0) bulk_wait0();
   if (a.J_partial) {
     const double s = block_sum<NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
@@ -376,6 +405,12 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
 // ---------------------------------------------------------------------------------
 // Adjoint
 // ---------------------------------------------------------------------------------
+// Output tensor maps of the adjoint kernel (boxes TX x TY): the 6 (9) moments.
+template <bool TH>
+struct AdjOutMaps {
+  CUtensorMap m[TH ? 9 : 6];
+};
+
 template <bool TH>
 struct AdjTmaArgs {
   float* m0[9];       // adjoint moments at level t
@@ -395,11 +430,12 @@ __host__ __device__ constexpr int adj_tma_nf(bool th, bool same) {
 template <bool TH, bool SAME, int TX_, int TY_>
 constexpr int adj_tma_smem_bytes() {
   return 2 * adj_tma_nf(TH, SAME) * (TX_ + 8) * (TY_ + 4) * 4 + (9 + 3 + (TH ? 1 : 0)) * (TX_ + 2) * (TY_ + 2) * 4 +
-         256;
+         (TH ? 9 : 6) * TX_ * TY_ * 4 + 256;
 }
 
 template <bool TH, bool SAME, int TX_, int TY_, int NT>
 __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ TmaMaps<adj_tma_nf(TH, SAME)> maps,
+                                                     const __grid_constant__ AdjOutMaps<TH> omaps,
                                                      AdjTmaArgs<TH> a, Geom g, Coef<float> c) {
   constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
@@ -410,7 +446,8 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
   constexpr int FAL = SAME ? NA + 2 : NA + 4, FBI = FAL + 1, FT0 = FAL + 2, FB = FAL + 3;
   extern __shared__ unsigned char smem_raw[];
   float* stage = reinterpret_cast<float*>(smem_base128(smem_raw));  // [2][NF][BOX]
-  float* Pq = stage + 2 * NF * BOX;                                  // [9][A1] push values P + c_k.V
+  float* sout = stage + 2 * NF * BOX;                                // [NA][TX*TY] output tile
+  float* Pq = sout + NA * TX_ * TY_;                                 // [9][A1] push values P + c_k.V
   float* cS = Pq + 9 * A1;                                           // [3][A1] strain of the level-t state
   float* cG = cS + 3 * A1;                                           // thermal: G~ on the halo-1 region
   uint64_t* bar = reinterpret_cast<uint64_t*>(cG + (TH ? A1 : 0));
@@ -439,7 +476,10 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
     if (threadIdx.x == 0 && tile + (int)gridDim.x < a.ntiles) issue(tile + gridDim.x, st ^ 1);
     if (!mbar_wait(&bar[st], (it >> 1) & 1)) {
       raise_status(a.status, 6);
-      if (threadIdx.x == 0) mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+      if (threadIdx.x == 0) {
+        mbar_wait(&bar[st ^ 1], ((it + 1) >> 1) & 1);
+        bulk_wait0();
+      }
       return;
     }
     const float* S = stage + st * NF * BOX;
@@ -614,13 +654,13 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             m[r] = acc + M[r * 10 + 9] * kT;
           }
         }
-        const size_t o = (size_t)j * nx + i;
 #pragma unroll
-        for (int f = 0; f < NA; ++f) a.m0[f][o] = m[f];
+        for (int f = 0; f < NA; ++f) sout[f * TX_ * TY_ + q] = m[f];
         if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
       }
     };
 
+    if (threadIdx.x == 0) bulk_wait_read0();  // the previous tile's output copies have left sout
     if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
       phase_a(std::false_type{});
       __syncthreads();
@@ -630,8 +670,14 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
       __syncthreads();
       phase_b(std::true_type{});
     }
+    fence_proxy_async();
     __syncthreads();
+    if (threadIdx.x == 0) {
+      for (int f = 0; f < NA; ++f) tma_store_2d(&omaps.m[f], x0, y0, sout + f * TX_ * TY_);
+      bulk_commit();
+    }
   }
+  if (threadIdx.x == 0) bulk_wait0();
 }
 
 }  // namespace lks
