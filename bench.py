@@ -160,6 +160,71 @@ def run_reference(args):
                                      "d2h_bytes_per_step": 0}}))
 
 
+def run_checkpoint_study(args):
+    """Unsteady thermal config3 (1024x512, 20000 steps): the plain FP32 form (every
+    level of u, v, T kept) against recomputation checkpoints every K steps with
+    FP32 / BF16 / FP16 snapshots; seconds per gradient, device memory and gradient
+    error relative to the plain form.  One JSON line, metric of the checkpointed
+    BF16 form with K = 100."""
+    import torch
+    from paper_2411_03090_gb300 import LKS
+
+    pb = inputs.config3()
+    if args.steps_override:
+        pb = pb.with_(n_steps=args.steps_override)
+    dev = torch.device("cuda", 0)
+    gamma = torch.from_numpy(pb.gamma()).to(dev, torch.float32)
+    N = pb.n_nodes
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def timed(s, reps):
+        s.gradient(gamma)  # warm-up
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(reps):
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            J, g = s.gradient(gamma)
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        return min(ts), J.item(), g.double()
+
+    reps = max(1, min(args.steps, 2))
+    rows = []
+    plain = LKS(pb, real="f32", checkpoint_every=0, device=dev)
+    t_plain, J_plain, g_plain = timed(plain, reps)
+    ws_plain = plain.workspace.numel()
+    rows.append({"form": "plain FP32 trajectory", "K": 0, "snapshot": "-", "s_per_gradient": t_plain,
+                 "workspace_GB": ws_plain / 1e9, "grad_rel_err_vs_plain": 0.0, "J": J_plain})
+    del plain
+    torch.cuda.empty_cache()
+    norm = torch.linalg.vector_norm(g_plain).item()
+    for K in (100, 500, 2000):
+        for snap in ("f32", "bf16", "f16"):
+            s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap, device=dev)
+            t, J, g = timed(s, reps)
+            err = torch.linalg.vector_norm(g - g_plain).item() / norm
+            rows.append({"form": "checkpointed", "K": K, "snapshot": snap, "s_per_gradient": t,
+                         "workspace_GB": s.workspace.numel() / 1e9, "grad_rel_err_vs_plain": err, "J": J})
+            del s
+            torch.cuda.empty_cache()
+    head = [r for r in rows if r["K"] == 100 and r["snapshot"] == "bf16"][0]
+    updates = N * pb.n_steps * 3  # forward + recomputed forward + adjoint per level
+    print(json.dumps({
+        "metric": METRIC, "value": N * 2 * pb.n_steps / head["s_per_gradient"] / 1e6, "unit": "MLUPS",
+        "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": head["s_per_gradient"] * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"config3: 1024x512 unsteady thermal channel, Re=200, Pr=0.71, pulsed inlet, "
+                               f"{pb.n_steps} steps; headline = checkpoints every 100 steps, BF16 snapshots",
+                   "updates_counted": "forward + adjoint levels (recomputation not counted)",
+                   "l2": "flushed before each timed gradient"},
+        "checkpoint_study": rows,
+        "speedup_vs_plain": t_plain / head["s_per_gradient"],
+        "memory_ratio_vs_plain": head["workspace_GB"] / (ws_plain / 1e9)}))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -169,9 +234,13 @@ def main():
     ap.add_argument("--workload", default="config2")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--steps-override", type=int, default=0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.workload == "config3":
+        run_checkpoint_study(args)
         return
 
     import torch

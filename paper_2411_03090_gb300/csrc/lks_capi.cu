@@ -582,7 +582,7 @@ EncodeTiledFn encode_fn() {
 }
 
 constexpr int kFwdTX = 64, kFwdTY = 8, kAdjTX = 64, kAdjTY = 8;
-constexpr int kFwdNT = 512, kAdjNT = 512;
+constexpr int kFwdNT = 256, kAdjNT = 512;
 
 bool tma_ok(lks_handle* h) {
   return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
