@@ -411,67 +411,106 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
 // residual r_i = (n.c_i) g~_i - B sum_j w_j (n.c_j) g~_j + m_i with the multiplier
 // column m = 1 (prescribed T) or m = c.n - u.n (prescribed flux); the g~_i whose
 // gather point is off the lattice and the multiplier minimise ||r||_2 over the nine
-// rows (normal equations in double; unknown links with c.n = 0 do not enter the
-// residual and are set to zero).  g[] holds the known values (zeros elsewhere) on
-// entry and all nine on exit; returns the multiplier.
-__device__ __forceinline__ double thermal_edge_solve(int n_x, int n_y, double B, bool flux, double un,
-                                                     double* g) {
-  constexpr int cx_[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
-  constexpr int cy_[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
-  constexpr double w_[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
-  int live[5];
-  int nl = 0;
-  double sknown = 0.0;  // sum_j w_j (n.c_j) g_j over known j
+// rows (unknown links with c.n = 0 do not enter the residual and are set to zero).
+// For every edge or corner normal exactly three unknown links have c.n != 0, so the
+// normal equations are a 4x4 Gram system, symmetric positive definite: Gauss-Jordan
+// elimination without pivoting is stable on it.  The normal is a template parameter so
+// that the link sets are compile-time constants and the whole solve stays in registers
+// (the double-precision pipe of this part is a small fraction of the FP32 one, so the
+// solve runs in the kernel's own precision).  g[] holds the known values (zeros
+// elsewhere) on entry and all nine on exit; returns the multiplier.
+template <int NX, int NY>
+struct EdgeLinks {
+  __host__ __device__ static constexpr int cx(int k) { return k == 1 || k == 5 || k == 8 ? 1 : (k == 3 || k == 6 || k == 7 ? -1 : 0); }
+  __host__ __device__ static constexpr int cy(int k) { return k == 2 || k == 5 || k == 6 ? 1 : (k == 4 || k == 7 || k == 8 ? -1 : 0); }
+  __host__ __device__ static constexpr int cn(int k) { return cx(k) * NX + cy(k) * NY; }
+  __host__ __device__ static constexpr bool unknown(int k) { return cx(k) * NX > 0 || cy(k) * NY > 0; }
+  __host__ __device__ static constexpr int live(int a) {
+    int n = 0;
+    for (int k = 0; k < 9; ++k)
+      if (unknown(k) && cn(k) != 0) {
+        if (n == a) return k;
+        ++n;
+      }
+    return -1;
+  }
+  __host__ __device__ static constexpr int nlive() {
+    int n = 0;
+    for (int k = 0; k < 9; ++k)
+      if (unknown(k) && cn(k) != 0) ++n;
+    return n;
+  }
+};
+
+template <typename T, int NX, int NY>
+__device__ __forceinline__ T thermal_edge_solve_n(T B, bool flux, T un, T* g) {
+  using L = EdgeLinks<NX, NY>;
+  constexpr int NL = 3, NC = 4;
+  static_assert(L::nlive() == NL, "three unknown links with c.n != 0 on every edge normal");
+  T sknown = T(0);  // sum_j w_j (n.c_j) g_j over known j
 #pragma unroll
   for (int k = 0; k < 9; ++k) {
-    const int cn = cx_[k] * n_x + cy_[k] * n_y;
-    const bool unk = (cx_[k] * n_x > 0) || (cy_[k] * n_y > 0);
-    if (unk) {
-      g[k] = 0.0;
-      if (cn != 0 && nl < 4) live[nl++] = k;
-    } else {
-      sknown += w_[k] * cn * g[k];
-    }
+    if (L::unknown(k))
+      g[k] = T(0);
+    else if (L::cn(k) != 0)
+      sknown += wk<T>(k) * T(L::cn(k)) * g[k];
   }
-  const int nc = nl + 1;
-  double G[5][6];
-  for (int a = 0; a < nc; ++a)
-    for (int b = 0; b <= nc; ++b) G[a][b] = 0.0;
+  T G[NC][NC + 1];
+#pragma unroll
+  for (int a = 0; a < NC; ++a)
+#pragma unroll
+    for (int b = 0; b <= NC; ++b) G[a][b] = T(0);
 #pragma unroll
   for (int r = 0; r < 9; ++r) {
-    const int cnr = cx_[r] * n_x + cy_[r] * n_y;
-    const bool unk_r = (cx_[r] * n_x > 0) || (cy_[r] * n_y > 0);
-    double col[5];
-    for (int a = 0; a < nl; ++a) {
-      const int u = live[a];
-      const int cnu = cx_[u] * n_x + cy_[u] * n_y;
-      col[a] = (r == u ? (double)cnu : 0.0) - B * w_[u] * cnu;
+    T col[NC];
+#pragma unroll
+    for (int a = 0; a < NL; ++a) {
+      const int u = L::live(a);
+      col[a] = (r == u ? T(L::cn(u)) : T(0)) - B * wk<T>(u) * T(L::cn(u));
     }
-    col[nl] = flux ? ((double)cnr - un) : 1.0;
-    const double rhs = -((unk_r ? 0.0 : cnr * g[r]) - B * sknown);
-    for (int a = 0; a < nc; ++a) {
-      for (int b = 0; b < nc; ++b) G[a][b] += col[a] * col[b];
-      G[a][nc] += col[a] * rhs;
+    col[NL] = flux ? (T(L::cn(r)) - un) : T(1);
+    const T rhs = B * sknown - (L::unknown(r) ? T(0) : T(L::cn(r)) * g[r]);
+#pragma unroll
+    for (int a = 0; a < NC; ++a) {
+#pragma unroll
+      for (int b = a; b < NC; ++b) G[a][b] += col[a] * col[b];
+      G[a][NC] += col[a] * rhs;
     }
   }
-  for (int cc = 0; cc < nc; ++cc) {
-    int p = cc;
-    for (int r = cc + 1; r < nc; ++r)
-      if (fabs(G[r][cc]) > fabs(G[p][cc])) p = r;
-    if (p != cc)
-      for (int q = 0; q <= nc; ++q) {
-        const double t = G[cc][q];
-        G[cc][q] = G[p][q];
-        G[p][q] = t;
-      }
-    for (int r = 0; r < nc; ++r) {
+#pragma unroll
+  for (int a = 1; a < NC; ++a)
+#pragma unroll
+    for (int b = 0; b < a; ++b) G[a][b] = G[b][a];
+  T inv[NC];
+#pragma unroll
+  for (int cc = 0; cc < NC; ++cc) {
+    inv[cc] = T(1) / G[cc][cc];
+#pragma unroll
+    for (int r = 0; r < NC; ++r) {
       if (r == cc) continue;
-      const double f = G[r][cc] / G[cc][cc];
-      for (int q = cc; q <= nc; ++q) G[r][q] -= f * G[cc][q];
+      const T f = G[r][cc] * inv[cc];
+#pragma unroll
+      for (int q = cc; q <= NC; ++q) G[r][q] -= f * G[cc][q];
     }
   }
-  for (int a = 0; a < nl; ++a) g[live[a]] = G[a][nc] / G[a][a];
-  return G[nl][nc] / G[nl][nl];
+#pragma unroll
+  for (int a = 0; a < NL; ++a) g[L::live(a)] = G[a][NC] * inv[a];
+  return G[NL][NC] * inv[NL];
+}
+
+template <typename T>
+__device__ __forceinline__ T thermal_edge_solve(int n_x, int n_y, T B, bool flux, T un, T* g) {
+  switch ((n_x + 1) * 3 + (n_y + 1)) {
+    case 0: return thermal_edge_solve_n<T, -1, -1>(B, flux, un, g);
+    case 1: return thermal_edge_solve_n<T, -1, 0>(B, flux, un, g);
+    case 2: return thermal_edge_solve_n<T, -1, 1>(B, flux, un, g);
+    case 3: return thermal_edge_solve_n<T, 0, -1>(B, flux, un, g);
+    case 5: return thermal_edge_solve_n<T, 0, 1>(B, flux, un, g);
+    case 6: return thermal_edge_solve_n<T, 1, -1>(B, flux, un, g);
+    case 7: return thermal_edge_solve_n<T, 1, 0>(B, flux, un, g);
+    case 8: return thermal_edge_solve_n<T, 1, 1>(B, flux, un, g);
+    default: return T(0);  // interior nodes have no edge rule
+  }
 }
 
 // =====================================================================================
@@ -668,17 +707,13 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
         node_class(g, i, j, nxo, nyo);
         const int e = thermal_edge(g, i, j);
         const bool flux = g.t_kind[e] != 0;
-        const double un = (double)(su0[s2] * R(nxo) + sv0[s2] * R(nyo));
-        double gd[9];
-#pragma unroll
-        for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
-        const double kap = thermal_edge_solve(nxo, nyo, (double)B_of(c, __ldg(a.gamma + (size_t)j * nx + i)),
-                                              flux, un, gd);
+        const R un = su0[s2] * R(nxo) + sv0[s2] * R(nyo);
+        const R kap = thermal_edge_solve<R>(nxo, nyo, B_of(c, __ldg(a.gamma + (size_t)j * nx + i)), flux, un, gt);
         R T_, qx_, qy_;
         T_ = qx_ = qy_ = R(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
-          const R gk = (R)gd[k] * wk<R>(k);
+          const R gk = gt[k] * wk<R>(k);
           T_ += gk;
           qx_ += R(cxk(k)) * gk;
           qy_ += R(cyk(k)) * gk;
@@ -686,7 +721,7 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
         m[6] = T_;
         m[7] = qx_;
         m[8] = qy_;
-        if (flux) kT = (R)kap * sT0[s2];
+        if (flux) kT = kap * sT0[s2];
       }
       const R* M = a.emap + ec * 60;
 #pragma unroll

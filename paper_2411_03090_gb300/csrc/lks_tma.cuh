@@ -627,15 +627,12 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             node_class(g, i, j, nxo, nyo);
             const int e = thermal_edge(g, i, j);
             const bool flux = g.t_kind[e] != 0;
-            const double un = (double)(su0[s2] * (float)nxo + sv0[s2] * (float)nyo);
-            double gd[9];
-#pragma unroll
-            for (int k = 0; k < 9; ++k) gd[k] = (double)gt[k];
-            const double kap = thermal_edge_solve(nxo, nyo, (double)sB[s2], flux, un, gd);
+            const float un = su0[s2] * (float)nxo + sv0[s2] * (float)nyo;
+            const float kap = thermal_edge_solve<float>(nxo, nyo, sB[s2], flux, un, gt);
             float T_ = 0.f, qx_ = 0.f, qy_ = 0.f;
 #pragma unroll
             for (int k = 0; k < 9; ++k) {
-              const float gk = (float)gd[k] * wk<float>(k);
+              const float gk = gt[k] * wk<float>(k);
               T_ += gk;
               qx_ += (float)cxk(k) * gk;
               qy_ += (float)cyk(k) * gk;
@@ -643,7 +640,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             m[6] = T_;
             m[7] = qx_;
             m[8] = qy_;
-            if (flux) kT = (float)kap * sT0[s2];
+            if (flux) kT = kap * sT0[s2];
           }
           const float* M = a.emap + edge_class(g, i, j) * 60;
 #pragma unroll
