@@ -219,6 +219,82 @@ lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_
  * afboundaryuq, afboundarypq). */
 lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
 
+/* ---------------------------------------------------------------------------------
+ * Batched form: many designs (load cases, optimiser candidates) of unequal lattice
+ * size marched in lock step.  One persistent launch per time step covers every
+ * tile of every design, and the whole gradient (Steps 2-5 of Sec. 2.7 for all
+ * designs: forward march with checkpoints, objective, checkpointed adjoint with
+ * segment recomputation, sensitivity) is one CUDA graph launch.  The paper runs one
+ * design at a time; this is the same per-node computation as lks_forward +
+ * alks_adjoint + lks_sensitivity of an unsteady FP32 problem with
+ * checkpoint_every = K, applied to each design.
+ *
+ * Scope: unsteady, non-thermal, FP32 designs that share n_steps.  Each descriptor
+ * passes the lks_create checks; its checkpoint_every, snapshot_type and exec_path
+ * are ignored (the batch options rule).  nx need not be a multiple of 4.
+ *
+ * Layout: the designs' lattices are packed side by side into one arena per field
+ * (shelf packing of rectangles whose extents are rounded up to 128 x 16 nodes), so
+ * a single tensor map per field serves every design; a work list names each
+ * (design, tile) pair.  The tile shape is one of LKS_BATCH_TILE_CONFIGS fixed
+ * shapes, picked by timing each on the batch at lks_batch_create (tile_config = -1)
+ * or given.  K = 0 picks the checkpoint spacing that minimises workspace bytes
+ * (snapshots + segment buffer), a pure function of the descriptors.
+ * --------------------------------------------------------------------------------- */
+#define LKS_BATCH_VERSION 1
+#define LKS_BATCH_TILE_CONFIGS 4
+typedef struct lks_batch lks_batch;
+
+typedef struct {
+  int32_t version;          /* LKS_BATCH_VERSION */
+  int32_t checkpoint_every; /* K >= 1, or 0: memory-optimal K */
+  int32_t snapshot_type;    /* lks_snap_type of the checkpoints (per design and field max-abs scale) */
+  int32_t tile_config;      /* -1: autotune at create; else 0 .. LKS_BATCH_TILE_CONFIGS - 1:
+                               0 = 64x8, 1 = 32x16, 2 = 128x4, 3 = 64x16 output nodes per tile */
+  int32_t use_graph;        /* 1: each gradient is one CUDA graph launch; 0: direct launches */
+  int32_t reserved[7];      /* must be zero */
+} lks_batch_options;
+
+typedef struct {
+  int32_t n_designs;
+  int32_t tile_config;      /* the shape in use */
+  int32_t checkpoint_every; /* K in use */
+  int32_t n_ckpt;
+  int32_t arena_w, arena_h; /* arena extent in nodes */
+  int32_t graph;            /* 1 when a gradient is one graph launch */
+  int32_t device_status;    /* lks_status the kernels recorded (0 = none) */
+  int64_t nodes;            /* sum of nx * ny over the designs */
+  int64_t ntiles;           /* work-list length at the tile shape in use */
+  int64_t workspace_bytes;
+  int64_t kernel_launches;  /* kernels one gradient launches (inside the graph when used) */
+  int64_t gradients;        /* gradients computed so far */
+  float tune_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward + adjoint step of each shape (0: not timed) */
+} lks_batch_stats;
+
+/* Host only.  n designs described by descs[0..n-1]; opt as above (NULL: K = 0,
+ * BF16 snapshots, autotuned tile, graph).  *bytes: device workspace to pass to
+ * lks_batch_create. */
+lks_status lks_batch_workspace_size(int32_t n, const lks_problem_desc *descs, const lks_batch_options *opt,
+                                    size_t *bytes);
+/* Lays out the arena and the work lists, uploads per-design tables, autotunes the
+ * tile shape when asked (running short marches on a uniform design) and captures
+ * the gradient graph.  workspace: caller-owned device memory of at least the size
+ * above, 256-byte aligned; never freed by the library.  Synchronises the stream. */
+lks_status lks_batch_create(int32_t n, const lks_problem_desc *descs, const lks_batch_options *opt,
+                            void *workspace, size_t bytes, void *cuda_stream, lks_batch **out);
+/* All designs' gradients.  gamma_dev: host array of n device pointers to each
+ * design's gamma (ny x nx FP32, row-major, read only).  J_dev: device array of n
+ * doubles (objective of each design).  dJdgamma_dev: host array of n device
+ * pointers (ny x nx FP32, written).  Stream-ordered: returns after enqueueing; the
+ * host arrays may be reused at once.  Device-detected errors (instability, a
+ * timed-out wait) are reported by lks_batch_query. */
+lks_status lks_batch_gradient(lks_batch *b, const float *const *gamma_dev, double *J_dev,
+                              float *const *dJdgamma_dev);
+/* Synchronises the stream and fills *out. */
+lks_status lks_batch_query(lks_batch *b, lks_batch_stats *out);
+lks_status lks_batch_destroy(lks_batch *b);
+const char *lks_batch_last_error(const lks_batch *b);
+
 #ifdef __cplusplus
 }
 #endif

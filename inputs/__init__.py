@@ -143,6 +143,26 @@ def config3() -> Problem:
     return p
 
 
+def config5(n_designs: int = 64, n_steps: int = 5000) -> List[Problem]:
+    """Batch of unsteady channel designs of unequal size.  Sizes and Reynolds
+    numbers come from one generator seeded 5, drawn design by design as
+    (nx ~ U{128..512}, ny ~ U{64..256}, Re ~ U[20, 200]); nu = min(0.05 L / Re, 0.30)
+    with L = ny - 1 (the clamp keeps nu inside the stable range of the scheme) and
+    u_max = Re nu / L; pulsed inlet as config3; design k's gamma uses seed 500 + k."""
+    rng = np.random.default_rng(5)
+    out = []
+    for k in range(n_designs):
+        nx = int(rng.integers(128, 513))
+        ny = int(rng.integers(64, 257))
+        Re = float(rng.uniform(20.0, 200.0))
+        L = ny - 1
+        nu = min(0.05 * L / Re, 0.30)
+        out.append(Problem(nx=nx, ny=ny, nu=nu, alpha_bar=1e3 * nu, u_max=Re * nu / L, steady=False,
+                           n_steps=n_steps, n_adj=n_steps, pulse_mean=0.75, pulse_amp=0.25,
+                           pulse_period=2000.0, seed=500 + k))
+    return out
+
+
 def roofline2d(n: int = 8192) -> Problem:
     """Large 2-D steady channel used to load HBM (working set >> L2)."""
     return channel(n, n, Re=100.0 * (n - 1) / 255.0, seed=6, n_steps=200, n_adj=200)

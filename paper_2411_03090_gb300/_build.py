@@ -10,8 +10,9 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "liblks.so")
-SOURCES = [os.path.join(CSRC, "lks_capi.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, "lks_kernels.cuh"), os.path.join(ROOT, "include", "lks.h")]
+SOURCES = [os.path.join(CSRC, "lks_capi.cu"), os.path.join(CSRC, "lks_batch.cu")]
+DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("lks_kernels.cuh", "lks_resident.cuh", "lks_tma.cuh",
+                                                   "lks_host.cuh")] + [os.path.join(ROOT, "include", "lks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
@@ -30,11 +31,26 @@ def build(force: bool = False, verbose: bool = False) -> str:
             return LIB
         os.makedirs(LIB_DIR, exist_ok=True)
         nvcc = os.environ.get("NVCC", "nvcc")
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-shared",
-               "-o", tmp, *SOURCES]
-        if verbose:
-            print(" ".join(cmd))
-        subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
+        tag = f".tmp{os.getpid()}"
+        objs = [os.path.join(LIB_DIR, os.path.basename(src) + tag + ".o") for src in SOURCES]
+        procs = []
+        for src, obj in zip(SOURCES, objs):  # translation units compile in parallel
+            cmd = [nvcc, *ARCH, "-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-c", "-o", obj, src]
+            if verbose:
+                print(" ".join(cmd))
+            procs.append((cmd, subprocess.Popen(cmd)))
+        failed = [cmd for cmd, p in procs if p.wait() != 0]
+        try:
+            if failed:
+                raise subprocess.CalledProcessError(1, failed[0])
+            tmp = LIB + tag
+            cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
+            if verbose:
+                print(" ".join(cmd))
+            subprocess.run(cmd, check=True)
+            os.replace(tmp, LIB)
+        finally:
+            for obj in objs:
+                if os.path.exists(obj):
+                    os.remove(obj)
         return LIB

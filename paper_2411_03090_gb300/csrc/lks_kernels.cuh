@@ -775,7 +775,7 @@ __global__ void __launch_bounds__(NTHREADS) objective_kernel(const R* __restrict
 }
 
 // Deterministic sum of n partials (one block) plus an optional second array.
-__global__ void reduce_partials_kernel(const double* __restrict__ p, int n, const double* __restrict__ p2,
+static __global__ void reduce_partials_kernel(const double* __restrict__ p, int n, const double* __restrict__ p2,
                                        int n2, double* out) {
   __shared__ double red[NTHREADS / 32];
   double acc = 0.0;

@@ -103,7 +103,7 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 
 // Material fields of one march: 1 / (1 + alpha_gamma), alpha_gamma (Eq. brinkman)
 // and B_gamma (Eqs. conductivity, B), one float each per node.
-__global__ void material_kernel(const float* __restrict__ gamma, size_t n, Coef<float> c, float* __restrict__ binv,
+static __global__ void material_kernel(const float* __restrict__ gamma, size_t n, Coef<float> c, float* __restrict__ binv,
                                 float* __restrict__ alpha, float* __restrict__ B) {
   for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
     const float gm = gamma[o];
@@ -119,6 +119,75 @@ __global__ void material_kernel(const float* __restrict__ gamma, size_t n, Coef<
 __device__ __forceinline__ bool tile_is_interior(int x0, int y0, int tx_, int ty_, int nx, int ny) {
   return x0 >= 2 && y0 >= 2 && x0 + tx_ + 2 <= nx && y0 + ty_ + 2 <= ny;
 }
+
+// ---------------------------------------------------------------------------------
+// Batched form: several lattices of unequal size packed into one arena (one 2-D
+// array per field, row pitch `pitch`).  Each design owns a rectangle of the arena
+// whose origin and extent are multiples of the tile shape, so the tensor maps of the
+// arena serve every design and a tile's output box never leaves its design's
+// rectangle.  A work list names every (design, tile) pair; each CTA walks it with the
+// same static stride as the single-lattice kernels.  The per-node arithmetic is that
+// of the single-lattice form, with the design's own geometry and coefficients.
+// ---------------------------------------------------------------------------------
+struct BatchDesign {
+  Geom g;
+  Coef<float> c;
+  int ax, ay;  // arena origin of the design's node (0, 0)
+};
+struct __align__(16) BatchTile {
+  int d;         // design index
+  int x0, y0;    // tile origin in the design's lattice
+  int interior;  // 1 when the tile's two-node halo lies inside the lattice
+};
+
+// Arena coordinates of a tile's output origin.
+template <bool BATCH, int TX_, int TY_>
+__device__ __forceinline__ void tile_arena_origin(int tile, int ntx, const BatchTile* work,
+                                                  const BatchDesign* designs, int& gx, int& gy) {
+  if constexpr (BATCH) {
+    const BatchTile w = work[tile];
+    gx = designs[w.d].ax + w.x0;
+    gy = designs[w.d].ay + w.y0;
+  } else {
+    gx = (tile % ntx) * TX_;
+    gy = (tile / ntx) * TY_;
+  }
+}
+
+// Everything a CTA needs to know about the tile it works on.
+// Geometry and coefficients are read in place (kernel parameters of the single-lattice
+// form, the design table of the batched form), never copied to local memory.
+template <bool BATCH>
+struct TileCtx {
+  const Geom* g;
+  const Coef<float>* c;
+  int d, x0, y0, gx, gy;  // design, origin in the design's lattice, origin in the arena
+  bool interior;
+  __device__ __forceinline__ TileCtx(int tile, int ntx, int tx_, int ty_, const BatchTile* work,
+                                     const BatchDesign* designs, const Geom& g0, const Coef<float>& c0) {
+    if constexpr (BATCH) {
+      const BatchTile w = work[tile];
+      const BatchDesign& bd = designs[w.d];
+      g = &bd.g;
+      c = &bd.c;
+      d = w.d;
+      x0 = w.x0;
+      y0 = w.y0;
+      gx = bd.ax + x0;
+      gy = bd.ay + y0;
+      interior = w.interior != 0;
+    } else {
+      g = &g0;
+      c = &c0;
+      d = 0;
+      x0 = (tile % ntx) * tx_;
+      y0 = (tile / ntx) * ty_;
+      gx = x0;
+      gy = y0;
+      interior = tile_is_interior(x0, y0, tx_, ty_, g0.nx, g0.ny);
+    }
+  }
+};
 
 // ---------------------------------------------------------------------------------
 // Forward
@@ -144,6 +213,10 @@ struct FwdTmaArgs {
   float* traj_v;
   float* traj_T;
   int ntx, ntiles;
+  // batched form only
+  const BatchTile* work;
+  const BatchDesign* designs;
+  const float* u_in_d;  // inlet amplitude of each design at the new level
 };
 
 // fields staged per stage: drho, u, v, 1/(1+alpha) (, T, B)
@@ -154,10 +227,11 @@ constexpr int fwd_tma_smem_bytes() {
          (TH ? 4 : 3) * TX_ * TY_ * 4 + 384;
 }
 
-template <bool TH, int TX_, int TY_, int NT>
+template <bool TH, bool BATCH, int TX_, int TY_, int NT>
 __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ TmaMaps<fwd_tma_nf(TH)> maps,
                                                      const __grid_constant__ FwdOutMaps<TH> omaps,
-                                                     FwdTmaArgs<TH> a, Geom g, Coef<float> c) {
+                                                     FwdTmaArgs<TH> a, const __grid_constant__ Geom g0,
+                                                     const __grid_constant__ Coef<float> c0) {
   constexpr int NF = fwd_tma_nf(TH);
   constexpr int NO = TH ? 4 : 3;
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
@@ -172,12 +246,12 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
 
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(stage, bar, a.status)) return;
-  const int nx = g.nx, ny = g.ny;
   auto issue = [&](int tile, int st) {
-    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    int gx, gy;
+    tile_arena_origin<BATCH, TX_, TY_>(tile, a.ntx, a.work, a.designs, gx, gy);
     mbar_expect_tx(&bar[st], NF * BOX * 4);
     for (int f = 0; f < NF; ++f)
-      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], tx * TX_ - TMA_BXPAD, ty * TY_ - 2, &bar[st]);
+      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], gx - TMA_BXPAD, gy - 2, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -207,8 +281,11 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     const float* sbi = stage + (st * NF + 3) * BOX;  // 1 / (1 + alpha)
     const float* sT = stage + (st * NF + 4) * BOX;   // thermal
     const float* sB = stage + (st * NF + 5) * BOX;   // thermal
-    const int tx = tile % a.ntx, ty = tile / a.ntx;
-    const int x0 = tx * TX_, y0 = ty * TY_;
+    TileCtx<BATCH> tc(tile, a.ntx, TX_, TY_, a.work, a.designs, g0, c0);
+    const Geom& g = *tc.g;
+    const Coef<float>& c = *tc.c;
+    const int nx = g.nx, ny = g.ny, x0 = tc.x0, y0 = tc.y0;
+    const float u_in = BATCH ? a.u_in_d[tc.d] : a.u_in;
 
     // push values on the halo-1 region
     auto phase_a = [&](auto edge_tag) {
@@ -298,7 +375,11 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
       for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
         const int oy = q / TX_, ox = q - oy * TX_;
         const int i = x0 + ox, j = y0 + oy;
-        if (EDGE && (i >= nx || j >= ny)) continue;
+        if (EDGE && (i >= nx || j >= ny)) {  // outside the lattice: the output box carries zeros
+#pragma unroll
+          for (int f = 0; f < NO; ++f) sout[f * TX_ * TY_ + q] = 0.f;
+          continue;
+        }
         const int q1 = (oy + 1) * LX1 + (ox + 1);
         const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
         int nxo = 0, nyo = 0;
@@ -343,7 +424,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
             un = 0.f;
             if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
               const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
-              un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
+              un = u_in * (float)(4.0 * y * (H - y) / (H * H));
             }
             vn = 0.f;
             drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
@@ -374,7 +455,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     };
 
     if (threadIdx.x == 0) bulk_wait_read0();  // the previous tile's output copies have left sout
-    if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
+    if (tc.interior) {
       phase_a(std::false_type{});
       __syncthreads();
       phase_b(std::false_type{});
@@ -386,17 +467,22 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
     fence_proxy_async();  // make this thread's sout writes visible to the bulk copies
     __syncthreads();      // stage st and the push arrays are free again; sout complete
     if (threadIdx.x == 0) {
-      for (int f = 0; f < NO; ++f) tma_store_2d(&omaps.m[f], x0, y0, sout + f * TX_ * TY_);
+      for (int f = 0; f < NO; ++f) tma_store_2d(&omaps.m[f], tc.gx, tc.gy, sout + f * TX_ * TY_);
       if (a.traj_u) {
-        tma_store_2d(&omaps.m[NO], x0, y0, sout + TX_ * TY_);
-        tma_store_2d(&omaps.m[NO + 1], x0, y0, sout + 2 * TX_ * TY_);
-        if (TH) tma_store_2d(&omaps.m[NO + 2], x0, y0, sout + 3 * TX_ * TY_);
+        tma_store_2d(&omaps.m[NO], tc.gx, tc.gy, sout + TX_ * TY_);
+        tma_store_2d(&omaps.m[NO + 1], tc.gx, tc.gy, sout + 2 * TX_ * TY_);
+        if (TH) tma_store_2d(&omaps.m[NO + 2], tc.gx, tc.gy, sout + 3 * TX_ * TY_);
       }
       bulk_commit();
     }
+    if (BATCH && a.J_partial) {  // per-tile objective partial (each tile has one owner CTA)
+      const double s = block_sum<NT>(jloc, red);
+      if (threadIdx.x == 0) a.J_partial[tile] += s;
+      jloc = 0.0;
+    }
   }
   if (threadIdx.x == 0) bulk_wait0();
-  if (a.J_partial) {
+  if (!BATCH && a.J_partial) {
     const double s = block_sum<NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
   }
@@ -420,6 +506,11 @@ struct AdjTmaArgs {
   int sens_flow, sens_thermal;
   int* status;
   int ntx, ntiles;
+  // batched form only (gamma, sens and emap then cover every design: gamma and sens
+  // with row pitch `pitch` in arena coordinates, emap with 9 x 60 entries per design)
+  const BatchTile* work;
+  const BatchDesign* designs;
+  int pitch;
 };
 
 // Staged fields: 6 adjoint (+3 thermal), u1, v1, [u0, v0], alpha, 1/(1+alpha),
@@ -433,10 +524,11 @@ constexpr int adj_tma_smem_bytes() {
          (TH ? 9 : 6) * TX_ * TY_ * 4 + 256;
 }
 
-template <bool TH, bool SAME, int TX_, int TY_, int NT>
+template <bool TH, bool SAME, bool BATCH, int TX_, int TY_, int NT>
 __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ TmaMaps<adj_tma_nf(TH, SAME)> maps,
                                                      const __grid_constant__ AdjOutMaps<TH> omaps,
-                                                     AdjTmaArgs<TH> a, Geom g, Coef<float> c) {
+                                                     AdjTmaArgs<TH> a, const __grid_constant__ Geom g0,
+                                                     const __grid_constant__ Coef<float> c0) {
   constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
   constexpr int BW = TX_ + 8, BH = TY_ + 4, BOX = BW * BH;
@@ -454,12 +546,12 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
 
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(stage, bar, a.status)) return;
-  const int nx = g.nx, ny = g.ny;
   auto issue = [&](int tile, int st) {
-    const int tx = tile % a.ntx, ty = tile / a.ntx;
+    int gx, gy;
+    tile_arena_origin<BATCH, TX_, TY_>(tile, a.ntx, a.work, a.designs, gx, gy);
     mbar_expect_tx(&bar[st], NF * BOX * 4);
     for (int f = 0; f < NF; ++f)
-      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], tx * TX_ - TMA_BXPAD, ty * TY_ - 2, &bar[st]);
+      tma_load_2d(stage + (st * NF + f) * BOX, &maps.m[f], gx - TMA_BXPAD, gy - 2, &bar[st]);
   };
   if (threadIdx.x == 0) {
     mbar_init(&bar[0], 1);
@@ -495,8 +587,14 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
     const float* sbi = S + FBI * BOX;
     const float* sT0 = S + FT0 * BOX;  // thermal
     const float* sB = S + FB * BOX;    // thermal
-    const int tx = tile % a.ntx, ty = tile / a.ntx;
-    const int x0 = tx * TX_, y0 = ty * TY_;
+    TileCtx<BATCH> tc(tile, a.ntx, TX_, TY_, a.work, a.designs, g0, c0);
+    const Geom& g = *tc.g;
+    const Coef<float>& c = *tc.c;
+    const int nx = g.nx, ny = g.ny, x0 = tc.x0, y0 = tc.y0;
+    // global index of node (i, j): gbase + j * gpitch + i
+    const int gpitch = BATCH ? a.pitch : nx;
+    const size_t gbase = BATCH ? (size_t)(tc.gy - y0) * a.pitch + (size_t)(tc.gx - x0) : 0;
+    const float* emap = BATCH ? a.emap + (size_t)tc.d * 540 : a.emap;
 
     auto phase_a = [&](auto edge_tag) {
       constexpr bool EDGE = decltype(edge_tag)::value;
@@ -558,7 +656,11 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
       for (int q = threadIdx.x; q < TX_ * TY_; q += NT) {
         const int oy = q / TX_, ox = q - oy * TX_;
         const int i = x0 + ox, j = y0 + oy;
-        if (EDGE && (i >= nx || j >= ny)) continue;
+        if (EDGE && (i >= nx || j >= ny)) {  // outside the lattice: the output box carries zeros
+#pragma unroll
+          for (int f = 0; f < NA; ++f) sout[f * TX_ * TY_ + q] = 0.f;
+          continue;
+        }
         const int q1 = (oy + 1) * LX1 + (ox + 1);
         const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
         const bool interior = !EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1);
@@ -598,7 +700,8 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
           m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
           m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
           if (a.sens) {
-            const float gm = __ldg(a.gamma + (size_t)j * nx + i);
+            const size_t gi = gbase + (size_t)j * gpitch + i;
+            const float gm = __ldg(a.gamma + gi);
             float sacc = 0.f;
             if (a.sens_flow) {
               const float dd = c.q_alpha + gm;
@@ -610,7 +713,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
               const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
               sacc -= dB_of(c, gm) * (dTx * m[7] + dTy * m[8]);
             }
-            a.sens[(size_t)j * nx + i] += sacc;
+            a.sens[gi] += sacc;
           }
         } else {
 #pragma unroll
@@ -642,7 +745,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             m[8] = qy_;
             if (flux) kT = kap * sT0[s2];
           }
-          const float* M = a.emap + edge_class(g, i, j) * 60;
+          const float* M = emap + edge_class(g, i, j) * 60;
 #pragma unroll
           for (int r = 0; r < 6; ++r) {
             float acc = 0.f;
@@ -658,7 +761,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
     };
 
     if (threadIdx.x == 0) bulk_wait_read0();  // the previous tile's output copies have left sout
-    if (tile_is_interior(x0, y0, TX_, TY_, nx, ny)) {
+    if (tc.interior) {
       phase_a(std::false_type{});
       __syncthreads();
       phase_b(std::false_type{});
@@ -670,7 +773,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
     fence_proxy_async();
     __syncthreads();
     if (threadIdx.x == 0) {
-      for (int f = 0; f < NA; ++f) tma_store_2d(&omaps.m[f], x0, y0, sout + f * TX_ * TY_);
+      for (int f = 0; f < NA; ++f) tma_store_2d(&omaps.m[f], tc.gx, tc.gy, sout + f * TX_ * TY_);
       bulk_commit();
     }
   }

@@ -61,11 +61,31 @@ class Stats(C.Structure):
                 ("fwd_path", C.c_int32), ("adj_path", C.c_int32)]
 
 
+LKS_BATCH_VERSION = 1
+LKS_BATCH_TILE_CONFIGS = 4
+TILE_SHAPES = ((64, 8), (32, 16), (128, 4), (64, 16))
+
+
+class BatchOptions(C.Structure):
+    _fields_ = [("version", C.c_int32), ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
+                ("tile_config", C.c_int32), ("use_graph", C.c_int32), ("reserved", C.c_int32 * 7)]
+
+
+class BatchStats(C.Structure):
+    _fields_ = [("n_designs", C.c_int32), ("tile_config", C.c_int32), ("checkpoint_every", C.c_int32),
+                ("n_ckpt", C.c_int32), ("arena_w", C.c_int32), ("arena_h", C.c_int32),
+                ("graph", C.c_int32), ("device_status", C.c_int32), ("nodes", C.c_int64),
+                ("ntiles", C.c_int64), ("workspace_bytes", C.c_int64), ("kernel_launches", C.c_int64),
+                ("gradients", C.c_int64), ("tune_us", C.c_float * LKS_BATCH_TILE_CONFIGS)]
+
+
 # Every symbol the header declares (checked by the CPU test-suite).
 EXPORTS = ("lks_workspace_size", "lks_create", "lks_forward", "alks_adjoint", "lks_sensitivity",
            "lks_gradient_host", "lks_set_state", "lks_get_state", "lks_march", "alks_set_adjoint",
            "alks_get_adjoint", "alks_march", "lks_query", "lks_destroy", "lks_status_string",
-           "lks_last_error", "lks_edge_moment_map", "lks_gradient_noalloc")
+           "lks_last_error", "lks_edge_moment_map", "lks_gradient_noalloc",
+           "lks_batch_workspace_size", "lks_batch_create", "lks_batch_gradient", "lks_batch_query",
+           "lks_batch_destroy", "lks_batch_last_error")
 
 _lib = None
 
@@ -106,8 +126,16 @@ def load(build_if_missing: bool = True):
     L.lks_last_error.restype = C.c_char_p
     L.lks_edge_moment_map.argtypes = [C.c_double, i32, dp]
     L.lks_gradient_noalloc.argtypes = [C.POINTER(Desc), vp, vp, vp, vp]
+    L.lks_batch_workspace_size.argtypes = [i32, C.POINTER(Desc), C.POINTER(BatchOptions), C.POINTER(C.c_size_t)]
+    L.lks_batch_create.argtypes = [i32, C.POINTER(Desc), C.POINTER(BatchOptions), vp, C.c_size_t, vp,
+                                   C.POINTER(hp)]
+    L.lks_batch_gradient.argtypes = [hp, C.POINTER(vp), vp, C.POINTER(vp)]
+    L.lks_batch_query.argtypes = [hp, C.POINTER(BatchStats)]
+    L.lks_batch_destroy.argtypes = [hp]
+    L.lks_batch_last_error.argtypes = [hp]
+    L.lks_batch_last_error.restype = C.c_char_p
     for name in EXPORTS:
-        if name not in ("lks_status_string", "lks_last_error"):
+        if name not in ("lks_status_string", "lks_last_error", "lks_batch_last_error"):
             getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -280,4 +308,101 @@ class LKS:
         st = self.L.lks_query(self.h, C.byref(s))
         if st not in (0, s.device_status):
             _check(st, "lks_query", self.h)
+        return s
+
+
+# ---------------------------------------------------------------------------------
+# Batched form
+# ---------------------------------------------------------------------------------
+def batch_options(checkpoint_every: int = 0, snapshot: str = "bf16", tile_config: int = -1,
+                  use_graph: bool = True) -> BatchOptions:
+    o = BatchOptions()
+    o.version = LKS_BATCH_VERSION
+    o.checkpoint_every = int(checkpoint_every)
+    o.snapshot_type = SNAP[snapshot]
+    o.tile_config = int(tile_config)
+    o.use_graph = 1 if use_graph else 0
+    return o
+
+
+def batch_descs(problems) -> "C.Array":
+    arr = (Desc * len(problems))()
+    for k, pb in enumerate(problems):
+        arr[k] = make_desc(pb, "f32")
+    return arr
+
+
+def batch_workspace_size(problems, opt: Optional[BatchOptions] = None) -> int:
+    L = load()
+    descs = batch_descs(problems)
+    n = C.c_size_t(0)
+    _check(L.lks_batch_workspace_size(len(problems), descs, C.byref(opt) if opt is not None else None,
+                                      C.byref(n)), "lks_batch_workspace_size")
+    return int(n.value)
+
+
+class LKSBatch:
+    """Many unsteady FP32 designs of unequal size, marched in lock step by one
+    persistent launch per step; a gradient of every design is one call (one CUDA
+    graph launch when ``use_graph``)."""
+
+    def __init__(self, problems, checkpoint_every: int = 0, snapshot: str = "bf16", tile_config: int = -1,
+                 use_graph: bool = True, device: Optional[torch.device] = None,
+                 stream: Optional[torch.cuda.Stream] = None):
+        if not torch.cuda.is_available():
+            raise RuntimeError("the LKS library needs a CUDA device")
+        self.L = load()
+        self.problems = list(problems)
+        self.n = len(self.problems)
+        self.shapes = [(int(p.ny), int(p.nx)) for p in self.problems]
+        self.opt = batch_options(checkpoint_every, snapshot, tile_config, use_graph)
+        self.descs = batch_descs(self.problems)
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        with torch.cuda.device(self.device):
+            self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+            n = C.c_size_t(0)
+            _check(self.L.lks_batch_workspace_size(self.n, self.descs, C.byref(self.opt), C.byref(n)),
+                   "lks_batch_workspace_size")
+            self.workspace = torch.empty(int(n.value), dtype=torch.uint8, device=self.device)
+            h = C.c_void_p()
+            st = self.L.lks_batch_create(self.n, self.descs, C.byref(self.opt),
+                                         C.c_void_p(self.workspace.data_ptr()), n,
+                                         C.c_void_p(self.stream.cuda_stream), C.byref(h))
+            if st != 0:
+                raise LKSError(st, "lks_batch_create")
+        self.h = h
+        self.J = torch.zeros(self.n, dtype=torch.float64, device=self.device)
+        self.grads = [torch.empty(s, dtype=torch.float32, device=self.device) for s in self.shapes]
+        self._gptr = (C.c_void_p * self.n)()
+        self._dptr = (C.c_void_p * self.n)(*[g.data_ptr() for g in self.grads])
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                self.L.lks_batch_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    def gradient(self, gammas: Sequence[torch.Tensor]):
+        """(J[n] float64 tensor, [dJ/dgamma per design]) -- the returned tensors are
+        reused by the next call."""
+        if len(gammas) != self.n:
+            raise ValueError("one gamma per design")
+        keep = []
+        for k, (g, s) in enumerate(zip(gammas, self.shapes)):
+            if g.dtype != torch.float32 or g.device != self.device or tuple(g.shape) != s or not g.is_contiguous():
+                g = g.to(device=self.device, dtype=torch.float32).reshape(s).contiguous()
+            keep.append(g)
+            self._gptr[k] = g.data_ptr()
+        st = self.L.lks_batch_gradient(self.h, self._gptr, C.c_void_p(self.J.data_ptr()), self._dptr)
+        if st != 0:
+            raise LKSError(st, "lks_batch_gradient: " + self.L.lks_batch_last_error(self.h).decode())
+        self._keep = keep  # inputs stay alive until the stream has consumed them
+        return self.J, self.grads
+
+    def query(self) -> BatchStats:
+        s = BatchStats()
+        _check(self.L.lks_batch_query(self.h, C.byref(s)), "lks_batch_query")
         return s

@@ -101,3 +101,76 @@ def test_create_rejects_bad_workspace_without_gpu_work():
     h = C.c_void_p()
     st = L.lks_create(C.byref(d), None, C.c_size_t(16), None, C.byref(h))
     assert st == 2 and not h.value
+
+
+# ---------------------------------------------------------------------------------------
+# Batched form: host-side planning (no GPU work)
+# ---------------------------------------------------------------------------------------
+def _batch(n_steps=120):
+    kw = dict(steady=False, n_steps=n_steps, n_adj=n_steps, pulse_mean=0.75, pulse_amp=0.25, pulse_period=50.0)
+    return [inputs.channel(130, 70, Re=50.0, seed=10, **kw), inputs.channel(256, 64, Re=20.0, seed=11, **kw),
+            inputs.channel(33, 20, Re=10.0, seed=12, **kw)]
+
+
+def _bsize(descs, opt):
+    n = C.c_size_t(0)
+    st = lks.load().lks_batch_workspace_size(len(descs), descs, C.byref(opt) if opt is not None else None,
+                                             C.byref(n))
+    return st, n.value
+
+
+def test_batch_workspace_validation():
+    pbs = _batch()
+    ok = lks.batch_descs(pbs)
+    st, n = _bsize(ok, None)
+    assert st == 0 and n > 0
+    for mutate in (lambda d: setattr(d[1], "steady", 1), lambda d: setattr(d[0], "thermal", 1),
+                   lambda d: setattr(d[2], "real_type", 1), lambda d: setattr(d[1], "n_steps", 119),
+                   lambda d: setattr(d[0], "nu", 0.9)):
+        d = lks.batch_descs(pbs)
+        mutate(d)
+        assert _bsize(d, None)[0] == 1
+    for field, val in (("version", 7), ("tile_config", 4), ("snapshot_type", 3), ("use_graph", 2),
+                       ("checkpoint_every", -1)):
+        o = lks.batch_options()
+        setattr(o, field, val)
+        assert _bsize(ok, o)[0] == 1, field
+    o = lks.batch_options()
+    o.reserved[2] = 1
+    assert _bsize(ok, o)[0] == 1
+    assert lks.load().lks_batch_workspace_size(0, ok, None, C.byref(C.c_size_t())) == 1
+
+
+def test_batch_memory_optimal_checkpoint_spacing():
+    """K = 0 picks the spacing with the least workspace; the snapshot width and the
+    number of designs enter as expected."""
+    pbs = _batch()
+    d = lks.batch_descs(pbs)
+    auto = _bsize(d, lks.batch_options(checkpoint_every=0))[1]
+    for K in (1, 2, 5, 9, 10, 11, 12, 20, 60, 120, 500):
+        assert auto <= _bsize(d, lks.batch_options(checkpoint_every=K))[1], K
+    bf = _bsize(d, lks.batch_options(checkpoint_every=10, snapshot="bf16"))[1]
+    f32 = _bsize(d, lks.batch_options(checkpoint_every=10, snapshot="f32"))[1]
+    assert bf < f32
+    assert _bsize(lks.batch_descs(pbs[:2]), None)[1] < auto
+
+
+def test_batch_create_rejects_bad_workspace_without_gpu_work():
+    L = lks.load()
+    d = lks.batch_descs(_batch())
+    h = C.c_void_p()
+    assert L.lks_batch_create(3, d, None, None, C.c_size_t(16), None, C.byref(h)) == 2 and not h.value
+    o = lks.batch_options()
+    o.tile_config = 9
+    assert L.lks_batch_create(3, d, C.byref(o), None, C.c_size_t(16), None, C.byref(h)) == 1 and not h.value
+
+
+def test_config5_recipe():
+    pbs = inputs.config5()
+    assert len(pbs) == 64
+    assert all(128 <= p.nx <= 512 and 64 <= p.ny <= 256 for p in pbs)
+    assert all(0.012 <= p.nu <= 0.30 for p in pbs)
+    Re = [p.u_max * (p.ny - 1) / p.nu for p in pbs]
+    assert all(20.0 - 1e-9 <= r <= 200.0 + 1e-9 for r in Re)
+    assert [p.seed for p in pbs] == list(range(500, 564))
+    assert all(p.n_steps == 5000 and not p.steady for p in pbs)
