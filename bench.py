@@ -6,7 +6,12 @@ sensitivity).  Default workload: 512 x 256 steady channel, Re = 100, 20000 forwa
 + 20000 adjoint steps, FP32 (the second configuration of the paper-derived set).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload config2|roofline8192|config1]
+                    [--workload config2|roofline8192|config1|config3|config5]
+
+config3 runs the checkpoint study (plain FP32 trajectory against checkpoints every
+K steps with FP32 / BF16 / FP16 snapshots); config5 runs the batched form (64
+designs of unequal size, one persistent launch per step, one CUDA graph per
+gradient) against the plain FP32 form design by design.
 
 Under torchrun every rank runs an independent replica (designs are independent;
 no collective on the data path); rank 0 prints one JSON line.
@@ -33,6 +38,10 @@ import inputs  # noqa: E402
 # gradients recomputed from the halo; gamma read once).
 BYTES_FWD = 4 * (3 + 3 + 1)            # drho,u,v in; drho,u,v out; gamma
 BYTES_ADJ_STEADY = 4 * (6 + 6 + 2 + 1)  # 6 adjoint fields in + out; u,v; gamma
+# Unsteady checkpointed gradient, per node and level: forward (28), recomputed
+# forward storing the level's u, v (28 + 8), adjoint reading both levels' u, v with
+# the FP32 sensitivity read-modify-write (4 * (6 + 6 + 4 + 1) + 8 = 76).
+BYTES_CKPT_LEVEL = BYTES_FWD + (BYTES_FWD + 8) + (4 * (6 + 6 + 4 + 1) + 8)
 
 METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e-3 rel"
 
@@ -225,6 +234,127 @@ def run_checkpoint_study(args):
         "memory_ratio_vs_plain": head["workspace_GB"] / (ws_plain / 1e9)}))
 
 
+def run_batch_study(args):
+    """Batched config5: 64 unsteady designs (128x64 .. 512x256, 5000 steps) in one
+    persistent launch per step, the gradient of all of them one CUDA graph launch,
+    BF16 checkpoints at the memory-optimal spacing, autotuned tile shape.  Compared
+    with the plain FP32 form (full u, v trajectory, per-step launches) run design by
+    design on the same GPU: seconds per batch of gradients, device memory and the
+    gradient error between the two."""
+    import torch
+    from paper_2411_03090_gb300 import LKS, LKSBatch
+
+    pbs = inputs.config5()
+    if args.steps_override:
+        pbs = [p.with_(n_steps=args.steps_override, n_adj=args.steps_override) for p in pbs]
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    n_steps = pbs[0].n_steps
+    N = sum(p.n_nodes for p in pbs)
+    gam_np = [p.gamma().astype(np.float32) for p in pbs]
+    gam = [torch.from_numpy(g).to(dev) for g in gam_np]
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    t0 = time.perf_counter()
+    b = LKSBatch(pbs, snapshot="bf16", device=dev)
+    create_s = time.perf_counter() - t0
+    st = b.query()
+    for _ in range(max(args.warmup, 3)):
+        b.gradient(gam)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        J, G = b.gradient(gam)
+        e1.record(b.stream)
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1) * 1e-3)
+    clk = clocks.stop()
+    st = b.query()
+    if st.device_status != 0:
+        raise SystemExit(f"device status {st.device_status}")
+    t_batch = sum(times) / len(times)
+    Jb = J.cpu().numpy().copy()
+    Gb = [g.double().cpu().numpy() for g in G]
+
+    # end to end: gamma from pinned host buffers, J and gradients back to pinned host
+    e2e_val = None
+    if not args.no_e2e:
+        gh = [torch.from_numpy(g).pin_memory() for g in gam_np]
+        oh = [torch.empty(p.ny, p.nx, dtype=torch.float32).pin_memory() for p in pbs]
+        Jh = torch.empty(len(pbs), dtype=torch.float64).pin_memory()
+        dg = [torch.empty(p.ny, p.nx, dtype=torch.float32, device=dev) for p in pbs]
+        ts = []
+        for _ in range(2):
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            with torch.cuda.stream(b.stream):
+                for d, h in zip(dg, gh):
+                    d.copy_(h, non_blocking=True)
+            J2, G2 = b.gradient(dg)
+            with torch.cuda.stream(b.stream):
+                for o, g in zip(oh, G2):
+                    o.copy_(g, non_blocking=True)
+                Jh.copy_(J2, non_blocking=True)
+            b.stream.synchronize()
+            ts.append(time.perf_counter() - t1)
+        e2e_val = N * 2 * n_steps / min(ts) / 1e6
+
+    # the plain FP32 form, design by design
+    t_plain, errs, peak_ws, sum_ws = 0.0, [], 0, 0
+    if not args.no_plain:
+        for k, p in enumerate(pbs):
+            s = LKS(p, real="f32", checkpoint_every=0, device=dev)
+            peak_ws = max(peak_ws, s.workspace.numel())
+            sum_ws += s.workspace.numel()
+            s.gradient(gam[k])
+            torch.cuda.synchronize()
+            flush.fill_(1.0)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s.stream)
+            _, gp = s.gradient(gam[k])
+            e1.record(s.stream)
+            torch.cuda.synchronize()
+            t_plain += e0.elapsed_time(e1) * 1e-3
+            gp = gp.double().cpu().numpy()
+            errs.append(float(np.linalg.norm(Gb[k] - gp) / np.linalg.norm(gp)))
+            del s
+            torch.cuda.empty_cache()
+    hbm, peak_kind = peaks()
+    gbs = BYTES_CKPT_LEVEL * N * n_steps / t_batch / 1e9
+    value = N * 2 * n_steps / t_batch / 1e6
+    print(json.dumps({
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_batch * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": f"config5: {len(pbs)} unsteady designs 128x64..512x256 (seed 5), Re 20-200, "
+                               f"{n_steps} steps, BF16 checkpoints, one graph launch per batch of gradients",
+                   "nodes": N, "updates_counted": "forward + adjoint levels (recomputation not counted)",
+                   "l2": "flushed before each timed gradient (256 MB write); arena > L2",
+                   "tile_shape": list(__import__("paper_2411_03090_gb300").lks.TILE_SHAPES[st.tile_config]),
+                   "autotune_us_per_step": [round(x, 1) for x in st.tune_us],
+                   "checkpoint_every": st.checkpoint_every, "arena": [st.arena_w, st.arena_h],
+                   "tiles": st.ntiles, "create_s": create_s},
+        "roofline": {"bound": "hbm", "kernel": "whole gradient (graph: fwd_tma/adj_tma BATCH kernels)",
+                     "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
+                     "peak_kind": peak_kind, "algorithmic_bytes_per_node_level": BYTES_CKPT_LEVEL},
+        "batch_vs_plain": {"s_per_batch_gradient": t_batch, "plain_fp32_s_design_by_design": t_plain or None,
+                           "speedup": (t_plain / t_batch) if t_plain else None,
+                           "batch_workspace_GB": st.workspace_bytes / 1e9,
+                           "plain_workspace_GB_all_designs": sum_ws / 1e9 or None,
+                           "plain_workspace_GB_largest_design": peak_ws / 1e9 or None,
+                           "grad_rel_err_vs_plain_max": max(errs) if errs else None,
+                           "grad_rel_err_vs_plain_median": float(np.median(errs)) if errs else None},
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N + 8 * len(pbs)},
+        "gpu_launches": int(st.kernel_launches),
+        "clocks": clk,
+    }))
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -235,12 +365,16 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-override", type=int, default=0)
+    ap.add_argument("--no-plain", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
         return
     if args.workload == "config3":
         run_checkpoint_study(args)
+        return
+    if args.workload == "config5":
+        run_batch_study(args)
         return
 
     import torch
@@ -317,8 +451,9 @@ def main():
     fwd_gbs = BYTES_FWD * N / fwd_launch_s / 1e9
     traffic = None
     st = s.query()
-    kname = {1: ("adj_step_kernel<float,false>", "fwd_step_kernel<float,false>"),
-             2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>")}
+    step_names = (("adj_tma_kernel<false,true,false>", "fwd_tma_kernel<false,false>") if pb.nx % 4 == 0 else
+                  ("adj_step_kernel<float,false>", "fwd_step_kernel<float,false>"))
+    kname = {1: step_names, 2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>")}
     adj_k = kname.get(st.adj_path, kname[1])[0]
     fwd_k = kname.get(st.fwd_path, kname[1])[1]
     roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
