@@ -163,6 +163,69 @@ def config5(n_designs: int = 64, n_steps: int = 5000) -> List[Problem]:
     return out
 
 
+def gamma_field3(nx: int, ny: int, nz: int, seed: int, sigma: float = 6.0, strip: int = 4) -> np.ndarray:
+    """Seeded smoothed-noise design field of a 3-D lattice, shape (nz, ny, nx): the
+    2-D recipe with the filter applied along all three axes; gamma = 1 on
+    ``strip`` node layers at the inlet and outlet and on every face node."""
+    rng = np.random.default_rng(seed)
+    noise = rng.random((nz, ny, nx))
+    s = _gauss1d(_gauss1d(_gauss1d(noise, sigma, 0), sigma, 1), sigma, 2)
+    z = (s - s.mean()) / max(float(s.std()), 1e-300)
+    g = np.clip(0.5 + 0.5 * z, 0.0, 1.0)
+    g[:, :, :strip] = 1.0
+    g[:, :, nx - strip:] = 1.0
+    g[0, :, :] = g[-1, :, :] = 1.0
+    g[:, 0, :] = g[:, -1, :] = 1.0
+    g[:, :, 0] = g[:, :, -1] = 1.0
+    return g
+
+
+@dataclass
+class Problem3:
+    """One 3-D (D3Q19) steady duct: inlet face x = 0, outlet face x = nx - 1, walls
+    on the four side faces (lattice units)."""
+
+    nx: int
+    ny: int
+    nz: int
+    nu: float
+    alpha_bar: float
+    q_alpha: float = 0.1
+    u_max: float = 0.05
+    rho_out: float = 1.0
+    profile: int = 0         # inlet: 0 duct (product of parabolas), 1 plane channel (parabola in y)
+    steady: bool = True
+    n_steps: int = 1000
+    n_adj: int = 1000
+    seed: int = 4
+    sigma: float = 6.0
+    strip: int = 4
+
+    @property
+    def n_nodes(self) -> int:
+        return self.nx * self.ny * self.nz
+
+    def gamma(self) -> np.ndarray:
+        return gamma_field3(self.nx, self.ny, self.nz, self.seed, self.sigma, self.strip)
+
+    def with_(self, **kw) -> "Problem3":
+        return replace(self, **kw)
+
+
+def duct(nx: int, ny: int, nz: int, Re: float, u_max: float = 0.05, **kw) -> Problem3:
+    """Duct with the inlet over the whole x = 0 face; nu = u_max L / Re with L the
+    inlet width ny - 1; alpha_bar = 1e3 nu."""
+    nu = u_max * (ny - 1) / Re
+    kw.setdefault("alpha_bar", 1e3 * nu)
+    return Problem3(nx=nx, ny=ny, nz=nz, nu=nu, u_max=u_max, **kw)
+
+
+def config4() -> Problem3:
+    """192^3 steady duct, Re = 50 (nu = 0.191), sigma = 6, 1000 forward + 1000
+    adjoint steps."""
+    return duct(192, 192, 192, Re=50.0, seed=4, n_steps=1000, n_adj=1000)
+
+
 def roofline2d(n: int = 8192) -> Problem:
     """Large 2-D steady channel used to load HBM (working set >> L2)."""
     return channel(n, n, Re=100.0 * (n - 1) / 255.0, seed=6, n_steps=200, n_adj=200)

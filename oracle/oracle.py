@@ -20,6 +20,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "lks_oracle.c")
+_SRC3 = os.path.join(_HERE, "lks3d_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liblks_oracle.so")
 _lock = threading.Lock()
 _lib = None
@@ -46,15 +47,31 @@ class OrcProblem(C.Structure):
     ]
 
 
+class OrcProblem3(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+        ("nu", C.c_double),
+        ("alpha_bar", C.c_double), ("q_alpha", C.c_double),
+        ("u_max", C.c_double),
+        ("rho_out", C.c_double),
+        ("profile", C.c_int),
+    ]
+
+
+NADJ3 = 10
+ADJ3_NAMES = ("rho_t", "ux_t", "uy_t", "uz_t", "sxx_t", "sxy_t", "sxz_t", "syy_t", "syz_t", "szz_t")
+
+
 def build(force: bool = False) -> str:
     """Compile the oracle with gcc (FP64, OpenMP).  Returns the library path."""
     with _lock:
-        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= max(
+                os.path.getmtime(_SRC), os.path.getmtime(_SRC3)):
             return _LIB
         os.makedirs(os.path.dirname(_LIB), exist_ok=True)
         tmp = _LIB + f".tmp{os.getpid()}"
         cmd = ["gcc", "-O2", "-std=c11", "-D_DEFAULT_SOURCE", "-fopenmp", "-fPIC", "-shared",
-               "-o", tmp, _SRC, "-lm"]
+               "-o", tmp, _SRC, _SRC3, "-lm"]
         subprocess.run(cmd, check=True)
         os.replace(tmp, _LIB)
         return _LIB
@@ -86,6 +103,25 @@ def lib():
         L.orc_steady_adjoint.argtypes = [prob, P, P, P, P, C.c_int, P, P]
         L.orc_steady_adjoint.restype = C.c_double
         L.orc_unsteady_adjoint.argtypes = [prob, P, C.c_int, P, P, P]
+        p3 = C.POINTER(OrcProblem3)
+        IP = C.POINTER(C.c_int)
+        L.orc3_lattice.argtypes = [IP, P]
+        L.orc3_feq_moments.argtypes = [C.c_double, C.c_double, P, P, P]
+        L.orc3_forward_node.argtypes = [p3, P, P, PP, C.c_int, C.c_int, C.c_int, P]
+        L.orc3_forward_step.argtypes = [p3, P, P, P, P, P, P, P, P, P]
+        L.orc3_objective.argtypes = [p3, P, P, P, P]
+        L.orc3_objective.restype = C.c_double
+        L.orc3_dJdu_node.argtypes = [p3, P, PP, C.c_int, C.c_int, C.c_int, P]
+        L.orc3_bc_flow.argtypes = [IP, C.c_int, C.c_double, IP, P, P]
+        L.orc3_adjoint_eq.argtypes = [p3, PP, PP, PP]
+        L.orc3_adjoint_node.argtypes = [p3, P, PP, PP, C.c_int, C.c_int, C.c_int, P]
+        L.orc3_adjoint_step.argtypes = [p3, P, PP, PP, PP, PP, P]
+        L.orc3_sensitivity_accum.argtypes = [p3, P, PP, PP, P]
+        L.orc3_forward.argtypes = [p3, P, C.c_int, P, P, P, P, P, P]
+        L.orc3_forward.restype = C.c_double
+        L.orc3_steady_adjoint.argtypes = [p3, P, P, P, P, C.c_int, P, P]
+        L.orc3_steady_adjoint.restype = C.c_double
+        L.orc3_unsteady_adjoint.argtypes = [p3, P, C.c_int, P, P, P]
         L.orc_set_threads.argtypes = [C.c_int]
         L.orc_get_threads.restype = C.c_int
         _lib = L
@@ -327,3 +363,155 @@ def bc_thermal(n, flux: bool, B: float, un: float, known: np.ndarray, unknown_ma
     mult = np.zeros(1)
     L.orc_bc_thermal(int(n[0]), int(n[1]), int(flux), float(B), float(un), um, _p(g), _p(mult))
     return g, float(mult[0])
+
+
+# ---------------------------------------------------------------------------------
+# Three dimensions (D3Q19, steady duct; ``lks3d_oracle.c``)
+# ---------------------------------------------------------------------------------
+def make_problem3(pb) -> OrcProblem3:
+    s = OrcProblem3()
+    for name, _ in OrcProblem3._fields_:
+        setattr(s, name, type(getattr(s, name))(getattr(pb, name)))
+    return s
+
+
+class State3:
+    """rho, u, v, w fields, each (nz, ny, nx) float64."""
+
+    def __init__(self, nz: int, ny: int, nx: int):
+        self.rho = np.ones((nz, ny, nx))
+        self.u = np.zeros((nz, ny, nx))
+        self.v = np.zeros((nz, ny, nx))
+        self.w = np.zeros((nz, ny, nx))
+
+    def copy(self) -> "State3":
+        s = State3(*self.rho.shape)
+        s.rho, s.u, s.v, s.w = self.rho.copy(), self.u.copy(), self.v.copy(), self.w.copy()
+        return s
+
+    def vel(self):
+        return [self.u, self.v, self.w]
+
+
+def lattice3():
+    """(c (19, 3) int, w (19,)) of the 3-D oracle."""
+    c = (C.c_int * 57)()
+    w = np.zeros(19)
+    lib().orc3_lattice(c, _p(w))
+    return np.array(list(c), dtype=int).reshape(19, 3), w
+
+
+def feq_moments3(A: float, rho: float, u, grad) -> np.ndarray:
+    out = np.zeros(10)
+    lib().orc3_feq_moments(float(A), float(rho), _p(np.asarray(u, dtype=np.float64).copy()),
+                           _p(np.ascontiguousarray(grad, dtype=np.float64).reshape(9).copy()), _p(out))
+    return out
+
+
+def forward3(pb, gamma, n_steps: int, state: Optional[State3] = None, traj: bool = False,
+             accumulate_J: bool = False):
+    """3-D LKS march.  Returns (state, residual, traj or None, J_sum)."""
+    L = lib()
+    prob = make_problem3(pb)
+    st = state.copy() if state is not None else State3(pb.nz, pb.ny, pb.nx)
+    tr = np.zeros((n_steps + 1, 3, pb.nz, pb.ny, pb.nx)) if traj else None
+    Jacc = C.c_double(0.0)
+    res = L.orc3_forward(C.byref(prob), _p(_g(gamma)), int(n_steps), _p(st.rho), _p(st.u), _p(st.v),
+                         _p(st.w), _p(tr) if traj else None, C.byref(Jacc) if accumulate_J else None)
+    return st, res, tr, Jacc.value
+
+
+def forward_step3(pb, gamma, st: State3) -> State3:
+    out = State3(pb.nz, pb.ny, pb.nx)
+    lib().orc3_forward_step(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.rho), _p(st.u), _p(st.v),
+                            _p(st.w), _p(out.rho), _p(out.u), _p(out.v), _p(out.w))
+    return out
+
+
+def objective3(pb, gamma, st: State3) -> float:
+    return float(lib().orc3_objective(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.u), _p(st.v),
+                                      _p(st.w)))
+
+
+def dJdu3(pb, gamma, st: State3) -> np.ndarray:
+    L = lib()
+    prob = make_problem3(pb)
+    g = _g(gamma)
+    out = np.zeros((3, pb.nz, pb.ny, pb.nx))
+    o = np.zeros(3)
+    for k in range(pb.nz):
+        for j in range(pb.ny):
+            for i in range(pb.nx):
+                L.orc3_dJdu_node(C.byref(prob), _p(g), _pp(st.vel()), i, j, k, _p(o))
+                out[:, k, j, i] = o
+    return out
+
+
+def adjoint_eq3(pb, st: State3, adj: np.ndarray) -> np.ndarray:
+    """(P, Vx, Vy, Vz) at every node from the adjoint fields and the state."""
+    a = np.ascontiguousarray(adj, dtype=np.float64)
+    out = np.zeros((4, pb.nz, pb.ny, pb.nx))
+    lib().orc3_adjoint_eq(C.byref(make_problem3(pb)), _pp(st.vel()), _pp([a[q] for q in range(NADJ3)]),
+                          _pp([out[q] for q in range(4)]))
+    return out
+
+
+def adjoint_gather3(pb, gamma, PV: np.ndarray, st0: State3) -> np.ndarray:
+    """Adjoint moments at level t from the coefficients PV of level t+1."""
+    L = lib()
+    prob = make_problem3(pb)
+    g = _g(gamma)
+    c = [np.ascontiguousarray(PV[q], dtype=np.float64) for q in range(4)]
+    out = np.zeros((NADJ3, pb.nz, pb.ny, pb.nx))
+    o = np.zeros(NADJ3)
+    for k in range(pb.nz):
+        for j in range(pb.ny):
+            for i in range(pb.nx):
+                L.orc3_adjoint_node(C.byref(prob), _p(g), _pp(c), _pp(st0.vel()), i, j, k, _p(o))
+                out[:, k, j, i] = o
+    return out
+
+
+def adjoint_step3(pb, gamma, st1: State3, st0: State3, adj1: np.ndarray) -> np.ndarray:
+    a1 = np.ascontiguousarray(adj1, dtype=np.float64)
+    a0 = np.zeros_like(a1)
+    work = np.zeros((4, pb.nz, pb.ny, pb.nx))
+    lib().orc3_adjoint_step(C.byref(make_problem3(pb)), _p(_g(gamma)), _pp(st1.vel()), _pp(st0.vel()),
+                            _pp([a1[q] for q in range(NADJ3)]), _pp([a0[q] for q in range(NADJ3)]), _p(work))
+    return a0
+
+
+def steady_adjoint3(pb, gamma, st: State3, n_iter: int):
+    adj = np.zeros((NADJ3, pb.nz, pb.ny, pb.nx))
+    sens = np.zeros((pb.nz, pb.ny, pb.nx))
+    res = lib().orc3_steady_adjoint(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.u), _p(st.v),
+                                    _p(st.w), int(n_iter), _p(adj), _p(sens))
+    return adj, sens, res
+
+
+def unsteady_adjoint3(pb, gamma, traj: np.ndarray):
+    n = traj.shape[0] - 1
+    tr = np.ascontiguousarray(traj, dtype=np.float64)
+    adj = np.zeros((NADJ3, pb.nz, pb.ny, pb.nx))
+    sens = np.zeros((pb.nz, pb.ny, pb.nx))
+    lib().orc3_unsteady_adjoint(C.byref(make_problem3(pb)), _p(_g(gamma)), int(n), _p(tr), _p(adj), _p(sens))
+    return adj, sens
+
+
+def steady_gradient3(pb, gamma, n_steps: Optional[int] = None, n_adj: Optional[int] = None):
+    """Steps 2-5 for a steady 3-D problem with fixed step counts."""
+    n_steps = pb.n_steps if n_steps is None else n_steps
+    n_adj = pb.n_adj if n_adj is None else n_adj
+    st, _, _, _ = forward3(pb, gamma, n_steps)
+    J = objective3(pb, gamma, st)
+    adj, sens, _ = steady_adjoint3(pb, gamma, st, n_adj)
+    return dict(J=J, dJdgamma=sens, state=st, adjoint=adj)
+
+
+def bc_flow3(n, pressure: bool, A: float, known: np.ndarray, unknown_mask):
+    f = np.ascontiguousarray(known, dtype=np.float64).copy()
+    nn = (C.c_int * 3)(*[int(x) for x in n])
+    um = (C.c_int * 19)(*[int(x) for x in unknown_mask])
+    mult = np.zeros(3)
+    lib().orc3_bc_flow(nn, int(pressure), float(A), um, _p(f), _p(mult))
+    return f, mult
