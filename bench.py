@@ -6,7 +6,7 @@ sensitivity).  Default workload: 512 x 256 steady channel, Re = 100, 20000 forwa
 + 20000 adjoint steps, FP32 (the second configuration of the paper-derived set).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload config2|roofline8192|config1|config3|config5]
+                    [--workload config2|roofline8192|config1|config3|config4|config5]
 
 config3 runs the checkpoint study (plain FP32 trajectory against checkpoints every
 K steps with FP32 / BF16 / FP16 snapshots); config5 runs the batched form (64
@@ -42,6 +42,9 @@ BYTES_ADJ_STEADY = 4 * (6 + 6 + 2 + 1)  # 6 adjoint fields in + out; u,v; gamma
 # forward storing the level's u, v (28 + 8), adjoint reading both levels' u, v with
 # the FP32 sensitivity read-modify-write (4 * (6 + 6 + 4 + 1) + 8 = 76).
 BYTES_CKPT_LEVEL = BYTES_FWD + (BYTES_FWD + 8) + (4 * (6 + 6 + 4 + 1) + 8)
+# D3Q19: drho,u,v,w in + out and gamma; steady adjoint: 10 fields in + out, u,v,w, gamma.
+BYTES_FWD_3D = 4 * (4 + 4 + 1)
+BYTES_ADJ_3D = 4 * (10 + 10 + 3 + 1)
 
 METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e-3 rel"
 
@@ -51,6 +54,10 @@ def workload(name: str):
         return inputs.config2(), "config2: 512x256 steady channel, Re=100, 20000+20000 steps, FP32"
     if name == "config1":
         return inputs.config1(), "config1: 64x64 steady channel, Re=10, 5000+5000 steps, FP32"
+    if name == "config4":
+        pb = inputs.config4()
+        return pb, (f"config4: 192^3 steady D3Q19 duct, Re=50 (nu=0.191), {pb.n_steps}+{pb.n_adj} steps, "
+                    "FP32, objective = dissipation")
     if name.startswith("roofline"):
         n = int(name[len("roofline"):])
         pb = inputs.roofline2d(n)
@@ -127,12 +134,17 @@ def cpu_baseline(pb, n_fwd: int, n_adj: int):
     O.build()
     g = pb.gamma()
     t0 = time.perf_counter()
-    st, _, _, _ = O.forward(pb, g, n_fwd)
-    O.steady_adjoint(pb, g, st, n_adj)
+    if hasattr(pb, "nz"):
+        st, _, _, _ = O.forward3(pb, g, n_fwd)
+        O.steady_adjoint3(pb, g, st, n_adj)
+    else:
+        st, _, _, _ = O.forward(pb, g, n_fwd)
+        O.steady_adjoint(pb, g, st, n_adj)
     dt = time.perf_counter() - t0
     mlups = pb.n_nodes * (n_fwd + n_adj) / dt / 1e6
     return {"value": mlups, "unit": "MLUPS", "cores": O.get_threads(), "kind": "oracle",
-            "sample": f"{pb.nx}x{pb.ny} lattice, {n_fwd} forward + {n_adj} adjoint steps (of "
+            "sample": f"{pb.nx}x{pb.ny}{'x%d' % pb.nz if hasattr(pb, 'nz') else ''} lattice, "
+                      f"{n_fwd} forward + {n_adj} adjoint steps (of "
                       f"{pb.n_steps}+{pb.n_adj}), FP64, {dt:.1f} s"}
 
 
@@ -392,6 +404,9 @@ def main():
     from paper_2411_03090_gb300 import LKS
 
     pb, desc = workload(args.workload)
+    if args.steps_override:
+        pb = pb.with_(n_steps=args.steps_override, n_adj=args.steps_override)
+        desc += f" (shortened to {args.steps_override}+{args.steps_override} steps)"
     g_np = pb.gamma()
     gamma = torch.from_numpy(g_np).to(dev, torch.float32)
     s = LKS(pb, real="f32", device=dev)
@@ -447,8 +462,11 @@ def main():
     hbm, peak_kind = peaks()
     adj_launch_s = (sum(adj_ms) / len(adj_ms)) * 1e-3 / pb.n_adj
     fwd_launch_s = (sum(fwd_ms) / len(fwd_ms)) * 1e-3 / pb.n_steps
-    adj_gbs = BYTES_ADJ_STEADY * N / adj_launch_s / 1e9
-    fwd_gbs = BYTES_FWD * N / fwd_launch_s / 1e9
+    three_d = hasattr(pb, "nz")
+    b_adj = BYTES_ADJ_3D if three_d else BYTES_ADJ_STEADY
+    b_fwd = BYTES_FWD_3D if three_d else BYTES_FWD
+    adj_gbs = b_adj * N / adj_launch_s / 1e9
+    fwd_gbs = b_fwd * N / fwd_launch_s / 1e9
     traffic = None
     st = s.query()
     step_names = (("adj_tma_kernel<false,true,false>", "fwd_tma_kernel<false,false>") if pb.nx % 4 == 0 else
@@ -456,18 +474,20 @@ def main():
     kname = {1: step_names, 2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>")}
     adj_k = kname.get(st.adj_path, kname[1])[0]
     fwd_k = kname.get(st.fwd_path, kname[1])[1]
+    if three_d:
+        adj_k, fwd_k = "adj3_kernel<float>", "fwd3_kernel<float>"
     roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
                 "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,
-                "algorithmic_bytes_per_node": BYTES_ADJ_STEADY, "mean_step_us": adj_launch_s * 1e6,
+                "algorithmic_bytes_per_node": b_adj, "mean_step_us": adj_launch_s * 1e6,
                 "forward": {"kernel": fwd_k, "achieved": fwd_gbs,
-                            "frac": fwd_gbs / hbm, "algorithmic_bytes_per_node": BYTES_FWD,
+                            "frac": fwd_gbs / hbm, "algorithmic_bytes_per_node": b_fwd,
                             "mean_step_us": fwd_launch_s * 1e6}}
 
     # End to end through the C ABI with host buffers (pinned), copies inside.
     e2e_val = None
     if not args.no_e2e:
         g_host = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
-        grad_host = torch.empty(pb.ny, pb.nx, dtype=torch.float32).pin_memory().numpy()
+        grad_host = torch.empty(*g_np.shape, dtype=torch.float32).pin_memory().numpy()
         s.gradient_host(g_host, grad_host)
         e2e_t = []
         for _ in range(max(2, min(args.steps, 3))):
@@ -486,7 +506,8 @@ def main():
         "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc, "lattice": f"{pb.nx}x{pb.ny}", "forward_steps": pb.n_steps,
+        "config": {"workload": desc,
+                   "lattice": f"{pb.nx}x{pb.ny}" + (f"x{pb.nz}" if three_d else ""), "forward_steps": pb.n_steps,
                    "adjoint_steps": pb.n_adj, "l2": "flushed between timed steps (256 MB write)",
                    "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3},
         "roofline": roofline,
@@ -498,7 +519,7 @@ def main():
     if not args.no_cpu_baseline:
         try:
             out["cpu_baseline"] = cpu_baseline(pb, 40, 40) if args.workload == "config2" else \
-                cpu_baseline(pb, 5, 5)
+                cpu_baseline(pb, 2, 2) if three_d else cpu_baseline(pb, 5, 5)
         except Exception as e:  # the oracle is a reported baseline, not the product
             out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
     print(json.dumps(out))

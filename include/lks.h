@@ -98,8 +98,24 @@ typedef struct {
     int32_t exec_path;        /* lks_exec_path: 0 automatic, 1 one kernel launch per
                                  step, 2 resident persistent march (steady problems
                                  whose tiles fit on the GPU at once)                 */
-    int32_t reserved[7];      /* must be zero                                        */
+    int32_t lattice;          /* lks_lattice: 0 D2Q9 (default), 1 D3Q19 (see below)   */
+    int32_t nz;               /* D3Q19: nodes along z, >= 5; D2Q9: 0 or 1            */
+    int32_t reserved[5];      /* must be zero                                        */
 } lks_problem_desc;
+
+/* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in
+ * two dimensions (Secs. 2.4-2.5) and names three as the extension (Sec. 4); the
+ * D3Q19 form writes the same equations for 19 velocities (w = 1/3, 1/18, 1/36;
+ * nu = 1/6 - 2A/9 unchanged).  Geometry: a duct, inlet over the face x = 0 with
+ * u_x = u_max 16 y(1-y) z(1-z) (y, z scaled to [0, 1]), prescribed pressure on the
+ * face x = nx-1, walls on the four side faces; nodes on two or three faces are wall
+ * nodes.  Steady and non-thermal only (steady = 1, thermal = 0); the inlet and
+ * outlet spans, pulse, thermal and checkpoint fields are ignored.  Fields are
+ * nx*ny*nz values, x fastest, then y, then z.  lks_get_state returns w through its
+ * T pointer; alks_get_adjoint fills 10 fields (rho~, u~x, u~y, u~z, s~xx, s~xy,
+ * s~xz, s~yy, s~yz, s~zz).  lks_set_state, lks_march, alks_set_adjoint, alks_march
+ * and lks_gradient_noalloc answer LKS_ERR_INVALID_ARG for a D3Q19 handle. */
+typedef enum { LKS_LATTICE_D2Q9 = 0, LKS_LATTICE_D3Q19 = 1 } lks_lattice;
 
 /* Counters and the device status word, filled by lks_query. */
 typedef struct {

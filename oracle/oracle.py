@@ -515,3 +515,20 @@ def bc_flow3(n, pressure: bool, A: float, known: np.ndarray, unknown_mask):
     mult = np.zeros(3)
     lib().orc3_bc_flow(nn, int(pressure), float(A), um, _p(f), _p(mult))
     return f, mult
+
+
+def forward_node3(pb, gamma, st: State3, i: int, j: int, k: int) -> np.ndarray:
+    """(rho, u, v, w) at one node after one step from the state st."""
+    o = np.zeros(4)
+    lib().orc3_forward_node(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.rho), _pp(st.vel()), int(i),
+                            int(j), int(k), _p(o))
+    return o
+
+
+def adjoint_node3(pb, gamma, PV: np.ndarray, st0: State3, i: int, j: int, k: int) -> np.ndarray:
+    """Adjoint moments at one node from the coefficients PV of the previous level."""
+    o = np.zeros(NADJ3)
+    c = [np.ascontiguousarray(PV[q], dtype=np.float64) for q in range(4)]
+    lib().orc3_adjoint_node(C.byref(make_problem3(pb)), _p(_g(gamma)), _pp(c), _pp(st0.vel()), int(i), int(j),
+                            int(k), _p(o))
+    return o

@@ -1,0 +1,829 @@
+// lks_3d.cu -- the three-dimensional (D3Q19) steady duct path: LKS forward march,
+// ALKS adjoint iteration with the generalized-inverse face rules, sensitivity.
+//
+// The paper (arXiv 2411.03090) states LKS and ALKS in two dimensions (Secs.
+// 2.4-2.5, App. A); here every equation is written for 19 velocities:
+//   forward   f_k^eq = w_k { rho + 3 c.u + 9/2 (c.u)^2 - 3/2 u^2 + A c_a c_b S_ab }
+//             (Eq. feq2), streamed from x - c_k, rho = sum f, u = sum c f / (1+alpha)
+//   adjoint   f~_k = P(x + c_k) + c_k . V(x + c_k),  P = rho~,
+//             V_a = 3 (u~_a + 3 s~_ab u_b - rho~ u_a) - 2A d_b s~_ab  (Eq. afeq);
+//             moments rho~, u~ (implicit Brinkman, objective source), s~
+//   faces     Zou-He-type density / normal velocity (inlet velocity, outlet
+//             pressure, walls); the adjoint's unknown f~ by least squares over the
+//             19 rows (Sec. 2.5, Eq. r_definition), folded into 10 x 19 maps.
+//
+// Kernel structure (2.5-D march).  Each CTA owns a 32 x 8 column of output nodes
+// and marches a chunk of z planes.  Staged planes of the input fields sit in a
+// ring in shared memory (a two-node halo in x and y).  The forward step keeps the
+// pushed populations of the halo-1 ring grouped by c_z: the five links with
+// c_z = +1 are consumed two planes later, the nine with c_z = 0 one plane later,
+// the five with c_z = -1 at once, so three, two and one plane of them are kept.
+// The adjoint keeps P and V of three planes.  Every node's arithmetic is that of
+// the per-node formulas above; there is no blocking of the mathematics itself.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <type_traits>
+#include <vector>
+
+#include "lks_3d.cuh"
+#include "lks_kernels.cuh"
+
+namespace lks3 {
+
+using lks::block_sum;
+using lks::NTHREADS;
+using lks::raise_status;
+using lks::reduce_partials_kernel;
+
+constexpr int TX3 = 32, TY3 = 8, NT3 = TX3 * TY3, ZC3 = 32;
+constexpr int HX3 = TX3 + 4, HY3 = TY3 + 4, HA3 = HX3 * HY3;  // plane box with a 2-node halo
+constexpr int PX3 = TX3 + 2, PY3 = TY3 + 2, PA3 = PX3 * PY3;  // plane box with a 1-node halo
+
+// D3Q19 velocities: rest, six faces, twelve edges.
+__host__ __device__ constexpr int c3(int k, int a) {
+  constexpr int c[19][3] = {{0, 0, 0},  {1, 0, 0},   {-1, 0, 0}, {0, 1, 0},  {0, -1, 0}, {0, 0, 1},  {0, 0, -1},
+                            {1, 1, 0},  {-1, -1, 0}, {1, -1, 0}, {-1, 1, 0}, {1, 0, 1},  {-1, 0, -1}, {1, 0, -1},
+                            {-1, 0, 1}, {0, 1, 1},   {0, -1, -1}, {0, 1, -1}, {0, -1, 1}};
+  return c[k][a];
+}
+__host__ __device__ constexpr double w3d(int k) { return k == 0 ? 1.0 / 3.0 : (k < 7 ? 1.0 / 18.0 : 1.0 / 36.0); }
+// Link group by c_z (0: c_z = 0, 1: c_z = +1, 2: c_z = -1) and slot in its group.
+__host__ __device__ constexpr int grp3(int k) { return c3(k, 2) == 0 ? 0 : (c3(k, 2) > 0 ? 1 : 2); }
+__host__ __device__ constexpr int slot3(int k) {
+  int s = 0;
+  for (int q = 0; q < k; ++q)
+    if (grp3(q) == grp3(k)) ++s;
+  return s;
+}
+
+// Compile-time loop over the lattice links: every link index, velocity, weight and
+// slot inside fn is a constant expression.
+template <int B, int E, typename Fn>
+__device__ __forceinline__ void static_for(Fn&& fn) {
+  if constexpr (B < E) {
+    fn(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(fn);
+  }
+}
+
+__device__ __forceinline__ int mod5(int p) { return (p + 10) % 5; }
+__device__ __forceinline__ int mod3(int p) { return (p + 9) % 3; }
+__device__ __forceinline__ int mod2(int p) { return (p + 8) & 1; }
+
+template <typename R>
+struct Coef3 {
+  R A, nu, alpha_bar, q_alpha, drho_out;
+  double u_max;
+};
+struct Geom3 {
+  int nx, ny, nz;
+};
+
+template <typename R>
+__device__ __forceinline__ R alpha3(const Coef3<R>& c, R g) {
+  return c.alpha_bar * c.q_alpha * (R(1) - g) / (c.q_alpha + g);
+}
+template <typename R>
+__device__ __forceinline__ R dalpha3(const Coef3<R>& c, R g) {
+  const R d = c.q_alpha + g;
+  return -c.alpha_bar * c.q_alpha * (R(1) + c.q_alpha) / (d * d);
+}
+
+// Derivative along an axis from values spaced `stride` apart around f[0]: central
+// inside, second-order one-sided on the faces (at = index along the axis).
+template <typename R>
+__device__ __forceinline__ R dax(const R* f, int stride, int at, int n) {
+  if (at == 0) return (R(-3) * f[0] + R(4) * f[stride] - f[2 * stride]) * R(0.5);
+  if (at == n - 1) return (R(3) * f[0] - R(4) * f[-stride] + f[-2 * stride]) * R(0.5);
+  return (f[stride] - f[-stride]) * R(0.5);
+}
+// The same along z through a ring of planes: plane(dz) returns the value dz planes away.
+template <typename R, typename Pl>
+__device__ __forceinline__ R daz(Pl plane, int p, int nz) {
+  if (p == 0) return (R(-3) * plane(0) + R(4) * plane(1) - plane(2)) * R(0.5);
+  if (p == nz - 1) return (R(3) * plane(0) - R(4) * plane(-1) + plane(-2)) * R(0.5);
+  return (plane(1) - plane(-1)) * R(0.5);
+}
+
+__device__ __forceinline__ size_t gidx(const Geom3& g, int i, int j, int k) {
+  return ((size_t)k * g.ny + j) * g.nx + i;
+}
+
+// Loads plane p of nf fields (halo h in x and y) into dst[f][box]; zeros outside.
+template <typename R, int NF, int H>
+__device__ __forceinline__ void load_plane(R* dst, const R* const* src, const Geom3& g, int x0, int y0, int p) {
+  constexpr int BX = TX3 + 2 * H, BA = BX * (TY3 + 2 * H);
+  const bool pin = p >= 0 && p < g.nz;
+  for (int q = threadIdx.x; q < NF * BA; q += NT3) {
+    const int f = q / BA, r = q - f * BA;
+    const int ly = r / BX, lx = r - ly * BX;
+    const int i = x0 - H + lx, j = y0 - H + ly;
+    R v = R(0);
+    if (pin && i >= 0 && i < g.nx && j >= 0 && j < g.ny) v = src[f][gidx(g, i, j, p)];
+    dst[f * BA + r] = v;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Forward
+// ------------------------------------------------------------------------------------
+template <typename R>
+struct Fwd3Args {
+  const R* in[4];  // drho, u, v, w
+  R* out[4];
+  const R* binv;   // 1 / (1 + alpha_gamma)
+  int* status;
+};
+
+template <typename R>
+constexpr size_t fwd3_smem() {
+  return sizeof(R) * (size_t)(5 * 4 * HA3 + 3 * 5 * PA3 + 2 * 9 * PA3 + 5 * PA3);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT3) fwd3_kernel(const __grid_constant__ Fwd3Args<R> a, Geom3 g, Coef3<R> c) {
+  extern __shared__ unsigned char smem3[];
+  R* stg = reinterpret_cast<R*>(smem3);  // [5 planes][4 fields][HA3]
+  R* up = stg + 5 * 4 * HA3;             // [3 planes][5 links][PA3]  c_z = +1
+  R* mid = up + 3 * 5 * PA3;             // [2 planes][9 links][PA3]  c_z = 0
+  R* dn = mid + 2 * 9 * PA3;             // [5 links][PA3]            c_z = -1
+  const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
+  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, g.nz);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+
+  auto load = [&](int p) { load_plane<R, 4, 2>(stg + mod5(p) * 4 * HA3, a.in, g, x0, y0, p); };
+
+  // Pushed populations of plane p on the halo-1 ring, for the link groups asked.
+  auto push = [&](int p, bool want_up, bool want_mid, bool want_dn) {
+    if (p < 0 || p >= nz) return;
+    for (int q = threadIdx.x; q < PA3; q += NT3) {
+      const int ly = q / PX3, lx = q - ly * PX3;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (i < 0 || i >= nx || j < 0 || j >= ny) continue;
+      const int off = (ly + 1) * HX3 + (lx + 1);
+      auto fld = [&](int f, int dz) { return stg + (mod5(p + dz) * 4 + f) * HA3 + off; };
+      R uu[3], gr[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R* f0 = fld(1 + d, 0);
+        uu[d] = f0[0];
+        gr[d][0] = dax(f0, 1, i, nx);
+        gr[d][1] = dax(f0, HX3, j, ny);
+        gr[d][2] = daz<R>([&](int dz) { return fld(1 + d, dz)[0]; }, p, nz);
+      }
+      const bool on[3] = {i == 0 || i == nx - 1, j == 0 || j == ny - 1, p == 0 || p == nz - 1};
+      const int faces = (int)on[0] + (int)on[1] + (int)on[2];
+      if (faces == 1) {  // continuity: normal derivative of the normal component
+        if (on[0]) gr[0][0] = -(gr[1][1] + gr[2][2]);
+        else if (on[1]) gr[1][1] = -(gr[0][0] + gr[2][2]);
+        else gr[2][2] = -(gr[0][0] + gr[1][1]);
+      } else if (faces >= 2) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (on[d]) gr[d][d] = R(0);
+      }
+      const R e0 = R(-1.5) * (uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+      const R bx = R(3) * uu[0], by = R(3) * uu[1], bz = R(3) * uu[2];
+      const R Qxx = R(4.5) * uu[0] * uu[0] + c.A * (R(2) * gr[0][0]);
+      const R Qyy = R(4.5) * uu[1] * uu[1] + c.A * (R(2) * gr[1][1]);
+      const R Qzz = R(4.5) * uu[2] * uu[2] + c.A * (R(2) * gr[2][2]);
+      const R Qxy = R(9) * uu[0] * uu[1] + R(2) * c.A * (gr[0][1] + gr[1][0]);
+      const R Qxz = R(9) * uu[0] * uu[2] + R(2) * c.A * (gr[0][2] + gr[2][0]);
+      const R Qyz = R(9) * uu[1] * uu[2] + R(2) * c.A * (gr[1][2] + gr[2][1]);
+      const R dr = fld(0, 0)[0];
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int gk = grp3(k), sl = slot3(k);
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        if ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
+        const R dest = fld(0, cz)[cy * HX3 + cx];
+        const R qk = R(cx * cx) * Qxx + R(cy * cy) * Qyy + R(cz * cz) * Qzz + R(cx * cy) * Qxy + R(cx * cz) * Qxz +
+                     R(cy * cz) * Qyz;
+        const R val = R(w3d(k)) * (((dr - dest) + e0) + (R(cx) * bx + R(cy) * by + R(cz) * bz) + qk);
+        if (gk == 0) mid[(mod2(p) * 9 + sl) * PA3 + q] = val;
+        else if (gk == 1) up[(mod3(p) * 5 + sl) * PA3 + q] = val;
+        else dn[sl * PA3 + q] = val;
+      });
+    }
+  };
+
+  // New state of output plane z.
+  auto gather = [&](int z) {
+    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
+    const int i = x0 + tx, j = y0 + ty;
+    if (i >= nx || j >= ny) return;
+    const int q1 = (ty + 1) * PX3 + (tx + 1);
+    R F[19];
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), gk = grp3(k), sl = slot3(k);
+      const int qs = q1 - cy * PX3 - cx;  // source x - c_k
+      if (gk == 0) F[k] = mid[(mod2(z) * 9 + sl) * PA3 + qs];
+      else if (gk == 1) F[k] = up[(mod3(z - 1) * 5 + sl) * PA3 + qs];
+      else F[k] = dn[sl * PA3 + qs];
+    });
+    const int off = (ty + 2) * HX3 + (tx + 2);
+    const R drx = stg[(mod5(z) * 4 + 0) * HA3 + off];
+    const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+    const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+    const int n2 = z == 0 ? -1 : (z == nz - 1 ? 1 : 0);
+    const int faces = abs(n0) + abs(n1) + abs(n2);
+    R drn, uo[3] = {R(0), R(0), R(0)};
+    if (faces == 0) {
+      R s = R(0), mx = R(0), my = R(0), mz = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        s += F[k];
+        if constexpr (c3(k, 0) != 0) mx += R(c3(k, 0)) * F[k];
+        if constexpr (c3(k, 1) != 0) my += R(c3(k, 1)) * F[k];
+        if constexpr (c3(k, 2) != 0) mz += R(c3(k, 2)) * F[k];
+      });
+      drn = drx + s;
+      const R inv = a.binv[gidx(g, i, j, z)];
+      uo[0] = mx * inv;
+      uo[1] = my * inv;
+      uo[2] = mz * inv;
+    } else if (faces >= 2) {  // wall node on two or three faces
+      const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
+      const int kn = (z == 0) ? 1 : (z == nz - 1 ? -1 : 0);
+      drn = stg[(mod5(z + kn) * 4 + 0) * HA3 + off + jn * HX3];
+    } else {
+      R s0 = R(0), sp = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        const int si = i - cx, sj = j - cy, sk = z - cz;
+        if (si < 0 || si >= nx || sj < 0 || sj >= ny || sk < 0 || sk >= nz) return;
+        const int cn = cx * n0 + cy * n1 + cz * n2;
+        if (cn == 0) s0 += F[k];
+        else if (cn > 0) sp += F[k];
+      });
+      if (n0 == 1) {  // outlet: prescribed pressure, tangential velocity zero
+        drn = c.drho_out;
+        uo[0] = (s0 + R(2) * sp) + (drx - c.drho_out);
+      } else {
+        if (n0 == -1) {
+          const double y = (double)j / (double)(ny - 1), zz = (double)z / (double)(nz - 1);
+          uo[0] = (R)(c.u_max * 16.0 * y * (1.0 - y) * zz * (1.0 - zz));
+        }
+        drn = drx + (s0 + R(2) * sp - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2)));
+      }
+    }
+    const size_t o = gidx(g, i, j, z);
+    a.out[0][o] = drn;
+    a.out[1][o] = uo[0];
+    a.out[2][o] = uo[1];
+    a.out[3][o] = uo[2];
+    const R m = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
+    if (!(m <= R(0.25))) raise_status(a.status, 4);
+  };
+
+  for (int p = z0 - 2; p <= z0 + 2; ++p) load(p);
+  __syncthreads();
+  push(z0 - 1, true, false, false);
+  push(z0, true, true, false);
+  __syncthreads();
+  for (int z = z0; z < z1; ++z) {
+    load(z + 3);
+    __syncthreads();
+    push(z + 1, true, true, true);
+    __syncthreads();
+    gather(z);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Adjoint
+// ------------------------------------------------------------------------------------
+template <typename R>
+struct Adj3Args {
+  const R* m1[kNA3];  // adjoint at level t+1: rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz
+  R* m0[kNA3];        // adjoint at level t
+  const R* u[3];      // state (frozen)
+  const R* binv;
+  const R* src[3];    // objective source -(1/3) dJ_O/du
+  const R* emap;      // kClasses3 x 10 x 19
+  int* status;
+  const R* zs[3];     // staged with a plane ring: s~xz, s~yz, s~zz
+  const R* ps[3];     // staged for one plane: s~xx, s~xy, s~yy
+  const R* ns[7];     // staged for one plane on the halo-1 ring: rho~, u~ (3), u (3)
+};
+
+template <typename R>
+constexpr size_t adj3_smem() {
+  return sizeof(R) * (size_t)(5 * 3 * HA3 + 3 * HA3 + 7 * PA3 + 3 * 4 * PA3);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NT3) adj3_kernel(const __grid_constant__ Adj3Args<R> a, Geom3 g, Coef3<R> c) {
+  extern __shared__ unsigned char smem3[];
+  R* szr = reinterpret_cast<R*>(smem3);  // [5 planes][s~xz, s~yz, s~zz][HA3]
+  R* spl = szr + 5 * 3 * HA3;            // [s~xx, s~xy, s~yy][HA3] of plane p
+  R* nd = spl + 3 * HA3;                 // [rho~, u~x, u~y, u~z, u, v, w][PA3] of plane p
+  R* PV = nd + 7 * PA3;                  // [3 planes][P, Vx, Vy, Vz][PA3]
+  const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
+  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, g.nz);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  auto load_ring = [&](int p) { load_plane<R, 3, 2>(szr + mod5(p) * 3 * HA3, a.zs, g, x0, y0, p); };
+  auto load_pl = [&](int p) {
+    load_plane<R, 3, 2>(spl, a.ps, g, x0, y0, p);
+    load_plane<R, 7, 1>(nd, a.ns, g, x0, y0, p);
+  };
+  // P and V of plane p on the halo-1 ring (Eq. afeq); zero off the lattice.
+  auto coefs = [&](int p) {
+    R* out = PV + mod3(p) * 4 * PA3;
+    for (int q = threadIdx.x; q < PA3; q += NT3) {
+      const int ly = q / PX3, lx = q - ly * PX3;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (p < 0 || p >= nz || i < 0 || i >= nx || j < 0 || j >= ny) {
+        out[q] = out[PA3 + q] = out[2 * PA3 + q] = out[3 * PA3 + q] = R(0);
+        continue;
+      }
+      const int off = (ly + 1) * HX3 + (lx + 1);
+      auto ring = [&](int f, int dz) { return szr[(mod5(p + dz) * 3 + f) * HA3 + off]; };
+      const R* sxx = spl + off;
+      const R* sxy = spl + HA3 + off;
+      const R* syy = spl + 2 * HA3 + off;
+      const R* sxz = szr + (mod5(p) * 3 + 0) * HA3 + off;
+      const R* syz = szr + (mod5(p) * 3 + 1) * HA3 + off;
+      const R Dx = R(2) * (dax(sxx, 1, i, nx) + dax(sxy, HX3, j, ny) + daz<R>([&](int dz) { return ring(0, dz); }, p, nz));
+      const R Dy = R(2) * (dax(sxy, 1, i, nx) + dax(syy, HX3, j, ny) + daz<R>([&](int dz) { return ring(1, dz); }, p, nz));
+      const R Dz = R(2) * (dax(sxz, 1, i, nx) + dax(syz, HX3, j, ny) + daz<R>([&](int dz) { return ring(2, dz); }, p, nz));
+      const R rt = nd[q], ux = nd[PA3 + q], uy = nd[2 * PA3 + q], uz = nd[3 * PA3 + q];
+      const R u0 = nd[4 * PA3 + q], u1 = nd[5 * PA3 + q], u2 = nd[6 * PA3 + q];
+      const R vxx = sxx[0], vxy = sxy[0], vyy = syy[0], vxz = sxz[0], vyz = syz[0], vzz = ring(2, 0);
+      out[q] = rt;
+      out[PA3 + q] = R(3) * (ux + R(3) * (vxx * u0 + vxy * u1 + vxz * u2) - rt * u0) - c.A * Dx;
+      out[2 * PA3 + q] = R(3) * (uy + R(3) * (vxy * u0 + vyy * u1 + vyz * u2) - rt * u1) - c.A * Dy;
+      out[3 * PA3 + q] = R(3) * (uz + R(3) * (vxz * u0 + vyz * u1 + vzz * u2) - rt * u2) - c.A * Dz;
+    }
+  };
+  // Adjoint moments of output plane z.
+  auto gather = [&](int z) {
+    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
+    const int i = x0 + tx, j = y0 + ty;
+    if (i >= nx || j >= ny) return;
+    const int q1 = (ty + 1) * PX3 + (tx + 1);
+    const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+    const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+    const int n2 = z == 0 ? -1 : (z == nz - 1 ? 1 : 0);
+    const bool edge = (n0 | n1 | n2) != 0;
+    R f[19];
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+      const R* pv = PV + mod3(z + cz) * 4 * PA3 + q1 + cy * PX3 + cx;
+      R v = pv[0];
+      if constexpr (cx != 0) v += R(cx) * pv[PA3];
+      if constexpr (cy != 0) v += R(cy) * pv[2 * PA3];
+      if constexpr (cz != 0) v += R(cz) * pv[3 * PA3];
+      f[k] = v;
+      if (edge) {
+        const int gi = i + cx, gj = j + cy, gk = z + cz;
+        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny || gk < 0 || gk >= nz) f[k] = R(0);
+      }
+    });
+    R m[kNA3];
+    const size_t o = gidx(g, i, j, z);
+    if (!edge) {
+#pragma unroll
+      for (int r = 0; r < kNA3; ++r) m[r] = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        const R wf = R(w3d(k)) * f[k];
+        m[0] += wf;
+        if constexpr (cx != 0) m[1] += R(cx) * wf;
+        if constexpr (cy != 0) m[2] += R(cy) * wf;
+        if constexpr (cz != 0) m[3] += R(cz) * wf;
+        if constexpr (cx != 0) m[4] += wf;
+        if constexpr (cx * cy != 0) m[5] += R(cx * cy) * wf;
+        if constexpr (cx * cz != 0) m[6] += R(cx * cz) * wf;
+        if constexpr (cy != 0) m[7] += wf;
+        if constexpr (cy * cz != 0) m[8] += R(cy * cz) * wf;
+        if constexpr (cz != 0) m[9] += wf;
+      });
+      const R inv = a.binv[o];
+      m[1] = (m[1] + a.src[0][o]) * inv;
+      m[2] = (m[2] + a.src[1][o]) * inv;
+      m[3] = (m[3] + a.src[2][o]) * inv;
+    } else {
+      const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+#pragma unroll
+      for (int r = 0; r < kNA3; ++r) {
+        R s = R(0);
+        static_for<0, 19>([&](auto kk) {
+          constexpr int k = decltype(kk)::value;
+          s += M[r * 19 + k] * f[k];
+        });
+        m[r] = s;
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
+    if (!(m[1] * m[1] + m[2] * m[2] + m[3] * m[3] < R(1e30))) raise_status(a.status, 4);
+  };
+
+  for (int p = z0 - 2; p <= z0 + 2; ++p) load_ring(p);
+  load_pl(z0 - 1);
+  __syncthreads();
+  coefs(z0 - 1);
+  __syncthreads();
+  load_pl(z0);
+  __syncthreads();
+  coefs(z0);
+  __syncthreads();
+  for (int z = z0; z < z1; ++z) {
+    load_ring(z + 3);
+    load_pl(z + 1);
+    __syncthreads();
+    coefs(z + 1);
+    __syncthreads();
+    gather(z);
+    __syncthreads();
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Pointwise kernels: material, objective source, objective, sensitivity
+// ------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ bool interior3(const Geom3& g, int i, int j, int k) {
+  return i > 0 && j > 0 && k > 0 && i < g.nx - 1 && j < g.ny - 1 && k < g.nz - 1;
+}
+// S_ab = du_a/dx_b + du_b/dx_a at an interior node (central differences).
+template <typename R>
+__device__ __forceinline__ R strain3(const R* const* u, const Geom3& g, int i, int j, int k, int a, int b) {
+  const size_t o = gidx(g, i, j, k);
+  const size_t st[3] = {1, (size_t)g.nx, (size_t)g.nx * g.ny};
+  return (u[a][o + st[b]] - u[a][o - st[b]]) * R(0.5) + (u[b][o + st[a]] - u[b][o - st[a]]) * R(0.5);
+}
+
+// binv = 1/(1+alpha) and src_a = -(1/3) dJ_O/du_a of the frozen state:
+//   dJ_O/du_a = nu sum_d [S_ad(x - e_d) - S_ad(x + e_d)] (interior neighbours)
+//               + 2 alpha u_a (interior x).
+template <typename R>
+__global__ void src3_kernel(const R* __restrict__ gamma, const R* u0, const R* u1, const R* u2, Geom3 g, Coef3<R> c,
+                            R* __restrict__ binv, R* __restrict__ s0, R* __restrict__ s1, R* __restrict__ s2) {
+  const R* u[3] = {u0, u1, u2};
+  R* s[3] = {s0, s1, s2};
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < N; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / ((size_t)g.nx * g.ny));
+    const R al = alpha3(c, gamma[o]);
+    binv[o] = R(1) / (R(1) + al);
+    const bool in = interior3<R>(g, i, j, k);
+    for (int aa = 0; aa < 3; ++aa) {
+      R acc = R(0);
+      for (int d = 0; d < 3; ++d) {
+        const int di = d == 0, dj = d == 1, dk = d == 2;
+        if (interior3<R>(g, i - di, j - dj, k - dk)) acc += strain3(u, g, i - di, j - dj, k - dk, aa, d);
+        if (interior3<R>(g, i + di, j + dj, k + dk)) acc -= strain3(u, g, i + di, j + dj, k + dk, aa, d);
+      }
+      acc *= c.nu;
+      if (in) acc += R(2) * al * u[aa][o];
+      s[aa][o] = -acc / R(3);
+    }
+  }
+}
+
+template <typename R>
+__global__ void __launch_bounds__(NTHREADS) objective3_kernel(const R* __restrict__ gamma, const R* u0, const R* u1,
+                                                              const R* u2, Geom3 g, Coef3<R> c, double* partial) {
+  __shared__ double red[NTHREADS / 32];
+  const R* u[3] = {u0, u1, u2};
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  double acc = 0.0;
+  for (size_t o = (size_t)blockIdx.x * NTHREADS + threadIdx.x; o < N; o += (size_t)gridDim.x * NTHREADS) {
+    const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / ((size_t)g.nx * g.ny));
+    if (!interior3<R>(g, i, j, k)) continue;
+    R SS = R(0), uu = R(0);
+    for (int aa = 0; aa < 3; ++aa) {
+      uu += u[aa][o] * u[aa][o];
+      for (int b = 0; b < 3; ++b) {
+        const R s = strain3(u, g, i, j, k, aa, b);
+        SS += s * s;
+      }
+    }
+    acc += (double)(R(0.5) * c.nu * SS + alpha3(c, gamma[o]) * uu);
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// dJ/dgamma of the steady state: alpha' |u|^2 + 3 alpha' u.u~ at interior nodes.
+template <typename R>
+__global__ void sens3_kernel(const R* __restrict__ gamma, const R* u0, const R* u1, const R* u2, const R* a1,
+                             const R* a2, const R* a3, Geom3 g, Coef3<R> c, R* __restrict__ out) {
+  const size_t N = (size_t)g.nx * g.ny * g.nz;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < N; o += (size_t)gridDim.x * blockDim.x) {
+    const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / ((size_t)g.nx * g.ny));
+    R s = R(0);
+    if (interior3<R>(g, i, j, k)) {
+      const R da = dalpha3(c, gamma[o]);
+      const R x = u0[o], y = u1[o], z = u2[o];
+      s = da * (x * x + y * y + z * z) + R(3) * da * (x * a1[o] + y * a2[o] + z * a3[o]);
+    }
+    out[o] = s;
+  }
+}
+
+// ------------------------------------------------------------------------------------
+// Host side
+// ------------------------------------------------------------------------------------
+namespace {
+
+size_t up256(size_t x) { return (x + 255) / 256 * 256; }
+
+template <typename R>
+Coef3<R> coef3(const lks_problem_desc& d) {
+  Coef3<R> c;
+  c.A = (R)((1.0 / 6.0 - d.nu) * 4.5);
+  c.nu = (R)d.nu;
+  c.alpha_bar = (R)d.alpha_bar;
+  c.q_alpha = (R)d.q_alpha;
+  c.drho_out = (R)(d.rho_out - 1.0);
+  c.u_max = d.u_max;
+  return c;
+}
+Geom3 geom3(const lks_problem_desc& d) { return Geom3{d.nx, d.ny, d.nz}; }
+
+lks_status fail3(const Ctx3& c, lks_status s, const std::string& m) {
+  if (c.err) *c.err = m;
+  return s;
+}
+#define CK3(c, call)                                                                      \
+  do {                                                                                    \
+    cudaError_t e_ = (call);                                                              \
+    if (e_ != cudaSuccess)                                                                \
+      return fail3(c, LKS_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+template <typename R>
+R* fld3(const Ctx3& c, size_t off, int k = 0) {
+  return reinterpret_cast<R*>(c.ws + off) + (size_t)k * c.L->N;
+}
+template <typename R>
+R* st3(const Ctx3& c, int which, int f) {
+  return fld3<R>(c, which == 0 ? c.L->stA : c.L->stB, f);
+}
+template <typename R>
+R* ad3(const Ctx3& c, int which, int f) {
+  return fld3<R>(c, which == 0 ? c.L->adA : c.L->adB, f);
+}
+int ew_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+dim3 march_grid(const lks_problem_desc& d) {
+  return dim3((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + ZC3 - 1) / ZC3);
+}
+
+template <typename R>
+lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur_out) {
+  const auto& d = *c.d;
+  const auto& L = *c.L;
+  const size_t fb = L.N * sizeof(R);
+  if (gamma_dev != c.ws + L.gamma)
+    CK3(c, cudaMemcpyAsync(c.ws + L.gamma, gamma_dev, fb, cudaMemcpyDeviceToDevice, c.stream));
+  CK3(c, cudaMemsetAsync(c.ws + L.stA, 0, fb * 4, c.stream));
+  CK3(c, cudaMemsetAsync(c.ws + L.status, 0, sizeof(int), c.stream));
+  const Geom3 g = geom3(d);
+  const Coef3<R> cf = coef3<R>(d);
+  const R* gam = fld3<R>(c, L.gamma);
+  // 1/(1+alpha) (the objective source is not needed for the forward march)
+  src3_kernel<R><<<ew_grid(L.N), 256, 0, c.stream>>>(gam, st3<R>(c, 0, 1), st3<R>(c, 0, 2), st3<R>(c, 0, 3), g, cf,
+                                                     fld3<R>(c, L.binv), fld3<R>(c, L.src, 0), fld3<R>(c, L.src, 1),
+                                                     fld3<R>(c, L.src, 2));
+  CK3(c, cudaGetLastError());
+  ++*c.launches;
+  const size_t smem = fwd3_smem<R>();
+  CK3(c, cudaFuncSetAttribute(fwd3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int cur = 0;
+  for (int s = 0; s < d.n_steps; ++s) {
+    Fwd3Args<R> a;
+    for (int f = 0; f < 4; ++f) {
+      a.in[f] = st3<R>(c, cur, f);
+      a.out[f] = st3<R>(c, 1 - cur, f);
+    }
+    a.binv = fld3<R>(c, L.binv);
+    a.status = reinterpret_cast<int*>(c.ws + L.status);
+    fwd3_kernel<R><<<march_grid(d), NT3, smem, c.stream>>>(a, g, cf);
+    CK3(c, cudaGetLastError());
+    ++*c.launches;
+    cur = 1 - cur;
+  }
+  double* part = reinterpret_cast<double*>(c.ws + L.jpart);
+  double* jval = reinterpret_cast<double*>(c.ws + L.jval);
+  objective3_kernel<R><<<L.jblocks, NTHREADS, 0, c.stream>>>(gam, st3<R>(c, cur, 1), st3<R>(c, cur, 2),
+                                                             st3<R>(c, cur, 3), g, cf, part);
+  reduce_partials_kernel<<<1, NTHREADS, 0, c.stream>>>(part, L.jblocks, nullptr, 0, jval);
+  CK3(c, cudaGetLastError());
+  *c.launches += 2;
+  if (J_dev) CK3(c, cudaMemcpyAsync(J_dev, jval, sizeof(double), cudaMemcpyDeviceToDevice, c.stream));
+  *cur_out = cur;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out) {
+  const auto& d = *c.d;
+  const auto& L = *c.L;
+  const size_t fb = L.N * sizeof(R);
+  const Geom3 g = geom3(d);
+  const Coef3<R> cf = coef3<R>(d);
+  const R* gam = fld3<R>(c, L.gamma);
+  src3_kernel<R><<<ew_grid(L.N), 256, 0, c.stream>>>(gam, st3<R>(c, cur, 1), st3<R>(c, cur, 2), st3<R>(c, cur, 3), g,
+                                                     cf, fld3<R>(c, L.binv), fld3<R>(c, L.src, 0),
+                                                     fld3<R>(c, L.src, 1), fld3<R>(c, L.src, 2));
+  CK3(c, cudaGetLastError());
+  ++*c.launches;
+  CK3(c, cudaMemsetAsync(c.ws + L.adA, 0, fb * kNA3, c.stream));
+  const size_t smem = adj3_smem<R>();
+  CK3(c, cudaFuncSetAttribute(adj3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int acur = 0;
+  for (int it = 0; it < d.n_adj; ++it) {
+    Adj3Args<R> a;
+    for (int q = 0; q < kNA3; ++q) {
+      a.m1[q] = ad3<R>(c, acur, q);
+      a.m0[q] = ad3<R>(c, 1 - acur, q);
+    }
+    for (int q = 0; q < 3; ++q) {
+      a.u[q] = st3<R>(c, cur, 1 + q);
+      a.src[q] = fld3<R>(c, L.src, q);
+    }
+    a.binv = fld3<R>(c, L.binv);
+    a.emap = reinterpret_cast<const R*>(c.ws + L.emap);
+    a.status = reinterpret_cast<int*>(c.ws + L.status);
+    const int zi[3] = {6, 8, 9}, pi[3] = {4, 5, 7};
+    for (int q = 0; q < 3; ++q) {
+      a.zs[q] = a.m1[zi[q]];
+      a.ps[q] = a.m1[pi[q]];
+    }
+    for (int q = 0; q < 4; ++q) a.ns[q] = a.m1[q];
+    for (int q = 0; q < 3; ++q) a.ns[4 + q] = a.u[q];
+    adj3_kernel<R><<<march_grid(d), NT3, smem, c.stream>>>(a, g, cf);
+    CK3(c, cudaGetLastError());
+    ++*c.launches;
+    acur = 1 - acur;
+  }
+  *acur_out = acur;
+  return LKS_OK;
+}
+
+template <typename R>
+lks_status sensitivity3_t(const Ctx3& c, int cur, int acur, void* out) {
+  const auto& L = *c.L;
+  sens3_kernel<R><<<ew_grid(L.N), 256, 0, c.stream>>>(
+      fld3<R>(c, L.gamma), st3<R>(c, cur, 1), st3<R>(c, cur, 2), st3<R>(c, cur, 3), ad3<R>(c, acur, 1),
+      ad3<R>(c, acur, 2), ad3<R>(c, acur, 3), geom3(*c.d), coef3<R>(*c.d), reinterpret_cast<R*>(out));
+  CK3(c, cudaGetLastError());
+  ++*c.launches;
+  return LKS_OK;
+}
+
+// Least squares by the normal equations with partial pivoting: m <= 19 rows,
+// columns that are identically zero are dropped (their unknowns are zero).
+void lsq19(const double* A, int nc, const double* rhs, double* x) {
+  int live[24], nl = 0;
+  for (int q = 0; q < nc; ++q) {
+    double s = 0.0;
+    for (int r = 0; r < 19; ++r) s += std::fabs(A[r * nc + q]);
+    x[q] = 0.0;
+    if (s > 0) live[nl++] = q;
+  }
+  double G[24][25];
+  for (int p = 0; p < nl; ++p) {
+    for (int q = 0; q < nl; ++q) {
+      double s = 0.0;
+      for (int r = 0; r < 19; ++r) s += A[r * nc + live[p]] * A[r * nc + live[q]];
+      G[p][q] = s;
+    }
+    double s = 0.0;
+    for (int r = 0; r < 19; ++r) s += A[r * nc + live[p]] * rhs[r];
+    G[p][nl] = s;
+  }
+  for (int col = 0; col < nl; ++col) {
+    int pv = col;
+    for (int r = col + 1; r < nl; ++r)
+      if (std::fabs(G[r][col]) > std::fabs(G[pv][col])) pv = r;
+    for (int q = 0; q <= nl; ++q) std::swap(G[col][q], G[pv][q]);
+    for (int r = 0; r < nl; ++r) {
+      if (r == col) continue;
+      const double f = G[r][col] / G[col][col];
+      for (int q = col; q <= nl; ++q) G[r][q] -= f * G[col][q];
+    }
+  }
+  for (int p = 0; p < nl; ++p) x[live[p]] = G[p][nl] / G[p][p];
+}
+
+}  // namespace
+
+void flow_moment_map3(double A, int cls, double* out) {
+  const int n[3] = {cls / 9 - 1, (cls / 3) % 3 - 1, cls % 3 - 1};
+  std::memset(out, 0, sizeof(double) * kNA3 * 19);
+  if (n[0] == 0 && n[1] == 0 && n[2] == 0) return;
+  const int faces = std::abs(n[0]) + std::abs(n[1]) + std::abs(n[2]);
+  const bool pressure = faces == 1 && n[0] == 1;
+  bool unk[19];
+  int U[19], nu = 0;
+  for (int k = 0; k < 19; ++k) {
+    unk[k] = false;
+    for (int a = 0; a < 3; ++a) unk[k] = unk[k] || c3(k, a) * n[a] > 0;
+    if (unk[k]) U[nu++] = k;
+  }
+  auto cdot = [](int k, const int* v) { return c3(k, 0) * v[0] + c3(k, 1) * v[1] + c3(k, 2) * v[2]; };
+  double M[19][19];
+  for (int r = 0; r < 19; ++r)
+    for (int q = 0; q < 19; ++q) {
+      const int cq[3] = {c3(q, 0), c3(q, 1), c3(q, 2)};
+      M[r][q] = (r == q ? (double)cdot(r, n) : 0.0) - 2.0 * A * w3d(q) * cdot(q, n) * cdot(r, cq);
+    }
+  const int nc = nu + 3;
+  std::vector<double> Am(19 * nc);
+  const int ax = n[0] != 0 ? 0 : (n[1] != 0 ? 1 : 2);
+  for (int r = 0; r < 19; ++r) {
+    for (int q = 0; q < nu; ++q) Am[r * nc + q] = M[r][U[q]];
+    if (pressure) {
+      Am[r * nc + nu] = 1.0;
+      Am[r * nc + nu + 1] = c3(r, (ax + 1) % 3);
+      Am[r * nc + nu + 2] = c3(r, (ax + 2) % 3);
+    } else {
+      for (int a = 0; a < 3; ++a) Am[r * nc + nu + a] = c3(r, a);
+    }
+  }
+  double X[19][19] = {};  // X[u][k]: unknown u per unit of the known f~_k
+  for (int k = 0; k < 19; ++k) {
+    if (unk[k]) continue;
+    double rhs[19], x[24];
+    for (int r = 0; r < 19; ++r) rhs[r] = -M[r][k];
+    lsq19(Am.data(), nc, rhs, x);
+    for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
+  }
+  auto mom = [](int r, int k) {
+    const double cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+    const double phi[kNA3] = {1, cx, cy, cz, cx * cx, cx * cy, cx * cz, cy * cy, cy * cz, cz * cz};
+    return w3d(k) * phi[r];
+  };
+  for (int r = 0; r < kNA3; ++r)
+    for (int k = 0; k < 19; ++k) {
+      if (unk[k]) continue;
+      double s = mom(r, k);
+      for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * X[U[q]][k];
+      out[r * 19 + k] = s;
+    }
+}
+
+Layout3 make_layout3(const lks_problem_desc& d) {
+  Layout3 L;
+  L.N = (size_t)d.nx * d.ny * d.nz;
+  L.rsize = d.real_type == LKS_REAL_F64 ? 8 : 4;
+  L.jblocks = (int)std::min<size_t>((L.N + NTHREADS - 1) / NTHREADS, 1024);
+  size_t off = 0;
+  auto take = [&](size_t b) {
+    const size_t o = off;
+    off = up256(off + b);
+    return o;
+  };
+  const size_t fb = L.N * L.rsize;
+  L.gamma = take(fb);
+  L.stA = take(fb * 4);
+  L.stB = take(fb * 4);
+  L.adA = take(fb * kNA3);
+  L.adB = take(fb * kNA3);
+  L.binv = take(fb);
+  L.src = take(fb * 3);
+  L.jpart = take(sizeof(double) * L.jblocks);
+  L.jval = take(sizeof(double));
+  L.status = take(sizeof(int));
+  L.emap = take(L.rsize * kClasses3 * kNA3 * 19);
+  L.total = off;
+  return L;
+}
+
+lks_status upload_maps3(const Ctx3& c) {
+  const double A = (1.0 / 6.0 - c.d->nu) * 4.5;
+  std::vector<double> m((size_t)kClasses3 * kNA3 * 19);
+  for (int cls = 0; cls < kClasses3; ++cls) flow_moment_map3(A, cls, &m[(size_t)cls * kNA3 * 19]);
+  if (c.L->rsize == 8) {
+    CK3(c, cudaMemcpy(c.ws + c.L->emap, m.data(), m.size() * 8, cudaMemcpyHostToDevice));
+  } else {
+    std::vector<float> f(m.begin(), m.end());
+    CK3(c, cudaMemcpy(c.ws + c.L->emap, f.data(), f.size() * 4, cudaMemcpyHostToDevice));
+  }
+  return LKS_OK;
+}
+
+lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur) {
+  return c.L->rsize == 8 ? forward3_t<double>(c, gamma_dev, J_dev, cur) : forward3_t<float>(c, gamma_dev, J_dev, cur);
+}
+lks_status adjoint3(const Ctx3& c, int cur, int* acur) {
+  return c.L->rsize == 8 ? adjoint3_t<double>(c, cur, acur) : adjoint3_t<float>(c, cur, acur);
+}
+lks_status sensitivity3(const Ctx3& c, int cur, int acur, void* out) {
+  return c.L->rsize == 8 ? sensitivity3_t<double>(c, cur, acur, out) : sensitivity3_t<float>(c, cur, acur, out);
+}
+
+}  // namespace lks3

@@ -20,6 +20,7 @@
 #include "../../include/lks.h"
 #include "lks_kernels.cuh"
 #include "lks_resident.cuh"
+#include "lks_3d.cuh"
 #include "lks_host.cuh"
 #include "lks_tma.cuh"
 
@@ -116,6 +117,8 @@ struct lks_handle {
   std::vector<float> emap_f;
   std::unordered_map<uint64_t, CUtensorMap> tmaps;  // (pointer, box) -> tensor map
   int tma_grid_fwd = 0, tma_grid_adj[2][2] = {{0, 0}, {0, 0}};  // adj: [thermal][same state]
+  bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
+  lks3::Layout3 L3;
   std::string err;
 };
 
@@ -870,6 +873,12 @@ lks_status upload_maps(lks_handle* h) {
 
 lks_status check_handle(lks_handle* h) { return h ? LKS_OK : LKS_ERR_INVALID_ARG; }
 
+lks3::Ctx3 ctx3(lks_handle* h) { return lks3::Ctx3{&h->d, &h->L3, h->ws, h->stream, &h->launches, &h->err}; }
+size_t status_off(const lks_handle* h) { return h->is3 ? h->L3.status : h->L.status; }
+lks_status reject3(lks_handle* h, const char* what) {
+  return fail(h, LKS_ERR_INVALID_ARG, std::string(what) + " is not available for a D3Q19 problem");
+}
+
 }  // namespace
 
 // ------------------------------------------------------------------------------------
@@ -897,7 +906,7 @@ lks_status lks_workspace_size(const lks_problem_desc* desc, size_t* bytes) {
   if (!bytes) return LKS_ERR_INVALID_ARG;
   lks_status s = check_desc(desc, nullptr);
   if (s != LKS_OK) return s;
-  *bytes = make_layout(desc).total;
+  *bytes = desc->lattice == LKS_LATTICE_D3Q19 ? lks3::make_layout3(*desc).total : make_layout(desc).total;
   return LKS_OK;
 }
 
@@ -908,6 +917,26 @@ lks_status lks_create(const lks_problem_desc* desc, void* workspace, size_t byte
   std::string why;
   lks_status s = check_desc(desc, &why);
   if (s != LKS_OK) return s;
+  if (desc->lattice == LKS_LATTICE_D3Q19) {
+    const lks3::Layout3 L3 = lks3::make_layout3(*desc);
+    if (!workspace || bytes < L3.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
+      return LKS_ERR_WORKSPACE;
+    lks_handle* h = new (std::nothrow) lks_handle();
+    if (!h) return LKS_ERR_INVALID_ARG;
+    h->d = *desc;
+    h->is3 = true;
+    h->L3 = L3;
+    h->ws = reinterpret_cast<unsigned char*>(workspace);
+    h->ws_bytes = bytes;
+    h->stream = reinterpret_cast<cudaStream_t>(stream);
+    cudaGetDevice(&h->device);
+    if ((s = lks3::upload_maps3(ctx3(h))) != LKS_OK) {
+      delete h;
+      return s;
+    }
+    *out = h;
+    return LKS_OK;
+  }
   const Layout L = make_layout(desc);
   if (!workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(workspace) % kAlign) != 0)
     return LKS_ERR_WORKSPACE;
@@ -937,6 +966,15 @@ lks_status lks_destroy(lks_handle* h) {
 
 lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
   if (check_handle(h) != LKS_OK || !gamma_dev) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  if (h->is3) {
+    const lks_status s = lks3::forward3(ctx3(h), gamma_dev, J_dev, &h->cur);
+    if (s == LKS_OK) {
+      h->phase = 1;
+      h->fwd_steps += h->d.n_steps;
+      h->fwd_path = LKS_PATH_STEP;
+    }
+    return s;
+  }
   return h->d.real_type == LKS_REAL_F64 ? forward_impl<double>(h, gamma_dev, J_dev)
                                         : forward_impl<float>(h, gamma_dev, J_dev);
 }
@@ -944,32 +982,44 @@ lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
 lks_status alks_adjoint(lks_handle* h) {
   if (check_handle(h) != LKS_OK) return LKS_ERR_INVALID_ARG;
   if (h->phase < 1) return fail(h, LKS_ERR_STATE, "alks_adjoint before lks_forward");
+  if (h->is3) {
+    const lks_status s = lks3::adjoint3(ctx3(h), h->cur, &h->acur);
+    if (s == LKS_OK) {
+      h->phase = 2;
+      h->adj_steps += h->d.n_adj;
+      h->adj_path = LKS_PATH_STEP;
+    }
+    return s;
+  }
   return h->d.real_type == LKS_REAL_F64 ? adjoint_impl<double>(h) : adjoint_impl<float>(h);
 }
 
 lks_status lks_sensitivity(lks_handle* h, void* out) {
   if (check_handle(h) != LKS_OK || !out) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
   if (h->phase < 2) return fail(h, LKS_ERR_STATE, "lks_sensitivity before alks_adjoint");
+  if (h->is3) return lks3::sensitivity3(ctx3(h), h->cur, h->acur, out);
   return h->d.real_type == LKS_REAL_F64 ? sensitivity_impl<double>(h, out) : sensitivity_impl<float>(h, out);
 }
 
 lks_status lks_gradient_host(lks_handle* h, const void* gamma_host, double* J_host, void* grad_host) {
   if (check_handle(h) != LKS_OK || !gamma_host || !J_host || !grad_host)
     return fail(h, LKS_ERR_INVALID_ARG, "null argument");
-  const size_t fb = h->L.N * h->L.rsize;
+  const size_t fb = h->is3 ? h->L3.N * h->L3.rsize : h->L.N * h->L.rsize;
   // The gradient is staged in the inactive adjoint buffer's first field, gamma in
   // the workspace copy itself (lks_forward copies device to device onto itself).
-  unsigned char* g_dev = h->ws + h->L.gamma;
+  unsigned char* g_dev = h->ws + (h->is3 ? h->L3.gamma : h->L.gamma);
   CKH(h, cudaMemcpyAsync(g_dev, gamma_host, fb, cudaMemcpyHostToDevice, h->stream));
   lks_status s = lks_forward(h, g_dev, nullptr);
   if (s == LKS_OK) s = alks_adjoint(h);
   if (s != LKS_OK) return s;
-  unsigned char* grad_dev = h->ws + (h->acur == 0 ? h->L.adB : h->L.adA);
+  const size_t adA = h->is3 ? h->L3.adA : h->L.adA, adB = h->is3 ? h->L3.adB : h->L.adB;
+  unsigned char* grad_dev = h->ws + (h->acur == 0 ? adB : adA);
   if ((s = lks_sensitivity(h, grad_dev)) != LKS_OK) return s;
   CKH(h, cudaMemcpyAsync(grad_host, grad_dev, fb, cudaMemcpyDeviceToHost, h->stream));
-  CKH(h, cudaMemcpyAsync(J_host, h->ws + h->L.jval, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaMemcpyAsync(J_host, h->ws + (h->is3 ? h->L3.jval : h->L.jval), sizeof(double), cudaMemcpyDeviceToHost,
+                         h->stream));
   int status = 0;
-  CKH(h, cudaMemcpyAsync(&status, h->ws + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaMemcpyAsync(&status, h->ws + status_off(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CKH(h, cudaStreamSynchronize(h->stream));
   if (status != 0) return fail(h, (lks_status)status, "device status set during the gradient");
   return LKS_OK;
@@ -979,6 +1029,7 @@ lks_status lks_set_state(lks_handle* h, const void* gamma_dev, const void* rho_d
                          const void* v_dev, const void* T_dev, int32_t t) {
   if (check_handle(h) != LKS_OK || !gamma_dev || !rho_dev || !u_dev || !v_dev || (h->d.thermal && !T_dev))
     return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  if (h->is3) return reject3(h, "lks_set_state");
   const size_t fb = h->L.N * h->L.rsize;
   CKH(h, cudaMemcpyAsync(h->ws + h->L.gamma, gamma_dev, fb, cudaMemcpyDeviceToDevice, h->stream));
   const void* src[4] = {rho_dev, u_dev, v_dev, T_dev};
@@ -991,10 +1042,17 @@ lks_status lks_set_state(lks_handle* h, const void* gamma_dev, const void* rho_d
 }
 
 lks_status lks_get_state(lks_handle* h, void* rho_dev, void* u_dev, void* v_dev, void* T_dev) {
-  if (check_handle(h) != LKS_OK || !rho_dev || !u_dev || !v_dev || (h->d.thermal && !T_dev))
+  if (check_handle(h) != LKS_OK || !rho_dev || !u_dev || !v_dev || ((h->d.thermal || h->is3) && !T_dev))
     return fail(h, LKS_ERR_INVALID_ARG, "null argument");
-  const size_t fb = h->L.N * h->L.rsize;
   void* dst[4] = {rho_dev, u_dev, v_dev, T_dev};
+  if (h->is3) {  // drho, u, v, w
+    const size_t fb3 = h->L3.N * h->L3.rsize;
+    const size_t base3 = h->cur == 0 ? h->L3.stA : h->L3.stB;
+    for (int f = 0; f < 4; ++f)
+      CKH(h, cudaMemcpyAsync(dst[f], h->ws + base3 + (size_t)f * fb3, fb3, cudaMemcpyDeviceToDevice, h->stream));
+    return LKS_OK;
+  }
+  const size_t fb = h->L.N * h->L.rsize;
   const size_t base = h->cur == 0 ? h->L.stA : h->L.stB;
   for (int f = 0; f < h->L.nF; ++f)
     CKH(h, cudaMemcpyAsync(dst[f], h->ws + base + (size_t)f * fb, fb, cudaMemcpyDeviceToDevice, h->stream));
@@ -1003,6 +1061,7 @@ lks_status lks_get_state(lks_handle* h, void* rho_dev, void* u_dev, void* v_dev,
 
 lks_status lks_march(lks_handle* h, int32_t n) {
   if (check_handle(h) != LKS_OK || n < 0) return fail(h, LKS_ERR_INVALID_ARG, "bad argument");
+  if (h->is3) return reject3(h, "lks_march");
   for (int s = 0; s < n; ++s) {
     lks_status st = h->d.real_type == LKS_REAL_F64
                         ? launch_fwd<double>(h, h->t + 1, nullptr, nullptr, nullptr, nullptr)
@@ -1014,6 +1073,7 @@ lks_status lks_march(lks_handle* h, int32_t n) {
 
 lks_status alks_set_adjoint(lks_handle* h, void* const* fields) {
   if (check_handle(h) != LKS_OK || !fields) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  if (h->is3) return reject3(h, "alks_set_adjoint");
   const size_t fb = h->L.N * h->L.rsize;
   h->acur = 0;
   for (int f = 0; f < h->L.nA; ++f) {
@@ -1025,6 +1085,15 @@ lks_status alks_set_adjoint(lks_handle* h, void* const* fields) {
 
 lks_status alks_get_adjoint(lks_handle* h, void* const* fields) {
   if (check_handle(h) != LKS_OK || !fields) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  if (h->is3) {
+    const size_t fb3 = h->L3.N * h->L3.rsize;
+    const size_t base3 = h->acur == 0 ? h->L3.adA : h->L3.adB;
+    for (int f = 0; f < lks3::kNA3; ++f) {
+      if (!fields[f]) return fail(h, LKS_ERR_INVALID_ARG, "null field");
+      CKH(h, cudaMemcpyAsync(fields[f], h->ws + base3 + (size_t)f * fb3, fb3, cudaMemcpyDeviceToDevice, h->stream));
+    }
+    return LKS_OK;
+  }
   const size_t fb = h->L.N * h->L.rsize;
   const size_t base = h->acur == 0 ? h->L.adA : h->L.adB;
   for (int f = 0; f < h->L.nA; ++f) {
@@ -1036,6 +1105,7 @@ lks_status alks_get_adjoint(lks_handle* h, void* const* fields) {
 
 lks_status alks_march(lks_handle* h, int32_t n) {
   if (check_handle(h) != LKS_OK || n < 0) return fail(h, LKS_ERR_INVALID_ARG, "bad argument");
+  if (h->is3) return reject3(h, "alks_march");
   for (int s = 0; s < n; ++s) {
     lks_status st;
     if (h->d.real_type == LKS_REAL_F64) {
@@ -1058,12 +1128,12 @@ lks_status alks_march(lks_handle* h, int32_t n) {
 lks_status lks_query(lks_handle* h, lks_stats* out) {
   if (check_handle(h) != LKS_OK || !out) return LKS_ERR_INVALID_ARG;
   int status = 0;
-  CKH(h, cudaMemcpyAsync(&status, h->ws + h->L.status, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaMemcpyAsync(&status, h->ws + status_off(h), sizeof(int), cudaMemcpyDeviceToHost, h->stream));
   CKH(h, cudaStreamSynchronize(h->stream));
   out->forward_steps = h->fwd_steps;
   out->adjoint_steps = h->adj_steps;
   out->kernel_launches = h->launches;
-  out->workspace_bytes = h->L.total;
+  out->workspace_bytes = h->is3 ? h->L3.total : h->L.total;
   out->device_status = status;
   out->phase = h->phase;
   out->fwd_path = h->fwd_path;
@@ -1134,6 +1204,7 @@ lks_status lks_gradient_noalloc(const lks_problem_desc* desc, const void* gamma_
   if (!gamma_dev || !J_dev || !dJdgamma_dev) return LKS_ERR_INVALID_ARG;
   lks_status s = check_desc(desc, nullptr);
   if (s != LKS_OK) return s;
+  if (desc->lattice != LKS_LATTICE_D2Q9) return LKS_ERR_INVALID_ARG;
   const Layout L = make_layout(desc);
   if (L.total > LKS_NOALLOC_SCRATCH_BYTES) return LKS_ERR_WORKSPACE;  // problem too large
   void* ws = nullptr;

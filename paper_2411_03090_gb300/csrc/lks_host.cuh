@@ -31,6 +31,20 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (!d) return bad("descriptor is NULL");
   if (d->version != LKS_DESC_VERSION) return bad("descriptor version mismatch");
   if (d->nx < 5 || d->ny < 5) return bad("nx and ny must be >= 5");
+  if (d->lattice != LKS_LATTICE_D2Q9 && d->lattice != LKS_LATTICE_D3Q19) return bad("bad lattice");
+  if (d->lattice == LKS_LATTICE_D3Q19) {
+    if (d->nz < 5) return bad("D3Q19: nz must be >= 5");
+    if ((int64_t)d->nx * d->ny * d->nz > (int64_t)1 << 31) return bad("lattice larger than 2^31 nodes");
+    if (d->real_type != LKS_REAL_F32 && d->real_type != LKS_REAL_F64) return bad("real_type must be F32 or F64");
+    if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
+    if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
+    if (!d->steady || d->thermal) return bad("D3Q19: steady, non-thermal problems only");
+    if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
+    for (int q = 0; q < 5; ++q)
+      if (d->reserved[q] != 0) return bad("reserved fields must be zero");
+    return LKS_OK;
+  }
+  if (d->nz != 0 && d->nz != 1) return bad("D2Q9: nz must be 0 or 1");
   if ((int64_t)d->nx * d->ny > (int64_t)1 << 31) return bad("lattice larger than 2^31 nodes");
   if (d->real_type != LKS_REAL_F32 && d->real_type != LKS_REAL_F64) return bad("real_type must be F32 or F64");
   if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
@@ -47,7 +61,7 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
   if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_RESIDENT) return bad("bad exec_path");
-  for (int q = 0; q < 7; ++q)
+  for (int q = 0; q < 5; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }

@@ -24,6 +24,8 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "u
 REAL = {"f32": 0, "f64": 1}
 SNAP = {"f32": 0, "bf16": 1, "f16": 2}
 PATH = {"auto": 0, "step": 1, "resident": 2}
+LATTICE_D3Q19 = 1
+N_ADJ_FIELDS_3D = 10
 N_ADJ_FIELDS = 9
 ADJ_NAMES = ("rho_t", "ux_t", "uy_t", "sxx_t", "sxy_t", "syy_t", "T_t", "qx_t", "qy_t")
 
@@ -50,7 +52,7 @@ class Desc(C.Structure):
         ("kappa_T", C.c_double),
         ("n_steps", C.c_int32), ("n_adj", C.c_int32),
         ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
-        ("exec_path", C.c_int32), ("reserved", C.c_int32 * 7),
+        ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("reserved", C.c_int32 * 5),
     ]
 
 
@@ -143,11 +145,20 @@ def load(build_if_missing: bool = True):
 
 def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
               path: str = "auto") -> Desc:
-    """Descriptor from an ``inputs.Problem``-like object."""
+    """Descriptor from an ``inputs.Problem``-like object (``inputs.Problem3``: a
+    D3Q19 duct)."""
     d = Desc()
     d.version = LKS_DESC_VERSION
     d.nx, d.ny = int(pb.nx), int(pb.ny)
     d.real_type = REAL[real]
+    if hasattr(pb, "nz"):
+        d.lattice, d.nz = LATTICE_D3Q19, int(pb.nz)
+        for name in ("nu", "alpha_bar", "q_alpha", "u_max", "rho_out"):
+            setattr(d, name, float(getattr(pb, name)))
+        d.steady, d.thermal = 1, 0
+        d.n_steps, d.n_adj = int(pb.n_steps), int(pb.n_adj)
+        d.exec_path = PATH[path]
+        return d
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T"):
         setattr(d, name, float(getattr(pb, name)))
@@ -205,7 +216,8 @@ class LKS:
         self.desc = make_desc(pb, real, checkpoint_every, snapshot, path)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.shape = (int(pb.ny), int(pb.nx))
+        self.is3 = hasattr(pb, "nz")
+        self.shape = (int(pb.nz), int(pb.ny), int(pb.nx)) if self.is3 else (int(pb.ny), int(pb.nx))
         with torch.cuda.device(self.device):
             self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
             nbytes = workspace_size(self.desc)
@@ -281,7 +293,7 @@ class LKS:
     def get_state(self):
         out = [self.empty() for _ in range(4)]
         _check(self.L.lks_get_state(self.h, *[self._ptr(x) for x in out]), "lks_get_state", self.h)
-        return out  # drho, u, v, T
+        return out  # drho, u, v, T (D3Q19: drho, u, v, w)
 
     def march(self, n: int) -> None:
         _check(self.L.lks_march(self.h, int(n)), "lks_march", self.h)
@@ -295,8 +307,9 @@ class LKS:
         _check(self.L.alks_set_adjoint(self.h, arr), "alks_set_adjoint", self.h)
 
     def get_adjoint(self):
-        out = [self.empty() for _ in range(N_ADJ_FIELDS)]
-        arr = (C.c_void_p * N_ADJ_FIELDS)(*[f.data_ptr() for f in out])
+        n = N_ADJ_FIELDS_3D if self.is3 else N_ADJ_FIELDS
+        out = [self.empty() for _ in range(n)]
+        arr = (C.c_void_p * n)(*[f.data_ptr() for f in out])
         _check(self.L.alks_get_adjoint(self.h, arr), "alks_get_adjoint", self.h)
         return out
 

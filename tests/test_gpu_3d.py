@@ -1,0 +1,123 @@
+"""GPU parity of the three-dimensional (D3Q19) steady duct path against the FP64
+oracle (``oracle/lks3d_oracle.c``), through the C ABI.
+
+Small ducts cover ragged tiles in x and y (37 = 32 + 5, 21 = 2 x 8 + 5) and a
+z-march split over two chunks (nz = 40 = 32 + 8); the FP64 instance matches the
+oracle to rounding, the FP32 instance to the FP32 tolerances.  At config 4's full
+size (192^3) one forward step and one adjoint step are checked on sampled nodes
+(interior, faces, box edges, corners) against the oracle's node updates computed
+from the GPU's own previous level.
+"""
+import numpy as np
+import pytest
+import torch
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover - CPU collection
+    pytest.skip("needs a CUDA GPU", allow_module_level=True)
+
+from oracle import oracle as O  # noqa: E402
+from paper_2411_03090_gb300 import LKS  # noqa: E402
+
+
+def rel_l2(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    nb = np.linalg.norm(b)
+    return np.linalg.norm(a - b) / (nb if nb > 0 else 1.0)
+
+
+def duct(nx=37, ny=21, nz=40, Re=20.0, n=60, **kw):
+    return inputs.duct(nx, ny, nz, Re=Re, seed=7, sigma=2.0, strip=2, n_steps=n, n_adj=n, **kw)
+
+
+def to_state(fields):
+    d, u, v, w = [f.double().cpu().numpy() for f in fields]
+    s = O.State3(*d.shape)
+    s.rho, s.u, s.v, s.w = d + 1.0, u, v, w
+    return s
+
+
+@pytest.mark.parametrize("real,tol_f,tol_g,tol_J", [("f64", 1e-10, 1e-10, 1e-11), ("f32", 1e-5, 1e-3, 1e-5)])
+@pytest.mark.parametrize("shape", [(37, 21, 40), (24, 16, 11)])
+def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape):
+    pb = duct(*shape)
+    g = pb.gamma()
+    ref = O.steady_gradient3(pb, g)
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    st = to_state(s.get_state())
+    for name in ("u", "v", "w"):
+        assert rel_l2(getattr(st, name), getattr(ref["state"], name)) <= tol_f, name
+    assert rel_l2(st.rho - 1, ref["state"].rho - 1) <= tol_f * 10
+    assert abs(J.item() - ref["J"]) <= tol_J * abs(ref["J"])
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    for q in range(O.NADJ3):
+        assert rel_l2(adj[q], ref["adjoint"][q]) <= tol_g, O.ADJ3_NAMES[q]
+    gr = grad.double().cpu().numpy()
+    assert rel_l2(gr, ref["dJdgamma"]) <= tol_g
+    assert np.all(gr[0] == 0) and np.all(gr[:, 0] == 0) and np.all(gr[:, :, 0] == 0)
+
+
+def test_gradient_host_and_query():
+    pb = duct(24, 16, 11, n=20)
+    g = pb.gamma()
+    s = LKS(pb, real="f32")
+    J, grad = s.gradient(torch.from_numpy(g))
+    Jh, gh = s.gradient_host(g.astype(np.float32))
+    assert Jh == J.item()
+    np.testing.assert_array_equal(gh, grad.cpu().numpy())
+    q = s.query()
+    assert q.device_status == 0 and q.forward_steps == 40 and q.adjoint_steps == 40
+
+
+def _sample_nodes(pb, rng, n_interior=40):
+    nx, ny, nz = pb.nx, pb.ny, pb.nz
+    nodes = {(0, 0, 0), (nx - 1, ny - 1, nz - 1), (0, ny // 2, nz // 2), (nx - 1, ny // 3, nz // 2),
+             (nx // 2, 0, nz // 2), (nx // 2, ny - 1, 7), (nx // 3, ny // 2, 0), (5, 9, nz - 1),
+             (0, 0, nz // 2), (nx - 1, 0, 5), (nx // 2, 0, 0), (33, ny - 1, nz - 1), (1, 1, 1),
+             (nx - 2, ny - 2, nz - 2), (31, 7, 31), (32, 8, 32), (63, 15, 95), (64, 16, 96)}
+    for _ in range(n_interior):
+        nodes.add(tuple(int(rng.integers(0, m)) for m in (nx, ny, nz)))
+    return sorted(nodes)
+
+
+def test_config4_full_size_one_step_sampled():
+    """192^3, FP32: one forward step and one adjoint step at sampled nodes equal
+    the oracle's node updates from the GPU's previous level (FP32 tolerance)."""
+    pb = inputs.config4().with_(n_steps=3, n_adj=1)
+    g = pb.gamma()
+    gt = torch.from_numpy(g)
+    s2 = LKS(pb.with_(n_steps=2), real="f32")
+    s2.lks_forward(gt)
+    prev = to_state(s2.get_state())
+    del s2
+    s = LKS(pb, real="f32")
+    s.lks_forward(gt)
+    cur = [f.double().cpu().numpy() for f in s.get_state()]
+    rng = np.random.default_rng(4)
+    nodes = _sample_nodes(pb, rng)
+    g32 = g.astype(np.float32).astype(np.float64)
+    scale = max(np.abs(cur[1]).max(), 1e-30)
+    for (i, j, k) in nodes:
+        o = O.forward_node3(pb, g32, prev, i, j, k)
+        assert abs(cur[0][k, j, i] - (o[0] - 1.0)) <= 2e-6, (i, j, k)
+        for c in range(3):
+            assert abs(cur[1 + c][k, j, i] - o[1 + c]) <= 2e-5 * scale, (i, j, k, c)
+    # adjoint: level 1 from zero, then level 2 from level 1 on the frozen state
+    st = to_state([torch.from_numpy(x) for x in cur])
+    s.alks_adjoint()
+    a1 = np.stack([a.double().cpu().numpy() for a in s.get_adjoint()])
+    s_b = LKS(pb.with_(n_adj=2), real="f32")
+    s_b.lks_forward(gt)
+    s_b.alks_adjoint()
+    a2 = np.stack([a.double().cpu().numpy() for a in s_b.get_adjoint()])
+    PV = O.adjoint_eq3(pb, st, a1)
+    ascale = np.abs(a2).reshape(O.NADJ3, -1).max(axis=1) + 1e-30
+    for (i, j, k) in nodes:
+        o = O.adjoint_node3(pb, g32, PV, st, i, j, k)
+        for q in range(O.NADJ3):
+            assert abs(a2[q, k, j, i] - o[q]) <= 2e-5 * ascale[q], (i, j, k, O.ADJ3_NAMES[q])
