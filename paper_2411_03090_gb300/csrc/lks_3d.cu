@@ -30,7 +30,9 @@
 #include <vector>
 
 #include "lks_3d.cuh"
+#include "lks_host.cuh"
 #include "lks_kernels.cuh"
+#include "lks_tma.cuh"
 
 namespace lks3 {
 
@@ -450,6 +452,475 @@ __global__ void __launch_bounds__(NT3) adj3_kernel(const __grid_constant__ Adj3A
 }
 
 // ------------------------------------------------------------------------------------
+// TMA-staged forms (FP32, nx % 4 == 0)
+// ------------------------------------------------------------------------------------
+// The same marches with every staged plane brought in by 3-D tensor copies
+// (cp.async.bulk.tensor.3d) into ring slots guarded by mbarriers with transaction
+// counts: the copy of a plane a few planes ahead overlaps the compute of the
+// current one, out-of-lattice parts of a box arrive as zeros, and no thread
+// computes a load address.  A box is 40 x 12 nodes starting at (x0 - 4, y0 - 2):
+// the two-node halo, with x rounded down to a multiple of four floats (16 bytes).
+// Columns whose two-node halo lies inside the lattice in x and y take a path
+// without face tests except on the z faces.  Every mbarrier wait is bounded; on a
+// timeout the kernel records LKS_ERR_TIMEOUT, drains its own copies and returns.
+constexpr int BW3 = TX3 + 8, BH3 = TY3 + 4, BOX3 = BW3 * BH3;
+constexpr int NSL3 = 6;  // plane ring slots
+constexpr int NFF3 = 5;  // forward: drho, u, v, w, 1/(1+alpha)
+
+struct Maps3F {
+  CUtensorMap m[NFF3];
+};
+struct Maps3A {
+  CUtensorMap zr[3];   // ring: s~xz, s~yz, s~zz
+  CUtensorMap pl[10];  // plane of PV: s~xx, s~xy, s~yy, rho~, u~x, u~y, u~z, u, v, w
+  CUtensorMap out[4];  // output plane (boxes 32 x 8): 1/(1+alpha), src x, y, z
+};
+
+__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, int x, int y, int z, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(
+          lks::smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(lks::smem_u32(bar))
+      : "memory");
+}
+
+__host__ __device__ constexpr size_t fwd3t_smem() {
+  return sizeof(float) * (size_t)(NSL3 * NFF3 * BOX3 + 3 * 5 * PA3 + 2 * 9 * PA3 + 5 * PA3) + 8 * NSL3 + 128;
+}
+__host__ __device__ constexpr size_t adj3t_smem() {
+  return sizeof(float) * (size_t)(NSL3 * 3 * BOX3 + 2 * 10 * BOX3 + 2 * 4 * NT3 + 3 * 4 * PA3) + 8 * (NSL3 + 4) + 128;
+}
+
+struct Fwd3TArgs {
+  float* out[4];
+  int* status;
+};
+
+__global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps3F maps, const __grid_constant__ Fwd3TArgs a,
+                                                    Geom3 g, Coef3<float> c) {
+  using R = float;
+  extern __shared__ unsigned char smem_raw3[];
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSL3][NFF3][BOX3]
+  R* up = ring + NSL3 * NFF3 * BOX3;                               // [3][5][PA3]
+  R* mid = up + 3 * 5 * PA3;                                       // [2][9][PA3]
+  R* dn = mid + 2 * 9 * PA3;                                       // [5][PA3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(dn + 5 * PA3);       // [NSL3]
+  if (lks::timed_out_before(a.status)) return;
+  if (!lks::tma_layout_ok(ring, bar, a.status)) return;
+  const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
+  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, g.nz);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int pbase = z0 - 2, plast = z1 + 2;
+  const bool xyi = x0 >= 2 && y0 >= 2 && x0 + TX3 + 2 <= nx && y0 + TY3 + 2 <= ny;
+  auto slot = [&](int p) { return (p - pbase) % NSL3; };
+  auto issue = [&](int p) {
+    const int sl = slot(p);
+    lks::mbar_expect_tx(&bar[sl], NFF3 * BOX3 * 4);
+    for (int f = 0; f < NFF3; ++f) tma_load_3d(ring + (sl * NFF3 + f) * BOX3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+  };
+  int waited = pbase - 1, issued = pbase - 1;
+  auto drain_and_fail = [&]() {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0)
+      for (int p = waited + 1; p <= issued; ++p) lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSL3) & 1);
+  };
+  auto wait = [&](int p) {
+    const bool ok = lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSL3) & 1);
+    if (ok) waited = p;
+    return ok;
+  };
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < NSL3; ++sl) lks::mbar_init(&bar[sl], 1);
+    lks::fence_mbar_init();
+    lks::fence_proxy_async();
+  }
+  __syncthreads();
+  for (int p = pbase; p < pbase + NSL3 && p <= plast; ++p) {
+    if (threadIdx.x == 0) issue(p);
+    issued = p;
+  }
+  auto plane = [&](int f, int p) -> const R* { return ring + (slot(p) * NFF3 + f) * BOX3; };
+
+  auto push = [&](int p, bool want_up, bool want_mid, bool want_dn, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    if (p < 0 || p >= nz) return;
+    const bool zf = p == 0 || p == nz - 1;
+    for (int q = threadIdx.x; q < PA3; q += NT3) {
+      const int ly = q / PX3, lx = q - ly * PX3;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (!FAST && (i < 0 || i >= nx || j < 0 || j >= ny)) continue;
+      const int boff = (ly + 1) * BW3 + (lx + 3);
+      R uu[3], gr[3][3];
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const R* f0 = plane(1 + d, p) + boff;
+        uu[d] = f0[0];
+        if (FAST) {
+          gr[d][0] = (f0[1] - f0[-1]) * R(0.5);
+          gr[d][1] = (f0[BW3] - f0[-BW3]) * R(0.5);
+        } else {
+          gr[d][0] = dax(f0, 1, i, nx);
+          gr[d][1] = dax(f0, BW3, j, ny);
+        }
+        gr[d][2] = zf ? daz<R>([&](int dz) { return plane(1 + d, p + dz)[boff]; }, p, nz)
+                      : (plane(1 + d, p + 1)[boff] - plane(1 + d, p - 1)[boff]) * R(0.5);
+      }
+      const bool on[3] = {!FAST && (i == 0 || i == nx - 1), !FAST && (j == 0 || j == ny - 1), zf};
+      const int faces = (int)on[0] + (int)on[1] + (int)on[2];
+      if (faces == 1) {
+        if (on[0]) gr[0][0] = -(gr[1][1] + gr[2][2]);
+        else if (on[1]) gr[1][1] = -(gr[0][0] + gr[2][2]);
+        else gr[2][2] = -(gr[0][0] + gr[1][1]);
+      } else if (faces >= 2) {
+#pragma unroll
+        for (int d = 0; d < 3; ++d)
+          if (on[d]) gr[d][d] = R(0);
+      }
+      const R e0 = R(-1.5) * (uu[0] * uu[0] + uu[1] * uu[1] + uu[2] * uu[2]);
+      const R bx = R(3) * uu[0], by = R(3) * uu[1], bz = R(3) * uu[2];
+      const R Qxx = R(4.5) * uu[0] * uu[0] + c.A * (R(2) * gr[0][0]);
+      const R Qyy = R(4.5) * uu[1] * uu[1] + c.A * (R(2) * gr[1][1]);
+      const R Qzz = R(4.5) * uu[2] * uu[2] + c.A * (R(2) * gr[2][2]);
+      const R Qxy = R(9) * uu[0] * uu[1] + R(2) * c.A * (gr[0][1] + gr[1][0]);
+      const R Qxz = R(9) * uu[0] * uu[2] + R(2) * c.A * (gr[0][2] + gr[2][0]);
+      const R Qyz = R(9) * uu[1] * uu[2] + R(2) * c.A * (gr[1][2] + gr[2][1]);
+      const R* d0 = plane(0, p) + boff;
+      const R* dm = plane(0, p - 1) + boff;
+      const R* dp = plane(0, p + 1) + boff;
+      const R dr = d0[0];
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int gk = grp3(k), sl = slot3(k);
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        if ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
+        const R dest = (cz == 0 ? d0 : (cz > 0 ? dp : dm))[cy * BW3 + cx];
+        const R qk = R(cx * cx) * Qxx + R(cy * cy) * Qyy + R(cz * cz) * Qzz + R(cx * cy) * Qxy + R(cx * cz) * Qxz +
+                     R(cy * cz) * Qyz;
+        const R val = R(w3d(k)) * (((dr - dest) + e0) + (R(cx) * bx + R(cy) * by + R(cz) * bz) + qk);
+        if (gk == 0) mid[(mod2(p) * 9 + sl) * PA3 + q] = val;
+        else if (gk == 1) up[(mod3(p) * 5 + sl) * PA3 + q] = val;
+        else dn[sl * PA3 + q] = val;
+      });
+    }
+  };
+
+  auto gather = [&](int z, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
+    const int i = x0 + tx, j = y0 + ty;
+    if (!FAST && (i >= nx || j >= ny)) return;
+    const int q1 = (ty + 1) * PX3 + (tx + 1);
+    R F[19];
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), gk = grp3(k), sl = slot3(k);
+      const int qs = q1 - cy * PX3 - cx;
+      if (gk == 0) F[k] = mid[(mod2(z) * 9 + sl) * PA3 + qs];
+      else if (gk == 1) F[k] = up[(mod3(z - 1) * 5 + sl) * PA3 + qs];
+      else F[k] = dn[sl * PA3 + qs];
+    });
+    const int boff = (ty + 2) * BW3 + (tx + 4);
+    const R drx = plane(0, z)[boff];
+    const int n0 = FAST ? 0 : (i == 0 ? -1 : (i == nx - 1 ? 1 : 0));
+    const int n1 = FAST ? 0 : (j == 0 ? -1 : (j == ny - 1 ? 1 : 0));
+    const int n2 = z == 0 ? -1 : (z == nz - 1 ? 1 : 0);
+    const int faces = abs(n0) + abs(n1) + abs(n2);
+    R drn, uo[3] = {R(0), R(0), R(0)};
+    if (faces == 0) {
+      R sm = R(0), mx = R(0), my = R(0), mz = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        sm += F[k];
+        if constexpr (c3(k, 0) != 0) mx += R(c3(k, 0)) * F[k];
+        if constexpr (c3(k, 1) != 0) my += R(c3(k, 1)) * F[k];
+        if constexpr (c3(k, 2) != 0) mz += R(c3(k, 2)) * F[k];
+      });
+      drn = drx + sm;
+      const R inv = plane(4, z)[boff];
+      uo[0] = mx * inv;
+      uo[1] = my * inv;
+      uo[2] = mz * inv;
+    } else if (faces >= 2) {
+      const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
+      const int kn = (z == 0) ? 1 : (z == nz - 1 ? -1 : 0);
+      drn = plane(0, z + kn)[boff + jn * BW3];
+    } else {
+      R s0 = R(0), sp = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        const int si = i - cx, sj = j - cy, sk = z - cz;
+        if (si < 0 || si >= nx || sj < 0 || sj >= ny || sk < 0 || sk >= nz) return;
+        const int cn = cx * n0 + cy * n1 + cz * n2;
+        if (cn == 0) s0 += F[k];
+        else if (cn > 0) sp += F[k];
+      });
+      if (n0 == 1) {
+        drn = c.drho_out;
+        uo[0] = (s0 + R(2) * sp) + (drx - c.drho_out);
+      } else {
+        if (n0 == -1) {
+          const double y = (double)j / (double)(ny - 1), zz = (double)z / (double)(nz - 1);
+          uo[0] = (R)(c.u_max * 16.0 * y * (1.0 - y) * zz * (1.0 - zz));
+        }
+        drn = drx + (s0 + R(2) * sp - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2)));
+      }
+    }
+    const size_t o = gidx(g, i, j, z);
+    a.out[0][o] = drn;
+    a.out[1][o] = uo[0];
+    a.out[2][o] = uo[1];
+    a.out[3][o] = uo[2];
+    const R m = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
+    if (!(m <= R(0.25))) raise_status(a.status, 4);
+  };
+
+  auto run = [&](auto fast_tag) {
+    for (int p = pbase; p <= pbase + 4; ++p)
+      if (!wait(p)) return false;
+    push(z0 - 1, true, false, false, fast_tag);
+    push(z0, true, true, false, fast_tag);
+    __syncthreads();
+    for (int z = z0; z < z1; ++z) {
+      if (z + 4 <= plast) {  // the slot of plane z - 2 is free
+        if (threadIdx.x == 0) issue(z + 4);
+        issued = z + 4;
+      }
+      if (!wait(z + 3)) return false;
+      push(z + 1, true, true, true, fast_tag);
+      __syncthreads();
+      gather(z, fast_tag);
+      __syncthreads();
+    }
+    return true;
+  };
+  const bool ok = xyi ? run(std::true_type{}) : run(std::false_type{});
+  if (!ok) drain_and_fail();
+}
+
+struct Adj3TArgs {
+  float* m0[kNA3];
+  const float* emap;
+  int* status;
+};
+
+__global__ void __launch_bounds__(NT3) adj3t_kernel(const __grid_constant__ Maps3A maps, const __grid_constant__ Adj3TArgs a,
+                                                    Geom3 g, Coef3<float> c) {
+  using R = float;
+  extern __shared__ unsigned char smem_raw3[];
+  R* ra = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSL3][3][BOX3]
+  R* rb = ra + NSL3 * 3 * BOX3;                                  // [2][10][BOX3]
+  R* rc = rb + 2 * 10 * BOX3;                                    // [2][4][NT3]
+  R* PV = rc + 2 * 4 * NT3;                                      // [3][4][PA3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(PV + 3 * 4 * PA3);  // A: NSL3, B: 2, C: 2
+  uint64_t* barB = bar + NSL3;
+  uint64_t* barC = barB + 2;
+  if (lks::timed_out_before(a.status)) return;
+  if (!lks::tma_layout_ok(ra, bar, a.status)) return;
+  const int x0 = blockIdx.x * TX3, y0 = blockIdx.y * TY3;
+  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, g.nz);
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int pa0 = z0 - 2, pa_last = z1 + 2;  // ring A planes
+  const int pb0 = z0 - 1, pb_last = z1;      // PV planes
+  const bool xyi = x0 >= 2 && y0 >= 2 && x0 + TX3 + 2 <= nx && y0 + TY3 + 2 <= ny;
+  auto slotA = [&](int p) { return (p - pa0) % NSL3; };
+  auto parA = [&](int p) { return (uint32_t)(((p - pa0) / NSL3) & 1); };
+  auto bufB = [&](int p) { return (p - pb0) & 1; };
+  auto parB = [&](int p) { return (uint32_t)(((p - pb0) >> 1) & 1); };
+  auto bufC = [&](int p) { return (p - z0) & 1; };
+  auto parC = [&](int p) { return (uint32_t)(((p - z0) >> 1) & 1); };
+  auto issueA = [&](int p) {
+    lks::mbar_expect_tx(&bar[slotA(p)], 3 * BOX3 * 4);
+    for (int f = 0; f < 3; ++f)
+      tma_load_3d(ra + (slotA(p) * 3 + f) * BOX3, &maps.zr[f], x0 - 4, y0 - 2, p, &bar[slotA(p)]);
+  };
+  auto issueB = [&](int p) {
+    lks::mbar_expect_tx(&barB[bufB(p)], 10 * BOX3 * 4);
+    for (int f = 0; f < 10; ++f)
+      tma_load_3d(rb + (bufB(p) * 10 + f) * BOX3, &maps.pl[f], x0 - 4, y0 - 2, p, &barB[bufB(p)]);
+  };
+  auto issueC = [&](int p) {
+    lks::mbar_expect_tx(&barC[bufC(p)], 4 * NT3 * 4);
+    for (int f = 0; f < 4; ++f) tma_load_3d(rc + (bufC(p) * 4 + f) * NT3, &maps.out[f], x0, y0, p, &barC[bufC(p)]);
+  };
+  // Copies in flight, for the drain on a timeout: [lo, hi] per group.
+  int a_lo = pa0, a_hi = pa0 - 1, b_lo = pb0, b_hi = pb0 - 1, c_lo = z0, c_hi = z0 - 1;
+  auto drain_and_fail = [&]() {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0) {
+      for (int p = a_lo; p <= a_hi; ++p) lks::mbar_wait(&bar[slotA(p)], parA(p));
+      for (int p = b_lo; p <= b_hi; ++p) lks::mbar_wait(&barB[bufB(p)], parB(p));
+      for (int p = c_lo; p <= c_hi; ++p) lks::mbar_wait(&barC[bufC(p)], parC(p));
+    }
+  };
+  auto waitA = [&](int p) { const bool ok = lks::mbar_wait(&bar[slotA(p)], parA(p)); if (ok) a_lo = p + 1; return ok; };
+  auto waitB = [&](int p) { const bool ok = lks::mbar_wait(&barB[bufB(p)], parB(p)); if (ok) b_lo = p + 1; return ok; };
+  auto waitC = [&](int p) { const bool ok = lks::mbar_wait(&barC[bufC(p)], parC(p)); if (ok) c_lo = p + 1; return ok; };
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < NSL3 + 4; ++q) lks::mbar_init(&bar[q], 1);
+    lks::fence_mbar_init();
+    lks::fence_proxy_async();
+  }
+  __syncthreads();
+  for (int p = pa0; p < pa0 + NSL3 && p <= pa_last; ++p) {
+    if (threadIdx.x == 0) issueA(p);
+    a_hi = p;
+  }
+  for (int p = pb0; p <= pb0 + 1 && p <= pb_last; ++p) {
+    if (threadIdx.x == 0) issueB(p);
+    b_hi = p;
+  }
+  if (threadIdx.x == 0) issueC(z0);
+  c_hi = z0;
+
+  auto ringv = [&](int f, int p) -> const R* { return ra + (slotA(p) * 3 + f) * BOX3; };
+  auto coefs = [&](int p, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    R* out = PV + mod3(p) * 4 * PA3;
+    const R* B = rb + bufB(p) * 10 * BOX3;
+    const bool zf = p == 0 || p == nz - 1;
+    for (int q = threadIdx.x; q < PA3; q += NT3) {
+      const int ly = q / PX3, lx = q - ly * PX3;
+      const int i = x0 - 1 + lx, j = y0 - 1 + ly;
+      if (p < 0 || p >= nz || (!FAST && (i < 0 || i >= nx || j < 0 || j >= ny))) {
+        out[q] = out[PA3 + q] = out[2 * PA3 + q] = out[3 * PA3 + q] = R(0);
+        continue;
+      }
+      const int boff = (ly + 1) * BW3 + (lx + 3);
+      const R* sxx = B + boff;
+      const R* sxy = B + BOX3 + boff;
+      const R* syy = B + 2 * BOX3 + boff;
+      const R* sxz = ringv(0, p) + boff;
+      const R* syz = ringv(1, p) + boff;
+      auto dzr = [&](int f) {
+        return zf ? daz<R>([&](int dz) { return ringv(f, p + dz)[boff]; }, p, nz)
+                  : (ringv(f, p + 1)[boff] - ringv(f, p - 1)[boff]) * R(0.5);
+      };
+      R Dx, Dy, Dz;
+      if (FAST) {
+        Dx = R(2) * ((sxx[1] - sxx[-1]) * R(0.5) + (sxy[BW3] - sxy[-BW3]) * R(0.5) + dzr(0));
+        Dy = R(2) * ((sxy[1] - sxy[-1]) * R(0.5) + (syy[BW3] - syy[-BW3]) * R(0.5) + dzr(1));
+        Dz = R(2) * ((sxz[1] - sxz[-1]) * R(0.5) + (syz[BW3] - syz[-BW3]) * R(0.5) + dzr(2));
+      } else {
+        Dx = R(2) * (dax(sxx, 1, i, nx) + dax(sxy, BW3, j, ny) + dzr(0));
+        Dy = R(2) * (dax(sxy, 1, i, nx) + dax(syy, BW3, j, ny) + dzr(1));
+        Dz = R(2) * (dax(sxz, 1, i, nx) + dax(syz, BW3, j, ny) + dzr(2));
+      }
+      const R rt = B[3 * BOX3 + boff], ux = B[4 * BOX3 + boff], uy = B[5 * BOX3 + boff], uz = B[6 * BOX3 + boff];
+      const R u0 = B[7 * BOX3 + boff], u1 = B[8 * BOX3 + boff], u2 = B[9 * BOX3 + boff];
+      const R vxx = sxx[0], vxy = sxy[0], vyy = syy[0], vxz = sxz[0], vyz = syz[0], vzz = ringv(2, p)[boff];
+      out[q] = rt;
+      out[PA3 + q] = R(3) * (ux + R(3) * (vxx * u0 + vxy * u1 + vxz * u2) - rt * u0) - c.A * Dx;
+      out[2 * PA3 + q] = R(3) * (uy + R(3) * (vxy * u0 + vyy * u1 + vyz * u2) - rt * u1) - c.A * Dy;
+      out[3 * PA3 + q] = R(3) * (uz + R(3) * (vxz * u0 + vyz * u1 + vzz * u2) - rt * u2) - c.A * Dz;
+    }
+  };
+  auto gather = [&](int z, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
+    const int i = x0 + tx, j = y0 + ty;
+    if (!FAST && (i >= nx || j >= ny)) return;
+    const int q1 = (ty + 1) * PX3 + (tx + 1);
+    const int n0 = FAST ? 0 : (i == 0 ? -1 : (i == nx - 1 ? 1 : 0));
+    const int n1 = FAST ? 0 : (j == 0 ? -1 : (j == ny - 1 ? 1 : 0));
+    const int n2 = z == 0 ? -1 : (z == nz - 1 ? 1 : 0);
+    const bool edge = (n0 | n1 | n2) != 0;
+    R f[19];
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+      const R* pv = PV + mod3(z + cz) * 4 * PA3 + q1 + cy * PX3 + cx;
+      R v = pv[0];
+      if constexpr (cx != 0) v += R(cx) * pv[PA3];
+      if constexpr (cy != 0) v += R(cy) * pv[2 * PA3];
+      if constexpr (cz != 0) v += R(cz) * pv[3 * PA3];
+      f[k] = v;
+      if (edge) {
+        const int gi = i + cx, gj = j + cy, gk = z + cz;
+        if (gi < 0 || gi >= nx || gj < 0 || gj >= ny || gk < 0 || gk >= nz) f[k] = R(0);
+      }
+    });
+    R m[kNA3];
+    if (!edge) {
+#pragma unroll
+      for (int r = 0; r < kNA3; ++r) m[r] = R(0);
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+        const R wf = R(w3d(k)) * f[k];
+        m[0] += wf;
+        if constexpr (cx != 0) m[1] += R(cx) * wf;
+        if constexpr (cy != 0) m[2] += R(cy) * wf;
+        if constexpr (cz != 0) m[3] += R(cz) * wf;
+        if constexpr (cx != 0) m[4] += wf;
+        if constexpr (cx * cy != 0) m[5] += R(cx * cy) * wf;
+        if constexpr (cx * cz != 0) m[6] += R(cx * cz) * wf;
+        if constexpr (cy != 0) m[7] += wf;
+        if constexpr (cy * cz != 0) m[8] += R(cy * cz) * wf;
+        if constexpr (cz != 0) m[9] += wf;
+      });
+      const R* C = rc + bufC(z) * 4 * NT3 + ty * TX3 + tx;
+      const R inv = C[0];
+      m[1] = (m[1] + C[NT3]) * inv;
+      m[2] = (m[2] + C[2 * NT3]) * inv;
+      m[3] = (m[3] + C[3 * NT3]) * inv;
+    } else {
+      const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+#pragma unroll
+      for (int r = 0; r < kNA3; ++r) {
+        R sacc = R(0);
+        static_for<0, 19>([&](auto kk) {
+          constexpr int k = decltype(kk)::value;
+          sacc += M[r * 19 + k] * f[k];
+        });
+        m[r] = sacc;
+      }
+    }
+    const size_t o = gidx(g, i, j, z);
+#pragma unroll
+    for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
+    if (!(m[1] * m[1] + m[2] * m[2] + m[3] * m[3] < R(1e30))) raise_status(a.status, 4);
+  };
+
+  auto run = [&](auto fast_tag) {
+    for (int p = pa0; p <= pa0 + 4; ++p)
+      if (!waitA(p)) return false;
+    if (!waitB(pb0)) return false;
+    coefs(pb0, fast_tag);
+    __syncthreads();
+    if (pb0 + 2 <= pb_last) {  // the buffer of plane z0 - 1 is free
+      if (threadIdx.x == 0) issueB(pb0 + 2);
+      b_hi = pb0 + 2;
+    }
+    if (!waitB(z0)) return false;
+    coefs(z0, fast_tag);
+    __syncthreads();
+    for (int z = z0; z < z1; ++z) {
+      if (z + 4 <= pa_last) {
+        if (threadIdx.x == 0) issueA(z + 4);
+        a_hi = z + 4;
+      }
+      if (z + 2 <= pb_last && z + 2 > b_hi) {
+        if (threadIdx.x == 0) issueB(z + 2);
+        b_hi = z + 2;
+      }
+      if (z + 1 < z1) {
+        if (threadIdx.x == 0) issueC(z + 1);
+        c_hi = z + 1;
+      }
+      if (!waitA(z + 3) || !waitB(z + 1) || !waitC(z)) return false;
+      coefs(z + 1, fast_tag);
+      __syncthreads();
+      gather(z, fast_tag);
+      __syncthreads();
+    }
+    return true;
+  };
+  const bool ok = xyi ? run(std::true_type{}) : run(std::false_type{});
+  if (!ok) drain_and_fail();
+}
+
+// ------------------------------------------------------------------------------------
 // Pointwise kernels: material, objective source, objective, sensitivity
 // ------------------------------------------------------------------------------------
 template <typename R>
@@ -581,6 +1052,23 @@ dim3 march_grid(const lks_problem_desc& d) {
   return dim3((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + ZC3 - 1) / ZC3);
 }
 
+// TMA-staged kernels: FP32 and rows whose byte pitch is a multiple of 16.
+bool tma3_ok(const lks_problem_desc& d) {
+  return d.real_type == LKS_REAL_F32 && d.nx % 4 == 0 && lks_host::encode_fn() != nullptr;
+}
+// Tensor map of one nx x ny x nz float field for boxes bw x bh x 1.
+lks_status map3(const Ctx3& c, const void* ptr, int bw, int bh, CUtensorMap* m) {
+  const auto& d = *c.d;
+  const cuuint64_t dims[3] = {(cuuint64_t)d.nx, (cuuint64_t)d.ny, (cuuint64_t)d.nz};
+  const cuuint64_t strides[2] = {(cuuint64_t)d.nx * 4, (cuuint64_t)d.nx * d.ny * 4};
+  const cuuint32_t box[3] = {(cuuint32_t)bw, (cuuint32_t)bh, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUresult r = lks_host::encode_fn()(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void*>(ptr), dims, strides,
+                                           box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                           CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? LKS_OK : fail3(c, LKS_ERR_CUDA, "cuTensorMapEncodeTiled (3-D) failed");
+}
+
 template <typename R>
 lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur_out) {
   const auto& d = *c.d;
@@ -599,10 +1087,31 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
                                                      fld3<R>(c, L.src, 2));
   CK3(c, cudaGetLastError());
   ++*c.launches;
+  int cur = 0;
+  if constexpr (sizeof(R) == 4) {
+    if (tma3_ok(d)) {
+      Maps3F maps[2];
+      Fwd3TArgs ta[2];
+      lks_status st;
+      for (int b = 0; b < 2; ++b) {
+        for (int f = 0; f < 4; ++f)
+          if ((st = map3(c, st3<float>(c, b, f), BW3, BH3, &maps[b].m[f])) != LKS_OK) return st;
+        if ((st = map3(c, fld3<float>(c, L.binv), BW3, BH3, &maps[b].m[4])) != LKS_OK) return st;
+        for (int f = 0; f < 4; ++f) ta[b].out[f] = st3<float>(c, 1 - b, f);
+        ta[b].status = reinterpret_cast<int*>(c.ws + L.status);
+      }
+      CK3(c, cudaFuncSetAttribute(fwd3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3t_smem()));
+      for (int s = 0; s < d.n_steps; ++s) {
+        fwd3t_kernel<<<march_grid(d), NT3, fwd3t_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
+        CK3(c, cudaGetLastError());
+        ++*c.launches;
+        cur = 1 - cur;
+      }
+    }
+  }
   const size_t smem = fwd3_smem<R>();
   CK3(c, cudaFuncSetAttribute(fwd3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int cur = 0;
-  for (int s = 0; s < d.n_steps; ++s) {
+  for (int s = 0; s < d.n_steps && !(sizeof(R) == 4 && tma3_ok(d)); ++s) {
     Fwd3Args<R> a;
     for (int f = 0; f < 4; ++f) {
       a.in[f] = st3<R>(c, cur, f);
@@ -641,9 +1150,40 @@ lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out) {
   CK3(c, cudaGetLastError());
   ++*c.launches;
   CK3(c, cudaMemsetAsync(c.ws + L.adA, 0, fb * kNA3, c.stream));
+  int acur = 0;
+  if constexpr (sizeof(R) == 4) {
+    if (tma3_ok(d)) {
+      Maps3A maps[2];
+      Adj3TArgs ta[2];
+      lks_status st;
+      const int zi[3] = {6, 8, 9}, pi[7] = {4, 5, 7, 0, 1, 2, 3};
+      for (int b = 0; b < 2; ++b) {
+        for (int f = 0; f < 3; ++f)
+          if ((st = map3(c, ad3<float>(c, b, zi[f]), BW3, BH3, &maps[b].zr[f])) != LKS_OK) return st;
+        for (int f = 0; f < 7; ++f)
+          if ((st = map3(c, ad3<float>(c, b, pi[f]), BW3, BH3, &maps[b].pl[f])) != LKS_OK) return st;
+        for (int f = 0; f < 3; ++f)
+          if ((st = map3(c, st3<float>(c, cur, 1 + f), BW3, BH3, &maps[b].pl[7 + f])) != LKS_OK) return st;
+        if ((st = map3(c, fld3<float>(c, L.binv), TX3, TY3, &maps[b].out[0])) != LKS_OK) return st;
+        for (int f = 0; f < 3; ++f)
+          if ((st = map3(c, fld3<float>(c, L.src, f), TX3, TY3, &maps[b].out[1 + f])) != LKS_OK) return st;
+        for (int q = 0; q < kNA3; ++q) ta[b].m0[q] = ad3<float>(c, 1 - b, q);
+        ta[b].emap = reinterpret_cast<const float*>(c.ws + L.emap);
+        ta[b].status = reinterpret_cast<int*>(c.ws + L.status);
+      }
+      CK3(c, cudaFuncSetAttribute(adj3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj3t_smem()));
+      for (int it = 0; it < d.n_adj; ++it) {
+        adj3t_kernel<<<march_grid(d), NT3, adj3t_smem(), c.stream>>>(maps[acur], ta[acur], g, cf);
+        CK3(c, cudaGetLastError());
+        ++*c.launches;
+        acur = 1 - acur;
+      }
+      *acur_out = acur;
+      return LKS_OK;
+    }
+  }
   const size_t smem = adj3_smem<R>();
   CK3(c, cudaFuncSetAttribute(adj3_kernel<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-  int acur = 0;
   for (int it = 0; it < d.n_adj; ++it) {
     Adj3Args<R> a;
     for (int q = 0; q < kNA3; ++q) {

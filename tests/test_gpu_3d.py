@@ -1,7 +1,8 @@
 """GPU parity of the three-dimensional (D3Q19) steady duct path against the FP64
 oracle (``oracle/lks3d_oracle.c``), through the C ABI.
 
-Small ducts cover ragged tiles in x and y (37 = 32 + 5, 21 = 2 x 8 + 5) and a
+Small ducts cover ragged tiles in x and y (37 = 32 + 5, 44 = 32 + 12, 21 = 2 x 8 + 5;
+nx % 4 == 0 runs the TMA-staged FP32 kernels, 37 the plain ones) and a
 z-march split over two chunks (nz = 40 = 32 + 8); the FP64 instance matches the
 oracle to rounding, the FP32 instance to the FP32 tolerances.  At config 4's full
 size (192^3) one forward step and one adjoint step are checked on sampled nodes
@@ -42,7 +43,7 @@ def to_state(fields):
 
 
 @pytest.mark.parametrize("real,tol_f,tol_g,tol_J", [("f64", 1e-10, 1e-10, 1e-11), ("f32", 1e-5, 1e-3, 1e-5)])
-@pytest.mark.parametrize("shape", [(37, 21, 40), (24, 16, 11)])
+@pytest.mark.parametrize("shape", [(37, 21, 40), (24, 16, 11), (44, 21, 40)])
 def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape):
     pb = duct(*shape)
     g = pb.gamma()
