@@ -65,6 +65,25 @@ def workload(name: str):
     raise SystemExit(f"unknown workload {name}")
 
 
+def max_over_ranks(ms: float, world: int, device=None) -> float:
+    """Slowest rank's time: every rank contributes its own timed milliseconds and
+    all receive the maximum (the whole job ends when its slowest replica does)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dist.barrier()
+    return float(t.item())
+
+
+def job_mlups(world: int, updates_per_replica_step: float, steps: int, max_ms: float) -> float:
+    """Whole-job throughput of `world` independent replicas (weak scaling): the
+    updates all ranks did, over the slowest rank's time."""
+    return world * updates_per_replica_step * steps / (max_ms * 1e-3) / 1e6
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -446,17 +465,12 @@ def main():
         fwd_ms.append(ev[0].elapsed_time(ev[1]))
         adj_ms.append(ev[1].elapsed_time(ev[2]))
     torch.cuda.synchronize()
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        dist.barrier()
+    total_ms = max_over_ranks(sum(step_ms), world, dev)
     clk = clocks.stop()
     launches = s.query().kernel_launches - launches0
 
     updates_per_step = N * (pb.n_steps + pb.n_adj)
-    value = world * updates_per_step * args.steps / (total_ms * 1e-3) / 1e6
+    value = job_mlups(world, updates_per_step, args.steps, total_ms)
 
     # Dominant kernel (adjoint step): algorithmic bytes per launch / mean duration.
     hbm, peak_kind = peaks()
