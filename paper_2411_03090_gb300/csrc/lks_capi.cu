@@ -21,6 +21,7 @@
 #include "lks_kernels.cuh"
 #include "lks_resident.cuh"
 #include "lks_3d.cuh"
+#include "lks_col.cuh"
 #include "lks_host.cuh"
 #include "lks_tma.cuh"
 
@@ -55,7 +56,8 @@ Layout make_layout(const lks_problem_desc* d) {
   L.nA = d->thermal ? 9 : 6;
   L.nT = d->thermal ? 3 : 2;
   const int gx = (d->nx + TX - 1) / TX, gy = (d->ny + TY - 1) / TY;
-  L.fwd_blocks = gx * gy;
+  const int col_tiles = ((d->nx + COL_W - 1) / COL_W) * ((d->ny + COL_H - 1) / COL_H);
+  L.fwd_blocks = std::max(gx * gy, col_tiles);  // J partials: one per block of the largest forward grid
   L.obj_blocks = obj_grid(L.N);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -438,8 +440,38 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
   return std::max(1, std::min(ntiles, per_sm * device_sms(h)));
 }
 
+// Warp-column forward (FP32, non-thermal, one lattice): one CTA per 28 x 64 tile.
+lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv) {
+  const auto& d = h->d;
+  const int src = h->cur, dst = 1 - h->cur;
+  TmaMaps<4> maps;
+  lks_status st;
+  const float* fsrc[4] = {state_ptr<float>(h, src, 0), state_ptr<float>(h, src, 1), state_ptr<float>(h, src, 2),
+                          fld<float>(h, h->L.mat, 0)};
+  for (int f = 0; f < 4; ++f)
+    if ((st = field_map(h, fsrc[f], COL_BW, COL_BH, &maps.m[f])) != LKS_OK) return st;
+  ColArgs a;
+  for (int f = 0; f < 3; ++f) a.out[f] = state_ptr<float>(h, dst, f);
+  a.traj_u = tu;
+  a.traj_v = tv;
+  a.J_partial = Jpartial;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.u_in = (float)inlet_amp(d, t_new);
+  a.ntx = (d.nx + COL_W - 1) / COL_W;
+  const int grid = a.ntx * ((d.ny + COL_H - 1) / COL_H);
+  fwd_col_kernel<<<grid, COL_NT, col_smem_bytes(), h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  CKH(h, cudaGetLastError());
+  h->cur = dst;
+  h->t = t_new;
+  h->fwd_steps++;
+  h->launches++;
+  h->fwd_path = LKS_PATH_STEP;
+  return LKS_OK;
+}
+
 template <bool TH>
 lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
+  if constexpr (!TH) return launch_fwd_col(h, t_new, Jpartial, tu, tv);
   constexpr int NF = fwd_tma_nf(TH);
   constexpr int BW = kFwdTX + 8, BH = kFwdTY + 4;
   const auto& d = h->d;

@@ -1,0 +1,263 @@
+// lks_col.cuh -- warp-column form of the FP32 forward step of one lattice (non-thermal).
+//
+// Each warp owns 32 adjacent lattice columns and marches down 16 output rows with
+// the state of three rows held in registers.  A lane computes the nine pushed
+// populations of its node (the per-node arithmetic of fwd_tma_kernel, term for
+// term), hands the ones that cross a column to its neighbour lane by warp shuffle,
+// and accumulates what its column receives per destination row; a row is complete
+// once the row below it has been pushed.  The two outer lanes on each side only
+// feed their neighbours, so a warp writes 28 columns.  Four warps stacked in y make
+// a 28 x 64 tile, staged by one tensor copy of each field (box 36 x 68 from
+// (x0 - 4, y0 - 2): the halo, with x on a 16-byte boundary).  There is no shared
+// push array and no barrier inside a tile.  Tiles whose halo reaches the domain
+// edge run the same march with the edge rules (one-sided derivatives, continuity,
+// Zou-He edges, corners), reading neighbours from the staged box.
+#pragma once
+#include "lks_tma.cuh"
+
+namespace lks {
+
+constexpr int COL_W = 28;                       // output columns per warp (32 lanes, 2 halo lanes per side)
+constexpr int COL_WARPS = 4;                    // warps per CTA, stacked in y
+constexpr int COL_R = 16;                       // output rows per warp
+constexpr int COL_H = COL_WARPS * COL_R;        // output rows per tile
+constexpr int COL_BW = COL_W + 8, COL_BH = COL_H + 4, COL_BOX = COL_BW * COL_BH;
+constexpr int COL_NT = 32 * COL_WARPS;
+constexpr int COL_FS = (COL_BOX * 4 + 127) / 128 * 128 / 4;  // field stride: copies land on 128-byte boundaries
+
+__host__ __device__ constexpr size_t col_smem_bytes() { return (size_t)4 * COL_FS * 4 + 128 + 8 + 8 * COL_WARPS; }
+
+struct ColArgs {
+  float* out[3];      // drho, u, v of the new level
+  float* traj_u;      // optional trajectory copies of u, v
+  float* traj_v;
+  double* J_partial;  // per-tile accumulator of J_O(old state), or null
+  int* status;
+  float u_in;         // inlet amplitude of the new level
+  int ntx;            // tiles along x
+};
+
+__global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__ TmaMaps<4> maps,
+                                                         const __grid_constant__ ColArgs a,
+                                                         const __grid_constant__ Geom g,
+                                                         const __grid_constant__ Coef<float> c) {
+  extern __shared__ unsigned char smem_raw[];
+  float* box = reinterpret_cast<float*>(smem_base128(smem_raw));  // [drho, u, v, 1/(1+alpha)][COL_FS]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(box + 4 * COL_FS);
+  double* red = reinterpret_cast<double*>(bar + 1);
+  if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(box, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny;
+  const int x0 = (blockIdx.x % a.ntx) * COL_W, y0 = (blockIdx.x / a.ntx) * COL_H;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    mbar_expect_tx(bar, 4 * COL_BOX * 4);
+    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * COL_FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0) mbar_wait(bar, 0);
+    return;
+  }
+  const float* sdr = box;
+  const float* su = box + COL_FS;
+  const float* sv = box + 2 * COL_FS;
+  const float* sbi = box + 3 * COL_FS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = x0 - 2 + lane;  // this lane's lattice column
+  const int bx = lane + 2;      // its column in the box
+  const int r0 = y0 + warp * COL_R;
+  const bool out_lane = lane >= 2 && lane < 2 + COL_W && i < nx;
+  const bool fast = x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + COL_H + 2 <= ny;
+  constexpr int BW = COL_BW;
+  double jloc = 0.0;
+  auto brow = [&](int y) { return (y - y0 + 2) * BW; };  // box offset of row y
+
+  auto march = [&](auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    float X[9], Y[9], Z[9];  // received populations of destination rows p-1, p, p+1
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = Y[k] = Z[k] = 0.f;
+    // register ring (fast path): drho, u, v of rows p-1 (A), p (B), p+1 (C)
+    float dA = 0.f, uA = 0.f, vA = 0.f, dB = 0.f, uB = 0.f, vB = 0.f, dC = 0.f, uC = 0.f, vC = 0.f;
+    if (!EDGE) {
+      const int o = brow(r0 - 2) + bx;
+      dA = sdr[o], uA = su[o], vA = sv[o];
+      dB = sdr[o + BW], uB = su[o + BW], vB = sv[o + BW];
+      dC = sdr[o + 2 * BW], uC = su[o + 2 * BW], vC = sv[o + 2 * BW];
+    }
+    for (int p = r0 - 1; p <= r0 + COL_R; ++p) {
+      float F[9];
+      const int s2 = brow(p) + bx;
+      bool has_obj = false, live = true;
+      float uu = 0.f, vv = 0.f, dudx = 0.f, dudy = 0.f, dvdx = 0.f, dvdy = 0.f, dr = 0.f;
+      float d_e = 0.f, d_w = 0.f, d_n = 0.f, d_s = 0.f, d_ne = 0.f, d_nw = 0.f, d_sw = 0.f, d_se = 0.f;
+      if (!EDGE) {
+        const float uL = __shfl_up_sync(0xffffffffu, uB, 1), uR = __shfl_down_sync(0xffffffffu, uB, 1);
+        const float vL = __shfl_up_sync(0xffffffffu, vB, 1), vR = __shfl_down_sync(0xffffffffu, vB, 1);
+        const float aL = __shfl_up_sync(0xffffffffu, dA, 1), aR = __shfl_down_sync(0xffffffffu, dA, 1);
+        const float bL = __shfl_up_sync(0xffffffffu, dB, 1), bR = __shfl_down_sync(0xffffffffu, dB, 1);
+        const float cL = __shfl_up_sync(0xffffffffu, dC, 1), cR = __shfl_down_sync(0xffffffffu, dC, 1);
+        uu = uB;
+        vv = vB;
+        dudx = (uR - uL) * 0.5f;
+        dudy = (uC - uA) * 0.5f;
+        dvdx = (vR - vL) * 0.5f;
+        dvdy = (vC - vA) * 0.5f;
+        dr = dB;
+        d_e = bR, d_w = bL, d_n = dC, d_s = dA, d_ne = cR, d_nw = cL, d_sw = aL, d_se = aR;
+        has_obj = true;
+      } else {
+        live = i >= 0 && i < nx && p >= 0 && p < ny;
+        if (!live) {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) F[k] = 0.f;
+        } else {
+          const int by = p - y0 + 2;
+          uu = su[s2];
+          vv = sv[s2];
+          dudx = dfdx<float, BW>(su, bx, by, i, nx);
+          dudy = dfdy<float, BW>(su, bx, by, p, ny);
+          dvdx = dfdx<float, BW>(sv, bx, by, i, nx);
+          dvdy = dfdy<float, BW>(sv, bx, by, p, ny);
+          const bool xe = (i == 0 || i == nx - 1), ye = (p == 0 || p == ny - 1);
+          if (xe && ye) {
+            dudx = 0.f;
+            dvdy = 0.f;
+          } else if (xe) {
+            dudx = -dvdy;
+          } else if (ye) {
+            dvdy = -dudx;
+          }
+          dr = sdr[s2];
+          d_e = sdr[s2 + 1], d_w = sdr[s2 - 1], d_n = sdr[s2 + BW], d_s = sdr[s2 - BW];
+          d_ne = sdr[s2 + BW + 1], d_nw = sdr[s2 + BW - 1], d_sw = sdr[s2 - BW - 1], d_se = sdr[s2 - BW + 1];
+          has_obj = i > 0 && p > 0 && i < nx - 1 && p < ny - 1;
+        }
+      }
+      if (live) {
+        const float e0 = -1.5f * (uu * uu + vv * vv);
+        const float bxv = 3.f * uu, byv = 3.f * vv;
+        const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
+        const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
+        const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
+        F[0] = e0 * (4.f / 9.f);
+        F[1] = ((dr - d_e) + e0 + bxv + qxx) * (1.f / 9.f);
+        F[3] = ((dr - d_w) + e0 - bxv + qxx) * (1.f / 9.f);
+        F[2] = ((dr - d_n) + e0 + byv + qyy) * (1.f / 9.f);
+        F[4] = ((dr - d_s) + e0 - byv + qyy) * (1.f / 9.f);
+        const float d0 = e0 + qxx + qyy;
+        F[5] = (((dr - d_ne) + d0) + bxv + byv + qxy) * (1.f / 36.f);
+        F[6] = (((dr - d_nw) + d0) - bxv + byv - qxy) * (1.f / 36.f);
+        F[7] = (((dr - d_sw) + d0) - bxv - byv + qxy) * (1.f / 36.f);
+        F[8] = (((dr - d_se) + d0) + bxv - byv - qxy) * (1.f / 36.f);
+        // objective of the old state at this warp's output nodes (unsteady accumulation)
+        if (a.J_partial && has_obj && out_lane && p >= r0 && p < r0 + COL_R && p < ny) {
+          const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
+          const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
+          const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
+          const float al = __fdividef(1.f, sbi[s2]) - 1.f;
+          jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+        }
+      }
+      // hand the populations that cross a column to the neighbour lane
+      {
+        const float g1 = __shfl_up_sync(0xffffffffu, F[1], 1);
+        const float g5 = __shfl_up_sync(0xffffffffu, F[5], 1);
+        const float g8 = __shfl_up_sync(0xffffffffu, F[8], 1);
+        const float g3 = __shfl_down_sync(0xffffffffu, F[3], 1);
+        const float g6 = __shfl_down_sync(0xffffffffu, F[6], 1);
+        const float g7 = __shfl_down_sync(0xffffffffu, F[7], 1);
+        X[4] = F[4];  // c = (0, -1): destination row p - 1
+        X[7] = g7;
+        X[8] = g8;
+        Y[0] = F[0];  // c_y = 0: destination row p
+        Y[1] = g1;
+        Y[3] = g3;
+        Z[2] = F[2];  // c_y = +1: destination row p + 1
+        Z[5] = g5;
+        Z[6] = g6;
+      }
+      // row p - 1 is complete
+      const int q = p - 1;
+      if (q >= r0 && q < r0 + COL_R && q < ny && out_lane) {
+        const int sq = brow(q) + bx;
+        const float drx = EDGE ? sdr[sq] : dA;
+        float drn, un, vn;
+        int nxo = 0, nyo = 0;
+        const int cls = EDGE ? node_class(g, i, q, nxo, nyo) : C_INTERIOR;
+        const float* fk = X;
+        if (cls == C_INTERIOR) {
+          drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
+          const float inv = sbi[sq];
+          un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
+          vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+        } else {
+          float s0 = 0.f, sp = 0.f;
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int cx = cxk(k), cy = cyk(k);
+            const int si = i - cx, sj = q - cy;
+            if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
+            const int cn = cx * nxo + cy * nyo;
+            if (cn == 0) s0 += fk[k];
+            else if (cn > 0) sp += fk[k];
+          }
+          if (cls == C_CORNER) {
+            const int jn = (q == 0) ? 1 : ny - 2;
+            drn = sdr[brow(jn) + bx];
+            un = vn = 0.f;
+          } else if (cls == C_VELOCITY) {
+            un = 0.f;
+            if (i == 0 && q >= g.in_y0 && q <= g.in_y1) {
+              const double H = (double)(g.in_y1 - g.in_y0), y = (double)(q - g.in_y0);
+              un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
+            }
+            vn = 0.f;
+            drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
+          } else {
+            drn = c.drho_out;
+            const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
+            un = unorm * (float)nxo;
+            vn = unorm * (float)nyo;
+          }
+        }
+        const size_t o = (size_t)q * nx + i;
+        a.out[0][o] = drn;
+        a.out[1][o] = un;
+        a.out[2][o] = vn;
+        if (a.traj_u) {
+          a.traj_u[o] = un;
+          a.traj_v[o] = vn;
+        }
+        if (bad_velocity(un, vn)) raise_status(a.status, 4);
+      }
+      // rotate the rows
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        X[k] = Y[k];
+        Y[k] = Z[k];
+        Z[k] = 0.f;
+      }
+      if (!EDGE) {
+        dA = dB, uA = uB, vA = vB;
+        dB = dC, uB = uC, vB = vC;
+        if (p + 2 <= r0 + COL_R + 1) {
+          const int o = brow(p + 2) + bx;
+          dC = sdr[o], uC = su[o], vC = sv[o];
+        }
+      }
+    }
+  };
+  if (fast) march(std::false_type{});
+  else march(std::true_type{});
+  if (a.J_partial) {
+    const double s = block_sum<COL_NT>(jloc, red);
+    if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
+  }
+}
+
+}  // namespace lks
