@@ -526,9 +526,52 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
   return LKS_OK;
 }
 
+// Warp-column adjoint (FP32, non-thermal, one lattice): one CTA per 28 x 32 tile.
+template <bool SAME>
+lks_status launch_adj_col(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
+                          float* sens, int sens_flow) {
+  constexpr int NF = acol_nf(SAME);
+  const auto& d = h->d;
+  const int src = h->acur, dst = 1 - h->acur;
+  TmaMaps<NF> maps;
+  lks_status st;
+  const float* mat = fld<float>(h, h->L.mat, 0);
+  const float* fs[12] = {adj_ptr<float>(h, src, 0), adj_ptr<float>(h, src, 1), adj_ptr<float>(h, src, 2),
+                         adj_ptr<float>(h, src, 3), adj_ptr<float>(h, src, 4), adj_ptr<float>(h, src, 5),
+                         u1, v1, u0, v0, mat + h->L.N, mat};  // ..., alpha, 1/(1+alpha)
+  int f = 0;
+  for (int q = 0; q < 12; ++q) {
+    if (SAME && (q == 8 || q == 9)) continue;
+    if ((st = field_map(h, fs[q], COL_BW, ACOL_BH, &maps.m[f++])) != LKS_OK) return st;
+  }
+  AdjColArgs a;
+  for (int q = 0; q < 6; ++q) a.m0[q] = adj_ptr<float>(h, dst, q);
+  a.gamma = fld<float>(h, h->L.gamma, 0);
+  a.emap = reinterpret_cast<const float*>(h->ws + h->L.emap);
+  a.sens = sens;
+  a.sens_flow = sens_flow;
+  a.status = reinterpret_cast<int*>(h->ws + h->L.status);
+  a.ntx = (d.nx + COL_W - 1) / COL_W;
+  const int grid = a.ntx * ((d.ny + ACOL_H - 1) / ACOL_H);
+  static bool attr_set = false;  // per process: the attribute belongs to the kernel
+  if (!attr_set) {
+    CKH(h, cudaFuncSetAttribute(adj_col_kernel<SAME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)acol_smem_bytes(SAME)));
+    attr_set = true;
+  }
+  adj_col_kernel<SAME><<<grid, COL_NT, acol_smem_bytes(SAME), h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  CKH(h, cudaGetLastError());
+  h->acur = dst;
+  h->adj_steps++;
+  h->launches++;
+  h->adj_path = LKS_PATH_STEP;
+  return LKS_OK;
+}
+
 template <bool TH, bool SAME>
 lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
                           const float* T0, float* sens, int sens_flow, int sens_thermal) {
+  if constexpr (!TH) return launch_adj_col<SAME>(h, u1, v1, u0, v0, sens, sens_flow);
   constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
   constexpr int BW = kAdjTX + 8, BH = kAdjTY + 4;

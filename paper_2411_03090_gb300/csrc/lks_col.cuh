@@ -260,4 +260,205 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
   }
 }
 
+
+// ---------------------------------------------------------------------------------
+// Warp-column ALKS step (FP32, non-thermal, one lattice)
+// ---------------------------------------------------------------------------------
+// The same march for the adjoint: a lane computes P + c_k . V (Eq. afeq) of its node
+// for the nine links and the strain of the level-t state, hands the values a
+// neighbouring column gathers to it by shuffle, and completes the moments of a row
+// once the row below has been computed.  Tiles of 28 x 32 outputs (four warps of
+// eight rows); the per-node arithmetic is that of adj_tma_kernel, term for term.
+constexpr int ACOL_R = 8;
+constexpr int ACOL_H = COL_WARPS * ACOL_R;
+constexpr int ACOL_BH = ACOL_H + 4, ACOL_BOX = COL_BW * ACOL_BH;
+constexpr int ACOL_FS = (ACOL_BOX * 4 + 127) / 128 * 128 / 4;
+
+__host__ __device__ constexpr int acol_nf(bool same) { return same ? 10 : 12; }
+__host__ __device__ constexpr size_t acol_smem_bytes(bool same) {
+  return (size_t)acol_nf(same) * ACOL_FS * 4 + 128 + 8;
+}
+
+struct AdjColArgs {
+  float* m0[6];       // adjoint moments at level t
+  const float* gamma;
+  const float* emap;  // 9 classes x 6 x 10
+  float* sens;        // optional sensitivity accumulator
+  int sens_flow;
+  int* status;
+  int ntx;
+};
+
+// Staged fields: rho~, u~x, u~y, s~xx, s~xy, s~yy, u1, v1, [u0, v0], alpha, 1/(1+alpha).
+template <bool SAME>
+__global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__ TmaMaps<acol_nf(SAME)> maps,
+                                                         const __grid_constant__ AdjColArgs a,
+                                                         const __grid_constant__ Geom g,
+                                                         const __grid_constant__ Coef<float> c) {
+  constexpr int NF = acol_nf(SAME);
+  constexpr int FU0 = SAME ? 6 : 8, FAL = SAME ? 8 : 10, FBI = FAL + 1;
+  constexpr int BW = COL_BW;
+  extern __shared__ unsigned char smem_raw[];
+  float* box = reinterpret_cast<float*>(smem_base128(smem_raw));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(box + NF * ACOL_FS);
+  if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(box, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny;
+  const int x0 = (blockIdx.x % a.ntx) * COL_W, y0 = (blockIdx.x / a.ntx) * ACOL_H;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    mbar_expect_tx(bar, NF * ACOL_BOX * 4);
+    for (int f = 0; f < NF; ++f) tma_load_2d(box + f * ACOL_FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0) mbar_wait(bar, 0);
+    return;
+  }
+  const float* sa0 = box;
+  const float* sa1 = box + ACOL_FS;
+  const float* sa2 = box + 2 * ACOL_FS;
+  const float* sa3 = box + 3 * ACOL_FS;
+  const float* sa4 = box + 4 * ACOL_FS;
+  const float* sa5 = box + 5 * ACOL_FS;
+  const float* su1 = box + 6 * ACOL_FS;
+  const float* sv1 = box + 7 * ACOL_FS;
+  const float* su0 = box + FU0 * ACOL_FS;
+  const float* sv0 = box + (FU0 + 1) * ACOL_FS;
+  const float* sal = box + FAL * ACOL_FS;
+  const float* sbi = box + FBI * ACOL_FS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = x0 - 2 + lane;
+  const int bx = lane + 2;
+  const int r0 = y0 + warp * ACOL_R;
+  const bool out_lane = lane >= 2 && lane < 2 + COL_W && i < nx;
+  const bool fast = x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + ACOL_H + 2 <= ny;
+  auto brow = [&](int y) { return (y - y0 + 2) * BW; };
+
+  auto march = [&](auto edge_tag) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    float X[9], Y[9], Z[9];  // gathered P + c.V of output rows p-1, p, p+1
+#pragma unroll
+    for (int k = 0; k < 9; ++k) X[k] = Y[k] = Z[k] = 0.f;
+    float S0m = 0.f, S1m = 0.f, S2m = 0.f;  // strain of the level-t state, rows p-2 (m), p-1 (c), p (p)
+    float S0c = 0.f, S1c = 0.f, S2c = 0.f;
+    for (int p = r0 - 1; p <= r0 + ACOL_R; ++p) {
+      const int s2 = brow(p) + bx;
+      float Pq[9];
+      float S0p = 0.f, S1p = 0.f, S2p = 0.f;
+      const bool live = !EDGE || (i >= 0 && i < nx && p >= 0 && p < ny);
+      if (!live) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Pq[k] = 0.f;
+      } else {
+        const float rt = sa0[s2], ux = sa1[s2], uy = sa2[s2];
+        const float sxx = sa3[s2], sxy = sa4[s2], syy = sa5[s2];
+        const float uu = su1[s2], vv = sv1[s2];
+        float Dx, Dy;
+        if (EDGE) {
+          const int by = p - y0 + 2;
+          Dx = 2.f * (dfdx<float, BW>(sa3, bx, by, i, nx) + dfdy<float, BW>(sa4, bx, by, p, ny));
+          Dy = 2.f * (dfdx<float, BW>(sa4, bx, by, i, nx) + dfdy<float, BW>(sa5, bx, by, p, ny));
+        } else {
+          Dx = 2.f * ((sa3[s2 + 1] - sa3[s2 - 1]) * 0.5f + (sa4[s2 + BW] - sa4[s2 - BW]) * 0.5f);
+          Dy = 2.f * ((sa4[s2 + 1] - sa4[s2 - 1]) * 0.5f + (sa5[s2 + BW] - sa5[s2 - BW]) * 0.5f);
+        }
+        const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
+        const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
+#pragma unroll
+        for (int k = 0; k < 9; ++k) Pq[k] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
+        if (!EDGE || (i > 0 && p > 0 && i < nx - 1 && p < ny - 1)) {
+          S0p = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
+          S1p = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
+          S2p = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
+        }
+      }
+      // output x gathers P + c_k.V at x + c_k: row p - c_y, column from the lane c_x away
+      X[2] = Pq[2];
+      X[5] = __shfl_down_sync(0xffffffffu, Pq[5], 1);
+      X[6] = __shfl_up_sync(0xffffffffu, Pq[6], 1);
+      Y[0] = Pq[0];
+      Y[1] = __shfl_down_sync(0xffffffffu, Pq[1], 1);
+      Y[3] = __shfl_up_sync(0xffffffffu, Pq[3], 1);
+      Z[4] = Pq[4];
+      Z[7] = __shfl_up_sync(0xffffffffu, Pq[7], 1);
+      Z[8] = __shfl_down_sync(0xffffffffu, Pq[8], 1);
+      // strain of row p - 1 from the neighbour lanes (J source of output row p - 1)
+      const float S0l = __shfl_up_sync(0xffffffffu, S0c, 1), S0r = __shfl_down_sync(0xffffffffu, S0c, 1);
+      const float S1l = __shfl_up_sync(0xffffffffu, S1c, 1), S1r = __shfl_down_sync(0xffffffffu, S1c, 1);
+      const int q = p - 1;
+      if (q >= r0 && q < r0 + ACOL_R && q < ny && out_lane) {
+        const int sq = brow(q) + bx;
+        const bool interior = !EDGE || (i > 0 && q > 0 && i < nx - 1 && q < ny - 1);
+        float ft[9];
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ft[k] = X[k];
+        float m[6];
+        if (interior) {
+          const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+          const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
+          m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
+          m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
+          m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
+          m[3] = w1 * ax + w5 * dg;
+          m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
+          m[5] = w1 * ay + w5 * dg;
+          const float al = sal[sq];
+          const float uu0 = su0[sq], vv0 = sv0[sq];
+          const float ju = c.nu * (S0l - S0r + S1m - S1p) + 2.f * al * uu0;
+          const float jv = c.nu * (S2m - S2p + S1l - S1r) + 2.f * al * vv0;
+          const float cpx = 0.f, cpy = 0.f;
+          const float inv = sbi[sq];
+          m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
+          m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
+          if (a.sens) {
+            const size_t gi = (size_t)q * nx + i;
+            const float gm = __ldg(a.gamma + gi);
+            float sacc = 0.f;
+            if (a.sens_flow) {
+              const float dd = c.q_alpha + gm;
+              const float da = __fdividef(-c.alpha_bar * c.q_alpha * (1.f + c.q_alpha), dd * dd);
+              sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
+            }
+            a.sens[gi] += sacc;
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) {
+            const int gi = i + cxk(k), gj = q + cyk(k);
+            if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = 0.f;
+          }
+          const float kT = 0.f;
+          const float* M = a.emap + edge_class(g, i, q) * 60;
+#pragma unroll
+          for (int r = 0; r < 6; ++r) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
+            m[r] = acc + M[r * 10 + 9] * kT;
+          }
+        }
+        (void)sq;
+        const size_t o = (size_t)q * nx + i;
+#pragma unroll
+        for (int f = 0; f < 6; ++f) a.m0[f][o] = m[f];
+        if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
+      }
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        X[k] = Y[k];
+        Y[k] = Z[k];
+        Z[k] = 0.f;
+      }
+      S0m = S0c, S1m = S1c, S2m = S2c;
+      S0c = S0p, S1c = S1p, S2c = S2p;
+    }
+  };
+  if (fast) march(std::false_type{});
+  else march(std::true_type{});
+}
+
 }  // namespace lks
