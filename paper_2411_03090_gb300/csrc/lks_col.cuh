@@ -252,8 +252,99 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
       }
     }
   };
-  if (fast) march(std::false_type{});
-  else march(std::true_type{});
+  // Interior tiles: the same march unrolled by three rows, so that the three-row
+  // register rings rotate by renaming; each row's neighbour values are shuffled
+  // once, when the row is loaded.
+  struct Row {
+    float d, u, v, dl, dr;  // drho, u, v of the lane's column and drho of the columns left and right
+  };
+  auto load_row = [&](Row& R, int y) {
+    const int o = brow(y) + bx;
+    R.d = sdr[o];
+    R.u = su[o];
+    R.v = sv[o];
+    R.dl = __shfl_up_sync(0xffffffffu, R.d, 1);
+    R.dr = __shfl_down_sync(0xffffffffu, R.d, 1);
+  };
+  // One row p of the march: A, B, C hold rows p-1, p, p+1; X, Y, Z collect the
+  // populations of destination rows p-1, p, p+1.  Row p+2 is loaded into A.
+  auto step = [&](int p, Row& A, Row& B, Row& C, float* X, float* Y, float* Z) {
+    const float uL = __shfl_up_sync(0xffffffffu, B.u, 1), uR = __shfl_down_sync(0xffffffffu, B.u, 1);
+    const float vL = __shfl_up_sync(0xffffffffu, B.v, 1), vR = __shfl_down_sync(0xffffffffu, B.v, 1);
+    const float uu = B.u, vv = B.v;
+    const float dudx = (uR - uL) * 0.5f;
+    const float dudy = (C.u - A.u) * 0.5f;
+    const float dvdx = (vR - vL) * 0.5f;
+    const float dvdy = (C.v - A.v) * 0.5f;
+    const float dr = B.d;
+    const float e0 = -1.5f * (uu * uu + vv * vv);
+    const float bxv = 3.f * uu, byv = 3.f * vv;
+    const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
+    const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
+    const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
+    float F[9];
+    F[0] = e0 * (4.f / 9.f);
+    F[1] = ((dr - B.dr) + e0 + bxv + qxx) * (1.f / 9.f);
+    F[3] = ((dr - B.dl) + e0 - bxv + qxx) * (1.f / 9.f);
+    F[2] = ((dr - C.d) + e0 + byv + qyy) * (1.f / 9.f);
+    F[4] = ((dr - A.d) + e0 - byv + qyy) * (1.f / 9.f);
+    const float d0 = e0 + qxx + qyy;
+    F[5] = (((dr - C.dr) + d0) + bxv + byv + qxy) * (1.f / 36.f);
+    F[6] = (((dr - C.dl) + d0) - bxv + byv - qxy) * (1.f / 36.f);
+    F[7] = (((dr - A.dl) + d0) - bxv - byv + qxy) * (1.f / 36.f);
+    F[8] = (((dr - A.dr) + d0) + bxv - byv - qxy) * (1.f / 36.f);
+    const int s2 = brow(p) + bx;
+    if (a.J_partial && out_lane && p >= r0 && p < r0 + COL_R) {
+      const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
+      const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
+      const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
+      const float al = __fdividef(1.f, sbi[s2]) - 1.f;
+      jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+    }
+    X[4] = F[4];
+    X[7] = __shfl_down_sync(0xffffffffu, F[7], 1);
+    X[8] = __shfl_up_sync(0xffffffffu, F[8], 1);
+    Y[0] = F[0];
+    Y[1] = __shfl_up_sync(0xffffffffu, F[1], 1);
+    Y[3] = __shfl_down_sync(0xffffffffu, F[3], 1);
+    Z[2] = F[2];
+    Z[5] = __shfl_up_sync(0xffffffffu, F[5], 1);
+    Z[6] = __shfl_down_sync(0xffffffffu, F[6], 1);
+    const int q = p - 1;
+    if (q >= r0 && out_lane) {  // row p - 1 is complete
+      const float* fk = X;
+      const float drn = A.d + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
+      const float inv = sbi[s2 - BW];
+      const float un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
+      const float vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+      const size_t o = (size_t)q * nx + i;
+      a.out[0][o] = drn;
+      a.out[1][o] = un;
+      a.out[2][o] = vn;
+      if (a.traj_u) {
+        a.traj_u[o] = un;
+        a.traj_v[o] = vn;
+      }
+      if (bad_velocity(un, vn)) raise_status(a.status, 4);
+    }
+    if (p + 2 <= r0 + COL_R + 1) load_row(A, p + 2);
+  };
+  if (fast) {
+    Row R0, R1, R2;
+    float X0[9], X1[9], X2[9];
+    load_row(R0, r0 - 2);
+    load_row(R1, r0 - 1);
+    load_row(R2, r0);
+    static_assert((COL_R + 2) % 3 == 0, "the unrolled march covers COL_R + 2 rows in threes");
+#pragma unroll 1
+    for (int p = r0 - 1; p <= r0 + COL_R; p += 3) {
+      step(p, R0, R1, R2, X0, X1, X2);
+      step(p + 1, R1, R2, R0, X1, X2, X0);
+      step(p + 2, R2, R0, R1, X2, X0, X1);
+    }
+  } else {
+    march(std::true_type{});
+  }
   if (a.J_partial) {
     const double s = block_sum<COL_NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
