@@ -56,10 +56,19 @@ typedef enum { LKS_REAL_F32 = 0, LKS_REAL_F64 = 1 } lks_real_type;
 /* Storage type of checkpoint snapshots (unsteady problems). */
 typedef enum { LKS_SNAP_F32 = 0, LKS_SNAP_BF16 = 1, LKS_SNAP_F16 = 2 } lks_snap_type;
 
-/* How the steady marches run: one kernel launch per time step over 32x16 tiles,
- * or one cooperative launch per march in which every tile stays resident in the
- * shared memory of its CTA (lattices whose tiles fit the GPU at once). */
-typedef enum { LKS_PATH_AUTO = 0, LKS_PATH_STEP = 1, LKS_PATH_RESIDENT = 2 } lks_exec_path;
+/* How the marches run.  STEP: one kernel launch per time step (FP32 lattices with
+ * nx % 4 == 0 stage their tiles by tensor copies; large non-thermal FP32 lattices,
+ * with at least four column tiles per SM, use the warp-column kernels).  RESIDENT:
+ * one cooperative launch per steady march in which every tile stays resident in
+ * the shared memory of its CTA (lattices whose tiles fit the GPU at once).  COLUMN:
+ * one launch per step of the warp-column kernels at any size (FP32, non-thermal,
+ * nx % 4 == 0; otherwise as STEP).  AUTO: RESIDENT where it fits, else STEP. */
+typedef enum {
+  LKS_PATH_AUTO = 0,
+  LKS_PATH_STEP = 1,
+  LKS_PATH_RESIDENT = 2,
+  LKS_PATH_COLUMN = 3
+} lks_exec_path;
 
 /* Thermal edge conditions (Sec. 2.4): prescribed temperature T = T_bar, or
  * prescribed heat flux -q.n = q_bar_w. */
@@ -97,7 +106,8 @@ typedef struct {
     int32_t snapshot_type;    /* lks_snap_type of the checkpoint snapshots           */
     int32_t exec_path;        /* lks_exec_path: 0 automatic, 1 one kernel launch per
                                  step, 2 resident persistent march (steady problems
-                                 whose tiles fit on the GPU at once)                 */
+                                 whose tiles fit on the GPU at once), 3 warp-column
+                                 kernels per step                                    */
     int32_t lattice;          /* lks_lattice: 0 D2Q9 (default), 1 D3Q19 (see below)   */
     int32_t nz;               /* D3Q19: nodes along z, >= 5; D2Q9: 0 or 1            */
     int32_t reserved[5];      /* must be zero                                        */

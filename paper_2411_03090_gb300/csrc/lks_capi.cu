@@ -46,6 +46,9 @@ struct Layout {
   size_t N = 0, rsize = 4, snap_elem = 4;
 };
 
+// Tile shapes of the TMA-staged per-step kernels.
+constexpr int kFwdTX = 64, kFwdTY = 8, kAdjTX = 64, kAdjTY = 8;
+
 int obj_grid(size_t N) { return (int)std::min<size_t>((N + NTHREADS - 1) / NTHREADS, 1024); }
 
 Layout make_layout(const lks_problem_desc* d) {
@@ -57,7 +60,10 @@ Layout make_layout(const lks_problem_desc* d) {
   L.nT = d->thermal ? 3 : 2;
   const int gx = (d->nx + TX - 1) / TX, gy = (d->ny + TY - 1) / TY;
   const int col_tiles = ((d->nx + COL_W - 1) / COL_W) * ((d->ny + COL_H - 1) / COL_H);
-  L.fwd_blocks = std::max(gx * gy, col_tiles);  // J partials: one per block of the largest forward grid
+  const int tma_tiles = ((d->nx + kFwdTX - 1) / kFwdTX) * ((d->ny + kFwdTY - 1) / kFwdTY);
+  // J partials: one per CTA of the largest forward grid (the persistent TMA grid is
+  // at most one CTA per tile)
+  L.fwd_blocks = std::max(std::max(gx * gy, col_tiles), tma_tiles);
   L.obj_blocks = obj_grid(L.N);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -119,6 +125,7 @@ struct lks_handle {
   std::vector<float> emap_f;
   std::unordered_map<uint64_t, CUtensorMap> tmaps;  // (pointer, box) -> tensor map
   int tma_grid_fwd = 0, tma_grid_adj[2][2] = {{0, 0}, {0, 0}};  // adj: [thermal][same state]
+  int sms = 0;        // multiprocessors of the device (queried once)
   bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
   lks3::Layout3 L3;
   std::string err;
@@ -275,9 +282,9 @@ struct ResPlan {
 constexpr int kResCfg[3][3] = {{64, 16, 512}, {32, 16, 256}, {32, 8, 256}};
 
 int device_sms(lks_handle* h) {
-  int sms = 0;
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
-  return sms;
+  if (h->sms == 0 && cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
+    h->sms = 0;
+  return h->sms > 0 ? h->sms : 1;
 }
 
 size_t res_smem_bytes(const lks_problem_desc& d, bool adjoint, int cfg) {
@@ -308,7 +315,7 @@ ResPlan plan_resident(lks_handle* h, bool adjoint) {
 }
 
 bool resident_wanted(lks_handle* h, bool adjoint) {
-  if (h->d.exec_path == LKS_PATH_STEP || !h->d.steady) return false;
+  if (h->d.exec_path == LKS_PATH_STEP || h->d.exec_path == LKS_PATH_COLUMN || !h->d.steady) return false;
   if (adjoint && h->d.thermal) return false;
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
@@ -403,7 +410,6 @@ lks_status launch_adj_resident(lks_handle* h, int n) {
 // ------------------------------------------------------------------------------------
 // TMA-staged per-step kernels (FP32, nx % 4 == 0)
 // ------------------------------------------------------------------------------------
-constexpr int kFwdTX = 64, kFwdTY = 8, kAdjTX = 64, kAdjTY = 8;
 constexpr int kFwdNT = 256, kAdjNT = 512;
 
 bool tma_ok(lks_handle* h) {
@@ -440,6 +446,14 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
   return std::max(1, std::min(ntiles, per_sm * device_sms(h)));
 }
 
+// Warp-column kernels: asked for, or the lattice has at least four column tiles per
+// SM (below that the per-tile TMA kernels, with fewer edge tiles, are faster).
+bool use_col(lks_handle* h) {
+  if (h->d.exec_path == LKS_PATH_COLUMN) return true;
+  const long long tiles = (long long)((h->d.nx + COL_W - 1) / COL_W) * ((h->d.ny + COL_H - 1) / COL_H);
+  return tiles >= 4ll * device_sms(h);
+}
+
 // Warp-column forward (FP32, non-thermal, one lattice): one CTA per 28 x 64 tile.
 lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv) {
   const auto& d = h->d;
@@ -465,13 +479,14 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
   h->t = t_new;
   h->fwd_steps++;
   h->launches++;
-  h->fwd_path = LKS_PATH_STEP;
+  h->fwd_path = LKS_PATH_COLUMN;
   return LKS_OK;
 }
 
 template <bool TH>
 lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
-  if constexpr (!TH) return launch_fwd_col(h, t_new, Jpartial, tu, tv);
+  if constexpr (!TH)
+    if (use_col(h)) return launch_fwd_col(h, t_new, Jpartial, tu, tv);
   constexpr int NF = fwd_tma_nf(TH);
   constexpr int BW = kFwdTX + 8, BH = kFwdTY + 4;
   const auto& d = h->d;
@@ -516,6 +531,7 @@ lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu,
     CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     h->tma_grid_fwd = persistent_grid(h, kern, kFwdNT, smem, a.ntiles);
   }
+  if (Jpartial && h->tma_grid_fwd > h->L.fwd_blocks) return fail(h, LKS_ERR_WORKSPACE, "objective partials undersized");
   kern<<<h->tma_grid_fwd, kFwdNT, smem, h->stream>>>(maps, omaps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->cur = dst;
@@ -564,14 +580,15 @@ lks_status launch_adj_col(lks_handle* h, const float* u1, const float* v1, const
   h->acur = dst;
   h->adj_steps++;
   h->launches++;
-  h->adj_path = LKS_PATH_STEP;
+  h->adj_path = LKS_PATH_COLUMN;
   return LKS_OK;
 }
 
 template <bool TH, bool SAME>
 lks_status launch_adj_tma(lks_handle* h, const float* u1, const float* v1, const float* u0, const float* v0,
                           const float* T0, float* sens, int sens_flow, int sens_thermal) {
-  if constexpr (!TH) return launch_adj_col<SAME>(h, u1, v1, u0, v0, sens, sens_flow);
+  if constexpr (!TH)
+    if (use_col(h)) return launch_adj_col<SAME>(h, u1, v1, u0, v0, sens, sens_flow);
   constexpr int NF = adj_tma_nf(TH, SAME);
   constexpr int NA = TH ? 9 : 6;
   constexpr int BW = kAdjTX + 8, BH = kAdjTY + 4;

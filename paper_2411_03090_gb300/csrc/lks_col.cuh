@@ -103,10 +103,10 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
         const float cL = __shfl_up_sync(0xffffffffu, dC, 1), cR = __shfl_down_sync(0xffffffffu, dC, 1);
         uu = uB;
         vv = vB;
-        dudx = (uR - uL) * 0.5f;
-        dudy = (uC - uA) * 0.5f;
-        dvdx = (vR - vL) * 0.5f;
-        dvdy = (vC - vA) * 0.5f;
+        dudx = cdiff(uR, uL);
+        dudy = cdiff(uC, uA);
+        dvdx = cdiff(vR, vL);
+        dvdy = cdiff(vC, vA);
         dr = dB;
         d_e = bR, d_w = bL, d_n = dC, d_s = dA, d_ne = cR, d_nw = cL, d_sw = aL, d_se = aR;
         has_obj = true;
@@ -139,21 +139,8 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
         }
       }
       if (live) {
-        const float e0 = -1.5f * (uu * uu + vv * vv);
-        const float bxv = 3.f * uu, byv = 3.f * vv;
-        const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
-        const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
-        const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
-        F[0] = e0 * (4.f / 9.f);
-        F[1] = ((dr - d_e) + e0 + bxv + qxx) * (1.f / 9.f);
-        F[3] = ((dr - d_w) + e0 - bxv + qxx) * (1.f / 9.f);
-        F[2] = ((dr - d_n) + e0 + byv + qyy) * (1.f / 9.f);
-        F[4] = ((dr - d_s) + e0 - byv + qyy) * (1.f / 9.f);
-        const float d0 = e0 + qxx + qyy;
-        F[5] = (((dr - d_ne) + d0) + bxv + byv + qxy) * (1.f / 36.f);
-        F[6] = (((dr - d_nw) + d0) - bxv + byv - qxy) * (1.f / 36.f);
-        F[7] = (((dr - d_sw) + d0) - bxv - byv + qxy) * (1.f / 36.f);
-        F[8] = (((dr - d_se) + d0) + bxv - byv - qxy) * (1.f / 36.f);
+        const float dn[9] = {0.f, d_e, d_n, d_w, d_s, d_ne, d_nw, d_sw, d_se};
+        push9(dr, dn, uu, vv, dudx, dudy, dvdx, dvdy, c.A, F);
         // objective of the old state at this warp's output nodes (unsteady accumulation)
         if (a.J_partial && has_obj && out_lane && p >= r0 && p < r0 + COL_R && p < ny) {
           const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
@@ -191,10 +178,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
         const int cls = EDGE ? node_class(g, i, q, nxo, nyo) : C_INTERIOR;
         const float* fk = X;
         if (cls == C_INTERIOR) {
-          drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
-          const float inv = sbi[sq];
-          un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
-          vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+          gather9(fk, drx, sbi[sq], drn, un, vn);
         } else {
           float s0 = 0.f, sp = 0.f;
 #pragma unroll
@@ -217,12 +201,12 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
               un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
             }
             vn = 0.f;
-            drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
+            drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));
           } else {
             drn = c.drho_out;
-            const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
-            un = unorm * (float)nxo;
-            vn = unorm * (float)nyo;
+            const float unorm = __fadd_rn(__fmaf_rn(2.f, sp, s0), __fsub_rn(drx, c.drho_out));
+            un = __fmul_rn(unorm, (float)nxo);
+            vn = __fmul_rn(unorm, (float)nyo);
           }
         }
         const size_t o = (size_t)q * nx + i;
@@ -272,27 +256,12 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
     const float uL = __shfl_up_sync(0xffffffffu, B.u, 1), uR = __shfl_down_sync(0xffffffffu, B.u, 1);
     const float vL = __shfl_up_sync(0xffffffffu, B.v, 1), vR = __shfl_down_sync(0xffffffffu, B.v, 1);
     const float uu = B.u, vv = B.v;
-    const float dudx = (uR - uL) * 0.5f;
-    const float dudy = (C.u - A.u) * 0.5f;
-    const float dvdx = (vR - vL) * 0.5f;
-    const float dvdy = (C.v - A.v) * 0.5f;
     const float dr = B.d;
-    const float e0 = -1.5f * (uu * uu + vv * vv);
-    const float bxv = 3.f * uu, byv = 3.f * vv;
-    const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
-    const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
-    const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
     float F[9];
-    F[0] = e0 * (4.f / 9.f);
-    F[1] = ((dr - B.dr) + e0 + bxv + qxx) * (1.f / 9.f);
-    F[3] = ((dr - B.dl) + e0 - bxv + qxx) * (1.f / 9.f);
-    F[2] = ((dr - C.d) + e0 + byv + qyy) * (1.f / 9.f);
-    F[4] = ((dr - A.d) + e0 - byv + qyy) * (1.f / 9.f);
-    const float d0 = e0 + qxx + qyy;
-    F[5] = (((dr - C.dr) + d0) + bxv + byv + qxy) * (1.f / 36.f);
-    F[6] = (((dr - C.dl) + d0) - bxv + byv - qxy) * (1.f / 36.f);
-    F[7] = (((dr - A.dl) + d0) - bxv - byv + qxy) * (1.f / 36.f);
-    F[8] = (((dr - A.dr) + d0) + bxv - byv - qxy) * (1.f / 36.f);
+    {
+      const float dn[9] = {0.f, B.dr, C.d, B.dl, A.d, C.dr, C.dl, A.dl, A.dr};
+      push9(dr, dn, uu, vv, cdiff(uR, uL), cdiff(C.u, A.u), cdiff(vR, vL), cdiff(C.v, A.v), c.A, F);
+    }
     const int s2 = brow(p) + bx;
     if (a.J_partial && out_lane && p >= r0 && p < r0 + COL_R) {
       const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
@@ -312,11 +281,8 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
     Z[6] = __shfl_down_sync(0xffffffffu, F[6], 1);
     const int q = p - 1;
     if (q >= r0 && out_lane) {  // row p - 1 is complete
-      const float* fk = X;
-      const float drn = A.d + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
-      const float inv = sbi[s2 - BW];
-      const float un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
-      const float vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+      float drn, un, vn;
+      gather9(X, A.d, sbi[s2 - BW], drn, un, vn);
       const size_t o = (size_t)q * nx + i;
       a.out[0][o] = drn;
       a.out[1][o] = un;
@@ -451,20 +417,17 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
         float Dx, Dy;
         if (EDGE) {
           const int by = p - y0 + 2;
-          Dx = 2.f * (dfdx<float, BW>(sa3, bx, by, i, nx) + dfdy<float, BW>(sa4, bx, by, p, ny));
-          Dy = 2.f * (dfdx<float, BW>(sa4, bx, by, i, nx) + dfdy<float, BW>(sa5, bx, by, p, ny));
+          Dx = adj_div2(dfdx<float, BW>(sa3, bx, by, i, nx), dfdy<float, BW>(sa4, bx, by, p, ny));
+          Dy = adj_div2(dfdx<float, BW>(sa4, bx, by, i, nx), dfdy<float, BW>(sa5, bx, by, p, ny));
         } else {
-          Dx = 2.f * ((sa3[s2 + 1] - sa3[s2 - 1]) * 0.5f + (sa4[s2 + BW] - sa4[s2 - BW]) * 0.5f);
-          Dy = 2.f * ((sa4[s2 + 1] - sa4[s2 - 1]) * 0.5f + (sa5[s2 + BW] - sa5[s2 - BW]) * 0.5f);
+          Dx = adj_div2(cdiff(sa3[s2 + 1], sa3[s2 - 1]), cdiff(sa4[s2 + BW], sa4[s2 - BW]));
+          Dy = adj_div2(cdiff(sa4[s2 + 1], sa4[s2 - 1]), cdiff(sa5[s2 + BW], sa5[s2 - BW]));
         }
-        const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
-        const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
-#pragma unroll
-        for (int k = 0; k < 9; ++k) Pq[k] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
+        adj_pv9(rt, ux, uy, sxx, sxy, syy, uu, vv, Dx, Dy, c.A, Pq);
         if (!EDGE || (i > 0 && p > 0 && i < nx - 1 && p < ny - 1)) {
-          S0p = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
-          S1p = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
-          S2p = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
+          S0p = __fmul_rn(2.f, cdiff(su0[s2 + 1], su0[s2 - 1]));
+          S1p = __fadd_rn(cdiff(su0[s2 + BW], su0[s2 - BW]), cdiff(sv0[s2 + 1], sv0[s2 - 1]));
+          S2p = __fmul_rn(2.f, cdiff(sv0[s2 + BW], sv0[s2 - BW]));
         }
       }
       // output x gathers P + c_k.V at x + c_k: row p - c_y, column from the lane c_x away
@@ -489,31 +452,19 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
         for (int k = 0; k < 9; ++k) ft[k] = X[k];
         float m[6];
         if (interior) {
-          const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-          const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
-          m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
-          m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
-          m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
-          m[3] = w1 * ax + w5 * dg;
-          m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
-          m[5] = w1 * ay + w5 * dg;
+          adj_moments6(ft, m);
           const float al = sal[sq];
           const float uu0 = su0[sq], vv0 = sv0[sq];
-          const float ju = c.nu * (S0l - S0r + S1m - S1p) + 2.f * al * uu0;
-          const float jv = c.nu * (S2m - S2p + S1l - S1r) + 2.f * al * vv0;
-          const float cpx = 0.f, cpy = 0.f;
+          const float ju = adj_jsrc(c.nu, __fsub_rn(__fadd_rn(__fsub_rn(S0l, S0r), S1m), S1p), al, uu0);
+          const float jv = adj_jsrc(c.nu, __fsub_rn(__fadd_rn(__fsub_rn(S2m, S2p), S1l), S1r), al, vv0);
           const float inv = sbi[sq];
-          m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
-          m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
+          m[1] = adj_brinkman(m[1], ju, 0.f, inv);
+          m[2] = adj_brinkman(m[2], jv, 0.f, inv);
           if (a.sens) {
             const size_t gi = (size_t)q * nx + i;
             const float gm = __ldg(a.gamma + gi);
             float sacc = 0.f;
-            if (a.sens_flow) {
-              const float dd = c.q_alpha + gm;
-              const float da = __fdividef(-c.alpha_bar * c.q_alpha * (1.f + c.q_alpha), dd * dd);
-              sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
-            }
+            if (a.sens_flow) sacc = __fadd_rn(sacc, sens_flow_term(c, gm, uu0, vv0, m[1], m[2]));
             a.sens[gi] += sacc;
           }
         } else {
@@ -522,15 +473,9 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
             const int gi = i + cxk(k), gj = q + cyk(k);
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = 0.f;
           }
-          const float kT = 0.f;
           const float* M = a.emap + edge_class(g, i, q) * 60;
 #pragma unroll
-          for (int r = 0; r < 6; ++r) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
-            m[r] = acc + M[r * 10 + 9] * kT;
-          }
+          for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, 0.f);
         }
         (void)sq;
         const size_t o = (size_t)q * nx + i;

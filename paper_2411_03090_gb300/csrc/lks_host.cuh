@@ -60,7 +60,7 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   }
   if (d->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
-  if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_RESIDENT) return bad("bad exec_path");
+  if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
   for (int q = 0; q < 5; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;

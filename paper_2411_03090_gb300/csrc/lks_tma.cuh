@@ -101,6 +101,107 @@ __device__ __forceinline__ void bulk_wait0() { asm volatile("cp.async.bulk.wait_
 __device__ __forceinline__ void fence_proxy_async() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory"); }
 
+
+// ---------------------------------------------------------------------------------
+// Per-node arithmetic of the FP32 staged kernels, written with explicit rounding
+// (every product and sum named, no contraction left to the compiler), so that the
+// per-tile, batched and warp-column kernels give bit-identical results.
+// ---------------------------------------------------------------------------------
+// Central difference (f[+1] - f[-1]) / 2.
+__device__ __forceinline__ float cdiff(float fp, float fm) { return __fmul_rn(__fsub_rn(fp, fm), 0.5f); }
+
+// The nine pushed populations of one node (Eq. feq2, increment form): F_k is sent
+// to x + c_k and carries w_k [(drho(x) - drho(x + c_k)) + e0 + c_k.b + c_k c_k : Q].
+// d[k] = drho(x + c_k) for k = 1..8 (d[0] unused).
+__device__ __forceinline__ void push9(float dr, const float* d, float uu, float vv, float dudx, float dudy,
+                                      float dvdx, float dvdy, float A, float* F) {
+  const float e0 = __fmul_rn(-1.5f, __fmaf_rn(vv, vv, __fmul_rn(uu, uu)));
+  const float bx = __fmul_rn(3.f, uu), by = __fmul_rn(3.f, vv);
+  const float A2 = __fmul_rn(2.f, A);
+  const float qxx = __fmaf_rn(A2, dudx, __fmul_rn(__fmul_rn(4.5f, uu), uu));
+  const float qyy = __fmaf_rn(A2, dvdy, __fmul_rn(__fmul_rn(4.5f, vv), vv));
+  const float qxy = __fmaf_rn(A2, __fadd_rn(dudy, dvdx), __fmul_rn(__fmul_rn(9.f, uu), vv));
+  const float d0 = __fadd_rn(__fadd_rn(e0, qxx), qyy);
+  F[0] = __fmul_rn(e0, 4.f / 9.f);
+  F[1] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[1]), e0), bx), qxx), 1.f / 9.f);
+  F[3] = __fmul_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[3]), e0), bx), qxx), 1.f / 9.f);
+  F[2] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[2]), e0), by), qyy), 1.f / 9.f);
+  F[4] = __fmul_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[4]), e0), by), qyy), 1.f / 9.f);
+  F[5] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[5]), d0), bx), by), qxy), 1.f / 36.f);
+  F[6] = __fmul_rn(__fsub_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[6]), d0), bx), by), qxy), 1.f / 36.f);
+  F[7] = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[7]), d0), bx), by), qxy), 1.f / 36.f);
+  F[8] = __fmul_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[8]), d0), bx), by), qxy), 1.f / 36.f);
+}
+
+// Interior gather of one node: drho, and u, v before / after the implicit Brinkman
+// division (fk[k] = F_k(x - c_k)).
+__device__ __forceinline__ void gather9(const float* fk, float drx, float inv, float& drn, float& un, float& vn) {
+  drn = __fadd_rn(drx, __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(fk[0], fk[1]), __fadd_rn(fk[2], fk[3])),
+                                           __fadd_rn(__fadd_rn(fk[4], fk[5]), __fadd_rn(fk[6], fk[7]))),
+                                 fk[8]));
+  un = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fsub_rn(fk[1], fk[3]), fk[5]), fk[6]), fk[7]), fk[8]), inv);
+  vn = __fmul_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(fk[2], fk[4]), fk[5]), fk[6]), fk[7]), fk[8]), inv);
+}
+
+// Adjoint equilibrium coefficients of one node (Eq. afeq): Pq[k] = P + c_k . V with
+// P = rho~, V_a = 3 (u~_a + 3 s~_ab u_b - rho~ u_a) - A D_a.
+__device__ __forceinline__ void adj_pv9(float rt, float ux, float uy, float sxx, float sxy, float syy, float uu,
+                                        float vv, float Dx, float Dy, float A, float* Pq) {
+  const float tx = __fsub_rn(__fmaf_rn(3.f, __fmaf_rn(sxy, vv, __fmul_rn(sxx, uu)), ux), __fmul_rn(rt, uu));
+  const float ty = __fsub_rn(__fmaf_rn(3.f, __fmaf_rn(syy, vv, __fmul_rn(sxy, uu)), uy), __fmul_rn(rt, vv));
+  const float Vx = __fsub_rn(__fmul_rn(3.f, tx), __fmul_rn(A, Dx));
+  const float Vy = __fsub_rn(__fmul_rn(3.f, ty), __fmul_rn(A, Dy));
+  const float rp = __fadd_rn(rt, Vx), rm = __fsub_rn(rt, Vx);
+  Pq[0] = rt;
+  Pq[1] = rp;
+  Pq[3] = rm;
+  Pq[2] = __fadd_rn(rt, Vy);
+  Pq[4] = __fsub_rn(rt, Vy);
+  Pq[5] = __fadd_rn(rp, Vy);
+  Pq[6] = __fadd_rn(rm, Vy);
+  Pq[7] = __fsub_rn(rm, Vy);
+  Pq[8] = __fsub_rn(rp, Vy);
+}
+// D_x = 2 (d_x s~xx + d_y s~xy), D_y = 2 (d_x s~xy + d_y s~yy) from the four derivatives.
+__device__ __forceinline__ float adj_div2(float d1, float d2) { return __fmul_rn(2.f, __fadd_rn(d1, d2)); }
+
+// Interior adjoint moments (rho~, u~*, s~) of the gathered f~ (ft[k] = P + c_k.V at x + c_k).
+__device__ __forceinline__ void adj_moments6(const float* ft, float* m) {
+  const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+  const float ax = __fadd_rn(ft[1], ft[3]), ay = __fadd_rn(ft[2], ft[4]);
+  const float dg = __fadd_rn(__fadd_rn(__fadd_rn(ft[5], ft[6]), ft[7]), ft[8]);
+  m[0] = __fmaf_rn(w5, dg, __fmaf_rn(w1, __fadd_rn(ax, ay), __fmul_rn(w0, ft[0])));
+  m[1] = __fmaf_rn(w5, __fadd_rn(__fsub_rn(__fsub_rn(ft[5], ft[6]), ft[7]), ft[8]), __fmul_rn(w1, __fsub_rn(ft[1], ft[3])));
+  m[2] = __fmaf_rn(w5, __fsub_rn(__fsub_rn(__fadd_rn(ft[5], ft[6]), ft[7]), ft[8]), __fmul_rn(w1, __fsub_rn(ft[2], ft[4])));
+  m[3] = __fmaf_rn(w5, dg, __fmul_rn(w1, ax));
+  m[4] = __fmul_rn(w5, __fsub_rn(__fadd_rn(__fsub_rn(ft[5], ft[6]), ft[7]), ft[8]));
+  m[5] = __fmaf_rn(w5, dg, __fmul_rn(w1, ay));
+}
+// Objective source of one velocity component: nu (sum of strain differences) + 2 alpha u.
+__device__ __forceinline__ float adj_jsrc(float nu, float diff, float al, float u0) {
+  return __fmaf_rn(__fmul_rn(2.f, al), u0, __fmul_rn(nu, diff));
+}
+// Implicit adjoint Brinkman: (m - j/3 + coupling) / (1 + alpha).
+__device__ __forceinline__ float adj_brinkman(float m, float j, float cp, float inv) {
+  return __fmul_rn(__fadd_rn(__fsub_rn(m, __fmul_rn(j, 1.f / 3.f)), cp), inv);
+}
+// Edge-node moment r from a 6 x 10 map row and the gathered f~ (unknown entries zero).
+__device__ __forceinline__ float adj_edge_row(const float* Mr, const float* ft, float kT) {
+  float acc = 0.f;
+#pragma unroll
+  for (int k = 0; k < 9; ++k) acc = __fmaf_rn(Mr[k], ft[k], acc);
+  return __fmaf_rn(Mr[9], kT, acc);
+}
+// Flow sensitivity of one level: alpha' |u|^2 + 3 alpha' u.u~.
+__device__ __forceinline__ float sens_flow_term(const Coef<float>& c, float gm, float uu0, float vv0, float m1,
+                                                float m2) {
+  const float dd = __fadd_rn(c.q_alpha, gm);
+  const float da = __fdividef(-c.alpha_bar * c.q_alpha * (1.f + c.q_alpha), __fmul_rn(dd, dd));
+  const float uuu = __fmaf_rn(vv0, vv0, __fmul_rn(uu0, uu0));
+  const float uut = __fmaf_rn(vv0, m2, __fmul_rn(uu0, m1));
+  return __fmaf_rn(__fmul_rn(3.f, da), uut, __fmul_rn(da, uuu));
+}
+
 // Material fields of one march: 1 / (1 + alpha_gamma), alpha_gamma (Eq. brinkman)
 // and B_gamma (Eqs. conductivity, B), one float each per node.
 static __global__ void material_kernel(const float* __restrict__ gamma, size_t n, Coef<float> c, float* __restrict__ binv,
@@ -319,27 +420,20 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
             dvdy = -dudx;
           }
         } else {
-          dudx = (su[s2 + 1] - su[s2 - 1]) * 0.5f;
-          dudy = (su[s2 + BW] - su[s2 - BW]) * 0.5f;
-          dvdx = (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
-          dvdy = (sv[s2 + BW] - sv[s2 - BW]) * 0.5f;
+          dudx = cdiff(su[s2 + 1], su[s2 - 1]);
+          dudy = cdiff(su[s2 + BW], su[s2 - BW]);
+          dvdx = cdiff(sv[s2 + 1], sv[s2 - 1]);
+          dvdy = cdiff(sv[s2 + BW], sv[s2 - BW]);
         }
-        const float e0 = -1.5f * (uu * uu + vv * vv);
-        const float bx = 3.f * uu, by = 3.f * vv;
-        const float qxx = 4.5f * uu * uu + c.A * (2.f * dudx);
-        const float qyy = 4.5f * vv * vv + c.A * (2.f * dvdy);
-        const float qxy = 9.f * uu * vv + 2.f * c.A * (dudy + dvdx);
         const float dr = sdr[s2];
-        F[q] = e0 * (4.f / 9.f);
-        F[1 * A1 + q] = ((dr - sdr[s2 + 1]) + e0 + bx + qxx) * (1.f / 9.f);
-        F[3 * A1 + q] = ((dr - sdr[s2 - 1]) + e0 - bx + qxx) * (1.f / 9.f);
-        F[2 * A1 + q] = ((dr - sdr[s2 + BW]) + e0 + by + qyy) * (1.f / 9.f);
-        F[4 * A1 + q] = ((dr - sdr[s2 - BW]) + e0 - by + qyy) * (1.f / 9.f);
-        const float d0 = e0 + qxx + qyy;
-        F[5 * A1 + q] = (((dr - sdr[s2 + BW + 1]) + d0) + bx + by + qxy) * (1.f / 36.f);
-        F[6 * A1 + q] = (((dr - sdr[s2 + BW - 1]) + d0) - bx + by - qxy) * (1.f / 36.f);
-        F[7 * A1 + q] = (((dr - sdr[s2 - BW - 1]) + d0) - bx - by + qxy) * (1.f / 36.f);
-        F[8 * A1 + q] = (((dr - sdr[s2 - BW + 1]) + d0) + bx - by - qxy) * (1.f / 36.f);
+        {
+          const float dn[9] = {0.f,           sdr[s2 + 1],      sdr[s2 + BW],     sdr[s2 - 1],     sdr[s2 - BW],
+                               sdr[s2 + BW + 1], sdr[s2 + BW - 1], sdr[s2 - BW - 1], sdr[s2 - BW + 1]};
+          float Fn[9];
+          push9(dr, dn, uu, vv, dudx, dudy, dvdx, dvdy, c.A, Fn);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) F[k * A1 + q] = Fn[k];
+        }
         if (TH) {
           const float TT = sT[s2];
           const float Bn = sB[s2];
@@ -390,10 +484,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
         for (int k = 0; k < 9; ++k) fk[k] = F[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
         float drn, un, vn, Tn = 0.f;
         if (cls == C_INTERIOR) {
-          drn = drx + (((fk[0] + fk[1]) + (fk[2] + fk[3])) + ((fk[4] + fk[5]) + (fk[6] + fk[7])) + fk[8]);
-          const float inv = sbi[s2];
-          un = (fk[1] - fk[3] + fk[5] - fk[6] - fk[7] + fk[8]) * inv;
-          vn = (fk[2] - fk[4] + fk[5] + fk[6] - fk[7] - fk[8]) * inv;
+          gather9(fk, drx, sbi[s2], drn, un, vn);
           if (TH) {
             float gs = 0.f;
 #pragma unroll
@@ -427,12 +518,12 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
               un = u_in * (float)(4.0 * y * (H - y) / (H * H));
             }
             vn = 0.f;
-            drn = drx + (s0 + 2.f * sp - (un * (float)nxo + vn * (float)nyo));
+            drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));
           } else {
             drn = c.drho_out;
-            const float unorm = (s0 + 2.f * sp) + (drx - c.drho_out);
-            un = unorm * (float)nxo;
-            vn = unorm * (float)nyo;
+            const float unorm = __fadd_rn(__fmaf_rn(2.f, sp, s0), __fsub_rn(drx, c.drho_out));
+            un = __fmul_rn(unorm, (float)nxo);
+            vn = __fmul_rn(unorm, (float)nyo);
           }
           if (TH) {
             const int e = thermal_edge(g, i, j);
@@ -614,20 +705,22 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
         const float uu = su1[s2], vv = sv1[s2];
         float Dx, Dy;
         if (EDGE) {
-          Dx = 2.f * (dfdx<float, BW>(sa3, sx, sy, i, nx) + dfdy<float, BW>(sa4, sx, sy, j, ny));
-          Dy = 2.f * (dfdx<float, BW>(sa4, sx, sy, i, nx) + dfdy<float, BW>(sa5, sx, sy, j, ny));
+          Dx = adj_div2(dfdx<float, BW>(sa3, sx, sy, i, nx), dfdy<float, BW>(sa4, sx, sy, j, ny));
+          Dy = adj_div2(dfdx<float, BW>(sa4, sx, sy, i, nx), dfdy<float, BW>(sa5, sx, sy, j, ny));
         } else {
-          Dx = 2.f * ((sa3[s2 + 1] - sa3[s2 - 1]) * 0.5f + (sa4[s2 + BW] - sa4[s2 - BW]) * 0.5f);
-          Dy = 2.f * ((sa4[s2 + 1] - sa4[s2 - 1]) * 0.5f + (sa5[s2 + BW] - sa5[s2 - BW]) * 0.5f);
+          Dx = adj_div2(cdiff(sa3[s2 + 1], sa3[s2 - 1]), cdiff(sa4[s2 + BW], sa4[s2 - BW]));
+          Dy = adj_div2(cdiff(sa4[s2 + 1], sa4[s2 - 1]), cdiff(sa5[s2 + BW], sa5[s2 - BW]));
         }
-        const float Vx = 3.f * (ux + 3.f * (sxx * uu + sxy * vv) - rt * uu) - c.A * Dx;
-        const float Vy = 3.f * (uy + 3.f * (sxy * uu + syy * vv) - rt * vv) - c.A * Dy;
+        {
+          float Pn[9];
+          adj_pv9(rt, ux, uy, sxx, sxy, syy, uu, vv, Dx, Dy, c.A, Pn);
 #pragma unroll
-        for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = rt + (float)cxk(k) * Vx + (float)cyk(k) * Vy;
+          for (int k = 0; k < 9; ++k) Pq[k * A1 + q] = Pn[k];
+        }
         if (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1)) {
-          cS[q] = 2.f * ((su0[s2 + 1] - su0[s2 - 1]) * 0.5f);
-          cS[A1 + q] = (su0[s2 + BW] - su0[s2 - BW]) * 0.5f + (sv0[s2 + 1] - sv0[s2 - 1]) * 0.5f;
-          cS[2 * A1 + q] = 2.f * ((sv0[s2 + BW] - sv0[s2 - BW]) * 0.5f);
+          cS[q] = __fmul_rn(2.f, cdiff(su0[s2 + 1], su0[s2 - 1]));
+          cS[A1 + q] = __fadd_rn(cdiff(su0[s2 + BW], su0[s2 - BW]), cdiff(sv0[s2 + 1], sv0[s2 - 1]));
+          cS[2 * A1 + q] = __fmul_rn(2.f, cdiff(sv0[s2 + BW], sv0[s2 - BW]));
         } else {
           cS[q] = cS[A1 + q] = cS[2 * A1 + q] = 0.f;
         }
@@ -674,18 +767,17 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
         float m[9];
         if (interior) {
           const float w0 = 4.f / 9.f, w1 = 1.f / 9.f, w5 = 1.f / 36.f;
-          const float ax = ft[1] + ft[3], ay = ft[2] + ft[4], dg = ft[5] + ft[6] + ft[7] + ft[8];
-          m[0] = w0 * ft[0] + w1 * (ax + ay) + w5 * dg;
-          m[1] = w1 * (ft[1] - ft[3]) + w5 * (ft[5] - ft[6] - ft[7] + ft[8]);
-          m[2] = w1 * (ft[2] - ft[4]) + w5 * (ft[5] + ft[6] - ft[7] - ft[8]);
-          m[3] = w1 * ax + w5 * dg;
-          m[4] = w5 * (ft[5] - ft[6] + ft[7] - ft[8]);
-          m[5] = w1 * ay + w5 * dg;
+          adj_moments6(ft, m);
           const float al = sal[s2];
           const float uu0 = su0[s2], vv0 = sv0[s2];
-          const float ju = c.nu * (cS[q1 - 1] - cS[q1 + 1] + cS[A1 + q1 - LX1] - cS[A1 + q1 + LX1]) + 2.f * al * uu0;
-          const float jv = c.nu * (cS[2 * A1 + q1 - LX1] - cS[2 * A1 + q1 + LX1] + cS[A1 + q1 - 1] - cS[A1 + q1 + 1]) +
-                           2.f * al * vv0;
+          const float ju = adj_jsrc(
+              c.nu, __fsub_rn(__fadd_rn(__fsub_rn(cS[q1 - 1], cS[q1 + 1]), cS[A1 + q1 - LX1]), cS[A1 + q1 + LX1]), al,
+              uu0);
+          const float jv = adj_jsrc(
+              c.nu,
+              __fsub_rn(__fadd_rn(__fsub_rn(cS[2 * A1 + q1 - LX1], cS[2 * A1 + q1 + LX1]), cS[A1 + q1 - 1]),
+                        cS[A1 + q1 + 1]),
+              al, vv0);
           float cpx = 0.f, cpy = 0.f;
           if (TH) {
             const float gx = gt[1] + gt[3], gy = gt[2] + gt[4], gd = gt[5] + gt[6] + gt[7] + gt[8];
@@ -697,17 +789,13 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             cpy = T0 * m[8];
           }
           const float inv = sbi[s2];
-          m[1] = (m[1] - ju * (1.f / 3.f) + cpx) * inv;
-          m[2] = (m[2] - jv * (1.f / 3.f) + cpy) * inv;
+          m[1] = adj_brinkman(m[1], ju, cpx, inv);
+          m[2] = adj_brinkman(m[2], jv, cpy, inv);
           if (a.sens) {
             const size_t gi = gbase + (size_t)j * gpitch + i;
             const float gm = __ldg(a.gamma + gi);
             float sacc = 0.f;
-            if (a.sens_flow) {
-              const float dd = c.q_alpha + gm;
-              const float da = __fdividef(-c.alpha_bar * c.q_alpha * (1.f + c.q_alpha), dd * dd);
-              sacc += da * (uu0 * uu0 + vv0 * vv0) + 3.f * da * (uu0 * m[1] + vv0 * m[2]);
-            }
+            if (a.sens_flow) sacc = __fadd_rn(sacc, sens_flow_term(c, gm, uu0, vv0, m[1], m[2]));
             if (TH && a.sens_thermal) {
               const float dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * 0.5f;
               const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
@@ -747,12 +835,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
           }
           const float* M = emap + edge_class(g, i, j) * 60;
 #pragma unroll
-          for (int r = 0; r < 6; ++r) {
-            float acc = 0.f;
-#pragma unroll
-            for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
-            m[r] = acc + M[r * 10 + 9] * kT;
-          }
+          for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, kT);
         }
 #pragma unroll
         for (int f = 0; f < NA; ++f) sout[f * TX_ * TY_ + q] = m[f];

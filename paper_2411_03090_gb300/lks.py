@@ -23,7 +23,7 @@ STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "u
           5: "not converged", 6: "timeout", 7: "calls out of order"}
 REAL = {"f32": 0, "f64": 1}
 SNAP = {"f32": 0, "bf16": 1, "f16": 2}
-PATH = {"auto": 0, "step": 1, "resident": 2}
+PATH = {"auto": 0, "step": 1, "resident": 2, "column": 3}
 LATTICE_D3Q19 = 1
 N_ADJ_FIELDS_3D = 10
 N_ADJ_FIELDS = 9

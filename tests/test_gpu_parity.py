@@ -328,10 +328,11 @@ def test_thermal_checkpoints_equal_plain():
 # ---------------------------------------------------------------------------------------
 # TMA-staged per-step kernels (FP32, nx % 4 == 0)
 # ---------------------------------------------------------------------------------------
-def test_tma_forward_matches_oracle():
+@pytest.mark.parametrize("path", ["step", "column"])
+def test_tma_forward_matches_oracle(path):
     pb = small(nx=136)
     g = pb.gamma()
-    s = LKS(pb, real="f32", path="step")
+    s = LKS(pb, real="f32", path=path)
     J = s.lks_forward(torch.from_numpy(g)).item()
     st, _, _, _ = O.forward(pb, g, pb.n_steps)
     got, _ = gpu_state(s)
@@ -340,10 +341,11 @@ def test_tma_forward_matches_oracle():
     assert abs(J - O.objective(pb, g, st)) <= 1e-5 * abs(J)
 
 
-def test_tma_steady_gradient_matches_oracle():
+@pytest.mark.parametrize("path", ["step", "column"])
+def test_tma_steady_gradient_matches_oracle(path):
     pb = small(nx=136)
     g = pb.gamma()
-    s = LKS(pb, real="f32", path="step")
+    s = LKS(pb, real="f32", path=path)
     J, grad = s.gradient(torch.from_numpy(g))
     ref = O.steady_gradient(pb, g)
     adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
@@ -352,11 +354,11 @@ def test_tma_steady_gradient_matches_oracle():
     assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
 
 
-@pytest.mark.parametrize("K", [0, 64])
-def test_tma_unsteady_gradient_matches_oracle(K):
+@pytest.mark.parametrize("K,path", [(0, "auto"), (64, "auto"), (0, "column"), (64, "column")])
+def test_tma_unsteady_gradient_matches_oracle(K, path):
     pb = small(steady=False, nx=136, n_steps=200)
     g = pb.gamma()
-    s = LKS(pb, real="f32", checkpoint_every=K)
+    s = LKS(pb, real="f32", checkpoint_every=K, path=path)
     J, grad = s.gradient(torch.from_numpy(g))
     ref = O.unsteady_gradient(pb, g)
     assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
@@ -374,3 +376,65 @@ def test_tma_thermal_gradient_matches_oracle(steady):
     ref = O.steady_gradient(pb, g) if steady else O.unsteady_gradient(pb, g)
     assert abs(J.item() - ref["J"]) <= 1e-4 * abs(ref["J"])
     assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+
+
+# ---------------------------------------------------------------------------------------
+# Warp-column kernels (path "column"; chosen automatically on large lattices)
+# ---------------------------------------------------------------------------------------
+def column_case(steady=True, **kw):
+    """200 x 150: interior column tiles (28 x 64 forward, 28 x 32 adjoint) as well as
+    edge tiles and a ragged last column of tiles (200 = 7 x 28 + 4)."""
+    base = dict(seed=9, sigma=3.0, strip=3, n_steps=300, n_adj=300)
+    base.update(kw)
+    if not steady:
+        base.update(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=90.0, n_steps=150)
+    return inputs.channel(200, 150, Re=60.0, **base)
+
+
+def test_column_steady_gradient_matches_oracle():
+    pb = column_case()
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="column")
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.fwd_path == 3 and q.adj_path == 3 and q.device_status == 0
+    ref = O.steady_gradient(pb, g)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(ref["state"])):
+        assert rel_l2(a, b) <= 1e-5
+    assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+
+
+@pytest.mark.parametrize("path", ["step", "column", "auto"])
+def test_unsteady_J_every_path_matches_oracle(path):
+    """J integrated over the march (Eq. fj, Sec. 2.5) on a 200 x 150 lattice, where the 64 x 8 TMA
+    tiles (76) outnumber the 32 x 16 plain tiles (70): every CTA's objective partial
+    must land in the partial sums."""
+    pb = column_case(False)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path=path, checkpoint_every=25)
+    J = s.lks_forward(torch.from_numpy(g)).item()
+    _, _, _, Jo = O.forward(pb, g, pb.n_steps, accumulate_J=True)
+    assert abs(J - Jo) <= 2e-6 * abs(Jo)
+
+
+@pytest.mark.parametrize("steady", [True, False])
+def test_column_equals_tma_step_bitwise(steady):
+    """The warp-column kernels compute every node with the arithmetic of the
+    per-tile TMA kernels: identical states, adjoints and gradients (J differs
+    only in the grouping of its FP64 partial sums)."""
+    pb = column_case(steady)
+    g = torch.from_numpy(pb.gamma())
+    a = LKS(pb, real="f32", path="column", checkpoint_every=0 if steady else 25)
+    b = LKS(pb, real="f32", path="step", checkpoint_every=0 if steady else 25)
+    Ja, ga = a.gradient(g)
+    Jb, gb = b.gradient(g)
+    assert a.query().fwd_path == 3 and b.query().fwd_path == 1
+    # non-thermal: get_state writes drho, u, v (the T output is left untouched)
+    for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
+        assert torch.equal(x, y)
+    for x, y in zip(a.get_adjoint()[:6], b.get_adjoint()[:6]):
+        assert torch.equal(x, y)
+    assert torch.equal(ga, gb)
+    assert abs(Ja.item() - Jb.item()) <= 1e-12 * abs(Jb.item())

@@ -178,7 +178,8 @@ def test_one_step_gradient_is_exact():
         gm[k, j, i] -= eps
         fd = (O.forward3(pb, gp, 1, state=st0, accumulate_J=True)[3] -
               O.forward3(pb, gm, 1, state=st0, accumulate_J=True)[3]) / (2 * eps)
-        assert abs(fd - sens[k, j, i]) <= 1e-7 * max(abs(fd), 1e-12) + 1e-13
+        # truncation O(eps^2) plus the rounding of the two J values, eps_mach |J| / eps
+        assert abs(fd - sens[k, j, i]) <= 1e-7 * abs(fd) + 4 * np.finfo(float).eps * abs(J) / eps
 
 
 @pytest.mark.parametrize("A", [-0.1095, 0.3])
