@@ -110,7 +110,10 @@ typedef struct {
                                  kernels per step                                    */
     int32_t lattice;          /* lks_lattice: 0 D2Q9 (default), 1 D3Q19 (see below)   */
     int32_t nz;               /* D3Q19: nodes along z, >= 5; D2Q9: 0 or 1            */
-    int32_t reserved[5];      /* must be zero                                        */
+    int32_t res_steps;        /* resident marches: time steps per exchange of tile
+                                 bands, 0 automatic or 1..3; the largest value up to
+                                 this that fits the tile shape and shared memory runs */
+    int32_t reserved[4];      /* must be zero                                        */
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in
@@ -137,6 +140,9 @@ typedef struct {
     int32_t phase;            /* 0 created, 1 forward done, 2 adjoint done           */
     int32_t fwd_path;         /* lks_exec_path the last forward march ran on         */
     int32_t adj_path;         /* lks_exec_path the last adjoint march ran on         */
+    int32_t res_steps_fwd;    /* steps per band exchange of the last resident forward
+                                 march (0: none ran)                                  */
+    int32_t res_steps_adj;    /* the same for the last resident adjoint march        */
 } lks_stats;
 
 typedef struct lks_handle lks_handle;

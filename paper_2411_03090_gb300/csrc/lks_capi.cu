@@ -14,12 +14,14 @@
 #include <mutex>
 #include <new>
 #include <string>
+#include <type_traits>
 #include <unordered_map>
 #include <vector>
 
 #include "../../include/lks.h"
 #include "lks_kernels.cuh"
 #include "lks_resident.cuh"
+#include "lks_resident_tb.cuh"
 #include "lks_3d.cuh"
 #include "lks_col.cuh"
 #include "lks_host.cuh"
@@ -63,7 +65,9 @@ Layout make_layout(const lks_problem_desc* d) {
   const int tma_tiles = ((d->nx + kFwdTX - 1) / kFwdTX) * ((d->ny + kFwdTY - 1) / kFwdTY);
   // J partials: one per CTA of the largest forward grid (the persistent TMA grid is
   // at most one CTA per tile)
-  L.fwd_blocks = std::max(std::max(gx * gy, col_tiles), tma_tiles);
+  // (the column forward launches its frame tiles and the two-column block tiles, at
+  // most 2 col_tiles)
+  L.fwd_blocks = std::max(std::max(gx * gy, 2 * col_tiles), tma_tiles);
   L.obj_blocks = obj_grid(L.N);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -126,6 +130,7 @@ struct lks_handle {
   std::unordered_map<uint64_t, CUtensorMap> tmaps;  // (pointer, box) -> tensor map
   int tma_grid_fwd = 0, tma_grid_adj[2][2] = {{0, 0}, {0, 0}};  // adj: [thermal][same state]
   int sms = 0;        // multiprocessors of the device (queried once)
+  int res_steps_fwd = 0, res_steps_adj = 0;  // steps per exchange of the last resident marches
   bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
   lks3::Layout3 L3;
   std::string err;
@@ -287,10 +292,14 @@ int device_sms(lks_handle* h) {
   return h->sms > 0 ? h->sms : 1;
 }
 
-size_t res_smem_bytes(const lks_problem_desc& d, bool adjoint, int cfg) {
+// Shared memory of a resident march with ks steps per exchange: fields with a halo
+// of 2 ks, push values with 2 ks - 1, per-node constants on the first sub-step's
+// output region (halo 2 ks - 2).
+size_t res_smem_bytes(const lks_problem_desc& d, bool adjoint, int cfg, int ks = 1) {
   const size_t rs = d.real_type == LKS_REAL_F64 ? 8 : 4;
-  const int tx = kResCfg[cfg][0], ty = kResCfg[cfg][1];
-  const size_t a2 = (size_t)(tx + 4) * (ty + 4), a1 = (size_t)(tx + 2) * (ty + 2), no = (size_t)tx * ty;
+  const int tx = kResCfg[cfg][0], ty = kResCfg[cfg][1], hh = 2 * ks;
+  const size_t a2 = (size_t)(tx + 2 * hh) * (ty + 2 * hh), a1 = (size_t)(tx + 2 * hh - 2) * (ty + 2 * hh - 2),
+               no = (size_t)(tx + 2 * hh - 4) * (ty + 2 * hh - 4);
   if (adjoint) return rs * (8 * a2 + 9 * a1 + 3 * no);
   return rs * ((d.thermal ? 4 : 3) * a2 + (d.thermal ? 19 : 9) * a1 + no);
 }
@@ -314,6 +323,21 @@ ResPlan plan_resident(lks_handle* h, bool adjoint) {
   return best;
 }
 
+// Steps per exchange of a resident march on tile shape cfg: res_steps (automatic:
+// kResStepsAuto), lowered until the band fits the tile twice and the shared memory
+// fits an SM; FP64 keeps one step per exchange.
+constexpr int kResStepsAuto = 2;
+int res_steps_for(lks_handle* h, bool adjoint, int cfg) {
+  if (h->d.real_type != LKS_REAL_F32) return 1;
+  int optin = 0;
+  cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
+  int ks = h->d.res_steps > 0 ? h->d.res_steps : kResStepsAuto;
+  while (ks > 1 && (4 * ks > std::min(kResCfg[cfg][0], kResCfg[cfg][1]) ||
+                    res_smem_bytes(h->d, adjoint, cfg, ks) + 1024 > (size_t)optin))
+    --ks;
+  return ks;
+}
+
 bool resident_wanted(lks_handle* h, bool adjoint) {
   if (h->d.exec_path == LKS_PATH_STEP || h->d.exec_path == LKS_PATH_COLUMN || !h->d.steady) return false;
   if (adjoint && h->d.thermal) return false;
@@ -322,12 +346,15 @@ bool resident_wanted(lks_handle* h, bool adjoint) {
   return coop && plan_resident(h, adjoint).ntiles > 0;
 }
 
-template <typename R, bool TH, int TXR, int TYR, int NT>
+template <typename R, bool TH, int TXR, int TYR, int NT, int KS>
 lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
   const auto& d = h->d;
   const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
-  const size_t smem = (size_t)fwd_res_smem_elems<TH, TXR, TYR>() * sizeof(R);
-  auto kern = fwd_resident_kernel<R, TH, TXR, TYR, NT>;
+  const size_t smem = (size_t)(KS == 1 ? fwd_res_smem_elems<TH, TXR, TYR>() : fwd_tb_smem_elems<TH, TXR, TYR, KS>()) *
+                      sizeof(R);
+  void (*kern)(ResArgs<R>, Geom, Coef<R>);
+  if constexpr (KS == 1) kern = fwd_resident_kernel<R, TH, TXR, TYR, NT>;
+  else kern = fwd_resident_tb_kernel<R, TH, TXR, TYR, NT, KS>;
   CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CKH(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -348,7 +375,8 @@ lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
   CKH(h, cudaMemsetAsync(a.flags, 0, sizeof(int) * nt, h->stream));
   void* args[] = {&a, &g, &c};
   CKH(h, cudaLaunchCooperativeKernel((const void*)kern, dim3(nt), dim3(NT), args, smem, h->stream));
-  h->cur = (h->cur + n) & 1;
+  h->cur = (h->cur + (KS == 1 ? n : (n + KS - 1) / KS)) & 1;  // buffer of the last exchange
+  h->res_steps_fwd = KS;
   h->t += n;
   h->fwd_steps += n;
   h->launches++;
@@ -356,12 +384,14 @@ lks_status launch_fwd_resident_cfg(lks_handle* h, int n) {
   return LKS_OK;
 }
 
-template <typename R, int TXR, int TYR, int NT>
+template <typename R, int TXR, int TYR, int NT, int KS>
 lks_status launch_adj_resident_cfg(lks_handle* h, int n) {
   const auto& d = h->d;
   const int ntx = (d.nx + TXR - 1) / TXR, nt = ntx * ((d.ny + TYR - 1) / TYR);
-  const size_t smem = (size_t)adj_res_smem_elems<TXR, TYR>() * sizeof(R);
-  auto kern = adj_resident_kernel<R, TXR, TYR, NT>;
+  const size_t smem = (size_t)(KS == 1 ? adj_res_smem_elems<TXR, TYR>() : adj_tb_smem_elems<TXR, TYR, KS>()) * sizeof(R);
+  void (*kern)(ResArgs<R>, Geom, Coef<R>);
+  if constexpr (KS == 1) kern = adj_resident_kernel<R, TXR, TYR, NT>;
+  else kern = adj_resident_tb_kernel<R, TXR, TYR, NT, KS>;
   CKH(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   int per_sm = 0;
   CKH(h, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, NT, smem));
@@ -383,28 +413,49 @@ lks_status launch_adj_resident_cfg(lks_handle* h, int n) {
   CKH(h, cudaMemsetAsync(a.flags, 0, sizeof(int) * nt, h->stream));
   void* args[] = {&a, &g, &c};
   CKH(h, cudaLaunchCooperativeKernel((const void*)kern, dim3(nt), dim3(NT), args, smem, h->stream));
-  h->acur = (h->acur + n) & 1;
+  h->acur = (h->acur + (KS == 1 ? n : (n + KS - 1) / KS)) & 1;  // buffer of the last exchange
+  h->res_steps_adj = KS;
   h->adj_steps += n;
   h->launches++;
   h->adj_path = LKS_PATH_RESIDENT;
   return LKS_OK;
 }
 
+template <typename R, bool TH>
+lks_status launch_fwd_resident_th(lks_handle* h, int n, int k, int ks) {
+  if constexpr (std::is_same_v<R, float>) {
+    if (k == 0 && ks == 3) return launch_fwd_resident_cfg<R, TH, 64, 16, 512, 3>(h, n);
+    if (k == 0 && ks == 2) return launch_fwd_resident_cfg<R, TH, 64, 16, 512, 2>(h, n);
+    if (k == 1 && ks == 3) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 3>(h, n);
+    if (k == 1 && ks == 2) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 2>(h, n);
+    if (k == 2 && ks == 2) return launch_fwd_resident_cfg<R, TH, 32, 8, 256, 2>(h, n);
+  }
+  if (k == 0) return launch_fwd_resident_cfg<R, TH, 64, 16, 512, 1>(h, n);
+  if (k == 1) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 1>(h, n);
+  return launch_fwd_resident_cfg<R, TH, 32, 8, 256, 1>(h, n);
+}
+
 template <typename R>
 lks_status launch_fwd_resident(lks_handle* h, int n) {
   const int k = plan_resident(h, false).cfg;
-  const bool th = h->d.thermal != 0;
-  if (k == 0) return th ? launch_fwd_resident_cfg<R, true, 64, 16, 512>(h, n) : launch_fwd_resident_cfg<R, false, 64, 16, 512>(h, n);
-  if (k == 1) return th ? launch_fwd_resident_cfg<R, true, 32, 16, 256>(h, n) : launch_fwd_resident_cfg<R, false, 32, 16, 256>(h, n);
-  return th ? launch_fwd_resident_cfg<R, true, 32, 8, 256>(h, n) : launch_fwd_resident_cfg<R, false, 32, 8, 256>(h, n);
+  const int ks = res_steps_for(h, false, k);
+  return h->d.thermal ? launch_fwd_resident_th<R, true>(h, n, k, ks) : launch_fwd_resident_th<R, false>(h, n, k, ks);
 }
 
 template <typename R>
 lks_status launch_adj_resident(lks_handle* h, int n) {
   const int k = plan_resident(h, true).cfg;
-  if (k == 0) return launch_adj_resident_cfg<R, 64, 16, 512>(h, n);
-  if (k == 1) return launch_adj_resident_cfg<R, 32, 16, 256>(h, n);
-  return launch_adj_resident_cfg<R, 32, 8, 256>(h, n);
+  const int ks = res_steps_for(h, true, k);
+  if constexpr (std::is_same_v<R, float>) {
+    if (k == 0 && ks == 3) return launch_adj_resident_cfg<R, 64, 16, 512, 3>(h, n);
+    if (k == 0 && ks == 2) return launch_adj_resident_cfg<R, 64, 16, 512, 2>(h, n);
+    if (k == 1 && ks == 3) return launch_adj_resident_cfg<R, 32, 16, 256, 3>(h, n);
+    if (k == 1 && ks == 2) return launch_adj_resident_cfg<R, 32, 16, 256, 2>(h, n);
+    if (k == 2 && ks == 2) return launch_adj_resident_cfg<R, 32, 8, 256, 2>(h, n);
+  }
+  if (k == 0) return launch_adj_resident_cfg<R, 64, 16, 512, 1>(h, n);
+  if (k == 1) return launch_adj_resident_cfg<R, 32, 16, 256, 1>(h, n);
+  return launch_adj_resident_cfg<R, 32, 8, 256, 1>(h, n);
 }
 
 // ------------------------------------------------------------------------------------
@@ -454,16 +505,20 @@ bool use_col(lks_handle* h) {
   return tiles >= 4ll * device_sms(h);
 }
 
-// Warp-column forward (FP32, non-thermal, one lattice): one CTA per 28 x 64 tile.
+// Warp-column forward (FP32, non-thermal, one lattice).  The tiles at least two
+// nodes inside the lattice form a block of 60 x 64 tiles from (28, 64) that
+// fwd_col2_kernel (two columns per lane) computes; fwd_col_kernel (28 x 64 tiles)
+// covers the frame around it, or the whole lattice when no block fits.
 lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv) {
   const auto& d = h->d;
   const int src = h->cur, dst = 1 - h->cur;
-  TmaMaps<4> maps;
   lks_status st;
   const float* fsrc[4] = {state_ptr<float>(h, src, 0), state_ptr<float>(h, src, 1), state_ptr<float>(h, src, 2),
                           fld<float>(h, h->L.mat, 0)};
-  for (int f = 0; f < 4; ++f)
-    if ((st = field_map(h, fsrc[f], COL_BW, COL_BH, &maps.m[f])) != LKS_OK) return st;
+  const Geom geo = make_geom(d);
+  const Coef<float> coef = make_coef<float>(d);
+  using G2 = Col2Geo<C2_R>;
+  const int ntx2 = (d.nx - 2 - COL_W) / C2_W, nty2 = (d.ny - 2 - COL_H) / G2::H;
   ColArgs a;
   for (int f = 0; f < 3; ++f) a.out[f] = state_ptr<float>(h, dst, f);
   a.traj_u = tu;
@@ -472,8 +527,45 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
   a.status = reinterpret_cast<int*>(h->ws + h->L.status);
   a.u_in = (float)inlet_amp(d, t_new);
   a.ntx = (d.nx + COL_W - 1) / COL_W;
-  const int grid = a.ntx * ((d.ny + COL_H - 1) / COL_H);
-  fwd_col_kernel<<<grid, COL_NT, col_smem_bytes(), h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  a.nty = (d.ny + COL_H - 1) / COL_H;
+  a.fr_txb = a.fr_tyb = 0;
+  a.bx0 = a.bx1 = a.by0 = a.by1 = 0;
+  int grid = a.ntx * a.nty;
+  if (ntx2 >= 1 && nty2 >= 1) {
+    TmaMaps<4> maps2;
+    for (int f = 0; f < 4; ++f)
+      if ((st = field_map(h, fsrc[f], C2_BW, G2::BH, &maps2.m[f])) != LKS_OK) return st;
+    Col2Args b;
+    for (int f = 0; f < 3; ++f) b.out[f] = a.out[f];
+    b.traj_u = tu;
+    b.traj_v = tv;
+    b.J_partial = Jpartial;
+    b.status = a.status;
+    b.u_in = a.u_in;
+    b.ntx = ntx2;
+    b.xa = COL_W;
+    b.ya = COL_H;
+    static bool attr2 = false;
+    if (!attr2) {
+      CKH(h, cudaFuncSetAttribute(fwd_col2_kernel<C2_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2::smem));
+      attr2 = true;
+    }
+    fwd_col2_kernel<C2_R><<<ntx2 * nty2, COL_NT, G2::smem, h->stream>>>(maps2, b, geo, coef);
+    CKH(h, cudaGetLastError());
+    h->launches++;
+    a.bx0 = COL_W;
+    a.bx1 = COL_W + ntx2 * C2_W;
+    a.by0 = COL_H;
+    a.by1 = COL_H + nty2 * G2::H;
+    a.fr_txb = a.bx1 / COL_W;
+    a.fr_tyb = a.by1 / COL_H;
+    grid = (1 + a.nty - a.fr_tyb) * a.ntx + (a.fr_tyb - 1) * (1 + a.ntx - a.fr_txb);
+    if (Jpartial) a.J_partial = Jpartial + ntx2 * nty2;
+  }
+  TmaMaps<4> maps;
+  for (int f = 0; f < 4; ++f)
+    if ((st = field_map(h, fsrc[f], COL_BW, COL_BH, &maps.m[f])) != LKS_OK) return st;
+  fwd_col_kernel<<<grid, COL_NT, col_smem_bytes(), h->stream>>>(maps, a, geo, coef);
   CKH(h, cudaGetLastError());
   h->cur = dst;
   h->t = t_new;
@@ -1230,6 +1322,8 @@ lks_status lks_query(lks_handle* h, lks_stats* out) {
   out->phase = h->phase;
   out->fwd_path = h->fwd_path;
   out->adj_path = h->adj_path;
+  out->res_steps_fwd = h->res_steps_fwd;
+  out->res_steps_adj = h->res_steps_adj;
   return status ? (lks_status)status : LKS_OK;
 }
 

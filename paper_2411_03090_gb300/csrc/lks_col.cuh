@@ -34,8 +34,33 @@ struct ColArgs {
   double* J_partial;  // per-tile accumulator of J_O(old state), or null
   int* status;
   float u_in;         // inlet amplitude of the new level
-  int ntx;            // tiles along x
+  int ntx, nty;       // tiles along x and y
+  // Frame mode (fr_txb > 0): the launch covers only the tiles outside an interior
+  // block [bx0, bx1) x [by0, by1) that fwd_col2_kernel computes: tile rows 0 and
+  // >= fr_tyb in full, columns 0 and >= fr_txb of the rows between; nodes inside the
+  // block are neither written nor counted in J.
+  int fr_txb, fr_tyb;
+  int bx0, bx1, by0, by1;
 };
+
+// Tile (tx, ty) of block b of a forward column launch (see ColArgs).
+__device__ __forceinline__ void col_tile(const ColArgs& a, int b, int& tx, int& ty) {
+  if (a.fr_txb <= 0) {
+    tx = b % a.ntx;
+    ty = b / a.ntx;
+    return;
+  }
+  const int nr = 1 + a.nty - a.fr_tyb;  // full rows
+  if (b < nr * a.ntx) {
+    const int r = b / a.ntx;
+    tx = b - r * a.ntx;
+    ty = r == 0 ? 0 : a.fr_tyb + r - 1;
+  } else {
+    const int nc = 1 + a.ntx - a.fr_txb, b2 = b - nr * a.ntx, r = b2 / nc, ci = b2 - r * nc;
+    ty = 1 + r;
+    tx = ci == 0 ? 0 : a.fr_txb + ci - 1;
+  }
+}
 
 __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__ TmaMaps<4> maps,
                                                          const __grid_constant__ ColArgs a,
@@ -48,7 +73,9 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(box, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny;
-  const int x0 = (blockIdx.x % a.ntx) * COL_W, y0 = (blockIdx.x / a.ntx) * COL_H;
+  int tx, ty;
+  col_tile(a, (int)blockIdx.x, tx, ty);
+  const int x0 = tx * COL_W, y0 = ty * COL_H;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -71,9 +98,10 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
   const int bx = lane + 2;      // its column in the box
   const int r0 = y0 + warp * COL_R;
   const bool out_lane = lane >= 2 && lane < 2 + COL_W && i < nx;
-  const bool fast = x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + COL_H + 2 <= ny;
+  const bool fast = a.fr_txb <= 0 && x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + COL_H + 2 <= ny;
   constexpr int BW = COL_BW;
   double jloc = 0.0;
+  auto in_block = [&](int y) { return i >= a.bx0 && i < a.bx1 && y >= a.by0 && y < a.by1; };
   auto brow = [&](int y) { return (y - y0 + 2) * BW; };  // box offset of row y
 
   auto march = [&](auto edge_tag) {
@@ -142,12 +170,8 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
         const float dn[9] = {0.f, d_e, d_n, d_w, d_s, d_ne, d_nw, d_sw, d_se};
         push9(dr, dn, uu, vv, dudx, dudy, dvdx, dvdy, c.A, F);
         // objective of the old state at this warp's output nodes (unsteady accumulation)
-        if (a.J_partial && has_obj && out_lane && p >= r0 && p < r0 + COL_R && p < ny) {
-          const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
-          const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
-          const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
-          const float al = __fdividef(1.f, sbi[s2]) - 1.f;
-          jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+        if (a.J_partial && has_obj && out_lane && p >= r0 && p < r0 + COL_R && p < ny && !in_block(p)) {
+          jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
         }
       }
       // hand the populations that cross a column to the neighbour lane
@@ -170,7 +194,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
       }
       // row p - 1 is complete
       const int q = p - 1;
-      if (q >= r0 && q < r0 + COL_R && q < ny && out_lane) {
+      if (q >= r0 && q < r0 + COL_R && q < ny && out_lane && !in_block(q)) {
         const int sq = brow(q) + bx;
         const float drx = EDGE ? sdr[sq] : dA;
         float drn, un, vn;
@@ -264,11 +288,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
     }
     const int s2 = brow(p) + bx;
     if (a.J_partial && out_lane && p >= r0 && p < r0 + COL_R) {
-      const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
-      const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
-      const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
-      const float al = __fdividef(1.f, sbi[s2]) - 1.f;
-      jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+      jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
     }
     X[4] = F[4];
     X[7] = __shfl_down_sync(0xffffffffu, F[7], 1);
@@ -311,6 +331,168 @@ __global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__
   } else {
     march(std::true_type{});
   }
+  if (a.J_partial) {
+    const double s = block_sum<COL_NT>(jloc, red);
+    if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
+  }
+}
+
+
+// ---------------------------------------------------------------------------------
+// Warp-column forward with two columns per lane (interior block of the lattice)
+// ---------------------------------------------------------------------------------
+// Lane l owns the columns x0 - 2 + 2l and x0 - 1 + 2l and marches down R rows like
+// fwd_col_kernel.  Neighbours inside the lane pair need no shuffle; a row costs two
+// shuffles per field crossing the lane boundary and six for the populations moving
+// to the neighbour lanes, and its loads and stores are 8-byte vectors.  Lanes 1..30
+// write, so a warp covers 60 columns.  Every tile lies at least two nodes inside the
+// lattice: the tile grid starts at (xa, ya) and the host sizes it so; the frame
+// around it runs fwd_col_kernel.  The per-node arithmetic is push9 / gather9, as in
+// the other FP32 staged kernels.
+constexpr int C2_W = 60;
+constexpr int C2_BW = C2_W + 8;
+template <int R>
+struct Col2Geo {
+  static constexpr int H = COL_WARPS * R;  // output rows per tile
+  static constexpr int BH = H + 4, BOX = C2_BW * BH;
+  static constexpr int FS = (BOX * 4 + 127) / 128 * 128 / 4;  // field stride: 128-byte aligned copies
+  static constexpr size_t smem = (size_t)4 * FS * 4 + 128 + 8 + 8 * COL_WARPS;
+  static_assert((R + 2) % 3 == 0, "the unrolled march covers R + 2 rows in threes");
+};
+constexpr int C2_R = 16;
+
+struct Col2Args {
+  float* out[3];      // drho, u, v of the new level
+  float* traj_u;      // optional trajectory copies of u, v
+  float* traj_v;
+  double* J_partial;  // per-tile accumulator of J_O(old state), or null
+  int* status;
+  float u_in;         // unused: no inlet node lies in the block
+  int ntx;            // tiles along x
+  int xa, ya;         // lattice origin of the tile grid
+};
+
+template <int R>
+__global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant__ TmaMaps<4> maps,
+                                                          const __grid_constant__ Col2Args a,
+                                                          const __grid_constant__ Geom g,
+                                                          const __grid_constant__ Coef<float> c) {
+  using G2 = Col2Geo<R>;
+  constexpr int BW = C2_BW, FS = G2::FS;
+  extern __shared__ unsigned char smem_raw[];
+  float* box = reinterpret_cast<float*>(smem_base128(smem_raw));  // [drho, u, v, 1/(1+alpha)][FS]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(box + 4 * FS);
+  double* red = reinterpret_cast<double*>(bar + 1);
+  if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(box, bar, a.status)) return;
+  const int nx = g.nx;
+  const int x0 = a.xa + (int)(blockIdx.x % a.ntx) * C2_W, y0 = a.ya + (int)(blockIdx.x / a.ntx) * G2::H;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    mbar_expect_tx(bar, 4 * G2::BOX * 4);
+    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0) mbar_wait(bar, 0);
+    return;
+  }
+  const float* sdr = box;
+  const float* su = box + FS;
+  const float* sv = box + 2 * FS;
+  const float* sbi = box + 3 * FS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = x0 - 2 + 2 * lane;            // the lane's first lattice column
+  const int bx = TMA_BXPAD - 2 + 2 * lane;     // its column in the box (even: 8-byte aligned)
+  const int r0 = y0 + warp * R;
+  const bool out_lane = lane >= 1 && lane <= 30;
+  auto brow = [&](int y) { return (y - y0 + 2) * BW; };
+  double jloc = 0.0;
+  bool bad = false;
+
+  struct Row {
+    float2 d, u, v;  // drho, u, v of the lane's two columns
+    float dl, dr;    // drho of the columns left and right of the pair
+  };
+  auto load_row = [&](Row& Q, int y) {
+    const int o = brow(y) + bx;
+    Q.d = *reinterpret_cast<const float2*>(sdr + o);
+    Q.u = *reinterpret_cast<const float2*>(su + o);
+    Q.v = *reinterpret_cast<const float2*>(sv + o);
+    Q.dl = __shfl_up_sync(0xffffffffu, Q.d.y, 1);
+    Q.dr = __shfl_down_sync(0xffffffffu, Q.d.x, 1);
+  };
+  // Destination row of the march: the nine populations arriving at each column.
+  struct Dst {
+    float a[9], b[9];
+  };
+  // Row p: A, B, C hold rows p-1, p, p+1; X, Y, Z collect destination rows p-1, p,
+  // p+1.  Row p-1 is complete afterwards and is written; row p+2 is loaded into A.
+  auto step = [&](int p, Row& A, Row& B, Row& C, Dst& X, Dst& Y, Dst& Z) {
+    const float uL = __shfl_up_sync(0xffffffffu, B.u.y, 1), uR = __shfl_down_sync(0xffffffffu, B.u.x, 1);
+    const float vL = __shfl_up_sync(0xffffffffu, B.v.y, 1), vR = __shfl_down_sync(0xffffffffu, B.v.x, 1);
+    float F0[9], F1[9];
+    {
+      const float dn[9] = {0.f, B.d.y, C.d.x, B.dl, A.d.x, C.d.y, C.dl, A.dl, A.d.y};
+      push9(B.d.x, dn, B.u.x, B.v.x, cdiff(B.u.y, uL), cdiff(C.u.x, A.u.x), cdiff(B.v.y, vL), cdiff(C.v.x, A.v.x),
+            c.A, F0);
+    }
+    {
+      const float dn[9] = {0.f, B.dr, C.d.y, B.d.x, A.d.y, C.dr, C.d.x, A.d.x, A.dr};
+      push9(B.d.y, dn, B.u.y, B.v.y, cdiff(uR, B.u.x), cdiff(C.u.y, A.u.y), cdiff(vR, B.v.x), cdiff(C.v.y, A.v.y),
+            c.A, F1);
+    }
+    if (a.J_partial && out_lane && p >= r0 && p < r0 + R) {
+      const int s2 = brow(p) + bx;
+      const float2 inv = *reinterpret_cast<const float2*>(sbi + s2);
+      jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, inv.x, B.u.x, B.v.x);
+      jloc += (double)jo_flow<BW>(su, sv, s2 + 1, c.nu, inv.y, B.u.y, B.v.y);
+    }
+    // populations of the first column moving left go to the previous lane's second
+    // column; those of the second column moving right to the next lane's first
+    const float r7 = __shfl_down_sync(0xffffffffu, F0[7], 1), r3 = __shfl_down_sync(0xffffffffu, F0[3], 1);
+    const float r6 = __shfl_down_sync(0xffffffffu, F0[6], 1);
+    const float l8 = __shfl_up_sync(0xffffffffu, F1[8], 1), l1 = __shfl_up_sync(0xffffffffu, F1[1], 1);
+    const float l5 = __shfl_up_sync(0xffffffffu, F1[5], 1);
+    X.a[4] = F0[4], X.a[7] = F1[7], X.a[8] = l8;  // c_y = -1: destination row p - 1
+    X.b[4] = F1[4], X.b[7] = r7, X.b[8] = F0[8];
+    Y.a[0] = F0[0], Y.a[1] = l1, Y.a[3] = F1[3];  // c_y = 0: destination row p
+    Y.b[0] = F1[0], Y.b[1] = F0[1], Y.b[3] = r3;
+    Z.a[2] = F0[2], Z.a[5] = l5, Z.a[6] = F1[6];  // c_y = +1: destination row p + 1
+    Z.b[2] = F1[2], Z.b[5] = F0[5], Z.b[6] = r6;
+    const int q = p - 1;
+    if (q >= r0 && out_lane) {
+      const float2 inv = *reinterpret_cast<const float2*>(sbi + brow(q) + bx);
+      float2 dn, un, vn;
+      gather9(X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
+      gather9(X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+      const size_t o = (size_t)q * nx + i0;
+      *reinterpret_cast<float2*>(a.out[0] + o) = dn;
+      *reinterpret_cast<float2*>(a.out[1] + o) = un;
+      *reinterpret_cast<float2*>(a.out[2] + o) = vn;
+      if (a.traj_u) {
+        *reinterpret_cast<float2*>(a.traj_u + o) = un;
+        *reinterpret_cast<float2*>(a.traj_v + o) = vn;
+      }
+      bad |= bad_velocity(un.x, vn.x) | bad_velocity(un.y, vn.y);
+    }
+    if (p + 2 <= r0 + R + 1) load_row(A, p + 2);
+  };
+  Row R0, R1, R2;
+  Dst X0, X1, X2;
+  load_row(R0, r0 - 2);
+  load_row(R1, r0 - 1);
+  load_row(R2, r0);
+#pragma unroll 1
+  for (int p = r0 - 1; p <= r0 + R; p += 3) {
+    step(p, R0, R1, R2, X0, X1, X2);
+    step(p + 1, R1, R2, R0, X1, X2, X0);
+    step(p + 2, R2, R0, R1, X2, X0, X1);
+  }
+  if (bad) raise_status(a.status, 4);
   if (a.J_partial) {
     const double s = block_sum<COL_NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;

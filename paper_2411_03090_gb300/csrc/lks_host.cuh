@@ -40,7 +40,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
     if (!d->steady || d->thermal) return bad("D3Q19: steady, non-thermal problems only");
     if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
-    for (int q = 0; q < 5; ++q)
+    if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
+    for (int q = 0; q < 4; ++q)
       if (d->reserved[q] != 0) return bad("reserved fields must be zero");
     return LKS_OK;
   }
@@ -61,7 +62,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->checkpoint_every < 0) return bad("checkpoint_every must be >= 0");
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
   if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
-  for (int q = 0; q < 5; ++q)
+  if (d->res_steps < 0 || d->res_steps > 3) return bad("res_steps must lie in 0..3");
+  for (int q = 0; q < 4; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }

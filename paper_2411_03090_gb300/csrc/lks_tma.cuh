@@ -110,27 +110,51 @@ __device__ __forceinline__ void fence_mbar_init() { asm volatile("fence.mbarrier
 // Central difference (f[+1] - f[-1]) / 2.
 __device__ __forceinline__ float cdiff(float fp, float fm) { return __fmul_rn(__fsub_rn(fp, fm), 0.5f); }
 
+// Local objective of one interior node (Eq. obj): nu/2 S:S + alpha |u|^2, with the
+// strain S_ab = d_b u_a + d_a u_b from central differences; s2 indexes the node in
+// staged u (su) and v (sv) arrays of row length BW, inv is 1 / (1 + alpha).
+template <int BW>
+__device__ __forceinline__ float jo_flow(const float* su, const float* sv, int s2, float nu, float inv, float uu,
+                                         float vv) {
+  const float Sxx = __fmul_rn(2.f, cdiff(su[s2 + 1], su[s2 - 1]));
+  const float Syy = __fmul_rn(2.f, cdiff(sv[s2 + BW], sv[s2 - BW]));
+  const float Sxy = __fadd_rn(cdiff(su[s2 + BW], su[s2 - BW]), cdiff(sv[s2 + 1], sv[s2 - 1]));
+  const float SS = __fmaf_rn(Syy, Syy, __fmaf_rn(__fmul_rn(2.f, Sxy), Sxy, __fmul_rn(Sxx, Sxx)));
+  const float al = __fsub_rn(__fdiv_rn(1.f, inv), 1.f);
+  return __fmaf_rn(al, __fmaf_rn(vv, vv, __fmul_rn(uu, uu)), __fmul_rn(__fmul_rn(0.5f, nu), SS));
+}
+
 // The nine pushed populations of one node (Eq. feq2, increment form): F_k is sent
-// to x + c_k and carries w_k [(drho(x) - drho(x + c_k)) + e0 + c_k.b + c_k c_k : Q].
-// d[k] = drho(x + c_k) for k = 1..8 (d[0] unused).
+// to x + c_k and carries w_k [(drho(x) - drho(x + c_k)) + e0 + c_k.b + c_k c_k : Q]
+// with e0 = -3/2 |u|^2, b = 3u, Q_ab = 9/2 u_a u_b + A (d_b u_a + d_a u_b).
+// d[k] = drho(x + c_k) for k = 1..8 (d[0] unused).  Evaluated as
+// F_k = G_k - w_k d[k] with G_k = w_k (drho(x) + e0 + c_k c_k : Q) + w_k c_k.b, the
+// partial sums shared between the links.
 __device__ __forceinline__ void push9(float dr, const float* d, float uu, float vv, float dudx, float dudy,
                                       float dvdx, float dvdy, float A, float* F) {
-  const float e0 = __fmul_rn(-1.5f, __fmaf_rn(vv, vv, __fmul_rn(uu, uu)));
-  const float bx = __fmul_rn(3.f, uu), by = __fmul_rn(3.f, vv);
+  constexpr float w1 = 1.f / 9.f, w5 = 1.f / 36.f;
+  const float uu2 = __fmul_rn(uu, uu), vv2 = __fmul_rn(vv, vv);
+  const float e0 = __fmul_rn(-1.5f, __fadd_rn(uu2, vv2));
   const float A2 = __fmul_rn(2.f, A);
-  const float qxx = __fmaf_rn(A2, dudx, __fmul_rn(__fmul_rn(4.5f, uu), uu));
-  const float qyy = __fmaf_rn(A2, dvdy, __fmul_rn(__fmul_rn(4.5f, vv), vv));
-  const float qxy = __fmaf_rn(A2, __fadd_rn(dudy, dvdx), __fmul_rn(__fmul_rn(9.f, uu), vv));
-  const float d0 = __fadd_rn(__fadd_rn(e0, qxx), qyy);
+  const float qxx = __fmaf_rn(4.5f, uu2, __fmul_rn(A2, dudx));
+  const float qyy = __fmaf_rn(4.5f, vv2, __fmul_rn(A2, dvdy));
+  const float qxy = __fmaf_rn(__fmul_rn(9.f, uu), vv, __fmul_rn(A2, __fadd_rn(dudy, dvdx)));
+  const float p0 = __fadd_rn(dr, e0);
+  const float px = __fadd_rn(p0, qxx), py = __fadd_rn(p0, qyy);
+  const float pd = __fadd_rn(px, qyy);  // drho + e0 + Q_xx + Q_yy
+  const float q1 = __fadd_rn(pd, qxy), q2 = __fsub_rn(pd, qxy);
+  const float wbx = __fmul_rn(1.f / 3.f, uu), wby = __fmul_rn(1.f / 3.f, vv);  // w1 b_x, w1 b_y
+  const float wsp = __fmul_rn(1.f / 12.f, __fadd_rn(uu, vv));                   // w5 (b_x + b_y)
+  const float wsm = __fmul_rn(1.f / 12.f, __fsub_rn(uu, vv));                   // w5 (b_x - b_y)
   F[0] = __fmul_rn(e0, 4.f / 9.f);
-  F[1] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[1]), e0), bx), qxx), 1.f / 9.f);
-  F[3] = __fmul_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[3]), e0), bx), qxx), 1.f / 9.f);
-  F[2] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[2]), e0), by), qyy), 1.f / 9.f);
-  F[4] = __fmul_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[4]), e0), by), qyy), 1.f / 9.f);
-  F[5] = __fmul_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[5]), d0), bx), by), qxy), 1.f / 36.f);
-  F[6] = __fmul_rn(__fsub_rn(__fadd_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[6]), d0), bx), by), qxy), 1.f / 36.f);
-  F[7] = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fsub_rn(dr, d[7]), d0), bx), by), qxy), 1.f / 36.f);
-  F[8] = __fmul_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(dr, d[8]), d0), bx), by), qxy), 1.f / 36.f);
+  F[1] = __fmaf_rn(-w1, d[1], __fmaf_rn(w1, px, wbx));
+  F[3] = __fmaf_rn(-w1, d[3], __fmaf_rn(w1, px, -wbx));
+  F[2] = __fmaf_rn(-w1, d[2], __fmaf_rn(w1, py, wby));
+  F[4] = __fmaf_rn(-w1, d[4], __fmaf_rn(w1, py, -wby));
+  F[5] = __fmaf_rn(-w5, d[5], __fmaf_rn(w5, q1, wsp));
+  F[7] = __fmaf_rn(-w5, d[7], __fmaf_rn(w5, q1, -wsp));
+  F[6] = __fmaf_rn(-w5, d[6], __fmaf_rn(w5, q2, -wsm));
+  F[8] = __fmaf_rn(-w5, d[8], __fmaf_rn(w5, q2, wsm));
 }
 
 // Interior gather of one node: drho, and u, v before / after the implicit Brinkman
@@ -139,8 +163,9 @@ __device__ __forceinline__ void gather9(const float* fk, float drx, float inv, f
   drn = __fadd_rn(drx, __fadd_rn(__fadd_rn(__fadd_rn(__fadd_rn(fk[0], fk[1]), __fadd_rn(fk[2], fk[3])),
                                            __fadd_rn(__fadd_rn(fk[4], fk[5]), __fadd_rn(fk[6], fk[7]))),
                                  fk[8]));
-  un = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fsub_rn(fk[1], fk[3]), fk[5]), fk[6]), fk[7]), fk[8]), inv);
-  vn = __fmul_rn(__fsub_rn(__fsub_rn(__fadd_rn(__fadd_rn(__fsub_rn(fk[2], fk[4]), fk[5]), fk[6]), fk[7]), fk[8]), inv);
+  const float a57 = __fsub_rn(fk[5], fk[7]), b86 = __fsub_rn(fk[8], fk[6]);
+  un = __fmul_rn(__fadd_rn(__fadd_rn(__fsub_rn(fk[1], fk[3]), a57), b86), inv);
+  vn = __fmul_rn(__fsub_rn(__fadd_rn(__fsub_rn(fk[2], fk[4]), a57), b86), inv);
 }
 
 // Adjoint equilibrium coefficients of one node (Eq. afeq): Pq[k] = P + c_k . V with
@@ -454,11 +479,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
         // objective of the old state at interior tile nodes (unsteady accumulation)
         if (a.J_partial && lx >= 1 && lx <= TX_ && ly >= 1 && ly <= TY_ &&
             (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1))) {
-          const float cSxx = 2.f * ((su[s2 + 1] - su[s2 - 1]) * 0.5f);
-          const float cSyy = 2.f * ((sv[s2 + BW] - sv[s2 - BW]) * 0.5f);
-          const float cSxy = (su[s2 + BW] - su[s2 - BW]) * 0.5f + (sv[s2 + 1] - sv[s2 - 1]) * 0.5f;
-          const float al = __fdividef(1.f, sbi[s2]) - 1.f;
-          jloc += (double)(0.5f * c.nu * (cSxx * cSxx + 2.f * cSxy * cSxy + cSyy * cSyy) + al * (uu * uu + vv * vv));
+          jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
           if (TH) jloc += (double)(c.kappa_T * sT[s2]);
         }
       }

@@ -52,7 +52,8 @@ class Desc(C.Structure):
         ("kappa_T", C.c_double),
         ("n_steps", C.c_int32), ("n_adj", C.c_int32),
         ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
-        ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("reserved", C.c_int32 * 5),
+        ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("res_steps", C.c_int32),
+        ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -60,7 +61,8 @@ class Stats(C.Structure):
     _fields_ = [("forward_steps", C.c_int64), ("adjoint_steps", C.c_int64),
                 ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_size_t),
                 ("device_status", C.c_int32), ("phase", C.c_int32),
-                ("fwd_path", C.c_int32), ("adj_path", C.c_int32)]
+                ("fwd_path", C.c_int32), ("adj_path", C.c_int32),
+                ("res_steps_fwd", C.c_int32), ("res_steps_adj", C.c_int32)]
 
 
 LKS_BATCH_VERSION = 1
@@ -144,7 +146,7 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
-              path: str = "auto") -> Desc:
+              path: str = "auto", res_steps: int = 0) -> Desc:
     """Descriptor from an ``inputs.Problem``-like object (``inputs.Problem3``: a
     D3Q19 duct)."""
     d = Desc()
@@ -175,6 +177,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.checkpoint_every = int(checkpoint_every)
     d.snapshot_type = SNAP[snapshot]
     d.exec_path = PATH[path]
+    d.res_steps = int(res_steps)
     return d
 
 
@@ -208,12 +211,12 @@ class LKS:
 
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
                  device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
-                 path: str = "auto"):
+                 path: str = "auto", res_steps: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.pb = pb
-        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path)
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.is3 = hasattr(pb, "nz")

@@ -76,7 +76,8 @@ def test_descriptor_validation():
     pb = inputs.config1()
     d = lks.make_desc(pb)
     assert lks.workspace_size(d) > 0
-    for field, val in (("nx", 3), ("real_type", 7), ("nu", 0.9), ("version", 99), ("n_steps", 0)):
+    for field, val in (("nx", 3), ("real_type", 7), ("nu", 0.9), ("version", 99), ("n_steps", 0),
+                       ("res_steps", 4), ("res_steps", -1)):
         bad = lks.make_desc(pb)
         setattr(bad, field, val)
         with pytest.raises(lks.LKSError) as e:
@@ -86,6 +87,8 @@ def test_descriptor_validation():
     bad.reserved[3] = 1
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
+    for ks in (1, 2, 3):
+        assert lks.workspace_size(lks.make_desc(pb, res_steps=ks)) == lks.workspace_size(d)
 
 
 def test_workspace_grows_with_checkpoint_storage():

@@ -174,6 +174,44 @@ def test_resident_equals_step_path_config2():
     assert rel_l2(ga.cpu().numpy(), gb.cpu().numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("ks", [1, 2, 3])
+def test_resident_steps_per_exchange_match_oracle(ks):
+    """Resident marches advancing ks steps per exchange of tile bands (temporal
+    blocking) on 320 x 130: 32 x 16 tiles with a ragged last tile row two nodes high
+    (narrower than the halo of 2 ks), and an odd step count, so that the last
+    exchange carries fewer than ks steps."""
+    pb = inputs.channel(320, 130, Re=40.0, seed=4, sigma=3.0, strip=3, n_steps=301, n_adj=301)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="resident", res_steps=ks)
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.fwd_path == 2 and q.adj_path == 2 and q.device_status == 0
+    assert q.res_steps_fwd == ks and q.res_steps_adj == ks
+    ref = O.steady_gradient(pb, g)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(ref["state"])):
+        assert rel_l2(a, b) <= 1e-5
+    assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    for k in range(6):
+        assert rel_l2(adj[k], ref["adjoint"][k]) <= 1e-3, k
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+
+
+@pytest.mark.parametrize("ks", [2, 3])
+def test_resident_steps_per_exchange_config2(ks):
+    """512 x 256 (the benchmark lattice, 64 x 16 tiles): ks steps per exchange give
+    the gradient of one step per exchange (the per-node arithmetic is the same)."""
+    pb = inputs.config2().with_(n_steps=2001, n_adj=2001)
+    g = torch.from_numpy(pb.gamma())
+    a = LKS(pb, real="f32", path="resident", res_steps=ks)
+    Ja, ga = a.gradient(g)
+    Jb, gb = LKS(pb, real="f32", path="resident", res_steps=1).gradient(g)
+    assert a.query().res_steps_fwd == ks and a.query().res_steps_adj == ks
+    assert abs(Ja.item() - Jb.item()) <= 1e-6 * abs(Jb.item())
+    assert rel_l2(ga.cpu().numpy(), gb.cpu().numpy()) <= 1e-5
+
+
 def test_sensitivity_zero_on_edges_and_finite():
     pb = small()
     s = LKS(pb, real="f32")
