@@ -486,7 +486,7 @@ def main():
     step_names = (("adj_tma_kernel<false,true,false>", "fwd_tma_kernel<false,false>") if pb.nx % 4 == 0 else
                   ("adj_step_kernel<float,false>", "fwd_step_kernel<float,false>"))
     kname = {1: step_names, 2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>"),
-             3: ("adj_col_kernel<true>", "fwd_col2_kernel<16> (interior block) + fwd_col_kernel (frame)")}
+             3: ("adj_col_kernel<true>", "fwd_col2_kernel<10>")}
     adj_k = kname.get(st.adj_path, kname[1])[0]
     fwd_k = kname.get(st.fwd_path, kname[1])[1]
     if three_d:

@@ -61,13 +61,11 @@ Layout make_layout(const lks_problem_desc* d) {
   L.nA = d->thermal ? 9 : 6;
   L.nT = d->thermal ? 3 : 2;
   const int gx = (d->nx + TX - 1) / TX, gy = (d->ny + TY - 1) / TY;
-  const int col_tiles = ((d->nx + COL_W - 1) / COL_W) * ((d->ny + COL_H - 1) / COL_H);
+  const int col_tiles = ((d->nx + C2_W - 1) / C2_W) * ((d->ny + Col2Geo<C2_R>::H - 1) / Col2Geo<C2_R>::H);
   const int tma_tiles = ((d->nx + kFwdTX - 1) / kFwdTX) * ((d->ny + kFwdTY - 1) / kFwdTY);
   // J partials: one per CTA of the largest forward grid (the persistent TMA grid is
   // at most one CTA per tile)
-  // (the column forward launches its frame tiles and the two-column block tiles, at
-  // most 2 col_tiles)
-  L.fwd_blocks = std::max(std::max(gx * gy, 2 * col_tiles), tma_tiles);
+  L.fwd_blocks = std::max(std::max(gx * gy, col_tiles), tma_tiles);
   L.obj_blocks = obj_grid(L.N);
   size_t off = 0;
   auto take = [&](size_t bytes) {
@@ -504,71 +502,37 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
 // SM (below that the per-tile TMA kernels, with fewer edge tiles, are faster).
 bool use_col(lks_handle* h) {
   if (h->d.exec_path == LKS_PATH_COLUMN) return true;
-  const long long tiles = (long long)((h->d.nx + COL_W - 1) / COL_W) * ((h->d.ny + COL_H - 1) / COL_H);
+  const long long tiles = (long long)((h->d.nx + C2_W - 1) / C2_W) * ((h->d.ny + Col2Geo<C2_R>::H - 1) / Col2Geo<C2_R>::H);
   return tiles >= 4ll * device_sms(h);
 }
 
-// Warp-column forward (FP32, non-thermal, one lattice).  The tiles at least two
-// nodes inside the lattice form a block of 60 x 64 tiles from (28, 64) that
-// fwd_col2_kernel (two columns per lane) computes; fwd_col_kernel (28 x 64 tiles)
-// covers the frame around it, or the whole lattice when no block fits.
+// Warp-column forward (FP32, non-thermal, one lattice): fwd_col2_kernel, one CTA per
+// 60 x 40 tile (two columns per lane).
 lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv) {
   const auto& d = h->d;
   const int src = h->cur, dst = 1 - h->cur;
-  lks_status st;
+  using G2 = Col2Geo<C2_R>;
   const float* fsrc[4] = {state_ptr<float>(h, src, 0), state_ptr<float>(h, src, 1), state_ptr<float>(h, src, 2),
                           fld<float>(h, h->L.mat, 0)};
-  const Geom geo = make_geom(d);
-  const Coef<float> coef = make_coef<float>(d);
-  using G2 = Col2Geo<C2_R>;
-  const int ntx2 = (d.nx - 2 - COL_W) / C2_W, nty2 = (d.ny - 2 - COL_H) / G2::H;
-  ColArgs a;
+  TmaMaps<4> maps;
+  lks_status st;
+  for (int f = 0; f < 4; ++f)
+    if ((st = field_map(h, fsrc[f], C2_BW, G2::BH, &maps.m[f])) != LKS_OK) return st;
+  Col2Args a;
   for (int f = 0; f < 3; ++f) a.out[f] = state_ptr<float>(h, dst, f);
   a.traj_u = tu;
   a.traj_v = tv;
   a.J_partial = Jpartial;
   a.status = reinterpret_cast<int*>(h->ws + h->L.status);
   a.u_in = (float)inlet_amp(d, t_new);
-  a.ntx = (d.nx + COL_W - 1) / COL_W;
-  a.nty = (d.ny + COL_H - 1) / COL_H;
-  a.fr_txb = a.fr_tyb = 0;
-  a.bx0 = a.bx1 = a.by0 = a.by1 = 0;
-  int grid = a.ntx * a.nty;
-  if (ntx2 >= 1 && nty2 >= 1) {
-    TmaMaps<4> maps2;
-    for (int f = 0; f < 4; ++f)
-      if ((st = field_map(h, fsrc[f], C2_BW, G2::BH, &maps2.m[f])) != LKS_OK) return st;
-    Col2Args b;
-    for (int f = 0; f < 3; ++f) b.out[f] = a.out[f];
-    b.traj_u = tu;
-    b.traj_v = tv;
-    b.J_partial = Jpartial;
-    b.status = a.status;
-    b.u_in = a.u_in;
-    b.ntx = ntx2;
-    b.xa = COL_W;
-    b.ya = COL_H;
-    static bool attr2 = false;
-    if (!attr2) {
-      CKH(h, cudaFuncSetAttribute(fwd_col2_kernel<C2_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2::smem));
-      attr2 = true;
-    }
-    fwd_col2_kernel<C2_R><<<ntx2 * nty2, COL_NT, G2::smem, h->stream>>>(maps2, b, geo, coef);
-    CKH(h, cudaGetLastError());
-    h->launches++;
-    a.bx0 = COL_W;
-    a.bx1 = COL_W + ntx2 * C2_W;
-    a.by0 = COL_H;
-    a.by1 = COL_H + nty2 * G2::H;
-    a.fr_txb = a.bx1 / COL_W;
-    a.fr_tyb = a.by1 / COL_H;
-    grid = (1 + a.nty - a.fr_tyb) * a.ntx + (a.fr_tyb - 1) * (1 + a.ntx - a.fr_txb);
-    if (Jpartial) a.J_partial = Jpartial + ntx2 * nty2;
+  a.ntx = (d.nx + C2_W - 1) / C2_W;
+  const int grid = a.ntx * ((d.ny + G2::H - 1) / G2::H);
+  static bool attr = false;
+  if (!attr) {
+    CKH(h, cudaFuncSetAttribute(fwd_col2_kernel<C2_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2::smem));
+    attr = true;
   }
-  TmaMaps<4> maps;
-  for (int f = 0; f < 4; ++f)
-    if ((st = field_map(h, fsrc[f], COL_BW, COL_BH, &maps.m[f])) != LKS_OK) return st;
-  fwd_col_kernel<<<grid, COL_NT, col_smem_bytes(), h->stream>>>(maps, a, geo, coef);
+  fwd_col2_kernel<C2_R><<<grid, COL_NT, G2::smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->cur = dst;
   h->t = t_new;

@@ -1,354 +1,39 @@
-// lks_col.cuh -- warp-column form of the FP32 forward step of one lattice (non-thermal).
+// lks_col.cuh -- warp-column forms of the FP32 LKS and ALKS steps of one lattice
+// (non-thermal).
 //
-// Each warp owns 32 adjacent lattice columns and marches down 16 output rows with
-// the state of three rows held in registers.  A lane computes the nine pushed
-// populations of its node (the per-node arithmetic of fwd_tma_kernel, term for
-// term), hands the ones that cross a column to its neighbour lane by warp shuffle,
-// and accumulates what its column receives per destination row; a row is complete
-// once the row below it has been pushed.  The two outer lanes on each side only
-// feed their neighbours, so a warp writes 28 columns.  Four warps stacked in y make
-// a 28 x 64 tile, staged by one tensor copy of each field (box 36 x 68 from
-// (x0 - 4, y0 - 2): the halo, with x on a 16-byte boundary).  There is no shared
-// push array and no barrier inside a tile.  Tiles whose halo reaches the domain
-// edge run the same march with the edge rules (one-sided derivatives, continuity,
-// Zou-He edges, corners), reading neighbours from the staged box.
+// A warp owns adjacent lattice columns and marches down its rows with the values of
+// three rows held in registers.  A lane computes the per-node coefficients of its
+// column(s) (the arithmetic of the TMA-staged kernels, term for term), hands the
+// values that cross a column to the neighbour lane by warp shuffle, and completes a
+// row once the row below it has been processed.  Each tile is staged by one tensor
+// copy per field (its halo included, x on a 16-byte boundary); there is no shared
+// push array and no barrier inside a tile.  Tiles whose halo reaches the domain edge
+// run the same march with the edge rules (one-sided derivatives, continuity, Zou-He
+// edges, corners).
 #pragma once
 #include "lks_tma.cuh"
 
 namespace lks {
 
-constexpr int COL_W = 28;                       // output columns per warp (32 lanes, 2 halo lanes per side)
-constexpr int COL_WARPS = 4;                    // warps per CTA, stacked in y
-constexpr int COL_R = 16;                       // output rows per warp
-constexpr int COL_H = COL_WARPS * COL_R;        // output rows per tile
-constexpr int COL_BW = COL_W + 8, COL_BH = COL_H + 4, COL_BOX = COL_BW * COL_BH;
+constexpr int COL_W = 28;     // adjoint: output columns per warp (32 lanes, 2 halo lanes per side)
+constexpr int COL_WARPS = 4;  // warps per CTA, stacked in y
+constexpr int COL_BW = COL_W + 8;
 constexpr int COL_NT = 32 * COL_WARPS;
-constexpr int COL_FS = (COL_BOX * 4 + 127) / 128 * 128 / 4;  // field stride: copies land on 128-byte boundaries
-
-__host__ __device__ constexpr size_t col_smem_bytes() { return (size_t)4 * COL_FS * 4 + 128 + 8 + 8 * COL_WARPS; }
-
-struct ColArgs {
-  float* out[3];      // drho, u, v of the new level
-  float* traj_u;      // optional trajectory copies of u, v
-  float* traj_v;
-  double* J_partial;  // per-tile accumulator of J_O(old state), or null
-  int* status;
-  float u_in;         // inlet amplitude of the new level
-  int ntx, nty;       // tiles along x and y
-  // Frame mode (fr_txb > 0): the launch covers only the tiles outside an interior
-  // block [bx0, bx1) x [by0, by1) that fwd_col2_kernel computes: tile rows 0 and
-  // >= fr_tyb in full, columns 0 and >= fr_txb of the rows between; nodes inside the
-  // block are neither written nor counted in J.
-  int fr_txb, fr_tyb;
-  int bx0, bx1, by0, by1;
-};
-
-// Tile (tx, ty) of block b of a forward column launch (see ColArgs).
-__device__ __forceinline__ void col_tile(const ColArgs& a, int b, int& tx, int& ty) {
-  if (a.fr_txb <= 0) {
-    tx = b % a.ntx;
-    ty = b / a.ntx;
-    return;
-  }
-  const int nr = 1 + a.nty - a.fr_tyb;  // full rows
-  if (b < nr * a.ntx) {
-    const int r = b / a.ntx;
-    tx = b - r * a.ntx;
-    ty = r == 0 ? 0 : a.fr_tyb + r - 1;
-  } else {
-    const int nc = 1 + a.ntx - a.fr_txb, b2 = b - nr * a.ntx, r = b2 / nc, ci = b2 - r * nc;
-    ty = 1 + r;
-    tx = ci == 0 ? 0 : a.fr_txb + ci - 1;
-  }
-}
-
-__global__ void __launch_bounds__(COL_NT) fwd_col_kernel(const __grid_constant__ TmaMaps<4> maps,
-                                                         const __grid_constant__ ColArgs a,
-                                                         const __grid_constant__ Geom g,
-                                                         const __grid_constant__ Coef<float> c) {
-  extern __shared__ unsigned char smem_raw[];
-  float* box = reinterpret_cast<float*>(smem_base128(smem_raw));  // [drho, u, v, 1/(1+alpha)][COL_FS]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(box + 4 * COL_FS);
-  double* red = reinterpret_cast<double*>(bar + 1);
-  if (timed_out_before(a.status)) return;
-  if (!tma_layout_ok(box, bar, a.status)) return;
-  const int nx = g.nx, ny = g.ny;
-  int tx, ty;
-  col_tile(a, (int)blockIdx.x, tx, ty);
-  const int x0 = tx * COL_W, y0 = ty * COL_H;
-  if (threadIdx.x == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-    fence_proxy_async();
-    mbar_expect_tx(bar, 4 * COL_BOX * 4);
-    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * COL_FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
-  }
-  __syncthreads();
-  if (!mbar_wait(bar, 0)) {
-    raise_status(a.status, 6);
-    if (threadIdx.x == 0) mbar_wait(bar, 0);
-    return;
-  }
-  const float* sdr = box;
-  const float* su = box + COL_FS;
-  const float* sv = box + 2 * COL_FS;
-  const float* sbi = box + 3 * COL_FS;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = x0 - 2 + lane;  // this lane's lattice column
-  const int bx = lane + 2;      // its column in the box
-  const int r0 = y0 + warp * COL_R;
-  const bool out_lane = lane >= 2 && lane < 2 + COL_W && i < nx;
-  const bool fast = a.fr_txb <= 0 && x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + COL_H + 2 <= ny;
-  constexpr int BW = COL_BW;
-  double jloc = 0.0;
-  auto in_block = [&](int y) { return i >= a.bx0 && i < a.bx1 && y >= a.by0 && y < a.by1; };
-  auto brow = [&](int y) { return (y - y0 + 2) * BW; };  // box offset of row y
-
-  auto march = [&](auto edge_tag) {
-    constexpr bool EDGE = decltype(edge_tag)::value;
-    float X[9], Y[9], Z[9];  // received populations of destination rows p-1, p, p+1
-#pragma unroll
-    for (int k = 0; k < 9; ++k) X[k] = Y[k] = Z[k] = 0.f;
-    // register ring (fast path): drho, u, v of rows p-1 (A), p (B), p+1 (C)
-    float dA = 0.f, uA = 0.f, vA = 0.f, dB = 0.f, uB = 0.f, vB = 0.f, dC = 0.f, uC = 0.f, vC = 0.f;
-    if (!EDGE) {
-      const int o = brow(r0 - 2) + bx;
-      dA = sdr[o], uA = su[o], vA = sv[o];
-      dB = sdr[o + BW], uB = su[o + BW], vB = sv[o + BW];
-      dC = sdr[o + 2 * BW], uC = su[o + 2 * BW], vC = sv[o + 2 * BW];
-    }
-    for (int p = r0 - 1; p <= r0 + COL_R; ++p) {
-      float F[9];
-      const int s2 = brow(p) + bx;
-      bool has_obj = false, live = true;
-      float uu = 0.f, vv = 0.f, dudx = 0.f, dudy = 0.f, dvdx = 0.f, dvdy = 0.f, dr = 0.f;
-      float d_e = 0.f, d_w = 0.f, d_n = 0.f, d_s = 0.f, d_ne = 0.f, d_nw = 0.f, d_sw = 0.f, d_se = 0.f;
-      if (!EDGE) {
-        const float uL = __shfl_up_sync(0xffffffffu, uB, 1), uR = __shfl_down_sync(0xffffffffu, uB, 1);
-        const float vL = __shfl_up_sync(0xffffffffu, vB, 1), vR = __shfl_down_sync(0xffffffffu, vB, 1);
-        const float aL = __shfl_up_sync(0xffffffffu, dA, 1), aR = __shfl_down_sync(0xffffffffu, dA, 1);
-        const float bL = __shfl_up_sync(0xffffffffu, dB, 1), bR = __shfl_down_sync(0xffffffffu, dB, 1);
-        const float cL = __shfl_up_sync(0xffffffffu, dC, 1), cR = __shfl_down_sync(0xffffffffu, dC, 1);
-        uu = uB;
-        vv = vB;
-        dudx = cdiff(uR, uL);
-        dudy = cdiff(uC, uA);
-        dvdx = cdiff(vR, vL);
-        dvdy = cdiff(vC, vA);
-        dr = dB;
-        d_e = bR, d_w = bL, d_n = dC, d_s = dA, d_ne = cR, d_nw = cL, d_sw = aL, d_se = aR;
-        has_obj = true;
-      } else {
-        live = i >= 0 && i < nx && p >= 0 && p < ny;
-        if (!live) {
-#pragma unroll
-          for (int k = 0; k < 9; ++k) F[k] = 0.f;
-        } else {
-          const int by = p - y0 + 2;
-          uu = su[s2];
-          vv = sv[s2];
-          dudx = dfdx<float, BW>(su, bx, by, i, nx);
-          dudy = dfdy<float, BW>(su, bx, by, p, ny);
-          dvdx = dfdx<float, BW>(sv, bx, by, i, nx);
-          dvdy = dfdy<float, BW>(sv, bx, by, p, ny);
-          const bool xe = (i == 0 || i == nx - 1), ye = (p == 0 || p == ny - 1);
-          if (xe && ye) {
-            dudx = 0.f;
-            dvdy = 0.f;
-          } else if (xe) {
-            dudx = -dvdy;
-          } else if (ye) {
-            dvdy = -dudx;
-          }
-          dr = sdr[s2];
-          d_e = sdr[s2 + 1], d_w = sdr[s2 - 1], d_n = sdr[s2 + BW], d_s = sdr[s2 - BW];
-          d_ne = sdr[s2 + BW + 1], d_nw = sdr[s2 + BW - 1], d_sw = sdr[s2 - BW - 1], d_se = sdr[s2 - BW + 1];
-          has_obj = i > 0 && p > 0 && i < nx - 1 && p < ny - 1;
-        }
-      }
-      if (live) {
-        const float dn[9] = {0.f, d_e, d_n, d_w, d_s, d_ne, d_nw, d_sw, d_se};
-        push9(dr, dn, uu, vv, dudx, dudy, dvdx, dvdy, c.A, F);
-        // objective of the old state at this warp's output nodes (unsteady accumulation)
-        if (a.J_partial && has_obj && out_lane && p >= r0 && p < r0 + COL_R && p < ny && !in_block(p)) {
-          jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
-        }
-      }
-      // hand the populations that cross a column to the neighbour lane
-      {
-        const float g1 = __shfl_up_sync(0xffffffffu, F[1], 1);
-        const float g5 = __shfl_up_sync(0xffffffffu, F[5], 1);
-        const float g8 = __shfl_up_sync(0xffffffffu, F[8], 1);
-        const float g3 = __shfl_down_sync(0xffffffffu, F[3], 1);
-        const float g6 = __shfl_down_sync(0xffffffffu, F[6], 1);
-        const float g7 = __shfl_down_sync(0xffffffffu, F[7], 1);
-        X[4] = F[4];  // c = (0, -1): destination row p - 1
-        X[7] = g7;
-        X[8] = g8;
-        Y[0] = F[0];  // c_y = 0: destination row p
-        Y[1] = g1;
-        Y[3] = g3;
-        Z[2] = F[2];  // c_y = +1: destination row p + 1
-        Z[5] = g5;
-        Z[6] = g6;
-      }
-      // row p - 1 is complete
-      const int q = p - 1;
-      if (q >= r0 && q < r0 + COL_R && q < ny && out_lane && !in_block(q)) {
-        const int sq = brow(q) + bx;
-        const float drx = EDGE ? sdr[sq] : dA;
-        float drn, un, vn;
-        int nxo = 0, nyo = 0;
-        const int cls = EDGE ? node_class(g, i, q, nxo, nyo) : C_INTERIOR;
-        const float* fk = X;
-        if (cls == C_INTERIOR) {
-          gather9(fk, drx, sbi[sq], drn, un, vn);
-        } else {
-          float s0 = 0.f, sp = 0.f;
-#pragma unroll
-          for (int k = 0; k < 9; ++k) {
-            const int cx = cxk(k), cy = cyk(k);
-            const int si = i - cx, sj = q - cy;
-            if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
-            const int cn = cx * nxo + cy * nyo;
-            if (cn == 0) s0 += fk[k];
-            else if (cn > 0) sp += fk[k];
-          }
-          if (cls == C_CORNER) {
-            const int jn = (q == 0) ? 1 : ny - 2;
-            drn = sdr[brow(jn) + bx];
-            un = vn = 0.f;
-          } else if (cls == C_VELOCITY) {
-            un = 0.f;
-            if (i == 0 && q >= g.in_y0 && q <= g.in_y1) {
-              const double H = (double)(g.in_y1 - g.in_y0), y = (double)(q - g.in_y0);
-              un = a.u_in * (float)(4.0 * y * (H - y) / (H * H));
-            }
-            vn = 0.f;
-            drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));
-          } else {
-            drn = c.drho_out;
-            const float unorm = __fadd_rn(__fmaf_rn(2.f, sp, s0), __fsub_rn(drx, c.drho_out));
-            un = __fmul_rn(unorm, (float)nxo);
-            vn = __fmul_rn(unorm, (float)nyo);
-          }
-        }
-        const size_t o = (size_t)q * nx + i;
-        a.out[0][o] = drn;
-        a.out[1][o] = un;
-        a.out[2][o] = vn;
-        if (a.traj_u) {
-          a.traj_u[o] = un;
-          a.traj_v[o] = vn;
-        }
-        if (bad_velocity(un, vn)) raise_status(a.status, 4);
-      }
-      // rotate the rows
-#pragma unroll
-      for (int k = 0; k < 9; ++k) {
-        X[k] = Y[k];
-        Y[k] = Z[k];
-        Z[k] = 0.f;
-      }
-      if (!EDGE) {
-        dA = dB, uA = uB, vA = vB;
-        dB = dC, uB = uC, vB = vC;
-        if (p + 2 <= r0 + COL_R + 1) {
-          const int o = brow(p + 2) + bx;
-          dC = sdr[o], uC = su[o], vC = sv[o];
-        }
-      }
-    }
-  };
-  // Interior tiles: the same march unrolled by three rows, so that the three-row
-  // register rings rotate by renaming; each row's neighbour values are shuffled
-  // once, when the row is loaded.
-  struct Row {
-    float d, u, v, dl, dr;  // drho, u, v of the lane's column and drho of the columns left and right
-  };
-  auto load_row = [&](Row& R, int y) {
-    const int o = brow(y) + bx;
-    R.d = sdr[o];
-    R.u = su[o];
-    R.v = sv[o];
-    R.dl = __shfl_up_sync(0xffffffffu, R.d, 1);
-    R.dr = __shfl_down_sync(0xffffffffu, R.d, 1);
-  };
-  // One row p of the march: A, B, C hold rows p-1, p, p+1; X, Y, Z collect the
-  // populations of destination rows p-1, p, p+1.  Row p+2 is loaded into A.
-  auto step = [&](int p, Row& A, Row& B, Row& C, float* X, float* Y, float* Z) {
-    const float uL = __shfl_up_sync(0xffffffffu, B.u, 1), uR = __shfl_down_sync(0xffffffffu, B.u, 1);
-    const float vL = __shfl_up_sync(0xffffffffu, B.v, 1), vR = __shfl_down_sync(0xffffffffu, B.v, 1);
-    const float uu = B.u, vv = B.v;
-    const float dr = B.d;
-    float F[9];
-    {
-      const float dn[9] = {0.f, B.dr, C.d, B.dl, A.d, C.dr, C.dl, A.dl, A.dr};
-      push9(dr, dn, uu, vv, cdiff(uR, uL), cdiff(C.u, A.u), cdiff(vR, vL), cdiff(C.v, A.v), c.A, F);
-    }
-    const int s2 = brow(p) + bx;
-    if (a.J_partial && out_lane && p >= r0 && p < r0 + COL_R) {
-      jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
-    }
-    X[4] = F[4];
-    X[7] = __shfl_down_sync(0xffffffffu, F[7], 1);
-    X[8] = __shfl_up_sync(0xffffffffu, F[8], 1);
-    Y[0] = F[0];
-    Y[1] = __shfl_up_sync(0xffffffffu, F[1], 1);
-    Y[3] = __shfl_down_sync(0xffffffffu, F[3], 1);
-    Z[2] = F[2];
-    Z[5] = __shfl_up_sync(0xffffffffu, F[5], 1);
-    Z[6] = __shfl_down_sync(0xffffffffu, F[6], 1);
-    const int q = p - 1;
-    if (q >= r0 && out_lane) {  // row p - 1 is complete
-      float drn, un, vn;
-      gather9(X, A.d, sbi[s2 - BW], drn, un, vn);
-      const size_t o = (size_t)q * nx + i;
-      a.out[0][o] = drn;
-      a.out[1][o] = un;
-      a.out[2][o] = vn;
-      if (a.traj_u) {
-        a.traj_u[o] = un;
-        a.traj_v[o] = vn;
-      }
-      if (bad_velocity(un, vn)) raise_status(a.status, 4);
-    }
-    if (p + 2 <= r0 + COL_R + 1) load_row(A, p + 2);
-  };
-  if (fast) {
-    Row R0, R1, R2;
-    float X0[9], X1[9], X2[9];
-    load_row(R0, r0 - 2);
-    load_row(R1, r0 - 1);
-    load_row(R2, r0);
-    static_assert((COL_R + 2) % 3 == 0, "the unrolled march covers COL_R + 2 rows in threes");
-#pragma unroll 1
-    for (int p = r0 - 1; p <= r0 + COL_R; p += 3) {
-      step(p, R0, R1, R2, X0, X1, X2);
-      step(p + 1, R1, R2, R0, X1, X2, X0);
-      step(p + 2, R2, R0, R1, X2, X0, X1);
-    }
-  } else {
-    march(std::true_type{});
-  }
-  if (a.J_partial) {
-    const double s = block_sum<COL_NT>(jloc, red);
-    if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
-  }
-}
-
 
 // ---------------------------------------------------------------------------------
-// Warp-column forward with two columns per lane (interior block of the lattice)
+// Warp-column forward with two columns per lane
 // ---------------------------------------------------------------------------------
 // Lane l owns the columns x0 - 2 + 2l and x0 - 1 + 2l and marches down R rows like
 // fwd_col_kernel.  Neighbours inside the lane pair need no shuffle; a row costs two
 // shuffles per field crossing the lane boundary and six for the populations moving
 // to the neighbour lanes, and its loads and stores are 8-byte vectors.  Lanes 1..30
-// write, so a warp covers 60 columns.  Every tile lies at least two nodes inside the
-// lattice: the tile grid starts at (xa, ya) and the host sizes it so; the frame
-// around it runs fwd_col_kernel.  The per-node arithmetic is push9 / gather9, as in
-// the other FP32 staged kernels.
+// write, so a tile is 60 columns wide; tiles start at x = 0 (the first box starts
+// at x = -4 and reads zeros left of the lattice).  nx even keeps a lane's two
+// columns both inside or both outside the lattice.  Tiles at least two nodes inside
+// the lattice take the march without edge tests; the others recompute velocity
+// gradients at edge nodes from the staged box (one-sided differences, continuity)
+// and apply the edge rules of Sec. 2.4 at the output.  The per-node arithmetic is
+// push9 / gather9, as in the other FP32 staged kernels.
 constexpr int C2_W = 60;
 constexpr int C2_BW = C2_W + 8;
 template <int R>
@@ -359,7 +44,7 @@ struct Col2Geo {
   static constexpr size_t smem = (size_t)4 * FS * 4 + 128 + 8 + 8 * COL_WARPS;
   static_assert((R + 2) % 3 == 0, "the unrolled march covers R + 2 rows in threes");
 };
-constexpr int C2_R = 16;
+constexpr int C2_R = 10;
 
 struct Col2Args {
   float* out[3];      // drho, u, v of the new level
@@ -367,9 +52,8 @@ struct Col2Args {
   float* traj_v;
   double* J_partial;  // per-tile accumulator of J_O(old state), or null
   int* status;
-  float u_in;         // unused: no inlet node lies in the block
+  float u_in;         // inlet amplitude of the new level
   int ntx;            // tiles along x
-  int xa, ya;         // lattice origin of the tile grid
 };
 
 template <int R>
@@ -385,8 +69,8 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
   double* red = reinterpret_cast<double*>(bar + 1);
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(box, bar, a.status)) return;
-  const int nx = g.nx;
-  const int x0 = a.xa + (int)(blockIdx.x % a.ntx) * C2_W, y0 = a.ya + (int)(blockIdx.x / a.ntx) * G2::H;
+  const int nx = g.nx, ny = g.ny;
+  const int x0 = (int)(blockIdx.x % a.ntx) * C2_W, y0 = (int)(blockIdx.x / a.ntx) * G2::H;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -405,10 +89,11 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
   const float* sv = box + 2 * FS;
   const float* sbi = box + 3 * FS;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i0 = x0 - 2 + 2 * lane;            // the lane's first lattice column
-  const int bx = TMA_BXPAD - 2 + 2 * lane;     // its column in the box (even: 8-byte aligned)
+  const int i0 = x0 - 2 + 2 * lane;         // the lane's first lattice column
+  const int bx = TMA_BXPAD - 2 + 2 * lane;  // its column in the box (even: 8-byte aligned)
   const int r0 = y0 + warp * R;
-  const bool out_lane = lane >= 1 && lane <= 30;
+  const bool out_lane = lane >= 1 && lane <= 30 && i0 >= 0 && i0 < nx;
+  const bool fast = x0 >= 2 && x0 + C2_W + 2 <= nx && y0 >= 2 && y0 + G2::H + 2 <= ny;
   auto brow = [&](int y) { return (y - y0 + 2) * BW; };
   double jloc = 0.0;
   bool bad = false;
@@ -425,31 +110,89 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     Q.dl = __shfl_up_sync(0xffffffffu, Q.d.y, 1);
     Q.dr = __shfl_down_sync(0xffffffffu, Q.d.x, 1);
   };
+  // Velocity gradients of an edge-tile node at lattice (i, p), box column bc: the
+  // one-sided differences and the continuity rule of the edge nodes.
+  auto edge_grad = [&](int i, int p, int bc, float& dudx, float& dudy, float& dvdx, float& dvdy) {
+    const int by = p - y0 + 2;
+    dudx = dfdx<float, BW>(su, bc, by, i, nx);
+    dudy = dfdy<float, BW>(su, bc, by, p, ny);
+    dvdx = dfdx<float, BW>(sv, bc, by, i, nx);
+    dvdy = dfdy<float, BW>(sv, bc, by, p, ny);
+    const bool xe = (i == 0 || i == nx - 1), ye = (p == 0 || p == ny - 1);
+    if (xe && ye) {
+      dudx = 0.f;
+      dvdy = 0.f;
+    } else if (xe) {
+      dudx = -dvdy;
+    } else if (ye) {
+      dvdy = -dudx;
+    }
+  };
+  // New level of the lattice node (i, q), box column bc, from the populations fk
+  // arriving there (fk[k] = F_k(x - c_k)): the interior gather, or the edge rule.
+  auto out_node = [&](int i, int q, int bc, const float* fk, float drx, float inv, float& drn, float& un,
+                      float& vn) {
+    int nxo = 0, nyo = 0;
+    const int cls = node_class(g, i, q, nxo, nyo);
+    if (cls == C_INTERIOR) {
+      gather9(fk, drx, inv, drn, un, vn);
+      return;
+    }
+    float s0 = 0.f, sp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int cx = cxk(k), cy = cyk(k);
+      const int si = i - cx, sj = q - cy;
+      if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
+      const int cn = cx * nxo + cy * nyo;
+      if (cn == 0) s0 += fk[k];
+      else if (cn > 0) sp += fk[k];
+    }
+    if (cls == C_CORNER) {
+      drn = sdr[brow(q == 0 ? 1 : ny - 2) + bc];
+      un = vn = 0.f;
+    } else if (cls == C_VELOCITY) {
+      un = (i == 0 && q >= g.in_y0 && q <= g.in_y1) ? a.u_in * inlet_profile<float>(g, q) : 0.f;
+      vn = 0.f;
+      drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));
+    } else {
+      drn = c.drho_out;
+      const float unorm = __fadd_rn(__fmaf_rn(2.f, sp, s0), __fsub_rn(drx, c.drho_out));
+      un = __fmul_rn(unorm, (float)nxo);
+      vn = __fmul_rn(unorm, (float)nyo);
+    }
+  };
   // Destination row of the march: the nine populations arriving at each column.
   struct Dst {
     float a[9], b[9];
   };
   // Row p: A, B, C hold rows p-1, p, p+1; X, Y, Z collect destination rows p-1, p,
   // p+1.  Row p-1 is complete afterwards and is written; row p+2 is loaded into A.
-  auto step = [&](int p, Row& A, Row& B, Row& C, Dst& X, Dst& Y, Dst& Z) {
+  auto step = [&](auto edge_tag, int p, Row& A, Row& B, Row& C, Dst& X, Dst& Y, Dst& Z) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
     const float uL = __shfl_up_sync(0xffffffffu, B.u.y, 1), uR = __shfl_down_sync(0xffffffffu, B.u.x, 1);
     const float vL = __shfl_up_sync(0xffffffffu, B.v.y, 1), vR = __shfl_down_sync(0xffffffffu, B.v.x, 1);
+    float g0[4] = {cdiff(B.u.y, uL), cdiff(C.u.x, A.u.x), cdiff(B.v.y, vL), cdiff(C.v.x, A.v.x)};
+    float g1[4] = {cdiff(uR, B.u.x), cdiff(C.u.y, A.u.y), cdiff(vR, B.v.x), cdiff(C.v.y, A.v.y)};
+    if (EDGE) {
+      if (i0 == 0 || p == 0 || p == ny - 1) edge_grad(i0, p, bx, g0[0], g0[1], g0[2], g0[3]);
+      if (i0 + 1 == nx - 1 || p == 0 || p == ny - 1) edge_grad(i0 + 1, p, bx + 1, g1[0], g1[1], g1[2], g1[3]);
+    }
     float F0[9], F1[9];
     {
       const float dn[9] = {0.f, B.d.y, C.d.x, B.dl, A.d.x, C.d.y, C.dl, A.dl, A.d.y};
-      push9(B.d.x, dn, B.u.x, B.v.x, cdiff(B.u.y, uL), cdiff(C.u.x, A.u.x), cdiff(B.v.y, vL), cdiff(C.v.x, A.v.x),
-            c.A, F0);
+      push9(B.d.x, dn, B.u.x, B.v.x, g0[0], g0[1], g0[2], g0[3], c.A, F0);
     }
     {
       const float dn[9] = {0.f, B.dr, C.d.y, B.d.x, A.d.y, C.dr, C.d.x, A.d.x, A.dr};
-      push9(B.d.y, dn, B.u.y, B.v.y, cdiff(uR, B.u.x), cdiff(C.u.y, A.u.y), cdiff(vR, B.v.x), cdiff(C.v.y, A.v.y),
-            c.A, F1);
+      push9(B.d.y, dn, B.u.y, B.v.y, g1[0], g1[1], g1[2], g1[3], c.A, F1);
     }
-    if (a.J_partial && out_lane && p >= r0 && p < r0 + R) {
+    // objective of the old state at the interior output nodes of row p
+    if (a.J_partial && out_lane && p >= r0 && p < r0 + R && (!EDGE || (p > 0 && p < ny - 1))) {
       const int s2 = brow(p) + bx;
       const float2 inv = *reinterpret_cast<const float2*>(sbi + s2);
-      jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, inv.x, B.u.x, B.v.x);
-      jloc += (double)jo_flow<BW>(su, sv, s2 + 1, c.nu, inv.y, B.u.y, B.v.y);
+      if (!EDGE || i0 > 0) jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, inv.x, B.u.x, B.v.x);
+      if (!EDGE || i0 + 1 < nx - 1) jloc += (double)jo_flow<BW>(su, sv, s2 + 1, c.nu, inv.y, B.u.y, B.v.y);
     }
     // populations of the first column moving left go to the previous lane's second
     // column; those of the second column moving right to the next lane's first
@@ -464,11 +207,16 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     Z.a[2] = F0[2], Z.a[5] = l5, Z.a[6] = F1[6];  // c_y = +1: destination row p + 1
     Z.b[2] = F1[2], Z.b[5] = F0[5], Z.b[6] = r6;
     const int q = p - 1;
-    if (q >= r0 && out_lane) {
+    if (q >= r0 && out_lane && (!EDGE || q < ny)) {
       const float2 inv = *reinterpret_cast<const float2*>(sbi + brow(q) + bx);
       float2 dn, un, vn;
-      gather9(X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
-      gather9(X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+      if (EDGE) {
+        out_node(i0, q, bx, X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
+        out_node(i0 + 1, q, bx + 1, X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+      } else {
+        gather9(X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
+        gather9(X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+      }
       const size_t o = (size_t)q * nx + i0;
       *reinterpret_cast<float2*>(a.out[0] + o) = dn;
       *reinterpret_cast<float2*>(a.out[1] + o) = un;
@@ -481,24 +229,27 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     }
     if (p + 2 <= r0 + R + 1) load_row(A, p + 2);
   };
-  Row R0, R1, R2;
-  Dst X0, X1, X2;
-  load_row(R0, r0 - 2);
-  load_row(R1, r0 - 1);
-  load_row(R2, r0);
+  auto march = [&](auto edge_tag) {
+    Row R0, R1, R2;
+    Dst X0, X1, X2;
+    load_row(R0, r0 - 2);
+    load_row(R1, r0 - 1);
+    load_row(R2, r0);
 #pragma unroll 1
-  for (int p = r0 - 1; p <= r0 + R; p += 3) {
-    step(p, R0, R1, R2, X0, X1, X2);
-    step(p + 1, R1, R2, R0, X1, X2, X0);
-    step(p + 2, R2, R0, R1, X2, X0, X1);
-  }
+    for (int p = r0 - 1; p <= r0 + R; p += 3) {
+      step(edge_tag, p, R0, R1, R2, X0, X1, X2);
+      step(edge_tag, p + 1, R1, R2, R0, X1, X2, X0);
+      step(edge_tag, p + 2, R2, R0, R1, X2, X0, X1);
+    }
+  };
+  if (fast) march(std::false_type{});
+  else march(std::true_type{});
   if (bad) raise_status(a.status, 4);
   if (a.J_partial) {
     const double s = block_sum<COL_NT>(jloc, red);
     if (threadIdx.x == 0) a.J_partial[blockIdx.x] += s;
   }
 }
-
 
 // ---------------------------------------------------------------------------------
 // Warp-column ALKS step (FP32, non-thermal, one lattice)

@@ -47,6 +47,20 @@ struct Geom {
   int t_kind[4];  // left, right, bottom, top
 };
 
+// Parabolic inlet profile 4 y (H - y) / H^2 at row j (y = j - in_y0, H = in_y1 -
+// in_y0), in the arithmetic of the instance: FP64 for double, explicitly rounded
+// FP32 for float (the same value in every FP32 kernel).
+template <typename R>
+__device__ __forceinline__ R inlet_profile(const Geom& g, int j) {
+  if constexpr (sizeof(R) == 8) {
+    const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
+    return 4.0 * y * (H - y) / (H * H);
+  } else {
+    const float H = (float)(g.in_y1 - g.in_y0), y = (float)(j - g.in_y0);
+    return __fdiv_rn(__fmul_rn(__fmul_rn(4.f, y), __fsub_rn(H, y)), __fmul_rn(H, H));
+  }
+}
+
 template <typename R>
 struct Coef {
   R A;          // Eq. (A): nu = 1/6 - 2A/9
@@ -370,8 +384,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
       } else if (cls == C_VELOCITY) {
         un = R(0);
         if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
-          const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
-          un = a.u_in * (R)(4.0 * y * (H - y) / (H * H));
+          un = a.u_in * inlet_profile<R>(g, j);
         }
         vn = R(0);
         drn = drx + (s0 + R(2) * sp - (un * R(nxo) + vn * R(nyo)));

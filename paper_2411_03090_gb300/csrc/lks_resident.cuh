@@ -339,8 +339,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_resident_kernel(ResArgs<R> a, Geom 
       } else if (cls == C_VELOCITY) {
         un = R(0);
         if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
-          const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
-          un = a.u_in * (R)(4.0 * y * (H - y) / (H * H));
+          un = a.u_in * inlet_profile<R>(g, j);
         }
         vn = R(0);
         drn = drx + (s0 + R(2) * sp - (un * R(nxo) + vn * R(nyo)));

@@ -535,8 +535,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
           } else if (cls == C_VELOCITY) {
             un = 0.f;
             if (i == 0 && j >= g.in_y0 && j <= g.in_y1) {
-              const double H = (double)(g.in_y1 - g.in_y0), y = (double)(j - g.in_y0);
-              un = u_in * (float)(4.0 * y * (H - y) / (H * H));
+              un = u_in * inlet_profile<float>(g, j);
             }
             vn = 0.f;
             drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));

@@ -420,8 +420,9 @@ def test_tma_thermal_gradient_matches_oracle(steady):
 # Warp-column kernels (path "column"; chosen automatically on large lattices)
 # ---------------------------------------------------------------------------------------
 def column_case(steady=True, **kw):
-    """200 x 150: interior column tiles (28 x 64 forward, 28 x 32 adjoint) as well as
-    edge tiles and a ragged last column of tiles (200 = 7 x 28 + 4)."""
+    """200 x 150: interior column tiles (60 x 40 forward, 28 x 32 adjoint) as well as
+    edge tiles and ragged last tiles (forward 200 = 3 x 60 + 20, 150 = 3 x 40 + 30;
+    adjoint 200 = 7 x 28 + 4)."""
     base = dict(seed=9, sigma=3.0, strip=3, n_steps=300, n_adj=300)
     base.update(kw)
     if not steady:
