@@ -367,6 +367,9 @@ def run_batch_study(args):
                    "l2": "flushed before each timed gradient (256 MB write); arena > L2",
                    "tile_shape": list(__import__("paper_2411_03090_gb300").lks.TILE_SHAPES[st.tile_config]),
                    "autotune_us_per_step": [round(x, 1) for x in st.tune_us],
+                   "forward_kernel": "warp-column (60x40 tiles)" if st.fwd_column else "TMA-staged tiles",
+                   "autotune_forward_us": {"tma": round(st.tune_fwd_us[st.tile_config], 1),
+                                           "column": round(st.tune_col_us, 1)},
                    "checkpoint_every": st.checkpoint_every, "arena": [st.arena_w, st.arena_h],
                    "tiles": st.ntiles, "create_s": create_s},
         "roofline": {"bound": "hbm", "kernel": "whole gradient (graph: fwd_tma/adj_tma BATCH kernels)",

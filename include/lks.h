@@ -268,9 +268,10 @@ lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
  * Layout: the designs' lattices are packed side by side into one arena per field
  * (shelf packing of rectangles whose extents are rounded up to 128 x 16 nodes), so
  * a single tensor map per field serves every design; a work list names each
- * (design, tile) pair.  The tile shape is one of LKS_BATCH_TILE_CONFIGS fixed
- * shapes, picked by timing each on the batch at lks_batch_create (tile_config = -1)
- * or given.  K = 0 picks the checkpoint spacing that minimises workspace bytes
+ * (design, tile) pair.  The tile shape of the TMA-staged kernels is one of
+ * LKS_BATCH_TILE_CONFIGS fixed shapes, picked by timing each on the batch at
+ * lks_batch_create (tile_config = -1) or given; the forward may instead run the
+ * warp-column kernel (fwd_column), again timed or given.  K = 0 picks the checkpoint spacing that minimises workspace bytes
  * (snapshots + segment buffer), a pure function of the descriptors.
  * --------------------------------------------------------------------------------- */
 #define LKS_BATCH_VERSION 1
@@ -284,7 +285,10 @@ typedef struct {
   int32_t tile_config;      /* -1: autotune at create; else 0 .. LKS_BATCH_TILE_CONFIGS - 1:
                                0 = 64x8, 1 = 32x16, 2 = 128x4, 3 = 64x16 output nodes per tile */
   int32_t use_graph;        /* 1: each gradient is one CUDA graph launch; 0: direct launches */
-  int32_t reserved[7];      /* must be zero */
+  int32_t fwd_column;       /* forward kernel: -1 the faster of the two, timed at create; 0 the
+                               TMA-staged kernel at tile_config; 1 the warp-column kernel
+                               (60 x 40 tiles, two columns per lane)                  */
+  int32_t reserved[6];      /* must be zero */
 } lks_batch_options;
 
 typedef struct {
@@ -301,6 +305,9 @@ typedef struct {
   int64_t kernel_launches;  /* kernels one gradient launches (inside the graph when used) */
   int64_t gradients;        /* gradients computed so far */
   float tune_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward + adjoint step of each shape (0: not timed) */
+  int32_t fwd_column;       /* 1 when the forward runs the warp-column kernel */
+  float tune_fwd_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward step of each shape (0: not timed) */
+  float tune_col_us;        /* autotuner: us per forward step of the warp-column kernel (0: not timed) */
 } lks_batch_stats;
 
 /* Host only.  n designs described by descs[0..n-1]; opt as above (NULL: K = 0,

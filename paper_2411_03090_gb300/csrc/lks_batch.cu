@@ -28,6 +28,7 @@
 #include "../../include/lks.h"
 #include "lks_host.cuh"
 #include "lks_kernels.cuh"
+#include "lks_col.cuh"
 #include "lks_tma.cuh"
 
 using namespace lks;
@@ -200,8 +201,12 @@ __global__ void batch_decode_kernel(const S* __restrict__ y, float* __restrict__
 // ------------------------------------------------------------------------------------
 // Plan: arena packing, work lists, checkpoint spacing and workspace layout
 // ------------------------------------------------------------------------------------
+// Work lists 0 .. kNCfg-1 belong to the tile shapes of the TMA-staged kernels, list
+// kColList to the warp-column forward (60 x 40 tiles).
+constexpr int kColList = kNCfg;
+constexpr int kNLists = kNCfg + 1;
 struct BLayout {
-  size_t designs = 0, work[kNCfg] = {}, rng[kNCfg] = {}, uin = 0, emap = 0, gptr = 0, dptr = 0;
+  size_t designs = 0, work[kNLists] = {}, rng[kNLists] = {}, uin = 0, emap = 0, gptr = 0, dptr = 0;
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, mat = 0, sens = 0, sens64 = 0;
   size_t jt = 0, jfin = 0, jval = 0, status = 0, snaps = 0, scales = 0, seg = 0, total = 0;
 };
@@ -211,8 +216,8 @@ struct Plan {
   size_t A = 0, snap_elem = 2;
   int64_t nodes = 0;
   std::vector<int> ax, ay;
-  std::vector<BatchTile> work[kNCfg];
-  std::vector<int> rng[kNCfg];
+  std::vector<BatchTile> work[kNLists];
+  std::vector<int> rng[kNLists];
   BLayout L;
 };
 
@@ -261,6 +266,7 @@ lks_batch_options default_options() {
   o.snapshot_type = LKS_SNAP_BF16;
   o.tile_config = -1;
   o.use_graph = 1;
+  o.fwd_column = -1;
   return o;
 }
 
@@ -277,7 +283,8 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   if (opt->snapshot_type < LKS_SNAP_F32 || opt->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
   if (opt->tile_config < -1 || opt->tile_config >= kNCfg) return bad("bad tile_config");
   if (opt->use_graph != 0 && opt->use_graph != 1) return bad("use_graph must be 0 or 1");
-  for (int q = 0; q < 7; ++q)
+  if (opt->fwd_column < -1 || opt->fwd_column > 1) return bad("fwd_column must be -1, 0 or 1");
+  for (int q = 0; q < 6; ++q)
     if (opt->reserved[q] != 0) return bad("reserved option fields must be zero");
   P->n = n;
   P->n_steps = descs[0].n_steps;
@@ -315,8 +322,8 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   P->A = (size_t)P->W * P->H;
   if (P->A > ((size_t)1 << 31)) return bad("arena larger than 2^31 nodes");
   // work lists, design by design, row-major tiles
-  for (int c = 0; c < kNCfg; ++c) {
-    const int TXc = kShape[c].tx, TYc = kShape[c].ty;
+  for (int c = 0; c < kNLists; ++c) {
+    const int TXc = c < kNCfg ? kShape[c].tx : C2_W, TYc = c < kNCfg ? kShape[c].ty : Col2Geo<C2_R>::H;
     P->work[c].clear();
     P->rng[c].assign(2 * n, 0);
     for (int d = 0; d < n; ++d) {
@@ -350,7 +357,7 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   };
   size_t max_tiles = 0;
   L.designs = take(sizeof(BatchDesign) * n);
-  for (int c = 0; c < kNCfg; ++c) {
+  for (int c = 0; c < kNLists; ++c) {
     L.work[c] = take(sizeof(BatchTile) * P->work[c].size());
     L.rng[c] = take(sizeof(int) * 2 * n);
     max_tiles = std::max(max_tiles, P->work[c].size());
@@ -394,13 +401,14 @@ struct lks_batch {
   cudaStream_t stream = nullptr;
   int device = 0, sms = 0;
   int cfg = 0;
+  bool fwd_col = false;  // forward on the warp-column kernel (work list kColList)
   int grid_fwd[kNCfg] = {}, grid_adj[kNCfg] = {};
   int cur = 0, acur = 0;
   std::unordered_map<uint64_t, CUtensorMap> tmaps;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0, launches_per_grad = 0, gradients = 0;
-  float tune_us[kNCfg] = {};
+  float tune_us[kNCfg] = {}, tune_fwd_us[kNCfg] = {}, tune_col_us = 0.f;
   std::string err;
 };
 
@@ -546,7 +554,37 @@ lks_status adj_step_c(lks_batch* b, const float* u1, const float* v1, const floa
   return LKS_OK;
 }
 
+// One forward step of every design on the warp-column kernel (one CTA per entry of
+// work list kColList).
+lks_status fwd_col_step(lks_batch* b, int t_new, bool jacc, float* tu, float* tv) {
+  using G2 = Col2Geo<C2_R>;
+  const int src = b->cur, dst = 1 - b->cur;
+  TmaMaps<4> maps;
+  lks_status st;
+  const float* fsrc[4] = {stp(b, src, 0), stp(b, src, 1), stp(b, src, 2), af(b, b->P.L.mat, 0)};
+  for (int f = 0; f < 4; ++f)
+    if ((st = arena_map(b, fsrc[f], C2_BW, G2::BH, &maps.m[f])) != LKS_OK) return st;
+  Col2Args a;
+  std::memset(&a, 0, sizeof(a));
+  for (int f = 0; f < 3; ++f) a.out[f] = stp(b, dst, f);
+  a.traj_u = tu;
+  a.traj_v = tv;
+  a.J_partial = jacc ? reinterpret_cast<double*>(b->ws + b->P.L.jt) : nullptr;
+  a.status = dstatus(b);
+  a.work = reinterpret_cast<const BatchTile*>(b->ws + b->P.L.work[kColList]);
+  a.designs = ddesigns(b);
+  a.u_in_d = reinterpret_cast<const float*>(b->ws + b->P.L.uin) + (size_t)t_new * b->n;
+  a.pitch = b->P.W;
+  fwd_col2_kernel<C2_R, true><<<(int)b->P.work[kColList].size(), COL_NT, G2::smem, b->stream>>>(
+      maps, a, Geom{}, Coef<float>{});
+  CKB(b, cudaGetLastError());
+  b->cur = dst;
+  b->launches++;
+  return LKS_OK;
+}
+
 lks_status fwd_step(lks_batch* b, int t_new, bool jacc, float* tu, float* tv) {
+  if (b->fwd_col) return fwd_col_step(b, t_new, jacc, tu, tv);
   switch (b->cfg) {
     case 0: return fwd_step_c<0>(b, t_new, jacc, tu, tv);
     case 1: return fwd_step_c<1>(b, t_new, jacc, tu, tv);
@@ -647,7 +685,8 @@ lks_status enqueue_gradient(lks_batch* b) {
   if ((st = materials(b)) != LKS_OK) return st;
   CKB(b, cudaMemsetAsync(b->ws + L.stA, 0, fb * 3, b->stream));
   CKB(b, cudaMemsetAsync(b->ws + L.status, 0, sizeof(int), b->stream));
-  CKB(b, cudaMemsetAsync(b->ws + L.jt, 0, sizeof(double) * P.work[b->cfg].size(), b->stream));
+  const int flist = b->fwd_col ? kColList : b->cfg;  // work list of the forward (J partials per tile)
+  CKB(b, cudaMemsetAsync(b->ws + L.jt, 0, sizeof(double) * P.work[flist].size(), b->stream));
   b->cur = 0;
   // forward march with a snapshot every K steps (Step 2), J accumulated per step (Step 3)
   for (int t = 0; t < n; ++t) {
@@ -658,7 +697,7 @@ lks_status enqueue_gradient(lks_batch* b) {
       stp(b, b->cur, 1), stp(b, b->cur, 2), af(b, L.gamma), ddesigns(b), P.W,
       reinterpret_cast<double*>(b->ws + L.jfin));
   batch_reduce_J_kernel<<<b->n, NTHREADS, 0, b->stream>>>(
-      reinterpret_cast<const double*>(b->ws + L.jt), reinterpret_cast<const int*>(b->ws + L.rng[b->cfg]),
+      reinterpret_cast<const double*>(b->ws + L.jt), reinterpret_cast<const int*>(b->ws + L.rng[flist]),
       reinterpret_cast<const double*>(b->ws + L.jfin), kJBX, reinterpret_cast<double*>(b->ws + L.jval));
   CKB(b, cudaGetLastError());
   b->launches += 2;
@@ -699,9 +738,11 @@ lks_status enqueue_gradient(lks_batch* b) {
   return LKS_OK;
 }
 
-// Times `steps` forward and adjoint steps of tile shape c on a uniform design.
-lks_status time_cfg(lks_batch* b, int c, int steps, float* us) {
+// Times `steps` forward and adjoint steps of tile shape c on a uniform design (the
+// forward on the warp-column kernel when col): us per forward and per adjoint step.
+lks_status time_cfg(lks_batch* b, int c, bool col, int steps, float* fwd_us, float* adj_us) {
   b->cfg = c;
+  b->fwd_col = col;
   const size_t fb = b->P.A * 4;
   CKB(b, cudaMemsetAsync(b->ws + b->P.L.stA, 0, fb * 3, b->stream));
   CKB(b, cudaMemsetAsync(b->ws + b->P.L.adA, 0, fb * 6, b->stream));
@@ -735,7 +776,8 @@ lks_status time_cfg(lks_batch* b, int c, int steps, float* us) {
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&m1, e[0], e[1]);
     if (ce == cudaSuccess) ce = cudaEventElapsedTime(&m2, e[1], e[2]);
     if (ce != cudaSuccess) st = bfail(b, LKS_ERR_CUDA, std::string("autotune timing: ") + cudaGetErrorString(ce));
-    *us = (m1 + m2) * 1000.f / (float)steps;
+    *fwd_us = m1 * 1000.f / (float)steps;
+    *adj_us = m2 * 1000.f / (float)steps;
   }
   for (auto& x : e) cudaEventDestroy(x);
   return st;
@@ -746,12 +788,26 @@ lks_status autotune(lks_batch* b) {
   CKB(b, cudaGetLastError());
   lks_status st;
   if ((st = materials(b)) != LKS_OK) return st;
-  int best = 0;
+  // tile shape (tile_config = -1): least forward + adjoint time per step
+  int best = b->opt.tile_config;
   for (int c = 0; c < kNCfg; ++c) {
-    if ((st = time_cfg(b, c, 8, &b->tune_us[c])) != LKS_OK) return st;
-    if (b->tune_us[c] < b->tune_us[best]) best = c;
+    if (b->opt.tile_config >= 0 && c != b->opt.tile_config) continue;
+    float fu = 0.f, au = 0.f;
+    if ((st = time_cfg(b, c, false, 8, &fu, &au)) != LKS_OK) return st;
+    b->tune_fwd_us[c] = fu;
+    b->tune_us[c] = fu + au;
+    if (best < 0 || b->tune_us[c] < b->tune_us[best]) best = c;
   }
   b->cfg = best;
+  // forward kernel (fwd_column = -1): the warp-column kernel when it beats the TMA
+  // forward of that shape
+  b->fwd_col = false;
+  if (b->opt.fwd_column != 0) {
+    float fu = 0.f, au = 0.f;
+    if ((st = time_cfg(b, best, true, 8, &fu, &au)) != LKS_OK) return st;
+    b->tune_col_us = fu;
+    b->fwd_col = b->opt.fwd_column == 1 || fu < b->tune_fwd_us[best];
+  }
   int dev_status = 0;
   CKB(b, cudaMemcpy(&dev_status, dstatus(b), sizeof(int), cudaMemcpyDeviceToHost));
   if (dev_status != 0) return bfail(b, (lks_status)dev_status, "device status raised while autotuning");
@@ -865,17 +921,21 @@ lks_status lks_batch_create(int32_t n, const lks_problem_desc* descs, const lks_
       up_h(P.L.uin, uin.data(), sizeof(float) * uin.size()) != cudaSuccess ||
       up_h(P.L.emap, emap.data(), sizeof(float) * emap.size()) != cudaSuccess)
     return fin(bfail(b, LKS_ERR_CUDA, "upload of the design tables failed"));
-  for (int c = 0; c < kNCfg; ++c)
+  for (int c = 0; c < kNLists; ++c)
     if (up_h(P.L.work[c], P.work[c].data(), sizeof(BatchTile) * P.work[c].size()) != cudaSuccess ||
         up_h(P.L.rng[c], P.rng[c].data(), sizeof(int) * P.rng[c].size()) != cudaSuccess)
       return fin(bfail(b, LKS_ERR_CUDA, "upload of the work lists failed"));
   if ((st = setup_cfg<0>(b)) != LKS_OK || (st = setup_cfg<1>(b)) != LKS_OK || (st = setup_cfg<2>(b)) != LKS_OK ||
       (st = setup_cfg<3>(b)) != LKS_OK)
     return fin(st);
-  if (b->opt.tile_config < 0) {
+  if (cudaFuncSetAttribute(fwd_col2_kernel<C2_R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)Col2Geo<C2_R>::smem) != cudaSuccess)
+    return fin(bfail(b, LKS_ERR_CUDA, "shared-memory attribute of the column forward"));
+  if (b->opt.tile_config < 0 || b->opt.fwd_column < 0) {  // time what is not given
     if ((st = autotune(b)) != LKS_OK) return fin(st);
   } else {
     b->cfg = b->opt.tile_config;
+    b->fwd_col = b->opt.fwd_column == 1;
   }
   if (b->opt.use_graph && (st = capture_graph(b)) != LKS_OK) return fin(st);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fin(bfail(b, LKS_ERR_CUDA, "create: sync failed"));
@@ -922,6 +982,9 @@ lks_status lks_batch_query(lks_batch* b, lks_batch_stats* out) {
   out->kernel_launches = b->launches_per_grad;
   out->gradients = b->gradients;
   for (int c = 0; c < kNCfg; ++c) out->tune_us[c] = b->tune_us[c];
+  out->fwd_column = b->fwd_col ? 1 : 0;
+  for (int c = 0; c < kNCfg; ++c) out->tune_fwd_us[c] = b->tune_fwd_us[c];
+  out->tune_col_us = b->tune_col_us;
   return LKS_OK;
 }
 

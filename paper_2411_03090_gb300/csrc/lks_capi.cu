@@ -519,6 +519,7 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
   for (int f = 0; f < 4; ++f)
     if ((st = field_map(h, fsrc[f], C2_BW, G2::BH, &maps.m[f])) != LKS_OK) return st;
   Col2Args a;
+  std::memset(&a, 0, sizeof(a));
   for (int f = 0; f < 3; ++f) a.out[f] = state_ptr<float>(h, dst, f);
   a.traj_u = tu;
   a.traj_v = tv;
@@ -529,10 +530,11 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
   const int grid = a.ntx * ((d.ny + G2::H - 1) / G2::H);
   static bool attr = false;
   if (!attr) {
-    CKH(h, cudaFuncSetAttribute(fwd_col2_kernel<C2_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2::smem));
+    CKH(h, cudaFuncSetAttribute(fwd_col2_kernel<C2_R, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)G2::smem));
     attr = true;
   }
-  fwd_col2_kernel<C2_R><<<grid, COL_NT, G2::smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  fwd_col2_kernel<C2_R, false><<<grid, COL_NT, G2::smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->cur = dst;
   h->t = t_new;

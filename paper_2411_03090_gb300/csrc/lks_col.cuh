@@ -52,15 +52,23 @@ struct Col2Args {
   float* traj_v;
   double* J_partial;  // per-tile accumulator of J_O(old state), or null
   int* status;
-  float u_in;         // inlet amplitude of the new level
-  int ntx;            // tiles along x
+  float u_in;         // inlet amplitude of the new level (single lattice)
+  int ntx;            // tiles along x (single lattice)
+  // batched form: one work-list entry per CTA, per-design tables, arena row pitch
+  const BatchTile* work;
+  const BatchDesign* designs;
+  const float* u_in_d;  // inlet amplitude of the new level, per design
+  int pitch;
 };
 
-template <int R>
+// BATCH: the lattices of many designs packed in one arena (tile origins and the
+// interior flag from the work list; geometry, coefficients and inlet amplitude from
+// the design table; fields addressed with the arena pitch, nx may be odd).
+template <int R, bool BATCH>
 __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant__ TmaMaps<4> maps,
                                                           const __grid_constant__ Col2Args a,
-                                                          const __grid_constant__ Geom g,
-                                                          const __grid_constant__ Coef<float> c) {
+                                                          const __grid_constant__ Geom g0,
+                                                          const __grid_constant__ Coef<float> c0) {
   using G2 = Col2Geo<R>;
   constexpr int BW = C2_BW, FS = G2::FS;
   extern __shared__ unsigned char smem_raw[];
@@ -69,14 +77,39 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
   double* red = reinterpret_cast<double*>(bar + 1);
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(box, bar, a.status)) return;
+  int x0, y0, ax = 0, ay = 0;
+  bool fast;
+  const Geom* gp = &g0;
+  const Coef<float>* cp = &c0;
+  float u_in = a.u_in;
+  size_t pitch;
+  if constexpr (BATCH) {
+    const BatchTile w = a.work[blockIdx.x];
+    const BatchDesign& bd = a.designs[w.d];
+    gp = &bd.g;
+    cp = &bd.c;
+    x0 = w.x0;
+    y0 = w.y0;
+    ax = bd.ax;
+    ay = bd.ay;
+    fast = w.interior != 0;
+    u_in = a.u_in_d[w.d];
+    pitch = (size_t)a.pitch;
+  } else {
+    x0 = (int)(blockIdx.x % a.ntx) * C2_W;
+    y0 = (int)(blockIdx.x / a.ntx) * G2::H;
+    fast = x0 >= 2 && x0 + C2_W + 2 <= g0.nx && y0 >= 2 && y0 + G2::H + 2 <= g0.ny;
+    pitch = (size_t)g0.nx;
+  }
+  const Geom& g = *gp;
+  const Coef<float>& c = *cp;
   const int nx = g.nx, ny = g.ny;
-  const int x0 = (int)(blockIdx.x % a.ntx) * C2_W, y0 = (int)(blockIdx.x / a.ntx) * G2::H;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
     fence_proxy_async();
     mbar_expect_tx(bar, 4 * G2::BOX * 4);
-    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * FS, &maps.m[f], ax + x0 - TMA_BXPAD, ay + y0 - 2, bar);
   }
   __syncthreads();
   if (!mbar_wait(bar, 0)) {
@@ -93,7 +126,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
   const int bx = TMA_BXPAD - 2 + 2 * lane;  // its column in the box (even: 8-byte aligned)
   const int r0 = y0 + warp * R;
   const bool out_lane = lane >= 1 && lane <= 30 && i0 >= 0 && i0 < nx;
-  const bool fast = x0 >= 2 && x0 + C2_W + 2 <= nx && y0 >= 2 && y0 + G2::H + 2 <= ny;
+  const bool out1 = i0 + 1 < nx;  // second column inside too (always, for even nx)
   auto brow = [&](int y) { return (y - y0 + 2) * BW; };
   double jloc = 0.0;
   bool bad = false;
@@ -152,7 +185,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
       drn = sdr[brow(q == 0 ? 1 : ny - 2) + bc];
       un = vn = 0.f;
     } else if (cls == C_VELOCITY) {
-      un = (i == 0 && q >= g.in_y0 && q <= g.in_y1) ? a.u_in * inlet_profile<float>(g, q) : 0.f;
+      un = (i == 0 && q >= g.in_y0 && q <= g.in_y1) ? u_in * inlet_profile<float>(g, q) : 0.f;
       vn = 0.f;
       drn = __fadd_rn(drx, __fsub_rn(__fmaf_rn(2.f, sp, s0), __fmaf_rn(vn, (float)nyo, __fmul_rn(un, (float)nxo))));
     } else {
@@ -172,20 +205,21 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     constexpr bool EDGE = decltype(edge_tag)::value;
     const float uL = __shfl_up_sync(0xffffffffu, B.u.y, 1), uR = __shfl_down_sync(0xffffffffu, B.u.x, 1);
     const float vL = __shfl_up_sync(0xffffffffu, B.v.y, 1), vR = __shfl_down_sync(0xffffffffu, B.v.x, 1);
-    float g0[4] = {cdiff(B.u.y, uL), cdiff(C.u.x, A.u.x), cdiff(B.v.y, vL), cdiff(C.v.x, A.v.x)};
-    float g1[4] = {cdiff(uR, B.u.x), cdiff(C.u.y, A.u.y), cdiff(vR, B.v.x), cdiff(C.v.y, A.v.y)};
+    float gr0[4] = {cdiff(B.u.y, uL), cdiff(C.u.x, A.u.x), cdiff(B.v.y, vL), cdiff(C.v.x, A.v.x)};
+    float gr1[4] = {cdiff(uR, B.u.x), cdiff(C.u.y, A.u.y), cdiff(vR, B.v.x), cdiff(C.v.y, A.v.y)};
     if (EDGE) {
-      if (i0 == 0 || p == 0 || p == ny - 1) edge_grad(i0, p, bx, g0[0], g0[1], g0[2], g0[3]);
-      if (i0 + 1 == nx - 1 || p == 0 || p == ny - 1) edge_grad(i0 + 1, p, bx + 1, g1[0], g1[1], g1[2], g1[3]);
+      const bool ye = p == 0 || p == ny - 1;
+      if (i0 == 0 || i0 == nx - 1 || ye) edge_grad(i0, p, bx, gr0[0], gr0[1], gr0[2], gr0[3]);
+      if (i0 + 1 == nx - 1 || ye) edge_grad(i0 + 1, p, bx + 1, gr1[0], gr1[1], gr1[2], gr1[3]);
     }
     float F0[9], F1[9];
     {
       const float dn[9] = {0.f, B.d.y, C.d.x, B.dl, A.d.x, C.d.y, C.dl, A.dl, A.d.y};
-      push9(B.d.x, dn, B.u.x, B.v.x, g0[0], g0[1], g0[2], g0[3], c.A, F0);
+      push9(B.d.x, dn, B.u.x, B.v.x, gr0[0], gr0[1], gr0[2], gr0[3], c.A, F0);
     }
     {
       const float dn[9] = {0.f, B.dr, C.d.y, B.d.x, A.d.y, C.dr, C.d.x, A.d.x, A.dr};
-      push9(B.d.y, dn, B.u.y, B.v.y, g1[0], g1[1], g1[2], g1[3], c.A, F1);
+      push9(B.d.y, dn, B.u.y, B.v.y, gr1[0], gr1[1], gr1[2], gr1[3], c.A, F1);
     }
     // objective of the old state at the interior output nodes of row p
     if (a.J_partial && out_lane && p >= r0 && p < r0 + R && (!EDGE || (p > 0 && p < ny - 1))) {
@@ -210,22 +244,35 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     if (q >= r0 && out_lane && (!EDGE || q < ny)) {
       const float2 inv = *reinterpret_cast<const float2*>(sbi + brow(q) + bx);
       float2 dn, un, vn;
+      const size_t o = (size_t)(ay + q) * pitch + (size_t)(ax + i0);
       if (EDGE) {
         out_node(i0, q, bx, X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
-        out_node(i0 + 1, q, bx + 1, X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+        if (out1) {
+          out_node(i0 + 1, q, bx + 1, X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
+        } else {  // odd nx (batched designs): the pair's second column lies outside
+          a.out[0][o] = dn.x;
+          a.out[1][o] = un.x;
+          a.out[2][o] = vn.x;
+          if (a.traj_u) {
+            a.traj_u[o] = un.x;
+            a.traj_v[o] = vn.x;
+          }
+          bad |= bad_velocity(un.x, vn.x);
+        }
       } else {
         gather9(X.a, A.d.x, inv.x, dn.x, un.x, vn.x);
         gather9(X.b, A.d.y, inv.y, dn.y, un.y, vn.y);
       }
-      const size_t o = (size_t)q * nx + i0;
-      *reinterpret_cast<float2*>(a.out[0] + o) = dn;
-      *reinterpret_cast<float2*>(a.out[1] + o) = un;
-      *reinterpret_cast<float2*>(a.out[2] + o) = vn;
-      if (a.traj_u) {
-        *reinterpret_cast<float2*>(a.traj_u + o) = un;
-        *reinterpret_cast<float2*>(a.traj_v + o) = vn;
+      if (!EDGE || out1) {
+        *reinterpret_cast<float2*>(a.out[0] + o) = dn;
+        *reinterpret_cast<float2*>(a.out[1] + o) = un;
+        *reinterpret_cast<float2*>(a.out[2] + o) = vn;
+        if (a.traj_u) {
+          *reinterpret_cast<float2*>(a.traj_u + o) = un;
+          *reinterpret_cast<float2*>(a.traj_v + o) = vn;
+        }
+        bad |= bad_velocity(un.x, vn.x) | bad_velocity(un.y, vn.y);
       }
-      bad |= bad_velocity(un.x, vn.x) | bad_velocity(un.y, vn.y);
     }
     if (p + 2 <= r0 + R + 1) load_row(A, p + 2);
   };

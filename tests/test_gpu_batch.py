@@ -105,6 +105,26 @@ def test_batch_tile_shapes_agree():
             assert abs(J[k] - J0[k]) <= 1e-12 * abs(J0[k])
 
 
+def test_batch_column_forward_equals_tma_forward():
+    """The warp-column forward (60 x 40 tiles, two columns per lane) computes each
+    node with the arithmetic of the TMA-staged forward, also for an odd nx (the last
+    lane pair half outside its design): identical gradients; J differs only in the
+    order of its FP64 partial sums.  The odd design also matches the oracle."""
+    kw = dict(steady=False, n_steps=60, n_adj=60, pulse_mean=0.75, pulse_amp=0.25, pulse_period=40.0,
+              sigma=2.0, strip=2)
+    pbs = designs() + [inputs.channel(45, 30, Re=15.0, seed=35, **kw), inputs.channel(131, 85, Re=30.0, seed=36, **kw)]
+    Jt, gt, st = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=0)
+    Jc, gc, sc = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=1)
+    assert st.fwd_column == 0 and sc.fwd_column == 1
+    for k in range(len(pbs)):
+        np.testing.assert_array_equal(gc[k], gt[k])
+        assert abs(Jc[k] - Jt[k]) <= 1e-12 * abs(Jt[k]), k
+    for k in (4, 5):
+        ref = O.unsteady_gradient(pbs[k], pbs[k].gamma())
+        assert abs(Jc[k] - ref["J"]) <= 1e-5 * abs(ref["J"]), k
+        assert rel_l2(gc[k], ref["dJdgamma"]) <= 1e-3, k
+
+
 def test_batch_graph_equals_direct_launches():
     pbs = designs()
     Jg, gg, sg = run(pbs, checkpoint_every=13, snapshot="bf16", tile_config=1, use_graph=True)
@@ -124,6 +144,8 @@ def test_batch_single_segment_and_autotune():
     assert st.n_ckpt == 1 and st.checkpoint_every == 25
     assert all(t > 0 for t in st.tune_us)
     assert st.tile_config == int(np.argmin(list(st.tune_us)))
+    assert st.tune_col_us > 0
+    assert st.fwd_column == int(st.tune_col_us < st.tune_fwd_us[st.tile_config])
     assert abs(J[0] - ref["J"]) <= 1e-5 * abs(ref["J"])
     assert rel_l2(grads[0], ref["dJdgamma"]) <= 1e-3
 
