@@ -366,7 +366,7 @@ def run_batch_study(args):
                    "nodes": N, "updates_counted": "forward + adjoint levels (recomputation not counted)",
                    "l2": "flushed before each timed gradient (256 MB write); arena > L2",
                    "tile_shape": list(__import__("paper_2411_03090_gb300").lks.TILE_SHAPES[st.tile_config]),
-                   "autotune_us_per_step": [round(x, 1) for x in st.tune_us],
+                   "autotune_us_per_level": [round(x, 1) for x in st.tune_us],
                    "forward_kernel": "warp-column (60x40 tiles)" if st.fwd_column else "TMA-staged tiles",
                    "autotune_forward_us": {"tma": round(st.tune_fwd_us[st.tile_config], 1),
                                            "column": round(st.tune_col_us, 1)},

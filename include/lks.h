@@ -304,10 +304,12 @@ typedef struct {
   int64_t workspace_bytes;
   int64_t kernel_launches;  /* kernels one gradient launches (inside the graph when used) */
   int64_t gradients;        /* gradients computed so far */
-  float tune_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward + adjoint step of each shape (0: not timed) */
+  float tune_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per level of each shape, two forward steps
+                                            (march, recompute) + one adjoint step (0: not timed) */
   int32_t fwd_column;       /* 1 when the forward runs the warp-column kernel */
   float tune_fwd_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward step of each shape (0: not timed) */
-  float tune_col_us;        /* autotuner: us per forward step of the warp-column kernel (0: not timed) */
+  float tune_col_us;        /* autotuner: us per forward step of the warp-column kernel (0: not timed);
+                               the pair (shape, forward kernel) of least per-level time is used */
 } lks_batch_stats;
 
 /* Host only.  n designs described by descs[0..n-1]; opt as above (NULL: K = 0,

@@ -761,9 +761,18 @@ lks_status time_cfg(lks_batch* b, int c, bool col, int steps, float* fwd_us, flo
       if ((s2 = adj_step(b, u, v, u, v, 1)) != LKS_OK) return s2;
     return LKS_OK;
   };
+  // forward steps as a gradient runs them: half of them accumulate the objective
+  // partials (the march), half store the level's u, v in the segment buffer (the
+  // recompute)
+  float* seg = af(b, b->P.L.seg);
+  auto fwd_as_used = [&](int q) {
+    if (q % 2 == 0) return fwd_step(b, 4 + q, true, nullptr, nullptr);
+    float* lv = seg + (size_t)(1 + (q / 2) % (b->P.seg_levels - 1)) * 2 * b->P.A;
+    return fwd_step(b, 4 + q, false, lv, lv + b->P.A);
+  };
   if ((st = run(3)) == LKS_OK) {
     cudaEventRecord(e[0], b->stream);
-    for (int q = 0; q < steps && st == LKS_OK; ++q) st = fwd_step(b, 4 + q, false, nullptr, nullptr);
+    for (int q = 0; q < steps && st == LKS_OK; ++q) st = fwd_as_used(q);
     cudaEventRecord(e[1], b->stream);
     const float* u = stp(b, b->cur, 1);
     const float* v = stp(b, b->cur, 2);
@@ -788,26 +797,43 @@ lks_status autotune(lks_batch* b) {
   CKB(b, cudaGetLastError());
   lks_status st;
   if ((st = materials(b)) != LKS_OK) return st;
-  // tile shape (tile_config = -1): least forward + adjoint time per step
-  int best = b->opt.tile_config;
+  // A gradient runs two forward steps (march, recompute) and one adjoint step per
+  // level.  tune_us[c]: that per-level time of tile shape c with its TMA forward;
+  // tune_col_us: a forward step of the warp-column kernel.  The shape and forward
+  // kernel with the least per-level time win (within what the options fix).
+  const int shape_given = b->opt.tile_config;
+  float adj_us[kNCfg] = {};
   for (int c = 0; c < kNCfg; ++c) {
-    if (b->opt.tile_config >= 0 && c != b->opt.tile_config) continue;
+    if (shape_given >= 0 && c != shape_given) continue;
     float fu = 0.f, au = 0.f;
     if ((st = time_cfg(b, c, false, 8, &fu, &au)) != LKS_OK) return st;
     b->tune_fwd_us[c] = fu;
-    b->tune_us[c] = fu + au;
-    if (best < 0 || b->tune_us[c] < b->tune_us[best]) best = c;
+    adj_us[c] = au;
+    b->tune_us[c] = 2.f * fu + au;
   }
-  b->cfg = best;
-  // forward kernel (fwd_column = -1): the warp-column kernel when it beats the TMA
-  // forward of that shape
-  b->fwd_col = false;
+  b->tune_col_us = 0.f;
   if (b->opt.fwd_column != 0) {
     float fu = 0.f, au = 0.f;
-    if ((st = time_cfg(b, best, true, 8, &fu, &au)) != LKS_OK) return st;
+    if ((st = time_cfg(b, shape_given >= 0 ? shape_given : 0, true, 8, &fu, &au)) != LKS_OK) return st;
     b->tune_col_us = fu;
-    b->fwd_col = b->opt.fwd_column == 1 || fu < b->tune_fwd_us[best];
   }
+  int best = -1;
+  bool best_col = false;
+  float best_us = 0.f;
+  for (int c = 0; c < kNCfg; ++c) {
+    if (shape_given >= 0 && c != shape_given) continue;
+    for (int col = 0; col < 2; ++col) {
+      if ((col == 1 && b->opt.fwd_column == 0) || (col == 0 && b->opt.fwd_column == 1)) continue;
+      const float us = adj_us[c] + 2.f * (col ? b->tune_col_us : b->tune_fwd_us[c]);
+      if (best < 0 || us < best_us) {
+        best = c;
+        best_col = col == 1;
+        best_us = us;
+      }
+    }
+  }
+  b->cfg = best;
+  b->fwd_col = best_col;
   int dev_status = 0;
   CKB(b, cudaMemcpy(&dev_status, dstatus(b), sizeof(int), cudaMemcpyDeviceToHost));
   if (dev_status != 0) return bfail(b, (lks_status)dev_status, "device status raised while autotuning");

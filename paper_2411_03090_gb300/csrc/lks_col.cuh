@@ -101,8 +101,10 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     fast = x0 >= 2 && x0 + C2_W + 2 <= g0.nx && y0 >= 2 && y0 + G2::H + 2 <= g0.ny;
     pitch = (size_t)g0.nx;
   }
-  const Geom& g = *gp;
-  const Coef<float>& c = *cp;
+  // copies held in registers: the kernel's global stores could alias the design
+  // table, so references into it would be re-read inside the march
+  const Geom g = *gp;
+  const Coef<float> c = *cp;
   const int nx = g.nx, ny = g.ny;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
@@ -427,6 +429,13 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
       if (q >= r0 && q < r0 + ACOL_R && q < ny && out_lane) {
         const int sq = brow(q) + bx;
         const bool interior = !EDGE || (i > 0 && q > 0 && i < nx - 1 && q < ny - 1);
+        // gamma and the sensitivity of the node, loaded ahead of the gather
+        const size_t gi = (size_t)q * nx + i;
+        float gm = 0.f, sold = 0.f;
+        if (a.sens && interior) {
+          gm = __ldg(a.gamma + gi);
+          sold = a.sens[gi];
+        }
         float ft[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) ft[k] = X[k];
@@ -441,11 +450,9 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
           m[1] = adj_brinkman(m[1], ju, 0.f, inv);
           m[2] = adj_brinkman(m[2], jv, 0.f, inv);
           if (a.sens) {
-            const size_t gi = (size_t)q * nx + i;
-            const float gm = __ldg(a.gamma + gi);
             float sacc = 0.f;
             if (a.sens_flow) sacc = __fadd_rn(sacc, sens_flow_term(c, gm, uu0, vv0, m[1], m[2]));
-            a.sens[gi] += sacc;
+            a.sens[gi] = sold + sacc;
           }
         } else {
 #pragma unroll

@@ -777,6 +777,14 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
         const int q1 = (oy + 1) * LX1 + (ox + 1);
         const int s2 = (oy + 2) * BW + (ox + TMA_BXPAD);
         const bool interior = !EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1);
+        // the node's gamma and sensitivity, loaded before the gather so that their
+        // latency overlaps it (each node belongs to one tile: no other writer)
+        const size_t gi = gbase + (size_t)j * gpitch + i;
+        float gm = 0.f, sold = 0.f;
+        if (a.sens && interior) {
+          gm = __ldg(a.gamma + gi);
+          sold = a.sens[gi];
+        }
         float ft[9], gt[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) {
@@ -812,8 +820,6 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
           m[1] = adj_brinkman(m[1], ju, cpx, inv);
           m[2] = adj_brinkman(m[2], jv, cpy, inv);
           if (a.sens) {
-            const size_t gi = gbase + (size_t)j * gpitch + i;
-            const float gm = __ldg(a.gamma + gi);
             float sacc = 0.f;
             if (a.sens_flow) sacc = __fadd_rn(sacc, sens_flow_term(c, gm, uu0, vv0, m[1], m[2]));
             if (TH && a.sens_thermal) {
@@ -821,7 +827,7 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
               const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;
               sacc -= dB_of(c, gm) * (dTx * m[7] + dTy * m[8]);
             }
-            a.sens[gi] += sacc;
+            a.sens[gi] = sold + sacc;
           }
         } else {
 #pragma unroll
