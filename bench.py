@@ -286,7 +286,7 @@ def run_batch_study(args):
     gam = [torch.from_numpy(g).to(dev) for g in gam_np]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
-    b = LKSBatch(pbs, snapshot="bf16", device=dev)
+    b = LKSBatch(pbs, snapshot="bf16", device=dev, tile_config=args.tile_config, fwd_column=args.fwd_column)
     create_s = time.perf_counter() - t0
     st = b.query()
     for _ in range(max(args.warmup, 3)):
@@ -400,6 +400,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-override", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--tile-config", type=int, default=-1,
+                    help="config5: TMA tile shape (-1: autotuned at create)")
+    ap.add_argument("--fwd-column", type=int, default=-1,
+                    help="config5: forward kernel (-1: autotuned, 0: TMA-staged, 1: warp-column)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -278,21 +278,33 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
     }
     if (p + 2 <= r0 + R + 1) load_row(A, p + 2);
   };
-  auto march = [&](auto edge_tag) {
-    Row R0, R1, R2;
-    Dst X0, X1, X2;
-    load_row(R0, r0 - 2);
-    load_row(R1, r0 - 1);
-    load_row(R2, r0);
+  Row R0, R1, R2;
+  Dst X0, X1, X2;
+  load_row(R0, r0 - 2);
+  load_row(R1, r0 - 1);
+  load_row(R2, r0);
+  if (fast) {  // unrolled by three rows: the register rings rotate by renaming
 #pragma unroll 1
     for (int p = r0 - 1; p <= r0 + R; p += 3) {
-      step(edge_tag, p, R0, R1, R2, X0, X1, X2);
-      step(edge_tag, p + 1, R1, R2, R0, X1, X2, X0);
-      step(edge_tag, p + 2, R2, R0, R1, X2, X0, X1);
+      step(std::false_type{}, p, R0, R1, R2, X0, X1, X2);
+      step(std::false_type{}, p + 1, R1, R2, R0, X1, X2, X0);
+      step(std::false_type{}, p + 2, R2, R0, R1, X2, X0, X1);
     }
-  };
-  if (fast) march(std::false_type{});
-  else march(std::true_type{});
+  } else {  // edge tiles: one row per iteration and explicit rotation, a third of the
+            // code (batched lattices run edge and interior tiles side by side)
+#pragma unroll 1
+    for (int p = r0 - 1; p <= r0 + R; ++p) {
+      step(std::true_type{}, p, R0, R1, R2, X0, X1, X2);
+      const Row t = R0;
+      R0 = R1;
+      R1 = R2;
+      R2 = t;
+      const Dst u = X0;
+      X0 = X1;
+      X1 = X2;
+      X2 = u;
+    }
+  }
   if (bad) raise_status(a.status, 4);
   if (a.J_partial) {
     const double s = block_sum<COL_NT>(jloc, red);
