@@ -286,7 +286,8 @@ def run_batch_study(args):
     gam = [torch.from_numpy(g).to(dev) for g in gam_np]
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     t0 = time.perf_counter()
-    b = LKSBatch(pbs, snapshot="bf16", device=dev, tile_config=args.tile_config, fwd_column=args.fwd_column)
+    b = LKSBatch(pbs, snapshot="bf16", device=dev, tile_config=args.tile_config, fwd_column=args.fwd_column,
+                 adj_column=args.adj_column)
     create_s = time.perf_counter() - t0
     st = b.query()
     for _ in range(max(args.warmup, 3)):
@@ -370,6 +371,9 @@ def run_batch_study(args):
                    "forward_kernel": "warp-column (60x40 tiles)" if st.fwd_column else "TMA-staged tiles",
                    "autotune_forward_us": {"tma": round(st.tune_fwd_us[st.tile_config], 1),
                                            "column": round(st.tune_col_us, 1)},
+                   "adjoint_kernel": "warp-column (28x32 tiles)" if st.adj_column else "TMA-staged tiles",
+                   "autotune_adjoint_us": {"tma": round(st.tune_us[st.tile_config] - 2 * st.tune_fwd_us[st.tile_config], 1),
+                                           "column": round(st.tune_acol_us, 1)},
                    "checkpoint_every": st.checkpoint_every, "arena": [st.arena_w, st.arena_h],
                    "tiles": st.ntiles, "create_s": create_s},
         "roofline": {"bound": "hbm", "kernel": "whole gradient (graph: fwd_tma/adj_tma BATCH kernels)",
@@ -404,6 +408,8 @@ def main():
                     help="config5: TMA tile shape (-1: autotuned at create)")
     ap.add_argument("--fwd-column", type=int, default=-1,
                     help="config5: forward kernel (-1: autotuned, 0: TMA-staged, 1: warp-column)")
+    ap.add_argument("--adj-column", type=int, default=-1,
+                    help="config5: adjoint kernel (-1: autotuned, 0: TMA-staged, 1: warp-column)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

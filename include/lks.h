@@ -270,8 +270,8 @@ lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
  * a single tensor map per field serves every design; a work list names each
  * (design, tile) pair.  The tile shape of the TMA-staged kernels is one of
  * LKS_BATCH_TILE_CONFIGS fixed shapes, picked by timing each on the batch at
- * lks_batch_create (tile_config = -1) or given; the forward may instead run the
- * warp-column kernel (fwd_column), again timed or given.  K = 0 picks the checkpoint spacing that minimises workspace bytes
+ * lks_batch_create (tile_config = -1) or given; the forward and the adjoint may
+ * instead run the warp-column kernels (fwd_column, adj_column), again timed or given.  K = 0 picks the checkpoint spacing that minimises workspace bytes
  * (snapshots + segment buffer), a pure function of the descriptors.
  * --------------------------------------------------------------------------------- */
 #define LKS_BATCH_VERSION 1
@@ -288,7 +288,10 @@ typedef struct {
   int32_t fwd_column;       /* forward kernel: -1 the faster of the two, timed at create; 0 the
                                TMA-staged kernel at tile_config; 1 the warp-column kernel
                                (60 x 40 tiles, two columns per lane)                  */
-  int32_t reserved[6];      /* must be zero */
+  int32_t adj_column;       /* adjoint kernel: -1 the faster of the two, timed at create; 0 the
+                               TMA-staged kernel at tile_config; 1 the warp-column kernel
+                               (28 x 32 tiles)                                        */
+  int32_t reserved[5];      /* must be zero */
 } lks_batch_options;
 
 typedef struct {
@@ -308,8 +311,11 @@ typedef struct {
                                             (march, recompute) + one adjoint step (0: not timed) */
   int32_t fwd_column;       /* 1 when the forward runs the warp-column kernel */
   float tune_fwd_us[LKS_BATCH_TILE_CONFIGS]; /* autotuner: us per forward step of each shape (0: not timed) */
-  float tune_col_us;        /* autotuner: us per forward step of the warp-column kernel (0: not timed);
-                               the pair (shape, forward kernel) of least per-level time is used */
+  float tune_col_us;        /* autotuner: us per forward step of the warp-column kernel (0: not timed) */
+  int32_t adj_column;       /* 1 when the adjoint runs the warp-column kernel */
+  float tune_acol_us;       /* autotuner: us per adjoint step of the warp-column kernel (0: not timed);
+                               the (shape, forward kernel, adjoint kernel) of least per-level time
+                               is used */
 } lks_batch_stats;
 
 /* Host only.  n designs described by descs[0..n-1]; opt as above (NULL: K = 0,

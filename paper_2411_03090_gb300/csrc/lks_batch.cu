@@ -202,9 +202,11 @@ __global__ void batch_decode_kernel(const S* __restrict__ y, float* __restrict__
 // Plan: arena packing, work lists, checkpoint spacing and workspace layout
 // ------------------------------------------------------------------------------------
 // Work lists 0 .. kNCfg-1 belong to the tile shapes of the TMA-staged kernels, list
-// kColList to the warp-column forward (60 x 40 tiles).
+// kColList to the warp-column forward (60 x 40 tiles), kAdjColList to the
+// warp-column adjoint (28 x 32 tiles).
 constexpr int kColList = kNCfg;
-constexpr int kNLists = kNCfg + 1;
+constexpr int kAdjColList = kNCfg + 1;
+constexpr int kNLists = kNCfg + 2;
 struct BLayout {
   size_t designs = 0, work[kNLists] = {}, rng[kNLists] = {}, uin = 0, emap = 0, gptr = 0, dptr = 0;
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, mat = 0, sens = 0, sens64 = 0;
@@ -267,6 +269,7 @@ lks_batch_options default_options() {
   o.tile_config = -1;
   o.use_graph = 1;
   o.fwd_column = -1;
+  o.adj_column = -1;
   return o;
 }
 
@@ -284,7 +287,8 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   if (opt->tile_config < -1 || opt->tile_config >= kNCfg) return bad("bad tile_config");
   if (opt->use_graph != 0 && opt->use_graph != 1) return bad("use_graph must be 0 or 1");
   if (opt->fwd_column < -1 || opt->fwd_column > 1) return bad("fwd_column must be -1, 0 or 1");
-  for (int q = 0; q < 6; ++q)
+  if (opt->adj_column < -1 || opt->adj_column > 1) return bad("adj_column must be -1, 0 or 1");
+  for (int q = 0; q < 5; ++q)
     if (opt->reserved[q] != 0) return bad("reserved option fields must be zero");
   P->n = n;
   P->n_steps = descs[0].n_steps;
@@ -323,7 +327,8 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   if (P->A > ((size_t)1 << 31)) return bad("arena larger than 2^31 nodes");
   // work lists, design by design, row-major tiles
   for (int c = 0; c < kNLists; ++c) {
-    const int TXc = c < kNCfg ? kShape[c].tx : C2_W, TYc = c < kNCfg ? kShape[c].ty : Col2Geo<C2_R>::H;
+    const int TXc = c < kNCfg ? kShape[c].tx : c == kColList ? C2_W : COL_W;
+    const int TYc = c < kNCfg ? kShape[c].ty : c == kColList ? Col2Geo<C2_R>::H : ACOL_H;
     P->work[c].clear();
     P->rng[c].assign(2 * n, 0);
     for (int d = 0; d < n; ++d) {
@@ -402,13 +407,14 @@ struct lks_batch {
   int device = 0, sms = 0;
   int cfg = 0;
   bool fwd_col = false;  // forward on the warp-column kernel (work list kColList)
+  bool adj_col = false;  // adjoint on the warp-column kernel (work list kAdjColList)
   int grid_fwd[kNCfg] = {}, grid_adj[kNCfg] = {};
   int cur = 0, acur = 0;
   std::unordered_map<uint64_t, CUtensorMap> tmaps;
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   int64_t launches = 0, launches_per_grad = 0, gradients = 0;
-  float tune_us[kNCfg] = {}, tune_fwd_us[kNCfg] = {}, tune_col_us = 0.f;
+  float tune_us[kNCfg] = {}, tune_fwd_us[kNCfg] = {}, tune_col_us = 0.f, tune_acol_us = 0.f;
   std::string err;
 };
 
@@ -592,7 +598,40 @@ lks_status fwd_step(lks_batch* b, int t_new, bool jacc, float* tu, float* tv) {
     default: return fwd_step_c<3>(b, t_new, jacc, tu, tv);
   }
 }
+// One adjoint step of every design on the warp-column kernel (one CTA per entry of
+// work list kAdjColList).
+lks_status adj_col_step(lks_batch* b, const float* u1, const float* v1, const float* u0, const float* v0,
+                        int sens_flow) {
+  constexpr int NF = acol_nf(false);
+  const int src = b->acur, dst = 1 - b->acur;
+  TmaMaps<NF> maps;
+  lks_status st;
+  const float* mat = af(b, b->P.L.mat, 0);
+  const float* fsrc[NF] = {adp(b, src, 0), adp(b, src, 1), adp(b, src, 2), adp(b, src, 3), adp(b, src, 4),
+                           adp(b, src, 5), u1, v1, u0, v0, mat + b->P.A, mat};  // ..., alpha, 1/(1+alpha)
+  for (int f = 0; f < NF; ++f)
+    if ((st = arena_map(b, fsrc[f], COL_BW, ACOL_BH, &maps.m[f])) != LKS_OK) return st;
+  AdjColArgs a;
+  std::memset(&a, 0, sizeof(a));
+  for (int q = 0; q < 6; ++q) a.m0[q] = adp(b, dst, q);
+  a.gamma = af(b, b->P.L.gamma);
+  a.emap = reinterpret_cast<const float*>(b->ws + b->P.L.emap);
+  a.sens = af(b, b->P.L.sens);
+  a.sens_flow = sens_flow;
+  a.status = dstatus(b);
+  a.work = reinterpret_cast<const BatchTile*>(b->ws + b->P.L.work[kAdjColList]);
+  a.designs = ddesigns(b);
+  a.pitch = b->P.W;
+  adj_col_kernel<false, true><<<(int)b->P.work[kAdjColList].size(), COL_NT, acol_smem_bytes(false), b->stream>>>(
+      maps, a, Geom{}, Coef<float>{});
+  CKB(b, cudaGetLastError());
+  b->acur = dst;
+  b->launches++;
+  return LKS_OK;
+}
+
 lks_status adj_step(lks_batch* b, const float* u1, const float* v1, const float* u0, const float* v0, int sf) {
+  if (b->adj_col) return adj_col_step(b, u1, v1, u0, v0, sf);
   switch (b->cfg) {
     case 0: return adj_step_c<0>(b, u1, v1, u0, v0, sf);
     case 1: return adj_step_c<1>(b, u1, v1, u0, v0, sf);
@@ -739,10 +778,12 @@ lks_status enqueue_gradient(lks_batch* b) {
 }
 
 // Times `steps` forward and adjoint steps of tile shape c on a uniform design (the
-// forward on the warp-column kernel when col): us per forward and per adjoint step.
-lks_status time_cfg(lks_batch* b, int c, bool col, int steps, float* fwd_us, float* adj_us) {
+// forward / adjoint on the warp-column kernels when col / acol): us per forward and
+// per adjoint step.
+lks_status time_cfg(lks_batch* b, int c, bool col, bool acol, int steps, float* fwd_us, float* adj_us) {
   b->cfg = c;
   b->fwd_col = col;
+  b->adj_col = acol;
   const size_t fb = b->P.A * 4;
   CKB(b, cudaMemsetAsync(b->ws + b->P.L.stA, 0, fb * 3, b->stream));
   CKB(b, cudaMemsetAsync(b->ws + b->P.L.adA, 0, fb * 6, b->stream));
@@ -798,42 +839,48 @@ lks_status autotune(lks_batch* b) {
   lks_status st;
   if ((st = materials(b)) != LKS_OK) return st;
   // A gradient runs two forward steps (march, recompute) and one adjoint step per
-  // level.  tune_us[c]: that per-level time of tile shape c with its TMA forward;
-  // tune_col_us: a forward step of the warp-column kernel.  The shape and forward
-  // kernel with the least per-level time win (within what the options fix).
+  // level.  tune_us[c]: that per-level time of tile shape c with its TMA kernels;
+  // tune_col_us / tune_acol_us: a forward / adjoint step of the warp-column kernels.
+  // The tile shape and the forward and adjoint kernels with the least per-level
+  // time win (within what the options fix).
   const int shape_given = b->opt.tile_config;
   float adj_us[kNCfg] = {};
   for (int c = 0; c < kNCfg; ++c) {
     if (shape_given >= 0 && c != shape_given) continue;
     float fu = 0.f, au = 0.f;
-    if ((st = time_cfg(b, c, false, 8, &fu, &au)) != LKS_OK) return st;
+    if ((st = time_cfg(b, c, false, false, 8, &fu, &au)) != LKS_OK) return st;
     b->tune_fwd_us[c] = fu;
     adj_us[c] = au;
     b->tune_us[c] = 2.f * fu + au;
   }
-  b->tune_col_us = 0.f;
-  if (b->opt.fwd_column != 0) {
+  b->tune_col_us = b->tune_acol_us = 0.f;
+  if (b->opt.fwd_column != 0 || b->opt.adj_column != 0) {
     float fu = 0.f, au = 0.f;
-    if ((st = time_cfg(b, shape_given >= 0 ? shape_given : 0, true, 8, &fu, &au)) != LKS_OK) return st;
-    b->tune_col_us = fu;
+    if ((st = time_cfg(b, shape_given >= 0 ? shape_given : 0, true, true, 8, &fu, &au)) != LKS_OK) return st;
+    if (b->opt.fwd_column != 0) b->tune_col_us = fu;
+    if (b->opt.adj_column != 0) b->tune_acol_us = au;
   }
+  auto allowed = [](int option, int col) { return option < 0 || option == col; };
   int best = -1;
-  bool best_col = false;
+  bool best_col = false, best_acol = false;
   float best_us = 0.f;
   for (int c = 0; c < kNCfg; ++c) {
     if (shape_given >= 0 && c != shape_given) continue;
-    for (int col = 0; col < 2; ++col) {
-      if ((col == 1 && b->opt.fwd_column == 0) || (col == 0 && b->opt.fwd_column == 1)) continue;
-      const float us = adj_us[c] + 2.f * (col ? b->tune_col_us : b->tune_fwd_us[c]);
-      if (best < 0 || us < best_us) {
-        best = c;
-        best_col = col == 1;
-        best_us = us;
+    for (int col = 0; col < 2; ++col)
+      for (int acol = 0; acol < 2; ++acol) {
+        if (!allowed(b->opt.fwd_column, col) || !allowed(b->opt.adj_column, acol)) continue;
+        const float us = 2.f * (col ? b->tune_col_us : b->tune_fwd_us[c]) + (acol ? b->tune_acol_us : adj_us[c]);
+        if (best < 0 || us < best_us) {
+          best = c;
+          best_col = col == 1;
+          best_acol = acol == 1;
+          best_us = us;
+        }
       }
-    }
   }
   b->cfg = best;
   b->fwd_col = best_col;
+  b->adj_col = best_acol;
   int dev_status = 0;
   CKB(b, cudaMemcpy(&dev_status, dstatus(b), sizeof(int), cudaMemcpyDeviceToHost));
   if (dev_status != 0) return bfail(b, (lks_status)dev_status, "device status raised while autotuning");
@@ -955,13 +1002,16 @@ lks_status lks_batch_create(int32_t n, const lks_problem_desc* descs, const lks_
       (st = setup_cfg<3>(b)) != LKS_OK)
     return fin(st);
   if (cudaFuncSetAttribute(fwd_col2_kernel<C2_R, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                           (int)Col2Geo<C2_R>::smem) != cudaSuccess)
-    return fin(bfail(b, LKS_ERR_CUDA, "shared-memory attribute of the column forward"));
-  if (b->opt.tile_config < 0 || b->opt.fwd_column < 0) {  // time what is not given
+                           (int)Col2Geo<C2_R>::smem) != cudaSuccess ||
+      cudaFuncSetAttribute(adj_col_kernel<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                           (int)acol_smem_bytes(false)) != cudaSuccess)
+    return fin(bfail(b, LKS_ERR_CUDA, "shared-memory attributes of the column kernels"));
+  if (b->opt.tile_config < 0 || b->opt.fwd_column < 0 || b->opt.adj_column < 0) {  // time what is not given
     if ((st = autotune(b)) != LKS_OK) return fin(st);
   } else {
     b->cfg = b->opt.tile_config;
     b->fwd_col = b->opt.fwd_column == 1;
+    b->adj_col = b->opt.adj_column == 1;
   }
   if (b->opt.use_graph && (st = capture_graph(b)) != LKS_OK) return fin(st);
   if (cudaStreamSynchronize(b->stream) != cudaSuccess) return fin(bfail(b, LKS_ERR_CUDA, "create: sync failed"));
@@ -1011,6 +1061,8 @@ lks_status lks_batch_query(lks_batch* b, lks_batch_stats* out) {
   out->fwd_column = b->fwd_col ? 1 : 0;
   for (int c = 0; c < kNCfg; ++c) out->tune_fwd_us[c] = b->tune_fwd_us[c];
   out->tune_col_us = b->tune_col_us;
+  out->adj_column = b->adj_col ? 1 : 0;
+  out->tune_acol_us = b->tune_acol_us;
   return LKS_OK;
 }
 

@@ -622,6 +622,7 @@ lks_status launch_adj_col(lks_handle* h, const float* u1, const float* v1, const
     if ((st = field_map(h, fs[q], COL_BW, ACOL_BH, &maps.m[f++])) != LKS_OK) return st;
   }
   AdjColArgs a;
+  std::memset(&a, 0, sizeof(a));
   for (int q = 0; q < 6; ++q) a.m0[q] = adj_ptr<float>(h, dst, q);
   a.gamma = fld<float>(h, h->L.gamma, 0);
   a.emap = reinterpret_cast<const float*>(h->ws + h->L.emap);
@@ -632,11 +633,12 @@ lks_status launch_adj_col(lks_handle* h, const float* u1, const float* v1, const
   const int grid = a.ntx * ((d.ny + ACOL_H - 1) / ACOL_H);
   static bool attr_set = false;  // per process: the attribute belongs to the kernel
   if (!attr_set) {
-    CKH(h, cudaFuncSetAttribute(adj_col_kernel<SAME>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    CKH(h, cudaFuncSetAttribute(adj_col_kernel<SAME, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)acol_smem_bytes(SAME)));
     attr_set = true;
   }
-  adj_col_kernel<SAME><<<grid, COL_NT, acol_smem_bytes(SAME), h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
+  adj_col_kernel<SAME, false>
+      <<<grid, COL_NT, acol_smem_bytes(SAME), h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
   h->acur = dst;
   h->adj_steps++;

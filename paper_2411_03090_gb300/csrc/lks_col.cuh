@@ -333,19 +333,24 @@ __host__ __device__ constexpr size_t acol_smem_bytes(bool same) {
 struct AdjColArgs {
   float* m0[6];       // adjoint moments at level t
   const float* gamma;
-  const float* emap;  // 9 classes x 6 x 10
+  const float* emap;  // 9 classes x 6 x 10 (batched form: per design, 540 floats each)
   float* sens;        // optional sensitivity accumulator
   int sens_flow;
   int* status;
-  int ntx;
+  int ntx;            // tiles along x (single lattice)
+  // batched form: one work-list entry per CTA, per-design tables, arena row pitch
+  const BatchTile* work;
+  const BatchDesign* designs;
+  int pitch;
 };
 
 // Staged fields: rho~, u~x, u~y, s~xx, s~xy, s~yy, u1, v1, [u0, v0], alpha, 1/(1+alpha).
-template <bool SAME>
+// BATCH: the designs of a batch packed in one arena, as for fwd_col2_kernel.
+template <bool SAME, bool BATCH>
 __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__ TmaMaps<acol_nf(SAME)> maps,
                                                          const __grid_constant__ AdjColArgs a,
-                                                         const __grid_constant__ Geom g,
-                                                         const __grid_constant__ Coef<float> c) {
+                                                         const __grid_constant__ Geom g0,
+                                                         const __grid_constant__ Coef<float> c0) {
   constexpr int NF = acol_nf(SAME);
   constexpr int FU0 = SAME ? 6 : 8, FAL = SAME ? 8 : 10, FBI = FAL + 1;
   constexpr int BW = COL_BW;
@@ -354,14 +359,40 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
   uint64_t* bar = reinterpret_cast<uint64_t*>(box + NF * ACOL_FS);
   if (timed_out_before(a.status)) return;
   if (!tma_layout_ok(box, bar, a.status)) return;
+  int x0, y0, ax = 0, ay = 0;
+  bool fast;
+  const Geom* gp = &g0;
+  const Coef<float>* cp = &c0;
+  const float* emap = a.emap;
+  size_t pitch;
+  if constexpr (BATCH) {
+    const BatchTile w = a.work[blockIdx.x];
+    const BatchDesign& bd = a.designs[w.d];
+    gp = &bd.g;
+    cp = &bd.c;
+    x0 = w.x0;
+    y0 = w.y0;
+    ax = bd.ax;
+    ay = bd.ay;
+    fast = w.interior != 0;
+    emap += (size_t)w.d * 540;
+    pitch = (size_t)a.pitch;
+  } else {
+    x0 = (blockIdx.x % a.ntx) * COL_W;
+    y0 = (blockIdx.x / a.ntx) * ACOL_H;
+    fast = x0 >= 2 && x0 + COL_W + 2 <= g0.nx && y0 >= 2 && y0 + ACOL_H + 2 <= g0.ny;
+    pitch = (size_t)g0.nx;
+  }
+  const Geom g = *gp;  // register copies (see fwd_col2_kernel)
+  const Coef<float> c = *cp;
   const int nx = g.nx, ny = g.ny;
-  const int x0 = (blockIdx.x % a.ntx) * COL_W, y0 = (blockIdx.x / a.ntx) * ACOL_H;
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
     fence_proxy_async();
     mbar_expect_tx(bar, NF * ACOL_BOX * 4);
-    for (int f = 0; f < NF; ++f) tma_load_2d(box + f * ACOL_FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+    for (int f = 0; f < NF; ++f)
+      tma_load_2d(box + f * ACOL_FS, &maps.m[f], ax + x0 - TMA_BXPAD, ay + y0 - 2, bar);
   }
   __syncthreads();
   if (!mbar_wait(bar, 0)) {
@@ -386,7 +417,6 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
   const int bx = lane + 2;
   const int r0 = y0 + warp * ACOL_R;
   const bool out_lane = lane >= 2 && lane < 2 + COL_W && i < nx;
-  const bool fast = x0 >= 2 && x0 + COL_W + 2 <= nx && y0 >= 2 && y0 + ACOL_H + 2 <= ny;
   auto brow = [&](int y) { return (y - y0 + 2) * BW; };
 
   auto march = [&](auto edge_tag) {
@@ -442,7 +472,7 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
         const int sq = brow(q) + bx;
         const bool interior = !EDGE || (i > 0 && q > 0 && i < nx - 1 && q < ny - 1);
         // gamma and the sensitivity of the node, loaded ahead of the gather
-        const size_t gi = (size_t)q * nx + i;
+        const size_t gi = (size_t)(ay + q) * pitch + (size_t)(ax + i);
         float gm = 0.f, sold = 0.f;
         if (a.sens && interior) {
           gm = __ldg(a.gamma + gi);
@@ -472,14 +502,13 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
             const int gi = i + cxk(k), gj = q + cyk(k);
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = 0.f;
           }
-          const float* M = a.emap + edge_class(g, i, q) * 60;
+          const float* M = emap + edge_class(g, i, q) * 60;
 #pragma unroll
           for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, 0.f);
         }
         (void)sq;
-        const size_t o = (size_t)q * nx + i;
 #pragma unroll
-        for (int f = 0; f < 6; ++f) a.m0[f][o] = m[f];
+        for (int f = 0; f < 6; ++f) a.m0[f][gi] = m[f];
         if (!(m[1] * m[1] + m[2] * m[2] < 1e30f)) raise_status(a.status, 4);
       }
 #pragma unroll

@@ -73,7 +73,7 @@ TILE_SHAPES = ((64, 8), (32, 16), (128, 4), (64, 16))
 class BatchOptions(C.Structure):
     _fields_ = [("version", C.c_int32), ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
                 ("tile_config", C.c_int32), ("use_graph", C.c_int32), ("fwd_column", C.c_int32),
-                ("reserved", C.c_int32 * 6)]
+                ("adj_column", C.c_int32), ("reserved", C.c_int32 * 5)]
 
 
 class BatchStats(C.Structure):
@@ -83,7 +83,7 @@ class BatchStats(C.Structure):
                 ("ntiles", C.c_int64), ("workspace_bytes", C.c_int64), ("kernel_launches", C.c_int64),
                 ("gradients", C.c_int64), ("tune_us", C.c_float * LKS_BATCH_TILE_CONFIGS),
                 ("fwd_column", C.c_int32), ("tune_fwd_us", C.c_float * LKS_BATCH_TILE_CONFIGS),
-                ("tune_col_us", C.c_float)]
+                ("tune_col_us", C.c_float), ("adj_column", C.c_int32), ("tune_acol_us", C.c_float)]
 
 
 # Every symbol the header declares (checked by the CPU test-suite).
@@ -334,7 +334,7 @@ class LKS:
 # Batched form
 # ---------------------------------------------------------------------------------
 def batch_options(checkpoint_every: int = 0, snapshot: str = "bf16", tile_config: int = -1,
-                  use_graph: bool = True, fwd_column: int = -1) -> BatchOptions:
+                  use_graph: bool = True, fwd_column: int = -1, adj_column: int = -1) -> BatchOptions:
     o = BatchOptions()
     o.version = LKS_BATCH_VERSION
     o.checkpoint_every = int(checkpoint_every)
@@ -342,6 +342,7 @@ def batch_options(checkpoint_every: int = 0, snapshot: str = "bf16", tile_config
     o.tile_config = int(tile_config)
     o.use_graph = 1 if use_graph else 0
     o.fwd_column = int(fwd_column)
+    o.adj_column = int(adj_column)
     return o
 
 
@@ -368,14 +369,14 @@ class LKSBatch:
 
     def __init__(self, problems, checkpoint_every: int = 0, snapshot: str = "bf16", tile_config: int = -1,
                  use_graph: bool = True, device: Optional[torch.device] = None,
-                 stream: Optional[torch.cuda.Stream] = None, fwd_column: int = -1):
+                 stream: Optional[torch.cuda.Stream] = None, fwd_column: int = -1, adj_column: int = -1):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.problems = list(problems)
         self.n = len(self.problems)
         self.shapes = [(int(p.ny), int(p.nx)) for p in self.problems]
-        self.opt = batch_options(checkpoint_every, snapshot, tile_config, use_graph, fwd_column)
+        self.opt = batch_options(checkpoint_every, snapshot, tile_config, use_graph, fwd_column, adj_column)
         self.descs = batch_descs(self.problems)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         with torch.cuda.device(self.device):

@@ -134,7 +134,7 @@ def test_batch_workspace_validation():
         mutate(d)
         assert _bsize(d, None)[0] == 1
     for field, val in (("version", 7), ("tile_config", 4), ("snapshot_type", 3), ("use_graph", 2),
-                       ("checkpoint_every", -1), ("fwd_column", 2), ("fwd_column", -2)):
+                       ("checkpoint_every", -1), ("fwd_column", 2), ("fwd_column", -2), ("adj_column", 2)):
         o = lks.batch_options()
         setattr(o, field, val)
         assert _bsize(ok, o)[0] == 1, field

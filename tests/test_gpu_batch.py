@@ -105,17 +105,18 @@ def test_batch_tile_shapes_agree():
             assert abs(J[k] - J0[k]) <= 1e-12 * abs(J0[k])
 
 
-def test_batch_column_forward_equals_tma_forward():
-    """The warp-column forward (60 x 40 tiles, two columns per lane) computes each
-    node with the arithmetic of the TMA-staged forward, also for an odd nx (the last
-    lane pair half outside its design): identical gradients; J differs only in the
-    order of its FP64 partial sums.  The odd design also matches the oracle."""
+def test_batch_column_kernels_equal_tma_kernels():
+    """The warp-column forward (60 x 40 tiles, two columns per lane) and adjoint
+    (28 x 32 tiles) compute each node with the arithmetic of the TMA-staged kernels,
+    also for an odd nx (the forward's last lane pair half outside its design):
+    identical gradients; J differs only in the order of its FP64 partial sums.  The
+    odd designs also match the oracle."""
     kw = dict(steady=False, n_steps=60, n_adj=60, pulse_mean=0.75, pulse_amp=0.25, pulse_period=40.0,
               sigma=2.0, strip=2)
     pbs = designs() + [inputs.channel(45, 30, Re=15.0, seed=35, **kw), inputs.channel(131, 85, Re=30.0, seed=36, **kw)]
-    Jt, gt, st = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=0)
-    Jc, gc, sc = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=1)
-    assert st.fwd_column == 0 and sc.fwd_column == 1
+    Jt, gt, st = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=0, adj_column=0)
+    Jc, gc, sc = run(pbs, checkpoint_every=7, snapshot="f32", tile_config=0, fwd_column=1, adj_column=1)
+    assert st.fwd_column == 0 and sc.fwd_column == 1 and st.adj_column == 0 and sc.adj_column == 1
     for k in range(len(pbs)):
         np.testing.assert_array_equal(gc[k], gt[k])
         assert abs(Jc[k] - Jt[k]) <= 1e-12 * abs(Jt[k]), k
@@ -142,12 +143,14 @@ def test_batch_single_segment_and_autotune():
     ref = O.unsteady_gradient(pbs[0], pbs[0].gamma())
     J, grads, st = run(pbs, checkpoint_every=100, snapshot="f32")
     assert st.n_ckpt == 1 and st.checkpoint_every == 25
-    assert all(t > 0 for t in st.tune_us) and st.tune_col_us > 0
-    # per level: two forward steps and one adjoint step, the forward on the faster kernel
+    assert all(t > 0 for t in st.tune_us) and st.tune_col_us > 0 and st.tune_acol_us > 0
+    # per level: two forward steps and one adjoint step, each on its faster kernel
     fwd, lvl = np.array(list(st.tune_fwd_us)), np.array(list(st.tune_us))
-    cost = lvl - 2 * fwd + 2 * np.minimum(fwd, st.tune_col_us)
+    adj = lvl - 2 * fwd
+    cost = 2 * np.minimum(fwd, st.tune_col_us) + np.minimum(adj, st.tune_acol_us)
     assert st.tile_config == int(np.argmin(cost))
     assert st.fwd_column == int(st.tune_col_us < fwd[st.tile_config])
+    assert st.adj_column == int(st.tune_acol_us < adj[st.tile_config])
     assert abs(J[0] - ref["J"]) <= 1e-5 * abs(ref["J"])
     assert rel_l2(grads[0], ref["dJdgamma"]) <= 1e-3
 
