@@ -404,6 +404,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-override", type=int, default=0)
     ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--res-steps", type=int, default=0,
+                    help="resident marches: steps per exchange of tile bands (0: automatic)")
     ap.add_argument("--tile-config", type=int, default=-1,
                     help="config5: TMA tile shape (-1: autotuned at create)")
     ap.add_argument("--fwd-column", type=int, default=-1,
@@ -441,7 +443,7 @@ def main():
         desc += f" (shortened to {args.steps_override}+{args.steps_override} steps)"
     g_np = pb.gamma()
     gamma = torch.from_numpy(g_np).to(dev, torch.float32)
-    s = LKS(pb, real="f32", device=dev)
+    s = LKS(pb, real="f32", device=dev, res_steps=args.res_steps)
     stream = s.stream
     N = pb.n_nodes
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -537,7 +539,9 @@ def main():
         "config": {"workload": desc,
                    "lattice": f"{pb.nx}x{pb.ny}" + (f"x{pb.nz}" if three_d else ""), "forward_steps": pb.n_steps,
                    "adjoint_steps": pb.n_adj, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3},
+                   "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3,
+                   **({"resident_steps_per_exchange": [st.res_steps_fwd, st.res_steps_adj]}
+                      if st.fwd_path == 2 or st.adj_path == 2 else {})},
         "roofline": roofline,
         "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 4 * N,
                 "d2h_bytes_per_step": 4 * N + 8 + 4},
