@@ -326,8 +326,9 @@ constexpr int ACOL_BH = ACOL_H + 4, ACOL_BOX = COL_BW * ACOL_BH;
 constexpr int ACOL_FS = (ACOL_BOX * 4 + 127) / 128 * 128 / 4;
 
 __host__ __device__ constexpr int acol_nf(bool same) { return same ? 10 : 12; }
+// staged fields, alignment slack, the mbarrier, the edge maps (9 classes x 60)
 __host__ __device__ constexpr size_t acol_smem_bytes(bool same) {
-  return (size_t)acol_nf(same) * ACOL_FS * 4 + 128 + 8;
+  return (size_t)acol_nf(same) * ACOL_FS * 4 + 128 + 8 + 540 * 4;
 }
 
 struct AdjColArgs {
@@ -386,6 +387,7 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
   const Geom g = *gp;  // register copies (see fwd_col2_kernel)
   const Coef<float> c = *cp;
   const int nx = g.nx, ny = g.ny;
+  float* sem = reinterpret_cast<float*>(bar + 1);  // edge maps of the tile's lattice (edge tiles)
   if (threadIdx.x == 0) {
     mbar_init(bar, 1);
     fence_mbar_init();
@@ -394,6 +396,8 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
     for (int f = 0; f < NF; ++f)
       tma_load_2d(box + f * ACOL_FS, &maps.m[f], ax + x0 - TMA_BXPAD, ay + y0 - 2, bar);
   }
+  if (!fast)
+    for (int t = threadIdx.x; t < 540; t += COL_NT) sem[t] = __ldg(emap + t);
   __syncthreads();
   if (!mbar_wait(bar, 0)) {
     raise_status(a.status, 6);
@@ -426,7 +430,17 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
     for (int k = 0; k < 9; ++k) X[k] = Y[k] = Z[k] = 0.f;
     float S0m = 0.f, S1m = 0.f, S2m = 0.f;  // strain of the level-t state, rows p-2 (m), p-1 (c), p (p)
     float S0c = 0.f, S1c = 0.f, S2c = 0.f;
+    float gm_c = 0.f, sold_c = 0.f;  // gamma and sensitivity of output row p - 1
     for (int p = r0 - 1; p <= r0 + ACOL_R; ++p) {
+      // gamma and the old sensitivity of output row p, written in the next iteration:
+      // loaded a row ahead so that their latency overlaps a whole row
+      float gm_n = 0.f, sold_n = 0.f;
+      if (a.sens && out_lane && p >= r0 && p < r0 + ACOL_R && p < ny &&
+          (!EDGE || (i > 0 && p > 0 && i < nx - 1 && p < ny - 1))) {
+        const size_t gn = (size_t)(ay + p) * pitch + (size_t)(ax + i);
+        gm_n = __ldg(a.gamma + gn);
+        sold_n = a.sens[gn];
+      }
       const int s2 = brow(p) + bx;
       float Pq[9];
       float S0p = 0.f, S1p = 0.f, S2p = 0.f;
@@ -471,13 +485,8 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
       if (q >= r0 && q < r0 + ACOL_R && q < ny && out_lane) {
         const int sq = brow(q) + bx;
         const bool interior = !EDGE || (i > 0 && q > 0 && i < nx - 1 && q < ny - 1);
-        // gamma and the sensitivity of the node, loaded ahead of the gather
         const size_t gi = (size_t)(ay + q) * pitch + (size_t)(ax + i);
-        float gm = 0.f, sold = 0.f;
-        if (a.sens && interior) {
-          gm = __ldg(a.gamma + gi);
-          sold = a.sens[gi];
-        }
+        const float gm = gm_c, sold = sold_c;
         float ft[9];
 #pragma unroll
         for (int k = 0; k < 9; ++k) ft[k] = X[k];
@@ -502,7 +511,7 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
             const int gi = i + cxk(k), gj = q + cyk(k);
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = 0.f;
           }
-          const float* M = emap + edge_class(g, i, q) * 60;
+          const float* M = sem + edge_class(g, i, q) * 60;
 #pragma unroll
           for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, 0.f);
         }
@@ -519,6 +528,8 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
       }
       S0m = S0c, S1m = S1c, S2m = S2c;
       S0c = S0p, S1c = S1p, S2c = S2p;
+      gm_c = gm_n;
+      sold_c = sold_n;
     }
   };
   if (fast) march(std::false_type{});
