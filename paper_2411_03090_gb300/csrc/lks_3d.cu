@@ -42,6 +42,9 @@ using lks::raise_status;
 using lks::reduce_partials_kernel;
 
 constexpr int TX3 = 32, TY3 = 8, NT3 = TX3 * TY3, ZC3 = 32;
+// Threads of the TMA-staged forward and adjoint: enough for the halo-1 coefficient
+// region (34 x 10) in one pass; the first NT3 of them gather the 32 x 8 outputs.
+constexpr int NTF3 = 352;
 constexpr int HX3 = TX3 + 4, HY3 = TY3 + 4, HA3 = HX3 * HY3;  // plane box with a 2-node halo
 constexpr int PX3 = TX3 + 2, PY3 = TY3 + 2, PA3 = PX3 * PY3;  // plane box with a 1-node halo
 
@@ -60,6 +63,48 @@ __host__ __device__ constexpr int slot3(int k) {
   for (int q = 0; q < k; ++q)
     if (grp3(q) == grp3(k)) ++s;
   return s;
+}
+// First and second nonzero component of link k (-1: none).
+__host__ __device__ constexpr int ax3(int k, int which) {
+  int n = 0;
+  for (int a = 0; a < 3; ++a)
+    if (c3(k, a) != 0) {
+      if (n == which) return a;
+      ++n;
+    }
+  return -1;
+}
+
+// Component A of (x, y, z), chosen at compile time.
+template <int A, typename R>
+__device__ __forceinline__ R pick3(R x, R y, R z) {
+  if constexpr (A == 0) return x;
+  else if constexpr (A == 1) return y;
+  else return z;
+}
+
+// Pushed increment of link K (Eq. feq2 in 3-D, increment form):
+// w_K [(drho - drho(x + c_K)) + e0 + c_K.b + c_K c_K : Q] with b = 3u.  Only the
+// nonzero components of c_K enter (a product with a zero constant is not folded
+// away under IEEE rules).
+template <int K, typename R>
+__device__ __forceinline__ R push_link3(R dr, R dest, R e0, R bx, R by, R bz, R Qxx, R Qyy, R Qzz, R Qxy, R Qxz,
+                                        R Qyz) {
+  constexpr int a0 = ax3(K, 0), a1 = ax3(K, 1);
+  const R base = (dr - dest) + e0;
+  if constexpr (a0 < 0) {
+    return R(w3d(K)) * base;
+  } else if constexpr (a1 < 0) {
+    const R ba = pick3<a0>(bx, by, bz);
+    const R cb = c3(K, a0) > 0 ? ba : -ba;
+    return R(w3d(K)) * ((base + cb) + pick3<a0>(Qxx, Qyy, Qzz));
+  } else {
+    const R ba = pick3<a0>(bx, by, bz), bb = pick3<a1>(bx, by, bz);
+    const R cb = (c3(K, a0) > 0 ? ba : -ba) + (c3(K, a1) > 0 ? bb : -bb);
+    const R qab = pick3<3 - a0 - a1>(Qyz, Qxz, Qxy);  // the entry of the two axes a0, a1
+    const R qo = c3(K, a0) * c3(K, a1) > 0 ? qab : -qab;
+    return R(w3d(K)) * ((base + cb) + ((pick3<a0>(Qxx, Qyy, Qzz) + pick3<a1>(Qxx, Qyy, Qzz)) + qo));
+  }
 }
 
 // Compile-time loop over the lattice links: every link index, velocity, weight and
@@ -160,7 +205,9 @@ __global__ void __launch_bounds__(NT3) fwd3_kernel(const __grid_constant__ Fwd3A
   auto load = [&](int p) { load_plane<R, 4, 2>(stg + mod5(p) * 4 * HA3, a.in, g, x0, y0, p); };
 
   // Pushed populations of plane p on the halo-1 ring, for the link groups asked.
-  auto push = [&](int p, bool want_up, bool want_mid, bool want_dn) {
+  auto push = [&](int p, auto up_tag, auto mid_tag, auto dn_tag) {
+    constexpr bool want_up = decltype(up_tag)::value, want_mid = decltype(mid_tag)::value,
+                   want_dn = decltype(dn_tag)::value;
     if (p < 0 || p >= nz) return;
     for (int q = threadIdx.x; q < PA3; q += NT3) {
       const int ly = q / PX3, lx = q - ly * PX3;
@@ -197,18 +244,18 @@ __global__ void __launch_bounds__(NT3) fwd3_kernel(const __grid_constant__ Fwd3A
       const R Qxz = R(9) * uu[0] * uu[2] + R(2) * c.A * (gr[0][2] + gr[2][0]);
       const R Qyz = R(9) * uu[1] * uu[2] + R(2) * c.A * (gr[1][2] + gr[2][1]);
       const R dr = fld(0, 0)[0];
+      R* const midq = mid + mod2(p) * 9 * PA3 + q;
+      R* const upq = up + mod3(p) * 5 * PA3 + q;
+      R* const dnq = dn + q;
       static_for<0, 19>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         constexpr int gk = grp3(k), sl = slot3(k);
         constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
-        if ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
-        const R dest = fld(0, cz)[cy * HX3 + cx];
-        const R qk = R(cx * cx) * Qxx + R(cy * cy) * Qyy + R(cz * cz) * Qzz + R(cx * cy) * Qxy + R(cx * cz) * Qxz +
-                     R(cy * cz) * Qyz;
-        const R val = R(w3d(k)) * (((dr - dest) + e0) + (R(cx) * bx + R(cy) * by + R(cz) * bz) + qk);
-        if (gk == 0) mid[(mod2(p) * 9 + sl) * PA3 + q] = val;
-        else if (gk == 1) up[(mod3(p) * 5 + sl) * PA3 + q] = val;
-        else dn[sl * PA3 + q] = val;
+        if constexpr ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
+        const R val = push_link3<k>(dr, fld(0, cz)[cy * HX3 + cx], e0, bx, by, bz, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz);
+        if constexpr (gk == 0) midq[sl * PA3] = val;
+        else if constexpr (gk == 1) upq[sl * PA3] = val;
+        else dnq[sl * PA3] = val;
       });
     }
   };
@@ -286,13 +333,15 @@ __global__ void __launch_bounds__(NT3) fwd3_kernel(const __grid_constant__ Fwd3A
 
   for (int p = z0 - 2; p <= z0 + 2; ++p) load(p);
   __syncthreads();
-  push(z0 - 1, true, false, false);
-  push(z0, true, true, false);
+  using yes = std::true_type;
+  using no = std::false_type;
+  push(z0 - 1, yes{}, no{}, no{});
+  push(z0, yes{}, yes{}, no{});
   __syncthreads();
   for (int z = z0; z < z1; ++z) {
     load(z + 3);
     __syncthreads();
-    push(z + 1, true, true, true);
+    push(z + 1, yes{}, yes{}, yes{});
     __syncthreads();
     gather(z);
     __syncthreads();
@@ -496,7 +545,7 @@ struct Fwd3TArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps3F maps, const __grid_constant__ Fwd3TArgs a,
+__global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ Maps3F maps, const __grid_constant__ Fwd3TArgs a,
                                                     Geom3 g, Coef3<float> c) {
   using R = float;
   extern __shared__ unsigned char smem_raw3[];
@@ -541,11 +590,13 @@ __global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps
   }
   auto plane = [&](int f, int p) -> const R* { return ring + (slot(p) * NFF3 + f) * BOX3; };
 
-  auto push = [&](int p, bool want_up, bool want_mid, bool want_dn, auto fast_tag) {
+  auto push = [&](int p, auto up_tag, auto mid_tag, auto dn_tag, auto fast_tag) {
     constexpr bool FAST = decltype(fast_tag)::value;
+    constexpr bool want_up = decltype(up_tag)::value, want_mid = decltype(mid_tag)::value,
+                   want_dn = decltype(dn_tag)::value;
     if (p < 0 || p >= nz) return;
     const bool zf = p == 0 || p == nz - 1;
-    for (int q = threadIdx.x; q < PA3; q += NT3) {
+    for (int q = threadIdx.x; q < PA3; q += NTF3) {
       const int ly = q / PX3, lx = q - ly * PX3;
       const int i = x0 - 1 + lx, j = y0 - 1 + ly;
       if (!FAST && (i < 0 || i >= nx || j < 0 || j >= ny)) continue;
@@ -588,24 +639,26 @@ __global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps
       const R* dm = plane(0, p - 1) + boff;
       const R* dp = plane(0, p + 1) + boff;
       const R dr = d0[0];
+      R* const midq = mid + mod2(p) * 9 * PA3 + q;
+      R* const upq = up + mod3(p) * 5 * PA3 + q;
+      R* const dnq = dn + q;
       static_for<0, 19>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         constexpr int gk = grp3(k), sl = slot3(k);
         constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
-        if ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
-        const R dest = (cz == 0 ? d0 : (cz > 0 ? dp : dm))[cy * BW3 + cx];
-        const R qk = R(cx * cx) * Qxx + R(cy * cy) * Qyy + R(cz * cz) * Qzz + R(cx * cy) * Qxy + R(cx * cz) * Qxz +
-                     R(cy * cz) * Qyz;
-        const R val = R(w3d(k)) * (((dr - dest) + e0) + (R(cx) * bx + R(cy) * by + R(cz) * bz) + qk);
-        if (gk == 0) mid[(mod2(p) * 9 + sl) * PA3 + q] = val;
-        else if (gk == 1) up[(mod3(p) * 5 + sl) * PA3 + q] = val;
-        else dn[sl * PA3 + q] = val;
+        if constexpr ((gk == 0 && !want_mid) || (gk == 1 && !want_up) || (gk == 2 && !want_dn)) return;
+        const R val = push_link3<k>(dr, (cz == 0 ? d0 : (cz > 0 ? dp : dm))[cy * BW3 + cx], e0, bx, by, bz, Qxx, Qyy,
+                                    Qzz, Qxy, Qxz, Qyz);
+        if constexpr (gk == 0) midq[sl * PA3] = val;
+        else if constexpr (gk == 1) upq[sl * PA3] = val;
+        else dnq[sl * PA3] = val;
       });
     }
   };
 
   auto gather = [&](int z, auto fast_tag) {
     constexpr bool FAST = decltype(fast_tag)::value;
+    if (threadIdx.x >= NT3) return;
     const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
     const int i = x0 + tx, j = y0 + ty;
     if (!FAST && (i >= nx || j >= ny)) return;
@@ -678,8 +731,10 @@ __global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps
   auto run = [&](auto fast_tag) {
     for (int p = pbase; p <= pbase + 4; ++p)
       if (!wait(p)) return false;
-    push(z0 - 1, true, false, false, fast_tag);
-    push(z0, true, true, false, fast_tag);
+    using yes = std::true_type;
+    using no = std::false_type;
+    push(z0 - 1, yes{}, no{}, no{}, fast_tag);
+    push(z0, yes{}, yes{}, no{}, fast_tag);
     __syncthreads();
     for (int z = z0; z < z1; ++z) {
       if (z + 4 <= plast) {  // the slot of plane z - 2 is free
@@ -687,7 +742,7 @@ __global__ void __launch_bounds__(NT3) fwd3t_kernel(const __grid_constant__ Maps
         issued = z + 4;
       }
       if (!wait(z + 3)) return false;
-      push(z + 1, true, true, true, fast_tag);
+      push(z + 1, yes{}, yes{}, yes{}, fast_tag);
       __syncthreads();
       gather(z, fast_tag);
       __syncthreads();
@@ -704,7 +759,7 @@ struct Adj3TArgs {
   int* status;
 };
 
-__global__ void __launch_bounds__(NT3) adj3t_kernel(const __grid_constant__ Maps3A maps, const __grid_constant__ Adj3TArgs a,
+__global__ void __launch_bounds__(NTF3, 2) adj3t_kernel(const __grid_constant__ Maps3A maps, const __grid_constant__ Adj3TArgs a,
                                                     Geom3 g, Coef3<float> c) {
   using R = float;
   extern __shared__ unsigned char smem_raw3[];
@@ -779,7 +834,7 @@ __global__ void __launch_bounds__(NT3) adj3t_kernel(const __grid_constant__ Maps
     R* out = PV + mod3(p) * 4 * PA3;
     const R* B = rb + bufB(p) * 10 * BOX3;
     const bool zf = p == 0 || p == nz - 1;
-    for (int q = threadIdx.x; q < PA3; q += NT3) {
+    for (int q = threadIdx.x; q < PA3; q += NTF3) {
       const int ly = q / PX3, lx = q - ly * PX3;
       const int i = x0 - 1 + lx, j = y0 - 1 + ly;
       if (p < 0 || p >= nz || (!FAST && (i < 0 || i >= nx || j < 0 || j >= ny))) {
@@ -817,6 +872,7 @@ __global__ void __launch_bounds__(NT3) adj3t_kernel(const __grid_constant__ Maps
   };
   auto gather = [&](int z, auto fast_tag) {
     constexpr bool FAST = decltype(fast_tag)::value;
+    if (threadIdx.x >= NT3) return;
     const int tx = threadIdx.x % TX3, ty = threadIdx.x / TX3;
     const int i = x0 + tx, j = y0 + ty;
     if (!FAST && (i >= nx || j >= ny)) return;
@@ -1102,7 +1158,7 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
       }
       CK3(c, cudaFuncSetAttribute(fwd3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3t_smem()));
       for (int s = 0; s < d.n_steps; ++s) {
-        fwd3t_kernel<<<march_grid(d), NT3, fwd3t_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
+        fwd3t_kernel<<<march_grid(d), NTF3, fwd3t_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
         CK3(c, cudaGetLastError());
         ++*c.launches;
         cur = 1 - cur;
@@ -1173,7 +1229,7 @@ lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out) {
       }
       CK3(c, cudaFuncSetAttribute(adj3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj3t_smem()));
       for (int it = 0; it < d.n_adj; ++it) {
-        adj3t_kernel<<<march_grid(d), NT3, adj3t_smem(), c.stream>>>(maps[acur], ta[acur], g, cf);
+        adj3t_kernel<<<march_grid(d), NTF3, adj3t_smem(), c.stream>>>(maps[acur], ta[acur], g, cf);
         CK3(c, cudaGetLastError());
         ++*c.launches;
         acur = 1 - acur;
