@@ -506,9 +506,10 @@ bool use_col(lks_handle* h) {
   return tiles >= 4ll * device_sms(h);
 }
 
-// Warp-column forward (FP32, non-thermal, one lattice): fwd_col2_kernel, one CTA per
-// 60 x 40 tile (two columns per lane).
-lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv) {
+// Warp-column forward (FP32, one lattice): fwd_col2_kernel, one CTA per 60 x 40 tile
+// (two columns per lane); thermal problems then run fwd_colT_kernel on the same tiles
+// for T.
+lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
   const auto& d = h->d;
   const int src = h->cur, dst = 1 - h->cur;
   using G2 = Col2Geo<C2_R>;
@@ -536,6 +537,29 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
   }
   fwd_col2_kernel<C2_R, false><<<grid, COL_NT, G2::smem, h->stream>>>(maps, a, make_geom(d), make_coef<float>(d));
   CKH(h, cudaGetLastError());
+  if (d.thermal) {
+    const float* tsrc[4] = {state_ptr<float>(h, src, 3), fsrc[1], fsrc[2], fld<float>(h, h->L.mat, 0) + 2 * h->L.N};
+    TmaMaps<4> tmaps;
+    for (int f = 0; f < 4; ++f)
+      if ((st = field_map(h, tsrc[f], C2_BW, G2::BH, &tmaps.m[f])) != LKS_OK) return st;
+    ColTArgs b;
+    std::memset(&b, 0, sizeof(b));
+    b.T_out = state_ptr<float>(h, dst, 3);
+    b.traj_T = tT;
+    b.u_new = a.out[1];
+    b.v_new = a.out[2];
+    b.J_partial = Jpartial;
+    b.status = a.status;
+    b.ntx = a.ntx;
+    static bool attrT = false;
+    if (!attrT) {
+      CKH(h, cudaFuncSetAttribute(fwd_colT_kernel<C2_R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)G2::smem));
+      attrT = true;
+    }
+    fwd_colT_kernel<C2_R><<<grid, COL_NT, G2::smem, h->stream>>>(tmaps, b, make_geom(d), make_coef<float>(d));
+    CKH(h, cudaGetLastError());
+    h->launches++;
+  }
   h->cur = dst;
   h->t = t_new;
   h->fwd_steps++;
@@ -546,8 +570,7 @@ lks_status launch_fwd_col(lks_handle* h, int t_new, double* Jpartial, float* tu,
 
 template <bool TH>
 lks_status launch_fwd_tma(lks_handle* h, int t_new, double* Jpartial, float* tu, float* tv, float* tT) {
-  if constexpr (!TH)
-    if (use_col(h)) return launch_fwd_col(h, t_new, Jpartial, tu, tv);
+  if (use_col(h)) return launch_fwd_col(h, t_new, Jpartial, tu, tv, TH ? tT : nullptr);
   constexpr int NF = fwd_tma_nf(TH);
   constexpr int BW = kFwdTX + 8, BH = kFwdTY + 4;
   const auto& d = h->d;

@@ -313,6 +313,192 @@ __global__ void __launch_bounds__(COL_NT) fwd_col2_kernel(const __grid_constant_
 }
 
 // ---------------------------------------------------------------------------------
+// Warp-column thermal forward (the temperature lattice; runs after fwd_col2_kernel)
+// ---------------------------------------------------------------------------------
+// T of the new level depends on T, u, v and B of the old level (Eq. geq2); only the
+// heat-flux edge rule also takes the new normal velocity of its node, which the flow
+// kernel of the same step has written.  Same tiles, lane pairs and march as
+// fwd_col2_kernel; the per-node arithmetic is gpush9 / tgather8 / tflux_edge, as in
+// fwd_tma_kernel<TH = true>.
+struct ColTArgs {
+  float* T_out;         // T of the new level
+  float* traj_T;        // optional trajectory copy of T
+  const float* u_new;   // new u, v written by the flow kernel (heat-flux edges)
+  const float* v_new;
+  double* J_partial;    // per-tile accumulator of kappa_T T (old level), or null
+  int* status;
+  int ntx;
+};
+
+// Staged fields: T, u, v (old level), B.
+template <int R>
+__global__ void __launch_bounds__(COL_NT) fwd_colT_kernel(const __grid_constant__ TmaMaps<4> maps,
+                                                          const __grid_constant__ ColTArgs a,
+                                                          const __grid_constant__ Geom g,
+                                                          const __grid_constant__ Coef<float> c) {
+  using G2 = Col2Geo<R>;
+  constexpr int BW = C2_BW, FS = G2::FS;
+  extern __shared__ unsigned char smem_raw[];
+  float* box = reinterpret_cast<float*>(smem_base128(smem_raw));
+  uint64_t* bar = reinterpret_cast<uint64_t*>(box + 4 * FS);
+  double* red = reinterpret_cast<double*>(bar + 1);
+  if (timed_out_before(a.status)) return;
+  if (!tma_layout_ok(box, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny;
+  const int x0 = (int)(blockIdx.x % a.ntx) * C2_W, y0 = (int)(blockIdx.x / a.ntx) * G2::H;
+  const bool fast = x0 >= 2 && x0 + C2_W + 2 <= nx && y0 >= 2 && y0 + G2::H + 2 <= ny;
+  if (threadIdx.x == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+    fence_proxy_async();
+    mbar_expect_tx(bar, 4 * G2::BOX * 4);
+    for (int f = 0; f < 4; ++f) tma_load_2d(box + f * FS, &maps.m[f], x0 - TMA_BXPAD, y0 - 2, bar);
+  }
+  __syncthreads();
+  if (!mbar_wait(bar, 0)) {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0) mbar_wait(bar, 0);
+    return;
+  }
+  const float* sT = box;
+  const float* su = box + FS;
+  const float* sv = box + 2 * FS;
+  const float* sB = box + 3 * FS;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i0 = x0 - 2 + 2 * lane;
+  const int bx = TMA_BXPAD - 2 + 2 * lane;
+  const int r0 = y0 + warp * R;
+  const bool out_lane = lane >= 1 && lane <= 30 && i0 >= 0 && i0 < nx;
+  auto brow = [&](int y) { return (y - y0 + 2) * BW; };
+  double jloc = 0.0;
+
+  struct Row {
+    float2 T, u, v;  // T, u, v of the lane's two columns
+    float Tl, Tr;    // T of the columns left and right of the pair
+  };
+  auto load_row = [&](Row& Q, int y) {
+    const int o = brow(y) + bx;
+    Q.T = *reinterpret_cast<const float2*>(sT + o);
+    Q.u = *reinterpret_cast<const float2*>(su + o);
+    Q.v = *reinterpret_cast<const float2*>(sv + o);
+    Q.Tl = __shfl_up_sync(0xffffffffu, Q.T.y, 1);
+    Q.Tr = __shfl_down_sync(0xffffffffu, Q.T.x, 1);
+  };
+  // New T of the lattice node (i, q), box column bc, from the populations gk arriving
+  // there: the interior gather or the thermal edge rule.
+  auto out_node = [&](int i, int q, int bc, const float* gk, float TT) {
+    int nxo = 0, nyo = 0;
+    const int cls = node_class(g, i, q, nxo, nyo);
+    if (cls == C_INTERIOR) return tgather8(TT, gk);
+    const int e = thermal_edge(g, i, q);
+    if (g.t_kind[e] == 0) return c.t_val[e];
+    if (cls == C_CORNER) return sT[brow(q == 0 ? 1 : ny - 2) + bc];
+    float g0 = 0.f, gp = 0.f;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      const int cx = cxk(k), cy = cyk(k);
+      const int si = i - cx, sj = q - cy;
+      if (si < 0 || si >= nx || sj < 0 || sj >= ny) continue;
+      const int cn = cx * nxo + cy * nyo;
+      if (cn == 0) g0 += gk[k];
+      else if (cn > 0) gp += gk[k];
+    }
+    const size_t o = (size_t)q * nx + i;
+    return tflux_edge(TT, g0, gp, c.t_val[e], a.u_new[o], a.v_new[o], nxo, nyo);
+  };
+  struct Dst {
+    float a[9], b[9];
+  };
+  auto step = [&](auto edge_tag, int p, Row& A, Row& B, Row& C, Dst& X, Dst& Y, Dst& Z) {
+    constexpr bool EDGE = decltype(edge_tag)::value;
+    float dT0[2] = {cdiff(B.T.y, B.Tl), cdiff(C.T.x, A.T.x)};
+    float dT1[2] = {cdiff(B.Tr, B.T.x), cdiff(C.T.y, A.T.y)};
+    if (EDGE) {
+      const int by = p - y0 + 2;
+      const bool ye = p == 0 || p == ny - 1;
+      if (i0 == 0 || i0 == nx - 1 || ye) {
+        dT0[0] = dfdx<float, BW>(sT, bx, by, i0, nx);
+        dT0[1] = dfdy<float, BW>(sT, bx, by, p, ny);
+      }
+      if (i0 + 1 == nx - 1 || ye) {
+        dT1[0] = dfdx<float, BW>(sT, bx + 1, by, i0 + 1, nx);
+        dT1[1] = dfdy<float, BW>(sT, bx + 1, by, p, ny);
+      }
+    }
+    const float2 Bn = *reinterpret_cast<const float2*>(sB + brow(p) + bx);
+    float G0[9], G1[9];
+    {
+      const float tn[9] = {0.f, B.T.y, C.T.x, B.Tl, A.T.x, C.T.y, C.Tl, A.Tl, A.T.y};
+      gpush9(B.T.x, tn, B.u.x, B.v.x, dT0[0], dT0[1], Bn.x, G0);
+    }
+    {
+      const float tn[9] = {0.f, B.Tr, C.T.y, B.T.x, A.T.y, C.Tr, C.T.x, A.T.x, A.Tr};
+      gpush9(B.T.y, tn, B.u.y, B.v.y, dT1[0], dT1[1], Bn.y, G1);
+    }
+    // objective term kappa_T T of the old level at the interior output nodes of row p
+    if (a.J_partial && out_lane && p >= r0 && p < r0 + R && (!EDGE || (p > 0 && p < ny - 1))) {
+      if (!EDGE || i0 > 0) jloc += (double)__fmul_rn(c.kappa_T, B.T.x);
+      if (!EDGE || i0 + 1 < nx - 1) jloc += (double)__fmul_rn(c.kappa_T, B.T.y);
+    }
+    const float r7 = __shfl_down_sync(0xffffffffu, G0[7], 1), r3 = __shfl_down_sync(0xffffffffu, G0[3], 1);
+    const float r6 = __shfl_down_sync(0xffffffffu, G0[6], 1);
+    const float l8 = __shfl_up_sync(0xffffffffu, G1[8], 1), l1 = __shfl_up_sync(0xffffffffu, G1[1], 1);
+    const float l5 = __shfl_up_sync(0xffffffffu, G1[5], 1);
+    X.a[4] = G0[4], X.a[7] = G1[7], X.a[8] = l8;
+    X.b[4] = G1[4], X.b[7] = r7, X.b[8] = G0[8];
+    Y.a[0] = G0[0], Y.a[1] = l1, Y.a[3] = G1[3];
+    Y.b[0] = G1[0], Y.b[1] = G0[1], Y.b[3] = r3;
+    Z.a[2] = G0[2], Z.a[5] = l5, Z.a[6] = G1[6];
+    Z.b[2] = G1[2], Z.b[5] = G0[5], Z.b[6] = r6;
+    const int q = p - 1;
+    if (q >= r0 && out_lane && (!EDGE || q < ny)) {
+      const size_t o = (size_t)q * nx + i0;
+      float2 Tn;
+      if (EDGE) {
+        Tn.x = out_node(i0, q, bx, X.a, A.T.x);
+        Tn.y = out_node(i0 + 1, q, bx + 1, X.b, A.T.y);
+      } else {
+        Tn.x = tgather8(A.T.x, X.a);
+        Tn.y = tgather8(A.T.y, X.b);
+      }
+      *reinterpret_cast<float2*>(a.T_out + o) = Tn;
+      if (a.traj_T) *reinterpret_cast<float2*>(a.traj_T + o) = Tn;
+    }
+    if (p + 2 <= r0 + R + 1) load_row(A, p + 2);
+  };
+  Row R0, R1, R2;
+  Dst X0, X1, X2;
+  load_row(R0, r0 - 2);
+  load_row(R1, r0 - 1);
+  load_row(R2, r0);
+  if (fast) {
+#pragma unroll 1
+    for (int p = r0 - 1; p <= r0 + R; p += 3) {
+      step(std::false_type{}, p, R0, R1, R2, X0, X1, X2);
+      step(std::false_type{}, p + 1, R1, R2, R0, X1, X2, X0);
+      step(std::false_type{}, p + 2, R2, R0, R1, X2, X0, X1);
+    }
+  } else {
+#pragma unroll 1
+    for (int p = r0 - 1; p <= r0 + R; ++p) {
+      step(std::true_type{}, p, R0, R1, R2, X0, X1, X2);
+      const Row t = R0;
+      R0 = R1;
+      R1 = R2;
+      R2 = t;
+      const Dst u = X0;
+      X0 = X1;
+      X1 = X2;
+      X2 = u;
+    }
+  }
+  if (a.J_partial) {
+    const double sj = block_sum<COL_NT>(jloc, red);
+    if (threadIdx.x == 0) a.J_partial[blockIdx.x] += sj;
+  }
+}
+
+// ---------------------------------------------------------------------------------
 // Warp-column ALKS step (FP32, non-thermal, one lattice)
 // ---------------------------------------------------------------------------------
 // The same march for the adjoint: a lane computes P + c_k . V (Eq. afeq) of its node

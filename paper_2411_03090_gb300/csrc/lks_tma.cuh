@@ -157,6 +157,40 @@ __device__ __forceinline__ void push9(float dr, const float* d, float uu, float 
   F[8] = __fmaf_rn(-w5, d[8], __fmaf_rn(w5, q2, wsm));
 }
 
+// The thermal pushed populations of one node (Eq. geq2, increment form): G_k is sent
+// to x + c_k and carries w_k [(T(x) - T(x + c_k)) + c_k . (3 T u + B grad T)];
+// t[k] = T(x + c_k) for k = 1..8 (G_0 = 0).
+__device__ __forceinline__ void gpush9(float TT, const float* t, float uu, float vv, float dTx, float dTy,
+                                       float Bn, float* G) {
+  const float T3 = __fmul_rn(3.f, TT);
+  const float qx = __fmaf_rn(T3, uu, __fmul_rn(Bn, dTx));
+  const float qy = __fmaf_rn(T3, vv, __fmul_rn(Bn, dTy));
+  G[0] = 0.f;
+  G[1] = __fmul_rn(__fadd_rn(__fsub_rn(TT, t[1]), qx), 1.f / 9.f);
+  G[3] = __fmul_rn(__fsub_rn(__fsub_rn(TT, t[3]), qx), 1.f / 9.f);
+  G[2] = __fmul_rn(__fadd_rn(__fsub_rn(TT, t[2]), qy), 1.f / 9.f);
+  G[4] = __fmul_rn(__fsub_rn(__fsub_rn(TT, t[4]), qy), 1.f / 9.f);
+  G[5] = __fmul_rn(__fadd_rn(__fadd_rn(__fsub_rn(TT, t[5]), qx), qy), 1.f / 36.f);
+  G[6] = __fmul_rn(__fadd_rn(__fsub_rn(__fsub_rn(TT, t[6]), qx), qy), 1.f / 36.f);
+  G[7] = __fmul_rn(__fsub_rn(__fsub_rn(__fsub_rn(TT, t[7]), qx), qy), 1.f / 36.f);
+  G[8] = __fmul_rn(__fsub_rn(__fadd_rn(__fsub_rn(TT, t[8]), qx), qy), 1.f / 36.f);
+}
+// Interior thermal gather: T(x) + sum over k = 1..8 of G_k(x - c_k).
+__device__ __forceinline__ float tgather8(float TT, const float* gk) {
+  float gs = gk[1];
+#pragma unroll
+  for (int k = 2; k < 9; ++k) gs = __fadd_rn(gs, gk[k]);
+  return __fadd_rn(TT, gs);
+}
+// Heat-flux edge (Sec. 2.4 edge rule): (T + g0 + 2 gp + q_w) / (1 + u_n), with g0 / gp
+// the known tangential / inward populations and u_n the new normal velocity.
+__device__ __forceinline__ float tflux_edge(float TT, float g0, float gp, float qw, float un, float vn, int nxo,
+                                            int nyo) {
+  const float num = __fadd_rn(__fadd_rn(__fadd_rn(TT, g0), __fmul_rn(2.f, gp)), qw);
+  const float den = __fadd_rn(__fadd_rn(1.f, __fmul_rn(un, (float)nxo)), __fmul_rn(vn, (float)nyo));
+  return __fdiv_rn(num, den);
+}
+
 // Interior gather of one node: drho, and u, v before / after the implicit Brinkman
 // division (fk[k] = F_k(x - c_k)).
 __device__ __forceinline__ void gather9(const float* fk, float drx, float inv, float& drn, float& un, float& vn) {
@@ -461,26 +495,20 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
         }
         if (TH) {
           const float TT = sT[s2];
-          const float Bn = sB[s2];
-          const float dTx = EDGE ? dfdx<float, BW>(sT, sx, sy, i, nx) : (sT[s2 + 1] - sT[s2 - 1]) * 0.5f;
-          const float dTy = EDGE ? dfdy<float, BW>(sT, sx, sy, j, ny) : (sT[s2 + BW] - sT[s2 - BW]) * 0.5f;
-          const float tq_x = 3.f * TT * uu + Bn * dTx;
-          const float tq_y = 3.f * TT * vv + Bn * dTy;
-          Gp[q] = 0.f;
-          Gp[1 * A1 + q] = ((TT - sT[s2 + 1]) + tq_x) * (1.f / 9.f);
-          Gp[3 * A1 + q] = ((TT - sT[s2 - 1]) - tq_x) * (1.f / 9.f);
-          Gp[2 * A1 + q] = ((TT - sT[s2 + BW]) + tq_y) * (1.f / 9.f);
-          Gp[4 * A1 + q] = ((TT - sT[s2 - BW]) - tq_y) * (1.f / 9.f);
-          Gp[5 * A1 + q] = ((TT - sT[s2 + BW + 1]) + tq_x + tq_y) * (1.f / 36.f);
-          Gp[6 * A1 + q] = ((TT - sT[s2 + BW - 1]) - tq_x + tq_y) * (1.f / 36.f);
-          Gp[7 * A1 + q] = ((TT - sT[s2 - BW - 1]) - tq_x - tq_y) * (1.f / 36.f);
-          Gp[8 * A1 + q] = ((TT - sT[s2 - BW + 1]) + tq_x - tq_y) * (1.f / 36.f);
+          const float dTx = EDGE ? dfdx<float, BW>(sT, sx, sy, i, nx) : cdiff(sT[s2 + 1], sT[s2 - 1]);
+          const float dTy = EDGE ? dfdy<float, BW>(sT, sx, sy, j, ny) : cdiff(sT[s2 + BW], sT[s2 - BW]);
+          const float tn[9] = {0.f, sT[s2 + 1], sT[s2 + BW], sT[s2 - 1], sT[s2 - BW], sT[s2 + BW + 1], sT[s2 + BW - 1],
+                               sT[s2 - BW - 1], sT[s2 - BW + 1]};
+          float G[9];
+          gpush9(TT, tn, uu, vv, dTx, dTy, sB[s2], G);
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Gp[k * A1 + q] = G[k];
         }
         // objective of the old state at interior tile nodes (unsteady accumulation)
         if (a.J_partial && lx >= 1 && lx <= TX_ && ly >= 1 && ly <= TY_ &&
             (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1))) {
           jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
-          if (TH) jloc += (double)(c.kappa_T * sT[s2]);
+          if (TH) jloc += (double)__fmul_rn(c.kappa_T, sT[s2]);
         }
       }
     };
@@ -507,10 +535,10 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
         if (cls == C_INTERIOR) {
           gather9(fk, drx, sbi[s2], drn, un, vn);
           if (TH) {
-            float gs = 0.f;
+            float gk[9];
 #pragma unroll
-            for (int k = 1; k < 9; ++k) gs += Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
-            Tn = sT[s2] + gs;
+            for (int k = 1; k < 9; ++k) gk[k] = Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
+            Tn = tgather8(sT[s2], gk);
           }
         } else {
           float s0 = 0.f, sp = 0.f, g0 = 0.f, gp = 0.f;
@@ -553,7 +581,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
               const int jn = (j == 0) ? 1 : ny - 2;
               Tn = sT[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
             } else {
-              Tn = (sT[s2] + g0 + 2.f * gp + c.t_val[e]) / (1.f + un * (float)nxo + vn * (float)nyo);
+              Tn = tflux_edge(sT[s2], g0, gp, c.t_val[e], un, vn, nxo, nyo);
             }
           }
         }

@@ -311,6 +311,54 @@ def thermal_small(steady, nx=70, **kw):
     return p
 
 
+def thermal_column_case(steady=True):
+    """200 x 150 thermal channel with fixed-T and heat-flux edges: interior and edge
+    column tiles (60 x 40) for the flow and the temperature kernels."""
+    base = dict(seed=3, sigma=3.0, strip=3, n_steps=200, n_adj=200, thermal=1, kappa_T=1e-2,
+                t_kind=[0, 1, 0, 1], t_val=[0.0, 0.0, 1.0, 0.0])
+    if not steady:
+        base.update(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=90.0, n_steps=120)
+    p = inputs.channel(200, 150, Re=60.0, **base)
+    p.K_f = p.nu / 0.71
+    p.K_s = p.K_f
+    return p
+
+
+@pytest.mark.parametrize("steady", [True, False])
+def test_thermal_column_forward_equals_tma_step_bitwise(steady):
+    """The warp-column forward (flow kernel, then the temperature kernel) computes
+    every node with the arithmetic of the thermal TMA kernel: identical states,
+    adjoints and gradients; J differs only in the grouping of its FP64 sums."""
+    pb = thermal_column_case(steady)
+    g = torch.from_numpy(pb.gamma())
+    K = 0 if steady else 20
+    a = LKS(pb, real="f32", path="column", checkpoint_every=K)
+    b = LKS(pb, real="f32", path="step", checkpoint_every=K)
+    Ja, ga = a.gradient(g)
+    Jb, gb = b.gradient(g)
+    assert a.query().fwd_path == 3 and b.query().fwd_path == 1
+    for x, y in zip(a.get_state(), b.get_state()):
+        assert torch.equal(x, y)
+    for x, y in zip(a.get_adjoint(), b.get_adjoint()):
+        assert torch.equal(x, y)
+    assert torch.equal(ga, gb)
+    assert abs(Ja.item() - Jb.item()) <= 1e-12 * abs(Jb.item())
+
+
+def test_thermal_column_forward_matches_oracle():
+    pb = thermal_column_case(True)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="column")
+    J = s.lks_forward(torch.from_numpy(g)).item()
+    assert s.query().fwd_path == 3 and s.query().device_status == 0
+    st, _, _, _ = O.forward(pb, g, pb.n_steps)
+    got, T = gpu_state(s)
+    for x, y in zip(got, oracle_state(st)):
+        assert rel_l2(x, y) <= 1e-5
+    assert rel_l2(T, st.T) <= 1e-5
+    assert abs(J - O.objective(pb, g, st)) <= 1e-4 * abs(J)
+
+
 @pytest.mark.parametrize("path", ["step", "resident"])
 @pytest.mark.parametrize("real,tol", [("f64", 1e-11), ("f32", 1e-5)])
 def test_thermal_forward_matches_oracle(real, tol, path):
