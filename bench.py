@@ -146,6 +146,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def oracle_steps_for(pb, seconds: float) -> int:
+    """Forward (and as many adjoint) steps of the FP64 oracle on the full lattice that
+    take about `seconds` on the host cores, from a short timed calibration run."""
+    from oracle import oracle as O
+    O.build()
+    g = pb.gamma()
+    n = 2
+    t0 = time.perf_counter()
+    if hasattr(pb, "nz"):
+        st, _, _, _ = O.forward3(pb, g, n)
+        O.steady_adjoint3(pb, g, st, n)
+    else:
+        st, _, _, _ = O.forward(pb, g, n)
+        O.steady_adjoint(pb, g, st, n)
+    per_pair = (time.perf_counter() - t0) / n
+    return int(max(2, min(pb.n_steps, seconds / max(per_pair, 1e-9))))
+
+
 def cpu_baseline(pb, n_fwd: int, n_adj: int):
     """The FP64 oracle on the host cores, on a bounded sample of the workload: the
     full lattice for n_fwd forward + n_adj adjoint steps (steady iteration)."""
@@ -173,19 +191,20 @@ def run_reference(args):
     if rank != 0:
         return
     pb, desc = workload(args.workload)
-    n_f, n_a = (60, 60) if args.workload == "config2" else (20, 20)
-    if args.workload == "config1":
-        n_f, n_a = 500, 500
+    n_f = n_a = oracle_steps_for(pb, 3.0)  # each timed step: about 3 s of host work
     from oracle import oracle as O
     O.build()
     g = pb.gamma()
+    three_d = hasattr(pb, "nz")
+    fwd = O.forward3 if three_d else O.forward
+    adj = O.steady_adjoint3 if three_d else O.steady_adjoint
     for _ in range(args.warmup):
-        st, _, _, _ = O.forward(pb, g, 2)
+        st, _, _, _ = fwd(pb, g, 2)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        st, _, _, _ = O.forward(pb, g, n_f)
-        O.steady_adjoint(pb, g, st, n_a)
+        st, _, _, _ = fwd(pb, g, n_f)
+        adj(pb, g, st, n_a)
         times.append(time.perf_counter() - t0)
     dt = sum(times)
     value = pb.n_nodes * (n_f + n_a) * args.steps / dt / 1e6
@@ -550,8 +569,8 @@ def main():
     }
     if not args.no_cpu_baseline:
         try:
-            out["cpu_baseline"] = cpu_baseline(pb, 40, 40) if args.workload == "config2" else \
-                cpu_baseline(pb, 2, 2) if three_d else cpu_baseline(pb, 5, 5)
+            n_cb = oracle_steps_for(pb, 10.0)  # a bounded sample: about 10 s of host work
+            out["cpu_baseline"] = cpu_baseline(pb, n_cb, n_cb)
         except Exception as e:  # the oracle is a reported baseline, not the product
             out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
     print(json.dumps(out))
