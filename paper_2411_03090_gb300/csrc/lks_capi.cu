@@ -282,7 +282,9 @@ struct ResPlan {
 };
 
 // Tile shapes of the resident marches: {TXR, TYR, threads}.
-constexpr int kResCfg[3][3] = {{64, 16, 512}, {32, 16, 256}, {32, 8, 256}};
+// (64 x 14 puts the 512 x 256 channel on 8 x 19 = 152 tiles, one per SM of a GB300.)
+constexpr int kNResCfg = 4;
+constexpr int kResCfg[kNResCfg][3] = {{64, 16, 512}, {32, 16, 256}, {32, 8, 256}, {64, 14, 512}};
 
 int device_sms(lks_handle* h) {
   if (h->sms == 0 && cudaDeviceGetAttribute(&h->sms, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess)
@@ -310,7 +312,7 @@ ResPlan plan_resident(lks_handle* h, bool adjoint) {
   const int sms = device_sms(h);
   int optin = 0;
   cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, h->device);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < kNResCfg; ++k) {
     const int nt = ((h->d.nx + kResCfg[k][0] - 1) / kResCfg[k][0]) * ((h->d.ny + kResCfg[k][1] - 1) / kResCfg[k][1]);
     if (res_smem_bytes(h->d, adjoint, k) + 1024 > (size_t)optin) continue;
     if (nt <= sms && nt > best.ntiles) {
@@ -430,9 +432,12 @@ lks_status launch_fwd_resident_th(lks_handle* h, int n, int k, int ks) {
     if (k == 1 && ks == 3) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 3>(h, n);
     if (k == 1 && ks == 2) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 2>(h, n);
     if (k == 2 && ks == 2) return launch_fwd_resident_cfg<R, TH, 32, 8, 256, 2>(h, n);
+    if (k == 3 && ks == 3) return launch_fwd_resident_cfg<R, TH, 64, 14, 512, 3>(h, n);
+    if (k == 3 && ks == 2) return launch_fwd_resident_cfg<R, TH, 64, 14, 512, 2>(h, n);
   }
   if (k == 0) return launch_fwd_resident_cfg<R, TH, 64, 16, 512, 1>(h, n);
   if (k == 1) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 1>(h, n);
+  if (k == 3) return launch_fwd_resident_cfg<R, TH, 64, 14, 512, 1>(h, n);
   return launch_fwd_resident_cfg<R, TH, 32, 8, 256, 1>(h, n);
 }
 
@@ -453,9 +458,12 @@ lks_status launch_adj_resident(lks_handle* h, int n) {
     if (k == 1 && ks == 3) return launch_adj_resident_cfg<R, 32, 16, 256, 3>(h, n);
     if (k == 1 && ks == 2) return launch_adj_resident_cfg<R, 32, 16, 256, 2>(h, n);
     if (k == 2 && ks == 2) return launch_adj_resident_cfg<R, 32, 8, 256, 2>(h, n);
+    if (k == 3 && ks == 3) return launch_adj_resident_cfg<R, 64, 14, 512, 3>(h, n);
+    if (k == 3 && ks == 2) return launch_adj_resident_cfg<R, 64, 14, 512, 2>(h, n);
   }
   if (k == 0) return launch_adj_resident_cfg<R, 64, 16, 512, 1>(h, n);
   if (k == 1) return launch_adj_resident_cfg<R, 32, 16, 256, 1>(h, n);
+  if (k == 3) return launch_adj_resident_cfg<R, 64, 14, 512, 1>(h, n);
   return launch_adj_resident_cfg<R, 32, 8, 256, 1>(h, n);
 }
 
