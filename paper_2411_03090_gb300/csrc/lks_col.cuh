@@ -23,8 +23,10 @@ constexpr int COL_NT = 32 * COL_WARPS;
 // ---------------------------------------------------------------------------------
 // Warp-column forward with two columns per lane
 // ---------------------------------------------------------------------------------
-// Lane l owns the columns x0 - 2 + 2l and x0 - 1 + 2l and marches down R rows like
-// fwd_col_kernel.  Neighbours inside the lane pair need no shuffle; a row costs two
+// Lane l owns the columns x0 - 2 + 2l and x0 - 1 + 2l and marches down R rows with
+// three rows of values in registers.  A row pushes the nine populations of both
+// nodes and completes the row above it.  Neighbours inside the lane pair need no
+// shuffle; a row costs two
 // shuffles per field crossing the lane boundary and six for the populations moving
 // to the neighbour lanes, and its loads and stores are 8-byte vectors.  Lanes 1..30
 // write, so a tile is 60 columns wide; tiles start at x = 0 (the first box starts
@@ -504,8 +506,10 @@ __global__ void __launch_bounds__(COL_NT) fwd_colT_kernel(const __grid_constant_
 // The same march for the adjoint: a lane computes P + c_k . V (Eq. afeq) of its node
 // for the nine links and the strain of the level-t state, hands the values a
 // neighbouring column gathers to it by shuffle, and completes the moments of a row
-// once the row below has been computed.  Tiles of 28 x 32 outputs (four warps of
-// eight rows); the per-node arithmetic is that of adj_tma_kernel, term for term.
+// once the row below has been computed.  One column per lane (lanes 2..29 write),
+// tiles of 28 x 32 outputs (four warps of eight rows); the per-node arithmetic is
+// that of adj_tma_kernel, term for term.  The batched form runs the same kernel over
+// a (design, tile) work list.
 constexpr int ACOL_R = 8;
 constexpr int ACOL_H = COL_WARPS * ACOL_R;
 constexpr int ACOL_BH = ACOL_H + 4, ACOL_BOX = COL_BW * ACOL_BH;
