@@ -510,6 +510,7 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
 // SM (below that the per-tile TMA kernels, with fewer edge tiles, are faster).
 bool use_col(lks_handle* h) {
   if (h->d.exec_path == LKS_PATH_COLUMN) return true;
+  if (h->d.exec_path == LKS_PATH_STEP) return false;  // the per-tile kernels, as asked
   const long long tiles = (long long)((h->d.nx + C2_W - 1) / C2_W) * ((h->d.ny + Col2Geo<C2_R>::H - 1) / Col2Geo<C2_R>::H);
   return tiles >= 4ll * device_sms(h);
 }

@@ -506,6 +506,19 @@ def test_unsteady_J_every_path_matches_oracle(path):
     assert abs(J - Jo) <= 2e-6 * abs(Jo)
 
 
+def test_exec_path_is_honoured_on_a_large_lattice():
+    """2048 x 1024 has more than four column tiles per SM: the automatic choice is
+    the warp-column forward, while an explicit step path keeps the per-tile kernels."""
+    pb = inputs.roofline2d(2048).with_(ny=1024, n_steps=3, n_adj=3)
+    g = torch.from_numpy(pb.gamma())
+    paths = {}
+    for path in ("auto", "step", "column"):
+        s = LKS(pb, real="f32", path=path)
+        s.lks_forward(g)
+        paths[path] = s.query().fwd_path
+    assert paths == {"auto": 3, "step": 1, "column": 3}
+
+
 @pytest.mark.parametrize("steady", [True, False])
 def test_column_equals_tma_step_bitwise(steady):
     """The warp-column kernels compute every node with the arithmetic of the
