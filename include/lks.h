@@ -251,6 +251,16 @@ lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_
  * afboundaryuq, afboundarypq). */
 lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
 
+/* Diagnostics: runs one of the library's bounded device waits on a condition that
+ * never comes true, on cuda_stream, and returns in *recorded the status the kernel
+ * wrote: LKS_ERR_TIMEOUT when the wait gave up as designed.  which: 0 the tile-flag
+ * wait of the resident marches (about 2 s), 1 the mbarrier wait of the TMA-staged
+ * kernels (well under a second).  scratch_dev: 2 int32 of device memory owned by the
+ * caller, overwritten.  Synchronises the stream.  A wait that gives up returns (it
+ * does not trap), so the CUDA context stays usable.  Errors: LKS_ERR_INVALID_ARG for
+ * a bad which or a NULL pointer (before any GPU work), LKS_ERR_CUDA. */
+lks_status lks_selftest_wait(int32_t which, int32_t *scratch_dev, void *cuda_stream, int32_t *recorded);
+
 /* ---------------------------------------------------------------------------------
  * Batched form: many designs (load cases, optimiser candidates) of unequal lattice
  * size marched in lock step.  One persistent launch per time step covers every

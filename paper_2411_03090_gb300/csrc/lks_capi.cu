@@ -1071,6 +1071,21 @@ lks_status reject3(lks_handle* h, const char* what) {
 // ------------------------------------------------------------------------------------
 // C ABI
 // ------------------------------------------------------------------------------------
+// Self-test of the bounded device waits (lks_selftest_wait): one thread waits on a
+// tile flag nothing sets (0) or on an mbarrier no copy completes (1); the wait gives
+// up after its iteration limit and records LKS_ERR_TIMEOUT in *status.
+static __global__ void selftest_wait_kernel(int which, int* flag, int* status) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  if (which == 0) {
+    wait_flag(flag, 1, status);
+  } else {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
+    if (!mbar_wait(&bar, 0)) raise_status(status, LKS_ERR_TIMEOUT);
+  }
+}
+
 extern "C" {
 
 const char* lks_status_string(lks_status s) {
@@ -1408,6 +1423,20 @@ lks_status lks_gradient_noalloc(const lks_problem_desc* desc, const void* gamma_
   h.device = dev;
   return desc->real_type == LKS_REAL_F64 ? noalloc_run<double>(&h, gamma_dev, J_dev, dJdgamma_dev)
                                          : noalloc_run<float>(&h, gamma_dev, J_dev, dJdgamma_dev);
+}
+
+lks_status lks_selftest_wait(int32_t which, int32_t* scratch, void* stream, int32_t* recorded) {
+  if ((which != 0 && which != 1) || !scratch || !recorded) return LKS_ERR_INVALID_ARG;
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (cudaMemsetAsync(scratch, 0, 2 * sizeof(int32_t), s) != cudaSuccess) return LKS_ERR_CUDA;
+  selftest_wait_kernel<<<1, 32, 0, s>>>(which, scratch, scratch + 1);
+  if (cudaGetLastError() != cudaSuccess) return LKS_ERR_CUDA;
+  int32_t st = 0;
+  if (cudaMemcpyAsync(&st, scratch + 1, sizeof(int32_t), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+      cudaStreamSynchronize(s) != cudaSuccess)
+    return LKS_ERR_CUDA;
+  *recorded = st;
+  return LKS_OK;
 }
 
 lks_status lks_edge_moment_map(double A, int32_t cls, double* out) {

@@ -90,7 +90,7 @@ class BatchStats(C.Structure):
 EXPORTS = ("lks_workspace_size", "lks_create", "lks_forward", "alks_adjoint", "lks_sensitivity",
            "lks_gradient_host", "lks_set_state", "lks_get_state", "lks_march", "alks_set_adjoint",
            "alks_get_adjoint", "alks_march", "lks_query", "lks_destroy", "lks_status_string",
-           "lks_last_error", "lks_edge_moment_map", "lks_gradient_noalloc",
+           "lks_last_error", "lks_edge_moment_map", "lks_selftest_wait", "lks_gradient_noalloc",
            "lks_batch_workspace_size", "lks_batch_create", "lks_batch_gradient", "lks_batch_query",
            "lks_batch_destroy", "lks_batch_last_error")
 
@@ -132,6 +132,7 @@ def load(build_if_missing: bool = True):
     L.lks_last_error.argtypes = [hp]
     L.lks_last_error.restype = C.c_char_p
     L.lks_edge_moment_map.argtypes = [C.c_double, i32, dp]
+    L.lks_selftest_wait.argtypes = [i32, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
     L.lks_gradient_noalloc.argtypes = [C.POINTER(Desc), vp, vp, vp, vp]
     L.lks_batch_workspace_size.argtypes = [i32, C.POINTER(Desc), C.POINTER(BatchOptions), C.POINTER(C.c_size_t)]
     L.lks_batch_create.argtypes = [i32, C.POINTER(Desc), C.POINTER(BatchOptions), vp, C.c_size_t, vp,
@@ -197,6 +198,20 @@ def _check(status: int, what: str, handle=None) -> None:
         if handle is not None:
             msg += ": " + load().lks_last_error(handle).decode()
         raise LKSError(status, msg)
+
+
+def selftest_wait(which: int, device: Optional[torch.device] = None) -> int:
+    """Runs one of the library's bounded device waits on a condition that never comes
+    true (0: the resident marches' tile flag, 1: the TMA kernels' mbarrier) and
+    returns the status the kernel recorded (LKS_ERR_TIMEOUT = 6 when it gave up)."""
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    scratch = torch.zeros(2, dtype=torch.int32, device=dev)
+    rec = C.c_int32(-1)
+    with torch.cuda.device(dev):
+        stream = torch.cuda.current_stream(dev)
+        _check(load().lks_selftest_wait(int(which), C.c_void_p(scratch.data_ptr()), C.c_void_p(stream.cuda_stream),
+                                        C.byref(rec)), "lks_selftest_wait")
+    return int(rec.value)
 
 
 def edge_moment_map(A: float, cls: int) -> np.ndarray:

@@ -98,6 +98,15 @@ def test_workspace_grows_with_checkpoint_storage():
     assert ck < plain
 
 
+def test_selftest_wait_rejects_bad_arguments_without_gpu_work():
+    L = lks.load()
+    rec = C.c_int32(-1)
+    assert L.lks_selftest_wait(2, C.c_void_p(16), None, C.byref(rec)) == 1
+    assert L.lks_selftest_wait(0, None, None, C.byref(rec)) == 1
+    assert L.lks_selftest_wait(1, C.c_void_p(16), None, None) == 1
+    assert rec.value == -1
+
+
 def test_create_rejects_bad_workspace_without_gpu_work():
     L = lks.load()
     d = lks.make_desc(inputs.config1())

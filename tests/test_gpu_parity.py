@@ -212,6 +212,23 @@ def test_resident_steps_per_exchange_config2(ks):
     assert rel_l2(ga.cpu().numpy(), gb.cpu().numpy()) <= 1e-5
 
 
+@pytest.mark.parametrize("which", [0, 1])
+def test_bounded_waits_give_up_and_report(which):
+    """Failure detection without a GPU fault: a device wait on a condition nothing
+    satisfies (0: the resident marches' tile flag, 1: the TMA kernels' mbarrier)
+    gives up after its iteration limit, records LKS_ERR_TIMEOUT, and the context
+    stays usable for the next gradient."""
+    import time
+    from paper_2411_03090_gb300 import lks
+    t0 = time.time()
+    assert lks.selftest_wait(which) == 6
+    assert time.time() - t0 < 60
+    pb = small()
+    s = LKS(pb, real="f32")
+    J, grad = s.gradient(torch.from_numpy(pb.gamma()))
+    assert s.query().device_status == 0 and np.isfinite(J.item())
+
+
 def test_sensitivity_zero_on_edges_and_finite():
     pb = small()
     s = LKS(pb, real="f32")
