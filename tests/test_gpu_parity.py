@@ -391,6 +391,43 @@ def test_thermal_forward_matches_oracle(real, tol, path):
     assert abs(J - O.objective(pb, g, st)) <= 10 * tol * abs(J)
 
 
+def test_single_steps_full_size_config3():
+    """1024 x 512 thermal unsteady channel (config 3), FP32, the per-step TMA kernels
+    the benchmark runs: one forward step and one ALKS step from developed fields
+    equal the oracle's steps from the same fields (all nine adjoint fields)."""
+    pb = inputs.config3()
+    g = pb.gamma()
+    gf = g.astype(np.float32).astype(np.float64)
+    s = LKS(pb, real="f32")
+    gt = torch.from_numpy(g)
+    z = torch.zeros(pb.ny, pb.nx)
+    s.set_state(gt, z, z, z, z, t=0)
+    s.march(300)
+    (d0, u0, v0), T0 = gpu_state(s)
+    s.march(1)
+    assert s.query().fwd_path == 1 and s.query().device_status == 0
+    (d1, u1, v1), T1 = gpu_state(s)
+    st = O.State(pb.ny, pb.nx)
+    st.rho, st.u, st.v, st.T = d0 + 1.0, u0, v0, T0
+    ref = O.forward_step(pb, gf, 301, st)
+    for a, b, scale in ((d1, ref.rho - 1.0, np.abs(d0).max()), (u1, ref.u, pb.u_max),
+                        (v1, ref.v, pb.u_max), (T1, ref.T, 1.0)):
+        assert np.abs(a - b).max() <= 2e-6 * scale
+    # ALKS step with the state frozen at level 301
+    rng = np.random.default_rng(7)
+    s.set_adjoint([torch.from_numpy(1e-3 * rng.standard_normal((pb.ny, pb.nx))).float() for _ in range(9)])
+    s.adjoint_march(50)
+    a0 = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    s.adjoint_march(1)
+    a1 = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    st1 = O.State(pb.ny, pb.nx)
+    st1.rho, st1.u, st1.v, st1.T = d1 + 1.0, u1, v1, T1
+    ref_a = O.adjoint_step(pb, gf, st1, st1, np.stack(a0))
+    for q in range(9):
+        scale = np.abs(ref_a[q]).max()
+        assert np.abs(a1[q] - ref_a[q]).max() <= 1e-5 * scale, q
+
+
 @pytest.mark.parametrize("real,tol", [("f64", 1e-10), ("f32", 1e-3)])
 def test_thermal_steady_gradient_matches_oracle(real, tol):
     pb = thermal_small(True)
