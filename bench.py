@@ -431,6 +431,8 @@ def main():
                     help="config5: forward kernel (-1: autotuned, 0: TMA-staged, 1: warp-column)")
     ap.add_argument("--adj-column", type=int, default=-1,
                     help="config5: adjoint kernel (-1: autotuned, 0: TMA-staged, 1: warp-column)")
+    ap.add_argument("--exec-path", default="auto", choices=["auto", "step", "resident", "column"],
+                    help="config1/2/4: how the marches run (the library's exec_path)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
@@ -462,7 +464,7 @@ def main():
         desc += f" (shortened to {args.steps_override}+{args.steps_override} steps)"
     g_np = pb.gamma()
     gamma = torch.from_numpy(g_np).to(dev, torch.float32)
-    s = LKS(pb, real="f32", device=dev, res_steps=args.res_steps)
+    s = LKS(pb, real="f32", device=dev, res_steps=args.res_steps, path=args.exec_path)
     stream = s.stream
     N = pb.n_nodes
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
@@ -524,7 +526,9 @@ def main():
     adj_k = kname.get(st.adj_path, kname[1])[0]
     fwd_k = kname.get(st.fwd_path, kname[1])[1]
     if three_d:
-        adj_k, fwd_k = "adj3_kernel<float>", "fwd3_kernel<float>"
+        tma3 = pb.nx % 4 == 0
+        adj_k = "adj3t_kernel" if tma3 else "adj3_kernel<float>"
+        fwd_k = ("fwd3c_kernel" if st.fwd_path == 3 else "fwd3t_kernel") if tma3 else "fwd3_kernel<float>"
     roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
                 "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,
                 "algorithmic_bytes_per_node": b_adj, "mean_step_us": adj_launch_s * 1e6,

@@ -753,6 +753,310 @@ __global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ 
   if (!ok) drain_and_fail();
 }
 
+// ---------------------------------------------------------------------------------
+// Warp-column D3Q19 forward (FP32)
+// ---------------------------------------------------------------------------------
+// Lanes run along x (one column each; lanes 2..29 write, so a tile is 28 columns
+// wide), warp w owns row y0 - 1 + w (rows y0 .. y0 + NYC3 - 1 are outputs; the two
+// outer warps are halo rows whose pushes feed the tile), and the CTA marches a
+// chunk of z planes.  Planes arrive by 3-D tensor copies into a ring of NSLC3 slots
+// (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)).  For each source plane z a lane
+// computes the 19 pushed increments of its node (push_link3, Eq. feq2) and routes
+// each at once:
+//   - the 9 links with c_y = 0 stay in the warp: c_x by shuffle, c_z through a
+//     register ring of destination planes (plane d receives links 5, 11, 14 from
+//     plane d - 1, links 0, 1, 2 from plane d, links 6, 12, 13 from plane d + 1);
+//   - the 10 links with c_y = +-1 go to the neighbouring warps through a shared
+//     exchange buffer indexed by destination plane mod NXS3.
+// One barrier per plane separates the exchange writes from the gather of plane
+// z - 1, which is complete then.  A slot of the exchange buffer is rewritten two
+// steps after it is read, with that barrier in between; values pushed from nodes
+// outside the lattice are never read (the face rules skip such links, and every
+// source of an interior node is inside).
+constexpr int CX3 = 28, NYC3 = 8, NWC3 = NYC3 + 2, NTC3 = 32 * NWC3;
+constexpr int CBW3 = CX3 + 8, CBH3 = NYC3 + 4, CBOX3 = CBW3 * CBH3;
+constexpr int CFS3 = (CBOX3 * 4 + 127) / 128 * 128 / 4;  // field stride in a ring slot (128-byte multiple)
+constexpr int NSLC3 = 6;                                  // plane ring slots
+constexpr int NXS3 = 4;                                   // exchange slots (destination planes mod 4)
+constexpr int XW3 = 34;                                   // exchange row: x0 - 3 .. x0 + 30
+constexpr int NXL3 = 10;                                  // links with c_y != 0
+
+// Slot of link k among the ten links with c_y != 0, and among the nine with c_y = 0.
+__host__ __device__ constexpr int yslot3(int k) {
+  int s = 0;
+  for (int q = 0; q < k; ++q)
+    if (c3(q, 1) != 0) ++s;
+  return s;
+}
+__host__ __device__ constexpr int oslot3(int k) {
+  int s = 0;
+  for (int q = 0; q < k; ++q)
+    if (c3(q, 1) == 0) ++s;
+  return s;
+}
+
+__host__ __device__ constexpr size_t fwd3c_smem() {
+  return sizeof(float) * ((size_t)NSLC3 * NFF3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
+}
+
+// Sums of the pushed increments at a node on exactly one face, normal along axis A
+// with sign n (the face rules of the gather): s0 over links with c_A = 0, sp over
+// links pointing out of the lattice (c_A n > 0).  Off the normal's axis every
+// source is inside, so no link needs a bounds test; the sums run in link order.
+template <int A>
+__device__ __forceinline__ void face_sums3(const float (&F)[19], int n, float& s0, float& sp) {
+  float z = 0.f, p = 0.f, m = 0.f;
+  static_for<0, 19>([&](auto kk) {
+    constexpr int k = decltype(kk)::value;
+    if constexpr (c3(k, A) == 0) z += F[k];
+    else if constexpr (c3(k, A) > 0) p += F[k];
+    else m += F[k];
+  });
+  s0 = z;
+  sp = n > 0 ? p : m;
+}
+
+__global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ Maps3F maps,
+                                                        const __grid_constant__ Fwd3TArgs a, Geom3 g,
+                                                        Coef3<float> c) {
+  using R = float;
+  extern __shared__ unsigned char smem_raw3[];
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NFF3][CFS3]
+  R* ex = ring + NSLC3 * NFF3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NXL3 * XW3);
+  if (lks::timed_out_before(a.status)) return;
+  if (!lks::tma_layout_ok(ring, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
+  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, nz);
+  const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = x0 - 2 + lane, j = y0 - 1 + warp;
+  const int bx = lane + 2, by = warp + 1;  // the node's column and row in the staged box
+  const bool out_node = lane >= 2 && lane < 2 + CX3 && i < nx && warp >= 1 && warp <= NYC3 && j < ny;
+  const bool in_xy = i >= 0 && i < nx && j >= 0 && j < ny;
+  // Every thread's node, and every node whose push it reads, is off the x and y faces
+  // (lanes 1 .. 30 and warps 0 .. NYC3 + 1 push for the outputs).
+  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  auto slot = [&](int p) { return (p - pbase) % NSLC3; };
+  auto issue = [&](int p) {
+    const int sl = slot(p);
+    lks::mbar_expect_tx(&bar[sl], NFF3 * CBOX3 * 4);
+    for (int f = 0; f < NFF3; ++f)
+      tma_load_3d(ring + (sl * NFF3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+  };
+  int waited = pbase - 1, issued = pbase - 1;
+  auto wait = [&](int p) {
+    const bool ok = lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
+    if (ok) waited = p;
+    return ok;
+  };
+  auto drain_and_fail = [&]() {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0)
+      for (int p = waited + 1; p <= issued; ++p) lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
+  };
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < NSLC3; ++sl) lks::mbar_init(&bar[sl], 1);
+    lks::fence_mbar_init();
+    lks::fence_proxy_async();
+  }
+  __syncthreads();
+  for (int p = pbase; p < pbase + NSLC3 && p <= plast; ++p) {
+    if (threadIdx.x == 0) issue(p);
+    issued = p;
+  }
+  for (int p = pbase; p <= pbase + 4 && p <= plast; ++p)
+    if (!wait(p)) {
+      drain_and_fail();
+      return;
+    }
+  // zs: ring slot of the plane z being pushed; plane z + k sits in slot zs + k (mod NSLC3)
+  int zs = 2;
+  auto slk = [&](int k) {
+    const int s = zs + k;
+    return s >= NSLC3 ? s - NSLC3 : (s < 0 ? s + NSLC3 : s);
+  };
+  // field f of plane z + k at row offset dy and column offset dx from the node
+  auto at = [&](int f, int k, int dy, int dx) {
+    return ring[(slk(k) * NFF3 + f) * CFS3 + (by + dy) * CBW3 + bx + dx];
+  };
+  // exchange row `row` of destination plane p (slots by p mod NXS3)
+  auto xslot = [&](int p, int row) { return ex + ((p & (NXS3 - 1)) * NYC3 + row) * NXL3 * XW3; };
+
+  // the node's drho, u, v, w at planes z - 1 (m), z (c), z + 1 (p)
+  R dm = at(0, -1, 0, 0), um = at(1, -1, 0, 0), vm = at(2, -1, 0, 0), wm = at(3, -1, 0, 0);
+  R dc = at(0, 0, 0, 0), uc = at(1, 0, 0, 0), vc = at(2, 0, 0, 0), wc = at(3, 0, 0, 0);
+  R dp = at(0, 1, 0, 0), up = at(1, 1, 0, 0), vp = at(2, 1, 0, 0), wp = at(3, 1, 0, 0);
+  R Am[9], Ac[9], Ap[9];  // links with c_y = 0 arriving at planes z - 1, z, z + 1 (slot oslot3(k))
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Am[q] = Ac[q] = Ap[q] = R(0);
+
+  // One plane: push of plane z, then gather of plane z - 1.  FAST: no node of the
+  // tile at planes z and z - 1 lies on a face (and all of them are inside).
+  auto plane_step = [&](int z, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    const bool src = FAST || (in_xy && z >= 0 && z < nz);
+    const R dl = __shfl_up_sync(0xffffffffu, dc, 1), dr_ = __shfl_down_sync(0xffffffffu, dc, 1);
+    const R dml = __shfl_up_sync(0xffffffffu, dm, 1), dmr = __shfl_down_sync(0xffffffffu, dm, 1);
+    const R dpl = __shfl_up_sync(0xffffffffu, dp, 1), dpr = __shfl_down_sync(0xffffffffu, dp, 1);
+    R gr[3][3];  // gr[d][a] = d u_d / d x_a
+    gr[0][0] = (__shfl_down_sync(0xffffffffu, uc, 1) - __shfl_up_sync(0xffffffffu, uc, 1)) * R(0.5);
+    gr[1][0] = (__shfl_down_sync(0xffffffffu, vc, 1) - __shfl_up_sync(0xffffffffu, vc, 1)) * R(0.5);
+    gr[2][0] = (__shfl_down_sync(0xffffffffu, wc, 1) - __shfl_up_sync(0xffffffffu, wc, 1)) * R(0.5);
+    gr[0][1] = (at(1, 0, 1, 0) - at(1, 0, -1, 0)) * R(0.5);
+    gr[1][1] = (at(2, 0, 1, 0) - at(2, 0, -1, 0)) * R(0.5);
+    gr[2][1] = (at(3, 0, 1, 0) - at(3, 0, -1, 0)) * R(0.5);
+    gr[0][2] = (up - um) * R(0.5);
+    gr[1][2] = (vp - vm) * R(0.5);
+    gr[2][2] = (wp - wm) * R(0.5);
+    if constexpr (!FAST) {
+      const bool on[3] = {i == 0 || i == nx - 1, j == 0 || j == ny - 1, z == 0 || z == nz - 1};
+      if (src && (on[0] || on[1] || on[2])) {  // faces: one-sided differences and continuity
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const R* f0 = ring + (slk(0) * NFF3 + 1 + d) * CFS3 + by * CBW3 + bx;
+          if (on[0]) gr[d][0] = dax(f0, 1, i, nx);
+          if (on[1]) gr[d][1] = dax(f0, CBW3, j, ny);
+          if (on[2]) gr[d][2] = daz<R>([&](int dz) { return at(1 + d, dz, 0, 0); }, z, nz);
+        }
+        const int faces = (int)on[0] + (int)on[1] + (int)on[2];
+        if (faces == 1) {
+          if (on[0]) gr[0][0] = -(gr[1][1] + gr[2][2]);
+          else if (on[1]) gr[1][1] = -(gr[0][0] + gr[2][2]);
+          else gr[2][2] = -(gr[0][0] + gr[1][1]);
+        } else {
+#pragma unroll
+          for (int d = 0; d < 3; ++d)
+            if (on[d]) gr[d][d] = R(0);
+        }
+      }
+    }
+    const R e0 = R(-1.5) * (uc * uc + vc * vc + wc * wc);
+    const R bxv = R(3) * uc, byv = R(3) * vc, bzv = R(3) * wc;
+    const R Qxx = R(4.5) * uc * uc + c.A * (R(2) * gr[0][0]);
+    const R Qyy = R(4.5) * vc * vc + c.A * (R(2) * gr[1][1]);
+    const R Qzz = R(4.5) * wc * wc + c.A * (R(2) * gr[2][2]);
+    const R Qxy = R(9) * uc * vc + R(2) * c.A * (gr[0][1] + gr[1][0]);
+    const R Qxz = R(9) * uc * wc + R(2) * c.A * (gr[0][2] + gr[2][0]);
+    const R Qyz = R(9) * vc * wc + R(2) * c.A * (gr[1][2] + gr[2][1]);
+    R* const xr_m = xslot(z - 1, 0) + lane + 1;  // exchange rows of the destination planes
+    R* const xr_c = xslot(z, 0) + lane + 1;
+    R* const xr_p = xslot(z + 1, 0) + lane + 1;
+    const bool w_up = src && warp < NYC3, w_dn = src && warp >= 2;  // c_y = +1 / -1 lands on an output row
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+      R dest;
+      if constexpr (cy != 0) dest = at(0, cz, cy, cx);
+      else if constexpr (cx == 0) dest = cz == 0 ? dc : (cz > 0 ? dp : dm);
+      else if constexpr (cz == 0) dest = cx > 0 ? dr_ : dl;
+      else if constexpr (cz > 0) dest = cx > 0 ? dpr : dpl;
+      else dest = cx > 0 ? dmr : dml;
+      const R pv = push_link3<k>(dc, dest, e0, bxv, byv, bzv, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz);
+      const R val = FAST ? pv : (src ? pv : R(0));
+      if constexpr (cy != 0) {
+        // destination row warp - 1 + cy of the exchange
+        R* const xr = (cz < 0 ? xr_m : (cz == 0 ? xr_c : xr_p)) + ((cy > 0 ? 0 : -2) * NXL3 + yslot3(k)) * XW3 + cx;
+        if (cy > 0 ? w_up : w_dn) xr[warp * NXL3 * XW3] = val;
+      } else {
+        R v;
+        if constexpr (cx > 0) v = __shfl_up_sync(0xffffffffu, val, 1);  // sent by the lane on the left
+        else if constexpr (cx < 0) v = __shfl_down_sync(0xffffffffu, val, 1);
+        else v = val;
+        if constexpr (cz < 0) Am[oslot3(k)] = v;
+        else if constexpr (cz == 0) Ac[oslot3(k)] = v;
+        else Ap[oslot3(k)] = v;
+      }
+    });
+    __syncthreads();  // plane z's exchange writes are in; plane z - 1 is complete
+    if (z + 3 <= plast && z + 3 > issued) {  // the slot of plane z - 3 is free
+      if (threadIdx.x == 0) issue(z + 3);
+      issued = z + 3;
+    }
+    // ---- gather of node (i, j, z - 1) ----
+    const int zd = z - 1;
+    if (out_node && zd >= z0 && zd < z1) {
+      R F[19];
+      const R* xr = xslot(zd, warp - 1) + lane + 1;
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
+        else F[k] = Am[oslot3(k)];
+      });
+      const R drx = dm;
+      int n0 = 0, n1 = 0, n2 = 0, faces = 0;
+      if constexpr (!FAST) {
+        n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+        n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+        n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+        faces = abs(n0) + abs(n1) + abs(n2);
+      }
+      R drn, uo[3] = {R(0), R(0), R(0)};
+      if (FAST || faces == 0) {
+        R sm = R(0), mx = R(0), my = R(0), mz = R(0);
+        static_for<0, 19>([&](auto kk) {
+          constexpr int k = decltype(kk)::value;
+          sm += F[k];
+          if constexpr (c3(k, 0) != 0) mx += R(c3(k, 0)) * F[k];
+          if constexpr (c3(k, 1) != 0) my += R(c3(k, 1)) * F[k];
+          if constexpr (c3(k, 2) != 0) mz += R(c3(k, 2)) * F[k];
+        });
+        drn = drx + sm;
+        const R inv = at(4, -1, 0, 0);
+        uo[0] = mx * inv;
+        uo[1] = my * inv;
+        uo[2] = mz * inv;
+      } else if (faces >= 2) {
+        const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
+        const int kn = (zd == 0) ? 1 : (zd == nz - 1 ? -1 : 0);
+        drn = at(0, kn - 1, jn, 0);
+      } else {
+        R s0, sp;
+        if (n0 != 0) face_sums3<0>(F, n0, s0, sp);
+        else if (n1 != 0) face_sums3<1>(F, n1, s0, sp);
+        else face_sums3<2>(F, n2, s0, sp);
+        if (n0 == 1) {
+          drn = c.drho_out;
+          uo[0] = (s0 + R(2) * sp) + (drx - c.drho_out);
+        } else {
+          if (n0 == -1) {
+            const double y = (double)j / (double)(ny - 1), zz = (double)zd / (double)(nz - 1);
+            uo[0] = (R)(c.u_max * 16.0 * y * (1.0 - y) * zz * (1.0 - zz));
+          }
+          drn = drx + (s0 + R(2) * sp - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2)));
+        }
+      }
+      const size_t o = gidx(g, i, j, zd);
+      a.out[0][o] = drn;
+      a.out[1][o] = uo[0];
+      a.out[2][o] = uo[1];
+      a.out[3][o] = uo[2];
+      const R m = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
+      if (!(m <= R(0.25))) raise_status(a.status, 4);
+    }
+    // ---- rotate: the destination sets and the node's planes ----
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Am[q] = Ac[q];
+      Ac[q] = Ap[q];
+    }
+    dm = dc, um = uc, vm = vc, wm = wc;
+    dc = dp, uc = up, vc = vp, wc = wp;
+    if (z + 2 <= plast) dp = at(0, 2, 0, 0), up = at(1, 2, 0, 0), vp = at(2, 2, 0, 0), wp = at(3, 2, 0, 0);
+    zs = zs == NSLC3 - 1 ? 0 : zs + 1;
+  };
+
+  for (int z = z0 - 1; z <= z1; ++z) {
+    if (z + 2 <= plast && z + 2 > waited && !wait(z + 2)) {
+      drain_and_fail();
+      return;
+    }
+    if (tile_fast && z >= 2 && z <= nz - 2) plane_step(z, std::true_type{});
+    else plane_step(z, std::false_type{});
+  }
+}
+
 struct Adj3TArgs {
   float* m0[kNA3];
   const float* emap;
@@ -1126,7 +1430,7 @@ lks_status map3(const Ctx3& c, const void* ptr, int bw, int bh, CUtensorMap* m) 
 }
 
 template <typename R>
-lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur_out) {
+lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur_out, int* path_out) {
   const auto& d = *c.d;
   const auto& L = *c.L;
   const size_t fb = L.N * sizeof(R);
@@ -1144,24 +1448,40 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
   CK3(c, cudaGetLastError());
   ++*c.launches;
   int cur = 0;
+  *path_out = LKS_PATH_STEP;
   if constexpr (sizeof(R) == 4) {
     if (tma3_ok(d)) {
+      // the warp-column forward unless the per-tile kernels are asked for
+      const bool col = d.exec_path != LKS_PATH_STEP;
+      const int bw = col ? CBW3 : BW3, bh = col ? CBH3 : BH3;
       Maps3F maps[2];
       Fwd3TArgs ta[2];
       lks_status st;
       for (int b = 0; b < 2; ++b) {
         for (int f = 0; f < 4; ++f)
-          if ((st = map3(c, st3<float>(c, b, f), BW3, BH3, &maps[b].m[f])) != LKS_OK) return st;
-        if ((st = map3(c, fld3<float>(c, L.binv), BW3, BH3, &maps[b].m[4])) != LKS_OK) return st;
+          if ((st = map3(c, st3<float>(c, b, f), bw, bh, &maps[b].m[f])) != LKS_OK) return st;
+        if ((st = map3(c, fld3<float>(c, L.binv), bw, bh, &maps[b].m[4])) != LKS_OK) return st;
         for (int f = 0; f < 4; ++f) ta[b].out[f] = st3<float>(c, 1 - b, f);
         ta[b].status = reinterpret_cast<int*>(c.ws + L.status);
       }
-      CK3(c, cudaFuncSetAttribute(fwd3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3t_smem()));
-      for (int s = 0; s < d.n_steps; ++s) {
-        fwd3t_kernel<<<march_grid(d), NTF3, fwd3t_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
-        CK3(c, cudaGetLastError());
-        ++*c.launches;
-        cur = 1 - cur;
+      if (col) {
+        CK3(c, cudaFuncSetAttribute(fwd3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3c_smem()));
+        const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + ZC3 - 1) / ZC3);
+        for (int s = 0; s < d.n_steps; ++s) {
+          fwd3c_kernel<<<grid, NTC3, fwd3c_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
+          CK3(c, cudaGetLastError());
+          ++*c.launches;
+          cur = 1 - cur;
+        }
+        *path_out = LKS_PATH_COLUMN;
+      } else {
+        CK3(c, cudaFuncSetAttribute(fwd3t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3t_smem()));
+        for (int s = 0; s < d.n_steps; ++s) {
+          fwd3t_kernel<<<march_grid(d), NTF3, fwd3t_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
+          CK3(c, cudaGetLastError());
+          ++*c.launches;
+          cur = 1 - cur;
+        }
       }
     }
   }
@@ -1412,8 +1732,9 @@ lks_status upload_maps3(const Ctx3& c) {
   return LKS_OK;
 }
 
-lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur) {
-  return c.L->rsize == 8 ? forward3_t<double>(c, gamma_dev, J_dev, cur) : forward3_t<float>(c, gamma_dev, J_dev, cur);
+lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur, int* path) {
+  return c.L->rsize == 8 ? forward3_t<double>(c, gamma_dev, J_dev, cur, path)
+                         : forward3_t<float>(c, gamma_dev, J_dev, cur, path);
 }
 lks_status adjoint3(const Ctx3& c, int cur, int* acur) {
   return c.L->rsize == 8 ? adjoint3_t<double>(c, cur, acur) : adjoint3_t<float>(c, cur, acur);

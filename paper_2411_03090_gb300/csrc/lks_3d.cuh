@@ -46,8 +46,10 @@ struct Ctx3 {
 // Uploads the host-built adjoint edge maps (kClasses3 x 10 x 19).
 lks_status upload_maps3(const Ctx3& c);
 // Steps 2-3: gamma -> state after n_steps; J of the final state into J_dev (may be
-// null).  *cur receives the buffer (0 = A, 1 = B) holding the final state.
-lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur);
+// null).  *cur receives the buffer (0 = A, 1 = B) holding the final state, *path the
+// lks_exec_path that ran (column: the warp-column forward, FP32 with nx % 4 == 0
+// unless the step path is asked for).
+lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur, int* path);
 // Step 4: n_adj ALKS iterations on the frozen state `cur`; *acur receives the
 // adjoint buffer holding the result.
 lks_status adjoint3(const Ctx3& c, int cur, int* acur);

@@ -1169,11 +1169,12 @@ lks_status lks_destroy(lks_handle* h) {
 lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
   if (check_handle(h) != LKS_OK || !gamma_dev) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
   if (h->is3) {
-    const lks_status s = lks3::forward3(ctx3(h), gamma_dev, J_dev, &h->cur);
+    int path = LKS_PATH_STEP;
+    const lks_status s = lks3::forward3(ctx3(h), gamma_dev, J_dev, &h->cur, &path);
     if (s == LKS_OK) {
       h->phase = 1;
       h->fwd_steps += h->d.n_steps;
-      h->fwd_path = LKS_PATH_STEP;
+      h->fwd_path = path;
     }
     return s;
   }

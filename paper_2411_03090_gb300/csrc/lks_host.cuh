@@ -41,6 +41,7 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (!d->steady || d->thermal) return bad("D3Q19: steady, non-thermal problems only");
     if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
     if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
+    if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
     for (int q = 0; q < 4; ++q)
       if (d->reserved[q] != 0) return bad("reserved fields must be zero");
     return LKS_OK;

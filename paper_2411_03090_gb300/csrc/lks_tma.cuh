@@ -64,9 +64,11 @@ __device__ __forceinline__ bool timed_out_before(const int* status) {
   return status && *reinterpret_cast<const volatile int*>(status) == 6;
 }
 // Dynamic shared memory rounded up to 128 bytes (tensor copies need a 128-byte
-// aligned shared destination); the kernels declare no static shared memory.
+// aligned shared destination); the kernels declare no static shared memory.  The
+// offset is added to the shared array itself, not through an integer round trip,
+// so that the compiler keeps every access derived from it in the shared space.
 __device__ __forceinline__ unsigned char* smem_base128(unsigned char* raw) {
-  return reinterpret_cast<unsigned char*>((reinterpret_cast<uintptr_t>(raw) + 127) & ~uintptr_t(127));
+  return raw + ((128u - (smem_u32(raw) & 127u)) & 127u);
 }
 // Self-check before any copy: the stages 128-byte and the mbarriers 8-byte aligned.
 __device__ __forceinline__ bool tma_layout_ok(const void* stage, const void* bar, int* status) {

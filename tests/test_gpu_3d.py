@@ -42,14 +42,17 @@ def to_state(fields):
     return s
 
 
+@pytest.mark.parametrize("path", ["auto", "step"])
 @pytest.mark.parametrize("real,tol_f,tol_g,tol_J", [("f64", 1e-10, 1e-10, 1e-11), ("f32", 1e-5, 1e-3, 1e-5)])
 @pytest.mark.parametrize("shape", [(37, 21, 40), (24, 16, 11), (44, 21, 40)])
-def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape):
+def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape, path):
     pb = duct(*shape)
     g = pb.gamma()
     ref = O.steady_gradient3(pb, g)
-    s = LKS(pb, real=real)
+    s = LKS(pb, real=real, path=path)
     J, grad = s.gradient(torch.from_numpy(g))
+    tma = real == "f32" and shape[0] % 4 == 0
+    assert s.query().fwd_path == (3 if tma and path == "auto" else 1)
     st = to_state(s.get_state())
     for name in ("u", "v", "w"):
         assert rel_l2(getattr(st, name), getattr(ref["state"], name)) <= tol_f, name
@@ -61,6 +64,31 @@ def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape):
     gr = grad.double().cpu().numpy()
     assert rel_l2(gr, ref["dJdgamma"]) <= tol_g
     assert np.all(gr[0] == 0) and np.all(gr[:, 0] == 0) and np.all(gr[:, :, 0] == 0)
+
+
+@pytest.mark.parametrize("shape", [(60, 17, 37), (28, 8, 5), (44, 21, 40), (88, 9, 70), (116, 40, 37)])
+def test_column_forward_matches_step_forward_and_oracle(shape):
+    """The warp-column z-march forward (28 x 8 tiles, ragged in x, y and z) against
+    the plane-march forward and the oracle's state after the same steps.  116 x 40
+    has tiles whose threads are all off the x and y faces (the fast variant)."""
+    pb = duct(*shape, n=40)
+    g = pb.gamma()
+    gt = torch.from_numpy(g)
+    ref = O.forward3(pb, g, pb.n_steps)[0]
+    st = {}
+    for path in ("column", "step"):
+        s = LKS(pb, real="f32", path=path)
+        s.lks_forward(gt)
+        assert s.query().fwd_path == (3 if path == "column" else 1)
+        assert s.query().device_status == 0
+        st[path] = [f.double().cpu().numpy() for f in s.get_state()]
+    scale = max(np.abs(st["step"][1]).max(), 1e-30)
+    for c in range(4):
+        assert np.abs(st["column"][c] - st["step"][c]).max() <= 1e-6 * (1.0 if c == 0 else scale), c
+    col = to_state([torch.from_numpy(x) for x in st["column"]])
+    for name in ("u", "v", "w"):
+        assert rel_l2(getattr(col, name), getattr(ref, name)) <= 1e-5, name
+    assert rel_l2(col.rho - 1, ref.rho - 1) <= 1e-4
 
 
 def test_gradient_host_and_query():
@@ -86,18 +114,21 @@ def _sample_nodes(pb, rng, n_interior=40):
     return sorted(nodes)
 
 
-def test_config4_full_size_one_step_sampled():
+@pytest.mark.parametrize("path", ["auto", "step"])
+def test_config4_full_size_one_step_sampled(path):
     """192^3, FP32: one forward step and one adjoint step at sampled nodes equal
-    the oracle's node updates from the GPU's previous level (FP32 tolerance)."""
+    the oracle's node updates from the GPU's previous level (FP32 tolerance), on
+    the warp-column forward (auto) and on the plane-march forward (step)."""
     pb = inputs.config4().with_(n_steps=3, n_adj=1)
     g = pb.gamma()
     gt = torch.from_numpy(g)
-    s2 = LKS(pb.with_(n_steps=2), real="f32")
+    s2 = LKS(pb.with_(n_steps=2), real="f32", path=path)
     s2.lks_forward(gt)
     prev = to_state(s2.get_state())
     del s2
-    s = LKS(pb, real="f32")
+    s = LKS(pb, real="f32", path=path)
     s.lks_forward(gt)
+    assert s.query().fwd_path == (3 if path == "auto" else 1)
     cur = [f.double().cpu().numpy() for f in s.get_state()]
     rng = np.random.default_rng(4)
     nodes = _sample_nodes(pb, rng)
@@ -112,7 +143,7 @@ def test_config4_full_size_one_step_sampled():
     st = to_state([torch.from_numpy(x) for x in cur])
     s.alks_adjoint()
     a1 = np.stack([a.double().cpu().numpy() for a in s.get_adjoint()])
-    s_b = LKS(pb.with_(n_adj=2), real="f32")
+    s_b = LKS(pb.with_(n_adj=2), real="f32", path=path)
     s_b.lks_forward(gt)
     s_b.alks_adjoint()
     a2 = np.stack([a.double().cpu().numpy() for a in s_b.get_adjoint()])
