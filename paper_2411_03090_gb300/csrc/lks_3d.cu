@@ -542,7 +542,9 @@ __host__ __device__ constexpr size_t adj3t_smem() {
 
 struct Fwd3TArgs {
   float* out[4];
+  const float* binv;  // 1/(1+alpha) per node (read by the warp-column forward)
   int* status;
+  int zc;             // z planes per CTA of the warp-column forward
 };
 
 __global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ Maps3F maps, const __grid_constant__ Fwd3TArgs a,
@@ -759,8 +761,10 @@ __global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ 
 // Lanes run along x (one column each; lanes 2..29 write, so a tile is 28 columns
 // wide), warp w owns row y0 - 1 + w (rows y0 .. y0 + NYC3 - 1 are outputs; the two
 // outer warps are halo rows whose pushes feed the tile), and the CTA marches a
-// chunk of z planes.  Planes arrive by 3-D tensor copies into a ring of NSLC3 slots
-// (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)).  For each source plane z a lane
+// chunk of z planes.  The fields drho, u, v, w of each plane arrive by 3-D tensor
+// copies into a ring of NSLC3 slots (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)),
+// requested three planes before they are first read; 1/(1+alpha) of an output node
+// is one global load, issued a plane ahead.  For each source plane z a lane
 // computes the 19 pushed increments of its node (push_link3, Eq. feq2) and routes
 // each at once:
 //   - the 9 links with c_y = 0 stay in the warp: c_x by shuffle, c_z through a
@@ -776,9 +780,10 @@ __global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ 
 constexpr int CX3 = 28, NYC3 = 8, NWC3 = NYC3 + 2, NTC3 = 32 * NWC3;
 constexpr int CBW3 = CX3 + 8, CBH3 = NYC3 + 4, CBOX3 = CBW3 * CBH3;
 constexpr int CFS3 = (CBOX3 * 4 + 127) / 128 * 128 / 4;  // field stride in a ring slot (128-byte multiple)
-constexpr int NSLC3 = 6;                                  // plane ring slots
+constexpr int NFC3 = 4;                                   // ring fields: drho, u, v, w
+constexpr int NSLC3 = 8;                                  // plane ring slots (planes z - 2 .. z + 5)
 constexpr int NXS3 = 4;                                   // exchange slots (destination planes mod 4)
-constexpr int XW3 = 34;                                   // exchange row: x0 - 3 .. x0 + 30
+constexpr int XW3 = CX3;                                  // exchange row: the output columns x0 .. x0 + 27
 constexpr int NXL3 = 10;                                  // links with c_y != 0
 
 // Slot of link k among the ten links with c_y != 0, and among the nine with c_y = 0.
@@ -796,7 +801,7 @@ __host__ __device__ constexpr int oslot3(int k) {
 }
 
 __host__ __device__ constexpr size_t fwd3c_smem() {
-  return sizeof(float) * ((size_t)NSLC3 * NFF3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
+  return sizeof(float) * ((size_t)NSLC3 * NFC3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
 }
 
 // Sums of the pushed increments at a node on exactly one face, normal along axis A
@@ -821,14 +826,14 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
                                                         Coef3<float> c) {
   using R = float;
   extern __shared__ unsigned char smem_raw3[];
-  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NFF3][CFS3]
-  R* ex = ring + NSLC3 * NFF3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NFC3][CFS3]
+  R* ex = ring + NSLC3 * NFC3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
   uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NXL3 * XW3);
   if (lks::timed_out_before(a.status)) return;
   if (!lks::tma_layout_ok(ring, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
   const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
-  const int z0 = blockIdx.z * ZC3, z1 = min(z0 + ZC3, nz);
+  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, nz);
   const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int i = x0 - 2 + lane, j = y0 - 1 + warp;
@@ -838,12 +843,13 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
   // Every thread's node, and every node whose push it reads, is off the x and y faces
   // (lanes 1 .. 30 and warps 0 .. NYC3 + 1 push for the outputs).
   const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
-  auto slot = [&](int p) { return (p - pbase) % NSLC3; };
+  static_assert((NSLC3 & (NSLC3 - 1)) == 0, "ring slots index by mask");
+  auto slot = [&](int p) { return (p - pbase) & (NSLC3 - 1); };
   auto issue = [&](int p) {
     const int sl = slot(p);
-    lks::mbar_expect_tx(&bar[sl], NFF3 * CBOX3 * 4);
-    for (int f = 0; f < NFF3; ++f)
-      tma_load_3d(ring + (sl * NFF3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+    lks::mbar_expect_tx(&bar[sl], NFC3 * CBOX3 * 4);
+    for (int f = 0; f < NFC3; ++f)
+      tma_load_3d(ring + (sl * NFC3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
   };
   int waited = pbase - 1, issued = pbase - 1;
   auto wait = [&](int p) {
@@ -873,16 +879,18 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
     }
   // zs: ring slot of the plane z being pushed; plane z + k sits in slot zs + k (mod NSLC3)
   int zs = 2;
-  auto slk = [&](int k) {
-    const int s = zs + k;
-    return s >= NSLC3 ? s - NSLC3 : (s < 0 ? s + NSLC3 : s);
-  };
+  auto slk = [&](int k) { return (zs + k) & (NSLC3 - 1); };
   // field f of plane z + k at row offset dy and column offset dx from the node
   auto at = [&](int f, int k, int dy, int dx) {
-    return ring[(slk(k) * NFF3 + f) * CFS3 + (by + dy) * CBW3 + bx + dx];
+    return ring[(slk(k) * NFC3 + f) * CFS3 + (by + dy) * CBW3 + bx + dx];
   };
   // exchange row `row` of destination plane p (slots by p mod NXS3)
   auto xslot = [&](int p, int row) { return ex + ((p & (NXS3 - 1)) * NYC3 + row) * NXL3 * XW3; };
+  // 1/(1+alpha) of the output node at plane p (loaded one plane before the gather reads it)
+  auto binv_at = [&](int p) {
+    return (out_node && p >= 0 && p < nz) ? __ldg(a.binv + gidx(g, i, j, p)) : R(0);
+  };
+  R inv_n = binv_at(z0 - 1);  // for the gather of plane z - 1 at step z
 
   // the node's drho, u, v, w at planes z - 1 (m), z (c), z + 1 (p)
   R dm = at(0, -1, 0, 0), um = at(1, -1, 0, 0), vm = at(2, -1, 0, 0), wm = at(3, -1, 0, 0);
@@ -915,7 +923,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       if (src && (on[0] || on[1] || on[2])) {  // faces: one-sided differences and continuity
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
-          const R* f0 = ring + (slk(0) * NFF3 + 1 + d) * CFS3 + by * CBW3 + bx;
+          const R* f0 = ring + (slk(0) * NFC3 + 1 + d) * CFS3 + by * CBW3 + bx;
           if (on[0]) gr[d][0] = dax(f0, 1, i, nx);
           if (on[1]) gr[d][1] = dax(f0, CBW3, j, ny);
           if (on[2]) gr[d][2] = daz<R>([&](int dz) { return at(1 + d, dz, 0, 0); }, z, nz);
@@ -940,10 +948,15 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
     const R Qxy = R(9) * uc * vc + R(2) * c.A * (gr[0][1] + gr[1][0]);
     const R Qxz = R(9) * uc * wc + R(2) * c.A * (gr[0][2] + gr[2][0]);
     const R Qyz = R(9) * vc * wc + R(2) * c.A * (gr[1][2] + gr[2][1]);
-    R* const xr_m = xslot(z - 1, 0) + lane + 1;  // exchange rows of the destination planes
-    R* const xr_c = xslot(z, 0) + lane + 1;
-    R* const xr_p = xslot(z + 1, 0) + lane + 1;
+    const R inv_c = inv_n;  // 1/(1+alpha) of node (i, j, z - 1)
+    inv_n = binv_at(z);
+    R* const xr_m = xslot(z - 1, 0) + lane - 2;  // exchange rows of the destination planes
+    R* const xr_c = xslot(z, 0) + lane - 2;
+    R* const xr_p = xslot(z + 1, 0) + lane - 2;
     const bool w_up = src && warp < NYC3, w_dn = src && warp >= 2;  // c_y = +1 / -1 lands on an output row
+    // destination lane lane + c_x is an output column (lanes 2 .. 29)
+    const bool xl_m = lane >= 3 && lane <= CX3 + 2, xl_c = lane >= 2 && lane <= CX3 + 1,
+               xl_p = lane >= 1 && lane <= CX3;
     static_for<0, 19>([&](auto kk) {
       constexpr int k = decltype(kk)::value;
       constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
@@ -958,7 +971,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       if constexpr (cy != 0) {
         // destination row warp - 1 + cy of the exchange
         R* const xr = (cz < 0 ? xr_m : (cz == 0 ? xr_c : xr_p)) + ((cy > 0 ? 0 : -2) * NXL3 + yslot3(k)) * XW3 + cx;
-        if (cy > 0 ? w_up : w_dn) xr[warp * NXL3 * XW3] = val;
+        if ((cy > 0 ? w_up : w_dn) && (cx < 0 ? xl_m : (cx == 0 ? xl_c : xl_p))) xr[warp * NXL3 * XW3] = val;
       } else {
         R v;
         if constexpr (cx > 0) v = __shfl_up_sync(0xffffffffu, val, 1);  // sent by the lane on the left
@@ -970,15 +983,15 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       }
     });
     __syncthreads();  // plane z's exchange writes are in; plane z - 1 is complete
-    if (z + 3 <= plast && z + 3 > issued) {  // the slot of plane z - 3 is free
-      if (threadIdx.x == 0) issue(z + 3);
-      issued = z + 3;
+    if (z + NSLC3 - 3 <= plast && z + NSLC3 - 3 > issued) {  // the slot of plane z - 3 is free
+      if (threadIdx.x == 0) issue(z + NSLC3 - 3);
+      issued = z + NSLC3 - 3;
     }
     // ---- gather of node (i, j, z - 1) ----
     const int zd = z - 1;
     if (out_node && zd >= z0 && zd < z1) {
       R F[19];
-      const R* xr = xslot(zd, warp - 1) + lane + 1;
+      const R* xr = xslot(zd, warp - 1) + lane - 2;
       static_for<0, 19>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
@@ -1003,10 +1016,9 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
           if constexpr (c3(k, 2) != 0) mz += R(c3(k, 2)) * F[k];
         });
         drn = drx + sm;
-        const R inv = at(4, -1, 0, 0);
-        uo[0] = mx * inv;
-        uo[1] = my * inv;
-        uo[2] = mz * inv;
+        uo[0] = mx * inv_c;
+        uo[1] = my * inv_c;
+        uo[2] = mz * inv_c;
       } else if (faces >= 2) {
         const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
         const int kn = (zd == 0) ? 1 : (zd == nz - 1 ? -1 : 0);
@@ -1044,7 +1056,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
     dm = dc, um = uc, vm = vc, wm = wc;
     dc = dp, uc = up, vc = vp, wc = wp;
     if (z + 2 <= plast) dp = at(0, 2, 0, 0), up = at(1, 2, 0, 0), vp = at(2, 2, 0, 0), wp = at(3, 2, 0, 0);
-    zs = zs == NSLC3 - 1 ? 0 : zs + 1;
+    zs = (zs + 1) & (NSLC3 - 1);
   };
 
   for (int z = z0 - 1; z <= z1; ++z) {
@@ -1408,6 +1420,22 @@ R* ad3(const Ctx3& c, int which, int f) {
   return fld3<R>(c, which == 0 ? c.L->adA : c.L->adB, f);
 }
 int ew_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+// z planes per CTA of the warp-column forward.  A CTA pushes its chunk and one halo
+// plane on each side; the CTAs run in rounds of `resident` (every SM's resident
+// CTAs), so the march takes about rounds x (zc + 2) plane steps.  The smallest such
+// cost over zc in 8 .. 64 avoids a nearly empty last round.
+int col_chunk3(const lks_problem_desc& d, int resident) {
+  const long long txy = (long long)((d.nx + CX3 - 1) / CX3) * ((d.ny + NYC3 - 1) / NYC3);
+  int best = ZC3;
+  long long best_cost = -1;
+  for (int zc = 8; zc <= 64; ++zc) {
+    const long long ctas = txy * ((d.nz + zc - 1) / zc);
+    const long long cost = (ctas + resident - 1) / resident * (zc + 2);
+    if (best_cost < 0 || cost < best_cost) best_cost = cost, best = zc;
+  }
+  return best;
+}
+
 dim3 march_grid(const lks_problem_desc& d) {
   return dim3((d.nx + TX3 - 1) / TX3, (d.ny + TY3 - 1) / TY3, (d.nz + ZC3 - 1) / ZC3);
 }
@@ -1462,11 +1490,18 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
           if ((st = map3(c, st3<float>(c, b, f), bw, bh, &maps[b].m[f])) != LKS_OK) return st;
         if ((st = map3(c, fld3<float>(c, L.binv), bw, bh, &maps[b].m[4])) != LKS_OK) return st;
         for (int f = 0; f < 4; ++f) ta[b].out[f] = st3<float>(c, 1 - b, f);
+        ta[b].binv = fld3<float>(c, L.binv);
         ta[b].status = reinterpret_cast<int*>(c.ws + L.status);
       }
       if (col) {
         CK3(c, cudaFuncSetAttribute(fwd3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3c_smem()));
-        const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + ZC3 - 1) / ZC3);
+        int dev = 0, sms = 0, per_sm = 0;
+        CK3(c, cudaGetDevice(&dev));
+        CK3(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd3c_kernel, NTC3, fwd3c_smem()));
+        const int zc = col_chunk3(d, std::max(1, sms * per_sm));
+        ta[0].zc = ta[1].zc = zc;
+        const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + zc - 1) / zc);
         for (int s = 0; s < d.n_steps; ++s) {
           fwd3c_kernel<<<grid, NTC3, fwd3c_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
           CK3(c, cudaGetLastError());
