@@ -527,7 +527,7 @@ def main():
     fwd_k = kname.get(st.fwd_path, kname[1])[1]
     if three_d:
         tma3 = pb.nx % 4 == 0
-        adj_k = "adj3t_kernel" if tma3 else "adj3_kernel<float>"
+        adj_k = ("adj3c_kernel" if st.adj_path == 3 else "adj3t_kernel") if tma3 else "adj3_kernel<float>"
         fwd_k = ("fwd3c_kernel" if st.fwd_path == 3 else "fwd3t_kernel") if tma3 else "fwd3_kernel<float>"
     roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
                 "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,

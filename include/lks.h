@@ -63,9 +63,9 @@ typedef enum { LKS_SNAP_F32 = 0, LKS_SNAP_BF16 = 1, LKS_SNAP_F16 = 2 } lks_snap_
  * the shared memory of its CTA (lattices whose tiles fit the GPU at once).  COLUMN:
  * one launch per step of the warp-column kernels at any size (FP32, non-thermal,
  * nx % 4 == 0; otherwise as STEP).  AUTO: RESIDENT where it fits, else STEP.
- * D3Q19 lattices (FP32, nx % 4 == 0): STEP runs the forward on the plane-march
- * kernel; every other value runs it on the warp-column z-march kernel; the
- * adjoint always runs on the plane-march kernel. */
+ * D3Q19 lattices (FP32, nx % 4 == 0): STEP runs the forward and the adjoint on
+ * the plane-march kernels; every other value runs both on the warp-column z-march
+ * kernels. */
 typedef enum {
   LKS_PATH_AUTO = 0,
   LKS_PATH_STEP = 1,

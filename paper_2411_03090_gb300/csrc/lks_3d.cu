@@ -1292,6 +1292,287 @@ __global__ void __launch_bounds__(NTF3, 2) adj3t_kernel(const __grid_constant__ 
   if (!ok) drain_and_fail();
 }
 
+// ---------------------------------------------------------------------------------
+// Warp-column D3Q19 steady adjoint (FP32)
+// ---------------------------------------------------------------------------------
+// The tiles, lanes, warps and z chunks of the warp-column forward.  The ALKS step of
+// a node gathers, over its 19 links, P + c_k . V taken at the neighbour x + c_k
+// (Sec. 2.5).  Here every node forms its own P, V and the 19 values P + c_k . V, and
+// routes value k to x - c_k: links with c_y = 0 by shuffles along x and a register
+// ring of destination planes along z, the ten others through the shared exchange
+// (indexed by destination plane mod NXS3).  Only the fields with y stencils (s~xy,
+// s~yy, s~yz) are staged by tensor copies; a lane loads the other fields of its own
+// node (coalesced along x) a plane before it uses them.  Sources outside the lattice
+// route zeros, so every exchange entry an output reads is rewritten each step.
+constexpr int NAY3 = 3;  // staged fields: s~xy, s~yy, s~yz
+
+__host__ __device__ constexpr size_t adj3c_smem() {
+  return sizeof(float) * ((size_t)NSLC3 * NAY3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
+}
+
+struct Adj3CArgs {
+  const float* own[10];  // previous level rho~, u~x, u~y, u~z, s~xx, s~xz, s~zz; frozen u, v, w
+  const float* cf[4];    // 1/(1+alpha), src x, src y, src z
+  float* m0[kNA3];       // adjoint at the new level
+  const float* emap;
+  int* status;
+  int zc;  // z planes per CTA
+};
+
+// d/dx at node `at` of n from values at offsets 0, +-1, +-2 (one-sided on a face),
+// the same formulas as dax.
+__device__ __forceinline__ float dax_v(float f0, float fp1, float fp2, float fm1, float fm2, int at, int n) {
+  if (at == 0) return (-3.f * f0 + 4.f * fp1 - fp2) * 0.5f;
+  if (at == n - 1) return (3.f * f0 - 4.f * fm1 + fm2) * 0.5f;
+  return (fp1 - fm1) * 0.5f;
+}
+
+__global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ Maps3F maps,
+                                                        const __grid_constant__ Adj3CArgs a, Geom3 g,
+                                                        Coef3<float> c) {
+  using R = float;
+  extern __shared__ unsigned char smem_raw3[];
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NAY3][CFS3]
+  R* ex = ring + NSLC3 * NAY3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NXL3 * XW3);
+  if (lks::timed_out_before(a.status)) return;
+  if (!lks::tma_layout_ok(ring, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
+  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, nz);
+  const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = x0 - 2 + lane, j = y0 - 1 + warp;
+  const int bx = lane + 2, by = warp + 1;  // the node's column and row in the staged box
+  const bool out_node = lane >= 2 && lane < 2 + CX3 && i < nx && warp >= 1 && warp <= NYC3 && j < ny;
+  const bool in_xy = i >= 0 && i < nx && j >= 0 && j < ny;
+  // lanes 0 .. 31 and warps 0 .. NYC3 + 1 inside the lattice, lanes 1 .. 30 and all
+  // warps off the x and y faces
+  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  static_assert((NSLC3 & (NSLC3 - 1)) == 0, "ring slots index by mask");
+  auto slot = [&](int p) { return (p - pbase) & (NSLC3 - 1); };
+  auto issue = [&](int p) {
+    const int sl = slot(p);
+    lks::mbar_expect_tx(&bar[sl], NAY3 * CBOX3 * 4);
+    for (int f = 0; f < NAY3; ++f)
+      tma_load_3d(ring + (sl * NAY3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+  };
+  int waited = pbase - 1, issued = pbase - 1;
+  auto wait = [&](int p) {
+    const bool ok = lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
+    if (ok) waited = p;
+    return ok;
+  };
+  auto drain_and_fail = [&]() {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0)
+      for (int p = waited + 1; p <= issued; ++p) lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
+  };
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < NSLC3; ++sl) lks::mbar_init(&bar[sl], 1);
+    lks::fence_mbar_init();
+    lks::fence_proxy_async();
+  }
+  __syncthreads();
+  for (int p = pbase; p < pbase + NSLC3 && p <= plast; ++p) {
+    if (threadIdx.x == 0) issue(p);
+    issued = p;
+  }
+  for (int p = pbase; p <= pbase + 4 && p <= plast; ++p)
+    if (!wait(p)) {
+      drain_and_fail();
+      return;
+    }
+  int zs = 2;  // ring slot of the plane z being formed; plane z + k sits in slot zs + k
+  auto slk = [&](int k) { return (zs + k) & (NSLC3 - 1); };
+  // staged field f (0 s~xy, 1 s~yy, 2 s~yz) of plane z + k at row dy, column dx from the node
+  auto at = [&](int f, int k, int dy, int dx) {
+    return ring[(slk(k) * NAY3 + f) * CFS3 + (by + dy) * CBW3 + bx + dx];
+  };
+  auto xslot = [&](int p, int row) { return ex + ((p & (NXS3 - 1)) * NYC3 + row) * NXL3 * XW3; };
+  // a field of the node at plane p; zero outside the lattice
+  auto ld = [&](const float* f, int p) { return (in_xy && p >= 0 && p < nz) ? __ldg(f + gidx(g, i, j, p)) : R(0); };
+  constexpr int kOwn[8] = {0, 1, 2, 3, 4, 7, 8, 9};  // rho~, u~x, u~y, u~z, s~xx, u, v, w
+  R cr[8], nr[8];  // those fields of the node at planes z and z + 1
+#pragma unroll
+  for (int q = 0; q < 8; ++q) cr[q] = ld(a.own[kOwn[q]], z0 - 1);
+  // s~xz and s~zz of the node at planes z - 1, z, z + 1
+  R xz_m = ld(a.own[5], z0 - 2), xz_c = ld(a.own[5], z0 - 1), xz_p = ld(a.own[5], z0);
+  R zz_m = ld(a.own[6], z0 - 2), zz_c = ld(a.own[6], z0 - 1), zz_p = ld(a.own[6], z0);
+  R Am[9], Ac[9], Ap[9];  // links with c_y = 0 arriving at planes z - 1, z, z + 1 (slot oslot3(k))
+#pragma unroll
+  for (int q = 0; q < 9; ++q) Am[q] = Ac[q] = Ap[q] = R(0);
+
+  // One plane: P, V and the routed values of plane z, then the gather of plane z - 1.
+  // FAST: no node of the tile at planes z and z - 1 lies on a face (all are inside).
+  auto plane_step = [&](int z, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    const bool src = FAST || (in_xy && z >= 0 && z < nz);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) nr[q] = ld(a.own[kOwn[q]], z + 1);
+    const R xz_n = ld(a.own[5], z + 2), zz_n = ld(a.own[6], z + 2);
+    const int zd = z - 1;
+    const bool gat = out_node && zd >= z0 && zd < z1;
+    R C[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) C[q] = gat ? ld(a.cf[q], zd) : R(0);
+
+    // ---- P and V of node (i, j, z) ----
+    const R rt = cr[0], ux = cr[1], uy = cr[2], uz = cr[3], vxx = cr[4], u0 = cr[5], u1 = cr[6], u2 = cr[7];
+    const R vxy = at(0, 0, 0, 0), vyy = at(1, 0, 0, 0), vyz = at(2, 0, 0, 0), vxz = xz_c, vzz = zz_c;
+    const R xx_r = __shfl_down_sync(0xffffffffu, vxx, 1), xx_l = __shfl_up_sync(0xffffffffu, vxx, 1);
+    const R xz_r = __shfl_down_sync(0xffffffffu, vxz, 1), xz_l = __shfl_up_sync(0xffffffffu, vxz, 1);
+    R d_xx_x = (xx_r - xx_l) * R(0.5);
+    R d_xy_x = (at(0, 0, 0, 1) - at(0, 0, 0, -1)) * R(0.5);
+    R d_xz_x = (xz_r - xz_l) * R(0.5);
+    R d_xy_y = (at(0, 0, 1, 0) - at(0, 0, -1, 0)) * R(0.5);
+    R d_yy_y = (at(1, 0, 1, 0) - at(1, 0, -1, 0)) * R(0.5);
+    R d_yz_y = (at(2, 0, 1, 0) - at(2, 0, -1, 0)) * R(0.5);
+    R d_xz_z = (xz_p - xz_m) * R(0.5);
+    R d_yz_z = (at(2, 1, 0, 0) - at(2, -1, 0, 0)) * R(0.5);
+    R d_zz_z = (zz_p - zz_m) * R(0.5);
+    if constexpr (!FAST) {
+      // one-sided differences on the faces (x: two lanes away, by shuffles of the whole warp)
+      const R xx_r2 = __shfl_down_sync(0xffffffffu, vxx, 2), xx_l2 = __shfl_up_sync(0xffffffffu, vxx, 2);
+      const R xz_r2 = __shfl_down_sync(0xffffffffu, vxz, 2), xz_l2 = __shfl_up_sync(0xffffffffu, vxz, 2);
+      if (src && (i == 0 || i == nx - 1)) {
+        d_xx_x = dax_v(vxx, xx_r, xx_r2, xx_l, xx_l2, i, nx);
+        d_xz_x = dax_v(vxz, xz_r, xz_r2, xz_l, xz_l2, i, nx);
+        d_xy_x = dax(&ring[(slk(0) * NAY3 + 0) * CFS3 + by * CBW3 + bx], 1, i, nx);
+      }
+      if (src && (j == 0 || j == ny - 1)) {
+        d_xy_y = dax(&ring[(slk(0) * NAY3 + 0) * CFS3 + by * CBW3 + bx], CBW3, j, ny);
+        d_yy_y = dax(&ring[(slk(0) * NAY3 + 1) * CFS3 + by * CBW3 + bx], CBW3, j, ny);
+        d_yz_y = dax(&ring[(slk(0) * NAY3 + 2) * CFS3 + by * CBW3 + bx], CBW3, j, ny);
+      }
+      if (src && (z == 0 || z == nz - 1)) {
+        d_xz_z = daz<R>([&](int dz) { return dz == 0 ? xz_c : dz == 1 ? xz_p : dz == -1 ? xz_m : ld(a.own[5], z + dz); },
+                        z, nz);
+        d_yz_z = daz<R>([&](int dz) { return at(2, dz, 0, 0); }, z, nz);
+        d_zz_z = daz<R>([&](int dz) { return dz == 0 ? zz_c : dz == 1 ? zz_p : dz == -1 ? zz_m : ld(a.own[6], z + dz); },
+                        z, nz);
+      }
+    }
+    const R Dx = R(2) * (d_xx_x + d_xy_y + d_xz_z);
+    const R Dy = R(2) * (d_xy_x + d_yy_y + d_yz_z);
+    const R Dz = R(2) * (d_xz_x + d_yz_y + d_zz_z);
+    R P = rt;
+    R Vx = R(3) * (ux + R(3) * (vxx * u0 + vxy * u1 + vxz * u2) - rt * u0) - c.A * Dx;
+    R Vy = R(3) * (uy + R(3) * (vxy * u0 + vyy * u1 + vyz * u2) - rt * u1) - c.A * Dy;
+    R Vz = R(3) * (uz + R(3) * (vxz * u0 + vyz * u1 + vzz * u2) - rt * u2) - c.A * Dz;
+    if constexpr (!FAST) {
+      if (!src) P = Vx = Vy = Vz = R(0);
+    }
+
+    // ---- P + c_k . V of node (i, j, z), routed to (i, j, z) - c_k ----
+    R* const xr_m = xslot(z - 1, 0) + lane - 2;  // exchange rows of the destination planes
+    R* const xr_c = xslot(z, 0) + lane - 2;
+    R* const xr_p = xslot(z + 1, 0) + lane - 2;
+    // destination row warp - 1 - c_y and lane lane - c_x are an output row and column
+    const bool r_dn = warp >= 2, r_up = warp < NYC3;
+    const bool xl_r = lane >= 3 && lane <= CX3 + 2, xl_c = lane >= 2 && lane <= CX3 + 1, xl_l = lane >= 1 && lane <= CX3;
+    static_for<0, 19>([&](auto kk) {
+      constexpr int k = decltype(kk)::value;
+      constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+      R v = P;
+      if constexpr (cx != 0) v += R(cx) * Vx;
+      if constexpr (cy != 0) v += R(cy) * Vy;
+      if constexpr (cz != 0) v += R(cz) * Vz;
+      if constexpr (cy != 0) {
+        R* const xr = (cz > 0 ? xr_m : (cz == 0 ? xr_c : xr_p)) + ((cy > 0 ? -2 : 0) * NXL3 + yslot3(k)) * XW3 - cx;
+        if ((cy > 0 ? r_dn : r_up) && (cx > 0 ? xl_r : (cx == 0 ? xl_c : xl_l))) xr[warp * NXL3 * XW3] = v;
+      } else {
+        R w;
+        if constexpr (cx > 0) w = __shfl_down_sync(0xffffffffu, v, 1);  // from the lane on the right
+        else if constexpr (cx < 0) w = __shfl_up_sync(0xffffffffu, v, 1);
+        else w = v;
+        if constexpr (cz > 0) Am[oslot3(k)] = w;
+        else if constexpr (cz == 0) Ac[oslot3(k)] = w;
+        else Ap[oslot3(k)] = w;
+      }
+    });
+    __syncthreads();  // plane z's exchange writes are in; plane z - 1 is complete
+    if (z + NSLC3 - 3 <= plast && z + NSLC3 - 3 > issued) {  // the slot of plane z - 3 is free
+      if (threadIdx.x == 0) issue(z + NSLC3 - 3);
+      issued = z + NSLC3 - 3;
+    }
+    // ---- gather of node (i, j, z - 1) ----
+    if (gat) {
+      R F[19];
+      const R* xr = xslot(zd, warp - 1) + lane - 2;
+      static_for<0, 19>([&](auto kk) {
+        constexpr int k = decltype(kk)::value;
+        if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
+        else F[k] = Am[oslot3(k)];
+      });
+      int n0 = 0, n1 = 0, n2 = 0;
+      if constexpr (!FAST) {
+        n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+        n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+        n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+      }
+      R m[kNA3];
+      if (FAST || (n0 | n1 | n2) == 0) {
+#pragma unroll
+        for (int r = 0; r < kNA3; ++r) m[r] = R(0);
+        static_for<0, 19>([&](auto kk) {
+          constexpr int k = decltype(kk)::value;
+          constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+          const R wf = R(w3d(k)) * F[k];
+          m[0] += wf;
+          if constexpr (cx != 0) m[1] += R(cx) * wf;
+          if constexpr (cy != 0) m[2] += R(cy) * wf;
+          if constexpr (cz != 0) m[3] += R(cz) * wf;
+          if constexpr (cx != 0) m[4] += wf;
+          if constexpr (cx * cy != 0) m[5] += R(cx * cy) * wf;
+          if constexpr (cx * cz != 0) m[6] += R(cx * cz) * wf;
+          if constexpr (cy != 0) m[7] += wf;
+          if constexpr (cy * cz != 0) m[8] += R(cy * cz) * wf;
+          if constexpr (cz != 0) m[9] += wf;
+        });
+        m[1] = (m[1] + C[1]) * C[0];
+        m[2] = (m[2] + C[2]) * C[0];
+        m[3] = (m[3] + C[3]) * C[0];
+      } else {
+        const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+#pragma unroll
+        for (int r = 0; r < kNA3; ++r) {
+          R sacc = R(0);
+          static_for<0, 19>([&](auto kk) {
+            constexpr int k = decltype(kk)::value;
+            sacc += M[r * 19 + k] * F[k];
+          });
+          m[r] = sacc;
+        }
+      }
+      const size_t o = gidx(g, i, j, zd);
+#pragma unroll
+      for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
+      if (!(m[1] * m[1] + m[2] * m[2] + m[3] * m[3] < R(1e30))) raise_status(a.status, 4);
+    }
+    // ---- rotate ----
+#pragma unroll
+    for (int q = 0; q < 9; ++q) {
+      Am[q] = Ac[q];
+      Ac[q] = Ap[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) cr[q] = nr[q];
+    xz_m = xz_c, xz_c = xz_p, xz_p = xz_n;
+    zz_m = zz_c, zz_c = zz_p, zz_p = zz_n;
+    zs = (zs + 1) & (NSLC3 - 1);
+  };
+
+  for (int z = z0 - 1; z <= z1; ++z) {
+    if (z + 2 <= plast && z + 2 > waited && !wait(z + 2)) {
+      drain_and_fail();
+      return;
+    }
+    if (tile_fast && z >= 2 && z <= nz - 2) plane_step(z, std::true_type{});
+    else plane_step(z, std::false_type{});
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Pointwise kernels: material, objective source, objective, sensitivity
 // ------------------------------------------------------------------------------------
@@ -1548,7 +1829,7 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
 }
 
 template <typename R>
-lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out) {
+lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out, int* path_out) {
   const auto& d = *c.d;
   const auto& L = *c.L;
   const size_t fb = L.N * sizeof(R);
@@ -1562,7 +1843,42 @@ lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out) {
   ++*c.launches;
   CK3(c, cudaMemsetAsync(c.ws + L.adA, 0, fb * kNA3, c.stream));
   int acur = 0;
+  *path_out = LKS_PATH_STEP;
   if constexpr (sizeof(R) == 4) {
+    if (tma3_ok(d) && d.exec_path != LKS_PATH_STEP) {  // the warp-column adjoint
+      Maps3F maps[2];
+      Adj3CArgs ca[2];
+      lks_status st;
+      const int yi[NAY3] = {5, 7, 8}, oi[7] = {0, 1, 2, 3, 4, 6, 9};
+      for (int b = 0; b < 2; ++b) {
+        for (int f = 0; f < NAY3; ++f)
+          if ((st = map3(c, ad3<float>(c, b, yi[f]), CBW3, CBH3, &maps[b].m[f])) != LKS_OK) return st;
+        for (int f = 0; f < 7; ++f) ca[b].own[f] = ad3<float>(c, b, oi[f]);
+        for (int f = 0; f < 3; ++f) ca[b].own[7 + f] = st3<float>(c, cur, 1 + f);
+        ca[b].cf[0] = fld3<float>(c, L.binv);
+        for (int f = 0; f < 3; ++f) ca[b].cf[1 + f] = fld3<float>(c, L.src, f);
+        for (int q = 0; q < kNA3; ++q) ca[b].m0[q] = ad3<float>(c, 1 - b, q);
+        ca[b].emap = reinterpret_cast<const float*>(c.ws + L.emap);
+        ca[b].status = reinterpret_cast<int*>(c.ws + L.status);
+      }
+      CK3(c, cudaFuncSetAttribute(adj3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)adj3c_smem()));
+      int dev = 0, sms = 0, per_sm = 0;
+      CK3(c, cudaGetDevice(&dev));
+      CK3(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj3c_kernel, NTC3, adj3c_smem()));
+      const int zc = col_chunk3(d, std::max(1, sms * per_sm));
+      ca[0].zc = ca[1].zc = zc;
+      const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + zc - 1) / zc);
+      for (int it = 0; it < d.n_adj; ++it) {
+        adj3c_kernel<<<grid, NTC3, adj3c_smem(), c.stream>>>(maps[acur], ca[acur], g, cf);
+        CK3(c, cudaGetLastError());
+        ++*c.launches;
+        acur = 1 - acur;
+      }
+      *acur_out = acur;
+      *path_out = LKS_PATH_COLUMN;
+      return LKS_OK;
+    }
     if (tma3_ok(d)) {
       Maps3A maps[2];
       Adj3TArgs ta[2];
@@ -1771,8 +2087,8 @@ lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cu
   return c.L->rsize == 8 ? forward3_t<double>(c, gamma_dev, J_dev, cur, path)
                          : forward3_t<float>(c, gamma_dev, J_dev, cur, path);
 }
-lks_status adjoint3(const Ctx3& c, int cur, int* acur) {
-  return c.L->rsize == 8 ? adjoint3_t<double>(c, cur, acur) : adjoint3_t<float>(c, cur, acur);
+lks_status adjoint3(const Ctx3& c, int cur, int* acur, int* path) {
+  return c.L->rsize == 8 ? adjoint3_t<double>(c, cur, acur, path) : adjoint3_t<float>(c, cur, acur, path);
 }
 lks_status sensitivity3(const Ctx3& c, int cur, int acur, void* out) {
   return c.L->rsize == 8 ? sensitivity3_t<double>(c, cur, acur, out) : sensitivity3_t<float>(c, cur, acur, out);

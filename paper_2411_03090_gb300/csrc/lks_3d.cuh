@@ -51,8 +51,9 @@ lks_status upload_maps3(const Ctx3& c);
 // unless the step path is asked for).
 lks_status forward3(const Ctx3& c, const void* gamma_dev, double* J_dev, int* cur, int* path);
 // Step 4: n_adj ALKS iterations on the frozen state `cur`; *acur receives the
-// adjoint buffer holding the result.
-lks_status adjoint3(const Ctx3& c, int cur, int* acur);
+// adjoint buffer holding the result, *path the lks_exec_path that ran (column: the
+// warp-column adjoint, under the same conditions as the forward's).
+lks_status adjoint3(const Ctx3& c, int cur, int* acur, int* path);
 // Step 5: dJ/dgamma of the final state and adjoint into out (N values).
 lks_status sensitivity3(const Ctx3& c, int cur, int acur, void* out);
 

@@ -1186,11 +1186,12 @@ lks_status alks_adjoint(lks_handle* h) {
   if (check_handle(h) != LKS_OK) return LKS_ERR_INVALID_ARG;
   if (h->phase < 1) return fail(h, LKS_ERR_STATE, "alks_adjoint before lks_forward");
   if (h->is3) {
-    const lks_status s = lks3::adjoint3(ctx3(h), h->cur, &h->acur);
+    int path = LKS_PATH_STEP;
+    const lks_status s = lks3::adjoint3(ctx3(h), h->cur, &h->acur, &path);
     if (s == LKS_OK) {
       h->phase = 2;
       h->adj_steps += h->d.n_adj;
-      h->adj_path = LKS_PATH_STEP;
+      h->adj_path = path;
     }
     return s;
   }

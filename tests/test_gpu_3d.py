@@ -53,6 +53,7 @@ def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape, path):
     J, grad = s.gradient(torch.from_numpy(g))
     tma = real == "f32" and shape[0] % 4 == 0
     assert s.query().fwd_path == (3 if tma and path == "auto" else 1)
+    assert s.query().adj_path == (3 if tma and path == "auto" else 1)
     st = to_state(s.get_state())
     for name in ("u", "v", "w"):
         assert rel_l2(getattr(st, name), getattr(ref["state"], name)) <= tol_f, name
@@ -67,28 +68,38 @@ def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape, path):
 
 
 @pytest.mark.parametrize("shape", [(60, 17, 37), (28, 8, 5), (44, 21, 40), (88, 9, 70), (116, 40, 37)])
-def test_column_forward_matches_step_forward_and_oracle(shape):
-    """The warp-column z-march forward (28 x 8 tiles, ragged in x, y and z) against
-    the plane-march forward and the oracle's state after the same steps.  116 x 40
-    has tiles whose threads are all off the x and y faces (the fast variant)."""
+def test_column_kernels_match_step_kernels_and_oracle(shape):
+    """The warp-column z-march forward and adjoint (28 x 8 tiles, ragged in x, y and
+    z) against the plane-march kernels and the oracle's gradient after the same
+    steps.  116 x 40 has tiles whose threads are all off the x and y faces (the fast
+    variants)."""
     pb = duct(*shape, n=40)
     g = pb.gamma()
     gt = torch.from_numpy(g)
-    ref = O.forward3(pb, g, pb.n_steps)[0]
-    st = {}
+    ref = O.steady_gradient3(pb, g)
+    st, adj, gr = {}, {}, {}
     for path in ("column", "step"):
         s = LKS(pb, real="f32", path=path)
-        s.lks_forward(gt)
-        assert s.query().fwd_path == (3 if path == "column" else 1)
-        assert s.query().device_status == 0
+        _, grad = s.gradient(gt)
+        q = s.query()
+        assert (q.fwd_path, q.adj_path) == ((3, 3) if path == "column" else (1, 1))
+        assert q.device_status == 0
         st[path] = [f.double().cpu().numpy() for f in s.get_state()]
+        adj[path] = [a.double().cpu().numpy() for a in s.get_adjoint()]
+        gr[path] = grad.double().cpu().numpy()
     scale = max(np.abs(st["step"][1]).max(), 1e-30)
     for c in range(4):
         assert np.abs(st["column"][c] - st["step"][c]).max() <= 1e-6 * (1.0 if c == 0 else scale), c
+    for q in range(O.NADJ3):
+        aq = max(np.abs(adj["step"][q]).max(), 1e-30)
+        assert np.abs(adj["column"][q] - adj["step"][q]).max() <= 1e-5 * aq, O.ADJ3_NAMES[q]
+        assert rel_l2(adj["column"][q], ref["adjoint"][q]) <= 1e-3, O.ADJ3_NAMES[q]
+    assert rel_l2(gr["column"], gr["step"]) <= 1e-5
+    assert rel_l2(gr["column"], ref["dJdgamma"]) <= 1e-3
     col = to_state([torch.from_numpy(x) for x in st["column"]])
     for name in ("u", "v", "w"):
-        assert rel_l2(getattr(col, name), getattr(ref, name)) <= 1e-5, name
-    assert rel_l2(col.rho - 1, ref.rho - 1) <= 1e-4
+        assert rel_l2(getattr(col, name), getattr(ref["state"], name)) <= 1e-5, name
+    assert rel_l2(col.rho - 1, ref["state"].rho - 1) <= 1e-4
 
 
 def test_gradient_host_and_query():
@@ -118,7 +129,7 @@ def _sample_nodes(pb, rng, n_interior=40):
 def test_config4_full_size_one_step_sampled(path):
     """192^3, FP32: one forward step and one adjoint step at sampled nodes equal
     the oracle's node updates from the GPU's previous level (FP32 tolerance), on
-    the warp-column forward (auto) and on the plane-march forward (step)."""
+    the warp-column kernels (auto) and on the plane-march kernels (step)."""
     pb = inputs.config4().with_(n_steps=3, n_adj=1)
     g = pb.gamma()
     gt = torch.from_numpy(g)
@@ -146,6 +157,7 @@ def test_config4_full_size_one_step_sampled(path):
     s_b = LKS(pb.with_(n_adj=2), real="f32", path=path)
     s_b.lks_forward(gt)
     s_b.alks_adjoint()
+    assert s_b.query().adj_path == (3 if path == "auto" else 1)
     a2 = np.stack([a.double().cpu().numpy() for a in s_b.get_adjoint()])
     PV = O.adjoint_eq3(pb, st, a1)
     ascale = np.abs(a2).reshape(O.NADJ3, -1).max(axis=1) + 1e-30
