@@ -395,7 +395,10 @@ def run_batch_study(args):
                                            "column": round(st.tune_acol_us, 1)},
                    "checkpoint_every": st.checkpoint_every, "arena": [st.arena_w, st.arena_h],
                    "tiles": st.ntiles, "create_s": create_s},
-        "roofline": {"bound": "hbm", "kernel": "whole gradient (graph: fwd_tma/adj_tma BATCH kernels)",
+        "roofline": {"bound": "hbm",
+                     "kernel": "whole gradient (graph: %s forward, %s adjoint, batched)" % (
+                         "fwd_col2_kernel" if st.fwd_column else "fwd_tma_kernel",
+                         "adj_col_kernel" if st.adj_column else "adj_tma_kernel"),
                      "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm, "traffic": None,
                      "peak_kind": peak_kind, "algorithmic_bytes_per_node_level": BYTES_CKPT_LEVEL},
         "batch_vs_plain": {"s_per_batch_gradient": t_batch, "plain_fp32_s_design_by_design": t_plain or None,
