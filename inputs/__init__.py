@@ -84,6 +84,7 @@ class Problem:
     t_kind: List[int] = field(default_factory=lambda: [T_FIXED, T_FLUX, T_FIXED, T_FLUX])
     t_val: List[float] = field(default_factory=lambda: [0.0, 0.0, 1.0, 0.0])
     kappa_T: float = 0.0
+    kappa_p: float = 0.0     # weight of the static pressure drop in J (J = J_O + kappa_p J_p)
     steady: bool = True
     n_steps: int = 1000
     n_adj: int = 1000
@@ -194,6 +195,7 @@ class Problem3:
     u_max: float = 0.05
     rho_out: float = 1.0
     profile: int = 0         # inlet: 0 duct (product of parabolas), 1 plane channel (parabola in y)
+    kappa_p: float = 0.0     # weight of the static pressure drop in J (J = J_O + kappa_p J_p)
     steady: bool = True
     n_steps: int = 1000
     n_adj: int = 1000
@@ -222,8 +224,8 @@ def duct(nx: int, ny: int, nz: int, Re: float, u_max: float = 0.05, **kw) -> Pro
 
 def config4() -> Problem3:
     """192^3 steady duct, Re = 50 (nu = 0.191), sigma = 6, 1000 forward + 1000
-    adjoint steps."""
-    return duct(192, 192, 192, Re=50.0, seed=4, n_steps=1000, n_adj=1000)
+    adjoint steps; J = total dissipation + static pressure drop (unit weights)."""
+    return duct(192, 192, 192, Re=50.0, seed=4, n_steps=1000, n_adj=1000, kappa_p=1.0)
 
 
 def roofline2d(n: int = 8192) -> Problem:

@@ -25,7 +25,10 @@
  *                      the four side faces: walls (u = 0); nodes on two or three
  *                      faces: wall nodes with the density carried over
  *   objective          total dissipation J_O = sum over interior nodes of
- *                      nu/2 S:S + alpha_gamma |u|^2
+ *                      nu/2 S:S + alpha_gamma |u|^2, plus kappa_p times the
+ *                      static pressure drop J_p = sum_in p - sum_out p (Eq.
+ *                      objective_pipebend, p = rho / 3, dGamma = 1) over the
+ *                      inlet and outlet nodes that lie on one face only
  *   adjoint            f~_k = P(x + c_k) + c_k . V(x + c_k) with P = rho~ and
  *                      V_a = 3 (u~_a + 3 s~_ab u_b - rho~ u_a) - 2A d_b s~_ab
  *                      (Eq. afeq), moments rho~, u~ (3), s~ (6); implicit adjoint
@@ -33,7 +36,9 @@
  *   adjoint BCs        the generalized inverse of Sec. 2.5 (residual Eq.
  *                      r_definition) over all 19 rows, velocity multipliers
  *                      mu~ in R^3, pressure multipliers lambda~ and two tangential
- *                      mu~ (Eq. afboundaryp)
+ *                      mu~ (Eq. afboundaryp); the boundary objective enters every
+ *                      row as +-kappa_p (inlet +, outlet -), the derivative of the
+ *                      integrand kappa_p p with respect to p
  *   sensitivity        alpha' |u|^2 + 3 alpha' u . u~ at interior nodes (Sec. 2.5)
  *
  * Readings (restated at the code they affect): lattice units dx = dt = 1; implicit
@@ -83,6 +88,7 @@ typedef struct {
     double u_max;
     double rho_out;
     int profile; /* inlet: 0 duct (product of parabolas), 1 plane channel (parabola in y) */
+    double kappa_p; /* weight of the static pressure drop in the objective */
 } orc3_problem;
 
 static double lks_A3(const orc3_problem *p) { return (1.0 / 6.0 - p->nu) * 9.0 / 2.0; }
@@ -307,6 +313,26 @@ double orc3_objective(const orc3_problem *p, const double *gamma, const double *
     return J;
 }
 
+/* Static pressure drop (Eq. objective_pipebend) with p = rho / 3 and dGamma = 1:
+ *   J_p = 1/3 (sum over inlet nodes of rho - sum over outlet nodes of rho),
+ * the inlet and outlet nodes being those of the faces x = 0 and x = nx-1 that lie on
+ * no other face (the face edges are wall nodes). */
+double orc3_pressure_drop(const orc3_problem *p, const double *rho) {
+    int nx = p->nx, ny = p->ny;
+    double s = 0.0;
+    for (int k = 1; k < p->nz - 1; ++k)
+        for (int j = 1; j < ny - 1; ++j) s += A3(rho, 0, j, k) - A3(rho, nx - 1, j, k);
+    return s / 3.0;
+}
+
+/* J = J_O + kappa_p J_p of one level. */
+double orc3_objective_total(const orc3_problem *p, const double *gamma, const double *rho,
+                            const double *u, const double *v, const double *w) {
+    double J = orc3_objective(p, gamma, u, v, w);
+    if (p->kappa_p != 0.0) J += p->kappa_p * orc3_pressure_drop(p, rho);
+    return J;
+}
+
 /* dJ_O/du_a at node (i, j, k), term by term: u_a(x) enters S_ad of the interior
  * neighbours x -+ e_d through their central differences, giving
  *   nu sum_d [ S_ad(x - e_d) - S_ad(x + e_d) ]  (+ 2 alpha u_a at interior x). */
@@ -373,16 +399,18 @@ static void lstsq3(int m, int n, const double *M, const double *b, double *x) {
 }
 
 /* Flow adjoint boundary rule at a face, box-edge or corner node.  Residual for
- * every direction r (Eq. r_definition with dx = 1):
- *   r_r = (n.c_r) f~_r - 2A sum_j w_j (n.c_j)(c_j.c_r) f~_j + m_r
+ * every direction r (Eq. r_definition with dx = 1, and the boundary objective term
+ * of Eqs. afboundaryu / afboundaryp):
+ *   r_r = (n.c_r) f~_r - 2A sum_j w_j (n.c_j)(c_j.c_r) f~_j + m_r + jb
  * with m_r = mu~ . c_r on velocity nodes (three multipliers) and
  *      m_r = lambda~ + mu~_1 (c_r.t_1) + mu~_2 (c_r.t_2) on the outlet face (t_1,
  *      t_2 the face's tangents).
  * The unknown f~ (gather point off the lattice) and the multipliers minimise
- * ||r||_2 over all 19 rows.  f[] holds the known values on entry and all 19 on
- * exit; mult[0..2] receives the multipliers. */
+ * ||r||_2 over all 19 rows.  jb = dJ_dO/df_k, the same for every k (the boundary
+ * objective depends on the f only through rho).  f[] holds the known values on
+ * entry and all 19 on exit; mult[0..2] receives the multipliers. */
 void orc3_bc_flow(const int *n, int pressure, double A, const int *unknown, double *f,
-                  double *mult) {
+                  double *mult, double jb) {
     int U[Q3], nu_ = 0;
     for (int q = 0; q < Q3; ++q)
         if (unknown[q]) U[nu_++] = q;
@@ -411,7 +439,7 @@ void orc3_bc_flow(const int *n, int pressure, double A, const int *unknown, doub
         double s = 0.0;
         for (int c = 0; c < Q3; ++c)
             if (!unknown[c]) s += M[r][c] * f[c];
-        rhs[r] = -s;
+        rhs[r] = -s - jb;
     }
     lstsq3(Q3, ncol, Ms, rhs, x);
     for (int q = 0; q < nu_; ++q) f[U[q]] = x[q];
@@ -475,7 +503,16 @@ void orc3_adjoint_node(const orc3_problem *p, const double *gamma, const double 
         f[q] = A3(PV[0], gi, gj, gk);
         for (int a = 0; a < 3; ++a) f[q] += C3[q][a] * A3(PV[1 + a], gi, gj, gk);
     }
-    if (cls != M_INTERIOR) orc3_bc_flow(n, cls == M_PRESSURE, A, unknown, f, NULL);
+    if (cls != M_INTERIOR) {
+        /* boundary objective term of every row: d(kappa_p p)/dp, + on the inlet and
+         * - on the outlet (reading: the row term is the derivative with respect
+         * to p; with it the gradient matches central differences in the paper's
+         * own pressure-drop verification, Sec. 2.6) */
+        double jb = 0.0;
+        if (cls == M_PRESSURE) jb = -p->kappa_p;
+        else if (cls == M_VELOCITY && n[0] == -1) jb = p->kappa_p;
+        orc3_bc_flow(n, cls == M_PRESSURE, A, unknown, f, NULL, jb);
+    }
     double m[NADJ3] = {0};
     for (int q = 0; q < Q3; ++q) {
         m[0] += W3[q] * f[q];
@@ -566,7 +603,7 @@ double orc3_forward(const orc3_problem *p, const double *gamma, int n_steps, dou
             memcpy(lv + N, v, N * sizeof(double));
             memcpy(lv + 2 * N, w, N * sizeof(double));
         }
-        if (J_acc) *J_acc += orc3_objective(p, gamma, u, v, w);
+        if (J_acc) *J_acc += orc3_objective_total(p, gamma, rho, u, v, w);
     }
     free(buf);
     return res;

@@ -20,11 +20,17 @@
  *                      and the Brinkman correction Eq. (lbef_ex) taken implicitly
  *   forward BCs        Sec. 2.4 (prescribed u, prescribed p and u_s, T or flux)
  *   objective          Eq. (fj) with a domain integrand J_O (total dissipation,
- *                      plus an optional kappa_T * T term)
+ *                      plus an optional kappa_T * T term) plus kappa_p times the
+ *                      static pressure drop J_p = sum_in p - sum_out p (Eq.
+ *                      objective_pipebend, p = rho / 3, dGamma = 1, over the
+ *                      inlet span and the outlet nodes)
  *   adjoint            Eqs. (ap)-(aq) with f~^eq Eq. (afeq), g~^eq Eq. (ageq) and
  *                      the sources of Eqs. (albef_ex), (albeg_ex) (App. A)
  *   adjoint BCs        Eq. (afboundaryu) solved in the least-squares sense as in
- *                      Sec. 2.5 (generalized inverse, residual Eq. (r_definition));
+ *                      Sec. 2.5 (generalized inverse, residual Eq. (r_definition)),
+ *                      with the boundary objective term on the inlet span and the
+ *                      outlet (+-kappa_p per row: the derivative of the integrand
+ *                      kappa_p p with respect to p);
  *                      the pressure, temperature and heat-flux versions of App. A
  *                      Eqs. (afboundaryp), (agboundaryT), (agboundaryq),
  *                      (afboundaryuq) by the same least-squares procedure
@@ -79,6 +85,7 @@ typedef struct {
     int t_kind[4];             /* per edge (left, right, bottom, top)         */
     double t_val[4];           /* T_bar or q_bar_w per edge                    */
     double kappa_T;            /* weight of the T term in J_O                  */
+    double kappa_p;            /* weight of the static pressure drop J_p       */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -343,6 +350,31 @@ double orc_objective(const orc_problem *p, const double *gamma, const double *u,
     return J;
 }
 
+/* Inlet nodes: the velocity nodes of the left edge inside the inlet span (not the
+ * corners); outlet nodes: the pressure nodes.  J_p = 1/3 (sum over inlet nodes of
+ * rho - sum over outlet nodes of rho): Eq. objective_pipebend with p = rho / 3 and
+ * dGamma = 1. */
+static int is_inlet(const orc_problem *p, int i, int j) {
+    return i == 0 && j > 0 && j < p->ny - 1 && j >= p->in_y0 && j <= p->in_y1;
+}
+double orc_pressure_drop(const orc_problem *p, const double *rho) {
+    int nx = p->nx, ny = p->ny;
+    double s = 0.0;
+    for (int j = 1; j < ny - 1; ++j) {
+        if (is_inlet(p, 0, j)) s += AT(rho, 0, j);
+        if (j >= p->out_y0 && j <= p->out_y1) s -= AT(rho, nx - 1, j);
+    }
+    return s / 3.0;
+}
+
+/* J = J_O + kappa_p J_p of one level. */
+double orc_objective_total(const orc_problem *p, const double *gamma, const double *rho,
+                           const double *u, const double *v, const double *T) {
+    double J = orc_objective(p, gamma, u, v, T);
+    if (p->kappa_p != 0.0) J += p->kappa_p * orc_pressure_drop(p, rho);
+    return J;
+}
+
 /* dJ_O/du and dJ_O/dv at node (i, j): the derivative of the sum above, written
  * out term by term (S at an interior neighbour z depends on u(i, j) through the
  * central differences of z). */
@@ -435,7 +467,7 @@ static void lstsq_small(int m, int n, const double *M /* m x n, row major */, co
  * f[] holds the known values on entry and all nine on exit.  mult[0..1] returns
  * the multipliers. */
 void orc_bc_flow(int n_x, int n_y, int pressure, double A, double kT, const int *unknown,
-                 double *f, double *mult) {
+                 double *f, double *mult, double jb) {
     int U[9], nu_ = 0;
     for (int k = 0; k < 9; ++k)
         if (unknown[k]) U[nu_++] = k;
@@ -462,7 +494,7 @@ void orc_bc_flow(int n_x, int n_y, int pressure, double A, double kT, const int 
         for (int c = 0; c < 9; ++c)
             if (!unknown[c]) s += Mfull[r][c] * f[c];
         s -= kT * (double)(CX[r] * n_x + CY[r] * n_y);
-        rhs[r] = -s;
+        rhs[r] = -s - jb;
     }
     lstsq_small(9, ncol, Ms, rhs, x);
     for (int q = 0; q < nu_; ++q) f[U[q]] = x[q];
@@ -591,7 +623,14 @@ void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P
             orc_bc_thermal(n_x, n_y, flux, B_of(p, AT(gamma, i, j)), un, unknown, g, &kap);
             if (flux) kT = kap * AT(T0, i, j);
         }
-        orc_bc_flow(n_x, n_y, cls == N_PRESSURE, A, kT, unknown, f, NULL);
+        /* boundary objective term of every row: d(kappa_p p)/dp, + on the inlet
+         * and - on the outlet (reading: the row term is the derivative with
+         * respect to p; with it the gradient matches central differences in the
+         * paper's own pressure-drop verification, Sec. 2.6) */
+        double jb = 0.0;
+        if (cls == N_PRESSURE) jb = -p->kappa_p;
+        else if (cls == N_VELOCITY && is_inlet(p, i, j)) jb = p->kappa_p;
+        orc_bc_flow(n_x, n_y, cls == N_PRESSURE, A, kT, unknown, f, NULL, jb);
     }
     double m[NADJ] = {0};
     for (int k = 0; k < 9; ++k) {
@@ -720,7 +759,7 @@ double orc_forward(const orc_problem *p, const double *gamma, int t0, int n_step
             if (p->thermal) memcpy(lv + 2 * N, T, N * sizeof(double));
             else memset(lv + 2 * N, 0, N * sizeof(double));
         }
-        if (J_acc) *J_acc += orc_objective(p, gamma, u, v, T);
+        if (J_acc) *J_acc += orc_objective_total(p, gamma, rho, u, v, T);
     }
     free(buf);
     return res;

@@ -44,6 +44,7 @@ class OrcProblem(C.Structure):
         ("t_kind", C.c_int * 4),
         ("t_val", C.c_double * 4),
         ("kappa_T", C.c_double),
+        ("kappa_p", C.c_double),
     ]
 
 
@@ -55,6 +56,7 @@ class OrcProblem3(C.Structure):
         ("u_max", C.c_double),
         ("rho_out", C.c_double),
         ("profile", C.c_int),
+        ("kappa_p", C.c_double),
     ]
 
 
@@ -91,7 +93,11 @@ def lib():
         L.orc_objective.restype = C.c_double
         L.orc_dJdu_node.argtypes = [prob, P, P, P, C.c_int, C.c_int, P, P]
         L.orc_bc_flow.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                                  C.POINTER(C.c_int), P, P]
+                                  C.POINTER(C.c_int), P, P, C.c_double]
+        L.orc_pressure_drop.argtypes = [prob, P]
+        L.orc_pressure_drop.restype = C.c_double
+        L.orc_objective_total.argtypes = [prob, P, P, P, P, P]
+        L.orc_objective_total.restype = C.c_double
         L.orc_bc_thermal.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
                                      C.POINTER(C.c_int), P, P]
         L.orc_adjoint_step.argtypes = [prob, P, P, P, P, P, P, PP, PP, P]
@@ -112,7 +118,11 @@ def lib():
         L.orc3_objective.argtypes = [p3, P, P, P, P]
         L.orc3_objective.restype = C.c_double
         L.orc3_dJdu_node.argtypes = [p3, P, PP, C.c_int, C.c_int, C.c_int, P]
-        L.orc3_bc_flow.argtypes = [IP, C.c_int, C.c_double, IP, P, P]
+        L.orc3_bc_flow.argtypes = [IP, C.c_int, C.c_double, IP, P, P, C.c_double]
+        L.orc3_pressure_drop.argtypes = [p3, P]
+        L.orc3_pressure_drop.restype = C.c_double
+        L.orc3_objective_total.argtypes = [p3, P, P, P, P, P]
+        L.orc3_objective_total.restype = C.c_double
         L.orc3_adjoint_eq.argtypes = [p3, PP, PP, PP]
         L.orc3_adjoint_node.argtypes = [p3, P, PP, PP, C.c_int, C.c_int, C.c_int, P]
         L.orc3_adjoint_step.argtypes = [p3, P, PP, PP, PP, PP, P]
@@ -228,10 +238,16 @@ def forward_node(pb, gamma, t, st: State, i: int, j: int) -> np.ndarray:
 
 
 def objective(pb, gamma, st: State) -> float:
-    """J_O of one state (Step 3)."""
+    """J = J_O + kappa_p J_p of one state (Step 3)."""
     L = lib()
     prob = make_problem(pb)
-    return float(L.orc_objective(C.byref(prob), _p(_g(gamma)), _p(st.u), _p(st.v), _p(st.T)))
+    return float(L.orc_objective_total(C.byref(prob), _p(_g(gamma)), _p(st.rho), _p(st.u), _p(st.v),
+                                       _p(st.T)))
+
+
+def pressure_drop(pb, st: State) -> float:
+    """J_p = sum_in p - sum_out p with p = rho / 3 (unweighted)."""
+    return float(lib().orc_pressure_drop(C.byref(make_problem(pb)), _p(st.rho)))
 
 
 def dJdu(pb, gamma, st: State):
@@ -345,13 +361,14 @@ def unsteady_gradient(pb, gamma, n_steps: Optional[int] = None):
     return dict(J=J, dJdgamma=sens, state=st, adjoint=adj, traj=tr)
 
 
-def bc_flow(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, kT: float = 0.0):
-    """Least-squares adjoint boundary rule for one node (flow lattice)."""
+def bc_flow(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, kT: float = 0.0, jb: float = 0.0):
+    """Least-squares adjoint boundary rule for one node (flow lattice); jb is the
+    boundary objective term added to every row."""
     L = lib()
     f = np.ascontiguousarray(known, dtype=np.float64).copy()
     um = (C.c_int * 9)(*[int(x) for x in unknown_mask])
     mult = np.zeros(2)
-    L.orc_bc_flow(int(n[0]), int(n[1]), int(pressure), float(A), float(kT), um, _p(f), _p(mult))
+    L.orc_bc_flow(int(n[0]), int(n[1]), int(pressure), float(A), float(kT), um, _p(f), _p(mult), float(jb))
     return f, mult
 
 
@@ -429,8 +446,20 @@ def forward_step3(pb, gamma, st: State3) -> State3:
 
 
 def objective3(pb, gamma, st: State3) -> float:
+    """J = J_O + kappa_p J_p of one state."""
+    return float(lib().orc3_objective_total(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.rho), _p(st.u),
+                                            _p(st.v), _p(st.w)))
+
+
+def dissipation3(pb, gamma, st: State3) -> float:
+    """J_O alone (total dissipation)."""
     return float(lib().orc3_objective(C.byref(make_problem3(pb)), _p(_g(gamma)), _p(st.u), _p(st.v),
                                       _p(st.w)))
+
+
+def pressure_drop3(pb, st: State3) -> float:
+    """J_p = sum_in p - sum_out p with p = rho / 3 (unweighted)."""
+    return float(lib().orc3_pressure_drop(C.byref(make_problem3(pb)), _p(st.rho)))
 
 
 def dJdu3(pb, gamma, st: State3) -> np.ndarray:
@@ -508,12 +537,12 @@ def steady_gradient3(pb, gamma, n_steps: Optional[int] = None, n_adj: Optional[i
     return dict(J=J, dJdgamma=sens, state=st, adjoint=adj)
 
 
-def bc_flow3(n, pressure: bool, A: float, known: np.ndarray, unknown_mask):
+def bc_flow3(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, jb: float = 0.0):
     f = np.ascontiguousarray(known, dtype=np.float64).copy()
     nn = (C.c_int * 3)(*[int(x) for x in n])
     um = (C.c_int * 19)(*[int(x) for x in unknown_mask])
     mult = np.zeros(3)
-    lib().orc3_bc_flow(nn, int(pressure), float(A), um, _p(f), _p(mult))
+    lib().orc3_bc_flow(nn, int(pressure), float(A), um, _p(f), _p(mult), float(jb))
     return f, mult
 
 

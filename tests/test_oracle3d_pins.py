@@ -182,10 +182,46 @@ def test_one_step_gradient_is_exact():
         assert abs(fd - sens[k, j, i]) <= 1e-7 * abs(fd) + 4 * np.finfo(float).eps * abs(J) / eps
 
 
+def test_pressure_drop_closed_form_3d():
+    """rho = 1 + a x: J_p = 1/3 (sum_in rho - sum_out rho) = -a (nx-1)(ny-2)(nz-2)/3
+    over the face-interior nodes of x = 0 and x = nx-1; the face edges (wall nodes)
+    do not enter, and J = J_O + kappa_p J_p."""
+    pb = inputs.Problem3(nx=12, ny=9, nz=8, nu=0.2, alpha_bar=10.0)
+    st = O.State3(pb.nz, pb.ny, pb.nx)
+    a = -0.021
+    st.rho = 1.0 + a * np.arange(pb.nx)[None, None, :] * np.ones((pb.nz, pb.ny, 1))
+    for i in (0, pb.nx - 1):
+        st.rho[0, :, i] = st.rho[-1, :, i] = st.rho[:, 0, i] = st.rho[:, -1, i] = 1e6
+    want = -a * (pb.nx - 1) * (pb.ny - 2) * (pb.nz - 2) / 3.0
+    assert abs(O.pressure_drop3(pb, st) - want) <= 1e-12 * abs(want) * 10
+    g = pb.gamma()
+    assert abs(O.objective3(pb.with_(kappa_p=1.5), g, st) - O.dissipation3(pb, g, st) - 1.5 * want) <= 1e-9
+
+
+def test_outlet_row_term_moves_only_lambda_3d():
+    """Outlet face: a constant row term is absorbed by lambda~ (Eq. afboundaryp), the
+    filled f~ are unchanged; on the inlet face it is not (mu~ . c_k cannot carry a
+    constant, since the rest link has c = 0)."""
+    c, w = O.lattice3()
+    rng = np.random.default_rng(6)
+    for n, pressure in (((1, 0, 0), True), ((-1, 0, 0), False)):
+        n = np.array(n)
+        unknown = np.array([(x * n > 0).any() for x in c])
+        known = rng.standard_normal(19) * ~unknown
+        f0, m0 = O.bc_flow3(n, pressure, -0.1095, known, unknown)
+        f1, m1 = O.bc_flow3(n, pressure, -0.1095, known, unknown, jb=0.8)
+        if pressure:
+            np.testing.assert_allclose(f1, f0, atol=1e-12)
+            assert abs((m1[0] - m0[0]) + 0.8) <= 1e-12
+        else:
+            assert np.abs(f1 - f0).max() > 0.1
+
+
 @pytest.mark.parametrize("A", [-0.1095, 0.3])
 def test_edge_rules_equal_numpy_least_squares(A):
     """Every face, box-edge and corner class: the oracle's normal-equation solve of
-    the generalized-inverse rule equals numpy's least squares on the same system."""
+    the generalized-inverse rule equals numpy's least squares on the same system,
+    with and without a boundary objective term (a constant added to every row)."""
     c, w = O.lattice3()
     rng = np.random.default_rng(5)
     for n in itertools.product((-1, 0, 1), repeat=3):
@@ -196,7 +232,8 @@ def test_edge_rules_equal_numpy_least_squares(A):
         pressure = faces == 1 and n[0] == 1
         unknown = np.array([(x * n > 0).any() for x in c])
         known = rng.standard_normal(19) * ~unknown
-        f, mult = O.bc_flow3(n, pressure, A, known, unknown)
+        jb = rng.standard_normal() if faces == 1 else 0.0
+        f, mult = O.bc_flow3(n, pressure, A, known, unknown, jb=jb)
         cn = c @ n
         M = np.diag(cn.astype(float)) - 2 * A * (w * cn)[None, :] * (c @ c.T)
         U = [k for k in range(19) if unknown[k] and np.abs(M[:, k]).sum() > 0]
@@ -205,7 +242,7 @@ def test_edge_rules_equal_numpy_least_squares(A):
         else:
             mc = [c[:, a].astype(float) for a in range(3)]
         Am = np.stack([M[:, k] for k in U] + mc, 1)
-        x = np.linalg.lstsq(Am, -(M @ known), rcond=None)[0]
+        x = np.linalg.lstsq(Am, -(M @ known) - jb, rcond=None)[0]
         np.testing.assert_allclose(f[U], x[:len(U)], rtol=1e-10, atol=1e-12)
         np.testing.assert_allclose(mult, x[len(U):], rtol=1e-10, atol=1e-12)
         dead = [k for k in range(19) if unknown[k] and k not in U]

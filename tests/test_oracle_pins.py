@@ -304,6 +304,86 @@ def _fd_gradient(pb, g, st, nodes, eps=1e-4):
     return out
 
 
+# --------------------------------------------------------------------------------------
+# Static pressure drop (Eq. objective_pipebend) and its adjoint boundary term
+# --------------------------------------------------------------------------------------
+def test_pressure_drop_closed_form():
+    """rho = 1 + a x: J_p = 1/3 (sum_in rho - sum_out rho) = -a (nx-1) n / 3 over the
+    n inlet nodes of the left edge (corners excluded) and the n outlet nodes; corner
+    values do not enter."""
+    pb = inputs.channel(23, 13, Re=10.0)
+    st = O.State(pb.ny, pb.nx)
+    a = 0.013
+    st.rho = 1.0 + a * np.arange(pb.nx)[None, :] * np.ones((pb.ny, 1))
+    st.rho[[0, 0, -1, -1], [0, -1, 0, -1]] = 1e6
+    n = pb.ny - 2
+    assert abs(O.pressure_drop(pb, st) - (-a * (pb.nx - 1) * n / 3.0)) <= 1e-12
+    assert abs(O.objective(pb.with_(kappa_p=2.5), pb.gamma(), st) - O.objective(pb, pb.gamma(), st)
+               - 2.5 * O.pressure_drop(pb, st)) <= 1e-9
+
+
+@pytest.mark.parametrize("n,pressure", [((-1, 0), False), ((1, 0), True)])
+def test_boundary_objective_row_term_matches_lstsq(n, pressure):
+    """The boundary objective term enters every residual row of Eqs. afboundaryu /
+    afboundaryp as a constant: the oracle's fill equals numpy's lstsq with that
+    constant added to the right-hand side."""
+    A, jb = 0.2, 0.7
+    rng = np.random.default_rng(12)
+    unknown = np.array([1 if (CX[k] * n[0] > 0 or CY[k] * n[1] > 0) else 0 for k in range(9)])
+    f = rng.standard_normal(9) * (1 - unknown)
+    sol, mult = O.bc_flow(n, pressure, A, f, unknown, jb=jb)
+    M, N = _residual_matrix_flow(n, A, pressure)
+    U = np.where(unknown)[0]
+    K = np.where(unknown == 0)[0]
+    x, *_ = np.linalg.lstsq(np.concatenate([M[:, U], N], 1), -M[:, K] @ f[K] - jb, rcond=None)
+    np.testing.assert_allclose(sol[U], x[:len(U)], atol=1e-12)
+    np.testing.assert_allclose(mult, x[len(U):], atol=1e-12)
+
+
+def test_outlet_row_term_moves_only_lambda():
+    """On the pressure outlet a constant row term lies in the span of the lambda~
+    column (Eq. afboundaryp), so the filled f~ do not change and lambda~ shifts by
+    minus the term: the outlet half of the pressure drop has no adjoint effect, as
+    its value is fixed by the outlet condition."""
+    rng = np.random.default_rng(13)
+    unknown = np.array([1 if CX[k] > 0 else 0 for k in range(9)])
+    f = rng.standard_normal(9) * (1 - unknown)
+    s0, m0 = O.bc_flow((1, 0), True, 0.2, f, unknown)
+    s1, m1 = O.bc_flow((1, 0), True, 0.2, f, unknown, jb=-0.9)
+    np.testing.assert_allclose(s1, s0, atol=1e-13)
+    assert abs((m1[0] - m0[0]) - 0.9) <= 1e-12 and abs(m1[1] - m0[1]) <= 1e-12
+
+
+def test_pressure_drop_gradient_matches_central_differences():
+    """Sec. 2.6 (non-thermal sensitivity verification) at 31 x 31 nodes: walls, a
+    parabolic inlet over y in [10, 20] of the left edge, an outlet over the same span
+    of the right edge, nu = 0.1, Re = 1 on the length 10, gamma = 0.1 in the centre
+    circle of radius 5 and 0.9 elsewhere, J = J_p.  ALKS and central finite
+    differences (eps = 1e-3) agree along the centre line.  Taking the row term as
+    d/df_k (1/3 per row) instead of d/dp would give a third of the ALKS value."""
+    n, steps = 31, 25000
+    nu = 0.1
+    pb = inputs.Problem(nx=n, ny=n, nu=nu, alpha_bar=1e3 * nu, u_max=nu / 10.0, in_y0=10, in_y1=20,
+                        out_y0=10, out_y1=20, n_steps=steps, n_adj=steps)
+    yy, xx = np.mgrid[0:n, 0:n]
+    g = np.where((xx - 15) ** 2 + (yy - 15) ** 2 <= 25.0, 0.1, 0.9)
+    st, res, _, _ = O.forward(pb, g, steps)
+    assert res < 1e-11  # max |du| of the last step; |u| ~ 1e-2
+    _, s0, _ = O.steady_adjoint(pb, g, st, steps)
+    _, s1, r1 = O.steady_adjoint(pb.with_(kappa_p=1.0), g, st, steps)
+    assert r1 < 1e-9
+    adj = s1 - s0
+    eps = 1e-3
+    for i in (6, 15, 21):
+        v = []
+        for sg in (1, -1):
+            gg = g.copy()
+            gg[15, i] += sg * eps
+            v.append(O.pressure_drop(pb, O.forward(pb, gg, steps)[0]))
+        fd = (v[0] - v[1]) / (2 * eps)
+        assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("nu", [0.1, 0.315])
 def test_steady_alks_agrees_with_finite_differences(nu):
