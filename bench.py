@@ -57,7 +57,7 @@ def workload(name: str):
     if name == "config4":
         pb = inputs.config4()
         return pb, (f"config4: 192^3 steady D3Q19 duct, Re=50 (nu=0.191), {pb.n_steps}+{pb.n_adj} steps, "
-                    "FP32, objective = dissipation")
+                    "FP32, objective = dissipation + static pressure drop (unit weights)")
     if name.startswith("roofline"):
         n = int(name[len("roofline"):])
         pb = inputs.roofline2d(n)

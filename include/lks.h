@@ -116,7 +116,9 @@ typedef struct {
     int32_t res_steps;        /* resident marches: time steps per exchange of tile
                                  bands, 0 automatic or 1..3; the largest value up to
                                  this that fits the tile shape and shared memory runs */
-    int32_t reserved[4];      /* must be zero                                        */
+    double kappa_p;           /* D3Q19: weight of the static pressure drop in J
+                                 (Eq. objective_pipebend, see below); D2Q9: 0        */
+    int32_t reserved[2];      /* must be zero                                        */
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in
@@ -126,7 +128,12 @@ typedef struct {
  * u_x = u_max 16 y(1-y) z(1-z) (y, z scaled to [0, 1]), prescribed pressure on the
  * face x = nx-1, walls on the four side faces; nodes on two or three faces are wall
  * nodes.  Steady and non-thermal only (steady = 1, thermal = 0); the inlet and
- * outlet spans, pulse, thermal and checkpoint fields are ignored.  Fields are
+ * outlet spans, pulse, thermal and checkpoint fields are ignored.  Objective:
+ * J = J_O + kappa_p J_p with the total dissipation J_O and the static pressure drop
+ * J_p = 1/3 (sum of rho over the inlet nodes - over the outlet nodes) of Eq.
+ * objective_pipebend (p = rho / 3, dGamma = 1, nodes on one face only); the adjoint
+ * edge rule carries +kappa_p (inlet) or -kappa_p (outlet) in every residual row of
+ * Eqs. afboundaryu / afboundaryp.  Fields are
  * nx*ny*nz values, x fastest, then y, then z.  lks_get_state returns w through its
  * T pointer; alks_get_adjoint fills 10 fields (rho~, u~x, u~y, u~z, s~xx, s~xy,
  * s~xz, s~yy, s~yz, s~zz).  lks_set_state, lks_march, alks_set_adjoint, alks_march

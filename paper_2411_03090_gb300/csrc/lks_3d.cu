@@ -125,6 +125,7 @@ template <typename R>
 struct Coef3 {
   R A, nu, alpha_bar, q_alpha, drho_out;
   double u_max;
+  double kappa_p;  // weight of the static pressure drop in J
 };
 struct Geom3 {
   int nx, ny, nz;
@@ -464,7 +465,9 @@ __global__ void __launch_bounds__(NT3) adj3_kernel(const __grid_constant__ Adj3A
       m[2] = (m[2] + a.src[1][o]) * inv;
       m[3] = (m[3] + a.src[2][o]) * inv;
     } else {
-      const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+      const int cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
+      const R* M = a.emap + cls * (kNA3 * 19);
+      const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
 #pragma unroll
       for (int r = 0; r < kNA3; ++r) {
         R s = R(0);
@@ -472,7 +475,7 @@ __global__ void __launch_bounds__(NT3) adj3_kernel(const __grid_constant__ Adj3A
           constexpr int k = decltype(kk)::value;
           s += M[r * 19 + k] * f[k];
         });
-        m[r] = s;
+        m[r] = s + M0[r];
       }
     }
 #pragma unroll
@@ -1237,7 +1240,9 @@ __global__ void __launch_bounds__(NTF3, 2) adj3t_kernel(const __grid_constant__ 
       m[2] = (m[2] + C[2 * NT3]) * inv;
       m[3] = (m[3] + C[3 * NT3]) * inv;
     } else {
-      const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+      const int cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
+      const R* M = a.emap + cls * (kNA3 * 19);
+      const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
 #pragma unroll
       for (int r = 0; r < kNA3; ++r) {
         R sacc = R(0);
@@ -1245,7 +1250,7 @@ __global__ void __launch_bounds__(NTF3, 2) adj3t_kernel(const __grid_constant__ 
           constexpr int k = decltype(kk)::value;
           sacc += M[r * 19 + k] * f[k];
         });
-        m[r] = sacc;
+        m[r] = sacc + M0[r];
       }
     }
     const size_t o = gidx(g, i, j, z);
@@ -1534,7 +1539,9 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
         m[2] = (m[2] + C[2]) * C[0];
         m[3] = (m[3] + C[3]) * C[0];
       } else {
-        const R* M = a.emap + ((n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1)) * (kNA3 * 19);
+        const int cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
+        const R* M = a.emap + cls * (kNA3 * 19);
+        const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
 #pragma unroll
         for (int r = 0; r < kNA3; ++r) {
           R sacc = R(0);
@@ -1542,7 +1549,7 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
             constexpr int k = decltype(kk)::value;
             sacc += M[r * 19 + k] * F[k];
           });
-          m[r] = sacc;
+          m[r] = sacc + M0[r];
         }
       }
       const size_t o = gidx(g, i, j, zd);
@@ -1617,15 +1624,22 @@ __global__ void src3_kernel(const R* __restrict__ gamma, const R* u0, const R* u
 }
 
 template <typename R>
-__global__ void __launch_bounds__(NTHREADS) objective3_kernel(const R* __restrict__ gamma, const R* u0, const R* u1,
-                                                              const R* u2, Geom3 g, Coef3<R> c, double* partial) {
+__global__ void __launch_bounds__(NTHREADS) objective3_kernel(const R* __restrict__ gamma, const R* drho, const R* u0,
+                                                              const R* u1, const R* u2, Geom3 g, Coef3<R> c,
+                                                              double* partial) {
   __shared__ double red[NTHREADS / 32];
   const R* u[3] = {u0, u1, u2};
   const size_t N = (size_t)g.nx * g.ny * g.nz;
   double acc = 0.0;
   for (size_t o = (size_t)blockIdx.x * NTHREADS + threadIdx.x; o < N; o += (size_t)gridDim.x * NTHREADS) {
     const int i = (int)(o % g.nx), j = (int)((o / g.nx) % g.ny), k = (int)(o / ((size_t)g.nx * g.ny));
-    if (!interior3<R>(g, i, j, k)) continue;
+    if (!interior3<R>(g, i, j, k)) {
+      // static pressure drop (Eq. objective_pipebend, p = rho / 3, dGamma = 1) over
+      // the inlet and outlet nodes on one face only; the unit densities cancel
+      if (c.kappa_p != 0.0 && (i == 0 || i == g.nx - 1) && j > 0 && j < g.ny - 1 && k > 0 && k < g.nz - 1)
+        acc += (i == 0 ? c.kappa_p : -c.kappa_p) * (double)drho[o] / 3.0;
+      continue;
+    }
     R SS = R(0), uu = R(0);
     for (int aa = 0; aa < 3; ++aa) {
       uu += u[aa][o] * u[aa][o];
@@ -1673,6 +1687,7 @@ Coef3<R> coef3(const lks_problem_desc& d) {
   c.q_alpha = (R)d.q_alpha;
   c.drho_out = (R)(d.rho_out - 1.0);
   c.u_max = d.u_max;
+  c.kappa_p = d.kappa_p;
   return c;
 }
 Geom3 geom3(const lks_problem_desc& d) { return Geom3{d.nx, d.ny, d.nz}; }
@@ -1818,8 +1833,8 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
   }
   double* part = reinterpret_cast<double*>(c.ws + L.jpart);
   double* jval = reinterpret_cast<double*>(c.ws + L.jval);
-  objective3_kernel<R><<<L.jblocks, NTHREADS, 0, c.stream>>>(gam, st3<R>(c, cur, 1), st3<R>(c, cur, 2),
-                                                             st3<R>(c, cur, 3), g, cf, part);
+  objective3_kernel<R><<<L.jblocks, NTHREADS, 0, c.stream>>>(gam, st3<R>(c, cur, 0), st3<R>(c, cur, 1),
+                                                             st3<R>(c, cur, 2), st3<R>(c, cur, 3), g, cf, part);
   reduce_partials_kernel<<<1, NTHREADS, 0, c.stream>>>(part, L.jblocks, nullptr, 0, jval);
   CK3(c, cudaGetLastError());
   *c.launches += 2;
@@ -1988,9 +2003,10 @@ void lsq19(const double* A, int nc, const double* rhs, double* x) {
 
 }  // namespace
 
-void flow_moment_map3(double A, int cls, double* out) {
+void flow_moment_map3(double A, int cls, double* out, double* unit) {
   const int n[3] = {cls / 9 - 1, (cls / 3) % 3 - 1, cls % 3 - 1};
   std::memset(out, 0, sizeof(double) * kNA3 * 19);
+  if (unit) std::memset(unit, 0, sizeof(double) * kNA3);
   if (n[0] == 0 && n[1] == 0 && n[2] == 0) return;
   const int faces = std::abs(n[0]) + std::abs(n[1]) + std::abs(n[2]);
   const bool pressure = faces == 1 && n[0] == 1;
@@ -2041,6 +2057,16 @@ void flow_moment_map3(double A, int cls, double* out) {
       for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * X[U[q]][k];
       out[r * 19 + k] = s;
     }
+  if (unit) {  // the unknowns' response to a unit term in every row, and its moments
+    double rhs[19], x[24];
+    for (int r = 0; r < 19; ++r) rhs[r] = -1.0;
+    lsq19(Am.data(), nc, rhs, x);
+    for (int r = 0; r < kNA3; ++r) {
+      double s = 0.0;
+      for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * x[q];
+      unit[r] = s;
+    }
+  }
 }
 
 Layout3 make_layout3(const lks_problem_desc& d) {
@@ -2065,15 +2091,24 @@ Layout3 make_layout3(const lks_problem_desc& d) {
   L.jpart = take(sizeof(double) * L.jblocks);
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
-  L.emap = take(L.rsize * kClasses3 * kNA3 * 19);
+  L.emap = take(L.rsize * kClasses3 * kNA3 * 20);  // maps, then the boundary objective terms
   L.total = off;
   return L;
 }
 
 lks_status upload_maps3(const Ctx3& c) {
   const double A = (1.0 / 6.0 - c.d->nu) * 4.5;
-  std::vector<double> m((size_t)kClasses3 * kNA3 * 19);
-  for (int cls = 0; cls < kClasses3; ++cls) flow_moment_map3(A, cls, &m[(size_t)cls * kNA3 * 19]);
+  // kClasses3 maps of 10 x 19, then per class the moments' response to the boundary
+  // objective term of every row: +kappa_p on the inlet face (class of n = (-1, 0, 0)),
+  // -kappa_p on the outlet face (n = (1, 0, 0)), absorbed there by lambda~
+  std::vector<double> m((size_t)kClasses3 * kNA3 * 20, 0.0);
+  double* off = &m[(size_t)kClasses3 * kNA3 * 19];
+  for (int cls = 0; cls < kClasses3; ++cls) {
+    double unit[kNA3];
+    flow_moment_map3(A, cls, &m[(size_t)cls * kNA3 * 19], unit);
+    const double jb = cls == 4 ? c.d->kappa_p : (cls == 22 ? -c.d->kappa_p : 0.0);
+    for (int r = 0; r < kNA3; ++r) off[cls * kNA3 + r] = jb * unit[r];
+  }
   if (c.L->rsize == 8) {
     CK3(c, cudaMemcpy(c.ws + c.L->emap, m.data(), m.size() * 8, cudaMemcpyHostToDevice));
   } else {

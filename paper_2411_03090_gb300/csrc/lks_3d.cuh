@@ -43,7 +43,8 @@ struct Ctx3 {
   std::string* err;
 };
 
-// Uploads the host-built adjoint edge maps (kClasses3 x 10 x 19).
+// Uploads the host-built adjoint edge maps (kClasses3 x 10 x 19) and the per-class
+// boundary objective terms of the moments (kClasses3 x 10).
 lks_status upload_maps3(const Ctx3& c);
 // Steps 2-3: gamma -> state after n_steps; J of the final state into J_dev (may be
 // null).  *cur receives the buffer (0 = A, 1 = B) holding the final state, *path the
@@ -59,7 +60,9 @@ lks_status sensitivity3(const Ctx3& c, int cur, int acur, void* out);
 
 // Host-only: the 10 x 19 adjoint moment map of one edge class at parameter A
 // (rows rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz; columns the 19
-// gathered f~, zero for unknown links).
-void flow_moment_map3(double A, int cls, double* out);
+// gathered f~, zero for unknown links).  unit (10 values, may be null): the moments
+// when every residual row carries a unit boundary objective term and the gathered
+// f~ are zero (Eqs. afboundaryu / afboundaryp).
+void flow_moment_map3(double A, int cls, double* out, double* unit);
 
 }  // namespace lks3

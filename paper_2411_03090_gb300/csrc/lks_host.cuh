@@ -42,7 +42,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
     if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
     if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
-    for (int q = 0; q < 4; ++q)
+    if (!std::isfinite(d->kappa_p)) return bad("kappa_p must be finite");
+    for (int q = 0; q < 2; ++q)
       if (d->reserved[q] != 0) return bad("reserved fields must be zero");
     return LKS_OK;
   }
@@ -64,7 +65,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
   if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
   if (d->res_steps < 0 || d->res_steps > 3) return bad("res_steps must lie in 0..3");
-  for (int q = 0; q < 4; ++q)
+  if (d->kappa_p != 0.0) return bad("D2Q9: kappa_p must be 0 (the pressure-drop term is D3Q19 only)");
+  for (int q = 0; q < 2; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }

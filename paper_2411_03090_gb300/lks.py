@@ -53,7 +53,8 @@ class Desc(C.Structure):
         ("n_steps", C.c_int32), ("n_adj", C.c_int32),
         ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
         ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("res_steps", C.c_int32),
-        ("reserved", C.c_int32 * 4),
+        ("kappa_p", C.c_double),
+        ("reserved", C.c_int32 * 2),
     ]
 
 
@@ -159,7 +160,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.real_type = REAL[real]
     if hasattr(pb, "nz"):
         d.lattice, d.nz = LATTICE_D3Q19, int(pb.nz)
-        for name in ("nu", "alpha_bar", "q_alpha", "u_max", "rho_out"):
+        for name in ("nu", "alpha_bar", "q_alpha", "u_max", "rho_out", "kappa_p"):
             setattr(d, name, float(getattr(pb, name)))
         d.steady, d.thermal = 1, 0
         d.n_steps, d.n_adj = int(pb.n_steps), int(pb.n_adj)

@@ -84,9 +84,18 @@ def test_descriptor_validation():
             lks.workspace_size(bad)
         assert e.value.status == 1
     bad = lks.make_desc(pb)
-    bad.reserved[3] = 1
+    bad.reserved[1] = 1
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
+    bad = lks.make_desc(pb)
+    bad.kappa_p = 1.0  # the pressure-drop term is D3Q19 only
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(bad)
+    d3 = lks.make_desc(inputs.config4())
+    assert d3.kappa_p == 1.0 and lks.workspace_size(d3) > 0
+    d3.kappa_p = float("nan")
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(d3)
     for ks in (1, 2, 3):
         assert lks.workspace_size(lks.make_desc(pb, res_steps=ks)) == lks.workspace_size(d)
 

@@ -73,7 +73,7 @@ def test_column_kernels_match_step_kernels_and_oracle(shape):
     z) against the plane-march kernels and the oracle's gradient after the same
     steps.  116 x 40 has tiles whose threads are all off the x and y faces (the fast
     variants)."""
-    pb = duct(*shape, n=40)
+    pb = duct(*shape, n=40, kappa_p=1.0)
     g = pb.gamma()
     gt = torch.from_numpy(g)
     ref = O.steady_gradient3(pb, g)
@@ -100,6 +100,34 @@ def test_column_kernels_match_step_kernels_and_oracle(shape):
     for name in ("u", "v", "w"):
         assert rel_l2(getattr(col, name), getattr(ref["state"], name)) <= 1e-5, name
     assert rel_l2(col.rho - 1, ref["state"].rho - 1) <= 1e-4
+
+
+@pytest.mark.parametrize("path", ["auto", "step"])
+@pytest.mark.parametrize("real,tol_g,tol_J", [("f64", 1e-10, 1e-11), ("f32", 1e-3, 1e-5)])
+@pytest.mark.parametrize("shape", [(44, 21, 40), (37, 21, 40)])
+def test_pressure_drop_objective_matches_oracle(real, tol_g, tol_J, shape, path):
+    """J = J_O + kappa_p J_p (Eq. objective_pipebend): J, the adjoint (whose inlet and
+    outlet edge rules carry the boundary objective term) and dJ/dgamma against the
+    oracle; the pressure-drop part alone (kappa_p = 2 minus kappa_p = 0) as well."""
+    base = duct(*shape)
+    g = base.gamma()
+    out = {}
+    for kp in (0.0, 2.0):
+        pb = base.with_(kappa_p=kp)
+        ref = O.steady_gradient3(pb, g)
+        s = LKS(pb, real=real, path=path)
+        J, grad = s.gradient(torch.from_numpy(g))
+        assert abs(J.item() - ref["J"]) <= tol_J * abs(ref["J"])
+        adj = [a.double().cpu().numpy() for a in s.get_adjoint()]
+        for q in range(O.NADJ3):
+            assert rel_l2(adj[q], ref["adjoint"][q]) <= tol_g, (kp, O.ADJ3_NAMES[q])
+        out[kp] = (J.item(), grad.double().cpu().numpy(), ref)
+    Jp = out[2.0][0] - out[0.0][0]
+    Jp_ref = out[2.0][2]["J"] - out[0.0][2]["J"]
+    assert abs(Jp - Jp_ref) <= 10 * tol_J * abs(out[2.0][2]["J"])
+    dg = out[2.0][1] - out[0.0][1]
+    dg_ref = out[2.0][2]["dJdgamma"] - out[0.0][2]["dJdgamma"]
+    assert rel_l2(dg, dg_ref) <= 3 * tol_g
 
 
 def test_gradient_host_and_query():
