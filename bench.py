@@ -576,7 +576,7 @@ def main():
     }
     if not args.no_cpu_baseline:
         try:
-            n_cb = oracle_steps_for(pb, 10.0)  # a bounded sample: about 10 s of host work
+            n_cb = oracle_steps_for(pb, 15.0)  # a bounded sample: 10-15 s of host work (the 2-step calibration runs long)
             out["cpu_baseline"] = cpu_baseline(pb, n_cb, n_cb)
         except Exception as e:  # the oracle is a reported baseline, not the product
             out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
