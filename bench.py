@@ -252,6 +252,8 @@ def run_checkpoint_study(args):
 
     reps = max(1, min(args.steps, 2))
     rows = []
+    clocks = ClockSampler(0)  # sampled over the whole study
+    clocks.start()
     plain = LKS(pb, real="f32", checkpoint_every=0, device=dev)
     t_plain, J_plain, g_plain = timed(plain, reps)
     ws_plain = plain.workspace.numel()
@@ -269,8 +271,8 @@ def run_checkpoint_study(args):
                          "workspace_GB": s.workspace.numel() / 1e9, "grad_rel_err_vs_plain": err, "J": J})
             del s
             torch.cuda.empty_cache()
+    clk = clocks.stop()
     head = [r for r in rows if r["K"] == 100 and r["snapshot"] == "bf16"][0]
-    updates = N * pb.n_steps * 3  # forward + recomputed forward + adjoint per level
     print(json.dumps({
         "metric": METRIC, "value": N * 2 * pb.n_steps / head["s_per_gradient"] / 1e6, "unit": "MLUPS",
         "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": head["s_per_gradient"] * 1e3,
@@ -281,7 +283,8 @@ def run_checkpoint_study(args):
                    "l2": "flushed before each timed gradient"},
         "checkpoint_study": rows,
         "speedup_vs_plain": t_plain / head["s_per_gradient"],
-        "memory_ratio_vs_plain": head["workspace_GB"] / (ws_plain / 1e9)}))
+        "memory_ratio_vs_plain": head["workspace_GB"] / (ws_plain / 1e9),
+        "clocks": clk}))
 
 
 def run_batch_study(args):

@@ -470,7 +470,11 @@ lks_status launch_adj_resident(lks_handle* h, int n) {
 // ------------------------------------------------------------------------------------
 // TMA-staged per-step kernels (FP32, nx % 4 == 0)
 // ------------------------------------------------------------------------------------
-constexpr int kFwdNT = 256, kAdjNT = 512;
+// Threads per CTA: the 66 x 10 coefficient region of a 64 x 8 tile takes two even
+// passes of the forward's 352 threads (two CTAs per SM) and one pass of the
+// adjoint's 704 (one CTA per SM); 256 / 512 left a short last pass and the other
+// threads waiting at its barrier (8 % slower on the 1024 x 512 thermal gradient).
+constexpr int kFwdNT = 352, kAdjNT = 704;
 
 bool tma_ok(lks_handle* h) {
   return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
