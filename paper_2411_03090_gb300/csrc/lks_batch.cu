@@ -949,7 +949,7 @@ lks_status lks_batch_create(int32_t n, const lks_problem_desc* descs, const lks_
     delete b;
     return LKS_ERR_WORKSPACE;
   }
-  if (!encode_fn()) {  // the tensor-map encoder of the driver is required
+  if (!encode_fn()) {  // the tensor-map encoder of the CUDA driver is required
     delete b;
     return LKS_ERR_CUDA;
   }

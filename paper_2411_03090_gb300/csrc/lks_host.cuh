@@ -1,7 +1,7 @@
 // lks_host.cuh -- host helpers shared by the single-lattice and the batched C ABI:
 // descriptor checks, coefficient and geometry records of a problem, the inlet
 // amplitude of the pulsed inflow, the generalized-inverse edge moment maps of the
-// adjoint (Sec. 2.5, App. A) and the driver entry point that encodes tensor maps.
+// adjoint (Sec. 2.5, App. A) and the CUDA driver entry point that encodes tensor maps.
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
