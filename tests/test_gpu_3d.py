@@ -67,13 +67,14 @@ def test_gradient_matches_oracle(real, tol_f, tol_g, tol_J, shape, path):
     assert np.all(gr[0] == 0) and np.all(gr[:, 0] == 0) and np.all(gr[:, :, 0] == 0)
 
 
-@pytest.mark.parametrize("shape", [(60, 17, 37), (28, 8, 5), (44, 21, 40), (88, 9, 70), (116, 40, 37)])
+@pytest.mark.parametrize("shape", [(60, 17, 37), (28, 8, 5), (44, 21, 40), (88, 9, 70), (116, 40, 37), (8, 5, 5),
+                                   (12, 6, 23)])
 def test_column_kernels_match_step_kernels_and_oracle(shape):
     """The warp-column z-march forward and adjoint (28 x 8 tiles, ragged in x, y and
     z) against the plane-march kernels and the oracle's gradient after the same
     steps.  116 x 40 has tiles whose threads are all off the x and y faces (the fast
     variants)."""
-    pb = duct(*shape, n=40, kappa_p=1.0)
+    pb = duct(*shape, n=40, kappa_p=1.0, Re=20.0 if shape[1] >= 9 else 2.0)  # nu >= 0.02
     g = pb.gamma()
     gt = torch.from_numpy(g)
     ref = O.steady_gradient3(pb, g)
