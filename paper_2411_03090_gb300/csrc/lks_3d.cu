@@ -1324,6 +1324,58 @@ struct Adj3CArgs {
   int zc;  // z planes per CTA
 };
 
+// Index of the link with velocity (x, y, z).
+__host__ __device__ constexpr int link3(int x, int y, int z) {
+  int k = 0;
+  while (k < 19 && !(c3(k, 0) == x && c3(k, 1) == y && c3(k, 2) == z)) ++k;
+  return k;
+}
+
+// The ten ALKS moments (rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz) of
+// the 19 gathered values F at an interior node, sum_k w_k F_k {1, c_k, c_k c_k}
+// (Sec. 2.5), summed by link class: the pair of axis links of each axis, and the
+// four diagonal links of each pair of axes, which enter the momentum of both axes,
+// the two diagonal second moments and the off-diagonal one.
+__device__ __forceinline__ void adj_moments3(const float (&F)[19], float (&m)[kNA3]) {
+  constexpr float w0 = (float)w3d(link3(0, 0, 0)), w1 = (float)w3d(link3(1, 0, 0)), w2 = (float)w3d(link3(1, 1, 0));
+  constexpr int sa[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};  // moment index of s~_ab
+  float sum_ax[3], dif_ax[3];
+  static_for<0, 3>([&](auto aa) {
+    constexpr int a = decltype(aa)::value;
+    constexpr int kp = link3(a == 0, a == 1, a == 2), km = link3(-(a == 0), -(a == 1), -(a == 2));
+    sum_ax[a] = F[kp] + F[km];
+    dif_ax[a] = F[kp] - F[km];
+  });
+  float mom[3] = {w1 * dif_ax[0], w1 * dif_ax[1], w1 * dif_ax[2]};
+  float dia[3] = {w1 * sum_ax[0], w1 * sum_ax[1], w1 * sum_ax[2]};
+  float s4all = 0.f;
+  static_for<0, 3>([&](auto pp) {
+    constexpr int p = decltype(pp)::value;
+    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;  // axis pairs (x,y), (x,z), (y,z)
+    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
+    constexpr int kpp = link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
+    constexpr int kmm = link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
+    constexpr int kpm = link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
+    constexpr int kmp = link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
+    const float P = F[kpp] + F[kmm], Q = F[kpm] + F[kmp];
+    const float Rr = F[kpp] - F[kmm], S = F[kpm] - F[kmp];
+    const float s4 = P + Q;
+    s4all += s4;
+    m[sa[a][b]] = w2 * (P - Q);
+    mom[a] += w2 * (Rr + S);
+    mom[b] += w2 * (Rr - S);
+    dia[a] += w2 * s4;
+    dia[b] += w2 * s4;
+  });
+  m[0] = w0 * F[0] + (w1 * (sum_ax[0] + sum_ax[1] + sum_ax[2]) + w2 * s4all);
+  m[1] = mom[0];
+  m[2] = mom[1];
+  m[3] = mom[2];
+  m[4] = dia[0];
+  m[7] = dia[1];
+  m[9] = dia[2];
+}
+
 // d/dx at node `at` of n from values at offsets 0, +-1, +-2 (one-sided on a face),
 // the same formulas as dax.
 __device__ __forceinline__ float dax_v(float f0, float fp1, float fp2, float fm1, float fm2, int at, int n) {
@@ -1518,23 +1570,7 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
       }
       R m[kNA3];
       if (FAST || (n0 | n1 | n2) == 0) {
-#pragma unroll
-        for (int r = 0; r < kNA3; ++r) m[r] = R(0);
-        static_for<0, 19>([&](auto kk) {
-          constexpr int k = decltype(kk)::value;
-          constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
-          const R wf = R(w3d(k)) * F[k];
-          m[0] += wf;
-          if constexpr (cx != 0) m[1] += R(cx) * wf;
-          if constexpr (cy != 0) m[2] += R(cy) * wf;
-          if constexpr (cz != 0) m[3] += R(cz) * wf;
-          if constexpr (cx != 0) m[4] += wf;
-          if constexpr (cx * cy != 0) m[5] += R(cx * cy) * wf;
-          if constexpr (cx * cz != 0) m[6] += R(cx * cz) * wf;
-          if constexpr (cy != 0) m[7] += wf;
-          if constexpr (cy * cz != 0) m[8] += R(cy * cz) * wf;
-          if constexpr (cz != 0) m[9] += wf;
-        });
+        adj_moments3(F, m);
         m[1] = (m[1] + C[1]) * C[0];
         m[2] = (m[2] + C[2]) * C[0];
         m[3] = (m[3] + C[3]) * C[0];
