@@ -118,7 +118,10 @@ typedef struct {
                                  this that fits the tile shape and shared memory runs */
     double kappa_p;           /* D3Q19: weight of the static pressure drop in J
                                  (Eq. objective_pipebend, see below); D2Q9: 0        */
-    int32_t reserved[2];      /* must be zero                                        */
+    double tol;               /* steady D2Q9: > 0 marches to a relative step change
+                                 of tol (see lks_forward); 0 fixed step counts        */
+    int32_t max_steps;        /* tol > 0: step limit of each march (>= n_steps, n_adj) */
+    int32_t reserved[1];      /* must be zero                                        */
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in
@@ -153,6 +156,9 @@ typedef struct {
     int32_t res_steps_fwd;    /* steps per band exchange of the last resident forward
                                  march (0: none ran)                                  */
     int32_t res_steps_adj;    /* the same for the last resident adjoint march        */
+    double fwd_change;        /* tol > 0: relative change of the last measured forward
+                                 step (0: none measured)                              */
+    double adj_change;        /* the same for the adjoint                            */
 } lks_stats;
 
 typedef struct lks_handle lks_handle;
@@ -174,7 +180,12 @@ lks_status lks_create(const lks_problem_desc *desc, void *workspace_dev, size_t 
  * workspace) and writes the objective J to J_dev (one double, device).  Steady: J
  * is J_O of the final state.  Unsteady: J is the sum of J_O over levels 1..n_steps;
  * snapshots or the full trajectory are kept for the adjoint.  J_O is the total
- * dissipation over interior nodes, sum nu/2 S:S + alpha_gamma |u|^2, plus kappa_T T. */
+ * dissipation over interior nodes, sum nu/2 S:S + alpha_gamma |u|^2, plus kappa_T T.
+ * Steady D2Q9 with tol > 0: after the n_steps steps one more step is taken and its
+ * relative change r = max(|du| + |dv|) / max(|u| + |v|) measured; chunks of n_steps
+ * steps and a measured step repeat until r <= tol or max_steps steps have run.  If
+ * the limit comes first the call returns LKS_ERR_NOT_CONVERGED with the state and J
+ * of the last step in place (lks_query reports r as fwd_change). */
 lks_status lks_forward(lks_handle *h, const void *gamma_dev, double *J_dev);
 
 /* Step 4 (Sec. 2.5, Eqs. ap-aq, afeq, ageq, albef_ex, ftilde; App. A): the ALKS
@@ -182,6 +193,10 @@ lks_status lks_forward(lks_handle *h, const void *gamma_dev, double *J_dev);
  * generalized-inverse edge rule.  Steady: n_adj iterations on the final state.
  * Unsteady: backward over all levels (recomputing segments from snapshots when
  * checkpoint_every > 0) and the sensitivity accumulated on the way.
+ * Steady D2Q9 with tol > 0: iterations in chunks of n_adj, each followed by one
+ * measured iteration (the relative change of u~, as for lks_forward), until the
+ * change is <= tol or max_steps iterations have run (LKS_ERR_NOT_CONVERGED, the
+ * adjoint of the last iteration in place; adj_change in lks_query).
  * LKS_ERR_STATE if lks_forward has not run. */
 lks_status alks_adjoint(lks_handle *h);
 

@@ -40,7 +40,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 // ------------------------------------------------------------------------------------
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
-  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0, mat = 0;
+  size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0, mat = 0, chg = 0;
   size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
@@ -83,6 +83,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.jobj = take(sizeof(double) * L.obj_blocks);
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
+  L.chg = take(2 * sizeof(unsigned));  // change of a measured step (tol > 0)
   L.emap = take(L.rsize * 9 * 60);
   L.flags = take(sizeof(int) * (size_t)((d->nx + 31) / 32) * (size_t)((d->ny + 7) / 8));
   L.mat = take(fb * 3);  // 1/(1+alpha), alpha, B (FP32 staged kernels)
@@ -129,6 +130,7 @@ struct lks_handle {
   int tma_grid_fwd = 0, tma_grid_adj[2][2] = {{0, 0}, {0, 0}};  // adj: [thermal][same state]
   int sms = 0;        // multiprocessors of the device (queried once)
   int res_steps_fwd = 0, res_steps_adj = 0;  // steps per exchange of the last resident marches
+  double fwd_change = 0.0, adj_change = 0.0;  // relative change of the last measured steps
   bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
   lks3::Layout3 L3;
   std::string err;
@@ -756,6 +758,25 @@ lks_status launch_objective(lks_handle* h, const R* u, const R* v, const R* T, d
 
 int elementwise_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
 
+// Relative change of one step of two fields (a0 -> a1, b0 -> b1):
+// max(|da| + |db|) / max(|a1| + |b1|).  Reads two words back (synchronises the stream).
+template <typename R>
+lks_status step_change(lks_handle* h, const R* a0, const R* a1, const R* b0, const R* b1, double* rel) {
+  unsigned* dv = reinterpret_cast<unsigned*>(h->ws + h->L.chg);
+  CKH(h, cudaMemsetAsync(dv, 0, 2 * sizeof(unsigned), h->stream));
+  change_kernel<R><<<elementwise_grid(h->L.N), 256, 0, h->stream>>>(a0, a1, b0, b1, h->L.N, dv);
+  CKH(h, cudaGetLastError());
+  h->launches++;
+  unsigned hv[2] = {0u, 0u};
+  CKH(h, cudaMemcpyAsync(hv, dv, sizeof(hv), cudaMemcpyDeviceToHost, h->stream));
+  CKH(h, cudaStreamSynchronize(h->stream));
+  float d = 0.f, m = 0.f;
+  std::memcpy(&d, &hv[0], sizeof(float));
+  std::memcpy(&m, &hv[1], sizeof(float));
+  *rel = m > 0.f ? (double)d / (double)m : (double)d;
+  return LKS_OK;
+}
+
 // Snapshot encode / decode of one field with a per-field scale (max |x|).
 template <typename R, typename S>
 __global__ void absmax_kernel(const R* __restrict__ x, size_t n, float* out) {
@@ -887,13 +908,36 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   double* jobj = reinterpret_cast<double*>(h->ws + L.jobj);
   double* jval = reinterpret_cast<double*>(h->ws + L.jval);
   lks_status st;
+  bool converged = true;
   if (d.steady) {
-    if (resident_wanted(h, false)) {
-      if ((st = launch_fwd_resident<R>(h, d.n_steps)) != LKS_OK) return st;
-    } else {
-      if (d.exec_path == LKS_PATH_RESIDENT) return fail(h, LKS_ERR_INVALID_ARG, "resident march unavailable");
-      for (int s = 1; s <= d.n_steps; ++s)
-        if ((st = launch_fwd<R>(h, s, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
+    if (!resident_wanted(h, false) && d.exec_path == LKS_PATH_RESIDENT)
+      return fail(h, LKS_ERR_INVALID_ARG, "resident march unavailable");
+    // fixed count: one chunk of n_steps; tol > 0: chunks, each followed by a measured step
+    h->fwd_change = 0.0;
+    converged = !(d.tol > 0.0);
+    int done = 0, chunk = d.n_steps;
+    for (;;) {
+      if (chunk > 0 && resident_wanted(h, false)) {
+        if ((st = launch_fwd_resident<R>(h, chunk)) != LKS_OK) return st;
+      } else {
+        for (int s = 0; s < chunk; ++s)
+          if ((st = launch_fwd<R>(h, h->t + 1, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
+      }
+      done += chunk;
+      if (converged) break;
+      const int prev = h->cur, path = h->fwd_path;  // the chunks' path stays the reported one
+      if ((st = launch_fwd<R>(h, h->t + 1, nullptr, nullptr, nullptr, nullptr)) != LKS_OK) return st;
+      if (chunk > 0) h->fwd_path = path;
+      ++done;
+      if ((st = step_change<R>(h, state_ptr<R>(h, prev, 1), state_ptr<R>(h, h->cur, 1), state_ptr<R>(h, prev, 2),
+                               state_ptr<R>(h, h->cur, 2), &h->fwd_change)) != LKS_OK)
+        return st;
+      if (h->fwd_change <= d.tol) {
+        converged = true;
+        break;
+      }
+      if (done >= d.max_steps) break;
+      chunk = std::min(d.n_steps, d.max_steps - done - 1);
     }
   } else {
     CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
@@ -926,7 +970,7 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   h->launches++;
   if (J_dev) CKH(h, cudaMemcpyAsync(J_dev, jval, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
   h->phase = 1;
-  return LKS_OK;
+  return converged ? LKS_OK : fail(h, LKS_ERR_NOT_CONVERGED, "forward march did not reach tol in max_steps");
 }
 
 template <typename R>
@@ -951,14 +995,34 @@ lks_status adjoint_impl(lks_handle* h) {
     const R* u = state_ptr<R>(h, h->cur, 1);
     const R* v = state_ptr<R>(h, h->cur, 2);
     const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
-    if (resident_wanted(h, true)) {
-      if ((st = launch_adj_resident<R>(h, d.n_adj)) != LKS_OK) return st;
-    } else {
-      for (int it = 0; it < d.n_adj; ++it)
-        if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+    h->adj_change = 0.0;
+    bool converged = !(d.tol > 0.0);
+    int done = 0, chunk = d.n_adj;
+    for (;;) {
+      if (chunk > 0 && resident_wanted(h, true)) {
+        if ((st = launch_adj_resident<R>(h, chunk)) != LKS_OK) return st;
+      } else {
+        for (int it = 0; it < chunk; ++it)
+          if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+      }
+      done += chunk;
+      if (converged) break;
+      const int prev = h->acur, path = h->adj_path;  // the chunks' path stays the reported one
+      if ((st = launch_adj<R>(h, u, v, u, v, T, nullptr, 0, 0)) != LKS_OK) return st;
+      if (chunk > 0) h->adj_path = path;
+      ++done;
+      if ((st = step_change<R>(h, adj_ptr<R>(h, prev, 1), adj_ptr<R>(h, h->acur, 1), adj_ptr<R>(h, prev, 2),
+                               adj_ptr<R>(h, h->acur, 2), &h->adj_change)) != LKS_OK)
+        return st;
+      if (h->adj_change <= d.tol) {
+        converged = true;
+        break;
+      }
+      if (done >= d.max_steps) break;
+      chunk = std::min(d.n_adj, d.max_steps - done - 1);
     }
     h->phase = 2;
-    return LKS_OK;
+    return converged ? LKS_OK : fail(h, LKS_ERR_NOT_CONVERGED, "adjoint march did not reach tol in max_steps");
   }
   CKH(h, cudaMemsetAsync(h->ws + L.sens, 0, fb, h->stream));
   CKH(h, cudaMemsetAsync(h->ws + L.sens64, 0, sizeof(double) * L.N, h->stream));
@@ -1349,6 +1413,8 @@ lks_status lks_query(lks_handle* h, lks_stats* out) {
   out->adj_path = h->adj_path;
   out->res_steps_fwd = h->res_steps_fwd;
   out->res_steps_adj = h->res_steps_adj;
+  out->fwd_change = h->fwd_change;
+  out->adj_change = h->adj_change;
   return status ? (lks_status)status : LKS_OK;
 }
 

@@ -43,7 +43,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
     if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
     if (!std::isfinite(d->kappa_p)) return bad("kappa_p must be finite");
-    for (int q = 0; q < 2; ++q)
+    if (d->tol != 0.0) return bad("D3Q19: tol must be 0 (fixed step counts)");
+    for (int q = 0; q < 1; ++q)
       if (d->reserved[q] != 0) return bad("reserved fields must be zero");
     return LKS_OK;
   }
@@ -66,7 +67,12 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
   if (d->res_steps < 0 || d->res_steps > 3) return bad("res_steps must lie in 0..3");
   if (d->kappa_p != 0.0) return bad("D2Q9: kappa_p must be 0 (the pressure-drop term is D3Q19 only)");
-  for (int q = 0; q < 2; ++q)
+  if (!(d->tol >= 0.0) || !std::isfinite(d->tol)) return bad("tol must be >= 0");
+  if (d->tol > 0.0) {
+    if (!d->steady) return bad("tol > 0: steady problems only");
+    if (d->max_steps < d->n_steps || d->max_steps < d->n_adj) return bad("tol > 0: max_steps >= n_steps, n_adj");
+  }
+  for (int q = 0; q < 1; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }

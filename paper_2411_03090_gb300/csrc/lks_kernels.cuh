@@ -835,6 +835,27 @@ __global__ void copy_shift_kernel(const R* __restrict__ x, S* __restrict__ y, si
     y[o] = (S)(x[o] + shift);
 }
 
+// Change of one step of two fields: out[0] = max over nodes of |a1 - a0| + |b1 - b0|,
+// out[1] = max of |a1| + |b1|, both as the bits of non-negative floats (which order
+// like the values, so an integer maximum finds them).  out is zeroed by the caller.
+template <typename R>
+__global__ void change_kernel(const R* __restrict__ a0, const R* __restrict__ a1, const R* __restrict__ b0,
+                              const R* __restrict__ b1, size_t n, unsigned* __restrict__ out) {
+  float dm = 0.f, mm = 0.f;
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    dm = fmaxf(dm, (float)(fabs(a1[o] - a0[o]) + fabs(b1[o] - b0[o])));
+    mm = fmaxf(mm, (float)(fabs(a1[o]) + fabs(b1[o])));
+  }
+  for (int off = 16; off > 0; off >>= 1) {
+    dm = fmaxf(dm, __shfl_xor_sync(0xffffffffu, dm, off));
+    mm = fmaxf(mm, __shfl_xor_sync(0xffffffffu, mm, off));
+  }
+  if ((threadIdx.x & 31) == 0) {
+    atomicMax(out, __float_as_uint(dm));
+    atomicMax(out + 1, __float_as_uint(mm));
+  }
+}
+
 // Accumulate a in FP64: acc += a; then a = 0.
 template <typename R>
 __global__ void flush_accum_kernel(R* __restrict__ a, double* __restrict__ acc, size_t n) {

@@ -54,7 +54,8 @@ class Desc(C.Structure):
         ("checkpoint_every", C.c_int32), ("snapshot_type", C.c_int32),
         ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("res_steps", C.c_int32),
         ("kappa_p", C.c_double),
-        ("reserved", C.c_int32 * 2),
+        ("tol", C.c_double), ("max_steps", C.c_int32),
+        ("reserved", C.c_int32 * 1),
     ]
 
 
@@ -63,7 +64,8 @@ class Stats(C.Structure):
                 ("kernel_launches", C.c_int64), ("workspace_bytes", C.c_size_t),
                 ("device_status", C.c_int32), ("phase", C.c_int32),
                 ("fwd_path", C.c_int32), ("adj_path", C.c_int32),
-                ("res_steps_fwd", C.c_int32), ("res_steps_adj", C.c_int32)]
+                ("res_steps_fwd", C.c_int32), ("res_steps_adj", C.c_int32),
+                ("fwd_change", C.c_double), ("adj_change", C.c_double)]
 
 
 LKS_BATCH_VERSION = 1
@@ -151,9 +153,10 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
-              path: str = "auto", res_steps: int = 0) -> Desc:
+              path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0) -> Desc:
     """Descriptor from an ``inputs.Problem``-like object (``inputs.Problem3``: a
-    D3Q19 duct)."""
+    D3Q19 duct).  tol > 0 (steady D2Q9): march to a relative step change of tol,
+    at most max_steps steps per march, in chunks of n_steps / n_adj."""
     d = Desc()
     d.version = LKS_DESC_VERSION
     d.nx, d.ny = int(pb.nx), int(pb.ny)
@@ -165,6 +168,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
         d.steady, d.thermal = 1, 0
         d.n_steps, d.n_adj = int(pb.n_steps), int(pb.n_adj)
         d.exec_path = PATH[path]
+        d.tol, d.max_steps = float(tol), int(max_steps)
         return d
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T"):
@@ -183,6 +187,8 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.snapshot_type = SNAP[snapshot]
     d.exec_path = PATH[path]
     d.res_steps = int(res_steps)
+    d.tol = float(tol)
+    d.max_steps = int(max_steps)
     return d
 
 
@@ -230,12 +236,12 @@ class LKS:
 
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
                  device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
-                 path: str = "auto", res_steps: int = 0):
+                 path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.pb = pb
-        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps)
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps, tol, max_steps)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.is3 = hasattr(pb, "nz")

@@ -84,7 +84,7 @@ def test_descriptor_validation():
             lks.workspace_size(bad)
         assert e.value.status == 1
     bad = lks.make_desc(pb)
-    bad.reserved[1] = 1
+    bad.reserved[0] = 1
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
     bad = lks.make_desc(pb)
@@ -96,6 +96,16 @@ def test_descriptor_validation():
     d3.kappa_p = float("nan")
     with pytest.raises(lks.LKSError):
         lks.workspace_size(d3)
+    d3 = lks.make_desc(inputs.config4(), tol=1e-6, max_steps=5000)  # D3Q19: fixed counts only
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(d3)
+    assert lks.workspace_size(lks.make_desc(pb, tol=1e-6, max_steps=pb.n_steps)) > 0
+    for kw in (dict(tol=-1.0), dict(tol=1e-6, max_steps=pb.n_steps - 1), dict(tol=float("inf"), max_steps=10**6)):
+        with pytest.raises(lks.LKSError):
+            lks.workspace_size(lks.make_desc(pb, **kw))
+    unsteady = inputs.config3().with_(nx=64, ny=32, n_steps=100)
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(lks.make_desc(unsteady, tol=1e-6, max_steps=1000))
     for ks in (1, 2, 3):
         assert lks.workspace_size(lks.make_desc(pb, res_steps=ks)) == lks.workspace_size(d)
 

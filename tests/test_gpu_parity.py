@@ -64,6 +64,68 @@ def test_forward_matches_oracle(real, tol, path):
     assert abs(J - O.objective(pb, g, st)) <= tol * abs(J)
 
 
+def test_tolerance_march_matches_oracle_at_the_same_step_count():
+    """tol > 0: chunks of n_steps with one measured step after each until the
+    relative change of a step is <= tol.  The state equals the oracle's after the
+    number of steps the library reports, the reported change is the oracle's
+    max |du| + |dv| of that step over max |u| + |v|, and the adjoint likewise."""
+    pb = small(n_steps=200, n_adj=200)
+    g = pb.gamma()
+    s = LKS(pb, real="f64", path="step", tol=1e-7, max_steps=60000)
+    s.lks_forward(torch.from_numpy(g))
+    q = s.query()
+    n = q.forward_steps
+    assert n % 201 == 0 and 0 < q.fwd_change <= 1e-7
+    st_prev, _, _, _ = O.forward(pb, g, n - 1)
+    st, _, _, _ = O.forward(pb, g, 1, state=st_prev)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(st)):
+        assert rel_l2(a, b) <= 1e-11
+    change = (np.abs(st.u - st_prev.u) + np.abs(st.v - st_prev.v)).max() / (np.abs(st.u) + np.abs(st.v)).max()
+    assert abs(q.fwd_change - change) <= 1e-6 * change  # the library takes the maxima in FP32
+    s.alks_adjoint()
+    q = s.query()
+    m = q.adjoint_steps
+    assert m % 201 == 0 and 0 < q.adj_change <= 1e-7
+    adj, _, _ = O.steady_adjoint(pb, g, st, m)
+    got_a = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    for qq in range(6):
+        assert rel_l2(got_a[qq], adj[qq]) <= 1e-10, qq
+
+
+def test_tolerance_march_on_the_resident_path():
+    """FP32, steady: the chunks run on the resident march and each measured step on
+    the per-step kernels; the state after the reported number of steps equals the
+    oracle's to FP32 tolerance."""
+    pb = inputs.channel(128, 64, Re=10.0, seed=2, sigma=2.0, strip=2, n_steps=500, n_adj=500)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="auto", tol=1e-4, max_steps=40000)
+    s.lks_forward(torch.from_numpy(g))
+    q = s.query()
+    assert q.fwd_path == 2 and q.forward_steps % 501 == 0 and q.fwd_change <= 1e-4
+    st, _, _, _ = O.forward(pb, g, q.forward_steps)
+    got, _ = gpu_state(s)
+    for a, b in zip(got[1:], oracle_state(st)[1:]):
+        assert rel_l2(a, b) <= 1e-5
+
+
+def test_tolerance_not_reached_reports_not_converged():
+    """A tolerance the march cannot reach within max_steps: LKS_ERR_NOT_CONVERGED after
+    exactly max_steps steps (chunks 100 + 1 + 100 + 1 + 47 + 1), state and J in place."""
+    pb = small(n_steps=100, n_adj=100)
+    g = torch.from_numpy(pb.gamma())
+    s = LKS(pb, real="f64", path="step", tol=1e-30, max_steps=250)
+    with pytest.raises(LKSError) as e:
+        s.lks_forward(g)
+    assert e.value.status == 5
+    q = s.query()
+    assert q.forward_steps == 250 and q.fwd_change > 0 and q.device_status == 0
+    st, _, _, _ = O.forward(pb, pb.gamma(), 250)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(st)):
+        assert rel_l2(a, b) <= 1e-12
+
+
 @pytest.mark.parametrize("nu", [0.1, 0.315])
 def test_poiseuille_on_gpu(nu):
     """Empty channel converges to the exact Poiseuille profile (FP64 instance)."""
