@@ -286,7 +286,7 @@ struct ResPlan {
 // Tile shapes of the resident marches: {TXR, TYR, threads}.
 // (64 x 14 puts the 512 x 256 channel on 8 x 19 = 152 tiles, one per SM of a GB300.)
 constexpr int kNResCfg = 4;
-// {tile x, tile y, threads}; the 64 x 14 forward with one step per exchange runs 640.
+// {tile x, tile y, threads}; the 64 x 14 forward with one step per exchange runs 768.
 constexpr int kResCfg[kNResCfg][3] = {{64, 16, 512}, {32, 16, 256}, {32, 8, 256}, {64, 14, 512}};
 
 int device_sms(lks_handle* h) {
@@ -440,9 +440,10 @@ lks_status launch_fwd_resident_th(lks_handle* h, int n, int k, int ks) {
   }
   if (k == 0) return launch_fwd_resident_cfg<R, TH, 64, 16, 512, 1>(h, n);
   if (k == 1) return launch_fwd_resident_cfg<R, TH, 32, 16, 256, 1>(h, n);
-  // 640 threads: the forward's phases on a 64 x 14 tile take fewer, fuller passes
-  // (2 % faster on the 512 x 256 channel); the adjoint measured 2 % slower with 640
-  if (k == 3) return launch_fwd_resident_cfg<R, TH, 64, 14, 640, 1>(h, n);
+  // 768 threads: the forward's phases on a 64 x 14 tile take fewer, fuller passes
+  // (the 62 x 12 coefficient region in one); 6 % faster per step on the 512 x 256
+  // channel than 640, 8 % than 512, and 896 was slower again
+  if (k == 3) return launch_fwd_resident_cfg<R, TH, 64, 14, 768, 1>(h, n);
   return launch_fwd_resident_cfg<R, TH, 32, 8, 256, 1>(h, n);
 }
 
