@@ -182,7 +182,8 @@ lks_status lks_create(const lks_problem_desc *desc, void *workspace_dev, size_t 
  * snapshots or the full trajectory are kept for the adjoint.  J_O is the total
  * dissipation over interior nodes, sum nu/2 S:S + alpha_gamma |u|^2, plus kappa_T T.
  * Steady D2Q9 with tol > 0: after the n_steps steps one more step is taken and its
- * relative change r = max(|du| + |dv|) / max(|u| + |v|) measured; chunks of n_steps
+ * relative change r = max(|du| + |dv|) / max(|u| + |v|) measured (the flow only;
+ * a thermal T is not part of the measure); chunks of n_steps
  * steps and a measured step repeat until r <= tol or max_steps steps have run.  If
  * the limit comes first the call returns LKS_ERR_NOT_CONVERGED with the state and J
  * of the last step in place (lks_query reports r as fwd_change). */
