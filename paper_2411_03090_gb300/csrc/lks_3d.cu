@@ -758,6 +758,89 @@ __global__ void __launch_bounds__(NTF3, 2) fwd3t_kernel(const __grid_constant__ 
   if (!ok) drain_and_fail();
 }
 
+// Index of the link with velocity (x, y, z).
+__host__ __device__ constexpr int link3(int x, int y, int z) {
+  int k = 0;
+  while (k < 19 && !(c3(k, 0) == x && c3(k, 1) == y && c3(k, 2) == z)) ++k;
+  return k;
+}
+
+// The ten ALKS moments (rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz) of
+// the 19 gathered values F at an interior node, sum_k w_k F_k {1, c_k, c_k c_k}
+// (Sec. 2.5), summed by link class: the pair of axis links of each axis, and the
+// four diagonal links of each pair of axes, which enter the momentum of both axes,
+// the two diagonal second moments and the off-diagonal one.
+__device__ __forceinline__ void adj_moments3(const float (&F)[19], float (&m)[kNA3]) {
+  constexpr float w0 = (float)w3d(link3(0, 0, 0)), w1 = (float)w3d(link3(1, 0, 0)), w2 = (float)w3d(link3(1, 1, 0));
+  constexpr int sa[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};  // moment index of s~_ab
+  float sum_ax[3], dif_ax[3];
+  static_for<0, 3>([&](auto aa) {
+    constexpr int a = decltype(aa)::value;
+    constexpr int kp = link3(a == 0, a == 1, a == 2), km = link3(-(a == 0), -(a == 1), -(a == 2));
+    sum_ax[a] = F[kp] + F[km];
+    dif_ax[a] = F[kp] - F[km];
+  });
+  float mom[3] = {w1 * dif_ax[0], w1 * dif_ax[1], w1 * dif_ax[2]};
+  float dia[3] = {w1 * sum_ax[0], w1 * sum_ax[1], w1 * sum_ax[2]};
+  float s4all = 0.f;
+  static_for<0, 3>([&](auto pp) {
+    constexpr int p = decltype(pp)::value;
+    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;  // axis pairs (x,y), (x,z), (y,z)
+    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
+    constexpr int kpp = link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
+    constexpr int kmm = link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
+    constexpr int kpm = link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
+    constexpr int kmp = link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
+    const float P = F[kpp] + F[kmm], Q = F[kpm] + F[kmp];
+    const float Rr = F[kpp] - F[kmm], S = F[kpm] - F[kmp];
+    const float s4 = P + Q;
+    s4all += s4;
+    m[sa[a][b]] = w2 * (P - Q);
+    mom[a] += w2 * (Rr + S);
+    mom[b] += w2 * (Rr - S);
+    dia[a] += w2 * s4;
+    dia[b] += w2 * s4;
+  });
+  m[0] = w0 * F[0] + (w1 * (sum_ax[0] + sum_ax[1] + sum_ax[2]) + w2 * s4all);
+  m[1] = mom[0];
+  m[2] = mom[1];
+  m[3] = mom[2];
+  m[4] = dia[0];
+  m[7] = dia[1];
+  m[9] = dia[2];
+}
+
+// Sum and first moments of the 19 increments F gathered at an interior node
+// (sum_k F_k and sum_k c_k F_k), summed by link class as in adj_moments3.
+__device__ __forceinline__ void fwd_moments3(const float (&F)[19], float& sm, float& mx, float& my, float& mz) {
+  float sum_ax = 0.f, dif[3];
+  static_for<0, 3>([&](auto aa) {
+    constexpr int a = decltype(aa)::value;
+    constexpr int kp = link3(a == 0, a == 1, a == 2), km = link3(-(a == 0), -(a == 1), -(a == 2));
+    sum_ax += F[kp] + F[km];
+    dif[a] = F[kp] - F[km];
+  });
+  float mom[3] = {dif[0], dif[1], dif[2]};
+  float s4all = 0.f;
+  static_for<0, 3>([&](auto pp) {
+    constexpr int p = decltype(pp)::value;
+    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;
+    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
+    constexpr int kpp = link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
+    constexpr int kmm = link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
+    constexpr int kpm = link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
+    constexpr int kmp = link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
+    const float Rr = F[kpp] - F[kmm], S = F[kpm] - F[kmp];
+    s4all += (F[kpp] + F[kmm]) + (F[kpm] + F[kmp]);
+    mom[a] += Rr + S;
+    mom[b] += Rr - S;
+  });
+  sm = F[0] + (sum_ax + s4all);
+  mx = mom[0];
+  my = mom[1];
+  mz = mom[2];
+}
+
 // ---------------------------------------------------------------------------------
 // Warp-column D3Q19 forward (FP32)
 // ---------------------------------------------------------------------------------
@@ -1010,14 +1093,8 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       }
       R drn, uo[3] = {R(0), R(0), R(0)};
       if (FAST || faces == 0) {
-        R sm = R(0), mx = R(0), my = R(0), mz = R(0);
-        static_for<0, 19>([&](auto kk) {
-          constexpr int k = decltype(kk)::value;
-          sm += F[k];
-          if constexpr (c3(k, 0) != 0) mx += R(c3(k, 0)) * F[k];
-          if constexpr (c3(k, 1) != 0) my += R(c3(k, 1)) * F[k];
-          if constexpr (c3(k, 2) != 0) mz += R(c3(k, 2)) * F[k];
-        });
+        R sm, mx, my, mz;
+        fwd_moments3(F, sm, mx, my, mz);
         drn = drx + sm;
         uo[0] = mx * inv_c;
         uo[1] = my * inv_c;
@@ -1323,58 +1400,6 @@ struct Adj3CArgs {
   int* status;
   int zc;  // z planes per CTA
 };
-
-// Index of the link with velocity (x, y, z).
-__host__ __device__ constexpr int link3(int x, int y, int z) {
-  int k = 0;
-  while (k < 19 && !(c3(k, 0) == x && c3(k, 1) == y && c3(k, 2) == z)) ++k;
-  return k;
-}
-
-// The ten ALKS moments (rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz) of
-// the 19 gathered values F at an interior node, sum_k w_k F_k {1, c_k, c_k c_k}
-// (Sec. 2.5), summed by link class: the pair of axis links of each axis, and the
-// four diagonal links of each pair of axes, which enter the momentum of both axes,
-// the two diagonal second moments and the off-diagonal one.
-__device__ __forceinline__ void adj_moments3(const float (&F)[19], float (&m)[kNA3]) {
-  constexpr float w0 = (float)w3d(link3(0, 0, 0)), w1 = (float)w3d(link3(1, 0, 0)), w2 = (float)w3d(link3(1, 1, 0));
-  constexpr int sa[3][3] = {{4, 5, 6}, {5, 7, 8}, {6, 8, 9}};  // moment index of s~_ab
-  float sum_ax[3], dif_ax[3];
-  static_for<0, 3>([&](auto aa) {
-    constexpr int a = decltype(aa)::value;
-    constexpr int kp = link3(a == 0, a == 1, a == 2), km = link3(-(a == 0), -(a == 1), -(a == 2));
-    sum_ax[a] = F[kp] + F[km];
-    dif_ax[a] = F[kp] - F[km];
-  });
-  float mom[3] = {w1 * dif_ax[0], w1 * dif_ax[1], w1 * dif_ax[2]};
-  float dia[3] = {w1 * sum_ax[0], w1 * sum_ax[1], w1 * sum_ax[2]};
-  float s4all = 0.f;
-  static_for<0, 3>([&](auto pp) {
-    constexpr int p = decltype(pp)::value;
-    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;  // axis pairs (x,y), (x,z), (y,z)
-    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
-    constexpr int kpp = link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
-    constexpr int kmm = link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
-    constexpr int kpm = link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
-    constexpr int kmp = link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
-    const float P = F[kpp] + F[kmm], Q = F[kpm] + F[kmp];
-    const float Rr = F[kpp] - F[kmm], S = F[kpm] - F[kmp];
-    const float s4 = P + Q;
-    s4all += s4;
-    m[sa[a][b]] = w2 * (P - Q);
-    mom[a] += w2 * (Rr + S);
-    mom[b] += w2 * (Rr - S);
-    dia[a] += w2 * s4;
-    dia[b] += w2 * s4;
-  });
-  m[0] = w0 * F[0] + (w1 * (sum_ax[0] + sum_ax[1] + sum_ax[2]) + w2 * s4all);
-  m[1] = mom[0];
-  m[2] = mom[1];
-  m[3] = mom[2];
-  m[4] = dia[0];
-  m[7] = dia[1];
-  m[9] = dia[2];
-}
 
 // d/dx at node `at` of n from values at offsets 0, +-1, +-2 (one-sided on a face),
 // the same formulas as dax.
