@@ -262,7 +262,9 @@ const char *lks_last_error(const lks_handle *h);
  * capture.  Every call shares the array and leaves its contents behind (each
  * call clears what it needs zeroed), so calls that overlap on the GPU -- on
  * different streams, or from different host threads -- race and corrupt each
- * other: order them.  Host memory for a temporary handle is still allocated. */
+ * other: order them.  Host memory for a temporary handle is still allocated.
+ * Descriptors with tol > 0 are rejected (LKS_ERR_INVALID_ARG): a tolerance march
+ * reads its measured change back to the host. */
 #define LKS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_dev, double *J_dev,
                                 void *dJdgamma_dev, void *stream);

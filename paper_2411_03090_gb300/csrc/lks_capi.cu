@@ -1486,6 +1486,7 @@ lks_status lks_gradient_noalloc(const lks_problem_desc* desc, const void* gamma_
   lks_status s = check_desc(desc, nullptr);
   if (s != LKS_OK) return s;
   if (desc->lattice != LKS_LATTICE_D2Q9) return LKS_ERR_INVALID_ARG;
+  if (desc->tol > 0.0) return LKS_ERR_INVALID_ARG;  // a tolerance march reads its change back (synchronises)
   const Layout L = make_layout(desc);
   if (L.total > LKS_NOALLOC_SCRATCH_BYTES) return LKS_ERR_WORKSPACE;  // problem too large
   void* ws = nullptr;

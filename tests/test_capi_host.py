@@ -126,6 +126,16 @@ def test_selftest_wait_rejects_bad_arguments_without_gpu_work():
     assert rec.value == -1
 
 
+def test_noalloc_rejects_tolerance_marches_without_gpu_work():
+    """lks_gradient_noalloc never synchronises, so a descriptor asking for a
+    tolerance march (which reads its change back) is refused before any GPU work."""
+    L = lks.load()
+    pb = inputs.config1()
+    d = lks.make_desc(pb, tol=1e-6, max_steps=pb.n_steps)
+    p = C.c_void_p(256)
+    assert L.lks_gradient_noalloc(C.byref(d), p, C.cast(p, C.POINTER(C.c_double)), p, None) == 1
+
+
 def test_create_rejects_bad_workspace_without_gpu_work():
     L = lks.load()
     d = lks.make_desc(inputs.config1())
