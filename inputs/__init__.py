@@ -91,6 +91,9 @@ class Problem:
     seed: int = 1
     sigma: float = 4.0
     strip: int = 4
+    periodic: int = 0        # oracle-only pin geometries: bit 0 x periodic, bit 1 y periodic
+    G_x: float = 0.0         # oracle-only pin geometries: uniform external force
+    G_y: float = 0.0
 
     def resolved(self, name: str):
         """Field value with negative span ends counted from the top edge (ny + v)."""

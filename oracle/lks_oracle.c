@@ -86,6 +86,9 @@ typedef struct {
     double t_val[4];           /* T_bar or q_bar_w per edge                    */
     double kappa_T;            /* weight of the T term in J_O                  */
     double kappa_p;            /* weight of the static pressure drop J_p       */
+    int periodic;              /* bit 0: x periodic (no left / right edges),
+                                  bit 1: y periodic (no bottom / top edges)    */
+    double G_x, G_y;           /* uniform external force G of Eq. (lbef_ex)   */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -115,7 +118,13 @@ static double dB_of(const orc_problem *p, double g) {
 /* ------------------------------------------------------------------------- */
 #define AT(f, i, j) ((f)[(size_t)(j) * (size_t)nx + (size_t)(i)])
 
-static int inside(int nx, int ny, int i, int j) { return i >= 0 && i < nx && j >= 0 && j < ny; }
+/* Maps (i, j) onto the lattice along periodic axes (wrap-around); returns 1 when
+ * the node exists (always along a periodic axis). */
+static int node_at(const orc_problem *p, int *i, int *j) {
+    if (p->periodic & 1) *i = ((*i % p->nx) + p->nx) % p->nx;
+    if (p->periodic & 2) *j = ((*j % p->ny) + p->ny) % p->ny;
+    return *i >= 0 && *i < p->nx && *j >= 0 && *j < p->ny;
+}
 
 /* Node classes. */
 enum { N_INTERIOR = 0, N_VELOCITY = 1, N_PRESSURE = 2, N_CORNER = 3 };
@@ -124,7 +133,9 @@ enum { N_INTERIOR = 0, N_VELOCITY = 1, N_PRESSURE = 2, N_CORNER = 3 };
  * a corner). */
 static int classify(const orc_problem *p, int i, int j, int *nxo, int *nyo) {
     int nx = p->nx, ny = p->ny;
-    int left = (i == 0), right = (i == nx - 1), bottom = (j == 0), top = (j == ny - 1);
+    int px = p->periodic & 1, py = p->periodic & 2;
+    int left = !px && (i == 0), right = !px && (i == nx - 1);
+    int bottom = !py && (j == 0), top = !py && (j == ny - 1);
     *nxo = (right ? 1 : 0) - (left ? 1 : 0);
     *nyo = (top ? 1 : 0) - (bottom ? 1 : 0);
     if ((left || right) && (bottom || top)) return N_CORNER;
@@ -155,13 +166,16 @@ static double inlet_u(const orc_problem *p, int j, double t) {
 /* Gradient operator: second-order central differences inside, second-order    */
 /* one-sided differences on the domain edge (the same operator everywhere).    */
 /* ------------------------------------------------------------------------- */
-static double ddx(const double *f, int nx, int ny, int i, int j) {
-    (void)ny;
+static double ddx(const orc_problem *p, const double *f, int i, int j) {
+    int nx = p->nx;
+    if (p->periodic & 1) return (AT(f, (i + 1) % nx, j) - AT(f, (i + nx - 1) % nx, j)) / 2.0;
     if (i == 0) return (-3.0 * AT(f, 0, j) + 4.0 * AT(f, 1, j) - AT(f, 2, j)) / 2.0;
     if (i == nx - 1) return (3.0 * AT(f, nx - 1, j) - 4.0 * AT(f, nx - 2, j) + AT(f, nx - 3, j)) / 2.0;
     return (AT(f, i + 1, j) - AT(f, i - 1, j)) / 2.0;
 }
-static double ddy(const double *f, int nx, int ny, int i, int j) {
+static double ddy(const orc_problem *p, const double *f, int i, int j) {
+    int nx = p->nx, ny = p->ny;
+    if (p->periodic & 2) return (AT(f, i, (j + 1) % ny) - AT(f, i, (j + ny - 1) % ny)) / 2.0;
     if (j == 0) return (-3.0 * AT(f, i, 0) + 4.0 * AT(f, i, 1) - AT(f, i, 2)) / 2.0;
     if (j == ny - 1) return (3.0 * AT(f, i, ny - 1) - 4.0 * AT(f, i, ny - 2) + AT(f, i, ny - 3)) / 2.0;
     return (AT(f, i, j + 1) - AT(f, i, j - 1)) / 2.0;
@@ -174,12 +188,14 @@ static double ddy(const double *f, int nx, int ny, int i, int j) {
  * differences along the edge; zero at corner nodes, where both edges carry a zero
  * tangential velocity).  The one-sided normal derivative of u_n makes the march
  * unstable for A < 0 (nu > 1/6); for the exact solutions the two agree. */
-static void vel_grad(const double *u, const double *v, int nx, int ny, int i, int j, double *g) {
-    g[0] = ddx(u, nx, ny, i, j);
-    g[1] = ddy(u, nx, ny, i, j);
-    g[2] = ddx(v, nx, ny, i, j);
-    g[3] = ddy(v, nx, ny, i, j);
-    int xe = (i == 0 || i == nx - 1), ye = (j == 0 || j == ny - 1);
+static void vel_grad(const orc_problem *p, const double *u, const double *v, int i, int j, double *g) {
+    int nx = p->nx, ny = p->ny;
+    g[0] = ddx(p, u, i, j);
+    g[1] = ddy(p, u, i, j);
+    g[2] = ddx(p, v, i, j);
+    g[3] = ddy(p, v, i, j);
+    int xe = !(p->periodic & 1) && (i == 0 || i == nx - 1);
+    int ye = !(p->periodic & 2) && (j == 0 || j == ny - 1);
     if (xe && ye) {
         g[0] = 0.0;
         g[3] = 0.0;
@@ -229,21 +245,22 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
     int known[9];
     for (int k = 0; k < 9; ++k) {
         int si = i - CX[k], sj = j - CY[k];
-        known[k] = inside(nx, ny, si, sj);
+        known[k] = node_at(p, &si, &sj);
         f[k] = g[k] = 0.0;
         if (!known[k]) continue;
         double gu[4];
-        vel_grad(u, v, nx, ny, si, sj, gu);
+        vel_grad(p, u, v, si, sj, gu);
         f[k] = feq(k, A, AT(rho, si, sj), AT(u, si, sj), AT(v, si, sj), gu[0], gu[1], gu[2], gu[3]);
         if (p->thermal)
             g[k] = geq(k, AT(T, si, sj), AT(u, si, sj), AT(v, si, sj), B_of(p, AT(gamma, si, sj)),
-                       ddx(T, nx, ny, si, sj), ddy(T, nx, ny, si, sj));
+                       ddx(p, T, si, sj), ddy(p, T, si, sj));
     }
 
     double r = 0.0, uu = 0.0, vv = 0.0, TT = 0.0;
     if (cls == N_INTERIOR) {
-        /* Eqs. (rho), (u), (T); Brinkman term of Eq. (lbef_ex) implicit:
-         * u = u* / (1 + alpha_gamma)  (sum of c_k times Eq. lbef_ex). */
+        /* Eqs. (rho), (u), (T); Brinkman and force terms of Eq. (lbef_ex), the
+         * Brinkman term implicit: u = (u* + G) / (1 + alpha_gamma)  (sum of c_k
+         * times Eq. lbef_ex, with sum_k w_k c_k c_k = 1/3). */
         double us = 0.0, vs = 0.0;
         for (int k = 0; k < 9; ++k) {
             r += f[k];
@@ -252,8 +269,8 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
             TT += g[k];
         }
         double a = alpha_of(p, AT(gamma, i, j));
-        uu = us / (1.0 + a);
-        vv = vs / (1.0 + a);
+        uu = (us + p->G_x) / (1.0 + a);
+        vv = (vs + p->G_y) / (1.0 + a);
     } else if (cls == N_CORNER) {
         /* Corner: wall node, u = 0; density carried over from the previous step
          * of the edge neighbour at the same x (one row into the lattice). */
@@ -331,17 +348,26 @@ void orc_forward_step(const orc_problem *p, const double *gamma, double t, const
 /*   J_O = sum over interior nodes of                                        */
 /*         nu/2 (S_xx^2 + 2 S_xy^2 + S_yy^2) + alpha_gamma |u|^2 + kappa_T T   */
 /* ------------------------------------------------------------------------- */
-static int is_interior(int nx, int ny, int i, int j) { return i > 0 && j > 0 && i < nx - 1 && j < ny - 1; }
+/* Node (i, j), wrapped along periodic axes, and whether it is an interior node
+ * (not on a domain edge; every node of a periodic axis is interior along it). */
+static int is_interior(const orc_problem *p, int *i, int *j) {
+    if (!node_at(p, i, j)) return 0;
+    int xin = (p->periodic & 1) || (*i > 0 && *i < p->nx - 1);
+    int yin = (p->periodic & 2) || (*j > 0 && *j < p->ny - 1);
+    return xin && yin;
+}
 
 double orc_objective(const orc_problem *p, const double *gamma, const double *u, const double *v,
                      const double *T) {
     int nx = p->nx, ny = p->ny;
     double J = 0.0;
 #pragma omp parallel for reduction(+ : J) schedule(static)
-    for (int j = 1; j < ny - 1; ++j)
-        for (int i = 1; i < nx - 1; ++i) {
-            double Sxx = 2.0 * ddx(u, nx, ny, i, j), Syy = 2.0 * ddy(v, nx, ny, i, j);
-            double Sxy = ddy(u, nx, ny, i, j) + ddx(v, nx, ny, i, j);
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int ii = i, jj = j;
+            if (!is_interior(p, &ii, &jj)) continue;
+            double Sxx = 2.0 * ddx(p, u, i, j), Syy = 2.0 * ddy(p, v, i, j);
+            double Sxy = ddy(p, u, i, j) + ddx(p, v, i, j);
             double uu = AT(u, i, j), vv = AT(v, i, j);
             J += 0.5 * p->nu * (Sxx * Sxx + 2.0 * Sxy * Sxy + Syy * Syy) +
                  alpha_of(p, AT(gamma, i, j)) * (uu * uu + vv * vv);
@@ -355,11 +381,12 @@ double orc_objective(const orc_problem *p, const double *gamma, const double *u,
  * rho - sum over outlet nodes of rho): Eq. objective_pipebend with p = rho / 3 and
  * dGamma = 1. */
 static int is_inlet(const orc_problem *p, int i, int j) {
-    return i == 0 && j > 0 && j < p->ny - 1 && j >= p->in_y0 && j <= p->in_y1;
+    return !(p->periodic & 1) && i == 0 && j > 0 && j < p->ny - 1 && j >= p->in_y0 && j <= p->in_y1;
 }
 double orc_pressure_drop(const orc_problem *p, const double *rho) {
     int nx = p->nx, ny = p->ny;
     double s = 0.0;
+    if (p->periodic & 1) return 0.0; /* no inlet or outlet */
     for (int j = 1; j < ny - 1; ++j) {
         if (is_inlet(p, 0, j)) s += AT(rho, 0, j);
         if (j >= p->out_y0 && j <= p->out_y1) s -= AT(rho, nx - 1, j);
@@ -378,28 +405,34 @@ double orc_objective_total(const orc_problem *p, const double *gamma, const doub
 /* dJ_O/du and dJ_O/dv at node (i, j): the derivative of the sum above, written
  * out term by term (S at an interior neighbour z depends on u(i, j) through the
  * central differences of z). */
-static double S_at(const double *u, const double *v, int nx, int ny, int i, int j, int which) {
-    if (which == 0) return 2.0 * ddx(u, nx, ny, i, j);
-    if (which == 2) return 2.0 * ddy(v, nx, ny, i, j);
-    return ddy(u, nx, ny, i, j) + ddx(v, nx, ny, i, j);
+/* S component `which` (0: S_xx, 1: S_xy, 2: S_yy) at the neighbour (i + di, j + dj)
+ * when that neighbour is an interior node, else 0. */
+static double S_nb(const orc_problem *p, const double *u, const double *v, int i, int j, int di, int dj,
+                   int which) {
+    int zi = i + di, zj = j + dj;
+    if (!is_interior(p, &zi, &zj)) return 0.0;
+    if (which == 0) return 2.0 * ddx(p, u, zi, zj);
+    if (which == 2) return 2.0 * ddy(p, v, zi, zj);
+    return ddy(p, u, zi, zj) + ddx(p, v, zi, zj);
 }
 void orc_dJdu_node(const orc_problem *p, const double *gamma, const double *u, const double *v,
                    int i, int j, double *ju, double *jv) {
-    int nx = p->nx, ny = p->ny;
+    int nx = p->nx;
     double a = 0.0, b = 0.0;
     /* S_xx(z) = u(z+ex) - u(z-ex): z = (i-1,j) gives +S_xx(z), z = (i+1,j) gives -S_xx(z)  */
-    if (is_interior(nx, ny, i - 1, j)) a += S_at(u, v, nx, ny, i - 1, j, 0);
-    if (is_interior(nx, ny, i + 1, j)) a -= S_at(u, v, nx, ny, i + 1, j, 0);
+    a += S_nb(p, u, v, i, j, -1, 0, 0);
+    a -= S_nb(p, u, v, i, j, +1, 0, 0);
     /* 2 S_xy^2 with S_xy(z) = (u(z+ey) - u(z-ey))/2 + ... : factor 2 * 1/2 = 1 */
-    if (is_interior(nx, ny, i, j - 1)) a += S_at(u, v, nx, ny, i, j - 1, 1);
-    if (is_interior(nx, ny, i, j + 1)) a -= S_at(u, v, nx, ny, i, j + 1, 1);
-    if (is_interior(nx, ny, i, j - 1)) b += S_at(u, v, nx, ny, i, j - 1, 2);
-    if (is_interior(nx, ny, i, j + 1)) b -= S_at(u, v, nx, ny, i, j + 1, 2);
-    if (is_interior(nx, ny, i - 1, j)) b += S_at(u, v, nx, ny, i - 1, j, 1);
-    if (is_interior(nx, ny, i + 1, j)) b -= S_at(u, v, nx, ny, i + 1, j, 1);
+    a += S_nb(p, u, v, i, j, 0, -1, 1);
+    a -= S_nb(p, u, v, i, j, 0, +1, 1);
+    b += S_nb(p, u, v, i, j, 0, -1, 2);
+    b -= S_nb(p, u, v, i, j, 0, +1, 2);
+    b += S_nb(p, u, v, i, j, -1, 0, 1);
+    b -= S_nb(p, u, v, i, j, +1, 0, 1);
     a *= p->nu;
     b *= p->nu;
-    if (is_interior(nx, ny, i, j)) {
+    int ii = i, jj = j;
+    if (is_interior(p, &ii, &jj)) {
         double al = alpha_of(p, AT(gamma, i, j));
         a += 2.0 * al * AT(u, i, j);
         b += 2.0 * al * AT(v, i, j);
@@ -562,15 +595,15 @@ static void adjoint_eq_fields(const orc_problem *p, const double *gamma, const d
             double rt = AT(a[0], i, j), ux = AT(a[1], i, j), uy = AT(a[2], i, j);
             double sxx = AT(a[3], i, j), sxy = AT(a[4], i, j), syy = AT(a[5], i, j);
             double uu = AT(u, i, j), vv = AT(v, i, j);
-            double Dx = 2.0 * (ddx(a[3], nx, ny, i, j) + ddy(a[4], nx, ny, i, j));
-            double Dy = 2.0 * (ddx(a[4], nx, ny, i, j) + ddy(a[5], nx, ny, i, j));
+            double Dx = 2.0 * (ddx(p, a[3], i, j) + ddy(p, a[4], i, j));
+            double Dy = 2.0 * (ddx(p, a[4], i, j) + ddy(p, a[5], i, j));
             AT(P, i, j) = rt;
             AT(Vx, i, j) = 3.0 * (ux + 3.0 * (sxx * uu + sxy * vv) - rt * uu) - A * Dx;
             AT(Vy, i, j) = 3.0 * (uy + 3.0 * (sxy * uu + syy * vv) - rt * vv) - A * Dy;
             if (p->thermal) {
                 double qx = AT(a[7], i, j), qy = AT(a[8], i, j);
-                double divq = ddx(a[7], nx, ny, i, j) + ddy(a[8], nx, ny, i, j);
-                double dBx = ddx(Bfield, nx, ny, i, j), dBy = ddy(Bfield, nx, ny, i, j);
+                double divq = ddx(p, a[7], i, j) + ddy(p, a[8], i, j);
+                double dBx = ddx(p, Bfield, i, j), dBy = ddy(p, Bfield, i, j);
                 AT(G, i, j) = AT(a[6], i, j) + 3.0 * (qx * uu + qy * vv) - AT(Bfield, i, j) * divq -
                               (dBx * qx + dBy * qy);
             }
@@ -599,7 +632,7 @@ void orc_adjoint_eq(const orc_problem *p, const double *gamma, const double *u, 
 void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P,
                       const double *Vx, const double *Vy, const double *G, const double *u0,
                       const double *v0, const double *T0, int i, int j, double *out) {
-    int nx = p->nx, ny = p->ny;
+    int nx = p->nx;
     double A = lks_A(p);
     int n_x, n_y;
     int cls = classify(p, i, j, &n_x, &n_y);
@@ -607,7 +640,7 @@ void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P
     int unknown[9];
     for (int k = 0; k < 9; ++k) {
         int gi = i + CX[k], gj = j + CY[k];
-        unknown[k] = !inside(nx, ny, gi, gj);
+        unknown[k] = !node_at(p, &gi, &gj);
         f[k] = g[k] = 0.0;
         if (unknown[k]) continue;
         f[k] = AT(P, gi, gj) + CX[k] * AT(Vx, gi, gj) + CY[k] * AT(Vy, gi, gj);
@@ -688,15 +721,17 @@ void orc_sensitivity_parts(const orc_problem *p, const double *gamma, const doub
                            int parts) {
     int nx = p->nx, ny = p->ny;
 #pragma omp parallel for schedule(static)
-    for (int j = 1; j < ny - 1; ++j)
-        for (int i = 1; i < nx - 1; ++i) {
+    for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+            int ii = i, jj = j;
+            if (!is_interior(p, &ii, &jj)) continue;
             double gm = AT(gamma, i, j);
             double da = dalpha_of(p, gm);
             double uu = AT(u, i, j), vv = AT(v, i, j);
             double s = 0.0;
             if (parts & 1) s += da * (uu * uu + vv * vv) + 3.0 * da * (uu * AT(a[1], i, j) + vv * AT(a[2], i, j));
             if (p->thermal && (parts & 2))
-                s -= dB_of(p, gm) * (ddx(T, nx, ny, i, j) * AT(a[7], i, j) + ddy(T, nx, ny, i, j) * AT(a[8], i, j));
+                s -= dB_of(p, gm) * (ddx(p, T, i, j) * AT(a[7], i, j) + ddy(p, T, i, j) * AT(a[8], i, j));
             AT(sens, i, j) += s;
         }
 }

@@ -45,6 +45,8 @@ class OrcProblem(C.Structure):
         ("t_val", C.c_double * 4),
         ("kappa_T", C.c_double),
         ("kappa_p", C.c_double),
+        ("periodic", C.c_int),
+        ("G_x", C.c_double), ("G_y", C.c_double),
     ]
 
 
@@ -162,6 +164,8 @@ def make_problem(pb) -> OrcProblem:
     for name, _ in OrcProblem._fields_:
         if name in ("t_kind", "t_val"):
             continue
+        if name in ("periodic", "G_x", "G_y") and not hasattr(pb, name):
+            continue  # channel problems: no periodic axis, no external force
         val = pb.resolved(name) if hasattr(pb, "resolved") else getattr(pb, name)
         setattr(s, name, type(getattr(s, name))(val))
     for e in range(4):

@@ -170,6 +170,8 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
         d.exec_path = PATH[path]
         d.tol, d.max_steps = float(tol), int(max_steps)
         return d
+    if getattr(pb, "periodic", 0) or getattr(pb, "G_x", 0.0) or getattr(pb, "G_y", 0.0):
+        raise ValueError("periodic lattices and an external force are not part of the CUDA path")
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T"):
         setattr(d, name, float(getattr(pb, name)))
