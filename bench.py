@@ -2,11 +2,14 @@
 gradient on one GB300, plus roofline, end-to-end and CPU-oracle figures.
 
 One step = one full gradient of the workload (LKS forward march, ALKS adjoint march,
-sensitivity).  Default workload: 512 x 256 steady channel, Re = 100, 20000 forward
-+ 20000 adjoint steps, FP32 (the second configuration of the paper-derived set).
+sensitivity).  Default workload: the 192^3 D3Q19 duct, Re = 50, 1000 forward + 1000
+adjoint steps, FP32, objective dissipation + static pressure drop (the largest
+single-GPU configuration of the paper-derived set, 7.08 M nodes, working set far
+larger than L2).  The same line carries, under "also", the 512 x 256 channel
+(config2, L2-resident) and the 8192^2 channel (67 M nodes) measured the same way.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                    [--workload config2|roofline8192|config1|config3|config4|config5]
+                    [--workload config4|config2|roofline8192|config1|config3|config5]
 
 config3 runs the checkpoint study (plain FP32 trajectory against checkpoints every
 K steps with FP32 / BF16 / FP16 snapshots); config5 runs the batched form (64
@@ -47,6 +50,17 @@ BYTES_FWD_3D = 4 * (4 + 4 + 1)
 BYTES_ADJ_3D = 4 * (10 + 10 + 3 + 1)
 
 METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e-3 rel"
+
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per node of one launch of
+# the step kernels, from ncu captures of the kernels as they stand (the summaries and
+# commands are in profiles/); None where no capture of the current kernel exists.
+# Multiplied by the nodes of a launch they give roofline.traffic.
+TRAFFIC_BYTES_PER_NODE = {
+    "adj3c_kernel": None,
+    "fwd3c_kernel": None,
+    "adj_col_kernel<true>": None,
+    "fwd_col2_kernel<10>": None,
+}
 
 
 def workload(name: str):
@@ -424,7 +438,9 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
-    ap.add_argument("--workload", default="config2")
+    ap.add_argument("--workload", default="config4")
+    ap.add_argument("--no-also", action="store_true",
+                    help="config4: skip the config2 and 8192^2 figures carried on the same line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-override", type=int, default=0)
@@ -462,18 +478,78 @@ def main():
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
 
-    from paper_2411_03090_gb300 import LKS
-
     pb, desc = workload(args.workload)
     if args.steps_override:
         pb = pb.with_(n_steps=args.steps_override, n_adj=args.steps_override)
         desc += f" (shortened to {args.steps_override}+{args.steps_override} steps)"
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
+    clocks = ClockSampler(local)
+    m = measure(pb, args, dev, flush, args.steps, max(args.warmup, 3), world, clocks=clocks, e2e=not args.no_e2e)
+    total_ms = m["total_ms"]
+    value = job_mlups(world, m["updates_per_step"], args.steps, total_ms)
+    e2e_val = m["e2e_single"] * world if m["e2e_single"] is not None else None
+
+    also = {}
+    if args.workload == "config4" and not args.steps_override and not args.no_also:
+        for name in ("config2", "roofline8192"):
+            pb2, desc2 = workload(name)
+            m2 = measure(pb2, args, dev, flush, 2, 1, 1, e2e=False)
+            also[name] = {"workload": desc2, "value": m2["updates_per_step"] * 2 / (m2["total_ms"] * 1e-3) / 1e6,
+                          "unit": "MLUPS", "s_per_gradient": m2["total_ms"] / 2 / 1e3, "roofline": m2["roofline"]}
+            if name == "config2":
+                also[name]["roofline"]["note"] = ("working set (0.5 MB per field) resident in L2 and shared "
+                                                  "memory: the fraction is of HBM, but the traffic is on chip")
+
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    N = pb.n_nodes
+    three_d = hasattr(pb, "nz")
+    st = m["stats"]
+    out = {
+        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc,
+                   "lattice": f"{pb.nx}x{pb.ny}" + (f"x{pb.nz}" if three_d else ""), "forward_steps": pb.n_steps,
+                   "adjoint_steps": pb.n_adj, "l2": "flushed between timed steps (256 MB write)",
+                   "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3,
+                   **({"resident_steps_per_exchange": [st.res_steps_fwd, st.res_steps_adj]}
+                      if st.fwd_path == 2 or st.adj_path == 2 else {})},
+        "roofline": m["roofline"],
+        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 4 * N,
+                "d2h_bytes_per_step": 4 * N + 8 + 4},
+        "gpu_launches": int(m["launches"]),
+        "clocks": m["clocks"],
+    }
+    if also:
+        out["also"] = also
+    if not args.no_cpu_baseline:
+        try:
+            n_cb = oracle_steps_for(pb, 15.0)  # a bounded sample: 10-15 s of host work (the 2-step calibration runs long)
+            out["cpu_baseline"] = cpu_baseline(pb, n_cb, n_cb)
+        except Exception as e:  # the oracle is a reported baseline, not the product
+            out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
+    print(json.dumps(out))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def measure(pb, args, dev, flush, steps, warmup, world, clocks=None, e2e=True):
+    """Times `steps` gradients of one steady problem (after `warmup` untimed ones)
+    with CUDA events on the library's stream: the whole gradient, the forward march
+    and the adjoint march.  Returns the slowest rank's total milliseconds, the
+    roofline of the adjoint and forward step kernels, the kernels launched in the
+    timed region and, when asked, the end-to-end rate through lks_gradient_host."""
+    import torch
+    from paper_2411_03090_gb300 import LKS
+
     g_np = pb.gamma()
     gamma = torch.from_numpy(g_np).to(dev, torch.float32)
     s = LKS(pb, real="f32", device=dev, res_steps=args.res_steps, path=args.exec_path)
     stream = s.stream
     N = pb.n_nodes
-    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2 (129 MB)
 
     def one_gradient(ev=None):
         J = s.lks_forward(gamma)
@@ -485,18 +561,19 @@ def main():
         g = s.lks_sensitivity()
         return J, g
 
-    for _ in range(max(args.warmup, 3)):
+    for _ in range(max(warmup, 1)):
         one_gradient()
     torch.cuda.synchronize()
 
     launches0 = s.query().kernel_launches
-    clocks = ClockSampler(local)
-    clocks.start()
+    if clocks is not None:
+        clocks.start()
     if world > 1:
+        import torch.distributed as dist
         dist.barrier()
     torch.cuda.synchronize()
     step_ms, fwd_ms, adj_ms = [], [], []
-    for _ in range(args.steps):
+    for _ in range(steps):
         flush.fill_(1.0)  # evict the previous gradient's working set from L2
         ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
         ev[0].record(stream)
@@ -508,11 +585,9 @@ def main():
         adj_ms.append(ev[1].elapsed_time(ev[2]))
     torch.cuda.synchronize()
     total_ms = max_over_ranks(sum(step_ms), world, dev)
-    clk = clocks.stop()
-    launches = s.query().kernel_launches - launches0
-
-    updates_per_step = N * (pb.n_steps + pb.n_adj)
-    value = job_mlups(world, updates_per_step, args.steps, total_ms)
+    clk = clocks.stop() if clocks is not None else None
+    st = s.query()
+    launches = st.kernel_launches - launches0
 
     # Dominant kernel (adjoint step): algorithmic bytes per launch / mean duration.
     hbm, peak_kind = peaks()
@@ -523,8 +598,6 @@ def main():
     b_fwd = BYTES_FWD_3D if three_d else BYTES_FWD
     adj_gbs = b_adj * N / adj_launch_s / 1e9
     fwd_gbs = b_fwd * N / fwd_launch_s / 1e9
-    traffic = None
-    st = s.query()
     step_names = (("adj_tma_kernel<false,true,false>", "fwd_tma_kernel<false,false>") if pb.nx % 4 == 0 else
                   ("adj_step_kernel<float,false>", "fwd_step_kernel<float,false>"))
     kname = {1: step_names, 2: ("adj_resident_kernel<float>", "fwd_resident_kernel<float,false>"),
@@ -535,57 +608,37 @@ def main():
         tma3 = pb.nx % 4 == 0
         adj_k = ("adj3c_kernel" if st.adj_path == 3 else "adj3t_kernel") if tma3 else "adj3_kernel<float>"
         fwd_k = ("fwd3c_kernel" if st.fwd_path == 3 else "fwd3t_kernel") if tma3 else "fwd3_kernel<float>"
+
+    def traffic(k):
+        b = TRAFFIC_BYTES_PER_NODE.get(k)
+        return None if b is None else b * N
+
     roofline = {"bound": "hbm", "kernel": adj_k, "achieved": adj_gbs, "peak": hbm,
-                "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic, "peak_kind": peak_kind,
+                "unit": "GB/s", "frac": adj_gbs / hbm, "traffic": traffic(adj_k), "peak_kind": peak_kind,
                 "algorithmic_bytes_per_node": b_adj, "mean_step_us": adj_launch_s * 1e6,
-                "forward": {"kernel": fwd_k, "achieved": fwd_gbs,
-                            "frac": fwd_gbs / hbm, "algorithmic_bytes_per_node": b_fwd,
+                "forward": {"kernel": fwd_k, "achieved": fwd_gbs, "frac": fwd_gbs / hbm,
+                            "traffic": traffic(fwd_k), "algorithmic_bytes_per_node": b_fwd,
                             "mean_step_us": fwd_launch_s * 1e6}}
 
     # End to end through the C ABI with host buffers (pinned), copies inside.
     e2e_val = None
-    if not args.no_e2e:
+    if e2e:
         g_host = torch.from_numpy(g_np.astype(np.float32)).pin_memory().numpy()
         grad_host = torch.empty(*g_np.shape, dtype=torch.float32).pin_memory().numpy()
         s.gradient_host(g_host, grad_host)
         e2e_t = []
-        for _ in range(max(2, min(args.steps, 3))):
+        for _ in range(max(2, min(steps, 3))):
             flush.fill_(1.0)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             s.gradient_host(g_host, grad_host)
             e2e_t.append(time.perf_counter() - t0)
-        e2e_val = world * updates_per_step / (sum(e2e_t) / len(e2e_t)) / 1e6
-
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    out = {
-        "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": desc,
-                   "lattice": f"{pb.nx}x{pb.ny}" + (f"x{pb.nz}" if three_d else ""), "forward_steps": pb.n_steps,
-                   "adjoint_steps": pb.n_adj, "l2": "flushed between timed steps (256 MB write)",
-                   "parallelism": f"replicas x{world}", "s_per_gradient": total_ms / args.steps / 1e3,
-                   **({"resident_steps_per_exchange": [st.res_steps_fwd, st.res_steps_adj]}
-                      if st.fwd_path == 2 or st.adj_path == 2 else {})},
-        "roofline": roofline,
-        "e2e": {"value": e2e_val, "unit": "MLUPS", "h2d_bytes_per_step": 4 * N,
-                "d2h_bytes_per_step": 4 * N + 8 + 4},
-        "gpu_launches": int(launches),
-        "clocks": clk,
-    }
-    if not args.no_cpu_baseline:
-        try:
-            n_cb = oracle_steps_for(pb, 15.0)  # a bounded sample: 10-15 s of host work (the 2-step calibration runs long)
-            out["cpu_baseline"] = cpu_baseline(pb, n_cb, n_cb)
-        except Exception as e:  # the oracle is a reported baseline, not the product
-            out["cpu_baseline"] = {"value": None, "unit": "MLUPS", "kind": "oracle", "error": str(e)}
-    print(json.dumps(out))
-    if world > 1:
-        dist.destroy_process_group()
+        e2e_val = N * (pb.n_steps + pb.n_adj) / (sum(e2e_t) / len(e2e_t)) / 1e6
+    out = {"total_ms": total_ms, "updates_per_step": N * (pb.n_steps + pb.n_adj), "roofline": roofline,
+           "launches": launches, "clocks": clk, "stats": st, "e2e_single": e2e_val}
+    del s
+    torch.cuda.empty_cache()
+    return out
 
 
 if __name__ == "__main__":

@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define LKS_DESC_VERSION 1
+#define LKS_DESC_VERSION 2
 
 typedef enum {
     LKS_OK = 0,
@@ -46,7 +46,7 @@ typedef enum {
     LKS_ERR_WORKSPACE = 2,     /* workspace too small or misaligned               */
     LKS_ERR_CUDA = 3,          /* a CUDA runtime call failed                      */
     LKS_ERR_UNSTABLE = 4,      /* non-finite or |u| > 0.5 seen on the device       */
-    LKS_ERR_NOT_CONVERGED = 5, /* reserved for tolerance-driven marches           */
+    LKS_ERR_NOT_CONVERGED = 5, /* a tolerance march (tol > 0) hit max_steps        */
     LKS_ERR_TIMEOUT = 6,       /* a bounded device wait gave up                    */
     LKS_ERR_STATE = 7          /* calls in the wrong order (e.g. adjoint first)    */
 } lks_status;
@@ -121,7 +121,17 @@ typedef struct {
     double tol;               /* steady D2Q9: > 0 marches to a relative step change
                                  of tol (see lks_forward); 0 fixed step counts        */
     int32_t max_steps;        /* tol > 0: step limit of each march (>= n_steps, n_adj) */
-    int32_t reserved[1];      /* must be zero                                        */
+    int32_t warm_start;       /* steady D2Q9: 1 = lks_forward marches from the handle's
+                                 current state (the last forward, lks_set_state or
+                                 lks_march) instead of from rest, and alks_adjoint
+                                 from the current adjoint fields instead of zero;
+                                 with no earlier state it starts from rest.  The
+                                 usual start inside an optimisation loop, where the
+                                 design changes little between calls              */
+    int32_t segment_type;     /* lks_snap_type of the recomputed segment trajectory
+                                 (checkpoint_every > 0): F32 (default) or BF16 / F16
+                                 with the snapshots' per-field scaling              */
+    int32_t reserved[4];      /* must be zero                                        */
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in
@@ -264,7 +274,14 @@ const char *lks_last_error(const lks_handle *h);
  * different streams, or from different host threads -- race and corrupt each
  * other: order them.  Host memory for a temporary handle is still allocated.
  * Descriptors with tol > 0 are rejected (LKS_ERR_INVALID_ARG): a tolerance march
- * reads its measured change back to the host. */
+ * reads its measured change back to the host.
+ * Errors: the return value covers what the host can see (arguments, size, launch
+ * failures); this entry point keeps no handle, so lks_last_error has no message for
+ * it.  A condition the kernels detect on the device (non-finite or runaway velocity,
+ * a bounded wait that gave up) cannot be returned without synchronising; the call
+ * then overwrites *J_dev with a quiet NaN after the gradient, so a caller that
+ * checks J for NaN sees every device-detected failure (dJdgamma is not valid then).
+ * Nothing the call enqueues reads host memory after it returns. */
 #define LKS_NOALLOC_SCRATCH_BYTES ((size_t)8 << 20)
 lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_dev, double *J_dev,
                                 void *dJdgamma_dev, void *stream);

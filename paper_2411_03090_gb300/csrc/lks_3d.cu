@@ -1776,7 +1776,7 @@ template <typename R>
 R* ad3(const Ctx3& c, int which, int f) {
   return fld3<R>(c, which == 0 ? c.L->adA : c.L->adB, f);
 }
-int ew_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+int ew_grid(size_t n) { return lks_host::elementwise_blocks(n); }
 // z planes per CTA of the warp-column forward.  A CTA pushes its chunk and one halo
 // plane on each side; the CTAs run in rounds of `resident` (every SM's resident
 // CTAs), so the march takes about rounds x (zc + 2) plane steps.  The smallest such

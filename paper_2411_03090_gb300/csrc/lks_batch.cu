@@ -641,7 +641,7 @@ lks_status adj_step(lks_batch* b, const float* u1, const float* v1, const float*
 }
 
 dim3 per_design_grid(lks_batch* b, int bx = kEwBX) { return dim3(bx, b->n); }
-int arena_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+int arena_grid(size_t n) { return lks_host::elementwise_blocks(n); }
 
 lks_status snap_store(lks_batch* b, int idx) {
   const Plan& P = b->P;

@@ -131,6 +131,7 @@ struct lks_handle {
   int sms = 0;        // multiprocessors of the device (queried once)
   int res_steps_fwd = 0, res_steps_adj = 0;  // steps per exchange of the last resident marches
   double fwd_change = 0.0, adj_change = 0.0;  // relative change of the last measured steps
+  bool have_adj = false;  // adjoint fields hold an earlier march (or alks_set_adjoint)
   bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
   lks3::Layout3 L3;
   std::string err;
@@ -760,7 +761,7 @@ lks_status launch_objective(lks_handle* h, const R* u, const R* v, const R* T, d
   return LKS_OK;
 }
 
-int elementwise_grid(size_t n) { return (int)std::min<size_t>((n + 255) / 256, 152 * 8); }
+int elementwise_grid(size_t n) { return lks_host::elementwise_blocks(n); }
 
 // Relative change of one step of two fields (a0 -> a1, b0 -> b1):
 // max(|da| + |db|) / max(|a1| + |b1|).  Reads two words back (synchronises the stream).
@@ -903,10 +904,12 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   const size_t fb = L.N * sizeof(R);
   if (gamma_dev != h->ws + L.gamma)
     CKH(h, cudaMemcpyAsync(h->ws + L.gamma, gamma_dev, fb, cudaMemcpyDeviceToDevice, h->stream));
-  CKH(h, cudaMemsetAsync(h->ws + L.stA, 0, fb * L.nF, h->stream));
   CKH(h, cudaMemsetAsync(h->ws + L.status, 0, sizeof(int), h->stream));
-  h->cur = 0;
-  h->t = 0;
+  if (!(d.steady && d.warm_start && h->phase >= 1)) {  // from rest (drho = 0, u = 0, T = 0)
+    CKH(h, cudaMemsetAsync(h->ws + L.stA, 0, fb * L.nF, h->stream));
+    h->cur = 0;
+    h->t = 0;
+  }
   if (lks_status ms = update_materials<R>(h); ms != LKS_OK) return ms;
   double* jfwd = reinterpret_cast<double*>(h->ws + L.jfwd);
   double* jobj = reinterpret_cast<double*>(h->ws + L.jobj);
@@ -992,8 +995,11 @@ lks_status adjoint_impl(lks_handle* h) {
   const auto& d = h->d;
   const auto& L = h->L;
   const size_t fb = L.N * sizeof(R);
-  CKH(h, cudaMemsetAsync(h->ws + L.adA, 0, fb * L.nA, h->stream));
-  h->acur = 0;
+  if (!(d.steady && d.warm_start && h->have_adj)) {  // from zero (Eqs. afinitial, aginitial)
+    CKH(h, cudaMemsetAsync(h->ws + L.adA, 0, fb * L.nA, h->stream));
+    h->acur = 0;
+  }
+  h->have_adj = true;
   lks_status st;
   if (d.steady) {
     const R* u = state_ptr<R>(h, h->cur, 1);
@@ -1353,6 +1359,7 @@ lks_status alks_set_adjoint(lks_handle* h, void* const* fields) {
   if (h->is3) return reject3(h, "alks_set_adjoint");
   const size_t fb = h->L.N * h->L.rsize;
   h->acur = 0;
+  h->have_adj = true;
   for (int f = 0; f < h->L.nA; ++f) {
     if (!fields[f]) return fail(h, LKS_ERR_INVALID_ARG, "null field");
     CKH(h, cudaMemcpyAsync(h->ws + h->L.adA + (size_t)f * fb, fields[f], fb, cudaMemcpyDeviceToDevice, h->stream));
@@ -1452,18 +1459,32 @@ lks_status noalloc_scratch(void** out, int* dev_out) {
   return LKS_OK;
 }
 
-// The edge maps, copied in stream order (pageable source: staged at the call).
+// The nine edge-class maps travel as a kernel argument (4320 bytes, within the
+// 32 KB parameter limit), so no host buffer is read after the call returns.
+struct EdgeMaps {
+  double v[9 * 60];
+};
+
+template <typename R>
+__global__ void fill_edge_maps_kernel(EdgeMaps m, R* dst) {
+  for (int i = threadIdx.x; i < 9 * 60; i += blockDim.x) dst[i] = (R)m.v[i];
+}
+
+// Device-detected failures (instability, a bounded wait that gave up) set the status
+// word in the scratch; the allocation-free call has no synchronising query, so the
+// objective it returns is overwritten with NaN instead.
+__global__ void flag_status_kernel(const int* status, double* J) {
+  if (*status != 0) *J = __longlong_as_double(0x7ff8000000000000LL);
+}
+
 template <typename R>
 lks_status upload_maps_async(lks_handle* h) {
   const double A = (1.0 / 6.0 - h->d.nu) * 4.5;
-  h->emap_h.assign(9 * 60, 0.0);
-  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &h->emap_h[cls * 60]);
-  if (sizeof(R) == 8) {
-    CKH(h, cudaMemcpyAsync(h->ws + h->L.emap, h->emap_h.data(), 9 * 60 * 8, cudaMemcpyHostToDevice, h->stream));
-  } else {
-    h->emap_f.assign(h->emap_h.begin(), h->emap_h.end());
-    CKH(h, cudaMemcpyAsync(h->ws + h->L.emap, h->emap_f.data(), 9 * 60 * 4, cudaMemcpyHostToDevice, h->stream));
-  }
+  EdgeMaps m;
+  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &m.v[cls * 60]);
+  fill_edge_maps_kernel<R><<<1, 256, 0, h->stream>>>(m, reinterpret_cast<R*>(h->ws + h->L.emap));
+  CKH(h, cudaGetLastError());
+  ++h->launches;
   return LKS_OK;
 }
 
@@ -1474,6 +1495,10 @@ lks_status noalloc_run(lks_handle* h, const void* gamma_dev, double* J_dev, void
   if (s == LKS_OK) s = forward_impl<R>(h, gamma_dev, J_dev);
   if (s == LKS_OK) s = adjoint_impl<R>(h);
   if (s == LKS_OK) s = sensitivity_impl<R>(h, grad_dev);
+  if (s == LKS_OK) {
+    flag_status_kernel<<<1, 1, 0, h->stream>>>(reinterpret_cast<const int*>(h->ws + h->L.status), J_dev);
+    if (cudaGetLastError() != cudaSuccess) s = LKS_ERR_CUDA;
+  }
   return s;
 }
 }  // namespace

@@ -23,6 +23,23 @@ constexpr int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int CYh[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
 constexpr double Wh[9] = {4.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 9, 1.0 / 36, 1.0 / 36, 1.0 / 36, 1.0 / 36};
 
+// Multiprocessors of the current device (looked up on first use; 152 on a GB300 if
+// the query fails).
+inline int device_sm_count() {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        n <= 0)
+      n = 152;
+    return n;
+  }();
+  return sms;
+}
+
+// Grid of an element-wise kernel over n items: 256-thread blocks, at most eight per
+// multiprocessor (the kernels loop over the rest).
+inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8); }
+
 inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   auto bad = [&](const char* m) {
     if (why) *why = m;
@@ -44,7 +61,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
     if (!std::isfinite(d->kappa_p)) return bad("kappa_p must be finite");
     if (d->tol != 0.0) return bad("D3Q19: tol must be 0 (fixed step counts)");
-    for (int q = 0; q < 1; ++q)
+    if (d->warm_start != 0) return bad("D3Q19: warm_start must be 0");
+    for (int q = 0; q < 4; ++q)
       if (d->reserved[q] != 0) return bad("reserved fields must be zero");
     return LKS_OK;
   }
@@ -72,7 +90,10 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (!d->steady) return bad("tol > 0: steady problems only");
     if (d->max_steps < d->n_steps || d->max_steps < d->n_adj) return bad("tol > 0: max_steps >= n_steps, n_adj");
   }
-  for (int q = 0; q < 1; ++q)
+  if (d->warm_start != 0 && d->warm_start != 1) return bad("warm_start must be 0 or 1");
+  if (d->warm_start && !d->steady) return bad("warm_start: steady problems only");
+  if (d->segment_type != LKS_SNAP_F32) return bad("segment_type: F32 only");
+  for (int q = 0; q < 4; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
 }

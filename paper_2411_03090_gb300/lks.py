@@ -18,7 +18,7 @@ import torch
 
 from . import _build
 
-LKS_DESC_VERSION = 1
+LKS_DESC_VERSION = 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "unstable",
           5: "not converged", 6: "timeout", 7: "calls out of order"}
 REAL = {"f32": 0, "f64": 1}
@@ -55,7 +55,8 @@ class Desc(C.Structure):
         ("exec_path", C.c_int32), ("lattice", C.c_int32), ("nz", C.c_int32), ("res_steps", C.c_int32),
         ("kappa_p", C.c_double),
         ("tol", C.c_double), ("max_steps", C.c_int32),
-        ("reserved", C.c_int32 * 1),
+        ("warm_start", C.c_int32), ("segment_type", C.c_int32),
+        ("reserved", C.c_int32 * 4),
     ]
 
 
@@ -153,10 +154,12 @@ def load(build_if_missing: bool = True):
 
 
 def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
-              path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0) -> Desc:
+              path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0,
+              warm_start: bool = False) -> Desc:
     """Descriptor from an ``inputs.Problem``-like object (``inputs.Problem3``: a
     D3Q19 duct).  tol > 0 (steady D2Q9): march to a relative step change of tol,
-    at most max_steps steps per march, in chunks of n_steps / n_adj."""
+    at most max_steps steps per march, in chunks of n_steps / n_adj.  warm_start
+    (steady D2Q9): each march starts from the handle's current state / adjoint."""
     d = Desc()
     d.version = LKS_DESC_VERSION
     d.nx, d.ny = int(pb.nx), int(pb.ny)
@@ -191,6 +194,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.res_steps = int(res_steps)
     d.tol = float(tol)
     d.max_steps = int(max_steps)
+    d.warm_start = int(bool(warm_start))
     return d
 
 
@@ -238,12 +242,13 @@ class LKS:
 
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
                  device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
-                 path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0):
+                 path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0,
+                 warm_start: bool = False):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.pb = pb
-        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps, tol, max_steps)
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps, tol, max_steps, warm_start)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.is3 = hasattr(pb, "nz")

@@ -76,17 +76,23 @@ def test_descriptor_validation():
     pb = inputs.config1()
     d = lks.make_desc(pb)
     assert lks.workspace_size(d) > 0
-    for field, val in (("nx", 3), ("real_type", 7), ("nu", 0.9), ("version", 99), ("n_steps", 0),
-                       ("res_steps", 4), ("res_steps", -1)):
+    for field, val in (("nx", 3), ("real_type", 7), ("nu", 0.9), ("version", 99), ("version", 1), ("n_steps", 0),
+                       ("res_steps", 4), ("res_steps", -1), ("warm_start", 2), ("segment_type", 7)):
         bad = lks.make_desc(pb)
         setattr(bad, field, val)
         with pytest.raises(lks.LKSError) as e:
             lks.workspace_size(bad)
         assert e.value.status == 1
-    bad = lks.make_desc(pb)
-    bad.reserved[0] = 1
+    for q in range(4):
+        bad = lks.make_desc(pb)
+        bad.reserved[q] = 1
+        with pytest.raises(lks.LKSError):
+            lks.workspace_size(bad)
+    bad = lks.make_desc(pb.with_(steady=False))
+    bad.warm_start = 1  # warm starts are for steady marches
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
+    assert lks.workspace_size(lks.make_desc(pb, warm_start=True)) == lks.workspace_size(d)
     bad = lks.make_desc(pb)
     bad.kappa_p = 1.0  # the pressure-drop term is D3Q19 only
     with pytest.raises(lks.LKSError):

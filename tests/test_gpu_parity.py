@@ -180,11 +180,11 @@ def test_steady_gradient_matches_oracle(real, ftol, gtol, path):
 
 
 @pytest.mark.parametrize("real,ftol,jtol,gtol", [("f64", 1e-11, 1e-11, 1e-10),
-                                                 ("f32", 1e-5, 1e-4, 1e-3)])
+                                                 ("f32", 1e-5, 1e-5, 1e-3)])
 def test_config1_full(real, ftol, jtol, gtol):
     """64 x 64, Re = 10 (nu = 0.315, A < 0), 5000 forward + 5000 adjoint steps.
-    Fields within ftol relative L2, gradient within gtol.  J sums squared velocity
-    gradients, so its FP32 rounding is about ten times that of the fields: jtol."""
+    Fields within ftol relative L2, J within jtol relative, gradient within gtol
+    (measured in FP32: fields 2e-6, J 3.4e-6, gradient 3.3e-6)."""
     pb = inputs.config1()
     g = pb.gamma()
     s = LKS(pb, real=real)
@@ -222,6 +222,30 @@ def test_single_adjoint_step_full_size_config2():
     for q in range(6):
         scale = np.abs(ref[q]).max()
         assert np.abs(a1[q] - ref[q]).max() <= 1e-5 * scale, q
+
+
+def test_bench_path_full_size_config2_matches_oracle():
+    """The benchmark's launch configuration at full size: 512 x 256 on the resident
+    marches (64 x 14 tiles, one per SM), 2000 forward + 2000 adjoint steps, against
+    the FP64 oracle element by element: state fields within 1e-5 relative L2 (the
+    field tolerance), the six adjoint fields and dJ/dgamma within 1e-3 (the gradient
+    tolerance; measured 2e-6 for the state, 8e-6 for the adjoint, 3e-6 for the
+    gradient)."""
+    pb = inputs.config2().with_(n_steps=2000, n_adj=2000)
+    g = pb.gamma()
+    s = LKS(pb, real="f32", path="auto")
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.fwd_path == 2 and q.adj_path == 2 and q.device_status == 0
+    ref = O.steady_gradient(pb, g)
+    got, _ = gpu_state(s)
+    for a, b in zip(got, oracle_state(ref["state"])):
+        assert rel_l2(a, b) <= 1e-5
+    assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    for k in range(6):
+        assert rel_l2(adj[k], ref["adjoint"][k]) <= 1e-3, k
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
 
 
 def test_resident_equals_step_path_config2():
@@ -327,20 +351,84 @@ def test_checkpoint_f32_snapshots_equal_plain(K):
     assert torch.equal(g0, g1)
 
 
+@pytest.mark.parametrize("nx", [70, 136])
+@pytest.mark.parametrize("K", [20, 50])
 @pytest.mark.parametrize("snap", ["bf16", "f16"])
-def test_checkpoint_reduced_snapshots_close(snap):
-    """BF16 / FP16 snapshots with per-field scaling: the gradient stays within 1e-2
-    relative L2 of the plain FP32 form (the error is reported by the benchmark)."""
-    pb = small(steady=False, n_steps=200)
-    g = torch.from_numpy(pb.gamma())
-    _, g0 = LKS(pb, real="f32", checkpoint_every=0).gradient(g)
-    _, g1 = LKS(pb, real="f32", checkpoint_every=50, snapshot=snap).gradient(g)
-    assert rel_l2(g1.double().cpu().numpy(), g0.double().cpu().numpy()) <= 1e-2
+def test_checkpoint_reduced_snapshots_match_oracle(snap, K, nx):
+    """BF16 / FP16 snapshots with per-field scaling, segments recomputed in FP32:
+    the gradient is within 1e-3 relative L2 of the FP64 oracle's (the gradient
+    tolerance of the FP32 path; measured 1.8e-4 to 2.7e-4 with BF16, 3e-5 to 5e-5
+    with FP16), and J, which the forward march computes before any snapshot is
+    read, within 1e-5.  nx = 136 runs the TMA-staged kernels."""
+    pb = small(steady=False, n_steps=200, nx=nx)
+    g = pb.gamma()
+    ref = O.unsteady_gradient(pb, g)
+    J1, g1 = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap).gradient(torch.from_numpy(g))
+    assert abs(J1.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    assert rel_l2(g1.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
 
 
 # ---------------------------------------------------------------------------------------
 # API behaviour
 # ---------------------------------------------------------------------------------------
+def test_warm_start_continues_the_march():
+    """warm_start = 1: a second lks_forward continues from the state the first one
+    left, and a second alks_adjoint from its adjoint fields, so two calls of n steps
+    equal one call of 2n steps bit for bit (the same kernels run in the same order)."""
+    pb = small(n_steps=150, n_adj=120)
+    g = torch.from_numpy(pb.gamma())
+    a = LKS(pb, real="f64", path="step", warm_start=True)
+    a.lks_forward(g)
+    Ja = a.lks_forward(g).item()
+    a.alks_adjoint()
+    a.alks_adjoint()
+    ga = a.lks_sensitivity()
+    b = LKS(pb.with_(n_steps=300, n_adj=240), real="f64", path="step")
+    Jb = b.lks_forward(g).item()
+    b.alks_adjoint()
+    gb = b.lks_sensitivity()
+    assert Ja == Jb
+    for x, y in zip(a.get_state()[:3], b.get_state()[:3]):
+        assert torch.equal(x, y)
+    assert torch.equal(ga, gb)
+    assert a.query().forward_steps == 300 and a.query().adjoint_steps == 240
+
+
+def test_gpu_gradient_agrees_with_central_differences():
+    """Sec. 2.6 verification on the GPU path (FP64 instance): a converged steady
+    porous channel, ALKS sensitivity against central differences of J with step
+    1e-4 (Eq. sensfdm) on 12 design nodes drawn with seed 22 at least 3 nodes from
+    an edge.  Each perturbed march is a tolerance march warm-started from the
+    converged state of the unperturbed design.  ALKS is a continuous adjoint with
+    approximate edge rules, so the check is on direction: cosine >= 0.99."""
+    pb = inputs.Problem(nx=40, ny=24, nu=0.1, alpha_bar=100.0, u_max=0.05, sigma=2.0, strip=2, seed=7,
+                        n_steps=2000, n_adj=2000)
+    g = pb.gamma()
+    s = LKS(pb, real="f64", tol=1e-14, max_steps=400000, warm_start=True)
+    gt = torch.from_numpy(g)
+    J0, grad = s.gradient(gt)
+    grad = grad.cpu().numpy()
+    base = [x.clone() for x in s.get_state()]
+    rng = np.random.default_rng(22)
+    cand = [(j, i) for j in range(3, pb.ny - 3) for i in range(3, pb.nx - 3)]
+    nodes = [cand[k] for k in rng.choice(len(cand), 12, replace=False)]
+    eps = 1e-4
+    fd, ad = [], []
+    for (j, i) in nodes:
+        Js = []
+        for sgn in (1.0, -1.0):
+            gp = g.copy()
+            gp[j, i] += sgn * eps
+            s.set_state(gt, base[0], base[1], base[2])
+            Js.append(s.lks_forward(torch.from_numpy(gp)).item())
+            assert s.query().fwd_change <= 1e-14
+        fd.append((Js[0] - Js[1]) / (2 * eps))
+        ad.append(grad[j, i])
+    fd, ad = np.array(fd), np.array(ad)
+    cos = fd @ ad / np.linalg.norm(fd) / np.linalg.norm(ad)
+    assert cos >= 0.99, (cos, ad / fd)
+
+
 def test_gradient_host_matches_device():
     pb = small()
     g = pb.gamma()
