@@ -16,6 +16,7 @@ class LKSObjective(torch.autograd.Function):
     def forward(ctx, gamma: torch.Tensor, solver: LKS) -> torch.Tensor:
         J = solver.lks_forward(gamma.detach()).clone()
         ctx.solver = solver
+        ctx.gamma_dtype = gamma.dtype
         return J
 
     @staticmethod
@@ -23,7 +24,7 @@ class LKSObjective(torch.autograd.Function):
         s: LKS = ctx.solver
         s.alks_adjoint()
         g = s.lks_sensitivity()
-        return (grad_J.to(g.dtype) * g), None
+        return (grad_J.to(g.dtype) * g).to(ctx.gamma_dtype), None
 
 
 def objective(gamma: torch.Tensor, solver: LKS) -> torch.Tensor:

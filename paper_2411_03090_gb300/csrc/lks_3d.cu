@@ -841,6 +841,41 @@ __device__ __forceinline__ void fwd_moments3(const float (&F)[19], float& sm, fl
   mz = mom[2];
 }
 
+// The 19 pushed values of a node, P_k = w_k [base + c_k.b + c_k c_k : Q] (Eq. feq2 in
+// 3-D, with base = drho + e0, b = 3u and Q the coefficients of c_a c_b, each
+// off-diagonal entry counted once).  Opposite links share w (base + Q) and differ by
+// the sign of w c_k.b; the four diagonal links of an axis pair share
+// w (base + Q_aa + Q_bb) and split by the sign of Q_ab.  Summed over the links a
+// destination receives, these give rho and u* directly (no increment form).
+__device__ __forceinline__ void push_all3(float base, float bx, float by, float bz, float Qxx, float Qyy, float Qzz,
+                                          float Qxy, float Qxz, float Qyz, float (&P)[19]) {
+  constexpr float w0 = (float)w3d(0), w1 = (float)w3d(1), w2 = (float)w3d(7);
+  const float w1b = w1 * base, w2b = w2 * base;
+  const float b1[3] = {w1 * bx, w1 * by, w1 * bz};
+  const float b2[3] = {0.5f * b1[0], 0.5f * b1[1], 0.5f * b1[2]};  // w2 = w1 / 2 exactly
+  const float Qd[3] = {Qxx, Qyy, Qzz};
+  P[0] = w0 * base;
+  static_for<0, 3>([&](auto aa) {
+    constexpr int a = decltype(aa)::value;
+    const float t = w1 * Qd[a] + w1b;
+    P[link3(a == 0, a == 1, a == 2)] = t + b1[a];
+    P[link3(-(a == 0), -(a == 1), -(a == 2))] = t - b1[a];
+  });
+  static_for<0, 3>([&](auto pp) {
+    constexpr int p = decltype(pp)::value;
+    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;  // axis pairs (x,y), (x,z), (y,z)
+    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
+    const float Qab = p == 0 ? Qxy : (p == 1 ? Qxz : Qyz);
+    const float sdiag = w2 * (Qd[a] + Qd[b]) + w2b, q = w2 * Qab;
+    const float sp = sdiag + q, sm = sdiag - q;
+    const float c1 = b2[a] + b2[b], c2 = b2[a] - b2[b];
+    P[link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2])] = sp + c1;
+    P[link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2])] = sp - c1;
+    P[link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2])] = sm + c2;
+    P[link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2])] = sm - c2;
+  });
+}
+
 // ---------------------------------------------------------------------------------
 // Warp-column D3Q19 forward (FP32)
 // ---------------------------------------------------------------------------------
@@ -851,8 +886,7 @@ __device__ __forceinline__ void fwd_moments3(const float (&F)[19], float& sm, fl
 // copies into a ring of NSLC3 slots (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)),
 // requested three planes before they are first read; 1/(1+alpha) of an output node
 // is one global load, issued a plane ahead.  For each source plane z a lane
-// computes the 19 pushed increments of its node (push_link3, Eq. feq2) and routes
-// each at once:
+// computes the 19 pushed values of its node (push_all3, Eq. feq2) and routes each:
 //   - the 9 links with c_y = 0 stay in the warp: c_x by shuffle, c_z through a
 //     register ring of destination planes (plane d receives links 5, 11, 14 from
 //     plane d - 1, links 0, 1, 2 from plane d, links 6, 12, 13 from plane d + 1);
@@ -978,8 +1012,8 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
   };
   R inv_n = binv_at(z0 - 1);  // for the gather of plane z - 1 at step z
 
-  // the node's drho, u, v, w at planes z - 1 (m), z (c), z + 1 (p)
-  R dm = at(0, -1, 0, 0), um = at(1, -1, 0, 0), vm = at(2, -1, 0, 0), wm = at(3, -1, 0, 0);
+  // the node's u, v, w at planes z - 1 (m), z (c), z + 1 (p), and drho at z and z + 1
+  R um = at(1, -1, 0, 0), vm = at(2, -1, 0, 0), wm = at(3, -1, 0, 0);
   R dc = at(0, 0, 0, 0), uc = at(1, 0, 0, 0), vc = at(2, 0, 0, 0), wc = at(3, 0, 0, 0);
   R dp = at(0, 1, 0, 0), up = at(1, 1, 0, 0), vp = at(2, 1, 0, 0), wp = at(3, 1, 0, 0);
   R Am[9], Ac[9], Ap[9];  // links with c_y = 0 arriving at planes z - 1, z, z + 1 (slot oslot3(k))
@@ -991,9 +1025,6 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
   auto plane_step = [&](int z, auto fast_tag) {
     constexpr bool FAST = decltype(fast_tag)::value;
     const bool src = FAST || (in_xy && z >= 0 && z < nz);
-    const R dl = __shfl_up_sync(0xffffffffu, dc, 1), dr_ = __shfl_down_sync(0xffffffffu, dc, 1);
-    const R dml = __shfl_up_sync(0xffffffffu, dm, 1), dmr = __shfl_down_sync(0xffffffffu, dm, 1);
-    const R dpl = __shfl_up_sync(0xffffffffu, dp, 1), dpr = __shfl_down_sync(0xffffffffu, dp, 1);
     R gr[3][3];  // gr[d][a] = d u_d / d x_a
     gr[0][0] = (__shfl_down_sync(0xffffffffu, uc, 1) - __shfl_up_sync(0xffffffffu, uc, 1)) * R(0.5);
     gr[1][0] = (__shfl_down_sync(0xffffffffu, vc, 1) - __shfl_up_sync(0xffffffffu, vc, 1)) * R(0.5);
@@ -1043,17 +1074,12 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
     // destination lane lane + c_x is an output column (lanes 2 .. 29)
     const bool xl_m = lane >= 3 && lane <= CX3 + 2, xl_c = lane >= 2 && lane <= CX3 + 1,
                xl_p = lane >= 1 && lane <= CX3;
+    R PV[19];
+    push_all3(dc + e0, bxv, byv, bzv, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, PV);
     static_for<0, 19>([&](auto kk) {
       constexpr int k = decltype(kk)::value;
       constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
-      R dest;
-      if constexpr (cy != 0) dest = at(0, cz, cy, cx);
-      else if constexpr (cx == 0) dest = cz == 0 ? dc : (cz > 0 ? dp : dm);
-      else if constexpr (cz == 0) dest = cx > 0 ? dr_ : dl;
-      else if constexpr (cz > 0) dest = cx > 0 ? dpr : dpl;
-      else dest = cx > 0 ? dmr : dml;
-      const R pv = push_link3<k>(dc, dest, e0, bxv, byv, bzv, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz);
-      const R val = FAST ? pv : (src ? pv : R(0));
+      const R val = FAST ? PV[k] : (src ? PV[k] : R(0));
       if constexpr (cy != 0) {
         // destination row warp - 1 + cy of the exchange
         R* const xr = (cz < 0 ? xr_m : (cz == 0 ? xr_c : xr_p)) + ((cy > 0 ? 0 : -2) * NXL3 + yslot3(k)) * XW3 + cx;
@@ -1083,7 +1109,6 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
         if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
         else F[k] = Am[oslot3(k)];
       });
-      const R drx = dm;
       int n0 = 0, n1 = 0, n2 = 0, faces = 0;
       if constexpr (!FAST) {
         n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
@@ -1095,7 +1120,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       if (FAST || faces == 0) {
         R sm, mx, my, mz;
         fwd_moments3(F, sm, mx, my, mz);
-        drn = drx + sm;
+        drn = sm;
         uo[0] = mx * inv_c;
         uo[1] = my * inv_c;
         uo[2] = mz * inv_c;
@@ -1108,15 +1133,17 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
         if (n0 != 0) face_sums3<0>(F, n0, s0, sp);
         else if (n1 != 0) face_sums3<1>(F, n1, s0, sp);
         else face_sums3<2>(F, n2, s0, sp);
+        // the known populations' weights in s0 + 2 sp sum to one, so the pushed
+        // values (not increments) give rho directly
         if (n0 == 1) {
           drn = c.drho_out;
-          uo[0] = (s0 + R(2) * sp) + (drx - c.drho_out);
+          uo[0] = (s0 + R(2) * sp) - c.drho_out;
         } else {
-          if (n0 == -1) {
-            const double y = (double)j / (double)(ny - 1), zz = (double)zd / (double)(nz - 1);
-            uo[0] = (R)(c.u_max * 16.0 * y * (1.0 - y) * zz * (1.0 - zz));
+          if (n0 == -1) {  // inlet profile in FP32 (FP64 division is slow on this GPU)
+            const float y = (float)j / (float)(ny - 1), zz = (float)zd / (float)(nz - 1);
+            uo[0] = ((float)c.u_max * 16.f) * (y * (1.f - y)) * (zz * (1.f - zz));
           }
-          drn = drx + (s0 + R(2) * sp - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2)));
+          drn = (s0 + R(2) * sp) - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2));
         }
       }
       const size_t o = gidx(g, i, j, zd);
@@ -1133,7 +1160,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       Am[q] = Ac[q];
       Ac[q] = Ap[q];
     }
-    dm = dc, um = uc, vm = vc, wm = wc;
+    um = uc, vm = vc, wm = wc;
     dc = dp, uc = up, vc = vp, wc = wp;
     if (z + 2 <= plast) dp = at(0, 2, 0, 0), up = at(1, 2, 0, 0), vp = at(2, 2, 0, 0), wp = at(3, 2, 0, 0);
     zs = (zs + 1) & (NSLC3 - 1);
@@ -1579,44 +1606,80 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
       issued = z + NSLC3 - 3;
     }
     // ---- gather of node (i, j, z - 1) ----
+    R F[19];
+    bool face = false;
+    int cls = 0;
     if (gat) {
-      R F[19];
       const R* xr = xslot(zd, warp - 1) + lane - 2;
       static_for<0, 19>([&](auto kk) {
         constexpr int k = decltype(kk)::value;
         if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
         else F[k] = Am[oslot3(k)];
       });
-      int n0 = 0, n1 = 0, n2 = 0;
       if constexpr (!FAST) {
-        n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
-        n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
-        n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+        const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+        const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+        const int n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+        face = (n0 | n1 | n2) != 0;
+        cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
       }
-      R m[kNA3];
-      if (FAST || (n0 | n1 | n2) == 0) {
+      if (!face) {
+        R m[kNA3];
         adj_moments3(F, m);
         m[1] = (m[1] + C[1]) * C[0];
         m[2] = (m[2] + C[2]) * C[0];
         m[3] = (m[3] + C[3]) * C[0];
-      } else {
-        const int cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
-        const R* M = a.emap + cls * (kNA3 * 19);
-        const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
+        const size_t o = gidx(g, i, j, zd);
 #pragma unroll
-        for (int r = 0; r < kNA3; ++r) {
+        for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
+        if (!(m[1] * m[1] + m[2] * m[2] + m[3] * m[3] < R(1e30))) raise_status(a.status, 4);
+      }
+    }
+    if constexpr (!FAST) {
+      // Face, box-edge and corner nodes apply their class's moment map (10 x 19, plus
+      // the boundary objective term).  Where few lanes of the warp are such nodes (the
+      // x faces: one lane), the whole warp computes each one's ten moments, one row
+      // per lane, and lanes 0..9 store them, instead of that lane alone running the
+      // 190 products while the others wait.
+      unsigned fm = __ballot_sync(0xffffffffu, gat && face);
+      if (__popc(fm) > 2) {
+        if (gat && face) {
+          const R* M = a.emap + cls * (kNA3 * 19);
+          const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
+          const size_t o = gidx(g, i, j, zd);
+          R u2 = R(0);
+#pragma unroll
+          for (int r = 0; r < kNA3; ++r) {
+            R sacc = R(0);
+            static_for<0, 19>([&](auto kk) {
+              constexpr int k = decltype(kk)::value;
+              sacc += M[r * 19 + k] * F[k];
+            });
+            sacc += M0[r];
+            a.m0[r][o] = sacc;
+            if (r >= 1 && r <= 3) u2 += sacc * sacc;
+          }
+          if (!(u2 < R(1e30))) raise_status(a.status, 4);
+        }
+      } else {
+        const int row = lane < kNA3 ? lane : kNA3 - 1;
+        while (fm) {
+          const int srcl = __ffs(fm) - 1;
+          fm &= fm - 1;
+          const int cs = __shfl_sync(0xffffffffu, cls, srcl);
+          const R* M = a.emap + (cs * kNA3 + row) * 19;
           R sacc = R(0);
           static_for<0, 19>([&](auto kk) {
             constexpr int k = decltype(kk)::value;
-            sacc += M[r * 19 + k] * F[k];
+            sacc += M[k] * __shfl_sync(0xffffffffu, F[k], srcl);
           });
-          m[r] = sacc + M0[r];
+          sacc += a.emap[kClasses3 * kNA3 * 19 + cs * kNA3 + row];
+          if (lane < kNA3) {
+            a.m0[lane][gidx(g, x0 - 2 + srcl, j, zd)] = sacc;
+            if (lane >= 1 && lane <= 3 && !(sacc * sacc < R(1e30))) raise_status(a.status, 4);
+          }
         }
       }
-      const size_t o = gidx(g, i, j, zd);
-#pragma unroll
-      for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
-      if (!(m[1] * m[1] + m[2] * m[2] + m[3] * m[3] < R(1e30))) raise_status(a.status, 4);
     }
     // ---- rotate ----
 #pragma unroll
