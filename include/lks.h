@@ -116,8 +116,15 @@ typedef struct {
     int32_t res_steps;        /* resident marches: time steps per exchange of tile
                                  bands, 0 automatic or 1..3; the largest value up to
                                  this that fits the tile shape and shared memory runs */
-    double kappa_p;           /* D3Q19: weight of the static pressure drop in J
-                                 (Eq. objective_pipebend, see below); D2Q9: 0        */
+    double kappa_p;           /* weight of the static pressure drop in J (Eq.
+                                 objective_pipebend): J = J_O + kappa_p J_p with
+                                 J_p = 1/3 (sum of rho over the inlet nodes - over
+                                 the outlet nodes); the adjoint edge rule carries
+                                 +kappa_p (inlet nodes) or -kappa_p (outlet nodes) in
+                                 every residual row of Eqs. afboundaryu / afboundaryp.
+                                 D2Q9: steady problems only; inlet nodes are the left
+                                 edge nodes inside [in_y0, in_y1] (corners excluded),
+                                 outlet nodes the pressure nodes.  D3Q19: see below */
     double tol;               /* steady D2Q9: > 0 marches to a relative step change
                                  of tol (see lks_forward); 0 fixed step counts        */
     int32_t max_steps;        /* tol > 0: step limit of each march (>= n_steps, n_adj) */
@@ -295,6 +302,13 @@ lks_status lks_gradient_noalloc(const lks_problem_desc *desc, const void *gamma_
  * every face by the least squares of Sec. 2.5 (Eqs. afboundaryu, afboundaryp,
  * afboundaryuq, afboundarypq). */
 lks_status lks_edge_moment_map(double A, int32_t cls, double *out);
+
+/* Host-only: the response of the six flow moments of an edge node of class cls to a
+ * unit boundary objective term added to every residual row (dJ_dO/df_i of Eqs.
+ * afboundaryu / afboundaryp, with the known f~ and kappa~ T zero).  The adjoint
+ * kernels add kappa_p times this (+ on inlet nodes, - on outlet nodes) for the
+ * static pressure drop.  out: 6 doubles. */
+lks_status lks_edge_objective_map(double A, int32_t cls, double *out);
 
 /* Diagnostics: runs one of the library's bounded device waits on a condition that
  * never comes true, on cuda_stream, and returns in *recorded the status the kernel

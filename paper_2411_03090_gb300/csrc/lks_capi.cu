@@ -84,7 +84,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
   L.chg = take(2 * sizeof(unsigned));  // change of a measured step (tol > 0)
-  L.emap = take(L.rsize * 9 * 60);
+  L.emap = take(L.rsize * lks::kEdgeMapLen);  // 9 classes x 6 x 10, then 9 x 6 boundary objective terms
   L.flags = take(sizeof(int) * (size_t)((d->nx + 31) / 32) * (size_t)((d->ny + 7) / 8));
   L.mat = take(fb * 3);  // 1/(1+alpha), alpha, B (FP32 staged kernels)
   if (!d->steady) {
@@ -972,7 +972,15 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   R* v = state_ptr<R>(h, h->cur, 2);
   R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
   if ((st = launch_objective<R>(h, u, v, T, jobj)) != LKS_OK) return st;
-  reduce_partials_kernel<<<1, NTHREADS, 0, h->stream>>>(jobj, L.obj_blocks, jfwd, d.steady ? 0 : L.fwd_blocks, jval);
+  int n2 = d.steady ? 0 : L.fwd_blocks;
+  if (d.steady && d.kappa_p != 0.0) {  // + kappa_p J_p in the first (unused) forward partial
+    pressure_drop_kernel<R><<<1, NTHREADS, 0, h->stream>>>(state_ptr<R>(h, h->cur, 0), make_geom(d), make_coef<R>(d),
+                                                           jfwd);
+    CKH(h, cudaGetLastError());
+    h->launches++;
+    n2 = 1;
+  }
+  reduce_partials_kernel<<<1, NTHREADS, 0, h->stream>>>(jobj, L.obj_blocks, jfwd, n2, jval);
   CKH(h, cudaGetLastError());
   h->launches++;
   if (J_dev) CKH(h, cudaMemcpyAsync(J_dev, jval, sizeof(double), cudaMemcpyDeviceToDevice, h->stream));
@@ -1126,13 +1134,13 @@ template <typename R>
 lks_status upload_maps(lks_handle* h) {
   const auto& d = h->d;
   const double A = (1.0 / 6.0 - d.nu) * 4.5;
-  h->emap_h.assign(9 * 60, 0.0);
-  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &h->emap_h[cls * 60]);
+  h->emap_h.assign(lks::kEdgeMapLen, 0.0);
+  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &h->emap_h[cls * 60], &h->emap_h[540 + cls * 6]);
   if (sizeof(R) == 8) {
-    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_h.data(), 9 * 60 * 8, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_h.data(), lks::kEdgeMapLen * 8, cudaMemcpyHostToDevice));
   } else {
     h->emap_f.assign(h->emap_h.begin(), h->emap_h.end());
-    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_f.data(), 9 * 60 * 4, cudaMemcpyHostToDevice));
+    CKH(h, cudaMemcpy(h->ws + h->L.emap, h->emap_f.data(), lks::kEdgeMapLen * 4, cudaMemcpyHostToDevice));
   }
   return LKS_OK;
 }
@@ -1459,15 +1467,15 @@ lks_status noalloc_scratch(void** out, int* dev_out) {
   return LKS_OK;
 }
 
-// The nine edge-class maps travel as a kernel argument (4320 bytes, within the
+// The nine edge-class maps travel as a kernel argument (4752 bytes, within the
 // 32 KB parameter limit), so no host buffer is read after the call returns.
 struct EdgeMaps {
-  double v[9 * 60];
+  double v[lks::kEdgeMapLen];
 };
 
 template <typename R>
 __global__ void fill_edge_maps_kernel(EdgeMaps m, R* dst) {
-  for (int i = threadIdx.x; i < 9 * 60; i += blockDim.x) dst[i] = (R)m.v[i];
+  for (int i = threadIdx.x; i < lks::kEdgeMapLen; i += blockDim.x) dst[i] = (R)m.v[i];
 }
 
 // Device-detected failures (instability, a bounded wait that gave up) set the status
@@ -1481,7 +1489,7 @@ template <typename R>
 lks_status upload_maps_async(lks_handle* h) {
   const double A = (1.0 / 6.0 - h->d.nu) * 4.5;
   EdgeMaps m;
-  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &m.v[cls * 60]);
+  for (int cls = 0; cls < 9; ++cls) flow_moment_map(A, cls, &m.v[cls * 60], &m.v[540 + cls * 6]);
   fill_edge_maps_kernel<R><<<1, 256, 0, h->stream>>>(m, reinterpret_cast<R*>(h->ws + h->L.emap));
   CKH(h, cudaGetLastError());
   ++h->launches;
@@ -1539,6 +1547,13 @@ lks_status lks_selftest_wait(int32_t which, int32_t* scratch, void* stream, int3
       cudaStreamSynchronize(s) != cudaSuccess)
     return LKS_ERR_CUDA;
   *recorded = st;
+  return LKS_OK;
+}
+
+lks_status lks_edge_objective_map(double A, int32_t cls, double* out) {
+  if (!out || cls < 0 || cls > 8) return LKS_ERR_INVALID_ARG;
+  double full[60];
+  flow_moment_map(A, cls, full, out);
   return LKS_OK;
 }
 

@@ -518,13 +518,13 @@ constexpr int ACOL_FS = (ACOL_BOX * 4 + 127) / 128 * 128 / 4;
 __host__ __device__ constexpr int acol_nf(bool same) { return same ? 10 : 12; }
 // staged fields, alignment slack, the mbarrier, the edge maps (9 classes x 60)
 __host__ __device__ constexpr size_t acol_smem_bytes(bool same) {
-  return (size_t)acol_nf(same) * ACOL_FS * 4 + 128 + 8 + 540 * 4;
+  return (size_t)acol_nf(same) * ACOL_FS * 4 + 128 + 8 + kEdgeMapLen * 4;
 }
 
 struct AdjColArgs {
   float* m0[6];       // adjoint moments at level t
   const float* gamma;
-  const float* emap;  // 9 classes x 6 x 10 (batched form: per design, 540 floats each)
+  const float* emap;  // kEdgeMapLen values (batched form: per design, the 540 maps only)
   float* sens;        // optional sensitivity accumulator
   int sens_flow;
   int* status;
@@ -586,8 +586,8 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
     for (int f = 0; f < NF; ++f)
       tma_load_2d(box + f * ACOL_FS, &maps.m[f], ax + x0 - TMA_BXPAD, ay + y0 - 2, bar);
   }
-  if (!fast)
-    for (int t = threadIdx.x; t < 540; t += COL_NT) sem[t] = __ldg(emap + t);
+  if (!fast)  // the batched form's per-design maps have no boundary objective terms
+    for (int t = threadIdx.x; t < (BATCH ? 540 : kEdgeMapLen); t += COL_NT) sem[t] = __ldg(emap + t);
   __syncthreads();
   if (!mbar_wait(bar, 0)) {
     raise_status(a.status, 6);
@@ -701,9 +701,16 @@ __global__ void __launch_bounds__(COL_NT) adj_col_kernel(const __grid_constant__
             const int gi = i + cxk(k), gj = q + cyk(k);
             if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = 0.f;
           }
-          const float* M = sem + edge_class(g, i, q) * 60;
+          const int ec = edge_class(g, i, q);
+          const float* M = sem + ec * 60;
 #pragma unroll
           for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, 0.f);
+          if constexpr (!BATCH) {  // the static pressure drop (steady single lattices only)
+            const float jb = edge_objective_term(g, c, ec, q);
+            if (jb != 0.f)
+#pragma unroll
+              for (int r = 0; r < 6; ++r) m[r] = __fmaf_rn(jb, sem[540 + ec * 6 + r], m[r]);
+          }
         }
         (void)sq;
 #pragma unroll

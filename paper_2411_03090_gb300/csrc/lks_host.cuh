@@ -84,7 +84,8 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->snapshot_type < LKS_SNAP_F32 || d->snapshot_type > LKS_SNAP_F16) return bad("bad snapshot_type");
   if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
   if (d->res_steps < 0 || d->res_steps > 3) return bad("res_steps must lie in 0..3");
-  if (d->kappa_p != 0.0) return bad("D2Q9: kappa_p must be 0 (the pressure-drop term is D3Q19 only)");
+  if (!std::isfinite(d->kappa_p)) return bad("kappa_p must be finite");
+  if (d->kappa_p != 0.0 && !d->steady) return bad("D2Q9: kappa_p != 0 needs a steady problem");
   if (!(d->tol >= 0.0) || !std::isfinite(d->tol)) return bad("tol must be >= 0");
   if (d->tol > 0.0) {
     if (!d->steady) return bad("tol > 0: steady problems only");
@@ -147,8 +148,11 @@ inline void class_geometry(int cls, int* nx, int* ny, int* pressure) {
 // Flow: 6 x 10 moment map for edge class cls at parameter A: columns 0..8 map the
 // nine gathered f~ (unknown entries ignored); column 9 is the response of the
 // moments to the heat-flux coupling term kappa~ T (c.n) of Eqs. afboundaryuq /
-// afboundarypq, which enters the residual as -kappa~ T (c_i.n).
-inline void flow_moment_map(double A, int cls, double* out) {
+// afboundarypq, which enters the residual as -kappa~ T (c_i.n).  jb_out (optional,
+// 6 values): the response to a boundary objective term added to every residual row
+// (dJ_dO/df_i of Eqs. afboundaryu / afboundaryp; +kappa_p on inlet nodes and
+// -kappa_p on outlet nodes for the static pressure drop).
+inline void flow_moment_map(double A, int cls, double* out, double* jb_out = nullptr) {
   int n_x, n_y, pres;
   class_geometry(cls, &n_x, &n_y, &pres);
   bool unk[9];
@@ -176,11 +180,11 @@ inline void flow_moment_map(double A, int cls, double* out) {
       Am[r * nc + nu + 1] = CYh[r];
     }
   }
-  double X[9][10] = {};  // X[u][k]: unknown u from known k; column 9: from kappa~ T
-  for (int k = 0; k < 10; ++k) {
+  double X[9][11] = {};  // X[u][k]: unknown u from known k; 9: from kappa~ T; 10: from a unit row term
+  for (int k = 0; k < 11; ++k) {
     if (k < 9 && unk[k]) continue;
     double rhs[9], x[16];
-    for (int r = 0; r < 9; ++r) rhs[r] = k < 9 ? -M[r][k] : (double)(CXh[r] * n_x + CYh[r] * n_y);
+    for (int r = 0; r < 9; ++r) rhs[r] = k < 9 ? -M[r][k] : (k == 9 ? (double)(CXh[r] * n_x + CYh[r] * n_y) : -1.0);
     lsq_solve(Am.data(), nc, rhs, x);
     for (int q = 0; q < nu; ++q) X[U[q]][k] = x[q];
   }
@@ -198,6 +202,16 @@ inline void flow_moment_map(double A, int cls, double* out) {
       }
       out[r * 10 + k] = s;
     }
+  if (jb_out)
+    for (int r = 0; r < 6; ++r) {
+      double s = 0.0;
+      for (int q = 0; q < nu; ++q) {
+        const double cx = CXh[U[q]], cy = CYh[U[q]];
+        const double f[6] = {1, cx, cy, cx * cx, cx * cy, cy * cy};
+        s += Wh[U[q]] * f[r] * X[U[q]][10];
+      }
+      jb_out[r] = s;
+    }
 }
 
 template <typename R>
@@ -212,6 +226,7 @@ inline Coef<R> make_coef(const lks_problem_desc& d) {
   c.K_s = (R)d.K_s;
   c.q_K = (R)d.q_K;
   c.kappa_T = (R)d.kappa_T;
+  c.kappa_p = (R)d.kappa_p;
   for (int e = 0; e < 4; ++e) c.t_val[e] = (R)d.t_val[e];
   return c;
 }

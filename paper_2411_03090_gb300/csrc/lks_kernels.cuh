@@ -70,7 +70,23 @@ struct Coef {
   R K_f, K_s, q_K;
   R kappa_T;
   R t_val[4];
+  R kappa_p;    // weight of the static pressure drop J_p in J (steady problems)
 };
+
+// Edge maps of one lattice: 9 classes x 6 moments x 10 columns (lks_edge_moment_map),
+// then 9 classes x 6 responses to a unit boundary objective term.
+constexpr int kEdgeMapLen = 9 * 60 + 9 * 6;
+
+// Boundary objective term of the static pressure drop at an edge node of class ec
+// (dJ_dO/df_i of Eqs. afboundaryu / afboundaryp, every residual row): +kappa_p on the
+// inlet nodes (left face inside the inlet span), -kappa_p on the outlet nodes
+// (pressure class), 0 elsewhere.
+template <typename R>
+__device__ __forceinline__ R edge_objective_term(const Geom& g, const Coef<R>& c, int ec, int j) {
+  if (ec == 1) return -c.kappa_p;
+  if (ec == 0 && j >= g.in_y0 && j <= g.in_y1) return c.kappa_p;
+  return R(0);
+}
 
 // Edge-class index of the moment maps (see lks_edge_moment_map in lks.h).
 __device__ __forceinline__ int edge_class(const Geom& g, int i, int j) {
@@ -737,12 +753,14 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
         if (flux) kT = kap * sT0[s2];
       }
       const R* M = a.emap + ec * 60;
+      const R jb = edge_objective_term(g, c, ec, j);
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
         R s = R(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) s += M[r * 10 + k] * ft[k];
         m[r] = s + M[r * 10 + 9] * kT;
+        if (jb != R(0)) m[r] += jb * a.emap[540 + ec * 6 + r];
       }
     }
     const size_t o = (size_t)j * nx + i;
@@ -785,6 +803,23 @@ __global__ void __launch_bounds__(NTHREADS) objective_kernel(const R* __restrict
   }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// Static pressure drop of Eq. objective_pipebend, kappa_p J_p with
+// J_p = 1/3 (sum of rho over the inlet nodes - over the outlet nodes) (p = rho / 3,
+// dGamma = 1; inlet: left face inside the inlet span, corners excluded; outlet: the
+// pressure nodes).  One block; drho = rho - 1 is the stored density.
+template <typename R>
+__global__ void __launch_bounds__(NTHREADS) pressure_drop_kernel(const R* __restrict__ drho, Geom g, Coef<R> c,
+                                                                 double* out) {
+  __shared__ double red[NTHREADS / 32];
+  double acc = 0.0;
+  for (int j = 1 + threadIdx.x; j < g.ny - 1; j += NTHREADS) {
+    if (j >= g.in_y0 && j <= g.in_y1) acc += 1.0 + (double)drho[(size_t)j * g.nx];
+    if (j >= g.out_y0 && j <= g.out_y1) acc -= 1.0 + (double)drho[(size_t)j * g.nx + g.nx - 1];
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) *out = (double)c.kappa_p * s / 3.0;
 }
 
 // Deterministic sum of n partials (one block) plus an optional second array.

@@ -457,12 +457,15 @@ __global__ void __launch_bounds__(NT, 1) adj_resident_tb_kernel(ResArgs<R> a, Ge
         const int gi = i + cxk(k), gj = j + cyk(k);
         if (gi < 0 || gi >= nx || gj < 0 || gj >= ny) ft[k] = R(0);
       }
-      const R* M = a.emap + edge_class(g, i, j) * 60;
+      const int ec = edge_class(g, i, j);
+      const R* M = a.emap + ec * 60;
+      const R jb = edge_objective_term(g, c, ec, j);  // the static pressure drop
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
         R acc = R(0);
 #pragma unroll
         for (int k = 0; k < 9; ++k) acc += M[r * 10 + k] * ft[k];
+        if (jb != R(0)) acc += jb * a.emap[540 + ec * 6 + r];
         o[r] = acc;
       }
     }

@@ -889,9 +889,16 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
             m[8] = qy_;
             if (flux) kT = kap * sT0[s2];
           }
-          const float* M = emap + edge_class(g, i, j) * 60;
+          const int ec = edge_class(g, i, j);
+          const float* M = emap + ec * 60;
 #pragma unroll
           for (int r = 0; r < 6; ++r) m[r] = adj_edge_row(M + r * 10, ft, kT);
+          if constexpr (!BATCH) {  // the static pressure drop (steady single lattices only)
+            const float jb = edge_objective_term(g, c, ec, j);
+            if (jb != 0.f)
+#pragma unroll
+              for (int r = 0; r < 6; ++r) m[r] = __fmaf_rn(jb, emap[540 + ec * 6 + r], m[r]);
+          }
         }
 #pragma unroll
         for (int f = 0; f < NA; ++f) sout[f * TX_ * TY_ + q] = m[f];

@@ -94,7 +94,8 @@ class BatchStats(C.Structure):
 EXPORTS = ("lks_workspace_size", "lks_create", "lks_forward", "alks_adjoint", "lks_sensitivity",
            "lks_gradient_host", "lks_set_state", "lks_get_state", "lks_march", "alks_set_adjoint",
            "alks_get_adjoint", "alks_march", "lks_query", "lks_destroy", "lks_status_string",
-           "lks_last_error", "lks_edge_moment_map", "lks_selftest_wait", "lks_gradient_noalloc",
+           "lks_last_error", "lks_edge_moment_map", "lks_edge_objective_map", "lks_selftest_wait",
+           "lks_gradient_noalloc",
            "lks_batch_workspace_size", "lks_batch_create", "lks_batch_gradient", "lks_batch_query",
            "lks_batch_destroy", "lks_batch_last_error")
 
@@ -136,6 +137,7 @@ def load(build_if_missing: bool = True):
     L.lks_last_error.argtypes = [hp]
     L.lks_last_error.restype = C.c_char_p
     L.lks_edge_moment_map.argtypes = [C.c_double, i32, dp]
+    L.lks_edge_objective_map.argtypes = [C.c_double, i32, dp]
     L.lks_selftest_wait.argtypes = [i32, C.c_void_p, C.c_void_p, C.POINTER(C.c_int32)]
     L.lks_gradient_noalloc.argtypes = [C.POINTER(Desc), vp, vp, vp, vp]
     L.lks_batch_workspace_size.argtypes = [i32, C.POINTER(Desc), C.POINTER(BatchOptions), C.POINTER(C.c_size_t)]
@@ -176,7 +178,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     if getattr(pb, "periodic", 0) or getattr(pb, "G_x", 0.0) or getattr(pb, "G_y", 0.0):
         raise ValueError("periodic lattices and an external force are not part of the CUDA path")
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
-                 "rho_out", "K_f", "K_s", "q_K", "kappa_T"):
+                 "rho_out", "K_f", "K_s", "q_K", "kappa_T", "kappa_p"):
         setattr(d, name, float(getattr(pb, name)))
     res = pb.resolved if hasattr(pb, "resolved") else (lambda n: getattr(pb, n))
     d.in_y0, d.in_y1 = int(res("in_y0")), int(res("in_y1"))
@@ -234,6 +236,15 @@ def edge_moment_map(A: float, cls: int) -> np.ndarray:
     _check(load().lks_edge_moment_map(float(A), int(cls),
                                       out.ctypes.data_as(C.POINTER(C.c_double))), "edge map")
     return out.reshape(6, 10)
+
+
+def edge_objective_map(A: float, cls: int) -> np.ndarray:
+    """Host-only: the response of the six flow moments of class ``cls`` to a unit
+    boundary objective term in every residual row."""
+    out = np.zeros(6)
+    _check(load().lks_edge_objective_map(float(A), int(cls),
+                                         out.ctypes.data_as(C.POINTER(C.c_double))), "edge objective map")
+    return out
 
 
 class LKS:

@@ -70,6 +70,11 @@ def test_edge_maps_match_oracle(cls, n, pressure):
     kT = 0.37
     full, _ = O.bc_flow(n, pressure, A, f, unknown, kT=kT)
     np.testing.assert_allclose(M[:, :9] @ f + M[:, 9] * kT, _moments(full), atol=1e-13)
+    # a boundary objective term in every residual row (the static pressure drop)
+    jb = -0.61
+    Mj = lks.edge_objective_map(A, cls)
+    full_j, _ = O.bc_flow(n, pressure, A, f, unknown, kT=kT, jb=jb)
+    np.testing.assert_allclose(M[:, :9] @ f + M[:, 9] * kT + Mj * jb, _moments(full_j), atol=1e-13)
 
 
 def test_descriptor_validation():
@@ -93,8 +98,9 @@ def test_descriptor_validation():
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
     assert lks.workspace_size(lks.make_desc(pb, warm_start=True)) == lks.workspace_size(d)
-    bad = lks.make_desc(pb)
-    bad.kappa_p = 1.0  # the pressure-drop term is D3Q19 only
+    ok = lks.make_desc(pb.with_(kappa_p=1.0))  # steady D2Q9: the pressure drop is accepted
+    assert ok.kappa_p == 1.0 and lks.workspace_size(ok) == lks.workspace_size(d)
+    bad = lks.make_desc(pb.with_(kappa_p=1.0, steady=False))  # unsteady D2Q9: not with kappa_p
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
     d3 = lks.make_desc(inputs.config4())

@@ -429,6 +429,70 @@ def test_gpu_gradient_agrees_with_central_differences():
     assert cos >= 0.99, (cos, ad / fd)
 
 
+@pytest.mark.parametrize("real,path,nx,ftol,gtol", [("f64", "step", 70, 1e-11, 1e-10), ("f32", "step", 136, 1e-5, 1e-3),
+                                                    ("f32", "resident", 136, 1e-5, 1e-3),
+                                                    ("f32", "column", 136, 1e-5, 1e-3)])
+def test_pressure_drop_objective_matches_oracle(real, path, nx, ftol, gtol):
+    """J = J_O + J_p with the static pressure drop (Eq. objective_pipebend, kappa_p = 1)
+    on a channel whose inlet covers rows 8..30 of the left edge (walls elsewhere on it)
+    and whose outlet covers rows 5..34: J and the adjoint fields (which carry the
+    boundary objective term of Eqs. afboundaryu / afboundaryp) and dJ/dgamma against
+    the oracle, on the per-step (plain and TMA-staged), resident and warp-column
+    kernels."""
+    pb = small(nx=nx, kappa_p=1.0, in_y0=8, in_y1=30, out_y0=5, out_y1=34)
+    g = pb.gamma()
+    s = LKS(pb, real=real, path=path)
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.device_status == 0 and q.fwd_path == {"step": 1, "resident": 2, "column": 3}[path]
+    ref = O.steady_gradient(pb, g)
+    assert abs(O.pressure_drop(pb, ref["state"])) > 1e-3 * abs(ref["J"])  # the term matters
+    assert abs(J.item() - ref["J"]) <= ftol * abs(ref["J"])
+    adj = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    for k in range(6):
+        assert rel_l2(adj[k], ref["adjoint"][k]) <= gtol, k
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= gtol
+
+
+def test_pressure_drop_verification_of_the_paper_on_the_gpu():
+    """Sec. 2.6's pressure-drop verification on the GPU path (FP64 instance), 31 x 31
+    nodes: walls, inlet and outlet over rows 10..20, nu = 0.1, Re = 1 on the length 10,
+    gamma = 0.1 in the centre circle of radius 5 and 0.9 elsewhere, J = J_p.  The
+    gradient equals the oracle's to 1e-10, and ALKS agrees with central differences of
+    J (eps = 1e-3, tolerance marches warm-started from the converged state) along the
+    centre line within 0.75..1.1, as the oracle pin finds."""
+    n, nu = 31, 0.1
+    pb = inputs.Problem(nx=n, ny=n, nu=nu, alpha_bar=1e3 * nu, u_max=nu / 10.0, in_y0=10, in_y1=20,
+                        out_y0=10, out_y1=20, n_steps=25000, n_adj=25000)
+    yy, xx = np.mgrid[0:n, 0:n]
+    g = np.where((xx - 15) ** 2 + (yy - 15) ** 2 <= 25.0, 0.1, 0.9)
+    # J_p alone: the dissipation's share is removed by differencing kappa_p = 1 and 0
+    s1 = LKS(pb.with_(kappa_p=1.0), real="f64")
+    s0 = LKS(pb, real="f64")
+    J1, g1 = s1.gradient(torch.from_numpy(g))
+    J0, g0 = s0.gradient(torch.from_numpy(g))
+    adj = (g1 - g0).cpu().numpy()
+    r1 = O.steady_gradient(pb.with_(kappa_p=1.0), g)
+    r0 = O.steady_gradient(pb, g)
+    assert rel_l2(adj, r1["dJdgamma"] - r0["dJdgamma"]) <= 1e-9
+    st = LKS(pb.with_(n_steps=500), real="f64", tol=1e-15, max_steps=400000, warm_start=True)
+    gt = torch.from_numpy(g)
+    st.lks_forward(gt)
+    base = [x.clone() for x in st.get_state()]
+    eps = 1e-3
+    for i in (6, 15, 21):
+        v = []
+        for sg in (1, -1):
+            gg = g.copy()
+            gg[15, i] += sg * eps
+            st.set_state(gt, base[0], base[1], base[2])
+            st.lks_forward(torch.from_numpy(gg))
+            d = st.get_state()[0].cpu().numpy()  # rho - 1
+            v.append((d[10:21, 0].sum() - d[10:21, -1].sum()) / 3.0)  # J_p (the 1s cancel)
+        fd = (v[0] - v[1]) / (2 * eps)
+        assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
+
+
 def test_gradient_host_matches_device():
     pb = small()
     g = pb.gamma()
