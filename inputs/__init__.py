@@ -94,6 +94,12 @@ class Problem:
     periodic: int = 0        # oracle-only pin geometries: bit 0 x periodic, bit 1 y periodic
     G_x: float = 0.0         # oracle-only pin geometries: uniform external force
     G_y: float = 0.0
+    beta_bar: float = 0.0    # heat source Q = beta_gamma (1 - T) (0: none)
+    q_beta: float = 0.1
+    kappa_Q: float = 0.0     # weight of the heat-exchange objective -sum beta_gamma (1 - T)
+    gb_x: float = 0.0        # Boussinesq force G = g beta (T - T_ref): the products g_a beta
+    gb_y: float = 0.0
+    T_ref: float = 0.0
 
     def resolved(self, name: str):
         """Field value with negative span ends counted from the top edge (ny + v)."""

@@ -89,6 +89,13 @@ typedef struct {
     int periodic;              /* bit 0: x periodic (no left / right edges),
                                   bit 1: y periodic (no bottom / top edges)    */
     double G_x, G_y;           /* uniform external force G of Eq. (lbef_ex)   */
+    double beta_bar, q_beta;   /* heat source Q = beta_gamma (1 - T), Eqs.
+                                  (heatsource), (betagamma); beta_bar = 0: none */
+    double kappa_Q;            /* weight of the heat-exchange objective
+                                  -sum beta_gamma (1 - T), Eq. (objective_heatexchanger) */
+    double gb_x, gb_y;         /* Boussinesq force G = g beta (T - T_ref),
+                                  Eq. (boussinesqforce): the products g_a beta */
+    double T_ref;
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -107,6 +114,14 @@ static double K_of(const orc_problem *p, double g) {
     return p->K_f + (p->K_s - p->K_f) * p->q_K * (1.0 - g) / (p->q_K + g);
 }
 static double B_of(const orc_problem *p, double g) { return 3.0 * (1.0 / 6.0 - K_of(p, g)); }
+/* Eq. (betagamma): beta_gamma = beta_bar q_beta (1 - gamma) / (q_beta + gamma) */
+static double beta_of(const orc_problem *p, double g) {
+    return p->beta_bar * p->q_beta * (1.0 - g) / (p->q_beta + g);
+}
+static double dbeta_of(const orc_problem *p, double g) {
+    double d = p->q_beta + g;
+    return -p->beta_bar * p->q_beta * (1.0 + p->q_beta) / (d * d);
+}
 static double dB_of(const orc_problem *p, double g) {
     double d = p->q_K + g;
     double dK = -(p->K_s - p->K_f) * p->q_K * (1.0 + p->q_K) / (d * d);
@@ -260,7 +275,10 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
     if (cls == N_INTERIOR) {
         /* Eqs. (rho), (u), (T); Brinkman and force terms of Eq. (lbef_ex), the
          * Brinkman term implicit: u = (u* + G) / (1 + alpha_gamma)  (sum of c_k
-         * times Eq. lbef_ex, with sum_k w_k c_k c_k = 1/3). */
+         * times Eq. lbef_ex, with sum_k w_k c_k c_k = 1/3).  The heat source of
+         * Eq. (lbeg_ex) enters T once per step at t + dt, implicitly as the Brinkman
+         * term: T = (T* + beta_gamma) / (1 + beta_gamma) for Q = beta_gamma (1 - T).
+         * G = G0 + g beta (T - T_ref) uses that new T (Eq. boussinesqforce). */
         double us = 0.0, vs = 0.0;
         for (int k = 0; k < 9; ++k) {
             r += f[k];
@@ -268,9 +286,18 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
             vs += CY[k] * f[k];
             TT += g[k];
         }
+        double Gx = p->G_x, Gy = p->G_y;
+        if (p->thermal) {
+            if (p->beta_bar != 0.0) {
+                double b = beta_of(p, AT(gamma, i, j));
+                TT = (TT + b) / (1.0 + b);
+            }
+            Gx += p->gb_x * (TT - p->T_ref);
+            Gy += p->gb_y * (TT - p->T_ref);
+        }
         double a = alpha_of(p, AT(gamma, i, j));
-        uu = (us + p->G_x) / (1.0 + a);
-        vv = (vs + p->G_y) / (1.0 + a);
+        uu = (us + Gx) / (1.0 + a);
+        vv = (vs + Gy) / (1.0 + a);
     } else if (cls == N_CORNER) {
         /* Corner: wall node, u = 0; density carried over from the previous step
          * of the edge neighbour at the same x (one row into the lattice). */
@@ -371,7 +398,11 @@ double orc_objective(const orc_problem *p, const double *gamma, const double *u,
             double uu = AT(u, i, j), vv = AT(v, i, j);
             J += 0.5 * p->nu * (Sxx * Sxx + 2.0 * Sxy * Sxy + Syy * Syy) +
                  alpha_of(p, AT(gamma, i, j)) * (uu * uu + vv * vv);
-            if (p->thermal) J += p->kappa_T * AT(T, i, j);
+            if (p->thermal) {
+                J += p->kappa_T * AT(T, i, j);
+                /* heat exchange, Eq. (objective_heatexchanger): -sum beta_gamma (1 - T) */
+                if (p->kappa_Q != 0.0) J -= p->kappa_Q * beta_of(p, AT(gamma, i, j)) * (1.0 - AT(T, i, j));
+            }
         }
     return J;
 }
@@ -682,9 +713,17 @@ void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P
         orc_dJdu_node(p, gamma, u0, v0, i, j, &ju, &jv);
         double a = alpha_of(p, AT(gamma, i, j));
         double Tn = p->thermal ? AT(T0, i, j) : 0.0;
-        if (p->thermal) m[6] -= p->kappa_T;
         m[1] = (m[1] - ju / 3.0 + Tn * m[7]) / (1.0 + a);
         m[2] = (m[2] - jv / 3.0 + Tn * m[8]) / (1.0 + a);
+        if (p->thermal) {
+            /* Eq. (albeg_ex): the source -dJ_O/dg_k = -dJ_O/dT; the Boussinesq term
+             * 3 (dG_a/dg_k) u~_a = 3 g_a beta u~_a with u~ of this level; the heat
+             * source term dQ/dg_k T~ = -beta_gamma T~ taken implicitly, as in the
+             * forward step: T~ = (T~* + 3 g beta . u~ - dJ_O/dT) / (1 + beta_gamma). */
+            double b = p->beta_bar != 0.0 ? beta_of(p, AT(gamma, i, j)) : 0.0;
+            double dJdT = p->kappa_T + p->kappa_Q * b;
+            m[6] = (m[6] + 3.0 * (p->gb_x * m[1] + p->gb_y * m[2]) - dJdT) / (1.0 + b);
+        }
     }
     for (int q = 0; q < NADJ; ++q) out[q] = m[q];
 }
@@ -730,6 +769,12 @@ void orc_sensitivity_parts(const orc_problem *p, const double *gamma, const doub
             double uu = AT(u, i, j), vv = AT(v, i, j);
             double s = 0.0;
             if (parts & 1) s += da * (uu * uu + vv * vv) + 3.0 * da * (uu * AT(a[1], i, j) + vv * AT(a[2], i, j));
+            if (p->thermal && p->beta_bar != 0.0 && (parts & 1)) {
+                /* heat source and heat-exchange objective, paired with the level whose
+                 * T they enter: -dQ/dgamma T~ - kappa_Q beta' (1 - T) */
+                double db = dbeta_of(p, gm), Tv = AT(T, i, j);
+                s += -db * (1.0 - Tv) * AT(a[6], i, j) - p->kappa_Q * db * (1.0 - Tv);
+            }
             if (p->thermal && (parts & 2))
                 s -= dB_of(p, gm) * (ddx(p, T, i, j) * AT(a[7], i, j) + ddy(p, T, i, j) * AT(a[8], i, j));
             AT(sens, i, j) += s;

@@ -47,6 +47,8 @@ class OrcProblem(C.Structure):
         ("kappa_p", C.c_double),
         ("periodic", C.c_int),
         ("G_x", C.c_double), ("G_y", C.c_double),
+        ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
+        ("gb_x", C.c_double), ("gb_y", C.c_double), ("T_ref", C.c_double),
     ]
 
 
@@ -164,8 +166,9 @@ def make_problem(pb) -> OrcProblem:
     for name, _ in OrcProblem._fields_:
         if name in ("t_kind", "t_val"):
             continue
-        if name in ("periodic", "G_x", "G_y") and not hasattr(pb, name):
-            continue  # channel problems: no periodic axis, no external force
+        if not hasattr(pb, name) and name in ("periodic", "G_x", "G_y", "beta_bar", "q_beta", "kappa_Q", "gb_x",
+                                              "gb_y", "T_ref"):
+            continue  # fields a problem description may leave out: zero
         val = pb.resolved(name) if hasattr(pb, "resolved") else getattr(pb, name)
         setattr(s, name, type(getattr(s, name))(val))
     for e in range(4):

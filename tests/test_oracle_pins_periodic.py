@@ -253,3 +253,82 @@ def test_periodic_conservation_of_mass_and_momentum():
     n = st.u.size
     assert abs(s1.u.sum() - (st.u.sum() + n * pb2.G_x) / (1 + a)) <= 1e-14
     assert abs(s1.v.sum() - (st.v.sum() + n * pb2.G_y) / (1 + a)) <= 1e-14
+
+
+# --------------------------------------------------------------------------------------
+# Heat source (Eqs. heatsource, betagamma) and Boussinesq force (Eq. boussinesqforce)
+# --------------------------------------------------------------------------------------
+def beta_paper(beta_bar, q, g):
+    """Eq. (betagamma): beta_gamma = beta_bar q (1 - gamma) / (q + gamma)."""
+    return beta_bar * q * (1.0 - g) / (q + g)
+
+
+@pytest.mark.parametrize("g0", [0.0, 0.4])
+def test_heat_source_relaxation_closed_form(g0):
+    """Fluid at rest with uniform T on a periodic box: the thermal step maps T to
+    (T + beta_gamma) / (1 + beta_gamma) (source Q = beta_gamma (1 - T) of Eq.
+    heatsource at t + dt, Eq. lbeg_ex), so T_n = 1 - (1 - T_0)(1 + beta)^-n: the
+    solid heats towards 1.  gamma = 0 gives beta = beta_bar for any q_beta."""
+    bb, q = 0.3, 0.1
+    pb = inputs.Problem(nx=6, ny=5, nu=0.1, alpha_bar=0.0, u_max=0.0, periodic=3, thermal=1, K_f=0.1, K_s=0.1,
+                        beta_bar=bb, q_beta=q)
+    g = np.full((pb.ny, pb.nx), g0)
+    b = beta_paper(bb, q, g0)
+    st = O.State(pb.ny, pb.nx)
+    st.T[:] = 0.2
+    done = 0
+    for n in (1, 3, 25):
+        st, _, _, _ = O.forward(pb, g, n - done, state=st)
+        done = n
+        assert np.abs(st.T - (1.0 - 0.8 * (1.0 + b) ** (-n))).max() <= 1e-14
+        assert np.abs(st.u).max() == 0.0
+
+
+def test_boussinesq_force_of_a_uniform_temperature():
+    """Uniform T != T_ref on a periodic box: G = g beta (T - T_ref) is uniform, so the
+    velocity follows the implicit Darcy march u_n = (G / alpha)(1 - (1 + alpha)^-n)
+    (Eq. lbef_ex with Eq. boussinesqforce); T stays uniform."""
+    pb = inputs.Problem(nx=6, ny=5, nu=0.1, alpha_bar=2.0, q_alpha=0.1, u_max=0.0, periodic=3, thermal=1,
+                        K_f=0.1, K_s=0.1, gb_x=2e-4, gb_y=-7e-4, T_ref=0.25)
+    g = np.full((pb.ny, pb.nx), 0.3)
+    a = alpha_paper(2.0, 0.1, 0.3)
+    st = O.State(pb.ny, pb.nx)
+    st.T[:] = 0.75
+    st, _, _, _ = O.forward(pb, g, 9, state=st)
+    for comp, gb in (("u", pb.gb_x), ("v", pb.gb_y)):
+        G = gb * (0.75 - 0.25)
+        assert np.abs(getattr(st, comp) - G / a * (1 - (1 + a) ** -9)).max() <= 1e-15 * 9 + 1e-13 * abs(G / a)
+    assert np.abs(st.T - 0.75).max() <= 1e-14
+
+
+def test_one_step_gradient_with_heat_source_and_boussinesq_is_exact():
+    """Unsteady thermal problem of one step, J = J_O(state(1)) with the dissipation,
+    kappa_T sum T and the heat-exchange objective -kappa_Q sum beta_gamma (1 - T)
+    (Eq. objective_heatexchanger), a heat source and a Boussinesq force: the ALKS
+    level-1 adjoint (T~ with the implicit source division and the 3 g beta . u~
+    coupling of Eq. albeg_ex) and the sensitivity terms 3 alpha' u.u~,
+    -beta' (1 - T) T~ and -kappa_Q beta' (1 - T) give the exact derivative, compared
+    with central differences.  K_s = K_f, so the B-term (level 0) is absent."""
+    pb = inputs.Problem(nx=12, ny=10, nu=0.2, alpha_bar=30.0, seed=4, sigma=1.5, strip=1, steady=False, n_steps=1,
+                        thermal=1, K_f=0.1, K_s=0.1, kappa_T=0.3, beta_bar=0.2, q_beta=0.1, kappa_Q=0.7,
+                        gb_x=0.01, gb_y=-0.02, T_ref=0.4, t_kind=[0, 1, 0, 1], t_val=[0.0, 0.0, 1.0, 0.0])
+    g = pb.gamma()
+    rng = np.random.default_rng(3)
+    st0 = O.State(pb.ny, pb.nx)
+    st0.u = 0.03 * rng.standard_normal(st0.u.shape)
+    st0.v = 0.03 * rng.standard_normal(st0.u.shape)
+    st0.rho = 1 + 0.01 * rng.standard_normal(st0.u.shape)
+    st0.T = rng.random(st0.u.shape)
+    _, _, tr, J = O.forward(pb, g, 1, state=st0, traj=True, accumulate_J=True)
+    adj, sens = O.unsteady_adjoint(pb, g, tr)
+    # J ~ 10 (the kappa_T sum T term), so the step is 1e-4: the central difference
+    # error then falls as eps^2 (3.6e-5 at 1e-3, 3.6e-7 at 1e-4) down to round-off
+    eps = 1e-4
+    for (j, i) in [(1, 1), (3, 4), (5, 7), (8, 10), (4, 2)]:
+        gp, gm = g.copy(), g.copy()
+        gp[j, i] += eps
+        gm[j, i] -= eps
+        Jp = O.forward(pb, gp, 1, state=st0, accumulate_J=True)[3]
+        Jm = O.forward(pb, gm, 1, state=st0, accumulate_J=True)[3]
+        fd = (Jp - Jm) / (2 * eps)
+        assert abs(fd - sens[j, i]) <= 1e-6 * abs(fd), (j, i, fd, sens[j, i])
