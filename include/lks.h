@@ -139,6 +139,21 @@ typedef struct {
                                  (checkpoint_every > 0): F32 (default) or BF16 / F16
                                  with the snapshots' per-field scaling              */
     int32_t reserved[4];      /* must be zero                                        */
+    /* Thermal source terms (thermal = 1; they run on the per-step kernels, so
+     * exec_path must be AUTO or STEP).  Heat source Q = beta_gamma (1 - T) of Eq.
+     * (heatsource) with beta_gamma = beta_bar q_beta (1 - gamma) / (q_beta + gamma)
+     * (Eq. betagamma), entering T once per step, implicitly:
+     * T = (T* + beta_gamma) / (1 + beta_gamma) on interior nodes; its adjoint divides
+     * T~ likewise and the sensitivity gains -beta' (1 - T) T~.  Heat-exchange
+     * objective (Eq. objective_heatexchanger): J_O gains -kappa_Q beta_gamma (1 - T)
+     * per interior node.  Boussinesq force G = g beta (T - T_ref) (Eq.
+     * boussinesqforce; gb = the products g_x beta, g_y beta) with T of the new level:
+     * u = (u* + G) / (1 + alpha_gamma); its adjoint adds 3 g beta . u~ to T~ (Eq.
+     * albeg_ex).  All zero: none. */
+    double beta_bar, q_beta;
+    double kappa_Q;
+    double gb[2];
+    double T_ref;
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in

@@ -347,6 +347,7 @@ int res_steps_for(lks_handle* h, bool adjoint, int cfg) {
 
 bool resident_wanted(lks_handle* h, bool adjoint) {
   if (h->d.exec_path == LKS_PATH_STEP || h->d.exec_path == LKS_PATH_COLUMN || !h->d.steady) return false;
+  if (lks_host::has_sources(h->d)) return false;  // the source terms are in the per-step kernels
   if (adjoint && h->d.thermal) return false;
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
@@ -521,6 +522,7 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
 // Warp-column kernels: asked for, or the lattice has at least four column tiles per
 // SM (below that the per-tile TMA kernels, with fewer edge tiles, are faster).
 bool use_col(lks_handle* h) {
+  if (lks_host::has_sources(h->d)) return false;  // the source terms are in the per-step kernels
   if (h->d.exec_path == LKS_PATH_COLUMN) return true;
   if (h->d.exec_path == LKS_PATH_STEP) return false;  // the per-tile kernels, as asked
   const long long tiles = (long long)((h->d.nx + C2_W - 1) / C2_W) * ((h->d.ny + Col2Geo<C2_R>::H - 1) / Col2Geo<C2_R>::H);
@@ -1112,14 +1114,15 @@ lks_status sensitivity_impl(lks_handle* h, void* out) {
     const R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
     const R* ux = adj_ptr<R>(h, h->acur, 1);
     const R* uy = adj_ptr<R>(h, h->acur, 2);
+    const R* Tt = d.thermal ? adj_ptr<R>(h, h->acur, 6) : nullptr;
     const R* qx = d.thermal ? adj_ptr<R>(h, h->acur, 7) : nullptr;
     const R* qy = d.thermal ? adj_ptr<R>(h, h->acur, 8) : nullptr;
     const R* gam = fld<R>(h, L.gamma, 0);
     if (d.thermal)
-      sensitivity_kernel<R, true><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, qx, qy, gam, g, c,
+      sensitivity_kernel<R, true><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, Tt, qx, qy, gam, g, c,
                                                                             reinterpret_cast<R*>(out));
     else
-      sensitivity_kernel<R, false><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, qx, qy, gam, g, c,
+      sensitivity_kernel<R, false><<<L.obj_blocks, NTHREADS, 0, h->stream>>>(u, v, T, ux, uy, Tt, qx, qy, gam, g, c,
                                                                              reinterpret_cast<R*>(out));
   } else {
     copy_shift_kernel<double, R><<<elementwise_grid(L.N), 256, 0, h->stream>>>(

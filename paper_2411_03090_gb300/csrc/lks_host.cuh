@@ -40,6 +40,11 @@ inline int device_sm_count() {
 // multiprocessor (the kernels loop over the rest).
 inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255) / 256, (size_t)device_sm_count() * 8); }
 
+// Any of the thermal source terms (heat source, heat-exchange objective, Boussinesq).
+inline bool has_sources(const lks_problem_desc& d) {
+  return d.beta_bar != 0.0 || d.kappa_Q != 0.0 || d.gb[0] != 0.0 || d.gb[1] != 0.0;
+}
+
 inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   auto bad = [&](const char* m) {
     if (why) *why = m;
@@ -55,7 +60,7 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (d->real_type != LKS_REAL_F32 && d->real_type != LKS_REAL_F64) return bad("real_type must be F32 or F64");
     if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
     if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
-    if (!d->steady || d->thermal) return bad("D3Q19: steady, non-thermal problems only");
+    if (!d->steady || d->thermal || has_sources(*d)) return bad("D3Q19: steady, non-thermal problems only");
     if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
     if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
     if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
@@ -90,6 +95,15 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->tol > 0.0) {
     if (!d->steady) return bad("tol > 0: steady problems only");
     if (d->max_steps < d->n_steps || d->max_steps < d->n_adj) return bad("tol > 0: max_steps >= n_steps, n_adj");
+  }
+  if (has_sources(*d)) {
+    if (!d->thermal) return bad("heat source, heat-exchange objective and Boussinesq force need thermal = 1");
+    if (d->exec_path == LKS_PATH_RESIDENT || d->exec_path == LKS_PATH_COLUMN)
+      return bad("thermal source terms run on the per-step kernels (exec_path AUTO or STEP)");
+    if (d->beta_bar != 0.0 && !(d->q_beta > 0.0)) return bad("q_beta must be > 0");
+    if (!std::isfinite(d->beta_bar) || !std::isfinite(d->kappa_Q) || !std::isfinite(d->gb[0]) ||
+        !std::isfinite(d->gb[1]) || !std::isfinite(d->T_ref) || d->beta_bar < 0.0)
+      return bad("thermal source parameters must be finite, beta_bar >= 0");
   }
   if (d->warm_start != 0 && d->warm_start != 1) return bad("warm_start must be 0 or 1");
   if (d->warm_start && !d->steady) return bad("warm_start: steady problems only");
@@ -227,6 +241,12 @@ inline Coef<R> make_coef(const lks_problem_desc& d) {
   c.q_K = (R)d.q_K;
   c.kappa_T = (R)d.kappa_T;
   c.kappa_p = (R)d.kappa_p;
+  c.beta_bar = (R)d.beta_bar;
+  c.q_beta = (R)d.q_beta;
+  c.kappa_Q = (R)d.kappa_Q;
+  c.gb_x = (R)d.gb[0];
+  c.gb_y = (R)d.gb[1];
+  c.T_ref = (R)d.T_ref;
   for (int e = 0; e < 4; ++e) c.t_val[e] = (R)d.t_val[e];
   return c;
 }

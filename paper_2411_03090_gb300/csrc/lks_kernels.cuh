@@ -71,6 +71,9 @@ struct Coef {
   R kappa_T;
   R t_val[4];
   R kappa_p;    // weight of the static pressure drop J_p in J (steady problems)
+  R beta_bar, q_beta;  // heat source Q = beta_gamma (1 - T) (Eqs. heatsource, betagamma); 0: none
+  R kappa_Q;           // weight of the heat-exchange objective -sum beta_gamma (1 - T)
+  R gb_x, gb_y, T_ref; // Boussinesq force G = g beta (T - T_ref) (Eq. boussinesqforce)
 };
 
 // Edge maps of one lattice: 9 classes x 6 moments x 10 columns (lks_edge_moment_map),
@@ -129,6 +132,63 @@ __device__ __forceinline__ R dalpha_of(const Coef<R>& c, R gm) {
   return -c.alpha_bar * c.q_alpha * (R(1) + c.q_alpha) / (d * d);
 }
 // Conductivity interpolation, Eq. (conductivity), mapped to B by Eq. (B).
+// Eq. (betagamma) and its derivative.
+template <typename R>
+__device__ __forceinline__ R beta_of(const Coef<R>& c, R gm) {
+  return c.beta_bar * c.q_beta * (R(1) - gm) / (c.q_beta + gm);
+}
+template <typename R>
+__device__ __forceinline__ R dbeta_of(const Coef<R>& c, R gm) {
+  const R d = c.q_beta + gm;
+  return -c.beta_bar * c.q_beta * (R(1) + c.q_beta) / (d * d);
+}
+
+// Heat source and Boussinesq force at an interior node of the forward step: the new
+// T* becomes (T* + beta_gamma) / (1 + beta_gamma) (Q = beta_gamma (1 - T) at t + dt,
+// taken implicitly), and u = u* inv gains inv g beta (T - T_ref) with that new T
+// (Eq. lbef_ex with Eq. boussinesqforce; inv = 1 / (1 + alpha_gamma)).
+template <typename R>
+__device__ __forceinline__ void thermal_sources(const Coef<R>& c, R gm, R inv, R& T, R& u, R& v) {
+  if (c.beta_bar != R(0)) {
+    const R b = beta_of(c, gm);
+    T = (T + b) / (R(1) + b);
+  }
+  if (c.gb_x != R(0) || c.gb_y != R(0)) {
+    const R dT = T - c.T_ref;
+    u += inv * (c.gb_x * dT);
+    v += inv * (c.gb_y * dT);
+  }
+}
+__device__ __forceinline__ bool has_thermal_sources(const Coef<float>& c) {
+  return c.beta_bar != 0.f || c.gb_x != 0.f || c.gb_y != 0.f || c.kappa_Q != 0.f;
+}
+template <typename R>
+__device__ __forceinline__ bool has_thermal_sources(const Coef<R>& c) {
+  return c.beta_bar != R(0) || c.gb_x != R(0) || c.gb_y != R(0) || c.kappa_Q != R(0);
+}
+
+// T~ of an interior node (Eq. albeg_ex) with the heat source and the Boussinesq
+// coupling: (T~* + 3 g beta . u~ - dJ_O/dT) / (1 + beta_gamma) with
+// dJ_O/dT = kappa_T + kappa_Q beta_gamma; u~ is the node's adjoint velocity of the
+// same level, after its Brinkman division.
+template <typename R>
+__device__ __forceinline__ R adj_thermal_T(const Coef<R>& c, R gm, R Tstar, R ux, R uy) {
+  const R b = c.beta_bar != R(0) ? beta_of(c, gm) : R(0);
+  return (Tstar + R(3) * (c.gb_x * ux + c.gb_y * uy) - (c.kappa_T + c.kappa_Q * b)) / (R(1) + b);
+}
+
+// Heat-exchange objective at an interior node, -kappa_Q beta_gamma (1 - T)
+// (Eq. objective_heatexchanger), and its sensitivity terms with the heat source:
+// -beta' (1 - T) (T~ + kappa_Q).
+template <typename R>
+__device__ __forceinline__ R heat_objective(const Coef<R>& c, R gm, R T) {
+  return c.kappa_Q != R(0) ? -c.kappa_Q * beta_of(c, gm) * (R(1) - T) : R(0);
+}
+template <typename R>
+__device__ __forceinline__ R heat_sensitivity(const Coef<R>& c, R gm, R T, R Tt) {
+  return c.beta_bar != R(0) ? -dbeta_of(c, gm) * (R(1) - T) * (Tt + c.kappa_Q) : R(0);
+}
+
 template <typename R>
 __device__ __forceinline__ R B_of(const Coef<R>& c, R gm) {
   const R K = c.K_f + (c.K_s - c.K_f) * c.q_K * (R(1) - gm) / (c.q_K + gm);
@@ -317,10 +377,11 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
         i < nx - 1 && j < ny - 1) {
       // central differences at interior nodes (objective J_O)
       const R cSxx = R(2) * dudx, cSyy = R(2) * dvdy, cSxy = dudy + dvdx;
-      const R al = alpha_of(c, __ldg(a.gamma + (size_t)j * nx + i));
+      const R gmo = __ldg(a.gamma + (size_t)j * nx + i);
+      const R al = alpha_of(c, gmo);
       jloc += (double)(R(0.5) * c.nu * (cSxx * cSxx + R(2) * cSxy * cSxy + cSyy * cSyy) +
                        al * (uu * uu + vv * vv));
-      if (TH) jloc += (double)(c.kappa_T * sT[sy * H2X + sx]);
+      if (TH) jloc += (double)(c.kappa_T * sT[sy * H2X + sx] + heat_objective(c, gmo, sT[sy * H2X + sx]));
     }
   }
   __syncthreads();
@@ -371,6 +432,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
         Ts += ((ct0[SW] - Tx) + ctx[SW] + cty[SW] + (ct0[SE] - Tx) - ctx[SE] + cty[SE] +
                (ct0[NE] - Tx) - ctx[NE] - cty[NE] + (ct0[NW] - Tx) + ctx[NW] - cty[NW]) * (R(1) / R(36));
         Tn = Tx + Ts;
+        if (has_thermal_sources(c)) thermal_sources(c, __ldg(a.gamma + (size_t)j * nx + i), inv, Tn, un, vn);
       }
     } else {
       // Edge node: the nine streamed populations, split by c.n.
@@ -702,11 +764,13 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
       const R inv = R(1) / (R(1) + al);
       m[1] = (m[1] - ju * (R(1) / R(3)) + cpx) * inv;
       m[2] = (m[2] - jv * (R(1) / R(3)) + cpy) * inv;
+      if (TH && has_thermal_sources(c)) m[6] = adj_thermal_T(c, gm, m[6] + c.kappa_T, m[1], m[2]);
       if (a.sens) {
         R s = R(0);
         if (a.sens_flow) {
           const R da = dalpha_of(c, gm);
           s += da * (uu0 * uu0 + vv0 * vv0) + R(3) * da * (uu0 * m[1] + vv0 * m[2]);
+          if (TH) s += heat_sensitivity(c, gm, sT0[s2], m[6]);
         }
         if (TH && a.sens_thermal) {
           const R dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * R(0.5);
@@ -799,7 +863,7 @@ __global__ void __launch_bounds__(NTHREADS) objective_kernel(const R* __restrict
     const R al = alpha_of(c, gamma[o]);
     acc += (double)(R(0.5) * c.nu * (Sxx * Sxx + R(2) * Sxy * Sxy + Syy * Syy) +
                     al * (u[o] * u[o] + v[o] * v[o]));
-    if (TH) acc += (double)(c.kappa_T * T[o]);
+    if (TH) acc += (double)(c.kappa_T * T[o] + heat_objective(c, gamma[o], T[o]));
   }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -840,6 +904,7 @@ __global__ void __launch_bounds__(NTHREADS) sensitivity_kernel(const R* __restri
                                                                const R* __restrict__ T,
                                                                const R* __restrict__ ux_t,
                                                                const R* __restrict__ uy_t,
+                                                               const R* __restrict__ T_t,
                                                                const R* __restrict__ qx_t,
                                                                const R* __restrict__ qy_t,
                                                                const R* __restrict__ gamma, Geom g,
@@ -857,6 +922,7 @@ __global__ void __launch_bounds__(NTHREADS) sensitivity_kernel(const R* __restri
       if (TH) {
         const R dTx = (T[o + 1] - T[o - 1]) * R(0.5), dTy = (T[o + nx] - T[o - nx]) * R(0.5);
         s -= dB_of(c, gm) * (dTx * qx_t[o] + dTy * qy_t[o]);
+        s += heat_sensitivity(c, gm, T[o], T_t[o]);
       }
     }
     out[o] = s;

@@ -511,6 +511,8 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
             (!EDGE || (i > 0 && j > 0 && i < nx - 1 && j < ny - 1))) {
           jloc += (double)jo_flow<BW>(su, sv, s2, c.nu, sbi[s2], uu, vv);
           if (TH) jloc += (double)__fmul_rn(c.kappa_T, sT[s2]);
+          if constexpr (TH && !BATCH)
+            if (c.kappa_Q != 0.f) jloc += (double)heat_objective(c, __ldg(a.gamma + (size_t)j * nx + i), sT[s2]);
         }
       }
     };
@@ -541,6 +543,8 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
 #pragma unroll
             for (int k = 1; k < 9; ++k) gk[k] = Gp[k * A1 + q1 - cxk(k) - cyk(k) * LX1];
             Tn = tgather8(sT[s2], gk);
+            if constexpr (!BATCH)
+              if (has_thermal_sources(c)) thermal_sources(c, __ldg(a.gamma + (size_t)j * nx + i), sbi[s2], Tn, un, vn);
           }
         } else {
           float s0 = 0.f, sp = 0.f, g0 = 0.f, gp = 0.f;
@@ -849,9 +853,16 @@ __global__ void __launch_bounds__(NT) adj_tma_kernel(const __grid_constant__ Tma
           const float inv = sbi[s2];
           m[1] = adj_brinkman(m[1], ju, cpx, inv);
           m[2] = adj_brinkman(m[2], jv, cpy, inv);
+          if constexpr (TH && !BATCH)
+            if (has_thermal_sources(c)) {
+              if (!a.sens) gm = __ldg(a.gamma + gi);
+              m[6] = adj_thermal_T(c, gm, m[6] + c.kappa_T, m[1], m[2]);
+            }
           if (a.sens) {
             float sacc = 0.f;
             if (a.sens_flow) sacc = __fadd_rn(sacc, sens_flow_term(c, gm, uu0, vv0, m[1], m[2]));
+            if constexpr (TH && !BATCH)
+              if (a.sens_flow) sacc += heat_sensitivity(c, gm, sT0[s2], m[6]);
             if (TH && a.sens_thermal) {
               const float dTx = (sT0[s2 + 1] - sT0[s2 - 1]) * 0.5f;
               const float dTy = (sT0[s2 + BW] - sT0[s2 - BW]) * 0.5f;

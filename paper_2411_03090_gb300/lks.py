@@ -57,6 +57,8 @@ class Desc(C.Structure):
         ("tol", C.c_double), ("max_steps", C.c_int32),
         ("warm_start", C.c_int32), ("segment_type", C.c_int32),
         ("reserved", C.c_int32 * 4),
+        ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
+        ("gb", C.c_double * 2), ("T_ref", C.c_double),
     ]
 
 
@@ -177,6 +179,10 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
         return d
     if getattr(pb, "periodic", 0) or getattr(pb, "G_x", 0.0) or getattr(pb, "G_y", 0.0):
         raise ValueError("periodic lattices and an external force are not part of the CUDA path")
+    for name in ("beta_bar", "q_beta", "kappa_Q", "T_ref"):
+        if hasattr(pb, name):
+            setattr(d, name, float(getattr(pb, name)))
+    d.gb[0], d.gb[1] = float(getattr(pb, "gb_x", 0.0)), float(getattr(pb, "gb_y", 0.0))
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T", "kappa_p"):
         setattr(d, name, float(getattr(pb, name)))

@@ -493,6 +493,48 @@ def test_pressure_drop_verification_of_the_paper_on_the_gpu():
         assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
 
 
+def thermal_sources_case(steady, nx, **kw):
+    """Thermal channel with a heat source Q = beta_gamma (1 - T) (beta_bar = 0.05), the
+    heat-exchange objective (kappa_Q = 0.5) and a Boussinesq force (g beta = (0,
+    -2e-3), T_ref = 0.5): a heated bottom wall drives buoyancy."""
+    base = dict(beta_bar=0.05, q_beta=0.1, kappa_Q=0.5, gb_x=0.0, gb_y=-2e-3, T_ref=0.5)
+    base.update(kw)
+    return thermal_small(steady, nx=nx, **base)
+
+
+@pytest.mark.parametrize("steady", [True, False])
+@pytest.mark.parametrize("real,nx,jtol,gtol", [("f64", 70, 1e-11, 1e-10), ("f32", 136, 1e-5, 1e-3)])
+def test_heat_source_and_boussinesq_match_oracle(steady, real, nx, jtol, gtol):
+    """Heat source (Eqs. heatsource, betagamma), heat-exchange objective (Eq.
+    objective_heatexchanger) and Boussinesq force (Eq. boussinesqforce) on the
+    per-step kernels (plain FP64, TMA-staged FP32): J, the nine adjoint fields and
+    dJ/dgamma against the oracle, steady and unsteady."""
+    pb = thermal_sources_case(steady, nx)
+    g = pb.gamma()
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.device_status == 0 and q.fwd_path == 1 and q.adj_path == 1
+    ref = O.steady_gradient(pb, g) if steady else O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= jtol * abs(ref["J"])
+    if steady:
+        adj = [a.double().cpu().numpy() for a in s.get_adjoint()]
+        for k in range(9):
+            assert rel_l2(adj[k], ref["adjoint"][k]) <= gtol, k
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= gtol
+    # the source terms matter: without them the gradient differs by far more than gtol
+    plain = O.steady_gradient(pb.with_(beta_bar=0.0, kappa_Q=0.0, gb_y=0.0), g) if steady else \
+        O.unsteady_gradient(pb.with_(beta_bar=0.0, kappa_Q=0.0, gb_y=0.0), g)
+    assert rel_l2(plain["dJdgamma"], ref["dJdgamma"]) > 100 * gtol
+
+
+def test_thermal_sources_reject_the_resident_and_column_paths():
+    pb = thermal_sources_case(True, 136)
+    for path in ("resident", "column"):
+        with pytest.raises(LKSError):
+            LKS(pb, real="f32", path=path)
+
+
 def test_gradient_host_matches_device():
     pb = small()
     g = pb.gamma()
