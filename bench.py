@@ -276,7 +276,7 @@ def run_checkpoint_study(args):
     del plain
     torch.cuda.empty_cache()
     norm = torch.linalg.vector_norm(g_plain).item()
-    for K in (100, 500, 2000):
+    for K in (16, 100, 500, 2000):
         for snap in ("f32", "bf16", "f16"):
             s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap, device=dev)
             t, J, g = timed(s, reps)
@@ -287,6 +287,27 @@ def run_checkpoint_study(args):
             torch.cuda.empty_cache()
     clk = clocks.stop()
     head = [r for r in rows if r["K"] == 100 and r["snapshot"] == "bf16"][0]
+
+    # Gradient error against the FP64 oracle on a truncated horizon (the oracle keeps
+    # every level in host memory): the first `oracle_levels` steps of the same problem.
+    vs_oracle = []
+    if args.oracle_levels > 0:
+        from oracle import oracle as O
+        pt = pb.with_(n_steps=args.oracle_levels, n_adj=args.oracle_levels)
+        g64 = pt.gamma()
+        t0 = time.perf_counter()
+        ref = O.unsteady_gradient(pt, g64)
+        t_or = time.perf_counter() - t0
+        rnorm = float(np.linalg.norm(ref["dJdgamma"]))
+        for K, snap in ((0, "-"), (20, "f32"), (20, "bf16"), (20, "f16"), (100, "bf16"), (100, "f16")):
+            s = LKS(pt, real="f32", checkpoint_every=K, snapshot=snap if K else "f32", device=dev)
+            J, gg = s.gradient(gamma)
+            err = float(np.linalg.norm(gg.double().cpu().numpy() - ref["dJdgamma"])) / rnorm
+            vs_oracle.append({"K": K, "snapshot": snap, "grad_rel_err_vs_oracle": err,
+                              "J_rel_err_vs_oracle": abs(J.item() - ref["J"]) / abs(ref["J"])})
+            del s
+            torch.cuda.empty_cache()
+        vs_oracle.append({"oracle_levels": args.oracle_levels, "oracle_seconds": t_or})
     print(json.dumps({
         "metric": METRIC, "value": N * 2 * pb.n_steps / head["s_per_gradient"] / 1e6, "unit": "MLUPS",
         "n_gpus": 1, "steps": reps, "warmup": 1, "ms_per_step": head["s_per_gradient"] * 1e3,
@@ -296,9 +317,63 @@ def run_checkpoint_study(args):
                    "updates_counted": "forward + adjoint levels (recomputation not counted)",
                    "l2": "flushed before each timed gradient"},
         "checkpoint_study": rows,
+        "vs_oracle_truncated_horizon": vs_oracle,
         "speedup_vs_plain": t_plain / head["s_per_gradient"],
         "memory_ratio_vs_plain": head["workspace_GB"] / (ws_plain / 1e9),
         "clocks": clk}))
+
+
+def run_fd_study(args):
+    """Config2's gradient check: the FP64 instance on the 512x256 channel (Re = 100),
+    both marches run to a relative step change of 1e-14 (tolerance marches), then
+    central differences of J with step 1e-4 (Eq. sensfdm) on 32 design nodes drawn
+    with seed 22 from the nodes at least 3 from an edge and 5 from the inlet and
+    outlet strips, each perturbed march warm-started from the converged state.
+    Reports the cosine between the ALKS gradient and the differences and the
+    per-node ratios (Sec. 2.6 made numeric)."""
+    import torch
+    from paper_2411_03090_gb300 import LKS
+
+    pb = inputs.config2().with_(n_steps=2000, n_adj=2000)
+    dev = torch.device("cuda", 0)
+    g = pb.gamma()
+    gt = torch.from_numpy(g).to(dev)
+    tol, cap = 1e-14, args.fd_max_steps
+    t0 = time.perf_counter()
+    s = LKS(pb, real="f64", device=dev, tol=tol, max_steps=cap, warm_start=True)
+    J0, grad = s.gradient(gt)
+    q = s.query()
+    base_steps, adj_steps = q.forward_steps, q.adjoint_steps
+    grad = grad.cpu().numpy()
+    base = [x.clone() for x in s.get_state()]
+    rng = np.random.default_rng(22)
+    cand = [(j, i) for j in range(3, pb.ny - 3) for i in range(pb.strip + 5, pb.nx - pb.strip - 5)]
+    nodes = [cand[k] for k in rng.choice(len(cand), 32, replace=False)]
+    eps = 1e-4
+    rows, steps = [], []
+    for (j, i) in nodes:
+        Js = []
+        for sg in (1.0, -1.0):
+            gp = g.copy()
+            gp[j, i] += sg * eps
+            s.set_state(gt, base[0], base[1], base[2])
+            before = s.query().forward_steps
+            Js.append(s.lks_forward(torch.from_numpy(gp).to(dev)).item())
+            steps.append(s.query().forward_steps - before)
+        fd = (Js[0] - Js[1]) / (2 * eps)
+        rows.append({"node": [int(i), int(j)], "alks": float(grad[j, i]), "fd": fd,
+                     "ratio": float(grad[j, i] / fd) if fd != 0 else None})
+    a = np.array([r["alks"] for r in rows])
+    b = np.array([r["fd"] for r in rows])
+    ratios = np.array([r["ratio"] for r in rows if r["ratio"] is not None])
+    print(json.dumps({
+        "study": "config2 gradient vs central differences (FP64 GPU instance)",
+        "lattice": f"{pb.nx}x{pb.ny}", "eps": eps, "tol": tol, "forward_steps_base": int(base_steps),
+        "adjoint_steps": int(adj_steps), "perturbed_steps_median": float(np.median(steps)),
+        "cosine": float(a @ b / np.linalg.norm(a) / np.linalg.norm(b)),
+        "rel_l2_alks_vs_fd": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
+        "ratio_median": float(np.median(ratios)), "ratio_p10": float(np.percentile(ratios, 10)),
+        "ratio_p90": float(np.percentile(ratios, 90)), "seconds": time.perf_counter() - t0, "nodes": rows}))
 
 
 def run_batch_study(args):
@@ -439,6 +514,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--workload", default="config4")
+    ap.add_argument("--oracle-levels", type=int, default=200,
+                    help="config3: levels of the truncated horizon compared with the FP64 oracle (0: none)")
+    ap.add_argument("--fd-max-steps", type=int, default=1500000,
+                    help="config2fd: step limit of each tolerance march")
     ap.add_argument("--no-also", action="store_true",
                     help="config4: skip the config2 and 8192^2 figures carried on the same line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -464,6 +543,9 @@ def main():
         return
     if args.workload == "config5":
         run_batch_study(args)
+        return
+    if args.workload == "config2fd":
+        run_fd_study(args)
         return
 
     import torch

@@ -5,9 +5,9 @@ Small ducts cover ragged tiles in x and y (37 = 32 + 5, 44 = 32 + 12, 21 = 2 x 8
 nx % 4 == 0 runs the TMA-staged FP32 kernels, 37 the plain ones) and a
 z-march split over two chunks (nz = 40 = 32 + 8); the FP64 instance matches the
 oracle to rounding, the FP32 instance to the FP32 tolerances.  At config 4's full
-size (192^3) one forward step and one adjoint step are checked on sampled nodes
-(interior, faces, box edges, corners) against the oracle's node updates computed
-from the GPU's own previous level.
+size (192^3) three forward steps and two adjoint iterations are checked against
+the oracle's over the whole lattice and at sampled nodes (interior, faces, box
+edges, corners).
 """
 import numpy as np
 import pytest
@@ -154,43 +154,43 @@ def _sample_nodes(pb, rng, n_interior=40):
     return sorted(nodes)
 
 
-@pytest.mark.parametrize("path", ["auto", "step"])
-def test_config4_full_size_one_step_sampled(path):
-    """192^3, FP32: one forward step and one adjoint step at sampled nodes equal
-    the oracle's node updates from the GPU's previous level (FP32 tolerance), on
-    the warp-column kernels (auto) and on the plane-march kernels (step)."""
-    pb = inputs.config4().with_(n_steps=3, n_adj=1)
+@pytest.fixture(scope="module")
+def config4_oracle_short():
+    """The oracle's config-4 duct (192^3) after 3 forward steps from rest and 2 adjoint
+    iterations on that state (FP64; a few seconds on the host cores)."""
+    pb = inputs.config4().with_(n_steps=3, n_adj=2)
     g = pb.gamma()
-    gt = torch.from_numpy(g)
-    s2 = LKS(pb.with_(n_steps=2), real="f32", path=path)
-    s2.lks_forward(gt)
-    prev = to_state(s2.get_state())
-    del s2
+    st, _, _, _ = O.forward3(pb, g, 3)
+    adj, _, _ = O.steady_adjoint3(pb, g, st, 2)
+    return pb, g, st, adj
+
+
+@pytest.mark.parametrize("path", ["auto", "step"])
+def test_config4_full_size_short_marches(path, config4_oracle_short):
+    """192^3, FP32, on the warp-column kernels (auto) and the plane-march kernels
+    (step): three forward steps from rest and two adjoint iterations on that state
+    against the oracle's, over the whole lattice (relative L2) and at sampled faces,
+    box edges, corners and interior nodes (max error of a node against the field's
+    scale)."""
+    pb, g, st, adj = config4_oracle_short
     s = LKS(pb, real="f32", path=path)
-    s.lks_forward(gt)
-    assert s.query().fwd_path == (3 if path == "auto" else 1)
-    cur = [f.double().cpu().numpy() for f in s.get_state()]
-    rng = np.random.default_rng(4)
-    nodes = _sample_nodes(pb, rng)
-    g32 = g.astype(np.float32).astype(np.float64)
-    scale = max(np.abs(cur[1]).max(), 1e-30)
-    for (i, j, k) in nodes:
-        o = O.forward_node3(pb, g32, prev, i, j, k)
-        assert abs(cur[0][k, j, i] - (o[0] - 1.0)) <= 2e-6, (i, j, k)
-        for c in range(3):
-            assert abs(cur[1 + c][k, j, i] - o[1 + c]) <= 2e-5 * scale, (i, j, k, c)
-    # adjoint: level 1 from zero, then level 2 from level 1 on the frozen state
-    st = to_state([torch.from_numpy(x) for x in cur])
+    s.lks_forward(torch.from_numpy(g))
     s.alks_adjoint()
-    a1 = np.stack([a.double().cpu().numpy() for a in s.get_adjoint()])
-    s_b = LKS(pb.with_(n_adj=2), real="f32", path=path)
-    s_b.lks_forward(gt)
-    s_b.alks_adjoint()
-    assert s_b.query().adj_path == (3 if path == "auto" else 1)
-    a2 = np.stack([a.double().cpu().numpy() for a in s_b.get_adjoint()])
-    PV = O.adjoint_eq3(pb, st, a1)
-    ascale = np.abs(a2).reshape(O.NADJ3, -1).max(axis=1) + 1e-30
-    for (i, j, k) in nodes:
-        o = O.adjoint_node3(pb, g32, PV, st, i, j, k)
-        for q in range(O.NADJ3):
-            assert abs(a2[q, k, j, i] - o[q]) <= 2e-5 * ascale[q], (i, j, k, O.ADJ3_NAMES[q])
+    q = s.query()
+    assert q.fwd_path == (3 if path == "auto" else 1) and q.adj_path == q.fwd_path and q.device_status == 0
+    cur = [f.double().cpu().numpy() for f in s.get_state()]
+    ref = [st.rho - 1.0, st.u, st.v, st.w]
+    for c in range(4):
+        assert rel_l2(cur[c], ref[c]) <= 1e-5, c
+    a = np.stack([x.double().cpu().numpy() for x in s.get_adjoint()])
+    for k in range(O.NADJ3):
+        assert rel_l2(a[k], adj[k]) <= 1e-5, O.ADJ3_NAMES[k]
+    nodes = _sample_nodes(pb, np.random.default_rng(4))
+    scale = max(np.abs(ref[1]).max(), 1e-30)
+    ascale = np.abs(adj).reshape(O.NADJ3, -1).max(axis=1) + 1e-30
+    for (i, j, kz) in nodes:
+        assert abs(cur[0][kz, j, i] - ref[0][kz, j, i]) <= 2e-6, (i, j, kz)
+        for c in range(1, 4):
+            assert abs(cur[c][kz, j, i] - ref[c][kz, j, i]) <= 2e-5 * scale, (i, j, kz, c)
+        for k in range(O.NADJ3):
+            assert abs(a[k, kz, j, i] - adj[k, kz, j, i]) <= 2e-5 * ascale[k], (i, j, kz, O.ADJ3_NAMES[k])

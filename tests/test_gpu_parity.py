@@ -42,6 +42,26 @@ def oracle_state(st):
     return [st.rho - 1.0, st.u, st.v]
 
 
+def f32(a):
+    """An array rounded to FP32 and back: the oracle and the FP32 kernels then start
+    a step from exactly the same values."""
+    return np.asarray(a, dtype=np.float32).astype(np.float64)
+
+
+def oracle_developed_state(pb, g, n):
+    """The oracle's state after n steps from rest, rounded to FP32 (drho rounded as
+    stored, rho - 1)."""
+    st, _, _, _ = O.forward(pb, g, n)
+    r = O.State(pb.ny, pb.nx)
+    r.rho, r.u, r.v, r.T = 1.0 + f32(st.rho - 1.0), f32(st.u), f32(st.v), f32(st.T)
+    return r
+
+
+def set_gpu_state(s, g, st, t):
+    z = lambda a: torch.from_numpy(np.ascontiguousarray(a))  # noqa: E731
+    s.set_state(z(g), z(st.rho - 1.0), z(st.u), z(st.v), z(st.T), t=t)
+
+
 def gpu_state(s):
     d, u, v, T = [x.double().cpu().numpy() for x in s.get_state()]
     return [d, u, v], T
@@ -142,19 +162,17 @@ def test_poiseuille_on_gpu(nu):
 
 def test_single_step_full_size_config2():
     """512 x 256 (the benchmark lattice), FP32, launch configuration of the bench:
-    one step from a developed state equals the oracle's step from the same state."""
+    one step from a developed state (the oracle's, after 400 steps, rounded to FP32)
+    equals the oracle's step from the same state."""
     pb = inputs.config2()
     g = pb.gamma()
+    st = oracle_developed_state(pb, g, 400)
     s = LKS(pb, real="f32")
-    gt = torch.from_numpy(g)
-    s.set_state(gt, torch.zeros(pb.ny, pb.nx), torch.zeros(pb.ny, pb.nx), torch.zeros(pb.ny, pb.nx), t=0)
-    s.march(400)
-    (d0, u0, v0), _ = gpu_state(s)
+    set_gpu_state(s, g, st, 400)
+    d0 = st.rho - 1.0
     s.march(1)
     (d1, u1, v1), _ = gpu_state(s)
-    st = O.State(pb.ny, pb.nx)
-    st.rho, st.u, st.v = d0 + 1.0, u0, v0
-    ref = O.forward_step(pb, g.astype(np.float32).astype(np.float64), 401, st)
+    ref = O.forward_step(pb, f32(g), 401, st)
     for a, b, scale in ((d1, ref.rho - 1.0, np.abs(d0).max()), (u1, ref.u, pb.u_max),
                         (v1, ref.v, pb.u_max)):
         assert np.abs(a - b).max() <= 2e-6 * scale
@@ -198,26 +216,21 @@ def test_config1_full(real, ftol, jtol, gtol):
 
 
 def test_single_adjoint_step_full_size_config2():
-    """512 x 256, FP32: one ALKS step from developed adjoint fields equals the
-    oracle's step from the same fields."""
+    """512 x 256, FP32: one ALKS step from developed adjoint fields (the oracle's
+    state after 300 steps and adjoint after 200 iterations, rounded to FP32) equals
+    the oracle's step from the same fields."""
     pb = inputs.config2()
     g = pb.gamma()
-    gf = g.astype(np.float32).astype(np.float64)
+    gf = f32(g)
+    st = oracle_developed_state(pb, g, 300)
+    adj, _, _ = O.steady_adjoint(pb, gf, st, 200)
+    full = np.zeros((9, pb.ny, pb.nx))
+    full[:6] = f32(adj[:6])
     s = LKS(pb, real="f32")
-    gt = torch.from_numpy(g)
-    z = torch.zeros(pb.ny, pb.nx)
-    s.set_state(gt, z, z, z, t=0)
-    s.march(300)
-    s.set_adjoint([z] * 6)
-    s.adjoint_march(200)
-    a0 = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
+    set_gpu_state(s, g, st, 300)
+    s.set_adjoint([torch.from_numpy(np.ascontiguousarray(full[q])) for q in range(6)])
     s.adjoint_march(1)
     a1 = [a.double().cpu().numpy() for a in s.get_adjoint()[:6]]
-    (d, u, v), _ = gpu_state(s)
-    st = O.State(pb.ny, pb.nx)
-    st.rho, st.u, st.v = d + 1.0, u, v
-    full = np.zeros((9, pb.ny, pb.nx))
-    full[:6] = np.stack(a0)
     ref = O.adjoint_step(pb, gf, st, st, full)
     for q in range(6):
         scale = np.abs(ref[q]).max()
@@ -649,36 +662,33 @@ def test_thermal_forward_matches_oracle(real, tol, path):
 
 def test_single_steps_full_size_config3():
     """1024 x 512 thermal unsteady channel (config 3), FP32, the per-step TMA kernels
-    the benchmark runs: one forward step and one ALKS step from developed fields
-    equal the oracle's steps from the same fields (all nine adjoint fields)."""
+    the benchmark runs: one forward step from a developed state (the oracle's after
+    300 steps, rounded to FP32) and one ALKS step from seeded adjoint fields equal
+    the oracle's steps from the same fields (all nine adjoint fields)."""
     pb = inputs.config3()
     g = pb.gamma()
-    gf = g.astype(np.float32).astype(np.float64)
+    gf = f32(g)
+    st = oracle_developed_state(pb, g, 300)
     s = LKS(pb, real="f32")
-    gt = torch.from_numpy(g)
-    z = torch.zeros(pb.ny, pb.nx)
-    s.set_state(gt, z, z, z, z, t=0)
-    s.march(300)
-    (d0, u0, v0), T0 = gpu_state(s)
+    set_gpu_state(s, g, st, 300)
+    d0 = st.rho - 1.0
     s.march(1)
     assert s.query().fwd_path == 1 and s.query().device_status == 0
     (d1, u1, v1), T1 = gpu_state(s)
-    st = O.State(pb.ny, pb.nx)
-    st.rho, st.u, st.v, st.T = d0 + 1.0, u0, v0, T0
     ref = O.forward_step(pb, gf, 301, st)
     for a, b, scale in ((d1, ref.rho - 1.0, np.abs(d0).max()), (u1, ref.u, pb.u_max),
                         (v1, ref.v, pb.u_max), (T1, ref.T, 1.0)):
         assert np.abs(a - b).max() <= 2e-6 * scale
-    # ALKS step with the state frozen at level 301
+    # ALKS step with the state frozen at the oracle's level 301 (rounded to FP32)
+    st1 = O.State(pb.ny, pb.nx)
+    st1.rho, st1.u, st1.v, st1.T = 1.0 + f32(ref.rho - 1.0), f32(ref.u), f32(ref.v), f32(ref.T)
+    set_gpu_state(s, g, st1, 301)
     rng = np.random.default_rng(7)
-    s.set_adjoint([torch.from_numpy(1e-3 * rng.standard_normal((pb.ny, pb.nx))).float() for _ in range(9)])
-    s.adjoint_march(50)
-    a0 = [a.double().cpu().numpy() for a in s.get_adjoint()]
+    a0 = f32(1e-3 * rng.standard_normal((9, pb.ny, pb.nx)))
+    s.set_adjoint([torch.from_numpy(np.ascontiguousarray(a0[q])) for q in range(9)])
     s.adjoint_march(1)
     a1 = [a.double().cpu().numpy() for a in s.get_adjoint()]
-    st1 = O.State(pb.ny, pb.nx)
-    st1.rho, st1.u, st1.v, st1.T = d1 + 1.0, u1, v1, T1
-    ref_a = O.adjoint_step(pb, gf, st1, st1, np.stack(a0))
+    ref_a = O.adjoint_step(pb, gf, st1, st1, a0)
     for q in range(9):
         scale = np.abs(ref_a[q]).max()
         assert np.abs(a1[q] - ref_a[q]).max() <= 1e-5 * scale, q
