@@ -275,17 +275,19 @@ def run_checkpoint_study(args):
     del plain
     torch.cuda.empty_cache()
     norm = torch.linalg.vector_norm(g_plain).item()
-    for K in (16, 100, 500, 2000):
-        for snap in ("f32", "bf16", "f16"):
-            s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap, device=dev)
-            t, J, g = timed(s, reps)
-            err = torch.linalg.vector_norm(g - g_plain).item() / norm
-            rows.append({"form": "checkpointed", "K": K, "snapshot": snap, "s_per_gradient": t,
-                         "workspace_GB": s.workspace.numel() / 1e9, "grad_rel_err_vs_plain": err, "J": J})
-            del s
-            torch.cuda.empty_cache()
+    variants = [(K, snap, "f32") for K in (16, 100, 500, 2000) for snap in ("f32", "bf16", "f16")]
+    variants += [(0, "-", "bf16"), (2000, "bf16", "bf16"), (500, "bf16", "bf16")]  # 16-bit stored levels
+    for K, snap, seg in variants:
+        s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap if K else "f32", segment=seg, device=dev)
+        t, J, g = timed(s, reps)
+        err = torch.linalg.vector_norm(g - g_plain).item() / norm
+        rows.append({"form": "checkpointed" if K else "plain", "K": K, "snapshot": snap, "levels": seg,
+                     "s_per_gradient": t, "workspace_GB": s.workspace.numel() / 1e9,
+                     "grad_rel_err_vs_plain": err, "J": J})
+        del s
+        torch.cuda.empty_cache()
     clk = clocks.stop()
-    head = [r for r in rows if r["K"] == 100 and r["snapshot"] == "bf16"][0]
+    head = [r for r in rows if r["K"] == 100 and r["snapshot"] == "bf16" and r.get("levels", "f32") == "f32"][0]
 
     # Gradient error against the FP64 oracle on a truncated horizon (the oracle keeps
     # every level in host memory): the first `oracle_levels` steps of the same problem.
@@ -298,11 +300,13 @@ def run_checkpoint_study(args):
         ref = O.unsteady_gradient(pt, g64)
         t_or = time.perf_counter() - t0
         rnorm = float(np.linalg.norm(ref["dJdgamma"]))
-        for K, snap in ((0, "-"), (20, "f32"), (20, "bf16"), (20, "f16"), (100, "bf16"), (100, "f16")):
-            s = LKS(pt, real="f32", checkpoint_every=K, snapshot=snap if K else "f32", device=dev)
+        for K, snap, seg in ((0, "-", "f32"), (20, "f32", "f32"), (20, "bf16", "f32"), (20, "f16", "f32"),
+                             (100, "bf16", "f32"), (100, "f16", "f32"), (0, "-", "bf16"), (20, "bf16", "bf16"),
+                             (20, "f16", "f16")):
+            s = LKS(pt, real="f32", checkpoint_every=K, snapshot=snap if K else "f32", segment=seg, device=dev)
             J, gg = s.gradient(gamma)
             err = float(np.linalg.norm(gg.double().cpu().numpy() - ref["dJdgamma"])) / rnorm
-            vs_oracle.append({"K": K, "snapshot": snap, "grad_rel_err_vs_oracle": err,
+            vs_oracle.append({"K": K, "snapshot": snap, "levels": seg, "grad_rel_err_vs_oracle": err,
                               "J_rel_err_vs_oracle": abs(J.item() - ref["J"]) / abs(ref["J"])})
             del s
             torch.cuda.empty_cache()
@@ -324,7 +328,7 @@ def run_checkpoint_study(args):
 
 def run_fd_study(args):
     """Config2's gradient check: the FP64 instance on the 512x256 channel (Re = 100),
-    both marches run to a relative step change of 1e-14 (tolerance marches), then
+    both marches run to a small relative step change (tolerance marches), then
     central differences of J with step 1e-4 (Eq. sensfdm) on 32 design nodes drawn
     with seed 22 from the nodes at least 3 from an edge and 5 from the inlet and
     outlet strips, each perturbed march warm-started from the converged state.
@@ -337,14 +341,29 @@ def run_fd_study(args):
     dev = torch.device("cuda", 0)
     g = pb.gamma()
     gt = torch.from_numpy(g).to(dev)
-    tol, cap = 1e-14, args.fd_max_steps
+    tol, cap = args.fd_tol, args.fd_max_steps
     t0 = time.perf_counter()
+    from paper_2411_03090_gb300 import LKSError
     s = LKS(pb, real="f64", device=dev, tol=tol, max_steps=cap, warm_start=True)
-    J0, grad = s.gradient(gt)
+    converged = {}
+    for name, call in (("forward", lambda: s.lks_forward(gt)), ("adjoint", s.alks_adjoint)):
+        try:  # a march that stops at the step limit leaves its last state in place
+            call()
+            converged[name] = True
+        except LKSError as e:
+            if e.status != 5:
+                raise
+            converged[name] = False
+    grad = s.lks_sensitivity()
     q = s.query()
-    base_steps, adj_steps = q.forward_steps, q.adjoint_steps
+    base_steps, adj_steps, fchg, achg = q.forward_steps, q.adjoint_steps, q.fwd_change, q.adj_change
     grad = grad.cpu().numpy()
     base = [x.clone() for x in s.get_state()]
+    # Perturbed marches: a fixed number of steps from the converged base state, the
+    # same for +eps and -eps, so that whatever drift remains in the base state
+    # cancels in the central difference.
+    M = args.fd_steps
+    s = LKS(pb.with_(n_steps=M), real="f64", device=dev, warm_start=True)
     rng = np.random.default_rng(22)
     cand = [(j, i) for j in range(3, pb.ny - 3) for i in range(pb.strip + 5, pb.nx - pb.strip - 5)]
     nodes = [cand[k] for k in rng.choice(len(cand), 32, replace=False)]
@@ -356,9 +375,8 @@ def run_fd_study(args):
             gp = g.copy()
             gp[j, i] += sg * eps
             s.set_state(gt, base[0], base[1], base[2])
-            before = s.query().forward_steps
             Js.append(s.lks_forward(torch.from_numpy(gp).to(dev)).item())
-            steps.append(s.query().forward_steps - before)
+            steps.append(M)
         fd = (Js[0] - Js[1]) / (2 * eps)
         rows.append({"node": [int(i), int(j)], "alks": float(grad[j, i]), "fd": fd,
                      "ratio": float(grad[j, i] / fd) if fd != 0 else None})
@@ -368,7 +386,9 @@ def run_fd_study(args):
     print(json.dumps({
         "study": "config2 gradient vs central differences (FP64 GPU instance)",
         "lattice": f"{pb.nx}x{pb.ny}", "eps": eps, "tol": tol, "forward_steps_base": int(base_steps),
-        "adjoint_steps": int(adj_steps), "perturbed_steps_median": float(np.median(steps)),
+        "forward_change_base": fchg, "adjoint_steps": int(adj_steps), "adjoint_change": achg,
+        "converged": converged,
+        "perturbed_steps": M,
         "cosine": float(a @ b / np.linalg.norm(a) / np.linalg.norm(b)),
         "rel_l2_alks_vs_fd": float(np.linalg.norm(a - b) / np.linalg.norm(b)),
         "ratio_median": float(np.median(ratios)), "ratio_p10": float(np.percentile(ratios, 10)),
@@ -516,7 +536,11 @@ def main():
     ap.add_argument("--oracle-levels", type=int, default=200,
                     help="config3: levels of the truncated horizon compared with the FP64 oracle (0: none)")
     ap.add_argument("--fd-max-steps", type=int, default=1500000,
-                    help="config2fd: step limit of each tolerance march")
+                    help="config2fd: step limit of the base tolerance marches")
+    ap.add_argument("--fd-tol", type=float, default=1e-12,
+                    help="config2fd: relative step change the base marches run to")
+    ap.add_argument("--fd-steps", type=int, default=30000,
+                    help="config2fd: steps of each perturbed march from the converged base state")
     ap.add_argument("--no-also", action="store_true",
                     help="config4: skip the config2 and 8192^2 figures carried on the same line")
     ap.add_argument("--no-cpu-baseline", action="store_true")

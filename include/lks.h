@@ -94,7 +94,8 @@ typedef struct {
     double pulse_amp;
     double pulse_period;      /* <= 0: steady inlet u_max * pulse_mean               */
     int32_t in_y0, in_y1;     /* inlet span, inclusive                               */
-    int32_t out_y0, out_y1;   /* outlet span, inclusive, inside [1, ny-2]            */
+    int32_t out_y0, out_y1;   /* outlet span, inclusive, inside [1, ny-2];
+                                 out_y1 = out_y0 - 1: no outlet (closed right wall) */
     double rho_out;           /* outlet density, p_bar = rho_out / 3                 */
     int32_t thermal;          /* 1: thermal lattice for T (Eqs. T, geq2)             */
     int32_t steady;           /* 1: steady (adjoint iterated on the final state)     */
@@ -135,9 +136,12 @@ typedef struct {
                                  with no earlier state it starts from rest.  The
                                  usual start inside an optimisation loop, where the
                                  design changes little between calls              */
-    int32_t segment_type;     /* lks_snap_type of the recomputed segment trajectory
-                                 (checkpoint_every > 0): F32 (default) or BF16 / F16
-                                 with the snapshots' per-field scaling              */
+    int32_t segment_type;     /* unsteady FP32: lks_snap_type of the stored levels
+                                 of u, v[, T] that the adjoint reads -- the whole
+                                 trajectory (checkpoint_every = 0) or the recomputed
+                                 segment (checkpoint_every > 0).  F32 (default), or
+                                 BF16 / F16 (half the bytes: each forward step's
+                                 level is packed, each adjoint step's unpacked)     */
     int32_t reserved[4];      /* must be zero                                        */
     /* Thermal source terms (thermal = 1; they run on the per-step kernels, so
      * exec_path must be AUTO or STEP).  Heat source Q = beta_gamma (1 - T) of Eq.
@@ -154,6 +158,12 @@ typedef struct {
     double kappa_Q;
     double gb[2];
     double T_ref;
+    /* Heated segment of a heat-flux bottom edge (t_kind[2] = LKS_T_FLUX): the nodes
+     * heat_x0 <= i <= heat_x1 of the bottom edge carry the flux heat_q instead of
+     * t_val[2] (the paper's heat sink: a short heated part of an otherwise adiabatic
+     * wall).  heat_x1 < heat_x0: none. */
+    int32_t heat_x0, heat_x1;
+    double heat_q;
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in

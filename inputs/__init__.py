@@ -100,6 +100,9 @@ class Problem:
     gb_x: float = 0.0        # Boussinesq force G = g beta (T - T_ref): the products g_a beta
     gb_y: float = 0.0
     T_ref: float = 0.0
+    heat_x0: int = 0         # heated segment [heat_x0, heat_x1] of a heat-flux bottom edge
+    heat_x1: int = -1        # (-1: none)
+    heat_q: float = 0.0      # its heat flux
 
     def resolved(self, name: str):
         """Field value with negative span ends counted from the top edge (ny + v)."""
@@ -240,6 +243,39 @@ def config4() -> Problem3:
 def roofline2d(n: int = 8192) -> Problem:
     """Large 2-D steady channel used to load HBM (working set >> L2)."""
     return channel(n, n, Re=100.0 * (n - 1) / 255.0, seed=6, n_steps=200, n_adj=200)
+
+
+def natural_convection_cavity(scale: float = 0.5, Ra: float = 2e4, Pr: float = 0.71, nu: float = 0.06,
+                              q0: float = 1e-2, kappa_T: float = 1e-3, n_steps: int = 2000) -> tuple:
+    """The natural-convection sensitivity check of Sec. 2.6 (its verification of the
+    natural convection problem): a closed 140 x 80 (dx) cavity of walls, scaled by
+    `scale`; T = 0 prescribed on the left, right and top walls; the bottom wall
+    adiabatic except a heated centre part of 4 dx (heat flux q0); gravity along -y
+    with the Boussinesq force G = g beta (T - 0), g beta from Ra = g beta L^3 / (nu K_f)
+    with L the cavity height and Delta T = 1; K_s = 10 K_f.  The design domain is the
+    central 80 x 50, gamma = 0.1 in its central 40 x 25 and 0.9 elsewhere in it, and
+    gamma = 1 (fluid) outside.  The objective is kappa_T times the sum of T over the
+    interior nodes (the paper does not state the check's objective).
+    Returns (problem, gamma)."""
+    nx, ny = int(round(140 * scale)) + 1, int(round(80 * scale)) + 1
+    L = ny - 1
+    K_f = nu / Pr
+    gb = Ra * nu * K_f / L ** 3
+    cx = (nx - 1) // 2
+    hw = max(1, int(round(2 * scale)))
+    pb = Problem(nx=nx, ny=ny, nu=nu, alpha_bar=1e3 * nu, u_max=0.0, in_y0=0, in_y1=ny - 1, out_y0=1, out_y1=0,
+                 thermal=1, K_f=K_f, K_s=10.0 * K_f, t_kind=[T_FIXED, T_FIXED, T_FLUX, T_FIXED],
+                 t_val=[0.0, 0.0, 0.0, 0.0], heat_x0=cx - hw, heat_x1=cx + hw, heat_q=q0, gb_x=0.0, gb_y=-gb,
+                 T_ref=0.0, kappa_T=kappa_T, n_steps=n_steps, n_adj=n_steps)
+    g = np.ones((ny, nx))
+    y, x = np.mgrid[0:ny, 0:nx]
+    dx0, dx1 = int(round(30 * scale)), int(round(110 * scale))
+    dy0, dy1 = int(round(15 * scale)), int(round(65 * scale))
+    g[(x >= dx0) & (x <= dx1) & (y >= dy0) & (y <= dy1)] = 0.9
+    ix0, ix1 = int(round(50 * scale)), int(round(90 * scale))
+    iy0, iy1 = int(round(27.5 * scale)), int(round(52.5 * scale))
+    g[(x >= ix0) & (x <= ix1) & (y >= iy0) & (y <= iy1)] = 0.1
+    return pb, g
 
 
 def poiseuille(nx: int = 33, ny: int = 17, nu: float = 0.1, u_max: float = 0.02) -> Problem:

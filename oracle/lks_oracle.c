@@ -96,6 +96,8 @@ typedef struct {
     double gb_x, gb_y;         /* Boussinesq force G = g beta (T - T_ref),
                                   Eq. (boussinesqforce): the products g_a beta */
     double T_ref;
+    int heat_x0, heat_x1;      /* heated segment of a flux-type bottom edge     */
+    double heat_q;             /* its heat flux (replaces t_val[bottom] there)   */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -337,14 +339,17 @@ void orc_forward_node(const orc_problem *p, const double *gamma, double t, const
             int jn = (j == 0) ? 1 : ny - 2;
             TT = AT(T, i, jn);
         } else {
-            /* -q.n = q_bar with q = sum (c - u) g:  T (1 + u.n) = sum_0 g + 2 sum_+ g + q_bar */
+            /* -q.n = q_bar with q = sum (c - u) g:  T (1 + u.n) = sum_0 g + 2 sum_+ g + q_bar;
+             * q_bar = heat_q on the heated segment of the bottom edge */
             double s0 = 0.0, sp = 0.0;
             for (int k = 0; k < 9; ++k) {
                 int cn = CX[k] * n_x + CY[k] * n_y;
                 if (cn == 0) s0 += g[k];
                 else if (cn > 0) sp += g[k];
             }
-            TT = (s0 + 2.0 * sp + p->t_val[e]) / (1.0 + uu * n_x + vv * n_y);
+            double qb = p->t_val[e];
+            if (e == ORC_BOTTOM && i >= p->heat_x0 && i <= p->heat_x1) qb = p->heat_q;
+            TT = (s0 + 2.0 * sp + qb) / (1.0 + uu * n_x + vv * n_y);
         }
     }
     out[0] = r;

@@ -49,6 +49,7 @@ class OrcProblem(C.Structure):
         ("G_x", C.c_double), ("G_y", C.c_double),
         ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
         ("gb_x", C.c_double), ("gb_y", C.c_double), ("T_ref", C.c_double),
+        ("heat_x0", C.c_int), ("heat_x1", C.c_int), ("heat_q", C.c_double),
     ]
 
 
@@ -167,8 +168,11 @@ def make_problem(pb) -> OrcProblem:
         if name in ("t_kind", "t_val"):
             continue
         if not hasattr(pb, name) and name in ("periodic", "G_x", "G_y", "beta_bar", "q_beta", "kappa_Q", "gb_x",
-                                              "gb_y", "T_ref"):
+                                              "gb_y", "T_ref", "heat_x0", "heat_q"):
             continue  # fields a problem description may leave out: zero
+        if not hasattr(pb, name) and name == "heat_x1":
+            s.heat_x1 = -1  # no heated segment
+            continue
         val = pb.resolved(name) if hasattr(pb, "resolved") else getattr(pb, name)
         setattr(s, name, type(getattr(s, name))(val))
     for e in range(4):

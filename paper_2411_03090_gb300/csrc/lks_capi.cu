@@ -41,7 +41,8 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
   size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0, mat = 0, chg = 0;
-  size_t traj = 0, snaps = 0, scales = 0, seg = 0, total = 0;
+  size_t traj = 0, snaps = 0, scales = 0, seg = 0, lvl_stage = 0, total = 0;
+  int lvl16 = 0;  // trajectory / segment levels stored in 16 bits (segment_type BF16 / F16)
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
   int n_ckpt = 0, seg_levels = 0;
@@ -90,8 +91,13 @@ Layout make_layout(const lks_problem_desc* d) {
   if (!d->steady) {
     L.sens = take(fb);
     L.sens64 = take(sizeof(double) * L.N);
+    // 16-bit levels (FP32 lattices): the level store holds 2-byte values, and three
+    // FP32 levels stage what a forward step writes and what an adjoint step reads
+    L.lvl16 = d->segment_type != LKS_SNAP_F32 && d->real_type == LKS_REAL_F32;
+    const size_t lb = L.lvl16 ? L.N * 2 : fb;  // bytes of one field of one stored level
+    if (L.lvl16) L.lvl_stage = take(fb * L.nT * 3);
     if (d->checkpoint_every == 0) {
-      L.traj = take(fb * L.nT * ((size_t)d->n_steps + 1));
+      L.traj = take(lb * L.nT * ((size_t)d->n_steps + 1));
     } else {
       const int K = d->checkpoint_every;
       L.n_ckpt = (d->n_steps + K - 1) / K;
@@ -99,7 +105,7 @@ Layout make_layout(const lks_problem_desc* d) {
       L.snaps = take(L.snap_elem * L.N * L.nF * (size_t)L.n_ckpt);
       L.scales = take(sizeof(float) * 2 * L.nF * (size_t)L.n_ckpt);
       L.seg_levels = K + 2;
-      L.seg = take(fb * L.nT * (size_t)L.seg_levels);
+      L.seg = take(lb * L.nT * (size_t)L.seg_levels);
     }
   }
   L.total = off;
@@ -820,6 +826,94 @@ __global__ void decode_kernel(const S* __restrict__ y, R* __restrict__ x, size_t
     x[o] = (R)(from_snap(y[o]) * s);
 }
 
+// 16-bit level store (segment_type BF16 / F16): nT fields of N values each.  BF16
+// keeps FP32's exponent range; FP16 covers the O(1e-5 .. 1) values of u, v, T here.
+template <typename S>
+__global__ void pack_level_kernel(const float* __restrict__ a, const float* __restrict__ b,
+                                  const float* __restrict__ c, S* __restrict__ dst, size_t n) {
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x) {
+    dst[o] = to_snap<S>(a[o]);
+    dst[n + o] = to_snap<S>(b[o]);
+    if (c) dst[2 * n + o] = to_snap<S>(c[o]);
+  }
+}
+template <typename S>
+__global__ void unpack_level_kernel(const S* __restrict__ src, float* __restrict__ dst, size_t n, int nf) {
+  for (size_t o = (size_t)blockIdx.x * blockDim.x + threadIdx.x; o < n; o += (size_t)gridDim.x * blockDim.x)
+    for (int f = 0; f < nf; ++f) dst[(size_t)f * n + o] = (float)src[(size_t)f * n + o];
+}
+
+// Level store of the unsteady adjoint (the plain trajectory at L.traj, or the segment
+// buffer at L.seg): level `lev` holds u, v[, T].  With 16-bit levels a forward step
+// writes into stage slot 2 and the level is packed from there; an adjoint step reads
+// a level unpacked into stage slot 0 or 1.
+template <typename R>
+R* level_write_ptr(lks_handle* h, size_t base, int lev) {
+  const auto& L = h->L;
+  if (L.lvl16) return fld<R>(h, L.lvl_stage, 0) + (size_t)2 * L.nT * L.N;
+  return fld<R>(h, base, 0) + (size_t)lev * L.nT * L.N;
+}
+template <typename R>
+lks_status level_pack(lks_handle* h, size_t base, int lev, const R* u, const R* v, const R* T) {
+  const auto& L = h->L;
+  if constexpr (sizeof(R) == 4) {
+    unsigned char* dst = h->ws + base + (size_t)lev * L.nT * L.N * 2;
+    const float* c = L.nT == 3 ? T : nullptr;
+    if (h->d.segment_type == LKS_SNAP_BF16)
+      pack_level_kernel<__nv_bfloat16><<<elementwise_grid(L.N), 256, 0, h->stream>>>(
+          u, v, c, reinterpret_cast<__nv_bfloat16*>(dst), L.N);
+    else
+      pack_level_kernel<__half><<<elementwise_grid(L.N), 256, 0, h->stream>>>(u, v, c, reinterpret_cast<__half*>(dst),
+                                                                            L.N);
+    CKH(h, cudaGetLastError());
+    h->launches++;
+  }
+  return LKS_OK;
+}
+// After a forward step wrote level `lev` through level_write_ptr.
+template <typename R>
+lks_status level_written(lks_handle* h, size_t base, int lev) {
+  const auto& L = h->L;
+  if (!L.lvl16) return LKS_OK;
+  const R* p = level_write_ptr<R>(h, base, lev);
+  return level_pack<R>(h, base, lev, p, p + L.N, p + 2 * L.N);
+}
+// Level `lev` copied from fields u, v[, T] of the state.
+template <typename R>
+lks_status level_from_state(lks_handle* h, size_t base, int lev, const R* u, const R* v, const R* T) {
+  const auto& L = h->L;
+  if (L.lvl16) return level_pack<R>(h, base, lev, u, v, T);
+  R* dst = fld<R>(h, base, 0) + (size_t)lev * L.nT * L.N;
+  const R* src[3] = {u, v, T};
+  for (int f = 0; f < L.nT; ++f)
+    CKH(h, cudaMemcpyAsync(dst + (size_t)f * L.N, src[f], L.N * sizeof(R), cudaMemcpyDeviceToDevice, h->stream));
+  return LKS_OK;
+}
+// FP32 (or FP64) fields of stored level `lev` for an adjoint step; 16-bit levels are
+// unpacked into stage slot `slot` first.
+template <typename R>
+lks_status level_read(lks_handle* h, size_t base, int lev, int slot, const R** p) {
+  const auto& L = h->L;
+  if constexpr (sizeof(R) == 4) {
+    if (L.lvl16) {
+      float* dst = fld<float>(h, L.lvl_stage, 0) + (size_t)slot * L.nT * L.N;
+      const unsigned char* src = h->ws + base + (size_t)lev * L.nT * L.N * 2;
+      if (h->d.segment_type == LKS_SNAP_BF16)
+        unpack_level_kernel<__nv_bfloat16><<<elementwise_grid(L.N), 256, 0, h->stream>>>(
+            reinterpret_cast<const __nv_bfloat16*>(src), dst, L.N, L.nT);
+      else
+        unpack_level_kernel<__half><<<elementwise_grid(L.N), 256, 0, h->stream>>>(
+            reinterpret_cast<const __half*>(src), dst, L.N, L.nT);
+      CKH(h, cudaGetLastError());
+      h->launches++;
+      *p = dst;
+      return LKS_OK;
+    }
+  }
+  *p = fld<R>(h, base, 0) + (size_t)lev * L.nT * L.N;
+  return LKS_OK;
+}
+
 template <typename R>
 lks_status snapshot_store(lks_handle* h, int idx) {
   const auto& L = h->L;
@@ -951,23 +1045,22 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   } else {
     CKH(h, cudaMemsetAsync(jfwd, 0, sizeof(double) * L.fwd_blocks, h->stream));
     const bool plain = d.checkpoint_every == 0;
-    if (plain) {  // level 0 of the trajectory
-      R* tr = fld<R>(h, L.traj, 0);
-      for (int f = 0; f < L.nT; ++f)
-        CKH(h, cudaMemcpyAsync(tr + (size_t)f * L.N, state_ptr<R>(h, h->cur, f == 2 ? 3 : f + 1), fb,
-                               cudaMemcpyDeviceToDevice, h->stream));
-    }
+    if (plain)  // level 0 of the trajectory
+      if ((st = level_from_state<R>(h, L.traj, 0, state_ptr<R>(h, h->cur, 1), state_ptr<R>(h, h->cur, 2),
+                                    d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr)) != LKS_OK)
+        return st;
     for (int t = 0; t < d.n_steps; ++t) {
       if (!plain && t % d.checkpoint_every == 0)
         if ((st = snapshot_store<R>(h, t / d.checkpoint_every)) != LKS_OK) return st;
       R *tu = nullptr, *tv = nullptr, *tT = nullptr;
       if (plain) {
-        R* tr = fld<R>(h, L.traj, 0) + (size_t)(t + 1) * L.nT * L.N;
+        R* tr = level_write_ptr<R>(h, L.traj, t + 1);
         tu = tr;
         tv = tr + L.N;
         tT = d.thermal ? tr + 2 * L.N : nullptr;
       }
       if ((st = launch_fwd<R>(h, t + 1, t >= 1 ? jfwd : nullptr, tu, tv, tT)) != LKS_OK) return st;
+      if (plain && (st = level_written<R>(h, L.traj, t + 1)) != LKS_OK) return st;
     }
   }
   R* u = state_ptr<R>(h, h->cur, 1);
@@ -1050,18 +1143,30 @@ lks_status adjoint_impl(lks_handle* h) {
   const int t_end = d.thermal ? 0 : 1;
   const int flush_every = 256;
   int since_flush = 0;
-  auto level_ptrs = [&](R* base, int lev, const R** u, const R** v, const R** T) {
-    R* p = base + (size_t)lev * L.nT * L.N;
-    *u = p;
-    *v = p + L.N;
-    *T = d.thermal ? p + 2 * L.N : nullptr;
+  // levels t + 1 and t of the level store at `base` (level numbers relative to `lo`);
+  // 16-bit stores unpack level t into stage slot t & 1 (level t + 1 is there from the
+  // step before, or unpacked first)
+  auto levels = [&](size_t base, int lo, int t, bool first, const R** u1, const R** v1, const R** u0,
+                    const R** v0, const R** T0) -> lks_status {
+    const int t1 = std::min(t + 1, n);
+    const R *p1, *p0;
+    lks_status ls;
+    if (first && t1 != t && (ls = level_read<R>(h, base, t1 - lo, t1 & 1, &p1)) != LKS_OK) return ls;
+    if ((ls = level_read<R>(h, base, t - lo, t & 1, &p0)) != LKS_OK) return ls;
+    if (t1 == t) p1 = p0;
+    else if (!first) p1 = L.lvl16 ? fld<R>(h, L.lvl_stage, 0) + (size_t)(t1 & 1) * L.nT * L.N
+                                  : fld<R>(h, base, 0) + (size_t)(t1 - lo) * L.nT * L.N;
+    *u1 = p1;
+    *v1 = p1 + L.N;
+    *u0 = p0;
+    *v0 = p0 + L.N;
+    *T0 = d.thermal ? p0 + 2 * L.N : nullptr;
+    return LKS_OK;
   };
   if (d.checkpoint_every == 0) {
-    R* tr = fld<R>(h, L.traj, 0);
     for (int t = n; t >= t_end; --t) {
-      const R *u1, *v1, *T1, *u0, *v0, *T0;
-      level_ptrs(tr, std::min(t + 1, n), &u1, &v1, &T1);
-      level_ptrs(tr, t, &u0, &v0, &T0);
+      const R *u1, *v1, *u0, *v0, *T0;
+      if ((st = levels(L.traj, 0, t, t == n, &u1, &v1, &u0, &v0, &T0)) != LKS_OK) return st;
       if ((st = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return st;
       if (++since_flush == flush_every) {
         if ((st = flush_sens<R>(h)) != LKS_OK) return st;
@@ -1070,25 +1175,24 @@ lks_status adjoint_impl(lks_handle* h) {
     }
   } else {
     const int K = d.checkpoint_every;
-    R* seg = fld<R>(h, L.seg, 0);
     for (int s = L.n_ckpt - 1; s >= 0; --s) {
       const int t_lo = s * K, t_hi = std::min((s + 1) * K, n), top = std::min(t_hi + 1, n);
       h->cur = 0;
       if ((st = snapshot_load<R>(h, s)) != LKS_OK) return st;
       // level t_lo into the segment buffer, then recompute t_lo+1 .. top
-      for (int f = 0; f < L.nT; ++f)
-        CKH(h, cudaMemcpyAsync(seg + (size_t)f * L.N, state_ptr<R>(h, h->cur, f == 2 ? 3 : f + 1), fb,
-                               cudaMemcpyDeviceToDevice, h->stream));
+      if ((st = level_from_state<R>(h, L.seg, 0, state_ptr<R>(h, h->cur, 1), state_ptr<R>(h, h->cur, 2),
+                                    d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr)) != LKS_OK)
+        return st;
       for (int t = t_lo; t < top; ++t) {
-        R* p = seg + (size_t)(t + 1 - t_lo) * L.nT * L.N;
+        R* p = level_write_ptr<R>(h, L.seg, t + 1 - t_lo);
         if ((st = launch_fwd<R>(h, t + 1, nullptr, p, p + L.N, d.thermal ? p + 2 * L.N : nullptr)) != LKS_OK)
           return st;
+        if ((st = level_written<R>(h, L.seg, t + 1 - t_lo)) != LKS_OK) return st;
       }
       const int t_stop = (s == 0) ? t_end : t_lo + 1;
       for (int t = t_hi; t >= t_stop; --t) {
-        const R *u1, *v1, *T1, *u0, *v0, *T0;
-        level_ptrs(seg, std::min(t + 1, n) - t_lo, &u1, &v1, &T1);
-        level_ptrs(seg, t - t_lo, &u0, &v0, &T0);
+        const R *u1, *v1, *u0, *v0, *T0;
+        if ((st = levels(L.seg, t_lo, t, t == t_hi, &u1, &v1, &u0, &v0, &T0)) != LKS_OK) return st;
         if ((st = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return st;
         if (++since_flush == flush_every) {
           if ((st = flush_sens<R>(h)) != LKS_OK) return st;

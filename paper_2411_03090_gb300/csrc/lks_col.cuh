@@ -406,7 +406,7 @@ __global__ void __launch_bounds__(COL_NT) fwd_colT_kernel(const __grid_constant_
       else if (cn > 0) gp += gk[k];
     }
     const size_t o = (size_t)q * nx + i;
-    return tflux_edge(TT, g0, gp, c.t_val[e], a.u_new[o], a.v_new[o], nxo, nyo);
+    return tflux_edge(TT, g0, gp, flux_value(g, c, e, i), a.u_new[o], a.v_new[o], nxo, nyo);
   };
   struct Dst {
     float a[9], b[9];

@@ -77,7 +77,9 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
   if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
   if (d->in_y0 < 0 || d->in_y1 > d->ny - 1 || d->in_y1 <= d->in_y0) return bad("bad inlet span");
-  if (d->out_y0 < 1 || d->out_y1 > d->ny - 2 || d->out_y1 < d->out_y0) return bad("bad outlet span");
+  // outlet span inside [1, ny-2]; out_y1 = out_y0 - 1 means no outlet (the right edge is a wall)
+  if (d->out_y0 < 1 || d->out_y1 > d->ny - 2 || d->out_y1 < d->out_y0 - 1) return bad("bad outlet span");
+  if (!std::isfinite(d->heat_q)) return bad("heat_q must be finite");
   if (d->n_steps < 1) return bad("n_steps must be >= 1");
   if (d->steady && d->n_adj < 1) return bad("n_adj must be >= 1 for a steady problem");
   if (d->thermal) {
@@ -107,7 +109,9 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   }
   if (d->warm_start != 0 && d->warm_start != 1) return bad("warm_start must be 0 or 1");
   if (d->warm_start && !d->steady) return bad("warm_start: steady problems only");
-  if (d->segment_type != LKS_SNAP_F32) return bad("segment_type: F32 only");
+  if (d->segment_type < LKS_SNAP_F32 || d->segment_type > LKS_SNAP_F16) return bad("bad segment_type");
+  if (d->segment_type != LKS_SNAP_F32 && (d->steady || d->real_type != LKS_REAL_F32))
+    return bad("segment_type BF16 / F16: unsteady FP32 problems only");
   for (int q = 0; q < 4; ++q)
     if (d->reserved[q] != 0) return bad("reserved fields must be zero");
   return LKS_OK;
@@ -247,6 +251,7 @@ inline Coef<R> make_coef(const lks_problem_desc& d) {
   c.gb_x = (R)d.gb[0];
   c.gb_y = (R)d.gb[1];
   c.T_ref = (R)d.T_ref;
+  c.heat_q = (R)d.heat_q;
   for (int e = 0; e < 4; ++e) c.t_val[e] = (R)d.t_val[e];
   return c;
 }
@@ -260,6 +265,8 @@ inline Geom make_geom(const lks_problem_desc& d) {
   g.out_y0 = d.out_y0;
   g.out_y1 = d.out_y1;
   for (int e = 0; e < 4; ++e) g.t_kind[e] = d.thermal ? d.t_kind[e] : 0;
+  g.hx0 = d.heat_x0;
+  g.hx1 = d.heat_x1;
   return g;
 }
 

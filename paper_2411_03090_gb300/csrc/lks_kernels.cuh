@@ -45,6 +45,7 @@ struct Geom {
   int nx, ny;
   int in_y0, in_y1, out_y0, out_y1;
   int t_kind[4];  // left, right, bottom, top
+  int hx0, hx1;   // heated segment of a heat-flux bottom edge (none when hx1 < hx0)
 };
 
 // Parabolic inlet profile 4 y (H - y) / H^2 at row j (y = j - in_y0, H = in_y1 -
@@ -74,6 +75,7 @@ struct Coef {
   R beta_bar, q_beta;  // heat source Q = beta_gamma (1 - T) (Eqs. heatsource, betagamma); 0: none
   R kappa_Q;           // weight of the heat-exchange objective -sum beta_gamma (1 - T)
   R gb_x, gb_y, T_ref; // Boussinesq force G = g beta (T - T_ref) (Eq. boussinesqforce)
+  R heat_q;            // heat flux q_w of the heated bottom segment
 };
 
 // Edge maps of one lattice: 9 classes x 6 moments x 10 columns (lks_edge_moment_map),
@@ -119,6 +121,13 @@ __device__ __forceinline__ int thermal_edge(const Geom& g, int i, int j) {
   if (j == 0) return 2;
   if (j == g.ny - 1) return 3;
   return i == 0 ? 0 : 1;
+}
+
+// Prescribed heat flux -q.n of a heat-flux edge node: the edge's value, or heat_q on
+// the heated segment [hx0, hx1] of the bottom edge.
+template <typename R>
+__device__ __forceinline__ R flux_value(const Geom& g, const Coef<R>& c, int e, int i) {
+  return (e == 2 && i >= g.hx0 && i <= g.hx1) ? c.heat_q : c.t_val[e];
 }
 
 // Brinkman interpolation, Eq. (brinkman), and its derivative.
@@ -480,7 +489,7 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
           const int jn = (j == 0) ? 1 : ny - 2;
           Tn = sT[(jn - y0 + 2) * H2X + (tx + 2)];
         } else {
-          Tn = (ct0[q] + g0 + R(2) * gp + c.t_val[e]) / (R(1) + un * R(nxo) + vn * R(nyo));
+          Tn = (ct0[q] + g0 + R(2) * gp + flux_value(g, c, e, i)) / (R(1) + un * R(nxo) + vn * R(nyo));
         }
       }
     }

@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(NT, 1) fwd_resident_tb_kernel(ResArgs<R> a, Ge
         } else if (cls == C_CORNER) {
           Tn = sT[sidx(i, (j == 0) ? 1 : ny - 2)];
         } else {
-          Tn = (sT[s2] + g0 + R(2) * gp + c.t_val[e]) / (R(1) + un * R(nxo) + vn * R(nyo));
+          Tn = (sT[s2] + g0 + R(2) * gp + flux_value(g, c, e, i)) / (R(1) + un * R(nxo) + vn * R(nyo));
         }
       }
     }

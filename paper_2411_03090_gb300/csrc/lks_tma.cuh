@@ -587,7 +587,7 @@ __global__ void __launch_bounds__(NT) fwd_tma_kernel(const __grid_constant__ Tma
               const int jn = (j == 0) ? 1 : ny - 2;
               Tn = sT[(jn - y0 + 2) * BW + (ox + TMA_BXPAD)];
             } else {
-              Tn = tflux_edge(sT[s2], g0, gp, c.t_val[e], un, vn, nxo, nyo);
+              Tn = tflux_edge(sT[s2], g0, gp, flux_value(g, c, e, i), un, vn, nxo, nyo);
             }
           }
         }

@@ -59,6 +59,7 @@ class Desc(C.Structure):
         ("reserved", C.c_int32 * 4),
         ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
         ("gb", C.c_double * 2), ("T_ref", C.c_double),
+        ("heat_x0", C.c_int32), ("heat_x1", C.c_int32), ("heat_q", C.c_double),
     ]
 
 
@@ -159,7 +160,7 @@ def load(build_if_missing: bool = True):
 
 def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
               path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0,
-              warm_start: bool = False) -> Desc:
+              warm_start: bool = False, segment: str = "f32") -> Desc:
     """Descriptor from an ``inputs.Problem``-like object (``inputs.Problem3``: a
     D3Q19 duct).  tol > 0 (steady D2Q9): march to a relative step change of tol,
     at most max_steps steps per march, in chunks of n_steps / n_adj.  warm_start
@@ -183,6 +184,8 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
         if hasattr(pb, name):
             setattr(d, name, float(getattr(pb, name)))
     d.gb[0], d.gb[1] = float(getattr(pb, "gb_x", 0.0)), float(getattr(pb, "gb_y", 0.0))
+    d.heat_x0, d.heat_x1 = int(getattr(pb, "heat_x0", 0)), int(getattr(pb, "heat_x1", -1))
+    d.heat_q = float(getattr(pb, "heat_q", 0.0))
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T", "kappa_p"):
         setattr(d, name, float(getattr(pb, name)))
@@ -203,6 +206,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.tol = float(tol)
     d.max_steps = int(max_steps)
     d.warm_start = int(bool(warm_start))
+    d.segment_type = SNAP[segment]
     return d
 
 
@@ -260,12 +264,13 @@ class LKS:
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
                  device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
                  path: str = "auto", res_steps: int = 0, tol: float = 0.0, max_steps: int = 0,
-                 warm_start: bool = False):
+                 warm_start: bool = False, segment: str = "f32"):
         if not torch.cuda.is_available():
             raise RuntimeError("the LKS library needs a CUDA device")
         self.L = load()
         self.pb = pb
-        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps, tol, max_steps, warm_start)
+        self.desc = make_desc(pb, real, checkpoint_every, snapshot, path, res_steps, tol, max_steps, warm_start,
+                              segment)
         self.dtype = torch.float64 if real == "f64" else torch.float32
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.is3 = hasattr(pb, "nz")

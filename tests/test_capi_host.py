@@ -82,7 +82,8 @@ def test_descriptor_validation():
     d = lks.make_desc(pb)
     assert lks.workspace_size(d) > 0
     for field, val in (("nx", 3), ("real_type", 7), ("nu", 0.9), ("version", 99), ("version", 1), ("n_steps", 0),
-                       ("res_steps", 4), ("res_steps", -1), ("warm_start", 2), ("segment_type", 7)):
+                       ("res_steps", 4), ("res_steps", -1), ("warm_start", 2), ("segment_type", 7),
+                       ("segment_type", 1)):  # a 16-bit segment needs an unsteady problem
         bad = lks.make_desc(pb)
         setattr(bad, field, val)
         with pytest.raises(lks.LKSError) as e:

@@ -381,6 +381,62 @@ def test_checkpoint_reduced_snapshots_match_oracle(snap, K, nx):
     assert rel_l2(g1.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
 
 
+def test_natural_convection_cavity_on_the_gpu():
+    """Sec. 2.6's natural-convection check (closed cavity, heated bottom segment,
+    Boussinesq force, K_s = 10 K_f; `inputs.natural_convection_cavity`) on the FP64
+    GPU path: after 46000 forward and 40000 adjoint steps the gradient equals the
+    oracle's to 1e-9, and ALKS agrees in direction (cosine >= 0.99) with central
+    differences of J computed on the GPU by tolerance marches warm-started from the
+    converged state."""
+    pb, g = inputs.natural_convection_cavity(0.5)
+    pb = pb.with_(n_steps=46000, n_adj=40000)
+    s = LKS(pb, real="f64")
+    J, grad = s.gradient(torch.from_numpy(g))
+    assert s.query().device_status == 0
+    ref = O.steady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= 1e-11 * abs(ref["J"])
+    gr = grad.cpu().numpy()
+    assert rel_l2(gr, ref["dJdgamma"]) <= 1e-9
+    w = LKS(pb.with_(n_steps=1000), real="f64", tol=1e-13, max_steps=400000, warm_start=True)
+    gt = torch.from_numpy(g)
+    w.lks_forward(gt)
+    base = [x.clone() for x in w.get_state()]
+    j, eps = pb.ny // 2, 1e-3
+    a, b = [], []
+    for i in (20, 28, 36, 44, 52):
+        v = []
+        for sg in (1, -1):
+            gg = g.copy()
+            gg[j, i] += sg * eps
+            w.set_state(gt, base[0], base[1], base[2], base[3])
+            v.append(w.lks_forward(torch.from_numpy(gg)).item())
+        a.append(gr[j, i])
+        b.append((v[0] - v[1]) / (2 * eps))
+    a, b = np.array(a), np.array(b)
+    assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) >= 0.99, a / b
+
+
+@pytest.mark.parametrize("thermal", [False, True])
+@pytest.mark.parametrize("K,snap", [(0, "f32"), (50, "bf16"), (37, "f32")])
+@pytest.mark.parametrize("seg", ["bf16", "f16"])
+def test_16bit_stored_levels_match_oracle(seg, K, snap, thermal):
+    """segment_type BF16 / F16: the levels of u, v (and T) that the adjoint reads --
+    the whole trajectory (K = 0) or the recomputed segment -- stored in 16 bits
+    (packed after each forward step, unpacked before each adjoint step).  J is
+    untouched (the forward march computes it) and the gradient stays within 1e-3 of
+    the FP64 oracle's; on the TMA-staged kernels (nx = 136), flow and thermal."""
+    pb = (thermal_small(False, nx=136) if thermal else small(steady=False, n_steps=200, nx=136))
+    g = pb.gamma()
+    ref = O.unsteady_gradient(pb, g)
+    s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap, segment=seg)
+    J, grad = s.gradient(torch.from_numpy(g))
+    assert s.query().device_status == 0
+    assert abs(J.item() - ref["J"]) <= 1e-5 * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= 1e-3
+    full = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap)
+    assert s.workspace.numel() < full.workspace.numel()
+
+
 # ---------------------------------------------------------------------------------------
 # API behaviour
 # ---------------------------------------------------------------------------------------
