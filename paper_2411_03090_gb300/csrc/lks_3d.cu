@@ -963,6 +963,8 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
   // Every thread's node, and every node whose push it reads, is off the x and y faces
   // (lanes 1 .. 30 and warps 0 .. NYC3 + 1 push for the outputs).
   const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  // every thread's row, and every row whose push it reads, is off the y faces
+  const bool tile_yfast = y0 >= 2 && y0 + NYC3 <= ny - 2;
   static_assert((NSLC3 & (NSLC3 - 1)) == 0, "ring slots index by mask");
   auto slot = [&](int p) { return (p - pbase) & (NSLC3 - 1); };
   auto issue = [&](int p) {
@@ -1020,11 +1022,14 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
 #pragma unroll
   for (int q = 0; q < 9; ++q) Am[q] = Ac[q] = Ap[q] = R(0);
 
-  // One plane: push of plane z, then gather of plane z - 1.  FAST: no node of the
-  // tile at planes z and z - 1 lies on a face (and all of them are inside).
-  auto plane_step = [&](int z, auto fast_tag) {
-    constexpr bool FAST = decltype(fast_tag)::value;
-    const bool src = FAST || (in_xy && z >= 0 && z < nz);
+  // One plane: push of plane z, then gather of plane z - 1.  MODE 0 (fast): no node
+  // of the tile at planes z and z - 1 lies on a face (and all of them are inside);
+  // MODE 1: only the x faces can occur (rows and planes are off the y and z faces);
+  // MODE 2: any face.
+  auto plane_step = [&](int z, auto mode_tag) {
+    constexpr int MODE = decltype(mode_tag)::value;
+    constexpr bool FAST = MODE == 0, XO = MODE == 1;
+    const bool src = FAST || (XO ? (i >= 0 && i < nx) : (in_xy && z >= 0 && z < nz));
     R gr[3][3];  // gr[d][a] = d u_d / d x_a
     gr[0][0] = (__shfl_down_sync(0xffffffffu, uc, 1) - __shfl_up_sync(0xffffffffu, uc, 1)) * R(0.5);
     gr[1][0] = (__shfl_down_sync(0xffffffffu, vc, 1) - __shfl_up_sync(0xffffffffu, vc, 1)) * R(0.5);
@@ -1036,7 +1041,7 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
     gr[1][2] = (vp - vm) * R(0.5);
     gr[2][2] = (wp - wm) * R(0.5);
     if constexpr (!FAST) {
-      const bool on[3] = {i == 0 || i == nx - 1, j == 0 || j == ny - 1, z == 0 || z == nz - 1};
+      const bool on[3] = {i == 0 || i == nx - 1, !XO && (j == 0 || j == ny - 1), !XO && (z == 0 || z == nz - 1)};
       if (src && (on[0] || on[1] || on[2])) {  // faces: one-sided differences and continuity
 #pragma unroll
         for (int d = 0; d < 3; ++d) {
@@ -1112,8 +1117,10 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       int n0 = 0, n1 = 0, n2 = 0, faces = 0;
       if constexpr (!FAST) {
         n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
-        n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
-        n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+        if constexpr (!XO) {
+          n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+          n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+        }
         faces = abs(n0) + abs(n1) + abs(n2);
       }
       R drn, uo[3] = {R(0), R(0), R(0)};
@@ -1171,8 +1178,10 @@ __global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ 
       drain_and_fail();
       return;
     }
-    if (tile_fast && z >= 2 && z <= nz - 2) plane_step(z, std::true_type{});
-    else plane_step(z, std::false_type{});
+    const bool zin = z >= 2 && z <= nz - 2;
+    if (tile_fast && zin) plane_step(z, std::integral_constant<int, 0>{});
+    else if (tile_yfast && zin) plane_step(z, std::integral_constant<int, 1>{});
+    else plane_step(z, std::integral_constant<int, 2>{});
   }
 }
 
