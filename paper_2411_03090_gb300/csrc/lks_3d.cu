@@ -920,6 +920,20 @@ __host__ __device__ constexpr int oslot3(int k) {
   return s;
 }
 
+// Link q (0..4, in link order) of face ff (axis a = ff / 2, outward sign s = +1 for
+// odd ff, -1 for even): among the links with c_a = s (unknown at that face) or with
+// c_a = -s (the opposite links).
+__host__ __device__ constexpr int face_link3(int ff, int q, bool unknown) {
+  const int a = ff / 2, want = ((ff & 1) ? 1 : -1) * (unknown ? 1 : -1);
+  int n = 0;
+  for (int k = 0; k < 19; ++k)
+    if (c3(k, a) == want) {
+      if (n == q) return k;
+      ++n;
+    }
+  return -1;
+}
+
 __host__ __device__ constexpr size_t fwd3c_smem() {
   return sizeof(float) * ((size_t)NSLC3 * NFC3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
 }
@@ -1425,7 +1439,8 @@ __global__ void __launch_bounds__(NTF3, 2) adj3t_kernel(const __grid_constant__ 
 constexpr int NAY3 = 3;  // staged fields: s~xy, s~yy, s~yz
 
 __host__ __device__ constexpr size_t adj3c_smem() {
-  return sizeof(float) * ((size_t)NSLC3 * NAY3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
+  return sizeof(float) * ((size_t)NSLC3 * NAY3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3 + 6 * kFillLen3) + 8 * NSLC3 +
+         128;
 }
 
 struct Adj3CArgs {
@@ -1452,7 +1467,8 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
   extern __shared__ unsigned char smem_raw3[];
   R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NAY3][CFS3]
   R* ex = ring + NSLC3 * NAY3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NXL3 * XW3);
+  R* fill = ex + NXS3 * NYC3 * NXL3 * XW3;                         // [6][kFillLen3]: single-face fills
+  uint64_t* bar = reinterpret_cast<uint64_t*>(fill + 6 * kFillLen3);
   if (lks::timed_out_before(a.status)) return;
   if (!lks::tma_layout_ok(ring, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
@@ -1491,6 +1507,7 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
     lks::fence_mbar_init();
     lks::fence_proxy_async();
   }
+  for (int q = threadIdx.x; q < 6 * kFillLen3; q += NTC3) fill[q] = a.emap[kClasses3 * kNA3 * 20 + q];
   __syncthreads();
   for (int p = pbase; p < pbase + NSLC3 && p <= plast; ++p) {
     if (threadIdx.x == 0) issue(p);
@@ -1616,8 +1633,7 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
     }
     // ---- gather of node (i, j, z - 1) ----
     R F[19];
-    bool face = false;
-    int cls = 0;
+    int nf = 0, cls = 0;  // faces the node lies on; its edge class
     if (gat) {
       const R* xr = xslot(zd, warp - 1) + lane - 2;
       static_for<0, 19>([&](auto kk) {
@@ -1629,15 +1645,41 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
         const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
         const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
         const int n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
-        face = (n0 | n1 | n2) != 0;
+        nf = abs(n0) + abs(n1) + abs(n2);
         cls = (n0 + 1) * 9 + (n1 + 1) * 3 + (n2 + 1);
+        if (nf == 1) {
+          // One face: its five unknown links (c . n > 0) from the five opposite ones
+          // (c . n < 0), the least-squares fill of the face rule, plus the boundary
+          // objective term; the other links' columns of the rule are zero.
+          const int ff = n0 != 0 ? (n0 > 0) : (n1 != 0 ? 2 + (n1 > 0) : 4 + (n2 > 0));
+          static_for<0, 6>([&](auto fc) {
+            constexpr int f = decltype(fc)::value;
+            if (ff == f) {
+              const R* X = fill + f * kFillLen3;
+              R O[5];
+              static_for<0, 5>([&](auto pp) {
+                constexpr int p = decltype(pp)::value;
+                O[p] = F[face_link3(f, p, false)];
+              });
+              static_for<0, 5>([&](auto qq) {
+                constexpr int q = decltype(qq)::value;
+                R v = X[25 + q];
+#pragma unroll
+                for (int p = 0; p < 5; ++p) v += X[q * 5 + p] * O[p];
+                F[face_link3(f, q, true)] = v;
+              });
+            }
+          });
+        }
       }
-      if (!face) {
+      if (nf <= 1) {
         R m[kNA3];
         adj_moments3(F, m);
-        m[1] = (m[1] + C[1]) * C[0];
-        m[2] = (m[2] + C[2]) * C[0];
-        m[3] = (m[3] + C[3]) * C[0];
+        if (nf == 0) {
+          m[1] = (m[1] + C[1]) * C[0];
+          m[2] = (m[2] + C[2]) * C[0];
+          m[3] = (m[3] + C[3]) * C[0];
+        }
         const size_t o = gidx(g, i, j, zd);
 #pragma unroll
         for (int r = 0; r < kNA3; ++r) a.m0[r][o] = m[r];
@@ -1645,14 +1687,14 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
       }
     }
     if constexpr (!FAST) {
-      // Face, box-edge and corner nodes apply their class's moment map (10 x 19, plus
-      // the boundary objective term).  Where few lanes of the warp are such nodes (the
-      // x faces: one lane), the whole warp computes each one's ten moments, one row
-      // per lane, and lanes 0..9 store them, instead of that lane alone running the
-      // 190 products while the others wait.
-      unsigned fm = __ballot_sync(0xffffffffu, gat && face);
+      // Box-edge and corner nodes apply their class's moment map (10 x 19, plus the
+      // boundary objective term).  Where few lanes of the warp are such nodes, the
+      // whole warp computes each one's ten moments, one row per lane, and lanes 0..9
+      // store them, instead of that lane alone running the 190 products while the
+      // others wait.
+      unsigned fm = __ballot_sync(0xffffffffu, gat && nf >= 2);
       if (__popc(fm) > 2) {
-        if (gat && face) {
+        if (gat && nf >= 2) {
           const R* M = a.emap + cls * (kNA3 * 19);
           const R* M0 = a.emap + kClasses3 * kNA3 * 19 + cls * kNA3;  // boundary objective term
           const size_t o = gidx(g, i, j, zd);
@@ -2136,10 +2178,11 @@ void lsq19(const double* A, int nc, const double* rhs, double* x) {
 
 }  // namespace
 
-void flow_moment_map3(double A, int cls, double* out, double* unit) {
+void flow_moment_map3(double A, int cls, double* out, double* unit, double* fill) {
   const int n[3] = {cls / 9 - 1, (cls / 3) % 3 - 1, cls % 3 - 1};
   std::memset(out, 0, sizeof(double) * kNA3 * 19);
   if (unit) std::memset(unit, 0, sizeof(double) * kNA3);
+  if (fill) std::memset(fill, 0, sizeof(double) * kFillLen3);
   if (n[0] == 0 && n[1] == 0 && n[2] == 0) return;
   const int faces = std::abs(n[0]) + std::abs(n[1]) + std::abs(n[2]);
   const bool pressure = faces == 1 && n[0] == 1;
@@ -2190,14 +2233,25 @@ void flow_moment_map3(double A, int cls, double* out, double* unit) {
       for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * X[U[q]][k];
       out[r * 19 + k] = s;
     }
-  if (unit) {  // the unknowns' response to a unit term in every row, and its moments
-    double rhs[19], x[24];
+  double xu[24];  // the unknowns' response to a unit term in every row
+  {
+    double rhs[19];
     for (int r = 0; r < 19; ++r) rhs[r] = -1.0;
-    lsq19(Am.data(), nc, rhs, x);
+    lsq19(Am.data(), nc, rhs, xu);
+  }
+  if (unit)  // its moments
     for (int r = 0; r < kNA3; ++r) {
       double s = 0.0;
-      for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * x[q];
+      for (int q = 0; q < nu; ++q) s += mom(r, U[q]) * xu[q];
       unit[r] = s;
+    }
+  if (fill && faces == 1) {
+    int O[19], no = 0;
+    for (int k = 0; k < 19; ++k)
+      if (cdot(k, n) < 0) O[no++] = k;
+    for (int q = 0; q < nu && q < 5; ++q) {
+      for (int p = 0; p < no && p < 5; ++p) fill[q * 5 + p] = X[U[q]][O[p]];
+      fill[25 + q] = xu[q];
     }
   }
 }
@@ -2224,7 +2278,8 @@ Layout3 make_layout3(const lks_problem_desc& d) {
   L.jpart = take(sizeof(double) * L.jblocks);
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
-  L.emap = take(L.rsize * kClasses3 * kNA3 * 20);  // maps, then the boundary objective terms
+  // maps, then the boundary objective terms, then the single-face fills
+  L.emap = take(L.rsize * (kClasses3 * kNA3 * 20 + 6 * kFillLen3));
   L.total = off;
   return L;
 }
@@ -2234,13 +2289,21 @@ lks_status upload_maps3(const Ctx3& c) {
   // kClasses3 maps of 10 x 19, then per class the moments' response to the boundary
   // objective term of every row: +kappa_p on the inlet face (class of n = (-1, 0, 0)),
   // -kappa_p on the outlet face (n = (1, 0, 0)), absorbed there by lambda~
-  std::vector<double> m((size_t)kClasses3 * kNA3 * 20, 0.0);
+  std::vector<double> m((size_t)kClasses3 * kNA3 * 20 + 6 * kFillLen3, 0.0);
   double* off = &m[(size_t)kClasses3 * kNA3 * 19];
+  double* fills = &m[(size_t)kClasses3 * kNA3 * 20];
   for (int cls = 0; cls < kClasses3; ++cls) {
-    double unit[kNA3];
-    flow_moment_map3(A, cls, &m[(size_t)cls * kNA3 * 19], unit);
+    double unit[kNA3], fill[kFillLen3];
+    flow_moment_map3(A, cls, &m[(size_t)cls * kNA3 * 19], unit, fill);
     const double jb = cls == 4 ? c.d->kappa_p : (cls == 22 ? -c.d->kappa_p : 0.0);
     for (int r = 0; r < kNA3; ++r) off[cls * kNA3 + r] = jb * unit[r];
+    const int n[3] = {cls / 9 - 1, (cls / 3) % 3 - 1, cls % 3 - 1};
+    if (std::abs(n[0]) + std::abs(n[1]) + std::abs(n[2]) == 1) {
+      const int a = n[0] != 0 ? 0 : (n[1] != 0 ? 1 : 2);
+      double* f = fills + (2 * a + (n[a] > 0)) * kFillLen3;
+      for (int q = 0; q < 25; ++q) f[q] = fill[q];
+      for (int q = 0; q < 5; ++q) f[25 + q] = jb * fill[25 + q];
+    }
   }
   if (c.L->rsize == 8) {
     CK3(c, cudaMemcpy(c.ws + c.L->emap, m.data(), m.size() * 8, cudaMemcpyHostToDevice));

@@ -32,6 +32,9 @@ constexpr int kNA3 = 10;
 // Edge classes: index (n_x + 1) * 9 + (n_y + 1) * 3 + (n_z + 1) of the outward
 // normal (sum of the face normals); class 22 (n = (1, 0, 0)) is the outlet face.
 constexpr int kClasses3 = 27;
+// Per single face (axis a, outward sign s; index 2a + (s > 0)): the 5 x 5 fill of the
+// unknown links from the opposite links, then the unknowns' boundary objective term.
+constexpr int kFillLen3 = 30;
 
 // Everything the 3-D marches need from the handle.
 struct Ctx3 {
@@ -43,8 +46,9 @@ struct Ctx3 {
   std::string* err;
 };
 
-// Uploads the host-built adjoint edge maps (kClasses3 x 10 x 19) and the per-class
-// boundary objective terms of the moments (kClasses3 x 10).
+// Uploads the host-built adjoint edge maps (kClasses3 x 10 x 19), the per-class
+// boundary objective terms of the moments (kClasses3 x 10) and the six single-face
+// fills (6 x kFillLen3).
 lks_status upload_maps3(const Ctx3& c);
 // Steps 2-3: gamma -> state after n_steps; J of the final state into J_dev (may be
 // null).  *cur receives the buffer (0 = A, 1 = B) holding the final state, *path the
@@ -62,7 +66,11 @@ lks_status sensitivity3(const Ctx3& c, int cur, int acur, void* out);
 // (rows rho~, u~x, u~y, u~z, s~xx, s~xy, s~xz, s~yy, s~yz, s~zz; columns the 19
 // gathered f~, zero for unknown links).  unit (10 values, may be null): the moments
 // when every residual row carries a unit boundary objective term and the gathered
-// f~ are zero (Eqs. afboundaryu / afboundaryp).
-void flow_moment_map3(double A, int cls, double* out, double* unit);
+// f~ are zero (Eqs. afboundaryu / afboundaryp).  fill (kFillLen3 values, may be
+// null; single faces only): the unknown links (c . n > 0, in link order) per unit of
+// each opposite link (c . n < 0, in link order), 5 x 5 row-major, then the unknowns
+// under a unit term in every row.  The rule's columns of the links with c . n = 0
+// are zero, so these determine the unknowns.
+void flow_moment_map3(double A, int cls, double* out, double* unit, double* fill = nullptr);
 
 }  // namespace lks3
