@@ -278,6 +278,28 @@ def natural_convection_cavity(scale: float = 0.5, Ra: float = 2e4, Pr: float = 0
     return pb, g
 
 
+def forced_convection_check(n: int = 31, Pr: float = 0.71, beta_bar: float = 0.01, nu: float = 0.1,
+                            kappa_Q: float = 1.0, n_steps: int = 40000) -> tuple:
+    """The forced-convection sensitivity check of Sec. 2.6 on the domain of its
+    non-thermal check, at n x n nodes: walls, a parabolic inlet over the middle third
+    of the left edge and an outlet over the same rows of the right edge, nu = 0.1,
+    Re = 1 on the inlet width; gamma = 0.1 in the centre circle of radius n / 6 and
+    0.9 elsewhere.  T = 0 is prescribed on the inlet (left) edge and every other edge
+    is adiabatic.  The solid heats the fluid through the source Q = beta_gamma (1 - T)
+    (Eqs. heatsource, betagamma) and J adds the heat-exchange objective
+    -kappa_Q sum beta_gamma (1 - T) (Eq. objective_heatexchanger) to the dissipation.
+    Unstated and chosen: Pr, beta_bar, K_s = K_f.  Returns (problem, gamma)."""
+    a, b = (n - 1) // 3, 2 * (n - 1) // 3
+    K = nu / Pr
+    pb = Problem(nx=n, ny=n, nu=nu, alpha_bar=1e3 * nu, u_max=nu / (b - a), in_y0=a, in_y1=b, out_y0=a, out_y1=b,
+                 thermal=1, K_f=K, K_s=K, t_kind=[T_FIXED, T_FLUX, T_FLUX, T_FLUX], t_val=[0.0, 0.0, 0.0, 0.0],
+                 beta_bar=beta_bar, kappa_Q=kappa_Q, n_steps=n_steps, n_adj=n_steps)
+    c = (n - 1) / 2.0
+    yy, xx = np.mgrid[0:n, 0:n]
+    g = np.where((xx - c) ** 2 + (yy - c) ** 2 <= (n / 6.0) ** 2, 0.1, 0.9)
+    return pb, g
+
+
 def poiseuille(nx: int = 33, ny: int = 17, nu: float = 0.1, u_max: float = 0.02) -> Problem:
     """Empty channel (gamma = 1 everywhere) for the Poiseuille pin."""
     return Problem(nx=nx, ny=ny, nu=nu, alpha_bar=1e3 * nu, u_max=u_max)

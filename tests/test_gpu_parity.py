@@ -416,6 +416,49 @@ def test_natural_convection_cavity_on_the_gpu():
     assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) >= 0.99, a / b
 
 
+def test_forced_convection_check_on_the_gpu():
+    """Sec. 2.6's forced-convection check (`inputs.forced_convection_check`: T fixed on
+    the inlet edge, adiabatic elsewhere, heat source Q = beta_gamma (1 - T) and the
+    heat-exchange objective) on the FP64 GPU path: after 40000 + 40000 steps J and
+    the gradient equal the oracle's to 1e-11 and 1e-9; the heat-exchange share of the
+    gradient (kappa_Q = 1 minus kappa_Q = 0) agrees with central differences of that
+    share computed on the GPU (tolerance marches warm-started from the converged
+    state) along the centre line: cosine >= 0.999, ratios 0.8..1.05, as the oracle
+    pin finds."""
+    pb, g = inputs.forced_convection_check()
+    s1 = LKS(pb, real="f64")
+    J1, g1 = s1.gradient(torch.from_numpy(g))
+    assert s1.query().device_status == 0
+    ref = O.steady_gradient(pb, g)
+    assert abs(J1.item() - ref["J"]) <= 1e-11 * abs(ref["J"])
+    assert rel_l2(g1.cpu().numpy(), ref["dJdgamma"]) <= 1e-9
+    s0 = LKS(pb.with_(kappa_Q=0.0), real="f64")
+    _, g0 = s0.gradient(torch.from_numpy(g))
+    sens = (g1 - g0).cpu().numpy()
+    gt = torch.from_numpy(g)
+    w = [LKS(pb.with_(n_steps=1000, kappa_Q=kq), real="f64", tol=1e-13, max_steps=400000, warm_start=True)
+         for kq in (1.0, 0.0)]
+    w[0].lks_forward(gt)
+    base = [x.clone() for x in w[0].get_state()]
+    j, eps = 15, 1e-3
+    a, b = [], []
+    for i in (6, 10, 15, 21, 25):
+        v = []
+        for sg in (1, -1):
+            gg = torch.from_numpy(g.copy())
+            gg[j, i] += sg * eps
+            jq = []
+            for h in w:
+                h.set_state(gt, base[0], base[1], base[2], base[3])
+                jq.append(h.lks_forward(gg).item())
+            v.append(jq[0] - jq[1])
+        a.append(sens[j, i])
+        b.append((v[0] - v[1]) / (2 * eps))
+    a, b = np.array(a), np.array(b)
+    assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) >= 0.999, a / b
+    assert np.all((a / b > 0.8) & (a / b < 1.05)), a / b
+
+
 @pytest.mark.parametrize("thermal", [False, True])
 @pytest.mark.parametrize("K,snap", [(0, "f32"), (50, "bf16"), (37, "f32")])
 @pytest.mark.parametrize("seg", ["bf16", "f16"])
