@@ -38,7 +38,7 @@
 extern "C" {
 #endif
 
-#define LKS_DESC_VERSION 2
+#define LKS_DESC_VERSION 3
 
 typedef enum {
     LKS_OK = 0,
@@ -164,6 +164,16 @@ typedef struct {
      * wall).  heat_x1 < heat_x0: none. */
     int32_t heat_x0, heat_x1;
     double heat_q;
+    /* Energy loss (Eq. objective_doublepipe), D2Q9: J gains kappa_E J_E with J_E the
+     * outflow of total pressure, the sum over the inlet nodes (as for kappa_p) and the
+     * outlet nodes of -n.u (p + |u|^2 / 2), p the pressure above the outlet's,
+     * (rho - rho_out) / 3; unsteady problems sum it over levels 1..n_steps.  The
+     * adjoint edge rule carries kappa_E u in every residual row of the inlet nodes
+     * (the integrand's derivative with respect to p) and, on the outlet nodes,
+     * 3 kappa_E (-3/2 u_n^2) (c_i.n) / rho_out (three times its derivative with
+     * respect to f_i through u_n).  Runs on the per-step kernels (exec_path AUTO or
+     * STEP).  0: none. */
+    double kappa_E;
 } lks_problem_desc;
 
 /* Three dimensions (lattice = LKS_LATTICE_D3Q19).  The paper states LKS / ALKS in

@@ -103,6 +103,7 @@ class Problem:
     heat_x0: int = 0         # heated segment [heat_x0, heat_x1] of a heat-flux bottom edge
     heat_x1: int = -1        # (-1: none)
     heat_q: float = 0.0      # its heat flux
+    kappa_E: float = 0.0     # weight of the energy loss J_E (sum of -n.u (p + |u|^2 / 2) over inlet and outlet)
 
     def resolved(self, name: str):
         """Field value with negative span ends counted from the top edge (ny + v)."""

@@ -23,14 +23,18 @@
  *                      plus an optional kappa_T * T term) plus kappa_p times the
  *                      static pressure drop J_p = sum_in p - sum_out p (Eq.
  *                      objective_pipebend, p = rho / 3, dGamma = 1, over the
- *                      inlet span and the outlet nodes)
+ *                      inlet span and the outlet nodes) plus kappa_E times the
+ *                      energy loss J_E = sum -n.u (p + |u|^2 / 2) over the same
+ *                      nodes (Eq. objective_doublepipe)
  *   adjoint            Eqs. (ap)-(aq) with f~^eq Eq. (afeq), g~^eq Eq. (ageq) and
  *                      the sources of Eqs. (albef_ex), (albeg_ex) (App. A)
  *   adjoint BCs        Eq. (afboundaryu) solved in the least-squares sense as in
  *                      Sec. 2.5 (generalized inverse, residual Eq. (r_definition)),
  *                      with the boundary objective term on the inlet span and the
  *                      outlet (+-kappa_p per row: the derivative of the integrand
- *                      kappa_p p with respect to p);
+ *                      kappa_p p with respect to p; for J_E the same on the inlet,
+ *                      and on the outlet three times its derivative with respect
+ *                      to f_i through u_n);
  *                      the pressure, temperature and heat-flux versions of App. A
  *                      Eqs. (afboundaryp), (agboundaryT), (agboundaryq),
  *                      (afboundaryuq) by the same least-squares procedure
@@ -98,6 +102,8 @@ typedef struct {
     double T_ref;
     int heat_x0, heat_x1;      /* heated segment of a flux-type bottom edge     */
     double heat_q;             /* its heat flux (replaces t_val[bottom] there)   */
+    double kappa_E;            /* weight of the energy loss J_E, Eq.
+                                  (objective_doublepipe)                          */
 } orc_problem;
 
 /* ------------------------------------------------------------------------- */
@@ -430,11 +436,37 @@ double orc_pressure_drop(const orc_problem *p, const double *rho) {
     return s / 3.0;
 }
 
-/* J = J_O + kappa_p J_p of one level. */
+/* Energy loss of one level, Eq. (objective_doublepipe): the flux of total pressure
+ * out of the domain, sum over boundary nodes of -n.u (p + |u|^2 / 2) with dGamma = 1.
+ * The walls carry u = 0, so the sum runs over the inlet nodes (n = (-1, 0):
+ * -n.u = u) and the outlet nodes (n = (1, 0): -n.u = -u), the nodes of J_p.
+ * Reading: p is the pressure above the outlet's, (rho - rho_bar) / 3.  A constant
+ * added to p adds that constant times the net mass flux, which vanishes at steady
+ * state, so the value is unchanged there and the outlet term keeps only its kinetic
+ * part. */
+double orc_energy_loss(const orc_problem *p, const double *rho, const double *u, const double *v) {
+    int nx = p->nx, ny = p->ny;
+    double s = 0.0;
+    if (p->periodic & 1) return 0.0;
+    for (int j = 1; j < ny - 1; ++j) {
+        if (is_inlet(p, 0, j)) {
+            double uu = AT(u, 0, j), vv = AT(v, 0, j);
+            s += uu * ((AT(rho, 0, j) - p->rho_out) / 3.0 + 0.5 * (uu * uu + vv * vv));
+        }
+        if (j >= p->out_y0 && j <= p->out_y1) {
+            double uu = AT(u, nx - 1, j), vv = AT(v, nx - 1, j);
+            s -= uu * ((AT(rho, nx - 1, j) - p->rho_out) / 3.0 + 0.5 * (uu * uu + vv * vv));
+        }
+    }
+    return s;
+}
+
+/* J = J_O + kappa_p J_p + kappa_E J_E of one level. */
 double orc_objective_total(const orc_problem *p, const double *gamma, const double *rho,
                            const double *u, const double *v, const double *T) {
     double J = orc_objective(p, gamma, u, v, T);
     if (p->kappa_p != 0.0) J += p->kappa_p * orc_pressure_drop(p, rho);
+    if (p->kappa_E != 0.0) J += p->kappa_E * orc_energy_loss(p, rho, u, v);
     return J;
 }
 
@@ -536,7 +568,7 @@ static void lstsq_small(int m, int n, const double *M /* m x n, row major */, co
  * f[] holds the known values on entry and all nine on exit.  mult[0..1] returns
  * the multipliers. */
 void orc_bc_flow(int n_x, int n_y, int pressure, double A, double kT, const int *unknown,
-                 double *f, double *mult, double jb) {
+                 double *f, double *mult, double jb, const double *jbv) {
     int U[9], nu_ = 0;
     for (int k = 0; k < 9; ++k)
         if (unknown[k]) U[nu_++] = k;
@@ -563,7 +595,7 @@ void orc_bc_flow(int n_x, int n_y, int pressure, double A, double kT, const int 
         for (int c = 0; c < 9; ++c)
             if (!unknown[c]) s += Mfull[r][c] * f[c];
         s -= kT * (double)(CX[r] * n_x + CY[r] * n_y);
-        rhs[r] = -s - jb;
+        rhs[r] = -s - jb - (jbv ? jbv[r] : 0.0);
     }
     lstsq_small(9, ncol, Ms, rhs, x);
     for (int q = 0; q < nu_; ++q) f[U[q]] = x[q];
@@ -696,10 +728,24 @@ void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P
          * and - on the outlet (reading: the row term is the derivative with
          * respect to p; with it the gradient matches central differences in the
          * paper's own pressure-drop verification, Sec. 2.6) */
-        double jb = 0.0;
+        double jb = 0.0, jbv[9] = {0};
         if (cls == N_PRESSURE) jb = -p->kappa_p;
         else if (cls == N_VELOCITY && is_inlet(p, i, j)) jb = p->kappa_p;
-        orc_bc_flow(n_x, n_y, cls == N_PRESSURE, A, kT, unknown, f, NULL, jb);
+        if (p->kappa_E != 0.0) {
+            /* energy loss: on the inlet, the derivative of u (p + |u|^2 / 2) with
+             * respect to p (u prescribed), as for J_p; on the outlet (p = p_bar, the
+             * zero of the gauge, and u_s = 0) the integrand -u_n^3 / 2 depends on the
+             * f_i through u_n = sum c_i.n f_i / rho_bar, and each row carries three
+             * times d/df_i, the scale of the J_p row term (d/dp = 3 d/drho = 3 d/df_i). */
+            if (cls == N_VELOCITY && is_inlet(p, i, j)) jb += p->kappa_E * AT(u0, i, j);
+            if (cls == N_PRESSURE) {
+                double un = AT(u0, i, j) * n_x + AT(v0, i, j) * n_y;
+                double dJ = -1.5 * un * un;
+                for (int r = 0; r < 9; ++r)
+                    jbv[r] = 3.0 * p->kappa_E * dJ * (double)(CX[r] * n_x + CY[r] * n_y) / p->rho_out;
+            }
+        }
+        orc_bc_flow(n_x, n_y, cls == N_PRESSURE, A, kT, unknown, f, NULL, jb, jbv);
     }
     double m[NADJ] = {0};
     for (int k = 0; k < 9; ++k) {

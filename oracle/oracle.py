@@ -50,6 +50,7 @@ class OrcProblem(C.Structure):
         ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
         ("gb_x", C.c_double), ("gb_y", C.c_double), ("T_ref", C.c_double),
         ("heat_x0", C.c_int), ("heat_x1", C.c_int), ("heat_q", C.c_double),
+        ("kappa_E", C.c_double),
     ]
 
 
@@ -98,9 +99,11 @@ def lib():
         L.orc_objective.restype = C.c_double
         L.orc_dJdu_node.argtypes = [prob, P, P, P, C.c_int, C.c_int, P, P]
         L.orc_bc_flow.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
-                                  C.POINTER(C.c_int), P, P, C.c_double]
+                                  C.POINTER(C.c_int), P, P, C.c_double, P]
         L.orc_pressure_drop.argtypes = [prob, P]
         L.orc_pressure_drop.restype = C.c_double
+        L.orc_energy_loss.argtypes = [prob, P, P, P]
+        L.orc_energy_loss.restype = C.c_double
         L.orc_objective_total.argtypes = [prob, P, P, P, P, P]
         L.orc_objective_total.restype = C.c_double
         L.orc_bc_thermal.argtypes = [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double,
@@ -168,7 +171,7 @@ def make_problem(pb) -> OrcProblem:
         if name in ("t_kind", "t_val"):
             continue
         if not hasattr(pb, name) and name in ("periodic", "G_x", "G_y", "beta_bar", "q_beta", "kappa_Q", "gb_x",
-                                              "gb_y", "T_ref", "heat_x0", "heat_q"):
+                                              "gb_y", "T_ref", "heat_x0", "heat_q", "kappa_E"):
             continue  # fields a problem description may leave out: zero
         if not hasattr(pb, name) and name == "heat_x1":
             s.heat_x1 = -1  # no heated segment
@@ -249,7 +252,7 @@ def forward_node(pb, gamma, t, st: State, i: int, j: int) -> np.ndarray:
 
 
 def objective(pb, gamma, st: State) -> float:
-    """J = J_O + kappa_p J_p of one state (Step 3)."""
+    """J = J_O + kappa_p J_p + kappa_E J_E of one state (Step 3)."""
     L = lib()
     prob = make_problem(pb)
     return float(L.orc_objective_total(C.byref(prob), _p(_g(gamma)), _p(st.rho), _p(st.u), _p(st.v),
@@ -259,6 +262,11 @@ def objective(pb, gamma, st: State) -> float:
 def pressure_drop(pb, st: State) -> float:
     """J_p = sum_in p - sum_out p with p = rho / 3 (unweighted)."""
     return float(lib().orc_pressure_drop(C.byref(make_problem(pb)), _p(st.rho)))
+
+
+def energy_loss(pb, st: State) -> float:
+    """J_E = sum over inlet and outlet nodes of -n.u (p + |u|^2 / 2) (unweighted)."""
+    return float(lib().orc_energy_loss(C.byref(make_problem(pb)), _p(st.rho), _p(st.u), _p(st.v)))
 
 
 def dJdu(pb, gamma, st: State):
@@ -372,14 +380,18 @@ def unsteady_gradient(pb, gamma, n_steps: Optional[int] = None):
     return dict(J=J, dJdgamma=sens, state=st, adjoint=adj, traj=tr)
 
 
-def bc_flow(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, kT: float = 0.0, jb: float = 0.0):
+def bc_flow(n, pressure: bool, A: float, known: np.ndarray, unknown_mask, kT: float = 0.0, jb: float = 0.0,
+            jbv=None):
     """Least-squares adjoint boundary rule for one node (flow lattice); jb is the
-    boundary objective term added to every row."""
+    boundary objective term added to every row, jbv (9 values, optional) a term per
+    row."""
     L = lib()
     f = np.ascontiguousarray(known, dtype=np.float64).copy()
     um = (C.c_int * 9)(*[int(x) for x in unknown_mask])
     mult = np.zeros(2)
-    L.orc_bc_flow(int(n[0]), int(n[1]), int(pressure), float(A), float(kT), um, _p(f), _p(mult), float(jb))
+    jv = None if jbv is None else np.ascontiguousarray(jbv, dtype=np.float64)
+    L.orc_bc_flow(int(n[0]), int(n[1]), int(pressure), float(A), float(kT), um, _p(f), _p(mult), float(jb),
+                  None if jv is None else _p(jv))
     return f, mult
 
 

@@ -300,6 +300,7 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
     if (descs[d].real_type != LKS_REAL_F32) return bad("batched designs must be FP32");
     if (descs[d].steady) return bad("batched designs must be unsteady");
     if (descs[d].thermal) return bad("batched designs must be non-thermal");
+    if (descs[d].kappa_E != 0.0) return bad("batched designs: kappa_E must be 0");
     if (descs[d].lattice != LKS_LATTICE_D2Q9) return bad("batched designs must be D2Q9");
     if (descs[d].n_steps != P->n_steps) return bad("batched designs must share n_steps");
     fw[d] = (int)up(descs[d].nx, kAlignX);

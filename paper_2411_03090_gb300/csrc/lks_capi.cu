@@ -80,7 +80,7 @@ Layout make_layout(const lks_problem_desc* d) {
   L.stB = take(fb * L.nF);
   L.adA = take(fb * L.nA);
   L.adB = take(fb * L.nA);
-  L.jfwd = take(sizeof(double) * L.fwd_blocks);
+  L.jfwd = take(sizeof(double) * (L.fwd_blocks + 1));  // per-block partials, then the boundary objectives
   L.jobj = take(sizeof(double) * L.obj_blocks);
   L.jval = take(sizeof(double));
   L.status = take(sizeof(int));
@@ -353,7 +353,7 @@ int res_steps_for(lks_handle* h, bool adjoint, int cfg) {
 
 bool resident_wanted(lks_handle* h, bool adjoint) {
   if (h->d.exec_path == LKS_PATH_STEP || h->d.exec_path == LKS_PATH_COLUMN || !h->d.steady) return false;
-  if (lks_host::has_sources(h->d)) return false;  // the source terms are in the per-step kernels
+  if (lks_host::step_kernels_only(h->d)) return false;  // terms only the per-step kernels carry
   if (adjoint && h->d.thermal) return false;
   int coop = 0;
   cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, h->device);
@@ -492,7 +492,8 @@ lks_status launch_adj_resident(lks_handle* h, int n) {
 constexpr int kFwdNT = 640, kAdjNT = 640;
 
 bool tma_ok(lks_handle* h) {
-  return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr;
+  // the energy loss is carried by the plain per-step kernels only
+  return h->d.real_type == LKS_REAL_F32 && (h->d.nx % 4) == 0 && encode_fn() != nullptr && h->d.kappa_E == 0.0;
 }
 
 // Tensor map of one field (nx x ny floats) for boxes of bw x bh, cached per handle.
@@ -528,7 +529,7 @@ int persistent_grid(lks_handle* h, K kern, int nt, size_t smem, int ntiles) {
 // Warp-column kernels: asked for, or the lattice has at least four column tiles per
 // SM (below that the per-tile TMA kernels, with fewer edge tiles, are faster).
 bool use_col(lks_handle* h) {
-  if (lks_host::has_sources(h->d)) return false;  // the source terms are in the per-step kernels
+  if (lks_host::step_kernels_only(h->d)) return false;  // terms only the per-step kernels carry
   if (h->d.exec_path == LKS_PATH_COLUMN) return true;
   if (h->d.exec_path == LKS_PATH_STEP) return false;  // the per-tile kernels, as asked
   const long long tiles = (long long)((h->d.nx + C2_W - 1) / C2_W) * ((h->d.ny + Col2Geo<C2_R>::H - 1) / Col2Geo<C2_R>::H);
@@ -1068,12 +1069,14 @@ lks_status forward_impl(lks_handle* h, const void* gamma_dev, double* J_dev) {
   R* T = d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr;
   if ((st = launch_objective<R>(h, u, v, T, jobj)) != LKS_OK) return st;
   int n2 = d.steady ? 0 : L.fwd_blocks;
-  if (d.steady && d.kappa_p != 0.0) {  // + kappa_p J_p in the first (unused) forward partial
-    pressure_drop_kernel<R><<<1, NTHREADS, 0, h->stream>>>(state_ptr<R>(h, h->cur, 0), make_geom(d), make_coef<R>(d),
-                                                           jfwd);
+  if ((d.steady && d.kappa_p != 0.0) || d.kappa_E != 0.0) {
+    // + kappa_p J_p + kappa_E J_E of the final level, after the forward partials (the
+    // per-step kernels summed the energy loss of levels 1 .. n - 1 into them)
+    boundary_objective_kernel<R><<<1, NTHREADS, 0, h->stream>>>(state_ptr<R>(h, h->cur, 0), u, v, make_geom(d),
+                                                                make_coef<R>(d), jfwd + n2);
     CKH(h, cudaGetLastError());
     h->launches++;
-    n2 = 1;
+    n2 += 1;
   }
   reduce_partials_kernel<<<1, NTHREADS, 0, h->stream>>>(jobj, L.obj_blocks, jfwd, n2, jval);
   CKH(h, cudaGetLastError());

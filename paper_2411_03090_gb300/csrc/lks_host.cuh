@@ -44,6 +44,8 @@ inline int elementwise_blocks(size_t n) { return (int)std::min<size_t>((n + 255)
 inline bool has_sources(const lks_problem_desc& d) {
   return d.beta_bar != 0.0 || d.kappa_Q != 0.0 || d.gb[0] != 0.0 || d.gb[1] != 0.0;
 }
+// Terms that only the per-step kernels carry: the thermal sources and the energy loss.
+inline bool step_kernels_only(const lks_problem_desc& d) { return has_sources(d) || d.kappa_E != 0.0; }
 
 inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   auto bad = [&](const char* m) {
@@ -61,6 +63,7 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
     if (!(d->nu > 0.0 && d->nu < 0.5)) return bad("nu must lie in (0, 0.5)");
     if (!(d->alpha_bar >= 0.0) || !(d->q_alpha > 0.0)) return bad("alpha_bar >= 0 and q_alpha > 0 required");
     if (!d->steady || d->thermal || has_sources(*d)) return bad("D3Q19: steady, non-thermal problems only");
+    if (d->kappa_E != 0.0) return bad("D3Q19: kappa_E must be 0");
     if (d->n_steps < 1 || d->n_adj < 1) return bad("n_steps and n_adj must be >= 1");
     if (d->res_steps != 0) return bad("D3Q19: res_steps must be 0");
     if (d->exec_path < LKS_PATH_AUTO || d->exec_path > LKS_PATH_COLUMN) return bad("bad exec_path");
@@ -93,6 +96,10 @@ inline lks_status check_desc(const lks_problem_desc* d, std::string* why) {
   if (d->res_steps < 0 || d->res_steps > 3) return bad("res_steps must lie in 0..3");
   if (!std::isfinite(d->kappa_p)) return bad("kappa_p must be finite");
   if (d->kappa_p != 0.0 && !d->steady) return bad("D2Q9: kappa_p != 0 needs a steady problem");
+  if (!std::isfinite(d->kappa_E)) return bad("kappa_E must be finite");
+  if (d->kappa_E != 0.0 && (d->exec_path == LKS_PATH_RESIDENT || d->exec_path == LKS_PATH_COLUMN))
+    return bad("the energy loss runs on the per-step kernels (exec_path AUTO or STEP)");
+  if (d->kappa_E != 0.0 && !(d->rho_out > 0.0)) return bad("kappa_E != 0 needs rho_out > 0");
   if (!(d->tol >= 0.0) || !std::isfinite(d->tol)) return bad("tol must be >= 0");
   if (d->tol > 0.0) {
     if (!d->steady) return bad("tol > 0: steady problems only");
@@ -252,6 +259,7 @@ inline Coef<R> make_coef(const lks_problem_desc& d) {
   c.gb_y = (R)d.gb[1];
   c.T_ref = (R)d.T_ref;
   c.heat_q = (R)d.heat_q;
+  c.kappa_E = (R)d.kappa_E;
   for (int e = 0; e < 4; ++e) c.t_val[e] = (R)d.t_val[e];
   return c;
 }

@@ -76,6 +76,7 @@ struct Coef {
   R kappa_Q;           // weight of the heat-exchange objective -sum beta_gamma (1 - T)
   R gb_x, gb_y, T_ref; // Boussinesq force G = g beta (T - T_ref) (Eq. boussinesqforce)
   R heat_q;            // heat flux q_w of the heated bottom segment
+  R kappa_E;           // weight of the energy loss J_E (Eq. objective_doublepipe); 0: none
 };
 
 // Edge maps of one lattice: 9 classes x 6 moments x 10 columns (lks_edge_moment_map),
@@ -91,6 +92,21 @@ __device__ __forceinline__ R edge_objective_term(const Geom& g, const Coef<R>& c
   if (ec == 1) return -c.kappa_p;
   if (ec == 0 && j >= g.in_y0 && j <= g.in_y1) return c.kappa_p;
   return R(0);
+}
+
+// Energy loss of one node (Eq. objective_doublepipe), kappa_E (-n.u) (p + |u|^2 / 2)
+// with p = (rho - rho_out) / 3 = (drho - drho_out) / 3 and dGamma = 1, on the inlet
+// nodes (left edge inside the inlet span, n = (-1, 0)) and the outlet nodes (right
+// edge inside the outlet span, n = (1, 0)), corners excluded; zero elsewhere.  FP64.
+template <typename R>
+__device__ __forceinline__ double energy_loss_node(const Geom& g, const Coef<R>& c, int i, int j, R drho, R u, R v) {
+  if (j < 1 || j > g.ny - 2) return 0.0;
+  double un;  // -n.u
+  if (i == 0 && j >= g.in_y0 && j <= g.in_y1) un = (double)u;
+  else if (i == g.nx - 1 && j >= g.out_y0 && j <= g.out_y1) un = -(double)u;
+  else return 0.0;
+  const double p = ((double)drho - (double)c.drho_out) / 3.0;
+  return (double)c.kappa_E * un * (p + 0.5 * ((double)u * (double)u + (double)v * (double)v));
 }
 
 // Edge-class index of the moment maps (see lks_edge_moment_map in lks.h).
@@ -392,6 +408,9 @@ __global__ void __launch_bounds__(NTHREADS) fwd_step_kernel(FwdArgs<R> a, Geom g
                        al * (uu * uu + vv * vv));
       if (TH) jloc += (double)(c.kappa_T * sT[sy * H2X + sx] + heat_objective(c, gmo, sT[sy * H2X + sx]));
     }
+    // energy loss of the old state on the inlet and outlet nodes of the tile
+    if (a.J_partial && c.kappa_E != R(0) && lx >= 1 && lx <= TX && ly >= 1 && ly <= TY && (i == 0 || i == nx - 1))
+      jloc += energy_loss_node(g, c, i, j, sr[q], uu, vv);
   }
   __syncthreads();
   if (a.J_partial) {
@@ -826,7 +845,18 @@ __global__ void __launch_bounds__(NTHREADS) adj_step_kernel(AdjArgs<R> a, Geom g
         if (flux) kT = kap * sT0[s2];
       }
       const R* M = a.emap + ec * 60;
-      const R jb = edge_objective_term(g, c, ec, j);
+      R jb = edge_objective_term(g, c, ec, j);
+      if (c.kappa_E != R(0)) {
+        // energy loss: kappa_E u in every row of an inlet node (d/dp of its
+        // integrand); on an outlet node 3 kappa_E (-3/2 u_n^2) (c_i.n) / rho_out, a
+        // row term along c.n like the heat-flux coupling -kappa~ T (c_i.n), whose
+        // response is column 9 of the map
+        if (ec == 0 && j >= g.in_y0 && j <= g.in_y1) jb += c.kappa_E * su0[s2];
+        if (ec == 1) {
+          const R un = su0[s2];
+          kT += R(3) * c.kappa_E * (R(1.5) * un * un) / (R(1) + c.drho_out);
+        }
+      }
 #pragma unroll
       for (int r = 0; r < 6; ++r) {
         R s = R(0);
@@ -878,21 +908,28 @@ __global__ void __launch_bounds__(NTHREADS) objective_kernel(const R* __restrict
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
 }
 
-// Static pressure drop of Eq. objective_pipebend, kappa_p J_p with
-// J_p = 1/3 (sum of rho over the inlet nodes - over the outlet nodes) (p = rho / 3,
-// dGamma = 1; inlet: left face inside the inlet span, corners excluded; outlet: the
-// pressure nodes).  One block; drho = rho - 1 is the stored density.
+// Boundary objectives of one state: the static pressure drop of Eq.
+// objective_pipebend, kappa_p J_p with J_p = 1/3 (sum of rho over the inlet nodes -
+// over the outlet nodes) (p = rho / 3, dGamma = 1; inlet: left face inside the inlet
+// span, corners excluded; outlet: the pressure nodes), plus the energy loss
+// kappa_E J_E on the same nodes (energy_loss_node).  One block; drho = rho - 1 is the
+// stored density.
 template <typename R>
-__global__ void __launch_bounds__(NTHREADS) pressure_drop_kernel(const R* __restrict__ drho, Geom g, Coef<R> c,
-                                                                 double* out) {
+__global__ void __launch_bounds__(NTHREADS) boundary_objective_kernel(const R* __restrict__ drho,
+                                                                      const R* __restrict__ u,
+                                                                      const R* __restrict__ v, Geom g, Coef<R> c,
+                                                                      double* out) {
   __shared__ double red[NTHREADS / 32];
-  double acc = 0.0;
+  double acc = 0.0, accE = 0.0;
   for (int j = 1 + threadIdx.x; j < g.ny - 1; j += NTHREADS) {
-    if (j >= g.in_y0 && j <= g.in_y1) acc += 1.0 + (double)drho[(size_t)j * g.nx];
-    if (j >= g.out_y0 && j <= g.out_y1) acc -= 1.0 + (double)drho[(size_t)j * g.nx + g.nx - 1];
+    const size_t l = (size_t)j * g.nx, r = l + g.nx - 1;
+    if (j >= g.in_y0 && j <= g.in_y1) acc += 1.0 + (double)drho[l];
+    if (j >= g.out_y0 && j <= g.out_y1) acc -= 1.0 + (double)drho[r];
+    if (c.kappa_E != R(0))
+      accE += energy_loss_node(g, c, 0, j, drho[l], u[l], v[l]) + energy_loss_node(g, c, g.nx - 1, j, drho[r], u[r], v[r]);
   }
-  const double s = block_sum(acc, red);
-  if (threadIdx.x == 0) *out = (double)c.kappa_p * s / 3.0;
+  const double s = block_sum((double)c.kappa_p * acc / 3.0 + accE, red);
+  if (threadIdx.x == 0) *out = s;
 }
 
 // Deterministic sum of n partials (one block) plus an optional second array.

@@ -18,7 +18,7 @@ import torch
 
 from . import _build
 
-LKS_DESC_VERSION = 2
+LKS_DESC_VERSION = 3
 STATUS = {0: "ok", 1: "invalid argument", 2: "workspace", 3: "CUDA error", 4: "unstable",
           5: "not converged", 6: "timeout", 7: "calls out of order"}
 REAL = {"f32": 0, "f64": 1}
@@ -60,6 +60,7 @@ class Desc(C.Structure):
         ("beta_bar", C.c_double), ("q_beta", C.c_double), ("kappa_Q", C.c_double),
         ("gb", C.c_double * 2), ("T_ref", C.c_double),
         ("heat_x0", C.c_int32), ("heat_x1", C.c_int32), ("heat_q", C.c_double),
+        ("kappa_E", C.c_double),
     ]
 
 
@@ -186,6 +187,7 @@ def make_desc(pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = 
     d.gb[0], d.gb[1] = float(getattr(pb, "gb_x", 0.0)), float(getattr(pb, "gb_y", 0.0))
     d.heat_x0, d.heat_x1 = int(getattr(pb, "heat_x0", 0)), int(getattr(pb, "heat_x1", -1))
     d.heat_q = float(getattr(pb, "heat_q", 0.0))
+    d.kappa_E = float(getattr(pb, "kappa_E", 0.0))
     for name in ("nu", "alpha_bar", "q_alpha", "u_max", "pulse_mean", "pulse_amp", "pulse_period",
                  "rho_out", "K_f", "K_s", "q_K", "kappa_T", "kappa_p"):
         setattr(d, name, float(getattr(pb, name)))

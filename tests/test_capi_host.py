@@ -104,6 +104,21 @@ def test_descriptor_validation():
     bad = lks.make_desc(pb.with_(kappa_p=1.0, steady=False))  # unsteady D2Q9: not with kappa_p
     with pytest.raises(lks.LKSError):
         lks.workspace_size(bad)
+    # the energy loss: D2Q9, steady or unsteady, on the per-step kernels
+    for st in (True, False):
+        ok = lks.make_desc(pb.with_(kappa_E=1.0, steady=st))
+        assert ok.kappa_E == 1.0 and lks.workspace_size(ok) > 0
+    for path in ("column", "resident"):
+        with pytest.raises(lks.LKSError):
+            lks.workspace_size(lks.make_desc(pb.with_(kappa_E=1.0), path=path))
+    bad = lks.make_desc(pb.with_(kappa_E=1.0))
+    bad.kappa_E = float("inf")
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(bad)
+    d3 = lks.make_desc(inputs.config4())
+    d3.kappa_E = 1.0  # D3Q19: not built
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(d3)
     d3 = lks.make_desc(inputs.config4())
     assert d3.kappa_p == 1.0 and lks.workspace_size(d3) > 0
     d3.kappa_p = float("nan")

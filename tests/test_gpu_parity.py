@@ -416,6 +416,81 @@ def test_natural_convection_cavity_on_the_gpu():
     assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) >= 0.99, a / b
 
 
+def _energy_loss_geometry(nx=31, steps=4000, **kw):
+    """The 31 x 31 check geometry of Sec. 2.6 (inlet and outlet over rows 10..20,
+    nu = 0.1, gamma = 0.1 in the centre circle of radius 5, 0.9 elsewhere) with the
+    energy loss in J; nx = 32 adds a column so that FP32 would take the per-tile TMA
+    kernels, which do not carry the energy loss, without the step-kernel gate."""
+    n, nu = 31, 0.1
+    pb = inputs.Problem(nx=nx, ny=n, nu=nu, alpha_bar=1e3 * nu, u_max=nu / 10.0, in_y0=10, in_y1=20,
+                        out_y0=10, out_y1=20, n_steps=steps, n_adj=steps, kappa_E=1.0, **kw)
+    yy, xx = np.mgrid[0:n, 0:nx]
+    return pb, np.where((xx - 15) ** 2 + (yy - 15) ** 2 <= 25.0, 0.1, 0.9)
+
+
+@pytest.mark.parametrize("nx", [31, 32])
+@pytest.mark.parametrize("real,jtol,gtol", [("f64", 1e-12, 1e-9), ("f32", 1e-5, 2e-3)])
+def test_energy_loss_steady_matches_oracle(real, jtol, gtol, nx):
+    """Energy loss (Eq. objective_doublepipe, kappa_E = 1) on the check geometry,
+    steady, 4000 + 4000 steps: J (dissipation + energy loss) and dJ/dgamma equal the
+    oracle's (FP64 to round-off; FP32 within its rounding), and the march ran on the
+    per-step kernels."""
+    pb, g = _energy_loss_geometry(nx)
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    q = s.query()
+    assert q.device_status == 0 and q.fwd_path == 1 and q.adj_path == 1
+    ref = O.steady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= jtol * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= gtol
+    # the energy loss's share is not negligible: without it J and the gradient move
+    r0 = O.steady_gradient(pb.with_(kappa_E=0.0), g)
+    assert rel_l2(r0["dJdgamma"], ref["dJdgamma"]) > 10 * gtol
+
+
+@pytest.mark.parametrize("real,jtol,gtol", [("f64", 1e-11, 1e-9), ("f32", 1e-5, 2e-3)])
+def test_energy_loss_unsteady_matches_oracle(real, jtol, gtol):
+    """The time integral of the energy loss under a pulsing inlet (u_in(t) = u_max
+    sin(2 pi t / 400), 1200 steps from rest, nx = 32): J summed over levels 1..n and
+    the unsteady gradient equal the oracle's."""
+    pb, g = _energy_loss_geometry(32, 1200, steady=False, pulse_mean=0.0, pulse_amp=1.0, pulse_period=400.0)
+    s = LKS(pb, real=real)
+    J, grad = s.gradient(torch.from_numpy(g))
+    assert s.query().device_status == 0
+    ref = O.unsteady_gradient(pb, g)
+    assert abs(J.item() - ref["J"]) <= jtol * abs(ref["J"])
+    assert rel_l2(grad.double().cpu().numpy(), ref["dJdgamma"]) <= gtol
+
+
+def test_energy_loss_gradient_agrees_with_central_differences_on_the_gpu():
+    """Steady energy loss on the 31 x 31 check geometry (FP64 GPU path): the J_E share
+    of the gradient (kappa_E = 1 minus 0) against central differences of J_E computed
+    on the GPU (tolerance marches warm-started from the converged state), along the
+    centre line: ratios 0.75..1.1, as the oracle pin finds."""
+    pb, g = _energy_loss_geometry(31, 25000)
+    _, g1 = LKS(pb, real="f64").gradient(torch.from_numpy(g))
+    _, g0 = LKS(pb.with_(kappa_E=0.0), real="f64").gradient(torch.from_numpy(g))
+    adj = (g1 - g0).cpu().numpy()
+    w = [LKS(pb.with_(n_steps=1000, kappa_E=ke), real="f64", tol=1e-15, max_steps=400000, warm_start=True)
+         for ke in (1.0, 0.0)]
+    gt = torch.from_numpy(g)
+    w[0].lks_forward(gt)
+    base = [x.clone() for x in w[0].get_state()]
+    eps = 1e-3
+    for i in (6, 10, 15, 21, 25):
+        v = []
+        for sg in (1, -1):
+            gg = torch.from_numpy(g.copy())
+            gg[15, i] += sg * eps
+            jj = []
+            for h in w:
+                h.set_state(gt, base[0], base[1], base[2])
+                jj.append(h.lks_forward(gg).item())
+            v.append(jj[0] - jj[1])
+        fd = (v[0] - v[1]) / (2 * eps)
+        assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
+
+
 def test_forced_convection_check_on_the_gpu():
     """Sec. 2.6's forced-convection check (`inputs.forced_convection_check`: T fixed on
     the inlet edge, adiabatic elsewhere, heat source Q = beta_gamma (1 - T) and the

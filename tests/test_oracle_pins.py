@@ -384,6 +384,111 @@ def test_pressure_drop_gradient_matches_central_differences():
         assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
 
 
+# --------------------------------------------------------------------------------------
+# Energy loss (Eq. objective_doublepipe) and its adjoint boundary terms
+# --------------------------------------------------------------------------------------
+@pytest.mark.parametrize("nu", [0.1, 0.315])
+def test_energy_loss_of_poiseuille_flow(nu):
+    """Steady Poiseuille flow (the exact discrete state of test_poiseuille_exact): the
+    inlet and outlet profiles are equal, so the kinetic parts cancel and the loss of
+    total pressure is the pressure drop times the flux, J_E = (8 nu u_max (nx - 1) / H^2)
+    sum_j U(j) over the inlet nodes, the power the pressure drop spends against the
+    viscous stresses.  kappa_E weights it into J."""
+    pb = inputs.poiseuille(33, 17, nu=nu, u_max=0.02)
+    g = np.ones((pb.ny, pb.nx))
+    st, res, _ = O.forward_to_steady(pb, g, tol=1e-14, max_steps=60000, chunk=1000)
+    assert res < 1e-13
+    H = pb.ny - 1
+    y = np.arange(1, pb.ny - 1)
+    U = 4 * pb.u_max * y * (H - y) / H ** 2
+    dp = 8 * nu * pb.u_max * (pb.nx - 1) / H ** 2
+    assert abs(O.energy_loss(pb, st) - dp * U.sum()) <= 1e-9 * dp * U.sum()
+    assert abs(O.objective(pb.with_(kappa_E=3.0), g, st) - O.objective(pb, g, st)
+               - 3.0 * O.energy_loss(pb, st)) <= 1e-12
+
+
+def test_per_row_boundary_term_matches_lstsq():
+    """A boundary objective term that differs per row (the energy loss on the outlet,
+    proportional to c_i . n) enters Eq. afboundaryp's right-hand side row by row: the
+    oracle's fill equals numpy's lstsq with the vector added, and unlike a constant it
+    moves the filled f~."""
+    A = 0.2
+    n = (1, 0)
+    rng = np.random.default_rng(14)
+    unknown = np.array([1 if CX[k] > 0 else 0 for k in range(9)])
+    f = rng.standard_normal(9) * (1 - unknown)
+    jbv = -0.4 * np.array([CX[k] for k in range(9)], dtype=float)
+    sol, mult = O.bc_flow(n, True, A, f, unknown, jbv=jbv)
+    M, N = _residual_matrix_flow(n, A, True)
+    U = np.where(unknown)[0]
+    K = np.where(unknown == 0)[0]
+    x, *_ = np.linalg.lstsq(np.concatenate([M[:, U], N], 1), -M[:, K] @ f[K] - jbv, rcond=None)
+    np.testing.assert_allclose(sol[U], x[:len(U)], atol=1e-12)
+    np.testing.assert_allclose(mult, x[len(U):], atol=1e-12)
+    s0, _ = O.bc_flow(n, True, A, f, unknown)
+    assert np.abs(sol[U] - s0[U]).max() > 1e-3
+
+
+def _verification_geometry(steps, **kw):
+    """The non-thermal check of Sec. 2.6 at 31 x 31 (as in the pressure-drop pin)."""
+    n, nu = 31, 0.1
+    pb = inputs.Problem(nx=n, ny=n, nu=nu, alpha_bar=1e3 * nu, u_max=nu / 10.0, in_y0=10, in_y1=20,
+                        out_y0=10, out_y1=20, n_steps=steps, n_adj=steps, **kw)
+    yy, xx = np.mgrid[0:n, 0:n]
+    return pb, np.where((xx - 15) ** 2 + (yy - 15) ** 2 <= 25.0, 0.1, 0.9)
+
+
+def test_energy_loss_gradient_matches_central_differences():
+    """Steady energy loss on the 31 x 31 check geometry: ALKS with the energy-loss
+    row terms (the J_E share: kappa_E = 1 minus 0) against central differences of J_E
+    (eps = 1e-3) along the centre line, ratios 0.75..1.1 as for the pressure drop.
+    With the absolute pressure rho / 3 in place of the gauge pressure, the outlet row
+    term p_bar c.n, whose true effect is p_bar times the change of the net mass flux
+    (zero), gives ratios of 1.7..5."""
+    steps = 25000
+    pb, g = _verification_geometry(steps)
+    st, res, _, _ = O.forward(pb, g, steps)
+    assert res < 1e-11
+    _, s0, _ = O.steady_adjoint(pb, g, st, steps)
+    _, s1, r1 = O.steady_adjoint(pb.with_(kappa_E=1.0), g, st, steps)
+    assert r1 < 1e-9
+    adj = s1 - s0
+    eps = 1e-3
+    for i in (6, 10, 15, 21, 25):
+        v = []
+        for sg in (1, -1):
+            gg = g.copy()
+            gg[15, i] += sg * eps
+            v.append(O.energy_loss(pb, O.forward(pb, gg, steps)[0]))
+        fd = (v[0] - v[1]) / (2 * eps)
+        assert 0.75 <= adj[15, i] / fd <= 1.1, (i, adj[15, i], fd)
+
+
+def test_unsteady_energy_loss_gradient_matches_central_differences():
+    """The paper's double-pipe objective is the time integral of J_E under a pulsing
+    inlet.  On the check geometry with u_in(t) = u_max sin(2 pi t / 400) over three
+    periods from rest, the unsteady ALKS gradient of sum_t J_E (kappa_E = 1 minus 0)
+    agrees with central differences of that sum (eps = 1e-3) along the centre line:
+    ratios 0.65..1.2, cosine >= 0.99."""
+    pb, g = _verification_geometry(1200, steady=False, pulse_mean=0.0, pulse_amp=1.0, pulse_period=400.0)
+    r1 = O.unsteady_gradient(pb.with_(kappa_E=1.0), g)
+    r0 = O.unsteady_gradient(pb, g)
+    adj = r1["dJdgamma"] - r0["dJdgamma"]
+    eps = 1e-3
+    a, b = [], []
+    for i in (6, 10, 15, 21, 25):
+        v = []
+        for sg in (1, -1):
+            gg = g.copy()
+            gg[15, i] += sg * eps
+            v.append(O.unsteady_gradient(pb.with_(kappa_E=1.0), gg)["J"] - O.unsteady_gradient(pb, gg)["J"])
+        a.append(adj[15, i])
+        b.append((v[0] - v[1]) / (2 * eps))
+    a, b = np.array(a), np.array(b)
+    assert a @ b / np.linalg.norm(a) / np.linalg.norm(b) >= 0.99
+    assert np.all((a / b > 0.65) & (a / b < 1.2)), a / b
+
+
 @pytest.mark.slow
 @pytest.mark.parametrize("nu", [0.1, 0.315])
 def test_steady_alks_agrees_with_finite_differences(nu):
