@@ -46,6 +46,11 @@
  * density / normal velocity on edges; corner rules; objective) are restated next
  * to the code they affect.
  *
+ * Parity unpinned: the outlet row term of the energy loss (its kinetic part, the
+ * only part left under the gauge-pressure reading).  At the check geometry's
+ * velocities its share of the gradient lies below what central differences resolve
+ * (dropping it moves the ALKS / FD ratios by 3e-4), so no test fixes it.
+ *
  * Storage: every field is an array of nx*ny doubles, node (i, j) at j*nx + i
  * (x fastest).  Node (i, j) sits at x = i, y = j; the domain edges carry nodes.
  */
