@@ -56,7 +56,7 @@ METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e
 # exists.  Multiplied by the nodes of a launch they give roofline.traffic.
 TRAFFIC_BYTES_PER_NODE = {
     "adj3c_kernel": 747.2e6 / 7077888,   # the 192^3 duct, 4 + 4 steps
-    "fwd3c_kernel": 219.6e6 / 7077888,
+    "fwd3p_kernel": 219.3e6 / 7077888,
     "adj_col_kernel<true>": None,        # changed since its last capture
     "fwd_col2_kernel<10>": 425.4e6 / 16777216,  # the 4096^2 channel, 4 + 4 steps
 }
@@ -712,7 +712,7 @@ def measure(pb, args, dev, flush, steps, warmup, world, clocks=None, e2e=True):
     if three_d:
         tma3 = pb.nx % 4 == 0
         adj_k = ("adj3c_kernel" if st.adj_path == 3 else "adj3t_kernel") if tma3 else "adj3_kernel<float>"
-        fwd_k = ("fwd3c_kernel" if st.fwd_path == 3 else "fwd3t_kernel") if tma3 else "fwd3_kernel<float>"
+        fwd_k = ("fwd3p_kernel" if st.fwd_path == 3 else "fwd3t_kernel") if tma3 else "fwd3_kernel<float>"
 
     def traffic(k):
         b = TRAFFIC_BYTES_PER_NODE.get(k)

@@ -877,31 +877,23 @@ __device__ __forceinline__ void push_all3(float base, float bx, float by, float 
 }
 
 // ---------------------------------------------------------------------------------
-// Warp-column D3Q19 forward (FP32)
+// Warp-column D3Q19 tiles (FP32)
 // ---------------------------------------------------------------------------------
-// Lanes run along x (one column each; lanes 2..29 write, so a tile is 28 columns
-// wide), warp w owns row y0 - 1 + w (rows y0 .. y0 + NYC3 - 1 are outputs; the two
-// outer warps are halo rows whose pushes feed the tile), and the CTA marches a
-// chunk of z planes.  The fields drho, u, v, w of each plane arrive by 3-D tensor
-// copies into a ring of NSLC3 slots (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)),
-// requested three planes before they are first read; 1/(1+alpha) of an output node
-// is one global load, issued a plane ahead.  For each source plane z a lane
-// computes the 19 pushed values of its node (push_all3, Eq. feq2) and routes each:
-//   - the 9 links with c_y = 0 stay in the warp: c_x by shuffle, c_z through a
-//     register ring of destination planes (plane d receives links 5, 11, 14 from
-//     plane d - 1, links 0, 1, 2 from plane d, links 6, 12, 13 from plane d + 1);
-//   - the 10 links with c_y = +-1 go to the neighbouring warps through a shared
-//     exchange buffer indexed by destination plane mod NXS3.
-// One barrier per plane separates the exchange writes from the gather of plane
-// z - 1, which is complete then.  A slot of the exchange buffer is rewritten two
-// steps after it is read, with that barrier in between; values pushed from nodes
-// outside the lattice are never read (the face rules skip such links, and every
-// source of an interior node is inside).
+// The column kernels (the paired forward fwd3p_kernel and the adjoint adj3c_kernel)
+// share one tiling: 28 x 8 output tiles, a halo row above and below, and a chunk of
+// z planes marched by each CTA.  The staged fields of each plane arrive by 3-D tensor
+// copies into a ring of plane slots (box 36 x (NYC3 + 4) from (x0 - 4, y0 - 2)).  The
+// pushed values of a source plane are routed at once: links with c_y = 0 stay in
+// the warp (c_x by shuffle, c_z through a register ring of destination planes), the
+// others go to the neighbouring rows through a shared exchange buffer indexed by
+// destination plane mod NXS3.  One barrier per plane separates the exchange writes
+// from the gather of plane z - 1, which is complete then.  A slot of the exchange
+// buffer is rewritten two steps after it is read, with that barrier in between.
 constexpr int CX3 = 28, NYC3 = 8, NWC3 = NYC3 + 2, NTC3 = 32 * NWC3;
 constexpr int CBW3 = CX3 + 8, CBH3 = NYC3 + 4, CBOX3 = CBW3 * CBH3;
 constexpr int CFS3 = (CBOX3 * 4 + 127) / 128 * 128 / 4;  // field stride in a ring slot (128-byte multiple)
-constexpr int NFC3 = 4;                                   // ring fields: drho, u, v, w
-constexpr int NSLC3 = 8;                                  // plane ring slots (planes z - 2 .. z + 5)
+constexpr int NFC3 = 4;                                   // forward ring fields: drho, u, v, w
+constexpr int NSLC3 = 8;                                  // adjoint ring slots (planes z - 2 .. z + 5)
 constexpr int NXS3 = 4;                                   // exchange slots (destination planes mod 4)
 constexpr int XW3 = CX3;                                  // exchange row: the output columns x0 .. x0 + 27
 constexpr int NXL3 = 10;                                  // links with c_y != 0
@@ -934,10 +926,6 @@ __host__ __device__ constexpr int face_link3(int ff, int q, bool unknown) {
   return -1;
 }
 
-__host__ __device__ constexpr size_t fwd3c_smem() {
-  return sizeof(float) * ((size_t)NSLC3 * NFC3 * CFS3 + (size_t)NXS3 * NYC3 * NXL3 * XW3) + 8 * NSLC3 + 128;
-}
-
 // Sums of the pushed increments at a node on exactly one face, normal along axis A
 // with sign n (the face rules of the gather): s0 over links with c_A = 0, sp over
 // links pointing out of the lattice (c_A n > 0).  Off the normal's axis every
@@ -953,250 +941,6 @@ __device__ __forceinline__ void face_sums3(const float (&F)[19], int n, float& s
   });
   s0 = z;
   sp = n > 0 ? p : m;
-}
-
-__global__ void __launch_bounds__(NTC3, 2) fwd3c_kernel(const __grid_constant__ Maps3F maps,
-                                                        const __grid_constant__ Fwd3TArgs a, Geom3 g,
-                                                        Coef3<float> c) {
-  using R = float;
-  extern __shared__ unsigned char smem_raw3[];
-  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLC3][NFC3][CFS3]
-  R* ex = ring + NSLC3 * NFC3 * CFS3;                              // [NXS3][NYC3][NXL3][XW3]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NXL3 * XW3);
-  if (lks::timed_out_before(a.status)) return;
-  if (!lks::tma_layout_ok(ring, bar, a.status)) return;
-  const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
-  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, nz);
-  const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = x0 - 2 + lane, j = y0 - 1 + warp;
-  const int bx = lane + 2, by = warp + 1;  // the node's column and row in the staged box
-  const bool out_node = lane >= 2 && lane < 2 + CX3 && i < nx && warp >= 1 && warp <= NYC3 && j < ny;
-  const bool in_xy = i >= 0 && i < nx && j >= 0 && j < ny;
-  // Every thread's node, and every node whose push it reads, is off the x and y faces
-  // (lanes 1 .. 30 and warps 0 .. NYC3 + 1 push for the outputs).
-  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
-  // every thread's row, and every row whose push it reads, is off the y faces
-  const bool tile_yfast = y0 >= 2 && y0 + NYC3 <= ny - 2;
-  static_assert((NSLC3 & (NSLC3 - 1)) == 0, "ring slots index by mask");
-  auto slot = [&](int p) { return (p - pbase) & (NSLC3 - 1); };
-  auto issue = [&](int p) {
-    const int sl = slot(p);
-    lks::mbar_expect_tx(&bar[sl], NFC3 * CBOX3 * 4);
-    for (int f = 0; f < NFC3; ++f)
-      tma_load_3d(ring + (sl * NFC3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
-  };
-  int waited = pbase - 1, issued = pbase - 1;
-  auto wait = [&](int p) {
-    const bool ok = lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
-    if (ok) waited = p;
-    return ok;
-  };
-  auto drain_and_fail = [&]() {
-    raise_status(a.status, 6);
-    if (threadIdx.x == 0)
-      for (int p = waited + 1; p <= issued; ++p) lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLC3) & 1);
-  };
-  if (threadIdx.x == 0) {
-    for (int sl = 0; sl < NSLC3; ++sl) lks::mbar_init(&bar[sl], 1);
-    lks::fence_mbar_init();
-    lks::fence_proxy_async();
-  }
-  __syncthreads();
-  for (int p = pbase; p < pbase + NSLC3 && p <= plast; ++p) {
-    if (threadIdx.x == 0) issue(p);
-    issued = p;
-  }
-  for (int p = pbase; p <= pbase + 4 && p <= plast; ++p)
-    if (!wait(p)) {
-      drain_and_fail();
-      return;
-    }
-  // zs: ring slot of the plane z being pushed; plane z + k sits in slot zs + k (mod NSLC3)
-  int zs = 2;
-  auto slk = [&](int k) { return (zs + k) & (NSLC3 - 1); };
-  // field f of plane z + k at row offset dy and column offset dx from the node
-  auto at = [&](int f, int k, int dy, int dx) {
-    return ring[(slk(k) * NFC3 + f) * CFS3 + (by + dy) * CBW3 + bx + dx];
-  };
-  // exchange row `row` of destination plane p (slots by p mod NXS3)
-  auto xslot = [&](int p, int row) { return ex + ((p & (NXS3 - 1)) * NYC3 + row) * NXL3 * XW3; };
-  // 1/(1+alpha) of the output node at plane p (loaded one plane before the gather reads it)
-  auto binv_at = [&](int p) {
-    return (out_node && p >= 0 && p < nz) ? __ldg(a.binv + gidx(g, i, j, p)) : R(0);
-  };
-  R inv_n = binv_at(z0 - 1);  // for the gather of plane z - 1 at step z
-
-  // the node's u, v, w at planes z - 1 (m), z (c), z + 1 (p), and drho at z and z + 1
-  R um = at(1, -1, 0, 0), vm = at(2, -1, 0, 0), wm = at(3, -1, 0, 0);
-  R dc = at(0, 0, 0, 0), uc = at(1, 0, 0, 0), vc = at(2, 0, 0, 0), wc = at(3, 0, 0, 0);
-  R dp = at(0, 1, 0, 0), up = at(1, 1, 0, 0), vp = at(2, 1, 0, 0), wp = at(3, 1, 0, 0);
-  R Am[9], Ac[9], Ap[9];  // links with c_y = 0 arriving at planes z - 1, z, z + 1 (slot oslot3(k))
-#pragma unroll
-  for (int q = 0; q < 9; ++q) Am[q] = Ac[q] = Ap[q] = R(0);
-
-  // One plane: push of plane z, then gather of plane z - 1.  MODE 0 (fast): no node
-  // of the tile at planes z and z - 1 lies on a face (and all of them are inside);
-  // MODE 1: only the x faces can occur (rows and planes are off the y and z faces);
-  // MODE 2: any face.
-  auto plane_step = [&](int z, auto mode_tag) {
-    constexpr int MODE = decltype(mode_tag)::value;
-    constexpr bool FAST = MODE == 0, XO = MODE == 1;
-    const bool src = FAST || (XO ? (i >= 0 && i < nx) : (in_xy && z >= 0 && z < nz));
-    R gr[3][3];  // gr[d][a] = d u_d / d x_a
-    gr[0][0] = (__shfl_down_sync(0xffffffffu, uc, 1) - __shfl_up_sync(0xffffffffu, uc, 1)) * R(0.5);
-    gr[1][0] = (__shfl_down_sync(0xffffffffu, vc, 1) - __shfl_up_sync(0xffffffffu, vc, 1)) * R(0.5);
-    gr[2][0] = (__shfl_down_sync(0xffffffffu, wc, 1) - __shfl_up_sync(0xffffffffu, wc, 1)) * R(0.5);
-    gr[0][1] = (at(1, 0, 1, 0) - at(1, 0, -1, 0)) * R(0.5);
-    gr[1][1] = (at(2, 0, 1, 0) - at(2, 0, -1, 0)) * R(0.5);
-    gr[2][1] = (at(3, 0, 1, 0) - at(3, 0, -1, 0)) * R(0.5);
-    gr[0][2] = (up - um) * R(0.5);
-    gr[1][2] = (vp - vm) * R(0.5);
-    gr[2][2] = (wp - wm) * R(0.5);
-    if constexpr (!FAST) {
-      const bool on[3] = {i == 0 || i == nx - 1, !XO && (j == 0 || j == ny - 1), !XO && (z == 0 || z == nz - 1)};
-      if (src && (on[0] || on[1] || on[2])) {  // faces: one-sided differences and continuity
-#pragma unroll
-        for (int d = 0; d < 3; ++d) {
-          const R* f0 = ring + (slk(0) * NFC3 + 1 + d) * CFS3 + by * CBW3 + bx;
-          if (on[0]) gr[d][0] = dax(f0, 1, i, nx);
-          if (on[1]) gr[d][1] = dax(f0, CBW3, j, ny);
-          if (on[2]) gr[d][2] = daz<R>([&](int dz) { return at(1 + d, dz, 0, 0); }, z, nz);
-        }
-        const int faces = (int)on[0] + (int)on[1] + (int)on[2];
-        if (faces == 1) {
-          if (on[0]) gr[0][0] = -(gr[1][1] + gr[2][2]);
-          else if (on[1]) gr[1][1] = -(gr[0][0] + gr[2][2]);
-          else gr[2][2] = -(gr[0][0] + gr[1][1]);
-        } else {
-#pragma unroll
-          for (int d = 0; d < 3; ++d)
-            if (on[d]) gr[d][d] = R(0);
-        }
-      }
-    }
-    const R e0 = R(-1.5) * (uc * uc + vc * vc + wc * wc);
-    const R bxv = R(3) * uc, byv = R(3) * vc, bzv = R(3) * wc;
-    const R Qxx = R(4.5) * uc * uc + c.A * (R(2) * gr[0][0]);
-    const R Qyy = R(4.5) * vc * vc + c.A * (R(2) * gr[1][1]);
-    const R Qzz = R(4.5) * wc * wc + c.A * (R(2) * gr[2][2]);
-    const R Qxy = R(9) * uc * vc + R(2) * c.A * (gr[0][1] + gr[1][0]);
-    const R Qxz = R(9) * uc * wc + R(2) * c.A * (gr[0][2] + gr[2][0]);
-    const R Qyz = R(9) * vc * wc + R(2) * c.A * (gr[1][2] + gr[2][1]);
-    const R inv_c = inv_n;  // 1/(1+alpha) of node (i, j, z - 1)
-    inv_n = binv_at(z);
-    R* const xr_m = xslot(z - 1, 0) + lane - 2;  // exchange rows of the destination planes
-    R* const xr_c = xslot(z, 0) + lane - 2;
-    R* const xr_p = xslot(z + 1, 0) + lane - 2;
-    const bool w_up = src && warp < NYC3, w_dn = src && warp >= 2;  // c_y = +1 / -1 lands on an output row
-    // destination lane lane + c_x is an output column (lanes 2 .. 29)
-    const bool xl_m = lane >= 3 && lane <= CX3 + 2, xl_c = lane >= 2 && lane <= CX3 + 1,
-               xl_p = lane >= 1 && lane <= CX3;
-    R PV[19];
-    push_all3(dc + e0, bxv, byv, bzv, Qxx, Qyy, Qzz, Qxy, Qxz, Qyz, PV);
-    static_for<0, 19>([&](auto kk) {
-      constexpr int k = decltype(kk)::value;
-      constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
-      const R val = FAST ? PV[k] : (src ? PV[k] : R(0));
-      if constexpr (cy != 0) {
-        // destination row warp - 1 + cy of the exchange
-        R* const xr = (cz < 0 ? xr_m : (cz == 0 ? xr_c : xr_p)) + ((cy > 0 ? 0 : -2) * NXL3 + yslot3(k)) * XW3 + cx;
-        if ((cy > 0 ? w_up : w_dn) && (cx < 0 ? xl_m : (cx == 0 ? xl_c : xl_p))) xr[warp * NXL3 * XW3] = val;
-      } else {
-        R v;
-        if constexpr (cx > 0) v = __shfl_up_sync(0xffffffffu, val, 1);  // sent by the lane on the left
-        else if constexpr (cx < 0) v = __shfl_down_sync(0xffffffffu, val, 1);
-        else v = val;
-        if constexpr (cz < 0) Am[oslot3(k)] = v;
-        else if constexpr (cz == 0) Ac[oslot3(k)] = v;
-        else Ap[oslot3(k)] = v;
-      }
-    });
-    __syncthreads();  // plane z's exchange writes are in; plane z - 1 is complete
-    if (z + NSLC3 - 3 <= plast && z + NSLC3 - 3 > issued) {  // the slot of plane z - 3 is free
-      if (threadIdx.x == 0) issue(z + NSLC3 - 3);
-      issued = z + NSLC3 - 3;
-    }
-    // ---- gather of node (i, j, z - 1) ----
-    const int zd = z - 1;
-    if (out_node && zd >= z0 && zd < z1) {
-      R F[19];
-      const R* xr = xslot(zd, warp - 1) + lane - 2;
-      static_for<0, 19>([&](auto kk) {
-        constexpr int k = decltype(kk)::value;
-        if constexpr (c3(k, 1) != 0) F[k] = xr[yslot3(k) * XW3];
-        else F[k] = Am[oslot3(k)];
-      });
-      int n0 = 0, n1 = 0, n2 = 0, faces = 0;
-      if constexpr (!FAST) {
-        n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
-        if constexpr (!XO) {
-          n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
-          n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
-        }
-        faces = abs(n0) + abs(n1) + abs(n2);
-      }
-      R drn, uo[3] = {R(0), R(0), R(0)};
-      if (FAST || faces == 0) {
-        R sm, mx, my, mz;
-        fwd_moments3(F, sm, mx, my, mz);
-        drn = sm;
-        uo[0] = mx * inv_c;
-        uo[1] = my * inv_c;
-        uo[2] = mz * inv_c;
-      } else if (faces >= 2) {
-        const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
-        const int kn = (zd == 0) ? 1 : (zd == nz - 1 ? -1 : 0);
-        drn = at(0, kn - 1, jn, 0);
-      } else {
-        R s0, sp;
-        if (n0 != 0) face_sums3<0>(F, n0, s0, sp);
-        else if (n1 != 0) face_sums3<1>(F, n1, s0, sp);
-        else face_sums3<2>(F, n2, s0, sp);
-        // the known populations' weights in s0 + 2 sp sum to one, so the pushed
-        // values (not increments) give rho directly
-        if (n0 == 1) {
-          drn = c.drho_out;
-          uo[0] = (s0 + R(2) * sp) - c.drho_out;
-        } else {
-          if (n0 == -1) {  // inlet profile in FP32 (FP64 division is slow on this GPU)
-            const float y = (float)j / (float)(ny - 1), zz = (float)zd / (float)(nz - 1);
-            uo[0] = ((float)c.u_max * 16.f) * (y * (1.f - y)) * (zz * (1.f - zz));
-          }
-          drn = (s0 + R(2) * sp) - (uo[0] * R(n0) + uo[1] * R(n1) + uo[2] * R(n2));
-        }
-      }
-      const size_t o = gidx(g, i, j, zd);
-      a.out[0][o] = drn;
-      a.out[1][o] = uo[0];
-      a.out[2][o] = uo[1];
-      a.out[3][o] = uo[2];
-      const R m = uo[0] * uo[0] + uo[1] * uo[1] + uo[2] * uo[2];
-      if (!(m <= R(0.25))) raise_status(a.status, 4);
-    }
-    // ---- rotate: the destination sets and the node's planes ----
-#pragma unroll
-    for (int q = 0; q < 9; ++q) {
-      Am[q] = Ac[q];
-      Ac[q] = Ap[q];
-    }
-    um = uc, vm = vc, wm = wc;
-    dc = dp, uc = up, vc = vp, wc = wp;
-    if (z + 2 <= plast) dp = at(0, 2, 0, 0), up = at(1, 2, 0, 0), vp = at(2, 2, 0, 0), wp = at(3, 2, 0, 0);
-    zs = (zs + 1) & (NSLC3 - 1);
-  };
-
-  for (int z = z0 - 1; z <= z1; ++z) {
-    if (z + 2 <= plast && z + 2 > waited && !wait(z + 2)) {
-      drain_and_fail();
-      return;
-    }
-    const bool zin = z >= 2 && z <= nz - 2;
-    if (tile_fast && zin) plane_step(z, std::integral_constant<int, 0>{});
-    else if (tile_yfast && zin) plane_step(z, std::integral_constant<int, 1>{});
-    else plane_step(z, std::integral_constant<int, 2>{});
-  }
 }
 
 struct Adj3TArgs {
@@ -1755,6 +1499,425 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
   }
 }
 
+// ---------------------------------------------------------------------------------
+// Paired-column D3Q19 kernels (FP32)
+// ---------------------------------------------------------------------------------
+// The tiles (CX3 x NYC3 outputs), z chunks, staged boxes and exchange protocol of
+// the warp-column kernels, with two nodes per lane and two rows per warp:
+//   - a lane owns an even column and the odd one after it (pair q of a half-warp owns
+//     columns x0 - 2 + 2q and x0 - 1 + 2q; pairs 1..14 write, 28 columns);
+//   - warp w owns rows y0 - 1 + 2w (lanes 0..15, the upper row) and y0 + 2w (lanes
+//     16..31); rows y0 .. y0 + NYC3 - 1 are outputs, the first warp's upper row and
+//     the last warp's lower row are halo.
+// Both nodes of a lane run as packed FP32 pairs (one f32x2 instruction for the two),
+// a node pair is loaded and stored as one 8-byte vector, and the per-lane work of the
+// plane loop (addresses, tests, rings) is shared by two nodes.  A routed value stays
+// in the lane between the pair's columns, moves by one shuffle between the lanes of
+// a row and by shuffles across the half-warps between the warp's two rows; only the
+// five links that leave the warp (one sign of c_y per row) pass through the shared
+// exchange.  The per-node formulas are those of the warp-column kernels.
+constexpr int NWP3 = 5, NTP3 = 32 * NWP3;
+// Plane ring of the paired forward: planes z - 2 .. z + 4 (seven slots keep three
+// CTAs of it on an SM).
+constexpr int NSLP3 = 7;
+static_assert(2 * NWP3 == NYC3 + 2, "two rows per warp, one halo row above and below the tile");
+static_assert(CX3 % 2 == 0 && XW3 % 2 == 0 && CFS3 % 2 == 0 && CBW3 % 2 == 0, "node pairs are 8-byte aligned");
+constexpr unsigned kFull3 = 0xffffffffu;
+// Links with c_y != 0 in classes by (c_x, c_z), two links (c_y = +1, -1) each:
+// 0: (0, 0), 1: (1, 0), 2: (-1, 0), 3: (0, 1), 4: (0, -1).
+constexpr int NCB3 = 5;
+__host__ __device__ constexpr int cbx3(int b) { return b == 1 ? 1 : (b == 2 ? -1 : 0); }
+__host__ __device__ constexpr int cbz3(int b) { return b == 3 ? 1 : (b == 4 ? -1 : 0); }
+__host__ __device__ constexpr int cls_of3(int cx, int cz) { return cz == 0 ? (cx == 0 ? 0 : (cx > 0 ? 1 : 2)) : (cz > 0 ? 3 : 4); }
+// Register slots of the values a node keeps for one destination plane (the links that
+// stay in the warp), grouped by c_z of the link:
+//   c_z = 0:  links (0,0,0), (1,0,0), (-1,0,0), classes 0, 1, 2 from the other row
+//   c_z = +1: links (0,0,1), (1,0,1), (-1,0,1), class 3
+//   c_z = -1: links (0,0,-1), (1,0,-1), (-1,0,-1), class 4
+constexpr int NRS3 = 14;
+__host__ __device__ constexpr int rs3(int cx, int cz) { return (cz == 0 ? 0 : (cz > 0 ? 6 : 10)) + (cx == 0 ? 0 : (cx > 0 ? 1 : 2)); }
+__host__ __device__ constexpr int rsb3(int b) { return b <= 2 ? 3 + b : (b == 3 ? 9 : 13); }
+
+using F2 = float2;
+__device__ __forceinline__ F2 p2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ F2 add2(F2 a, F2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ F2 sub2(F2 a, F2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+__device__ __forceinline__ F2 mul2(F2 a, F2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ F2 fma2(F2 a, F2 b, F2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ F2 zero2() { return make_float2(0.f, 0.f); }
+template <int C>
+__device__ __forceinline__ float& cmp2(F2& v) {
+  if constexpr (C == 0) return v.x;
+  else return v.y;
+}
+template <int C>
+__device__ __forceinline__ float cmp2(const F2& v) {
+  if constexpr (C == 0) return v.x;
+  else return v.y;
+}
+__device__ __forceinline__ F2 ld2s(const float* p) { return *reinterpret_cast<const F2*>(p); }
+__device__ __forceinline__ void st2s(float* p, F2 v) { *reinterpret_cast<F2*>(p) = v; }
+
+// At each column c of the pair, v taken at column c + CX of the same row.
+template <int CX>
+__device__ __forceinline__ F2 recv_x3(F2 v) {
+  if constexpr (CX > 0) return make_float2(v.y, __shfl_down_sync(kFull3, v.x, 1));
+  else if constexpr (CX < 0) return make_float2(__shfl_up_sync(kFull3, v.y, 1), v.x);
+  else return v;
+}
+// At each column c of the pair, v taken at column c + CX of the warp's other row
+// (oth: the lane of the same pair in that row).
+template <int CX>
+__device__ __forceinline__ F2 recv_xo3(F2 v, int oth) {
+  if constexpr (CX > 0) return make_float2(__shfl_sync(kFull3, v.y, oth), __shfl_sync(kFull3, v.x, oth + 1));
+  else if constexpr (CX < 0) return make_float2(__shfl_sync(kFull3, v.y, oth - 1), __shfl_sync(kFull3, v.x, oth));
+  else return make_float2(__shfl_sync(kFull3, v.x, oth), __shfl_sync(kFull3, v.y, oth));
+}
+
+// Class sums of the values a node pair gathered (interior rule), the groupings of
+// fwd_moments3 / adj_moments3: the links with c_y = 0 by slot, and per y class b the
+// sum S_b = F(c_y = +1) + F(c_y = -1) and difference D_b = F(c_y = +1) - F(c_y = -1).
+struct ClassSums3 {
+  F2 F000, ax, dx, az, dz, e1, e2, f1, f2;
+};
+__device__ __forceinline__ ClassSums3 class_sums3(const F2 (&A)[NRS3]) {
+  ClassSums3 s;
+  const F2 Fp00 = A[rs3(1, 0)], Fm00 = A[rs3(-1, 0)], F00p = A[rs3(0, 1)], F00m = A[rs3(0, -1)];
+  const F2 Fp0p = A[rs3(1, 1)], Fm0p = A[rs3(-1, 1)], Fp0m = A[rs3(1, -1)], Fm0m = A[rs3(-1, -1)];
+  s.F000 = A[rs3(0, 0)];
+  s.ax = add2(Fp00, Fm00);
+  s.dx = sub2(Fp00, Fm00);
+  s.az = add2(F00p, F00m);
+  s.dz = sub2(F00p, F00m);
+  s.e1 = add2(Fp0p, Fm0m);  // xz diagonals with c_x c_z = +1
+  s.e2 = add2(Fp0m, Fm0p);  // and with c_x c_z = -1
+  s.f1 = sub2(Fp0p, Fm0m);
+  s.f2 = sub2(Fp0m, Fm0p);
+  return s;
+}
+// The 19 gathered values of component C of the pair in link order (the face rules);
+// Fp[b] / Fm[b] are class b's links with c_y = +1 / -1.
+template <int C>
+__device__ __forceinline__ void gathered19(const F2 (&A)[NRS3], const F2 (&Fp)[NCB3], const F2 (&Fm)[NCB3],
+                                           float (&F)[19]) {
+  static_for<0, 19>([&](auto kk) {
+    constexpr int k = decltype(kk)::value;
+    constexpr int cx = c3(k, 0), cy = c3(k, 1), cz = c3(k, 2);
+    if constexpr (cy == 0) F[k] = cmp2<C>(A[rs3(cx, cz)]);
+    else if constexpr (cy > 0) F[k] = cmp2<C>(Fp[cls_of3(cx, cz)]);
+    else F[k] = cmp2<C>(Fm[cls_of3(cx, cz)]);
+  });
+}
+
+// Paired-column forward.  Every node pair computes its 19 pushed values (Eq. feq2,
+// push_all3's link-pair form) and routes value k to x + c_k: the links with c_y = 0
+// inside the row, one sign of c_y to the warp's other row by shuffles (the upper row
+// sends c_y = +1, the lower row c_y = -1), the other sign through the exchange.
+// drho, u, v, w of each plane arrive by tensor copies into the ring; 1/(1+alpha) of
+// an output pair is one 8-byte load, a plane ahead.
+__host__ __device__ constexpr size_t fwd3p_smem() {
+  return sizeof(float) * ((size_t)NSLP3 * NFC3 * CFS3 + (size_t)NXS3 * NYC3 * NCB3 * XW3) + 8 * NSLP3 + 128;
+}
+
+__global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ Maps3F maps,
+                                                        const __grid_constant__ Fwd3TArgs a, Geom3 g,
+                                                        Coef3<float> c) {
+  using R = float;
+  extern __shared__ unsigned char smem_raw3[];
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLP3][NFC3][CFS3]
+  R* ex = ring + NSLP3 * NFC3 * CFS3;                              // [NXS3][NYC3][NCB3][XW3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NCB3 * XW3);
+  if (lks::timed_out_before(a.status)) return;
+  if (!lks::tma_layout_ok(ring, bar, a.status)) return;
+  const int nx = g.nx, ny = g.ny, nz = g.nz;
+  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
+  const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, nz);
+  const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int h = lane >> 4, q = lane & 15, t = 2 * warp + h;
+  const int i0 = x0 - 2 + 2 * q, j = y0 - 1 + t;
+  const int bx = 2 + 2 * q, by = 1 + t;
+  const int xl = 2 * q - 2;
+  const int oth = lane ^ 16;
+  const bool in_xy = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
+  const bool out_node = q >= 1 && q <= 14 && i0 < nx && t >= 1 && t <= NYC3 && j < ny;
+  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  // sent inside the warp: the class value with c_y = +1 (upper row) / -1 (lower row)
+  const F2 sy2 = p2(h ? -1.f : 1.f);
+  auto slot = [&](int p) { return (p - pbase) % NSLP3; };
+  auto issue = [&](int p) {
+    const int sl = slot(p);
+    lks::mbar_expect_tx(&bar[sl], NFC3 * CBOX3 * 4);
+    for (int f = 0; f < NFC3; ++f)
+      tma_load_3d(ring + (sl * NFC3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+  };
+  int waited = pbase - 1, issued = pbase - 1;
+  auto wait = [&](int p) {
+    const bool ok = lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLP3) & 1);
+    if (ok) waited = p;
+    return ok;
+  };
+  auto drain_and_fail = [&]() {
+    raise_status(a.status, 6);
+    if (threadIdx.x == 0)
+      for (int p = waited + 1; p <= issued; ++p) lks::mbar_wait(&bar[slot(p)], ((p - pbase) / NSLP3) & 1);
+  };
+  if (threadIdx.x == 0) {
+    for (int sl = 0; sl < NSLP3; ++sl) lks::mbar_init(&bar[sl], 1);
+    lks::fence_mbar_init();
+    lks::fence_proxy_async();
+  }
+  __syncthreads();
+  for (int p = pbase; p < pbase + NSLP3 && p <= plast; ++p) {
+    if (threadIdx.x == 0) issue(p);
+    issued = p;
+  }
+  for (int p = pbase; p <= pbase + 4 && p <= plast; ++p)
+    if (!wait(p)) {
+      drain_and_fail();
+      return;
+    }
+  int zs = 2;  // ring slot of the plane z being pushed; plane z + k sits in slot zs + k
+  auto slk = [&](int k) {  // k in -2 .. 2
+    const int sk = zs + k;
+    return sk >= NSLP3 ? sk - NSLP3 : (sk < 0 ? sk + NSLP3 : sk);
+  };
+  // field f (0 drho, 1 u, 2 v, 3 w) of plane z + k at row offset dy, the pair's even column
+  auto fp = [&](int f, int k, int dy) { return ring + (slk(k) * NFC3 + f) * CFS3 + (by + dy) * CBW3 + bx; };
+  auto at2 = [&](int f, int k, int dy) { return ld2s(fp(f, k, dy)); };
+  auto xrow = [&](int p, int od) { return ex + ((p & (NXS3 - 1)) * NYC3 + od) * (NCB3 * XW3); };
+  // 1/(1+alpha) of the output pair at plane p (loaded one plane before the gather reads it)
+  auto binv_at = [&](int p) {
+    return (out_node && p >= 0 && p < nz) ? __ldg(reinterpret_cast<const float2*>(a.binv + gidx(g, i0, j, p)))
+                                          : zero2();
+  };
+  F2 inv_n = binv_at(z0 - 1);
+  // the pair's u, v, w at planes z - 1 (m), z (c), z + 1 (p), and drho at z and z + 1
+  F2 um = at2(1, -1, 0), vm = at2(2, -1, 0), wm = at2(3, -1, 0);
+  F2 dc = at2(0, 0, 0), uc = at2(1, 0, 0), vc = at2(2, 0, 0), wc = at2(3, 0, 0);
+  F2 dp = at2(0, 1, 0), up = at2(1, 1, 0), vp = at2(2, 1, 0), wp = at2(3, 1, 0);
+  F2 Am[NRS3], Ac[NRS3], Ap[NRS3];  // values for the destination planes z - 1, z, z + 1
+#pragma unroll
+  for (int s = 0; s < NRS3; ++s) Am[s] = Ac[s] = Ap[s] = zero2();
+
+  auto plane_step = [&](int z, auto fast_tag) {
+    constexpr bool FAST = decltype(fast_tag)::value;
+    const bool src = FAST || (in_xy && z >= 0 && z < nz);
+    // velocity gradient, g[d][a] = f(x + e_a) - f(x - e_a) of u_d (twice d u_d / d x_a)
+    F2 gr[3][3];
+    {
+      const F2 uvw[3] = {uc, vc, wc}, zp[3] = {up, vp, wp}, zm[3] = {um, vm, wm};
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        const float l = __shfl_up_sync(kFull3, uvw[d].y, 1), r = __shfl_down_sync(kFull3, uvw[d].x, 1);
+        gr[d][0] = sub2(make_float2(uvw[d].y, r), make_float2(l, uvw[d].x));
+        gr[d][1] = sub2(at2(1 + d, 0, 1), at2(1 + d, 0, -1));
+        gr[d][2] = sub2(zp[d], zm[d]);
+      }
+    }
+    if constexpr (!FAST) {
+      // faces: one-sided differences, then continuity (one face: the normal derivative
+      // of the normal velocity; two or more: zero normal derivatives)
+      static_for<0, 2>([&](auto cc) {
+        constexpr int CC = decltype(cc)::value;
+        const int i = i0 + CC;
+        const bool on[3] = {i == 0 || i == nx - 1, j == 0 || j == ny - 1, z == 0 || z == nz - 1};
+        if (src && (on[0] || on[1] || on[2])) {
+#pragma unroll
+          for (int d = 0; d < 3; ++d) {
+            const R* f0 = fp(1 + d, 0, 0) + CC;
+            if (on[0]) {
+              const int s = i == 0 ? 1 : -1;
+              cmp2<CC>(gr[d][0]) = (float)s * ((4.f * f0[s] - 3.f * f0[0]) - f0[2 * s]);
+            }
+            if (on[1]) {
+              const int s = j == 0 ? 1 : -1;
+              cmp2<CC>(gr[d][1]) = (float)s * ((4.f * f0[s * CBW3] - 3.f * f0[0]) - f0[2 * s * CBW3]);
+            }
+            if (on[2]) {
+              const int s = z == 0 ? 1 : -1;
+              cmp2<CC>(gr[d][2]) = (float)s * ((4.f * fp(1 + d, s, 0)[CC] - 3.f * f0[0]) - fp(1 + d, 2 * s, 0)[CC]);
+            }
+          }
+          const int faces = (int)on[0] + (int)on[1] + (int)on[2];
+          if (faces == 1) {
+            if (on[0]) cmp2<CC>(gr[0][0]) = -(cmp2<CC>(gr[1][1]) + cmp2<CC>(gr[2][2]));
+            else if (on[1]) cmp2<CC>(gr[1][1]) = -(cmp2<CC>(gr[0][0]) + cmp2<CC>(gr[2][2]));
+            else cmp2<CC>(gr[2][2]) = -(cmp2<CC>(gr[0][0]) + cmp2<CC>(gr[1][1]));
+          } else {
+#pragma unroll
+            for (int d = 0; d < 3; ++d)
+              if (on[d]) cmp2<CC>(gr[d][d]) = 0.f;
+          }
+        }
+      });
+    }
+    // Eq. feq2: base = drho + e0 with e0 = -3/2 |u|^2, b = 3u,
+    // Q_aa = 9/2 u_a^2 + A (2 d_a u_a), Q_ab = 9 u_a u_b + 2A (d_b u_a + d_a u_b)
+    const F2 A2 = p2(c.A);
+    const F2 uu = mul2(uc, uc), vv = mul2(vc, vc), ww = mul2(wc, wc);
+    F2 bs = fma2(p2(-1.5f), add2(add2(uu, vv), ww), dc);
+    F2 Qxx = fma2(p2(4.5f), uu, mul2(A2, gr[0][0]));
+    F2 Qyy = fma2(p2(4.5f), vv, mul2(A2, gr[1][1]));
+    F2 Qzz = fma2(p2(4.5f), ww, mul2(A2, gr[2][2]));
+    F2 Qxy = fma2(p2(9.f), mul2(uc, vc), mul2(A2, add2(gr[0][1], gr[1][0])));
+    F2 Qxz = fma2(p2(9.f), mul2(uc, wc), mul2(A2, add2(gr[0][2], gr[2][0])));
+    F2 Qyz = fma2(p2(9.f), mul2(vc, wc), mul2(A2, add2(gr[1][2], gr[2][1])));
+    F2 bxv = uc, byv = vc, bzv = wc;  // b / 3
+    if constexpr (!FAST) {
+      if (!src) bs = Qxx = Qyy = Qzz = Qxy = Qxz = Qyz = bxv = byv = bzv = zero2();
+    }
+    // pushed values by link pair (push_all3): w1 b = u / 6, w2 b = u / 12
+    const F2 w0 = p2((float)w3d(0)), w1 = p2((float)w3d(1)), w2 = p2((float)w3d(7));
+    const F2 w1b = mul2(w1, bs), w2b = mul2(w2, bs);
+    const F2 b1x = mul2(p2(3.f * (float)w3d(1)), bxv), b1y = mul2(p2(3.f * (float)w3d(1)), byv),
+             b1z = mul2(p2(3.f * (float)w3d(1)), bzv);
+    const F2 b2x = mul2(p2(0.5f), b1x), b2y = mul2(p2(0.5f), b1y), b2z = mul2(p2(0.5f), b1z);
+    const F2 tX = fma2(w1, Qxx, w1b), tY = fma2(w1, Qyy, w1b), tZ = fma2(w1, Qzz, w1b);
+    const F2 dXZ = fma2(w2, add2(Qxx, Qzz), w2b), qXZ = mul2(w2, Qxz);
+    const F2 dXY = fma2(w2, add2(Qxx, Qyy), w2b), qXY = mul2(w2, Qxy);
+    const F2 dYZ = fma2(w2, add2(Qyy, Qzz), w2b), qYZ = mul2(w2, Qyz);
+    // links with c_y = 0 (value at x goes to x + c): c_z = 0 to plane z, +1 to z + 1, -1 to z - 1
+    {
+      const F2 sp = add2(dXZ, qXZ), sm = sub2(dXZ, qXZ), c1 = add2(b2x, b2z), c2 = sub2(b2x, b2z);
+      Ac[rs3(0, 0)] = mul2(w0, bs);
+      Ac[rs3(1, 0)] = recv_x3<-1>(add2(tX, b1x));
+      Ac[rs3(-1, 0)] = recv_x3<1>(sub2(tX, b1x));
+      Ap[rs3(0, 1)] = add2(tZ, b1z);
+      Am[rs3(0, -1)] = sub2(tZ, b1z);
+      Ap[rs3(1, 1)] = recv_x3<-1>(add2(sp, c1));   // (1, 0, 1)
+      Am[rs3(-1, -1)] = recv_x3<1>(sub2(sp, c1));  // (-1, 0, -1)
+      Am[rs3(1, -1)] = recv_x3<-1>(add2(sm, c2));  // (1, 0, -1)
+      Ap[rs3(-1, 1)] = recv_x3<1>(sub2(sm, c2));   // (-1, 0, 1)
+    }
+    // y classes: P(c_x, +-1, c_z) = G_b +- H_b; one sign to the other row, the other
+    // through the exchange
+    const F2 G[NCB3] = {tY, add2(dXY, b2x), sub2(dXY, b2x), add2(dYZ, b2z), sub2(dYZ, b2z)};
+    const F2 sb1y = mul2(sy2, b1y), sb2y = mul2(sy2, b2y), sqxy = mul2(sy2, qXY), sqyz = mul2(sy2, qYZ);
+    const F2 sH[NCB3] = {sb1y, add2(sb2y, sqxy), sub2(sb2y, sqxy), add2(sb2y, sqyz), sub2(sb2y, sqyz)};
+    const int td = h ? t + 1 : t - 1;  // destination row (in the tile) of the exchanged links
+    const bool xw = td >= 1 && td <= NYC3;
+    static_for<0, NCB3>([&](auto bb) {
+      constexpr int b = decltype(bb)::value, cx = cbx3(b), cz = cbz3(b);
+      const F2 r = recv_xo3<-cx>(add2(G[b], sH[b]), oth);
+      if constexpr (cz == 0) Ac[rsb3(b)] = r;
+      else if constexpr (cz > 0) Ap[rsb3(b)] = r;
+      else Am[rsb3(b)] = r;
+      const F2 v = sub2(G[b], sH[b]);
+      R* const row = xrow(z + cz, td - 1) + b * XW3;
+      if (xw) {
+        if constexpr (cx == 0) {
+          if (q >= 1 && q <= 14) st2s(row + xl, v);
+        } else {
+          const int d0 = xl + cx;  // destination column of the even column
+          if (d0 >= 0 && d0 < XW3) row[d0] = v.x;
+          if (d0 + 1 >= 0 && d0 + 1 < XW3) row[d0 + 1] = v.y;
+        }
+      }
+    });
+    const F2 inv_c = inv_n;  // 1/(1+alpha) of the pair at plane z - 1
+    inv_n = binv_at(z);
+    __syncthreads();  // plane z's exchange writes are in; plane z - 1 is complete
+    if (z + NSLP3 - 3 <= plast && z + NSLP3 - 3 > issued) {  // the slot of plane z - 3 is free
+      if (threadIdx.x == 0) issue(z + NSLP3 - 3);
+      issued = z + NSLP3 - 3;
+    }
+    // ---- gather of the pair at plane z - 1 ----
+    const int zd = z - 1;
+    if (out_node && zd >= z0 && zd < z1) {
+      const R* xr = xrow(zd, t - 1) + xl;
+      F2 E[NCB3], S[NCB3], D[NCB3];
+      static_for<0, NCB3>([&](auto bb) {
+        constexpr int b = decltype(bb)::value;
+        E[b] = ld2s(xr + b * XW3);
+        S[b] = add2(Am[rsb3(b)], E[b]);
+        D[b] = sub2(E[b], Am[rsb3(b)]);  // the upper row's F(+1) - F(-1); the lower row's negative
+      });
+      const ClassSums3 s = class_sums3(Am);
+      F2 drn = add2(add2(add2(s.F000, add2(s.ax, s.az)), add2(s.e1, s.e2)),
+                    add2(add2(S[0], add2(S[1], S[2])), add2(S[3], S[4])));
+      const F2 ysg = p2(h ? -1.f : 1.f);
+      F2 uo0 = mul2(add2(add2(s.dx, add2(s.f1, s.f2)), sub2(S[1], S[2])), inv_c);
+      F2 uo1 = mul2(mul2(ysg, add2(add2(D[0], add2(D[1], D[2])), add2(D[3], D[4]))), inv_c);
+      F2 uo2 = mul2(add2(add2(s.dz, sub2(s.f1, s.f2)), sub2(S[3], S[4])), inv_c);
+      if constexpr (!FAST) {
+        F2 Fp[NCB3], Fm[NCB3];
+#pragma unroll
+        for (int b = 0; b < NCB3; ++b) {
+          Fp[b] = h ? Am[rsb3(b)] : E[b];
+          Fm[b] = h ? E[b] : Am[rsb3(b)];
+        }
+        static_for<0, 2>([&](auto cc) {
+          constexpr int CC = decltype(cc)::value;
+          const int i = i0 + CC;
+          const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
+          const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
+          const int n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+          const int faces = abs(n0) + abs(n1) + abs(n2);
+          if (faces >= 2) {
+            // wall edge or corner: density from the node one step inward along the
+            // side-wall normals, no velocity
+            const int jn = (j == 0) ? 1 : (j == ny - 1 ? -1 : 0);
+            const int kn = (zd == 0) ? 1 : (zd == nz - 1 ? -1 : 0);
+            cmp2<CC>(drn) = fp(0, kn - 1, jn)[CC];
+            cmp2<CC>(uo0) = cmp2<CC>(uo1) = cmp2<CC>(uo2) = 0.f;
+          } else if (faces == 1) {
+            float F[19];
+            gathered19<CC>(Am, Fp, Fm, F);
+            R s0, sp;
+            if (n0 != 0) face_sums3<0>(F, n0, s0, sp);
+            else if (n1 != 0) face_sums3<1>(F, n1, s0, sp);
+            else face_sums3<2>(F, n2, s0, sp);
+            R u0 = 0.f;
+            R dr;
+            // the known populations' weights in s0 + 2 sp sum to one, so the pushed
+            // values give rho directly
+            if (n0 == 1) {
+              dr = c.drho_out;
+              u0 = (s0 + R(2) * sp) - c.drho_out;
+            } else {
+              if (n0 == -1) {  // inlet profile in FP32
+                const float y = (float)j / (float)(ny - 1), zz = (float)zd / (float)(nz - 1);
+                u0 = ((float)c.u_max * 16.f) * (y * (1.f - y)) * (zz * (1.f - zz));
+              }
+              dr = (s0 + R(2) * sp) - u0 * R(n0);
+            }
+            cmp2<CC>(drn) = dr;
+            cmp2<CC>(uo0) = u0;
+            cmp2<CC>(uo1) = cmp2<CC>(uo2) = 0.f;
+          }
+        });
+      }
+      const size_t o = gidx(g, i0, j, zd);
+      st2s(a.out[0] + o, drn);
+      st2s(a.out[1] + o, uo0);
+      st2s(a.out[2] + o, uo1);
+      st2s(a.out[3] + o, uo2);
+      const F2 m = fma2(uo0, uo0, fma2(uo1, uo1, mul2(uo2, uo2)));
+      if (!(m.x <= R(0.25)) || !(m.y <= R(0.25))) raise_status(a.status, 4);
+    }
+    // ---- rotate: the destination sets and the pair's planes ----
+#pragma unroll
+    for (int s = 0; s < NRS3; ++s) {
+      Am[s] = Ac[s];
+      Ac[s] = Ap[s];
+    }
+    um = uc, vm = vc, wm = wc;
+    dc = dp, uc = up, vc = vp, wc = wp;
+    if (z + 2 <= plast) dp = at2(0, 2, 0), up = at2(1, 2, 0), vp = at2(2, 2, 0), wp = at2(3, 2, 0);
+    zs = zs + 1 == NSLP3 ? 0 : zs + 1;
+  };
+
+  for (int z = z0 - 1; z <= z1; ++z) {
+    if (z + 2 <= plast && z + 2 > waited && !wait(z + 2)) {
+      drain_and_fail();
+      return;
+    }
+    if (tile_fast && z >= 2 && z <= nz - 2) plane_step(z, std::true_type{});
+    else plane_step(z, std::false_type{});
+  }
+}
+
 // ------------------------------------------------------------------------------------
 // Pointwise kernels: material, objective source, objective, sensitivity
 // ------------------------------------------------------------------------------------
@@ -1965,16 +2128,16 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
         ta[b].status = reinterpret_cast<int*>(c.ws + L.status);
       }
       if (col) {
-        CK3(c, cudaFuncSetAttribute(fwd3c_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3c_smem()));
+        CK3(c, cudaFuncSetAttribute(fwd3p_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fwd3p_smem()));
         int dev = 0, sms = 0, per_sm = 0;
         CK3(c, cudaGetDevice(&dev));
         CK3(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd3c_kernel, NTC3, fwd3c_smem()));
+        CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd3p_kernel, NTP3, fwd3p_smem()));
         const int zc = col_chunk3(d, std::max(1, sms * per_sm));
         ta[0].zc = ta[1].zc = zc;
         const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + zc - 1) / zc);
         for (int s = 0; s < d.n_steps; ++s) {
-          fwd3c_kernel<<<grid, NTC3, fwd3c_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
+          fwd3p_kernel<<<grid, NTP3, fwd3p_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
           CK3(c, cudaGetLastError());
           ++*c.launches;
           cur = 1 - cur;
