@@ -106,7 +106,9 @@ typedef struct {
     int32_t n_steps;          /* forward steps                                       */
     int32_t n_adj;            /* steady: adjoint iterations; unsteady: ignored       */
     int32_t checkpoint_every; /* unsteady: K > 0 recompute segments of K steps from
-                                 snapshots; 0 keeps every level (plain form)         */
+                                 snapshots (two segment stores in the workspace:
+                                 the recompute of a segment overlaps the adjoint of
+                                 the next); 0 keeps every level (plain form)         */
     int32_t snapshot_type;    /* lks_snap_type of the checkpoint snapshots           */
     int32_t exec_path;        /* lks_exec_path: 0 automatic, 1 one kernel launch per
                                  step, 2 resident persistent march (steady problems
@@ -222,7 +224,11 @@ lks_status lks_workspace_size(const lks_problem_desc *desc, size_t *bytes);
 /* Creates a handle on the current device.  workspace_dev: caller-owned device
  * memory of at least lks_workspace_size bytes, 256-byte aligned, kept alive and
  * unused by the caller until lks_destroy.  stream: a cudaStream_t (NULL = legacy
- * default stream).  Host allocation of the handle itself only. */
+ * default stream).  Host allocation of the handle itself only; for unsteady
+ * problems with checkpoint_every > 0 the handle also creates one non-blocking
+ * stream and five events of its own (destroyed by lks_destroy), on which
+ * alks_adjoint runs the segment recomputations (see alks_adjoint).  Returns
+ * LKS_ERR_CUDA if they cannot be created. */
 lks_status lks_create(const lks_problem_desc *desc, void *workspace_dev, size_t bytes,
                       void *stream, lks_handle **out);
 
@@ -245,7 +251,11 @@ lks_status lks_forward(lks_handle *h, const void *gamma_dev, double *J_dev);
  * march from the terminal condition (Eqs. afinitial, aginitial) with the
  * generalized-inverse edge rule.  Steady: n_adj iterations on the final state.
  * Unsteady: backward over all levels (recomputing segments from snapshots when
- * checkpoint_every > 0) and the sensitivity accumulated on the way.
+ * checkpoint_every > 0) and the sensitivity accumulated on the way.  With
+ * checkpoints, segment s - 1 is recomputed on the handle's own stream while the
+ * adjoint marches segment s on the caller's stream (events order the two; the
+ * results are those of recomputing and marching one segment after the other); the
+ * call returns with the caller's stream waiting for all of that work.
  * Steady D2Q9 with tol > 0: iterations in chunks of n_adj, each followed by one
  * measured iteration (the relative change of u~, as for lks_forward), until the
  * change is <= tol or max_steps iterations have run (LKS_ERR_NOT_CONVERGED, the

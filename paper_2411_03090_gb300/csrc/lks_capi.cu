@@ -41,7 +41,7 @@ inline size_t align_up(size_t x) { return (x + kAlign - 1) / kAlign * kAlign; }
 struct Layout {
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, sens = 0, sens64 = 0;
   size_t jfwd = 0, jobj = 0, jval = 0, status = 0, emap = 0, flags = 0, mat = 0, chg = 0;
-  size_t traj = 0, snaps = 0, scales = 0, seg = 0, lvl_stage = 0, total = 0;
+  size_t traj = 0, snaps = 0, scales = 0, seg = 0, seg2 = 0, lvl_stage = 0, total = 0;
   int lvl16 = 0;  // trajectory / segment levels stored in 16 bits (segment_type BF16 / F16)
   int nF = 3, nA = 6, nT = 2;  // state fields, adjoint fields, trajectory fields
   int fwd_blocks = 0, obj_blocks = 0;
@@ -54,7 +54,9 @@ constexpr int kFwdTX = 32, kFwdTY = 16, kAdjTX = 32, kAdjTY = 16;
 
 int obj_grid(size_t N) { return (int)std::min<size_t>((N + NTHREADS - 1) / NTHREADS, 1024); }
 
-Layout make_layout(const lks_problem_desc* d) {
+// overlap: a second segment store, so that the recompute of a segment can run while
+// the adjoint marches the one after it (checkpointed unsteady problems).
+Layout make_layout(const lks_problem_desc* d, bool overlap = true) {
   Layout L;
   L.N = (size_t)d->nx * d->ny;
   L.rsize = d->real_type == LKS_REAL_F64 ? 8 : 4;
@@ -106,6 +108,7 @@ Layout make_layout(const lks_problem_desc* d) {
       L.scales = take(sizeof(float) * 2 * L.nF * (size_t)L.n_ckpt);
       L.seg_levels = K + 2;
       L.seg = take(lb * L.nT * (size_t)L.seg_levels);
+      if (overlap) L.seg2 = take(lb * L.nT * (size_t)L.seg_levels);
     }
   }
   L.total = off;
@@ -141,6 +144,16 @@ struct lks_handle {
   bool is3 = false;  // D3Q19 problem: the lks3 path with layout L3
   lks3::Layout3 L3;
   std::string err;
+  // Checkpointed unsteady problems: a second stream, on which the recompute of a
+  // segment runs while the adjoint marches the next one, and the events that order
+  // the two segment stores between them.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_seg[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
+  ~lks_handle() {
+    for (cudaEvent_t e : {ev_fork, ev_seg[0], ev_seg[1], ev_adj[0], ev_adj[1]})
+      if (e) cudaEventDestroy(e);
+    if (aux) cudaStreamDestroy(aux);
+  }
 };
 
 namespace {
@@ -1178,29 +1191,75 @@ lks_status adjoint_impl(lks_handle* h) {
     }
   } else {
     const int K = d.checkpoint_every;
-    for (int s = L.n_ckpt - 1; s >= 0; --s) {
+    // Segment s recomputed from its snapshot into the store at `base`: level t_lo,
+    // then the forward steps t_lo + 1 .. top.
+    auto recompute = [&](int s, size_t base) -> lks_status {
       const int t_lo = s * K, t_hi = std::min((s + 1) * K, n), top = std::min(t_hi + 1, n);
+      lks_status rs;
       h->cur = 0;
-      if ((st = snapshot_load<R>(h, s)) != LKS_OK) return st;
-      // level t_lo into the segment buffer, then recompute t_lo+1 .. top
-      if ((st = level_from_state<R>(h, L.seg, 0, state_ptr<R>(h, h->cur, 1), state_ptr<R>(h, h->cur, 2),
+      if ((rs = snapshot_load<R>(h, s)) != LKS_OK) return rs;
+      if ((rs = level_from_state<R>(h, base, 0, state_ptr<R>(h, h->cur, 1), state_ptr<R>(h, h->cur, 2),
                                     d.thermal ? state_ptr<R>(h, h->cur, 3) : nullptr)) != LKS_OK)
-        return st;
+        return rs;
       for (int t = t_lo; t < top; ++t) {
-        R* p = level_write_ptr<R>(h, L.seg, t + 1 - t_lo);
-        if ((st = launch_fwd<R>(h, t + 1, nullptr, p, p + L.N, d.thermal ? p + 2 * L.N : nullptr)) != LKS_OK)
-          return st;
-        if ((st = level_written<R>(h, L.seg, t + 1 - t_lo)) != LKS_OK) return st;
+        R* p = level_write_ptr<R>(h, base, t + 1 - t_lo);
+        if ((rs = launch_fwd<R>(h, t + 1, nullptr, p, p + L.N, d.thermal ? p + 2 * L.N : nullptr)) != LKS_OK)
+          return rs;
+        if ((rs = level_written<R>(h, base, t + 1 - t_lo)) != LKS_OK) return rs;
       }
+      return LKS_OK;
+    };
+    // The adjoint steps over segment s, reading its levels from the store at `base`.
+    auto march = [&](int s, size_t base) -> lks_status {
+      const int t_lo = s * K, t_hi = std::min((s + 1) * K, n);
       const int t_stop = (s == 0) ? t_end : t_lo + 1;
+      lks_status ms;
       for (int t = t_hi; t >= t_stop; --t) {
         const R *u1, *v1, *u0, *v0, *T0;
-        if ((st = levels(L.seg, t_lo, t, t == t_hi, &u1, &v1, &u0, &v0, &T0)) != LKS_OK) return st;
-        if ((st = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return st;
+        if ((ms = levels(base, t_lo, t, t == t_hi, &u1, &v1, &u0, &v0, &T0)) != LKS_OK) return ms;
+        if ((ms = launch_adj<R>(h, u1, v1, u0, v0, T0, fld<R>(h, L.sens, 0), t >= 1, t < n)) != LKS_OK) return ms;
         if (++since_flush == flush_every) {
-          if ((st = flush_sens<R>(h)) != LKS_OK) return st;
+          if ((ms = flush_sens<R>(h)) != LKS_OK) return ms;
           since_flush = 0;
         }
+      }
+      return LKS_OK;
+    };
+    const int last = L.n_ckpt - 1;
+    if (!h->aux || !L.seg2) {
+      for (int s = last; s >= 0; --s)
+        if ((st = recompute(s, L.seg)) != LKS_OK || (st = march(s, L.seg)) != LKS_OK) return st;
+    } else {
+      // Segment s - 1 is recomputed on a second stream while the adjoint marches
+      // segment s on the caller's stream, so that the recompute fills what the
+      // adjoint's launches leave idle; segment s sits in store s & 1.  The caller's
+      // stream waits for each recompute before its adjoint, and a recompute waits for
+      // the adjoint that last read its store.  The last recompute (segment 0) is
+      // waited for before the last adjoint, so the second stream ends joined.
+      auto store = [&](int s) { return (s & 1) ? L.seg2 : L.seg; };
+      struct Restore {
+        lks_handle* h;
+        cudaStream_t s;
+        ~Restore() { h->stream = s; }
+      } restore{h, h->stream};
+      const cudaStream_t main = h->stream;
+      CKH(h, cudaEventRecord(h->ev_fork, main));
+      CKH(h, cudaStreamWaitEvent(h->aux, h->ev_fork, 0));
+      h->stream = h->aux;
+      if ((st = recompute(last, store(last))) != LKS_OK) return st;
+      CKH(h, cudaEventRecord(h->ev_seg[last & 1], h->aux));
+      for (int s = last; s >= 0; --s) {
+        h->stream = main;
+        CKH(h, cudaStreamWaitEvent(main, h->ev_seg[s & 1], 0));
+        if (s > 0) {
+          h->stream = h->aux;
+          if (s < last) CKH(h, cudaStreamWaitEvent(h->aux, h->ev_adj[(s + 1) & 1], 0));
+          if ((st = recompute(s - 1, store(s - 1))) != LKS_OK) return st;
+          CKH(h, cudaEventRecord(h->ev_seg[(s - 1) & 1], h->aux));
+          h->stream = main;
+        }
+        if ((st = march(s, store(s))) != LKS_OK) return st;
+        CKH(h, cudaEventRecord(h->ev_adj[s & 1], main));
       }
     }
   }
@@ -1347,6 +1406,15 @@ lks_status lks_create(const lks_problem_desc* desc, void* workspace, size_t byte
   h->ws_bytes = bytes;
   h->stream = reinterpret_cast<cudaStream_t>(stream);
   cudaGetDevice(&h->device);
+  if (L.seg2) {
+    bool ok = cudaStreamCreateWithFlags(&h->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&h->ev_fork, &h->ev_seg[0], &h->ev_seg[1], &h->ev_adj[0], &h->ev_adj[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) {
+      delete h;
+      return LKS_ERR_CUDA;
+    }
+  }
   s = desc->real_type == LKS_REAL_F64 ? set_smem_attrs<double>() : set_smem_attrs<float>();
   if (s == LKS_OK) s = desc->real_type == LKS_REAL_F64 ? upload_maps<double>(h) : upload_maps<float>(h);
   if (s != LKS_OK) {
@@ -1630,7 +1698,7 @@ lks_status lks_gradient_noalloc(const lks_problem_desc* desc, const void* gamma_
   if (s != LKS_OK) return s;
   if (desc->lattice != LKS_LATTICE_D2Q9) return LKS_ERR_INVALID_ARG;
   if (desc->tol > 0.0) return LKS_ERR_INVALID_ARG;  // a tolerance march reads its change back (synchronises)
-  const Layout L = make_layout(desc);
+  const Layout L = make_layout(desc, false);  // one segment store: this entry point has one stream
   if (L.total > LKS_NOALLOC_SCRATCH_BYTES) return LKS_ERR_WORKSPACE;  // problem too large
   void* ws = nullptr;
   int dev = 0;
