@@ -210,7 +210,7 @@ constexpr int kNLists = kNCfg + 2;
 struct BLayout {
   size_t designs = 0, work[kNLists] = {}, rng[kNLists] = {}, uin = 0, emap = 0, gptr = 0, dptr = 0;
   size_t gamma = 0, stA = 0, stB = 0, adA = 0, adB = 0, mat = 0, sens = 0, sens64 = 0;
-  size_t jt = 0, jfin = 0, jval = 0, status = 0, snaps = 0, scales = 0, seg = 0, total = 0;
+  size_t jt = 0, jfin = 0, jval = 0, status = 0, snaps = 0, scales = 0, seg = 0, seg2 = 0, total = 0;
 };
 
 struct Plan {
@@ -245,13 +245,14 @@ int shelf_pack(const std::vector<int>& fw, const std::vector<int>& fh, int W, st
   return y + sh;
 }
 
-// Checkpoint spacing that minimises snapshot + segment-buffer bytes.
+// Checkpoint spacing that minimises snapshot + segment-store bytes (two segment
+// stores: the recompute of a segment overlaps the adjoint of the next).
 int memory_optimal_K(int n_steps, size_t A, size_t se) {
   size_t best = SIZE_MAX;
   int bk = 1;
   for (int K = 1; K <= n_steps; ++K) {
     const size_t nck = (size_t)((n_steps + K - 1) / K);
-    const size_t bytes = nck * 3 * A * se + (size_t)(K + 2) * 2 * A * 4;
+    const size_t bytes = nck * 3 * A * se + 2 * (size_t)(K + 2) * 2 * A * 4;
     if (bytes < best) {
       best = bytes;
       bk = K;
@@ -388,6 +389,7 @@ lks_status make_plan(int32_t n, const lks_problem_desc* descs, const lks_batch_o
   L.snaps = take(P->snap_elem * P->A * 3 * (size_t)P->n_ckpt);
   L.scales = take(sizeof(float) * 3 * (size_t)n * P->n_ckpt);
   L.seg = take(fb * 2 * (size_t)P->seg_levels);
+  L.seg2 = take(fb * 2 * (size_t)P->seg_levels);
   L.total = off;
   return LKS_OK;
 }
@@ -417,6 +419,16 @@ struct lks_batch {
   int64_t launches = 0, launches_per_grad = 0, gradients = 0;
   float tune_us[kNCfg] = {}, tune_fwd_us[kNCfg] = {}, tune_col_us = 0.f, tune_acol_us = 0.f;
   std::string err;
+  // The segment recompute runs on a second stream, overlapped with the adjoint of
+  // the next segment (a parallel branch of the captured graph); events order the
+  // two segment stores between the streams.
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_seg[2] = {nullptr, nullptr}, ev_adj[2] = {nullptr, nullptr};
+  ~lks_batch() {
+    for (cudaEvent_t e : {ev_fork, ev_seg[0], ev_seg[1], ev_adj[0], ev_adj[1]})
+      if (e) cudaEventDestroy(e);
+    if (aux) cudaStreamDestroy(aux);
+  }
 };
 
 namespace {
@@ -746,28 +758,68 @@ lks_status enqueue_gradient(lks_batch* b) {
   CKB(b, cudaMemsetAsync(b->ws + L.sens, 0, fb, b->stream));
   CKB(b, cudaMemsetAsync(b->ws + L.sens64, 0, A * 8, b->stream));
   b->acur = 0;
-  float* seg = af(b, L.seg);
   int since_flush = 0;
-  for (int s = P.n_ckpt - 1; s >= 0; --s) {
+  auto store = [&](int s) { return af(b, (s & 1) ? L.seg2 : L.seg); };
+  // segment s recomputed from its snapshot into store s & 1
+  auto recompute = [&](int s) -> lks_status {
     const int t_lo = s * K, t_hi = std::min((s + 1) * K, n), top = std::min(t_hi + 1, n);
+    float* seg = store(s);
+    lks_status rs;
     b->cur = 0;
-    if ((st = snap_load(b, s)) != LKS_OK) return st;
+    if ((rs = snap_load(b, s)) != LKS_OK) return rs;
     CKB(b, cudaMemcpyAsync(seg, stp(b, b->cur, 1), fb, cudaMemcpyDeviceToDevice, b->stream));
     CKB(b, cudaMemcpyAsync(seg + A, stp(b, b->cur, 2), fb, cudaMemcpyDeviceToDevice, b->stream));
     for (int t = t_lo; t < top; ++t) {
       float* p = seg + (size_t)(t + 1 - t_lo) * 2 * A;
-      if ((st = fwd_step(b, t + 1, false, p, p + A)) != LKS_OK) return st;
+      if ((rs = fwd_step(b, t + 1, false, p, p + A)) != LKS_OK) return rs;
     }
+    return LKS_OK;
+  };
+  // the adjoint steps over segment s
+  auto march = [&](int s) -> lks_status {
+    const int t_lo = s * K, t_hi = std::min((s + 1) * K, n);
+    const float* seg = store(s);
+    lks_status ms;
     const int t_stop = (s == 0) ? 1 : t_lo + 1;
     for (int t = t_hi; t >= t_stop; --t) {
       const float* l1 = seg + (size_t)(std::min(t + 1, n) - t_lo) * 2 * A;
       const float* l0 = seg + (size_t)(t - t_lo) * 2 * A;
-      if ((st = adj_step(b, l1, l1 + A, l0, l0 + A, t >= 1)) != LKS_OK) return st;
+      if ((ms = adj_step(b, l1, l1 + A, l0, l0 + A, t >= 1)) != LKS_OK) return ms;
       if (++since_flush == kFlushEvery) {
-        if ((st = flush(b)) != LKS_OK) return st;
+        if ((ms = flush(b)) != LKS_OK) return ms;
         since_flush = 0;
       }
     }
+    return LKS_OK;
+  };
+  // Segment s - 1 is recomputed on the second stream while the adjoint marches
+  // segment s; the adjoint waits for its segment's recompute, a recompute for the
+  // adjoint that last read its store, and the last recompute (segment 0) is waited
+  // for before the last adjoint, so the second stream ends joined.
+  const int last = P.n_ckpt - 1;
+  struct Restore {
+    lks_batch* b;
+    cudaStream_t s;
+    ~Restore() { b->stream = s; }
+  } restore{b, b->stream};
+  const cudaStream_t main = b->stream;
+  CKB(b, cudaEventRecord(b->ev_fork, main));
+  CKB(b, cudaStreamWaitEvent(b->aux, b->ev_fork, 0));
+  b->stream = b->aux;
+  if ((st = recompute(last)) != LKS_OK) return st;
+  CKB(b, cudaEventRecord(b->ev_seg[last & 1], b->aux));
+  for (int s = last; s >= 0; --s) {
+    b->stream = main;
+    CKB(b, cudaStreamWaitEvent(main, b->ev_seg[s & 1], 0));
+    if (s > 0) {
+      b->stream = b->aux;
+      if (s < last) CKB(b, cudaStreamWaitEvent(b->aux, b->ev_adj[(s + 1) & 1], 0));
+      if ((st = recompute(s - 1)) != LKS_OK) return st;
+      CKB(b, cudaEventRecord(b->ev_seg[(s - 1) & 1], b->aux));
+      b->stream = main;
+    }
+    if ((st = march(s)) != LKS_OK) return st;
+    CKB(b, cudaEventRecord(b->ev_adj[s & 1], main));
   }
   if ((st = flush(b)) != LKS_OK) return st;
   gather_grad_kernel<<<per_design_grid(b), 256, 0, b->stream>>>(
@@ -970,6 +1022,12 @@ lks_status lks_batch_create(int32_t n, const lks_problem_desc* descs, const lks_
   if (cudaGetDevice(&b->device) != cudaSuccess ||
       cudaDeviceGetAttribute(&b->sms, cudaDevAttrMultiProcessorCount, b->device) != cudaSuccess)
     return fin(LKS_ERR_CUDA);
+  {
+    bool ok = cudaStreamCreateWithFlags(&b->aux, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t* e : {&b->ev_fork, &b->ev_seg[0], &b->ev_seg[1], &b->ev_adj[0], &b->ev_adj[1]})
+      ok = ok && cudaEventCreateWithFlags(e, cudaEventDisableTiming) == cudaSuccess;
+    if (!ok) return fin(LKS_ERR_CUDA);
+  }
   const Plan& P = b->P;
   // per-design tables
   std::vector<BatchDesign> dz(n);
