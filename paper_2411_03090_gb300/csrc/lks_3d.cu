@@ -1517,9 +1517,10 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
 // five links that leave the warp (one sign of c_y per row) pass through the shared
 // exchange.  The per-node formulas are those of the warp-column kernels.
 constexpr int NWP3 = 5, NTP3 = 32 * NWP3;
-// Plane ring of the paired forward: planes z - 2 .. z + 4 (seven slots keep three
-// CTAs of it on an SM).
-constexpr int NSLP3 = 7;
+// Plane ring of the paired forward: planes z - 2 .. z + 5 (eight slots; three CTAs
+// of 75.5 KB, each with the 1 KB the system keeps per CTA, fit an SM's 228 KB).
+constexpr int NSLP3 = 8;
+static_assert((NSLP3 & (NSLP3 - 1)) == 0, "ring slots index by mask");
 static_assert(2 * NWP3 == NYC3 + 2, "two rows per warp, one halo row above and below the tile");
 static_assert(CX3 % 2 == 0 && XW3 % 2 == 0 && CFS3 % 2 == 0 && CBW3 % 2 == 0, "node pairs are 8-byte aligned");
 constexpr unsigned kFull3 = 0xffffffffu;
@@ -1642,9 +1643,11 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
   const bool in_xy = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
   const bool out_node = q >= 1 && q <= 14 && i0 < nx && t >= 1 && t <= NYC3 && j < ny;
   const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  // every lane's row, and every row whose push it reads, is off the y faces
+  const bool tile_yfast = y0 >= 2 && y0 + NYC3 <= ny - 2;
   // sent inside the warp: the class value with c_y = +1 (upper row) / -1 (lower row)
   const F2 sy2 = p2(h ? -1.f : 1.f);
-  auto slot = [&](int p) { return (p - pbase) % NSLP3; };
+  auto slot = [&](int p) { return (p - pbase) & (NSLP3 - 1); };
   auto issue = [&](int p) {
     const int sl = slot(p);
     lks::mbar_expect_tx(&bar[sl], NFC3 * CBOX3 * 4);
@@ -1678,10 +1681,7 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
       return;
     }
   int zs = 2;  // ring slot of the plane z being pushed; plane z + k sits in slot zs + k
-  auto slk = [&](int k) {  // k in -2 .. 2
-    const int sk = zs + k;
-    return sk >= NSLP3 ? sk - NSLP3 : (sk < 0 ? sk + NSLP3 : sk);
-  };
+  auto slk = [&](int k) { return (zs + k) & (NSLP3 - 1); };
   // field f (0 drho, 1 u, 2 v, 3 w) of plane z + k at row offset dy, the pair's even column
   auto fp = [&](int f, int k, int dy) { return ring + (slk(k) * NFC3 + f) * CFS3 + (by + dy) * CBW3 + bx; };
   auto at2 = [&](int f, int k, int dy) { return ld2s(fp(f, k, dy)); };
@@ -1700,9 +1700,13 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
 #pragma unroll
   for (int s = 0; s < NRS3; ++s) Am[s] = Ac[s] = Ap[s] = zero2();
 
-  auto plane_step = [&](int z, auto fast_tag) {
-    constexpr bool FAST = decltype(fast_tag)::value;
-    const bool src = FAST || (in_xy && z >= 0 && z < nz);
+  // One plane: push of plane z, then gather of plane z - 1.  MODE 0 (fast): no node
+  // of the tile at planes z and z - 1 lies on a face (all are inside); MODE 1: only
+  // the x faces can occur (rows and planes are off the y and z faces); MODE 2: any.
+  auto plane_step = [&](int z, auto mode_tag) {
+    constexpr int MODE = decltype(mode_tag)::value;
+    constexpr bool FAST = MODE == 0, XO = MODE == 1;
+    const bool src = FAST || (XO ? (i0 >= 0 && i0 < nx) : (in_xy && z >= 0 && z < nz));
     // velocity gradient, g[d][a] = f(x + e_a) - f(x - e_a) of u_d (twice d u_d / d x_a)
     F2 gr[3][3];
     {
@@ -1721,7 +1725,7 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
       static_for<0, 2>([&](auto cc) {
         constexpr int CC = decltype(cc)::value;
         const int i = i0 + CC;
-        const bool on[3] = {i == 0 || i == nx - 1, j == 0 || j == ny - 1, z == 0 || z == nz - 1};
+        const bool on[3] = {i == 0 || i == nx - 1, !XO && (j == 0 || j == ny - 1), !XO && (z == 0 || z == nz - 1)};
         if (src && (on[0] || on[1] || on[2])) {
 #pragma unroll
           for (int d = 0; d < 3; ++d) {
@@ -1851,8 +1855,8 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
           constexpr int CC = decltype(cc)::value;
           const int i = i0 + CC;
           const int n0 = i == 0 ? -1 : (i == nx - 1 ? 1 : 0);
-          const int n1 = j == 0 ? -1 : (j == ny - 1 ? 1 : 0);
-          const int n2 = zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0);
+          const int n1 = XO ? 0 : (j == 0 ? -1 : (j == ny - 1 ? 1 : 0));
+          const int n2 = XO ? 0 : (zd == 0 ? -1 : (zd == nz - 1 ? 1 : 0));
           const int faces = abs(n0) + abs(n1) + abs(n2);
           if (faces >= 2) {
             // wall edge or corner: density from the node one step inward along the
@@ -1905,7 +1909,7 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
     um = uc, vm = vc, wm = wc;
     dc = dp, uc = up, vc = vp, wc = wp;
     if (z + 2 <= plast) dp = at2(0, 2, 0), up = at2(1, 2, 0), vp = at2(2, 2, 0), wp = at2(3, 2, 0);
-    zs = zs + 1 == NSLP3 ? 0 : zs + 1;
+    zs = (zs + 1) & (NSLP3 - 1);
   };
 
   for (int z = z0 - 1; z <= z1; ++z) {
@@ -1913,8 +1917,10 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
       drain_and_fail();
       return;
     }
-    if (tile_fast && z >= 2 && z <= nz - 2) plane_step(z, std::true_type{});
-    else plane_step(z, std::false_type{});
+    const bool zin = z >= 2 && z <= nz - 2;
+    if (tile_fast && zin) plane_step(z, std::integral_constant<int, 0>{});
+    else if (tile_yfast && zin) plane_step(z, std::integral_constant<int, 1>{});
+    else plane_step(z, std::integral_constant<int, 2>{});
   }
 }
 
