@@ -810,72 +810,6 @@ __device__ __forceinline__ void adj_moments3(const float (&F)[19], float (&m)[kN
   m[9] = dia[2];
 }
 
-// Sum and first moments of the 19 increments F gathered at an interior node
-// (sum_k F_k and sum_k c_k F_k), summed by link class as in adj_moments3.
-__device__ __forceinline__ void fwd_moments3(const float (&F)[19], float& sm, float& mx, float& my, float& mz) {
-  float sum_ax = 0.f, dif[3];
-  static_for<0, 3>([&](auto aa) {
-    constexpr int a = decltype(aa)::value;
-    constexpr int kp = link3(a == 0, a == 1, a == 2), km = link3(-(a == 0), -(a == 1), -(a == 2));
-    sum_ax += F[kp] + F[km];
-    dif[a] = F[kp] - F[km];
-  });
-  float mom[3] = {dif[0], dif[1], dif[2]};
-  float s4all = 0.f;
-  static_for<0, 3>([&](auto pp) {
-    constexpr int p = decltype(pp)::value;
-    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;
-    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
-    constexpr int kpp = link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2]);
-    constexpr int kmm = link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2]);
-    constexpr int kpm = link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2]);
-    constexpr int kmp = link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2]);
-    const float Rr = F[kpp] - F[kmm], S = F[kpm] - F[kmp];
-    s4all += (F[kpp] + F[kmm]) + (F[kpm] + F[kmp]);
-    mom[a] += Rr + S;
-    mom[b] += Rr - S;
-  });
-  sm = F[0] + (sum_ax + s4all);
-  mx = mom[0];
-  my = mom[1];
-  mz = mom[2];
-}
-
-// The 19 pushed values of a node, P_k = w_k [base + c_k.b + c_k c_k : Q] (Eq. feq2 in
-// 3-D, with base = drho + e0, b = 3u and Q the coefficients of c_a c_b, each
-// off-diagonal entry counted once).  Opposite links share w (base + Q) and differ by
-// the sign of w c_k.b; the four diagonal links of an axis pair share
-// w (base + Q_aa + Q_bb) and split by the sign of Q_ab.  Summed over the links a
-// destination receives, these give rho and u* directly (no increment form).
-__device__ __forceinline__ void push_all3(float base, float bx, float by, float bz, float Qxx, float Qyy, float Qzz,
-                                          float Qxy, float Qxz, float Qyz, float (&P)[19]) {
-  constexpr float w0 = (float)w3d(0), w1 = (float)w3d(1), w2 = (float)w3d(7);
-  const float w1b = w1 * base, w2b = w2 * base;
-  const float b1[3] = {w1 * bx, w1 * by, w1 * bz};
-  const float b2[3] = {0.5f * b1[0], 0.5f * b1[1], 0.5f * b1[2]};  // w2 = w1 / 2 exactly
-  const float Qd[3] = {Qxx, Qyy, Qzz};
-  P[0] = w0 * base;
-  static_for<0, 3>([&](auto aa) {
-    constexpr int a = decltype(aa)::value;
-    const float t = w1 * Qd[a] + w1b;
-    P[link3(a == 0, a == 1, a == 2)] = t + b1[a];
-    P[link3(-(a == 0), -(a == 1), -(a == 2))] = t - b1[a];
-  });
-  static_for<0, 3>([&](auto pp) {
-    constexpr int p = decltype(pp)::value;
-    constexpr int a = p == 2 ? 1 : 0, b = p == 0 ? 1 : 2;  // axis pairs (x,y), (x,z), (y,z)
-    constexpr int ea[3] = {a == 0, a == 1, a == 2}, eb[3] = {b == 0, b == 1, b == 2};
-    const float Qab = p == 0 ? Qxy : (p == 1 ? Qxz : Qyz);
-    const float sdiag = w2 * (Qd[a] + Qd[b]) + w2b, q = w2 * Qab;
-    const float sp = sdiag + q, sm = sdiag - q;
-    const float c1 = b2[a] + b2[b], c2 = b2[a] - b2[b];
-    P[link3(ea[0] + eb[0], ea[1] + eb[1], ea[2] + eb[2])] = sp + c1;
-    P[link3(-ea[0] - eb[0], -ea[1] - eb[1], -ea[2] - eb[2])] = sp - c1;
-    P[link3(ea[0] - eb[0], ea[1] - eb[1], ea[2] - eb[2])] = sm + c2;
-    P[link3(eb[0] - ea[0], eb[1] - ea[1], eb[2] - ea[2])] = sm - c2;
-  });
-}
-
 // ---------------------------------------------------------------------------------
 // Warp-column D3Q19 tiles (FP32)
 // ---------------------------------------------------------------------------------
@@ -1500,10 +1434,10 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
 }
 
 // ---------------------------------------------------------------------------------
-// Paired-column D3Q19 kernels (FP32)
+// Paired-column D3Q19 forward (FP32)
 // ---------------------------------------------------------------------------------
 // The tiles (CX3 x NYC3 outputs), z chunks, staged boxes and exchange protocol of
-// the warp-column kernels, with two nodes per lane and two rows per warp:
+// the warp-column adjoint, with two nodes per lane and two rows per warp:
 //   - a lane owns an even column and the odd one after it (pair q of a half-warp owns
 //     columns x0 - 2 + 2q and x0 - 1 + 2q; pairs 1..14 write, 28 columns);
 //   - warp w owns rows y0 - 1 + 2w (lanes 0..15, the upper row) and y0 + 2w (lanes
@@ -1515,7 +1449,7 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
 // in the lane between the pair's columns, moves by one shuffle between the lanes of
 // a row and by shuffles across the half-warps between the warp's two rows; only the
 // five links that leave the warp (one sign of c_y per row) pass through the shared
-// exchange.  The per-node formulas are those of the warp-column kernels.
+// exchange.
 constexpr int NWP3 = 5, NTP3 = 32 * NWP3;
 // Plane ring of the paired forward: planes z - 2 .. z + 5 (eight slots; three CTAs
 // of 75.5 KB, each with the 1 KB the system keeps per CTA, fit an SM's 228 KB).
@@ -1576,7 +1510,7 @@ __device__ __forceinline__ F2 recv_xo3(F2 v, int oth) {
 }
 
 // Class sums of the values a node pair gathered (interior rule), the groupings of
-// fwd_moments3 / adj_moments3: the links with c_y = 0 by slot, and per y class b the
+// adj_moments3: the links with c_y = 0 by slot, and per y class b the
 // sum S_b = F(c_y = +1) + F(c_y = -1) and difference D_b = F(c_y = +1) - F(c_y = -1).
 struct ClassSums3 {
   F2 F000, ax, dx, az, dz, e1, e2, f1, f2;
@@ -1610,8 +1544,13 @@ __device__ __forceinline__ void gathered19(const F2 (&A)[NRS3], const F2 (&Fp)[N
   });
 }
 
-// Paired-column forward.  Every node pair computes its 19 pushed values (Eq. feq2,
-// push_all3's link-pair form) and routes value k to x + c_k: the links with c_y = 0
+// Paired-column forward.  Every node pair computes its 19 pushed values
+// P_k = w_k [base + c_k.b + c_k c_k : Q] (Eq. feq2 with base = drho + e0, b = 3u and
+// Q the coefficients of c_a c_b, each off-diagonal entry counted once), by link
+// pair: opposite links share w (base + Q) and differ by the sign of w c_k.b, the four
+// diagonal links of an axis pair share w (base + Q_aa + Q_bb) and split by the sign
+// of Q_ab.  Summed over the links a destination receives, these give rho and u*
+// directly.  Value k is routed to x + c_k: the links with c_y = 0
 // inside the row, one sign of c_y to the warp's other row by shuffles (the upper row
 // sends c_y = +1, the lower row c_y = -1), the other sign through the exchange.
 // drho, u, v, w of each plane arrive by tensor copies into the ring; 1/(1+alpha) of
@@ -1771,7 +1710,7 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
     if constexpr (!FAST) {
       if (!src) bs = Qxx = Qyy = Qzz = Qxy = Qxz = Qyz = bxv = byv = bzv = zero2();
     }
-    // pushed values by link pair (push_all3): w1 b = u / 6, w2 b = u / 12
+    // pushed values by link pair: w1 b = u / 6, w2 b = w1 b / 2
     const F2 w0 = p2((float)w3d(0)), w1 = p2((float)w3d(1)), w2 = p2((float)w3d(7));
     const F2 w1b = mul2(w1, bs), w2b = mul2(w2, bs);
     const F2 b1x = mul2(p2(3.f * (float)w3d(1)), bxv), b1y = mul2(p2(3.f * (float)w3d(1)), byv),
