@@ -797,10 +797,15 @@ lks_status enqueue_gradient(lks_batch* b) {
   // adjoint that last read its store, and the last recompute (segment 0) is waited
   // for before the last adjoint, so the second stream ends joined.
   const int last = P.n_ckpt - 1;
+  // On every exit, error paths included, the stream is restored and made to wait for
+  // whatever the second stream holds (inside a capture this is the join).
   struct Restore {
     lks_batch* b;
     cudaStream_t s;
-    ~Restore() { b->stream = s; }
+    ~Restore() {
+      b->stream = s;
+      if (cudaEventRecord(b->ev_fork, b->aux) == cudaSuccess) cudaStreamWaitEvent(s, b->ev_fork, 0);
+    }
   } restore{b, b->stream};
   const cudaStream_t main = b->stream;
   CKB(b, cudaEventRecord(b->ev_fork, main));

@@ -1237,10 +1237,15 @@ lks_status adjoint_impl(lks_handle* h) {
       // the adjoint that last read its store.  The last recompute (segment 0) is
       // waited for before the last adjoint, so the second stream ends joined.
       auto store = [&](int s) { return (s & 1) ? L.seg2 : L.seg; };
+      // On every exit, error paths included, the caller's stream is restored and
+      // made to wait for whatever the second stream holds.
       struct Restore {
         lks_handle* h;
         cudaStream_t s;
-        ~Restore() { h->stream = s; }
+        ~Restore() {
+          h->stream = s;
+          if (cudaEventRecord(h->ev_fork, h->aux) == cudaSuccess) cudaStreamWaitEvent(s, h->ev_fork, 0);
+        }
       } restore{h, h->stream};
       const cudaStream_t main = h->stream;
       CKH(h, cudaEventRecord(h->ev_fork, main));
