@@ -1450,13 +1450,16 @@ __global__ void __launch_bounds__(NTC3, 2) adj3c_kernel(const __grid_constant__ 
 // a row and by shuffles across the half-warps between the warp's two rows; only the
 // five links that leave the warp (one sign of c_y per row) pass through the shared
 // exchange.
-constexpr int NWP3 = 5, NTP3 = 32 * NWP3;
-// Plane ring of the paired forward: planes z - 2 .. z + 5 (eight slots; three CTAs
-// of 75.5 KB, each with the 1 KB the system keeps per CTA, fit an SM's 228 KB).
+// Tiles of the paired forward: CX3 x NYP3 outputs (taller than the adjoint's NYC3,
+// so that the two halo rows are a smaller share), boxes CBW3 x PBH3.
+constexpr int NYP3 = 12, NWP3 = NYP3 / 2 + 1, NTP3 = 32 * NWP3;
+constexpr int PBH3 = NYP3 + 4, PBOX3 = CBW3 * PBH3;
+constexpr int PFS3 = (PBOX3 * 4 + 127) / 128 * 128 / 4;  // field stride in a ring slot (128-byte multiple)
+// Plane ring of the paired forward: planes z - 2 .. z + 5 (eight slots).
 constexpr int NSLP3 = 8;
 static_assert((NSLP3 & (NSLP3 - 1)) == 0, "ring slots index by mask");
-static_assert(2 * NWP3 == NYC3 + 2, "two rows per warp, one halo row above and below the tile");
-static_assert(CX3 % 2 == 0 && XW3 % 2 == 0 && CFS3 % 2 == 0 && CBW3 % 2 == 0, "node pairs are 8-byte aligned");
+static_assert(2 * NWP3 == NYP3 + 2, "two rows per warp, one halo row above and below the tile");
+static_assert(CX3 % 2 == 0 && XW3 % 2 == 0 && PFS3 % 2 == 0 && CBW3 % 2 == 0, "node pairs are 8-byte aligned");
 constexpr unsigned kFull3 = 0xffffffffu;
 // Links with c_y != 0 in classes by (c_x, c_z), two links (c_y = +1, -1) each:
 // 0: (0, 0), 1: (1, 0), 2: (-1, 0), 3: (0, 1), 4: (0, -1).
@@ -1556,21 +1559,21 @@ __device__ __forceinline__ void gathered19(const F2 (&A)[NRS3], const F2 (&Fp)[N
 // drho, u, v, w of each plane arrive by tensor copies into the ring; 1/(1+alpha) of
 // an output pair is one 8-byte load, a plane ahead.
 __host__ __device__ constexpr size_t fwd3p_smem() {
-  return sizeof(float) * ((size_t)NSLP3 * NFC3 * CFS3 + (size_t)NXS3 * NYC3 * NCB3 * XW3) + 8 * NSLP3 + 128;
+  return sizeof(float) * ((size_t)NSLP3 * NFC3 * PFS3 + (size_t)NXS3 * NYP3 * NCB3 * XW3) + 8 * NSLP3 + 128;
 }
 
-__global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ Maps3F maps,
+__global__ void __launch_bounds__(NTP3, 2) fwd3p_kernel(const __grid_constant__ Maps3F maps,
                                                         const __grid_constant__ Fwd3TArgs a, Geom3 g,
                                                         Coef3<float> c) {
   using R = float;
   extern __shared__ unsigned char smem_raw3[];
-  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLP3][NFC3][CFS3]
-  R* ex = ring + NSLP3 * NFC3 * CFS3;                              // [NXS3][NYC3][NCB3][XW3]
-  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYC3 * NCB3 * XW3);
+  R* ring = reinterpret_cast<R*>(lks::smem_base128(smem_raw3));  // [NSLP3][NFC3][PFS3]
+  R* ex = ring + NSLP3 * NFC3 * PFS3;                              // [NXS3][NYP3][NCB3][XW3]
+  uint64_t* bar = reinterpret_cast<uint64_t*>(ex + NXS3 * NYP3 * NCB3 * XW3);
   if (lks::timed_out_before(a.status)) return;
   if (!lks::tma_layout_ok(ring, bar, a.status)) return;
   const int nx = g.nx, ny = g.ny, nz = g.nz;
-  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYC3;
+  const int x0 = blockIdx.x * CX3, y0 = blockIdx.y * NYP3;
   const int z0 = blockIdx.z * a.zc, z1 = min(z0 + a.zc, nz);
   const int pbase = z0 - 3, plast = z1 + 2;  // planes staged: z0 - 3 .. z1 + 2
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
@@ -1580,18 +1583,18 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
   const int xl = 2 * q - 2;
   const int oth = lane ^ 16;
   const bool in_xy = i0 >= 0 && i0 < nx && j >= 0 && j < ny;
-  const bool out_node = q >= 1 && q <= 14 && i0 < nx && t >= 1 && t <= NYC3 && j < ny;
-  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYC3 <= ny - 2;
+  const bool out_node = q >= 1 && q <= 14 && i0 < nx && t >= 1 && t <= NYP3 && j < ny;
+  const bool tile_fast = x0 >= 2 && x0 + CX3 <= nx - 2 && y0 >= 2 && y0 + NYP3 <= ny - 2;
   // every lane's row, and every row whose push it reads, is off the y faces
-  const bool tile_yfast = y0 >= 2 && y0 + NYC3 <= ny - 2;
+  const bool tile_yfast = y0 >= 2 && y0 + NYP3 <= ny - 2;
   // sent inside the warp: the class value with c_y = +1 (upper row) / -1 (lower row)
   const F2 sy2 = p2(h ? -1.f : 1.f);
   auto slot = [&](int p) { return (p - pbase) & (NSLP3 - 1); };
   auto issue = [&](int p) {
     const int sl = slot(p);
-    lks::mbar_expect_tx(&bar[sl], NFC3 * CBOX3 * 4);
+    lks::mbar_expect_tx(&bar[sl], NFC3 * PBOX3 * 4);
     for (int f = 0; f < NFC3; ++f)
-      tma_load_3d(ring + (sl * NFC3 + f) * CFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
+      tma_load_3d(ring + (sl * NFC3 + f) * PFS3, &maps.m[f], x0 - 4, y0 - 2, p, &bar[sl]);
   };
   int waited = pbase - 1, issued = pbase - 1;
   auto wait = [&](int p) {
@@ -1622,9 +1625,9 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
   int zs = 2;  // ring slot of the plane z being pushed; plane z + k sits in slot zs + k
   auto slk = [&](int k) { return (zs + k) & (NSLP3 - 1); };
   // field f (0 drho, 1 u, 2 v, 3 w) of plane z + k at row offset dy, the pair's even column
-  auto fp = [&](int f, int k, int dy) { return ring + (slk(k) * NFC3 + f) * CFS3 + (by + dy) * CBW3 + bx; };
+  auto fp = [&](int f, int k, int dy) { return ring + (slk(k) * NFC3 + f) * PFS3 + (by + dy) * CBW3 + bx; };
   auto at2 = [&](int f, int k, int dy) { return ld2s(fp(f, k, dy)); };
-  auto xrow = [&](int p, int od) { return ex + ((p & (NXS3 - 1)) * NYC3 + od) * (NCB3 * XW3); };
+  auto xrow = [&](int p, int od) { return ex + ((p & (NXS3 - 1)) * NYP3 + od) * (NCB3 * XW3); };
   // 1/(1+alpha) of the output pair at plane p (loaded one plane before the gather reads it)
   auto binv_at = [&](int p) {
     return (out_node && p >= 0 && p < nz) ? __ldg(reinterpret_cast<const float2*>(a.binv + gidx(g, i0, j, p)))
@@ -1739,7 +1742,7 @@ __global__ void __launch_bounds__(NTP3, 3) fwd3p_kernel(const __grid_constant__ 
     const F2 sb1y = mul2(sy2, b1y), sb2y = mul2(sy2, b2y), sqxy = mul2(sy2, qXY), sqyz = mul2(sy2, qYZ);
     const F2 sH[NCB3] = {sb1y, add2(sb2y, sqxy), sub2(sb2y, sqxy), add2(sb2y, sqyz), sub2(sb2y, sqyz)};
     const int td = h ? t + 1 : t - 1;  // destination row (in the tile) of the exchanged links
-    const bool xw = td >= 1 && td <= NYC3;
+    const bool xw = td >= 1 && td <= NYP3;
     static_for<0, NCB3>([&](auto bb) {
       constexpr int b = decltype(bb)::value, cx = cbx3(b), cz = cbz3(b);
       const F2 r = recv_xo3<-cx>(add2(G[b], sH[b]), oth);
@@ -2003,8 +2006,8 @@ int ew_grid(size_t n) { return lks_host::elementwise_blocks(n); }
 // plane on each side; the CTAs run in rounds of `resident` (every SM's resident
 // CTAs), so the march takes about rounds x (zc + 2) plane steps.  The smallest such
 // cost over zc in 8 .. 64 avoids a nearly empty last round.
-int col_chunk3(const lks_problem_desc& d, int resident) {
-  const long long txy = (long long)((d.nx + CX3 - 1) / CX3) * ((d.ny + NYC3 - 1) / NYC3);
+int col_chunk3(const lks_problem_desc& d, int resident, int tile_rows) {
+  const long long txy = (long long)((d.nx + CX3 - 1) / CX3) * ((d.ny + tile_rows - 1) / tile_rows);
   int best = ZC3;
   long long best_cost = -1;
   for (int zc = 8; zc <= 64; ++zc) {
@@ -2060,7 +2063,7 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
     if (tma3_ok(d)) {
       // the warp-column forward unless the per-tile kernels are asked for
       const bool col = d.exec_path != LKS_PATH_STEP;
-      const int bw = col ? CBW3 : BW3, bh = col ? CBH3 : BH3;
+      const int bw = col ? CBW3 : BW3, bh = col ? PBH3 : BH3;
       Maps3F maps[2];
       Fwd3TArgs ta[2];
       lks_status st;
@@ -2078,9 +2081,9 @@ lks_status forward3_t(const Ctx3& c, const void* gamma_dev, double* J_dev, int* 
         CK3(c, cudaGetDevice(&dev));
         CK3(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fwd3p_kernel, NTP3, fwd3p_smem()));
-        const int zc = col_chunk3(d, std::max(1, sms * per_sm));
+        const int zc = col_chunk3(d, std::max(1, sms * per_sm), NYP3);
         ta[0].zc = ta[1].zc = zc;
-        const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + zc - 1) / zc);
+        const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYP3 - 1) / NYP3, (d.nz + zc - 1) / zc);
         for (int s = 0; s < d.n_steps; ++s) {
           fwd3p_kernel<<<grid, NTP3, fwd3p_smem(), c.stream>>>(maps[cur], ta[cur], g, cf);
           CK3(c, cudaGetLastError());
@@ -2164,7 +2167,7 @@ lks_status adjoint3_t(const Ctx3& c, int cur, int* acur_out, int* path_out) {
       CK3(c, cudaGetDevice(&dev));
       CK3(c, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       CK3(c, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, adj3c_kernel, NTC3, adj3c_smem()));
-      const int zc = col_chunk3(d, std::max(1, sms * per_sm));
+      const int zc = col_chunk3(d, std::max(1, sms * per_sm), NYC3);
       ca[0].zc = ca[1].zc = zc;
       const dim3 grid((d.nx + CX3 - 1) / CX3, (d.ny + NYC3 - 1) / NYC3, (d.nz + zc - 1) / zc);
       for (int it = 0; it < d.n_adj; ++it) {
