@@ -1084,6 +1084,7 @@ lks_status lks_batch_create(int32_t n, const lks_problem_desc* descs, const lks_
 
 lks_status lks_batch_gradient(lks_batch* b, const float* const* gamma_dev, double* J_dev, float* const* dJdgamma_dev) {
   if (!b || !gamma_dev || !J_dev || !dJdgamma_dev) return LKS_ERR_INVALID_ARG;
+  const lks_host::Range range("lks_batch_gradient");
   for (int d = 0; d < b->n; ++d)
     if (!gamma_dev[d] || !dJdgamma_dev[d]) return bfail(b, LKS_ERR_INVALID_ARG, "NULL design pointer");
   const BLayout& L = b->P.L;

@@ -1194,6 +1194,7 @@ lks_status adjoint_impl(lks_handle* h) {
     // Segment s recomputed from its snapshot into the store at `base`: level t_lo,
     // then the forward steps t_lo + 1 .. top.
     auto recompute = [&](int s, size_t base) -> lks_status {
+      const Range range("segment recompute");
       const int t_lo = s * K, t_hi = std::min((s + 1) * K, n), top = std::min(t_hi + 1, n);
       lks_status rs;
       h->cur = 0;
@@ -1211,6 +1212,7 @@ lks_status adjoint_impl(lks_handle* h) {
     };
     // The adjoint steps over segment s, reading its levels from the store at `base`.
     auto march = [&](int s, size_t base) -> lks_status {
+      const Range range("segment adjoint");
       const int t_lo = s * K, t_hi = std::min((s + 1) * K, n);
       const int t_stop = (s == 0) ? t_end : t_lo + 1;
       lks_status ms;
@@ -1438,6 +1440,7 @@ lks_status lks_destroy(lks_handle* h) {
 
 lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
   if (check_handle(h) != LKS_OK || !gamma_dev) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
+  const Range range("lks_forward");
   if (h->is3) {
     int path = LKS_PATH_STEP;
     const lks_status s = lks3::forward3(ctx3(h), gamma_dev, J_dev, &h->cur, &path);
@@ -1455,6 +1458,7 @@ lks_status lks_forward(lks_handle* h, const void* gamma_dev, double* J_dev) {
 lks_status alks_adjoint(lks_handle* h) {
   if (check_handle(h) != LKS_OK) return LKS_ERR_INVALID_ARG;
   if (h->phase < 1) return fail(h, LKS_ERR_STATE, "alks_adjoint before lks_forward");
+  const Range range("alks_adjoint");
   if (h->is3) {
     int path = LKS_PATH_STEP;
     const lks_status s = lks3::adjoint3(ctx3(h), h->cur, &h->acur, &path);
@@ -1471,6 +1475,7 @@ lks_status alks_adjoint(lks_handle* h) {
 lks_status lks_sensitivity(lks_handle* h, void* out) {
   if (check_handle(h) != LKS_OK || !out) return fail(h, LKS_ERR_INVALID_ARG, "null argument");
   if (h->phase < 2) return fail(h, LKS_ERR_STATE, "lks_sensitivity before alks_adjoint");
+  const Range range("lks_sensitivity");
   if (h->is3) return lks3::sensitivity3(ctx3(h), h->cur, h->acur, out);
   return h->d.real_type == LKS_REAL_F64 ? sensitivity_impl<double>(h, out) : sensitivity_impl<float>(h, out);
 }

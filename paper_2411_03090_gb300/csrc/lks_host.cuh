@@ -12,12 +12,25 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "../../include/lks.h"
 #include "lks_kernels.cuh"
 
 namespace lks_host {
 using lks::Coef;
 using lks::Geom;
+
+// NVTX range over a scope of host code (the enqueue of a march, a segment, a
+// gradient); a profiler attached to the process shows it on the host timeline and
+// can restrict kernel captures to it (ncu --nvtx --nvtx-include).  Without a tool
+// attached the calls return at once.
+struct Range {
+  explicit Range(const char* name) { nvtxRangePushA(name); }
+  ~Range() { nvtxRangePop(); }
+  Range(const Range&) = delete;
+  Range& operator=(const Range&) = delete;
+};
 
 constexpr int CXh[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 constexpr int CYh[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
