@@ -172,6 +172,37 @@ def test_create_rejects_bad_workspace_without_gpu_work():
     assert st == 2 and not h.value
 
 
+def _cuda_device_present():
+    try:
+        import torch
+        return torch.cuda.is_available()
+    except Exception:  # pragma: no cover
+        return False
+
+
+@pytest.mark.skipif(_cuda_device_present(), reason="drives the error paths a machine without a GPU takes")
+@pytest.mark.parametrize("kw", [dict(), dict(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=10.0),
+                                dict(steady=False, pulse_mean=0.75, pulse_amp=0.25, pulse_period=10.0,
+                                     checkpoint_every=5)])
+def test_create_without_a_gpu_fails_with_cuda_error_and_message(kw):
+    """Without a GPU every CUDA call fails: lks_create (steady, plain unsteady, and
+    checkpointed unsteady, which also creates its own stream and events) must return
+    LKS_ERR_CUDA, hand back no handle and not crash.  The workspace is a correctly
+    sized, aligned host buffer that the library never reaches."""
+    L = lks.load()
+    ck = kw.pop("checkpoint_every", 0)
+    pb = inputs.channel(24, 12, Re=10.0, seed=1, n_steps=20, n_adj=20, **kw)
+    d = lks.make_desc(pb, checkpoint_every=ck, snapshot="bf16") if ck else lks.make_desc(pb)
+    n = C.c_size_t(0)
+    assert L.lks_workspace_size(C.byref(d), C.byref(n)) == 0 and n.value > 0
+    raw = np.zeros(n.value + 256, dtype=np.uint8)
+    base = raw.ctypes.data
+    ws = C.c_void_p(base + (-base) % 256)
+    h = C.c_void_p()
+    st = L.lks_create(C.byref(d), ws, C.c_size_t(n.value), None, C.byref(h))
+    assert st == 3 and not h.value  # LKS_ERR_CUDA
+
+
 # ---------------------------------------------------------------------------------------
 # Batched form: host-side planning (no GPU work)
 # ---------------------------------------------------------------------------------------
