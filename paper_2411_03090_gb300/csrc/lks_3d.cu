@@ -1635,9 +1635,6 @@ __global__ void __launch_bounds__(NTP3, 2) fwd3p_kernel(const __grid_constant__ 
   };
   F2 inv_n = binv_at(z0 - 1);
   // the pair's u, v, w at planes z - 1 (m), z (c), z + 1 (p), and drho at z and z + 1
-  F2 um = at2(1, -1, 0), vm = at2(2, -1, 0), wm = at2(3, -1, 0);
-  F2 dc = at2(0, 0, 0), uc = at2(1, 0, 0), vc = at2(2, 0, 0), wc = at2(3, 0, 0);
-  F2 dp = at2(0, 1, 0), up = at2(1, 1, 0), vp = at2(2, 1, 0), wp = at2(3, 1, 0);
   F2 Am[NRS3], Ac[NRS3], Ap[NRS3];  // values for the destination planes z - 1, z, z + 1
 #pragma unroll
   for (int s = 0; s < NRS3; ++s) Am[s] = Ac[s] = Ap[s] = zero2();
@@ -1649,16 +1646,20 @@ __global__ void __launch_bounds__(NTP3, 2) fwd3p_kernel(const __grid_constant__ 
     constexpr int MODE = decltype(mode_tag)::value;
     constexpr bool FAST = MODE == 0, XO = MODE == 1;
     const bool src = FAST || (XO ? (i0 >= 0 && i0 < nx) : (in_xy && z >= 0 && z < nz));
+    // the pair's drho, u, v, w at plane z (staged; planes z - 1 and z + 1 are read
+    // where the z differences need them)
+    const F2 dc = at2(0, 0, 0), uc = at2(1, 0, 0), vc = at2(2, 0, 0), wc = at2(3, 0, 0);
     // velocity gradient, g[d][a] = f(x + e_a) - f(x - e_a) of u_d (twice d u_d / d x_a)
     F2 gr[3][3];
     {
-      const F2 uvw[3] = {uc, vc, wc}, zp[3] = {up, vp, wp}, zm[3] = {um, vm, wm};
+      const F2 uvw[3] = {uc, vc, wc};
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
         const float l = __shfl_up_sync(kFull3, uvw[d].y, 1), r = __shfl_down_sync(kFull3, uvw[d].x, 1);
-        gr[d][0] = sub2(make_float2(uvw[d].y, r), make_float2(l, uvw[d].x));
+        gr[d][0].x = uvw[d].y - l;
+        gr[d][0].y = r - uvw[d].x;
         gr[d][1] = sub2(at2(1 + d, 0, 1), at2(1 + d, 0, -1));
-        gr[d][2] = sub2(zp[d], zm[d]);
+        gr[d][2] = sub2(at2(1 + d, 1, 0), at2(1 + d, -1, 0));
       }
     }
     if constexpr (!FAST) {
@@ -1848,9 +1849,6 @@ __global__ void __launch_bounds__(NTP3, 2) fwd3p_kernel(const __grid_constant__ 
       Am[s] = Ac[s];
       Ac[s] = Ap[s];
     }
-    um = uc, vm = vc, wm = wc;
-    dc = dp, uc = up, vc = vp, wc = wp;
-    if (z + 2 <= plast) dp = at2(0, 2, 0), up = at2(1, 2, 0), vp = at2(2, 2, 0), wp = at2(3, 2, 0);
     zs = (zs + 1) & (NSLP3 - 1);
   };
 
