@@ -439,8 +439,12 @@ lks_status lks_batch_workspace_size(int32_t n, const lks_problem_desc *descs, co
                                     size_t *bytes);
 /* Lays out the arena and the work lists, uploads per-design tables, autotunes the
  * tile shape when asked (running short marches on a uniform design) and captures
- * the gradient graph.  workspace: caller-owned device memory of at least the size
- * above, 256-byte aligned; never freed by the library.  Synchronises the stream. */
+ * the gradient graph, in which the recompute of a checkpoint segment is a branch
+ * parallel to the adjoint of the next segment (captured on a non-blocking stream
+ * the batch handle creates, with five events; destroyed by lks_batch_destroy).
+ * workspace: caller-owned device memory of at least the size above, 256-byte
+ * aligned (two segment stores); never freed by the library.  Synchronises the
+ * stream.  Returns LKS_ERR_CUDA if the stream or events cannot be created. */
 lks_status lks_batch_create(int32_t n, const lks_problem_desc *descs, const lks_batch_options *opt,
                             void *workspace, size_t bytes, void *cuda_stream, lks_batch **out);
 /* All designs' gradients.  gamma_dev: host array of n device pointers to each
