@@ -46,10 +46,12 @@
  * density / normal velocity on edges; corner rules; objective) are restated next
  * to the code they affect.
  *
- * Parity unpinned: the outlet row term of the energy loss (its kinetic part, the
- * only part left under the gauge-pressure reading).  At the check geometry's
- * velocities its share of the gradient lies below what central differences resolve
- * (dropping it moves the ALKS / FD ratios by 3e-4), so no test fixes it.
+ * The outlet row term of the energy loss (its kinetic part, the only part left
+ * under the gauge-pressure reading) is pinned as arithmetic only: it equals three
+ * times the derivative of the outlet integrand with respect to each population
+ * (brute-force central differences in the test).  Its effect on the gradient lies
+ * below what central differences of J resolve at the check geometry's velocities
+ * (dropping it moves the ALKS / FD ratios by 3e-4).
  *
  * Storage: every field is an array of nx*ny doubles, node (i, j) at j*nx + i
  * (x fastest).  Node (i, j) sits at x = i, y = j; the domain edges carry nodes.
@@ -689,6 +691,16 @@ void orc_adjoint_eq(const orc_problem *p, const double *gamma, const double *u, 
     adjoint_eq_fields(p, gamma, u, v, a, P, Vx, Vy, G, Bwork);
 }
 
+/* The row terms of the energy loss (Eq. objective_doublepipe) on an outlet node
+ * with outward normal (n_x, n_y) and normal velocity un: there p = p_bar (the
+ * gauge's zero) and u_s = 0, so the integrand is -un^3 / 2 with
+ * un = sum_i (c_i . n) f_i / rho_bar, and row r carries three times its derivative
+ * with respect to f_r (the scale of the pressure-drop row term, d/dp = 3 d/df_r). */
+void orc_energy_outlet_rows(const orc_problem *p, double un, int n_x, int n_y, double *jbv) {
+    double dJ = -1.5 * un * un;
+    for (int r = 0; r < 9; ++r) jbv[r] = 3.0 * p->kappa_E * dJ * (double)(CX[r] * n_x + CY[r] * n_y) / p->rho_out;
+}
+
 /* Adjoint node update at level t from the equilibrium coefficients at level t+1
  * (already evaluated into P, Vx, Vy, G), the state at level t (u0, v0, T0) and
  * gamma.  out[0..8] in the adjoint field order.
@@ -743,12 +755,8 @@ void orc_adjoint_node(const orc_problem *p, const double *gamma, const double *P
              * f_i through u_n = sum c_i.n f_i / rho_bar, and each row carries three
              * times d/df_i, the scale of the J_p row term (d/dp = 3 d/drho = 3 d/df_i). */
             if (cls == N_VELOCITY && is_inlet(p, i, j)) jb += p->kappa_E * AT(u0, i, j);
-            if (cls == N_PRESSURE) {
-                double un = AT(u0, i, j) * n_x + AT(v0, i, j) * n_y;
-                double dJ = -1.5 * un * un;
-                for (int r = 0; r < 9; ++r)
-                    jbv[r] = 3.0 * p->kappa_E * dJ * (double)(CX[r] * n_x + CY[r] * n_y) / p->rho_out;
-            }
+            if (cls == N_PRESSURE)
+                orc_energy_outlet_rows(p, AT(u0, i, j) * n_x + AT(v0, i, j) * n_y, n_x, n_y, jbv);
         }
         orc_bc_flow(n_x, n_y, cls == N_PRESSURE, A, kT, unknown, f, NULL, jb, jbv);
     }

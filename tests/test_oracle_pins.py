@@ -533,3 +533,38 @@ def test_memory_tables_reproduced():
                 assert abs(rounded - printed) > 0.5
             else:
                 assert rounded == printed, (p, val)
+
+
+@pytest.mark.parametrize("normal", [(1, 0), (-1, 0), (0, 1), (0, -1)])
+def test_energy_loss_outlet_row_terms_are_three_times_the_integrand_derivative(normal):
+    """Eq. (objective_doublepipe) on an outlet node (p at the gauge's zero, u_s = 0):
+    the integrand is -u_n^3 / 2 with u_n = sum_i (c_i . n) f_i / rho_bar, and each
+    adjoint row carries three times its derivative with respect to f_i (the scale of
+    the pressure-drop row term).  Brute force: the integrand differentiated by
+    central differences in each population of random population sets."""
+    import ctypes as C
+    L = O.lib()
+    fn = L.orc_energy_outlet_rows
+    fn.argtypes = [C.POINTER(O.OrcProblem), C.c_double, C.c_int, C.c_int, C.POINTER(C.c_double)]
+    fn.restype = None
+    pb = inputs.channel(20, 12, Re=10.0, kappa_E=0.7, rho_out=1.02)
+    prob = O.make_problem(pb)
+    nx_, ny_ = normal
+    cn = CX * nx_ + CY * ny_
+    rng = np.random.default_rng(26)
+    for _ in range(6):
+        f = rng.normal(0.05, 0.03, 9)
+
+        def integrand(ff):
+            un = float(np.dot(cn, ff)) / pb.rho_out
+            return -0.5 * un ** 3
+
+        out = (C.c_double * 9)()
+        fn(C.byref(prob), float(np.dot(cn, f)) / pb.rho_out, nx_, ny_, out)
+        for r in range(9):
+            h = 1e-5
+            fp, fm = f.copy(), f.copy()
+            fp[r] += h
+            fm[r] -= h
+            d = (integrand(fp) - integrand(fm)) / (2 * h)
+            assert abs(out[r] - 3.0 * pb.kappa_E * d) <= 1e-9, (r, out[r], 3.0 * pb.kappa_E * d)
