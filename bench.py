@@ -526,6 +526,92 @@ def run_batch_study(args):
     }))
 
 
+def also_config3(dev, flush):
+    """Config3 in brief for the default line: the plain FP32 form against checkpoints
+    every 100 steps with BF16 snapshots (the recompute overlapped with the adjoint),
+    one warm-up and one timed gradient each, L2 flushed before the timed one."""
+    import torch
+    from paper_2411_03090_gb300 import LKS
+
+    pb = inputs.config3()
+    gamma = torch.from_numpy(pb.gamma()).to(dev, torch.float32)
+    rows, g_plain = {}, None
+    for name, K, snap in (("plain_fp32", 0, "f32"), ("checkpointed_K100_bf16", 100, "bf16")):
+        s = LKS(pb, real="f32", checkpoint_every=K, snapshot=snap, device=dev)
+        s.gradient(gamma)
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        J, g = s.gradient(gamma)
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3
+        g = g.double()
+        rows[name] = {"s_per_gradient": t, "MLUPS": pb.n_nodes * 2 * pb.n_steps / t / 1e6,
+                      "workspace_GB": s.workspace.numel() / 1e9, "J": J.item()}
+        if g_plain is None:
+            g_plain = g
+        else:
+            rows[name]["grad_rel_err_vs_plain"] = (torch.linalg.vector_norm(g - g_plain)
+                                                   / torch.linalg.vector_norm(g_plain)).item()
+        del s, g
+        torch.cuda.empty_cache()
+    return {"workload": f"config3: 1024x512 unsteady thermal channel, {pb.n_steps} + {pb.n_adj} steps", **rows,
+            "updates_counted": "forward + adjoint levels (recomputation not counted)"}
+
+
+def also_config5(dev, flush):
+    """Config5 in brief for the default line: the 64-design batch (one graph launch
+    per batch of gradients, BF16 checkpoints, autotuned kernels) against the plain
+    FP32 form run design by design, one timed pass each after a warm-up."""
+    import torch
+    from paper_2411_03090_gb300 import LKS, LKSBatch
+
+    pbs = inputs.config5()
+    N, n_steps = sum(p.n_nodes for p in pbs), pbs[0].n_steps
+    gam = [torch.from_numpy(p.gamma().astype(np.float32)).to(dev) for p in pbs]
+    b = LKSBatch(pbs, snapshot="bf16", device=dev)
+    b.gradient(gam)
+    torch.cuda.synchronize()
+    flush.fill_(1.0)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    _, G = b.gradient(gam)
+    e1.record(b.stream)
+    torch.cuda.synchronize()
+    t_batch = e0.elapsed_time(e1) * 1e-3
+    st = b.query()
+    if st.device_status != 0:
+        raise RuntimeError(f"device status {st.device_status}")
+    Gb = [g.double() for g in G]
+    ws_batch = st.workspace_bytes / 1e9
+    del b, G
+    torch.cuda.empty_cache()
+    t_plain, errs, ws_plain = 0.0, [], 0
+    for k, p in enumerate(pbs):
+        s = LKS(p, real="f32", checkpoint_every=0, device=dev)
+        ws_plain += s.workspace.numel()
+        s.gradient(gam[k])
+        torch.cuda.synchronize()
+        flush.fill_(1.0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s.stream)
+        _, gp = s.gradient(gam[k])
+        e1.record(s.stream)
+        torch.cuda.synchronize()
+        t_plain += e0.elapsed_time(e1) * 1e-3
+        gp = gp.double()
+        errs.append((torch.linalg.vector_norm(Gb[k] - gp) / torch.linalg.vector_norm(gp)).item())
+        del s
+        torch.cuda.empty_cache()
+    return {"workload": f"config5: {len(pbs)} unsteady designs 128x64..512x256, {n_steps} + {n_steps} steps",
+            "batched_s_per_batch_gradient": t_batch, "batched_MLUPS": N * 2 * n_steps / t_batch / 1e6,
+            "batched_workspace_GB": ws_batch, "plain_fp32_s_design_by_design": t_plain,
+            "plain_workspace_GB_all_designs": ws_plain / 1e9, "speedup": t_plain / t_batch,
+            "grad_rel_err_vs_plain_max": max(errs)}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -542,7 +628,7 @@ def main():
     ap.add_argument("--fd-steps", type=int, default=30000,
                     help="config2fd: steps of each perturbed march from the converged base state")
     ap.add_argument("--no-also", action="store_true",
-                    help="config4: skip the config2 and 8192^2 figures carried on the same line")
+                    help="config4: skip the config2, 8192^2, config3 and config5 figures carried on the same line")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--steps-override", type=int, default=0)
@@ -604,6 +690,12 @@ def main():
             if name == "config2":
                 also[name]["roofline"]["note"] = ("working set (0.5 MB per field) resident in L2 and shared "
                                                   "memory: the fraction is of HBM, but the traffic is on chip")
+        if world == 1:  # the checkpointed and batched forms, once, on the single-GPU line
+            for name, fn in (("config3", also_config3), ("config5", also_config5)):
+                try:
+                    also[name] = fn(dev, flush)
+                except Exception as e:  # reported on the line, never silently dropped
+                    also[name] = {"error": f"{type(e).__name__}: {e}"}
 
     if rank != 0:
         if world > 1:
