@@ -1,6 +1,6 @@
 """Host models of the D3Q19 column kernels' tile indexing (fwd3p_kernel, adj3c_kernel).
 
-compute-sanitizer is not available on the GPU pool, so the shared-memory and global
+No memory checker runs over these kernels, so the shared-memory and global
 indices the kernel forms are checked here, on the CPU, for every lane, warp and
 tile of many lattice shapes: the staged box reads (rows and columns, including the
 one-sided differences on the faces), the exchange rows and columns written and
