@@ -57,7 +57,7 @@ METRIC = "forward+adjoint MLUPS & % HBM peak; s per gradient vs plain FP32 at 1e
 TRAFFIC_BYTES_PER_NODE = {
     "adj3c_kernel": 747.7e6 / 7077888,   # the 192^3 duct, 4 + 4 steps
     "fwd3p_kernel": 218.5e6 / 7077888,
-    "adj_col_kernel<true>": None,        # changed since its last capture
+    "adj_col_kernel<true>": 4.2666e9 / 67108864,  # the 8192^2 channel, 4 + 4 steps
     "fwd_col2_kernel<10>": 425.4e6 / 16777216,  # the 4096^2 channel, 4 + 4 steps
 }
 
