@@ -112,8 +112,7 @@ def test_segment_stores_are_written_before_read_and_not_overwritten_while_read(n
 
 def test_recompute_overlaps_the_adjoint_of_the_next_segment():
     """The schedule leaves the recompute of segment s - 1 unordered with the adjoint of
-    segment s (that is the overlap); with three stores' worth of ordering it would not
-    overlap at all."""
+    segment s: the two may run at the same time (that is the overlap)."""
     n_seg = 6
     ops, idx, hb = _replay(n_seg)
     for s in range(1, n_seg):
