@@ -11,8 +11,9 @@ CSRC = os.path.join(HERE, "csrc")
 LIB_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(LIB_DIR, "liblks.so")
 SOURCES = [os.path.join(CSRC, "lks_capi.cu"), os.path.join(CSRC, "lks_batch.cu"), os.path.join(CSRC, "lks_3d.cu")]
-DEPS = SOURCES + [os.path.join(CSRC, h) for h in ("lks_kernels.cuh", "lks_resident.cuh", "lks_resident_tb.cuh", "lks_tma.cuh",
-                                                   "lks_host.cuh", "lks_3d.cuh")] + [os.path.join(ROOT, "include", "lks.h")]
+# every header in csrc/ (a new one is picked up without listing it) and the C ABI
+DEPS = SOURCES + sorted(os.path.join(CSRC, h) for h in os.listdir(CSRC) if h.endswith(".cuh")) + [
+    os.path.join(ROOT, "include", "lks.h")]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 _lock = threading.Lock()
 
