@@ -261,7 +261,13 @@ def edge_objective_map(A: float, cls: int) -> np.ndarray:
 
 class LKS:
     """One problem on one device: owns its workspace (a torch uint8 tensor) and the
-    library handle.  Fields are (ny, nx) tensors of the descriptor's real type."""
+    library handle.  Fields are (ny, nx) tensors of the descriptor's real type.
+
+    Every call enqueues its kernels on ``stream`` (torch's current stream when the
+    handle was made, unless one is given) and reads its input tensors there.  A
+    caller that fills them on another stream orders the two first
+    (``h.stream.wait_stream(other)``); a tensor of another dtype, shape or device
+    is converted on torch's current stream."""
 
     def __init__(self, pb, real: str = "f32", checkpoint_every: int = 0, snapshot: str = "f32",
                  device: Optional[torch.device] = None, stream: Optional[torch.cuda.Stream] = None,
