@@ -222,7 +222,8 @@ def run_reference(args):
     dt = sum(times)
     value = pb.n_nodes * (n_f + n_a) * args.steps / dt / 1e6
     cb = {"value": value, "unit": "MLUPS", "cores": O.get_threads(), "kind": "oracle",
-          "sample": f"each step: {pb.nx}x{pb.ny} lattice, {n_f} forward + {n_a} adjoint steps (FP64)"}
+          "sample": f"each step: {pb.nx}x{pb.ny}{'x%d' % pb.nz if three_d else ''} lattice, "
+                    f"{n_f} forward + {n_a} adjoint steps from rest (FP64)"}
     print(json.dumps({
         "impl": "reference", "metric": METRIC, "value": value, "unit": "MLUPS", "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / args.steps,
