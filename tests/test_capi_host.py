@@ -138,6 +138,55 @@ def test_descriptor_validation():
         assert lks.workspace_size(lks.make_desc(pb, res_steps=ks)) == lks.workspace_size(d)
 
 
+@pytest.mark.parametrize("field,val", [("nx", 0), ("ny", 0), ("nx", -8), ("ny", 4), ("nz", 2), ("n_adj", 0),
+                                       ("checkpoint_every", -1), ("snapshot_type", 3), ("exec_path", 4),
+                                       ("exec_path", -1), ("nu", float("nan")), ("nu", 0.5), ("q_alpha", 0.0),
+                                       ("in_y0", -1), ("in_y1", 10**6), ("out_y0", 0)])
+def test_degenerate_descriptors_are_refused(field, val):
+    """Empty, negative and out-of-range fields of a D2Q9 descriptor: refused with
+    LKS_ERR_INVALID_ARG before any device work."""
+    bad = lks.make_desc(inputs.config1())
+    setattr(bad, field, val)
+    n = C.c_size_t(123)
+    assert lks.load().lks_workspace_size(C.byref(bad), C.byref(n)) == 1
+
+
+@pytest.mark.parametrize("field,val", [("nx", 4), ("nz", 0), ("nz", -3), ("n_steps", 0), ("n_adj", 0),
+                                       ("res_steps", 1), ("warm_start", 1), ("thermal", 1)])
+def test_degenerate_d3q19_descriptors_are_refused(field, val):
+    bad = lks.make_desc(inputs.config4())
+    setattr(bad, field, val)
+    with pytest.raises(lks.LKSError) as e:
+        lks.workspace_size(bad)
+    assert e.value.status == 1
+
+
+def test_largest_lattices_are_sized_without_overflow():
+    """The node count is limited to 2^31 (the kernels' node indices); at that limit the
+    workspace is computed in 64-bit arithmetic: it grows with the lattice and holds at
+    least two levels of the state and of the adjoint fields of every node."""
+    pb = inputs.config1()
+    small = lks.make_desc(pb)
+    big = lks.make_desc(pb)
+    big.nx, big.ny = 46340, 46340  # 2.147e9 nodes, just under 2^31
+    big.in_y0, big.in_y1, big.out_y0, big.out_y1 = 0, 46339, 1, 46338
+    n_small, n_big = lks.workspace_size(small), lks.workspace_size(big)
+    nodes = 46340 * 46340
+    assert n_big > n_small and n_big >= nodes * 4 * 2 * (3 + 6)  # FP32: delta-rho, u, v and six adjoint fields
+    over = lks.make_desc(pb)
+    over.nx, over.ny = 65536, 32769  # 2^31 + 65536 nodes
+    over.in_y0, over.in_y1, over.out_y0, over.out_y1 = 0, 32768, 1, 32767
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(over)
+    d3 = lks.make_desc(inputs.config4())
+    d3.nx = d3.ny = d3.nz = 1291  # 2.15e9 nodes > 2^31
+    with pytest.raises(lks.LKSError):
+        lks.workspace_size(d3)
+    d3.nx = d3.ny = d3.nz = 1290  # 2.147e9 nodes
+    # FP32: two levels of delta-rho, u, v, w and of the ten adjoint fields, and four coefficient fields
+    assert lks.workspace_size(d3) >= 1290 ** 3 * 4 * (2 * (4 + 10) + 4)
+
+
 def test_workspace_grows_with_checkpoint_storage():
     p3 = inputs.config3().with_(nx=64, ny=32, n_steps=1000)
     plain = lks.workspace_size(lks.make_desc(p3, checkpoint_every=0))
