@@ -6,7 +6,9 @@ sensitivity).  Default workload: the 192^3 D3Q19 duct, Re = 50, 1000 forward + 1
 adjoint steps, FP32, objective dissipation + static pressure drop (the largest
 single-GPU configuration of the paper-derived set, 7.08 M nodes, working set far
 larger than L2).  The same line carries, under "also", the 512 x 256 channel
-(config2, L2-resident) and the 8192^2 channel (67 M nodes) measured the same way.
+(config2, L2-resident) and the 8192^2 channel (67 M nodes) measured the same way,
+and on one GPU config3 (plain FP32 against K = 100 BF16 checkpoints) and config5
+(the 64-design batch against the plain form design by design) in brief.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
                     [--workload config4|config2|roofline8192|config1|config3|config5]
